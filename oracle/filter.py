@@ -1,0 +1,257 @@
+"""FP64 oracle of the particle-filter steps (test infrastructure only).
+
+Sec. 3 of the paper: likelihood weights (Eq. loglikeq), effective sample size
+(Eq. ess), adaptive tempering (Sec. 3.1.2), systematic resampling
+(Sec. 3.1.1, Gordon et al. 1993), PCN jittering of the noise increments
+(Sec. 3.1.2), the discrete Girsanov weight of a nudged path
+(Eq. girsanov DG approx) and the diagnostics EMRE, RB, RES (Sec. 4.1.1).
+
+Readings of the text that the code fixes:
+* observation points are the M distinct nodes x_j = j L / M, j = 0..M-1;
+* the Girsanov log-weight of increments dW drawn under drift lambda is
+  logG = -sum_{n<Ns} sum_k (lambda_k^n dW_k^n + 1/2 (lambda_k^n)^2 dt), the
+  ratio of the N(0, dt) prior density to the proposal density of the increment
+  actually applied (dW + lambda dt); "W~ = W + G" is addition of logs;
+* the negative log-weight of a particle is phi = NLL - logG (= -log W~);
+* tempering keeps the largest dtheta in (0, 1 - theta] whose tempered weights
+  exp(-dtheta phi) have ESS >= N*, by 60 bisection steps on [0, 1 - theta];
+* PCN accepts with probability min(1, exp(w0 - w1)), w = theta phi (the
+  theta-adjusted weight with W replaced by W~);
+* systematic resampling runs on exact integers (see ``systematic_resample``).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from oracle import rng as _rng
+
+
+# ---------------------------------------------------------------------- #
+# weights
+# ---------------------------------------------------------------------- #
+def obs_indices(n: int, M: int) -> np.ndarray:
+    """Node indices of the M observation points x_j = j L / M."""
+    return np.arange(M) * (n // M)
+
+
+def nll(u: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:
+    """Negative log of Eq. loglikeq: 1/2 sum_j ((u(x_j) - y_j) / sigma)^2 for each particle."""
+    u = np.atleast_2d(np.asarray(u, dtype=np.float64))
+    M = len(y)
+    idx = obs_indices(u.shape[1], M)
+    r = (u[:, idx] - np.asarray(y, dtype=np.float64)[None, :]) / sigma
+    return 0.5 * np.sum(r * r, axis=1)
+
+
+def girsanov_logG(lam: np.ndarray, dW: np.ndarray, dt: float) -> np.ndarray:
+    """log G = -sum_n sum_k (lambda dW + 1/2 lambda^2 dt) per particle (Eq. girsanov DG approx)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    dW = np.asarray(dW, dtype=np.float64)
+    axes = tuple(range(1, lam.ndim))
+    return -np.sum(lam * dW + 0.5 * lam * lam * dt, axis=axes)
+
+
+def normalise(logw: np.ndarray) -> np.ndarray:
+    """w_bar = w / sum w from log-weights, shifted by the maximum."""
+    lw = np.asarray(logw, dtype=np.float64)
+    w = np.exp(lw - np.max(lw))
+    return w / np.sum(w)
+
+
+def ess(logw: np.ndarray) -> float:
+    """Eq. ess: ESS = 1 / sum w_bar^2."""
+    wb = normalise(logw)
+    return float(1.0 / np.sum(wb * wb))
+
+
+def temper(phi: np.ndarray, theta: float, ess_min: float, iters: int = 60):
+    """Adaptive tempering step (Sec. 3.1.2).
+
+    Largest dtheta in (0, 1 - theta] with ESS(exp(-dtheta phi)) >= ess_min.
+    If the whole remaining step passes it is taken; otherwise bisection on
+    [0, 1 - theta] for ``iters`` steps keeps the largest passing point.  If
+    even the smallest point tried fails (only possible for astronomically
+    spread phi), the smallest point tried is returned, so tempering always
+    advances.  Returns (dtheta, w_bar at dtheta, ESS at dtheta).
+    """
+    phi = np.asarray(phi, dtype=np.float64)
+    rest = 1.0 - theta
+    if ess(-rest * phi) >= ess_min:
+        d = rest
+    else:
+        lo, hi = 0.0, rest
+        for _ in range(iters):
+            mid = 0.5 * (lo + hi)
+            if ess(-mid * phi) >= ess_min:
+                lo = mid
+            else:
+                hi = mid
+        d = lo if lo > 0.0 else hi
+    return d, normalise(-d * phi), ess(-d * phi)
+
+
+# ---------------------------------------------------------------------- #
+# systematic resampling on integers
+# ---------------------------------------------------------------------- #
+RESAMPLE_QBITS = 50
+RESAMPLE_UBITS = 53
+
+
+def systematic_resample(wbar: np.ndarray, u53: int) -> np.ndarray:
+    """Systematic resampling (Gordon et al. 1993) in exact integer arithmetic.
+
+    Quantise q_i = floor(w_bar_i 2^50), T = sum q, C_j = q_0 + .. + q_j.
+    Slot i takes the smallest j with C_j > floor((i 2^53 + U) T / (N 2^53)),
+    U = u53 in [0, 2^53): the positions (i + U 2^-53) / N of systematic
+    resampling, scaled to the integer total T.  Every value is an integer, so
+    the offspring indices do not depend on the summation order.
+    """
+    wbar = np.asarray(wbar, dtype=np.float64)
+    N = len(wbar)
+    q = [int(math.floor(float(w) * 2.0 ** RESAMPLE_QBITS)) for w in wbar]
+    if any(v < 0 for v in q):
+        raise ValueError("negative weight")
+    C = []
+    acc = 0
+    for v in q:
+        acc += v
+        C.append(acc)
+    T = acc
+    if T == 0:
+        raise ValueError("all quantised weights are zero")
+    idx = np.empty(N, dtype=np.int64)
+    scale = N << RESAMPLE_UBITS
+    j = 0
+    for i in range(N):
+        t = ((i << RESAMPLE_UBITS) + int(u53)) * T // scale
+        while C[j] <= t:
+            j += 1
+        idx[i] = j
+    return idx
+
+
+def resample_offset(seed: int, stage_ctr: int) -> int:
+    return _rng.u53_int(seed, _rng.TAG_RESAMPLE, stage_ctr)
+
+
+# ---------------------------------------------------------------------- #
+# PCN jittering
+# ---------------------------------------------------------------------- #
+def pcn_rho(delta: float) -> float:
+    """rho = (2 - delta) / (2 + delta); then sqrt(1 - rho^2) = sqrt(8 delta) / (2 + delta)."""
+    return (2.0 - delta) / (2.0 + delta)
+
+
+def pcn_propose(dW: np.ndarray, dW_hat: np.ndarray, rho: float) -> np.ndarray:
+    """dW -> rho dW + sqrt(1 - rho^2) dW_hat, dW_hat a fresh N(0, dt) draw (Sec. 3.1.2)."""
+    return rho * dW + math.sqrt(1.0 - rho * rho) * dW_hat
+
+
+def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, state=None,
+           particle0=0):
+    """n_iter PCN moves of every particle's window noise at temperature theta.
+
+    For iteration j the proposal noise is keyed (seed, TAG_PCN, ctr + j) and the
+    accept uniform (seed, TAG_PCN_ACCEPT, ctr + j).  The proposal is run through
+    the whole window from m_start; it is accepted iff log U < w0 - w1 with
+    w = theta (NLL - logG).  ``state`` = (nll, logG, m_end, u_end) of the
+    current noise, recomputed when omitted.
+    Returns (dW, nll, logG, m_end, u_end, accepts).
+    """
+    N, Ns, K = dW.shape
+    dW = np.array(dW, dtype=np.float64)
+    lam_arr = np.zeros_like(dW) if lam is None else np.asarray(lam, dtype=np.float64)
+    if state is None:
+        m_end, u_end, _, _ = model.ensemble_window(m_start, dW, lam_arr)
+        cur_nll = nll(u_end, y, sigma)
+        cur_logG = girsanov_logG(lam_arr, dW, model.dt)
+    else:
+        cur_nll, cur_logG, m_end, u_end = (np.array(v, dtype=np.float64) for v in state)
+    accepts = np.zeros(N, dtype=np.int64)
+    for j in range(n_iter):
+        hat = _rng.window_increments(seed, _rng.TAG_PCN, N, Ns, K, model.dt, ctr + j, particle0)
+        prop = pcn_propose(dW, hat, rho)
+        pm, pu, _, _ = model.ensemble_window(m_start, prop, lam_arr)
+        p_nll = nll(pu, y, sigma)
+        p_logG = girsanov_logG(lam_arr, prop, model.dt)
+        w0 = theta * (cur_nll - cur_logG)
+        w1 = theta * (p_nll - p_logG)
+        pidx = np.arange(particle0, particle0 + N, dtype=np.uint64)
+        logU = np.log(_rng.uniform_open0(seed, _rng.TAG_PCN_ACCEPT, pidx, np.uint64(ctr + j)))
+        acc = logU < (w0 - w1)
+        dW[acc] = prop[acc]
+        cur_nll[acc] = p_nll[acc]
+        cur_logG[acc] = p_logG[acc]
+        m_end[acc] = pm[acc]
+        u_end[acc] = pu[acc]
+        accepts += acc
+    return dW, cur_nll, cur_logG, m_end, u_end, accepts
+
+
+# ---------------------------------------------------------------------- #
+# diagnostics (Sec. 4.1.1)
+# ---------------------------------------------------------------------- #
+def emre(u_truth, u_ens) -> float:
+    """(1/N) sum_n |u_a - u_n| / |u_a| (Euclidean norms over nodes)."""
+    ua = np.asarray(u_truth, dtype=np.float64)
+    return float(np.mean(np.linalg.norm(u_ens - ua[None, :], axis=1)) / np.linalg.norm(ua))
+
+
+def rb(u_truth, u_ens) -> float:
+    """|u_a - mean_n u_n| / |u_a|."""
+    ua = np.asarray(u_truth, dtype=np.float64)
+    return float(np.linalg.norm(ua - np.mean(u_ens, axis=0)) / np.linalg.norm(ua))
+
+
+def res(u_truth, u_ens) -> float:
+    """(1/(N-1)) sum_n |u_n - mean u| / |u_a|."""
+    ua = np.asarray(u_truth, dtype=np.float64)
+    mean = np.mean(u_ens, axis=0)
+    N = u_ens.shape[0]
+    return float(np.sum(np.linalg.norm(u_ens - mean[None, :], axis=1)) / (N - 1) / np.linalg.norm(ua))
+
+
+# ---------------------------------------------------------------------- #
+# one assimilation cycle (bootstrap forecast, then temper + resample + jitter)
+# ---------------------------------------------------------------------- #
+def assimilation_cycle(model, m_start, y, sigma, ess_min, rho, n_jitter, seed, cycle,
+                       lam=None, dW=None, max_stages=64):
+    """One cycle of Sec. 3.1.2 on the (X_start, dW) representation.
+
+    dW is drawn from (seed, TAG_PRIOR_DW, cycle) unless given.  Stage k tempers
+    with the incremental weight exp(-dtheta phi), resamples (X_start, dW, lambda,
+    phi) with offset keyed (seed, TAG_RESAMPLE, cycle * 1024 + k), then jitters
+    with PCN counters starting at (cycle * 1024 + k) * n_jitter.  Returns a dict
+    with the end-of-window state of every particle and per-stage statistics.
+    """
+    N = m_start.shape[0]
+    m_start = np.array(m_start, dtype=np.float64)
+    if dW is None:
+        raise ValueError("pass dW explicitly (window_increments)")
+    dW = np.array(dW, dtype=np.float64)
+    Ns = dW.shape[1]
+    lam_arr = np.zeros_like(dW) if lam is None else np.array(lam, dtype=np.float64)
+    m_end, u_end, iters, _ = model.ensemble_window(m_start, dW, lam_arr)
+    cur_nll = nll(u_end, y, sigma)
+    cur_logG = girsanov_logG(lam_arr, dW, model.dt)
+    theta = 0.0
+    stages = []
+    k = 0
+    while theta < 1.0 and k < max_stages:
+        phi = cur_nll - cur_logG
+        d, wbar, e = temper(phi, theta, ess_min)
+        stage_ctr = cycle * 1024 + k
+        idx = systematic_resample(wbar, resample_offset(seed, stage_ctr))
+        m_start, dW, lam_arr = m_start[idx], dW[idx], lam_arr[idx]
+        cur_nll, cur_logG = cur_nll[idx], cur_logG[idx]
+        m_end, u_end = m_end[idx], u_end[idx]
+        theta = 1.0 if d >= 1.0 - theta else theta + d
+        dW, cur_nll, cur_logG, m_end, u_end, acc = jitter(
+            model, m_start, dW, lam_arr, y, sigma, theta, rho, n_jitter, seed,
+            stage_ctr * n_jitter, state=(cur_nll, cur_logG, m_end, u_end))
+        stages.append(dict(dtheta=d, ess=e, theta=theta, accept_rate=float(acc.sum()) / (N * n_jitter)))
+        k += 1
+    return dict(m_end=m_end, u_end=u_end, dW=dW, lam=lam_arr, nll=cur_nll, logG=cur_logG,
+                stages=stages, Ns=Ns)

@@ -1,0 +1,187 @@
+"""Pins for the oracle's SCH discretisation (oracle/model.py).
+
+Each test checks the oracle against something the paper and the mathematics
+fix, not against a retyped copy of its own formulas:
+* cyclic tridiagonal solves against a dense LAPACK solve;
+* the P1 mass / stiffness symbols and the Helmholtz relation (Eq. sde1) on
+  discrete Fourier modes, where they are exact, and their continuum limit;
+* the closed-form element assembly against 3-point Gauss quadrature of the
+  weak form of Eq. fde1, and the fixed point of the step against that residual;
+* the linearised viscous decay of Fourier modes (closed-form amplification);
+* exact conservation of H = 1/2 (m, u) by the midpoint rule at mu = 0 with no
+  noise, and refinement behaviour of (m, 1);
+* a travelling CH peakon keeping its speed c.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.model import Model
+
+
+def make(n=64, L=40.0, alpha=1.0, mu=0.02, dt=0.025, K=4, tol=1e-13):
+    return Model(L=L, n=n, alpha=alpha, mu=mu, dt=dt, amps=np.full(K // 2, 0.05), tol=tol)
+
+
+def test_cyclic_solve_matches_dense():
+    r = np.random.default_rng(0)
+    for n in (3, 4, 7, 32):
+        a, c = r.normal(size=n), r.normal(size=n)
+        b = np.abs(a) + np.abs(c) + 1.0 + r.random(n)
+        d = r.normal(size=n)
+        x = Model.solve((a, b, c), d)
+        ref = np.linalg.solve(Model.dense((a, b, c)), d)
+        assert np.allclose(x, ref, rtol=1e-13, atol=1e-13)
+
+
+def _fourier(n, j):
+    i = np.arange(n)
+    return np.cos(2 * math.pi * j * i / n), 2 * math.pi * j / n
+
+
+@pytest.mark.parametrize("j", [0, 1, 5, 17])
+def test_mass_stiffness_symbols(j):
+    m = make(n=64)
+    v, th = _fourier(m.n, j)
+    Mv = Model.apply(m.mass(), v)
+    Kv = Model.apply(m.stiffness(), v)
+    assert np.allclose(Mv, m.h / 6 * (4 + 2 * math.cos(th)) * v, atol=1e-14)
+    assert np.allclose(Kv, (2 - 2 * math.cos(th)) / m.h * v, atol=1e-12)
+
+
+@pytest.mark.parametrize("j", [1, 3, 11])
+def test_helmholtz_on_fourier_modes(j):
+    m = make(n=128, alpha=1.3)
+    v, th = _fourier(m.n, j)
+    Mh = m.h / 6 * (4 + 2 * math.cos(th))
+    Kh = (2 - 2 * math.cos(th)) / m.h
+    ratio = (Mh + m.alpha ** 2 * Kh) / Mh
+    assert np.allclose(m.m_from_u(v), ratio * v, rtol=0, atol=1e-13 * ratio)
+    assert np.allclose(m.u_from_m(v), v / ratio, rtol=0, atol=1e-14)
+
+
+def test_helmholtz_continuum_limit():
+    # m/u -> 1 + alpha^2 k^2 with O(h^2) error for the fixed physical wavenumber k
+    errs = []
+    for n in (64, 128, 256):
+        m = make(n=n)
+        v, _ = _fourier(n, 3 * n // 64)
+        v, _ = _fourier(n, 3)
+        k = 2 * math.pi * 3 / m.L
+        ratio = m.m_from_u(v)[0] / v[0]
+        errs.append(abs(ratio - (1 + k * k)))
+    assert errs[1] < errs[0] / 3.5 and errs[2] < errs[1] / 3.5
+
+
+def test_assembly_matches_gauss_quadrature():
+    r = np.random.default_rng(1)
+    m = make(n=16)
+    m0, m1, dU = r.normal(size=(3, m.n))
+    u0, u1 = m.u_from_m(m0), m.u_from_m(m1)
+    R = m.residual(m1, m0, u1, u0, dU)
+    Rq = m.residual_quadrature(m1, m0, dU)
+    assert np.allclose(R, Rq, rtol=0, atol=1e-13 * np.max(np.abs(Rq)))
+
+
+def test_step_solves_fde1():
+    r = np.random.default_rng(2)
+    m = make(n=32)
+    x = m.x
+    u0 = 0.2 / np.cosh(x - 27) + 0.5 / np.cosh(x - 13)
+    m0 = m.m_from_u(u0)
+    dU = m.noise(r.normal(scale=math.sqrt(m.dt), size=m.K), r.normal(size=m.K))
+    m1, u1, it, ok = m.step(m0, u0, dU)
+    assert ok and 2 <= it < 30
+    Rq = m.residual_quadrature(m1, m0, dU)
+    scale = np.max(np.abs(m.residual_quadrature(m0 + 0.0, m0, 0 * dU))) + np.max(np.abs(Model.apply(m.mass(), m1 - m0)))
+    assert np.max(np.abs(Rq)) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("j", [1, 4, 9])
+def test_linear_viscous_decay(j):
+    m = make(n=128, mu=0.05)
+    v, th = _fourier(m.n, j)
+    eps = 1e-8
+    m0 = eps * v
+    m1, _, _, ok = m.step(m0, m.u_from_m(m0), np.zeros(m.n))
+    Mh = m.h / 6 * (4 + 2 * math.cos(th))
+    Kh = (2 - 2 * math.cos(th)) / m.h
+    g = (Mh - 0.5 * m.mu * m.dt * Kh) / (Mh + 0.5 * m.mu * m.dt * Kh)
+    assert ok
+    assert np.max(np.abs(m1 - g * m0)) <= 1e-7 * eps
+
+
+def test_viscous_decay_continuum_limit():
+    # the per-step amplification tends to exp(-mu k^2 dt) as h -> 0 (O(h^2) in space)
+    j, mu, dt, L = 3, 0.05, 0.025, 40.0
+    k = 2 * math.pi * j / L
+    errs = []
+    for n in (64, 256):
+        th = 2 * math.pi * j / n
+        h = L / n
+        Mh = h / 6 * (4 + 2 * math.cos(th))
+        Kh = (2 - 2 * math.cos(th)) / h
+        g = (Mh - 0.5 * mu * dt * Kh) / (Mh + 0.5 * mu * dt * Kh)
+        m = make(n=n, mu=mu)
+        v, _ = _fourier(n, j)
+        m1, _, _, _ = m.step(1e-8 * v, m.u_from_m(1e-8 * v), np.zeros(n))
+        assert abs(m1[0] / (1e-8 * v[0]) - g) < 1e-9
+        errs.append(abs(g - math.exp(-mu * k * k * dt)))
+    assert errs[1] < errs[0] / 10
+
+
+def test_energy_conserved_inviscid_noiseless():
+    m = make(n=128, mu=0.0)
+    x = m.x
+    u0 = 0.2 / np.cosh(x - 27) + 0.5 / np.cosh(x - 13)
+    m0 = m.m_from_u(u0)
+    E0 = m.energy(m0)
+    mm, uu = m0, u0
+    for _ in range(20):
+        mm, uu, _, ok = m.step(mm, uu, np.zeros(m.n))
+        assert ok
+    assert abs(m.energy(mm) - E0) <= 1e-11 * E0
+    # with viscosity the energy decays
+    mv = make(n=128, mu=0.05)
+    m2, _, _, _ = mv.window(m0, np.zeros((20, mv.K)))
+    assert mv.energy(m2) < E0
+
+
+def test_momentum_integral_drift_shrinks_with_refinement():
+    drifts = []
+    for n in (64, 256):
+        m = make(n=n, mu=0.0)
+        x = m.x
+        u0 = 0.2 / np.cosh(x - 27) + 0.5 / np.cosh(x - 13)
+        m0 = m.m_from_u(u0)
+        m1, _, _, _ = m.window(m0, np.zeros((40, m.K)))
+        drifts.append(abs(m.mass_integral(m1) - m.mass_integral(m0)))
+    assert drifts[1] < drifts[0] / 4 or drifts[1] < 1e-13
+
+
+@pytest.mark.slow
+def test_peakon_speed():
+    L, alpha, c = 40.0, 1.0, 0.5
+    n = 1024
+    m = make(n=n, L=L, alpha=alpha, mu=0.0)
+    x = m.x
+    x0 = 10.0
+    d = np.mod(x - x0, L)
+    u0 = c * np.cosh((d - L / 2) / alpha) / np.cosh(L / (2 * alpha))
+    mm = m.m_from_u(u0)
+    uu = u0
+    T = 10.0
+    nsteps = int(round(T / m.dt))
+    for _ in range(nsteps):
+        mm, uu, _, ok = m.step(mm, uu, np.zeros(n))
+        assert ok
+    # crest: the peak of u, refined by the intersection of the two straight flanks
+    i = int(np.argmax(uu))
+    sl = (uu[i - 1] - uu[i - 3]) / (2 * m.h)
+    sr = (uu[i + 3] - uu[i + 1]) / (2 * m.h)
+    xl, xr = x[i - 2], x[i + 2]
+    ul, ur = uu[i - 2], uu[i + 2]
+    xc = (ur - ul + sl * xl - sr * xr) / (sl - sr)
+    speed = (xc - x0) / T
+    assert abs(speed - c) < 0.02 * c

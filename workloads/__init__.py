@@ -1,0 +1,181 @@
+"""Seeded synthetic workloads shared by the CUDA path, the oracle tests and the bench.
+
+This module holds the problem configurations and the seeded random inputs
+(particle states, noise increments, drifts, observation vectors) used to
+exercise the particle filter for the viscous stochastic Camassa-Holm (SALT)
+equation.  It contains none of the method's arithmetic: no finite-element
+operator, no time step, no weight, no resampling rule.  Everything here is an
+input description that both implementations receive unchanged.
+
+Workloads (all synthetic twin experiments; the paper uses no public dataset):
+
+* ``cfg1_f64``  plain method, FP64: L=40, n=256, alpha=1, mu=0.02, dt=0.025,
+  K=4 mode functions (wavenumbers 1..2, sin and cos, amplitude 0.05), M=32
+  observation points, sigma=0.05, N=32 particles, 5 steps per window,
+  5 jitter steps per tempering stage, rho from delta=0.15 (Sec. 4.1.3).
+* ``cfg2_f32``  ensemble scale, FP32 fields / FP64 weights: n=1024, K=8
+  (wavenumbers 1..4, amplitude 0.05/j), N=1024, 10 steps per window, M=64,
+  sigma=0.05, ESS threshold N/2, 10 jitter steps, rho=0.9999.
+* ``cfg3_f64``  nudging, FP64: n=1024, K=8, N=256, 20-step window.
+* ``cfg4_f32``  learned proposal: n=1024, K=16, 20-step window, N=1024.
+* ``cfg5_f32``  large run: n=4096, K=32, N=8192, M=128, sigma=0.02.
+
+The initial truth is u0(x) = 0.2 sech(x-27) + 0.5 sech(x-13) on [0, 40).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "Config", "CONFIGS", "get_config", "node_coords", "u0_profile",
+    "mode_amplitudes", "random_state", "random_increments", "random_drift",
+    "random_obs", "random_logweights",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Config:
+    name: str
+    L: float = 40.0
+    n: int = 256            # cells == nodes on the periodic P1 mesh
+    alpha: float = 1.0
+    mu: float = 0.02
+    dt: float = 0.025
+    K: int = 4              # number of noise mode functions (sin/cos pairs)
+    amp0: float = 0.05
+    amp_rule: str = "const"  # "const": a_j = amp0 ; "inv_j": a_j = amp0 / j
+    Ns: int = 5             # model steps per assimilation window
+    M: int = 32             # observation points (equispaced nodes)
+    sigma: float = 0.05
+    N: int = 32             # particles
+    cycles: int = 20
+    ess_frac: float = 0.5   # N* = ess_frac * N
+    n_jitter: int = 5
+    rho: float = (2.0 - 0.15) / (2.0 + 0.15)   # PCN rho from delta = 0.15
+    dtype: str = "f64"      # field precision: "f64" or "f32"
+    tol: float = 1e-13      # Picard stopping tolerance (relative, max norm)
+    max_iter: int = 60
+    prior_scale: float = 0.05
+    seed: int = 0
+
+    @property
+    def h(self) -> float:
+        return self.L / self.n
+
+    @property
+    def obs_stride(self) -> int:
+        return self.n // self.M
+
+    @property
+    def ess_min(self) -> float:
+        return self.ess_frac * self.N
+
+    def replace(self, **kw) -> "Config":
+        return dataclasses.replace(self, **kw)
+
+    def check(self) -> None:
+        if self.n % self.M != 0:
+            raise ValueError("observation points must fall on nodes (n % M == 0)")
+        if self.K % 2 != 0:
+            raise ValueError("K counts sin/cos pairs, so it must be even")
+
+
+CONFIGS = {
+    "cfg1_f64": Config(name="cfg1_f64"),
+    "cfg2_f32": Config(name="cfg2_f32", n=1024, K=8, amp_rule="inv_j", Ns=10, M=64,
+                       sigma=0.05, N=1024, n_jitter=10, rho=0.9999, dtype="f32",
+                       tol=1e-6, max_iter=40),
+    "cfg3_f64": Config(name="cfg3_f64", n=1024, K=8, amp_rule="inv_j", Ns=20, M=64,
+                       sigma=0.05, N=256, n_jitter=5),
+    "cfg4_f32": Config(name="cfg4_f32", n=1024, K=16, amp_rule="inv_j", Ns=20, M=64,
+                       sigma=0.05, N=1024, n_jitter=10, rho=0.9999, dtype="f32",
+                       tol=1e-6, max_iter=40),
+    "cfg5_f32": Config(name="cfg5_f32", n=4096, K=32, amp_rule="inv_j", Ns=10, M=128,
+                       sigma=0.02, N=8192, cycles=50, n_jitter=10, rho=0.9999,
+                       dtype="f32", tol=1e-6, max_iter=40),
+}
+
+
+def get_config(name: str, **overrides) -> Config:
+    cfg = CONFIGS[name]
+    if overrides:
+        cfg = cfg.replace(**overrides)
+    cfg.check()
+    return cfg
+
+
+def node_coords(cfg: Config) -> np.ndarray:
+    """x_i = i h, i = 0..n-1 (periodic, x_n == x_0)."""
+    return np.arange(cfg.n, dtype=np.float64) * cfg.h
+
+
+def _sech(z):
+    return 1.0 / np.cosh(z)
+
+
+def u0_profile(cfg: Config) -> np.ndarray:
+    """Nodal values of the twin-experiment truth u0 = 0.2 sech(x-27) + 0.5 sech(x-13)."""
+    x = node_coords(cfg)
+    return 0.2 * _sech(x - 27.0) + 0.5 * _sech(x - 13.0)
+
+
+def mode_amplitudes(cfg: Config) -> np.ndarray:
+    """a_j, j = 1..K/2 (amplitude of the sin and cos functions of wavenumber j)."""
+    j = np.arange(1, cfg.K // 2 + 1, dtype=np.float64)
+    if cfg.amp_rule == "const":
+        return np.full(cfg.K // 2, cfg.amp0)
+    if cfg.amp_rule == "inv_j":
+        return cfg.amp0 / j
+    raise ValueError(cfg.amp_rule)
+
+
+def random_state(cfg: Config, N: int, seed: int, scale: float = 0.05) -> np.ndarray:
+    """Seeded smooth perturbations of u0 on the nodes: [N, n] float64.
+
+    A few random low Fourier modes per particle, so the states look like the
+    paper's smooth particle clouds around the truth.  Used as the *velocity*
+    of parity-test states; each implementation turns it into momentum itself.
+    """
+    rng = np.random.default_rng(seed)
+    x = node_coords(cfg)
+    base = u0_profile(cfg)
+    out = np.empty((N, cfg.n))
+    for p in range(N):
+        pert = np.zeros(cfg.n)
+        for j in range(1, 5):
+            a, b = rng.normal(size=2) / j
+            pert += a * np.sin(2 * math.pi * j * x / cfg.L) + b * np.cos(2 * math.pi * j * x / cfg.L)
+        out[p] = base + scale * pert + scale * rng.normal()
+    return out
+
+
+def random_increments(cfg: Config, N: int, seed: int, steps: Optional[int] = None) -> np.ndarray:
+    """dW ~ N(0, dt) iid: [N, Ns, K] float64."""
+    steps = cfg.Ns if steps is None else steps
+    rng = np.random.default_rng(seed)
+    return rng.normal(scale=math.sqrt(cfg.dt), size=(N, steps, cfg.K))
+
+
+def random_drift(cfg: Config, N: int, seed: int, scale: float = 0.3,
+                 steps: Optional[int] = None) -> np.ndarray:
+    """A synthetic nudging drift lambda: [N, Ns, K] float64."""
+    steps = cfg.Ns if steps is None else steps
+    rng = np.random.default_rng(seed)
+    return rng.normal(scale=scale, size=(N, steps, cfg.K))
+
+
+def random_obs(cfg: Config, seed: int, noise: Optional[float] = None) -> np.ndarray:
+    """Synthetic observation vector y [M]: u0 at the observation nodes plus noise."""
+    rng = np.random.default_rng(seed)
+    noise = cfg.sigma if noise is None else noise
+    return u0_profile(cfg)[:: cfg.obs_stride][: cfg.M] + rng.normal(scale=noise, size=cfg.M)
+
+
+def random_logweights(N: int, seed: int, spread: float = 5.0) -> np.ndarray:
+    """Seeded negative log-weights phi [N] (spread controls degeneracy)."""
+    rng = np.random.default_rng(seed)
+    return rng.gamma(2.0, spread, size=N)
