@@ -1,0 +1,348 @@
+"""Benchmark: assimilation cycles of the SCH particle filter on one GB300.
+
+One step = one assimilation cycle over the whole ensemble: draw the window
+noise, propagate every particle through the window (fused likelihood), then
+adaptive tempering, systematic resampling and PCN jittering until the
+temperature reaches one.  Workload: n = 1024 cells, K = 8 SALT modes
+(amplitude 0.05/j), N = 1024 particles, 10 steps per window, 64 observations
+(sigma 0.05), ESS threshold N/2, 10 jitter steps per stage, rho = 0.9999, FP32
+fields with FP64 weights.  Synthetic twin experiment: the truth starts from
+u0 = 0.2 sech(x-27) + 0.5 sech(x-13) and is propagated by the same kernels.
+
+Metric: particle-timesteps/s, counting every forward model step the cycle
+executes (the first window plus every PCN re-run).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "cfg2_f32"
+METRIC = "particle-timesteps/s"
+# algorithmic flops per node per Picard iteration of the linearly implicit
+# midpoint step: dv 3, left operator 7, right-hand side 8,
+# cyclic variable tridiagonal solve 14, Helmholtz 10, convergence 2
+FLOPS_PER_NODE_ITER = 44
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_peak_tflops():
+    """FP32 FMA pipe: 152 SMs x 128 lanes x 2 flops x max SM clock."""
+    mhz = _peaks().get("sm_max_mhz", 2070.0)
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, ws
+
+
+def reduce_max(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------- #
+# CPU baseline: the FP64 oracle, as it stands, on a bounded sample
+# ---------------------------------------------------------------------- #
+def oracle_sample(cfg, budget_s: float = 12.0, min_particles: int = 1):
+    import numpy as np
+    from oracle.model import Model
+    from workloads import mode_amplitudes, random_increments, random_state
+    om = Model(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg))
+    u0 = random_state(cfg, 64, 123)
+    dW = random_increments(cfg, 64, 124)
+    t0 = time.perf_counter()
+    done = 0
+    while done < 64 and (done < min_particles or time.perf_counter() - t0 < budget_s):
+        m0 = om.m_from_u(u0[done])
+        om.window(m0, dW[done])
+        done += 1
+    el = time.perf_counter() - t0
+    return done * cfg.Ns / el, f"oracle window propagation (FP64, one thread) of {done} particles x {cfg.Ns} steps of the n={cfg.n} workload", el
+
+
+def run_reference(args):
+    """--impl reference: the oracle on the host cores, per step a bounded sample."""
+    from workloads import get_config
+    rank, ws = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    cfg = get_config(WORKLOAD)
+    for _ in range(args.warmup):
+        oracle_sample(cfg, budget_s=0.0, min_particles=1)
+    rates = []
+    t_all = 0.0
+    sample = ""
+    for _ in range(args.steps):
+        r, sample, el = oracle_sample(cfg, budget_s=8.0, min_particles=1)
+        rates.append(r)
+        t_all += el
+    value = statistics.mean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": cfg.n, "N": cfg.N, "Ns": cfg.Ns, "K": cfg.K},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------- #
+# GPU arm
+# ---------------------------------------------------------------------- #
+def run_ours(args):
+    import torch
+    from workloads import get_config, u0_profile
+    from paper_2402_06927_gb300 import _lib
+    from paper_2402_06927_gb300.api import SchModel
+    from paper_2402_06927_gb300.filter import EnsembleFilter, KernelTimer
+
+    rank, ws = dist_setup()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    cfg = get_config(WORKLOAD)
+    g = SchModel.from_config(cfg)
+    N = cfg.N
+    seed = 1000 + rank          # independent replicas on each rank
+    total_cycles = args.warmup + args.steps
+    dt = g.dtype
+    # twin experiment: truth trajectory and observations, resident in HBM before timing
+    u_truth = torch.as_tensor(u0_profile(cfg), dtype=dt, device="cuda")
+    m_truth = g.m_from_u(u_truth[None].contiguous())
+    ys, truths = [], []
+    for c in range(total_cycles + 1):
+        dWt = g.draw_increments(1, cfg.Ns, seed, _lib.TAG_TRUTH, c)
+        out = g.ensemble_step(m_truth, dWt)
+        m_truth = out["m"]
+        truths.append(out["u"][0].clone())
+        ys.append(g.synth_obs(out["u"][0].contiguous(), seed, c))
+    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    m0, _ = g.prior_sample(N, u_truth, seed, cfg.prior_scale)
+    f.set_state(m0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    diag_ws = torch.empty(cfg.n, dtype=torch.float64, device="cuda")
+    diag_out = torch.empty(8, dtype=torch.float64, device="cuda")
+
+    for c in range(args.warmup):
+        f.cycle(ys[c], c)
+        f.advance()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+
+    timer = KernelTimer()
+    step_ms, fwd, launches, stages = [], 0, 0, []
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            c = args.warmup + k
+            flush.fill_(float(k))                     # evict the ensemble from L2 (untimed)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = f.cycle(ys[c], c, timer=timer)
+            f.advance()
+            e1.record()
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            fwd += st.forward_steps
+            launches += st.launches
+            stages.append(len(st.stages))
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.summary()
+    dev_s = sum(step_ms) / 1000.0
+    dev_s_max = reduce_max(dev_s, ws)
+    fwd_all = reduce_sum(float(fwd), ws)
+    value = fwd_all / dev_s_max
+
+    # roofline of the dominant kernel (the fused PCN jitter kernel)
+    jit_ms = timer.elapsed_ms()
+    it_sum = sum(int(t.sum().item()) for t in timer.iters)
+    n_launch = len(jit_ms)
+    flops = cfg.n * (FLOPS_PER_NODE_ITER * it_sum + 2 * cfg.K * N * cfg.Ns * cfg.n_jitter * n_launch)
+    jit_s = sum(jit_ms) / 1000.0
+    achieved = flops / jit_s / 1e12
+    peak = fp32_peak_tflops()
+    mean_iters = it_sum / (N * cfg.Ns * cfg.n_jitter * n_launch)
+
+    # diagnostics of the last analysis
+    g.diagnostics(f.u_end, truths[args.warmup + args.steps - 1], ws=diag_ws, out=diag_out)
+    diag = diag_out[:4].cpu().tolist()
+
+    # end to end through the public API with host buffers: observations H2D,
+    # ensemble mean and diagnostics D2H, every step
+    y_host = [y.cpu().pin_memory() for y in ys]
+    mean_host = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
+    dg_host = torch.empty(8, dtype=torch.float64).pin_memory()
+    y_dev = torch.empty_like(ys[0])
+    e2e_steps = min(args.steps, 3)
+    f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    f2.set_state(m0)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    fwd2 = 0
+    for c in range(e2e_steps):
+        y_dev.copy_(y_host[c], non_blocking=True)
+        st = f2.cycle(y_dev, c)
+        f2.advance()
+        g.diagnostics(f2.u_end, truths[c], ws=diag_ws, out=diag_out)
+        mean_host.copy_(diag_ws, non_blocking=True)
+        dg_host.copy_(diag_out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        fwd2 += st.forward_steps
+    e2e_s = reduce_max(time.perf_counter() - t0, ws)
+    e2e_val = reduce_sum(float(fwd2), ws) / e2e_s
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, sample, _ = oracle_sample(cfg, budget_s=12.0)
+        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "SCH twin experiment n=1024 K=8 N=1024 Ns=10 M=64 sigma=0.05 "
+                                   "N*=N/2 jitter=10 rho=0.9999 (FP32 fields, FP64 weights)",
+                       "n": cfg.n, "N": N, "Ns": cfg.Ns, "K": cfg.K, "M": cfg.M,
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "cycles_per_s": args.steps * ws / dev_s_max,
+                       "mean_tempering_stages": statistics.mean(stages),
+                       "mean_picard_iters_per_step": mean_iters,
+                       "analysis_emre_rb_res_rmse": diag},
+            "roofline": {"bound": "alu", "kernel": "jitter_kernel<float,8>", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "peak_note": "FP32 FMA pipe 152 SMs x 128 lanes x 2 x max SM clock"},
+            "gpu_launches": launches,
+            "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": cfg.M * 4,
+                    "d2h_bytes_per_step": cfg.n * 8 + 64},
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * sch.h -- C ABI of the GB300 (sm_103a) particle-filter library for the
+ * viscous stochastic Camassa-Holm (SALT) equation.
+ *
+ * Method: Cotter, Crisan, Singh, "Data assimilation for the stochastic
+ * Camassa-Holm equation using particle filtering" (arXiv 2402.06927).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status: SCH_OK (0) or a negative SCH_ERR_*.
+ *    Argument errors are detected on the host before anything is launched.
+ *  - Array arguments are DEVICE pointers owned by the caller (for instance
+ *    PyTorch tensors), row-major and contiguous.  "real" means the field
+ *    precision chosen in sch_params.dtype: double for SCH_F64, float for
+ *    SCH_F32.  Log-weights, likelihoods and weights are always double.
+ *  - Particle data (the (X_start, dW) representation of Sec. 3.1.2):
+ *      m, u      real   [N][n]       momentum and velocity nodal values
+ *      dW        real   [N][Ns][K]   Brownian increments of the window
+ *      lambda    real   [N][Ns][K]   nudging drift (NULL means zero)
+ *      y         real   [M]          observations at x_j = j L / M
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *    Calls are asynchronous on that stream, allocate no device memory and do
+ *    not synchronise; sch_create / sch_destroy allocate and free the host-side
+ *    context.  Device-side failures (Picard non-convergence, non-finite
+ *    values) are reported per particle in the optional int32 `status` array:
+ *    bit SCH_DEV_NOCONVERGE or SCH_DEV_NONFINITE; 0 = fine.
+ *  - Sizes: n must equal C * TP with TP a power of two in [32, 512], where
+ *    C = 8 for SCH_F32 and C = 4 for SCH_F64 (so n in {256 .. 4096} for f32,
+ *    {128 .. 2048} for f64); n % M == 0; K even, 2 <= K <= 64.
+ *
+ * Random numbers: Philox4x64-10 (Salmon et al., SC'11), key (seed, purpose),
+ * counter (block, step, particle, stream counter); normals by Box-Muller on
+ * 53-bit uniforms.  Purposes are the SCH_TAG_* values below.
+ */
+#ifndef SCH_H_
+#define SCH_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    SCH_OK = 0,
+    SCH_ERR_ARG = -1,          /* bad size, pointer or parameter */
+    SCH_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    SCH_ERR_NOCONVERGE = -3,   /* returned by host helpers that read status */
+    SCH_ERR_NONFINITE = -4,
+    SCH_ERR_WORKSPACE = -5,    /* workspace missing or too small */
+    SCH_ERR_UNSUPPORTED = -6   /* size outside the compiled configurations */
+};
+
+enum { SCH_DEV_NOCONVERGE = 1, SCH_DEV_NONFINITE = 2 };
+
+enum { SCH_F64 = 0, SCH_F32 = 1 };
+
+enum {
+    SCH_TAG_PRIOR_DW = 1, SCH_TAG_PCN = 2, SCH_TAG_PCN_ACCEPT = 3, SCH_TAG_RESAMPLE = 4,
+    SCH_TAG_TRUTH = 5, SCH_TAG_OBS = 6, SCH_TAG_INIT = 7, SCH_TAG_NUDGE = 8
+};
+
+#define SCH_MAX_K 64
+
+/* Model and observation parameters (Sec. 2 and Sec. 3 of the paper). */
+typedef struct {
+    double L;            /* period of the domain [0, L) */
+    int32_t n;           /* cells = nodes of the periodic P1 mesh, h = L / n */
+    double alpha;        /* Helmholtz length: m = u - alpha^2 u_xx (Eq. CHe1) */
+    double mu;           /* viscosity */
+    double dt;           /* model time step */
+    int32_t K;           /* number of SALT mode functions (even) */
+    double amps[SCH_MAX_K / 2];  /* a_j, j = 1..K/2: xi_{2j-2} = a_j sin(2 pi j x/L),
+                                    xi_{2j-1} = a_j cos(2 pi j x/L) */
+    int32_t M;           /* observation points x_j = j L / M (on nodes) */
+    double sigma;        /* observation noise standard deviation */
+    double tol;          /* Picard stop: max|dm| <= tol * max(1, max|m|) */
+    int32_t max_iter;    /* Picard iteration limit per step */
+    int32_t dtype;       /* SCH_F64 or SCH_F32: precision of fields, dW, lambda */
+} sch_params;
+
+typedef struct sch_ctx sch_ctx;
+
+/* Create a context: validates the parameters and precomputes the scalar
+ * coefficients of the discretisation (host memory only; no device call).
+ * Returns SCH_ERR_ARG / SCH_ERR_UNSUPPORTED for invalid or uncompiled sizes. */
+int sch_create(const sch_params* params, sch_ctx** ctx);
+int sch_destroy(sch_ctx* ctx);
+
+/* Workspace bytes pf_resample needs to gather `row_bytes_total` bytes per
+ * particle in place for N particles. */
+size_t pf_resample_workspace_bytes(int N, size_t row_bytes_total);
+
+/* u = H^{-1} M m for every particle: the Helmholtz relation of Eq. sde1
+ * (first line), (u, psi) + alpha^2 (u_x, psi_x) = (m, psi) on P1.
+ * m, u: real [N][n]. */
+int sch_u_from_m(sch_ctx* ctx, int N, const void* m, void* u, void* stream);
+
+/* m = M^{-1} (M + alpha^2 K) u: the P1 momentum of a velocity (Eq. CHe1). */
+int sch_m_from_u(sch_ctx* ctx, int N, const void* u, void* m, void* stream);
+
+/* Draw dW[p][s][k] = sqrt(dt) z, z ~ N(0,1) from Philox keyed
+ * (seed, tag) and counter (k / 4, s, particle0 + p, ctr).  dW: real [N][nsteps][K].
+ * The prior of the window increments: iid N(0, dt) (Sec. 3.1.2). */
+int sch_draw_increments(sch_ctx* ctx, int N, int nsteps, uint64_t seed, uint64_t tag,
+                        uint64_t ctr, int particle0, void* dW, void* stream);
+
+/* Ensemble propagation (Sec. 2, Eq. fde1): advance each particle `nsteps`
+ * implicit-midpoint steps with SALT increments
+ *   dU^s(x_i) = sum_k xi_k(x_i) (dW[p][s][k] + lambda[p][s][k] dt),
+ * each step solved by linearly implicit Picard iteration to params.tol.
+ *   m      real [N][n]  in: start momentum; out: end momentum (may alias m_out)
+ *   m_out  real [N][n]  out (may equal m)
+ *   u_out  real [N][n]  out: end velocity
+ *   dW, lambda          real [N][nsteps][K]; lambda may be NULL
+ *   y      real [M]     optional: when non-NULL the kernel also writes the
+ *                       observation NLL (Eq. loglikeq) of the end state into
+ *                       nll[N] and the Girsanov log-weight into logG[N]
+ *                       (Eq. girsanov DG approx), both double
+ *   iters  int32 [N]    optional: Picard iterations summed over the steps
+ *   status int32 [N]    optional: SCH_DEV_* flags */
+int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_out, void* u_out,
+                      const void* dW, const void* lambda, const void* y, double* nll,
+                      double* logG, int32_t* iters, int32_t* status, void* stream);
+
+/* Observation log-likelihood and Girsanov weight of given end states:
+ *   nll[p]  = 1/2 sum_j ((u[p][j n/M] - y_j) / sigma)^2      (Eq. loglikeq)
+ *   logG[p] = -sum_{s,k} (lambda dW + 1/2 lambda^2 dt)        (Eq. girsanov DG approx)
+ * u real [N][n]; dW, lambda real [N][nsteps][K] (lambda NULL => logG = 0;
+ * dW may then be NULL too).  Differences in real, sums in double. */
+int sch_loglik(sch_ctx* ctx, int N, const void* u, const void* y, const void* dW,
+               const void* lambda, int nsteps, double* nll, double* logG, void* stream);
+
+/* Adaptive tempering (Sec. 3.1.2): given nll[N] and logG[N] (double; logG may
+ * be NULL for zero), phi = nll - logG = -log W~, and the current temperature
+ * theta, find the largest dtheta in (0, 1 - theta] with
+ * ESS(exp(-dtheta phi)) >= ess_min (Eq. ess): the whole step if it passes,
+ * else 60 bisection steps on [0, 1 - theta] (falls back to the smallest
+ * point tried if none passes).  Writes wbar[N] (double, normalised weights at
+ * dtheta) and out[4] = {dtheta, ESS, theta_new, status}; theta_new is exactly
+ * 1.0 when the remaining step was taken.  N <= 16384. */
+int pf_temper(int N, const double* nll, const double* logG, double theta, double ess_min,
+              double* wbar, double* out, void* stream);
+
+/* Systematic resampling (Sec. 3.1.1) on exact integers: q_i = floor(wbar_i 2^50),
+ * C_j = q_0 + .. + q_j, T = C_{N-1}; slot i takes the smallest j with
+ * C_j > floor((i 2^53 + U) T / (N 2^53)), U = (Philox (seed, SCH_TAG_RESAMPLE,
+ * counter (0, 0, 0, stage_ctr)) word 0) >> 11.  Writes idx[N] (int32).
+ * If n_arrays > 0, also gathers each arrays[a] (device pointer, N rows of
+ * row_bytes[a] bytes, rows 16-byte aligned) in place: row i <- old row idx[i],
+ * staged through `ws` (ws_bytes >= pf_resample_workspace_bytes).  `arrays` and
+ * `row_bytes` are host arrays.  N <= 16384. */
+int pf_resample(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
+                int n_arrays, void* const* arrays, const size_t* row_bytes, void* ws,
+                size_t ws_bytes, void* stream);
+
+/* Out-of-place row gather: dst row i = src row idx[i]; rows of row_bytes
+ * bytes (a multiple of 4; src and dst aligned to the largest of 16, 8, 4 that
+ * divides row_bytes). */
+int pf_gather_rows(int N, const int32_t* idx, const void* src, void* dst, size_t row_bytes,
+                   void* stream);
+
+/* PCN jittering at temperature theta (Sec. 3.1.2): n_iter Metropolis moves of
+ * each particle's window noise.  Iteration j proposes
+ *   dW' = rho dW + sqrt(1 - rho^2) sqrt(dt) z,  z keyed (seed, SCH_TAG_PCN, ctr + j),
+ * re-runs the whole window from m_start with dW' (and lambda), and accepts iff
+ *   log U < w0 - w1,  w = theta (NLL - logG),  U keyed (seed, SCH_TAG_PCN_ACCEPT, ctr + j).
+ * In/out: dW, nll, logG, m_end, u_end (the current state; updated on accept).
+ * accepts int32 [N] (out, accepted moves); iters, status optional as above. */
+int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double rho,
+              uint64_t seed, uint64_t ctr, const void* m_start, void* dW, const void* lambda,
+              const void* y, double* nll, double* logG, void* m_end, void* u_end,
+              int32_t* accepts, int32_t* iters, int32_t* status, void* stream);
+
+/* Synthetic observations of a truth velocity: y_j = u(x_j) + sigma z_j with
+ * z_j keyed (seed, SCH_TAG_OBS, (j / 4, 0, 0, ctr)).  u real [n], y real [M]. */
+int sch_synth_obs(sch_ctx* ctx, const void* u, uint64_t seed, uint64_t ctr, void* y, void* stream);
+
+/* Ensemble diagnostics against a truth velocity (Sec. 4.1.1): out[0] = EMRE,
+ * out[1] = RB, out[2] = RES, out[3] = RMSE of the ensemble mean over the nodes
+ * (out[4..7] are scratch).  u real [N][n], u_truth real [n], ws double [n]
+ * (caller-owned scratch for the ensemble mean), out double [8].  N >= 2. */
+int pf_diagnostics(sch_ctx* ctx, int N, const void* u, const void* u_truth, double* ws, double* out,
+                   void* stream);
+
+/* Prior ensemble about a truth velocity (a reading of Eq. init_solve): for
+ * particle p, W_p is a DG0 field with cell values sqrt(h) z (z keyed
+ * (seed, SCH_TAG_INIT, (b, 0, p, 0))), S = (M + K)^{-1} M-type P1 smoothing
+ * applied three times, u = u_truth + scale (a_p S^3 W_p + b_p) with a_p, b_p
+ * the next two normals; writes m and u (real [N][n]).  u_truth real [n]. */
+int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, double scale,
+                     void* m, void* u, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCH_H_ */

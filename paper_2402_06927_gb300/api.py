@@ -1,0 +1,242 @@
+"""Python binding of the C ABI (include/sch.h): argument marshalling only.
+
+Every function takes CUDA tensors, checks shapes and dtypes, passes raw device
+pointers and the current CUDA stream to the library, and raises on a
+non-zero status.  No arithmetic of the method happens here.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+from typing import Optional, Sequence
+
+import torch
+
+from . import _lib
+from ._lib import SCH_F32, SCH_F64, SchParams, check, lib
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class SchModel:
+    """A library context for one set of model and observation parameters."""
+
+    def __init__(self, L: float, n: int, alpha: float, mu: float, dt: float, amps: Sequence[float],
+                 M: int, sigma: float, tol: float, max_iter: int, dtype: str = "f32"):
+        p = SchParams()
+        p.L, p.n, p.alpha, p.mu, p.dt = L, n, alpha, mu, dt
+        p.K = 2 * len(amps)
+        for j, a in enumerate(amps):
+            p.amps[j] = float(a)
+        p.M, p.sigma, p.tol, p.max_iter = M, sigma, tol, max_iter
+        p.dtype = SCH_F32 if dtype == "f32" else SCH_F64
+        self.params = p
+        self.n, self.K, self.M, self.dt = n, p.K, M, dt
+        self.dtype = torch.float32 if dtype == "f32" else torch.float64
+        h = ct.c_void_p()
+        check(lib().sch_create(ct.byref(p), ct.byref(h)), "sch_create")
+        self._h = h
+
+    @classmethod
+    def from_config(cls, cfg, **over):
+        from workloads import mode_amplitudes
+        kw = dict(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=list(mode_amplitudes(cfg)),
+                  M=cfg.M, sigma=cfg.sigma, tol=cfg.tol, max_iter=cfg.max_iter, dtype=cfg.dtype)
+        kw.update(over)
+        return cls(**kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sch_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ #
+    def u_from_m(self, m: torch.Tensor, u: Optional[torch.Tensor] = None) -> torch.Tensor:
+        N = m.shape[0]
+        _need(m, self.dtype, (N, self.n), "m")
+        u = torch.empty_like(m) if u is None else u
+        check(lib().sch_u_from_m(self._h, N, _ptr(m), _ptr(u), _stream()), "sch_u_from_m")
+        return u
+
+    def m_from_u(self, u: torch.Tensor, m: Optional[torch.Tensor] = None) -> torch.Tensor:
+        N = u.shape[0]
+        _need(u, self.dtype, (N, self.n), "u")
+        m = torch.empty_like(u) if m is None else m
+        check(lib().sch_m_from_u(self._h, N, _ptr(u), _ptr(m), _stream()), "sch_m_from_u")
+        return m
+
+    def draw_increments(self, N: int, nsteps: int, seed: int, tag: int, ctr: int, particle0: int = 0,
+                        out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = torch.empty((N, nsteps, self.K), dtype=self.dtype, device="cuda") if out is None else out
+        _need(out, self.dtype, (N, nsteps, self.K), "dW")
+        check(lib().sch_draw_increments(self._h, N, nsteps, seed, tag, ctr, particle0, _ptr(out), _stream()),
+              "sch_draw_increments")
+        return out
+
+    def ensemble_step(self, m: torch.Tensor, dW: torch.Tensor, lam: Optional[torch.Tensor] = None,
+                      y: Optional[torch.Tensor] = None, m_out: Optional[torch.Tensor] = None,
+                      u_out: Optional[torch.Tensor] = None, nll: Optional[torch.Tensor] = None,
+                      logG: Optional[torch.Tensor] = None, iters: Optional[torch.Tensor] = None,
+                      status: Optional[torch.Tensor] = None, want_iters: bool = True):
+        """sch_ensemble_step: returns dict(m, u, nll, logG, iters, status)."""
+        N = m.shape[0]
+        nsteps = dW.shape[1]
+        _need(m, self.dtype, (N, self.n), "m")
+        _need(dW, self.dtype, (N, nsteps, self.K), "dW")
+        if lam is not None:
+            _need(lam, self.dtype, (N, nsteps, self.K), "lambda")
+        m_out = torch.empty_like(m) if m_out is None else m_out
+        u_out = torch.empty_like(m) if u_out is None else u_out
+        _need(m_out, self.dtype, (N, self.n), "m_out")
+        _need(u_out, self.dtype, (N, self.n), "u_out")
+        if y is not None:
+            _need(y, self.dtype, (self.M,), "y")
+            nll = torch.empty(N, dtype=torch.float64, device=m.device) if nll is None else nll
+            logG = torch.empty(N, dtype=torch.float64, device=m.device) if logG is None else logG
+            _need(nll, torch.float64, (N,), "nll")
+            _need(logG, torch.float64, (N,), "logG")
+        else:
+            nll = logG = None
+        if iters is None and want_iters:
+            iters = torch.empty(N, dtype=torch.int32, device=m.device)
+        status = torch.empty(N, dtype=torch.int32, device=m.device) if status is None else status
+        check(lib().sch_ensemble_step(self._h, N, nsteps, _ptr(m), _ptr(m_out), _ptr(u_out), _ptr(dW), _ptr(lam),
+                                      _ptr(y), _ptr(nll), _ptr(logG), _ptr(iters), _ptr(status), _stream()),
+              "sch_ensemble_step")
+        return dict(m=m_out, u=u_out, nll=nll, logG=logG, iters=iters, status=status)
+
+    def loglik(self, u: torch.Tensor, y: torch.Tensor, dW: Optional[torch.Tensor] = None,
+               lam: Optional[torch.Tensor] = None):
+        N = u.shape[0]
+        _need(u, self.dtype, (N, self.n), "u")
+        _need(y, self.dtype, (self.M,), "y")
+        nsteps = 0 if dW is None else dW.shape[1]
+        nll = torch.empty(N, dtype=torch.float64, device=u.device)
+        logG = torch.empty(N, dtype=torch.float64, device=u.device)
+        check(lib().sch_loglik(self._h, N, _ptr(u), _ptr(y), _ptr(dW), _ptr(lam), nsteps, _ptr(nll), _ptr(logG),
+                               _stream()), "sch_loglik")
+        return nll, logG
+
+    def jitter(self, m_start, dW, lam, y, nll, logG, m_end, u_end, theta: float, rho: float, n_iter: int,
+               seed: int, ctr: int, want_iters: bool = False, accepts=None, iters=None, status=None):
+        """pf_jitter: updates dW, nll, logG, m_end, u_end in place; returns (accepts, iters, status)."""
+        N, nsteps, K = dW.shape
+        _need(m_start, self.dtype, (N, self.n), "m_start")
+        _need(dW, self.dtype, (N, nsteps, self.K), "dW")
+        _need(m_end, self.dtype, (N, self.n), "m_end")
+        _need(u_end, self.dtype, (N, self.n), "u_end")
+        _need(y, self.dtype, (self.M,), "y")
+        _need(nll, torch.float64, (N,), "nll")
+        _need(logG, torch.float64, (N,), "logG")
+        if lam is not None:
+            _need(lam, self.dtype, (N, nsteps, self.K), "lambda")
+        acc = torch.empty(N, dtype=torch.int32, device=dW.device) if accepts is None else accepts
+        if iters is None and want_iters:
+            iters = torch.empty(N, dtype=torch.int32, device=dW.device)
+        status = torch.empty(N, dtype=torch.int32, device=dW.device) if status is None else status
+        check(lib().pf_jitter(self._h, N, nsteps, n_iter, theta, rho, seed, ctr, _ptr(m_start), _ptr(dW),
+                              _ptr(lam), _ptr(y), _ptr(nll), _ptr(logG), _ptr(m_end), _ptr(u_end), _ptr(acc),
+                              _ptr(iters), _ptr(status), _stream()), "pf_jitter")
+        return acc, iters, status
+
+    def synth_obs(self, u: torch.Tensor, seed: int, ctr: int, y: Optional[torch.Tensor] = None):
+        _need(u, self.dtype, (self.n,), "u")
+        y = torch.empty(self.M, dtype=self.dtype, device=u.device) if y is None else y
+        check(lib().sch_synth_obs(self._h, _ptr(u), seed, ctr, _ptr(y), _stream()), "sch_synth_obs")
+        return y
+
+    def diagnostics(self, u: torch.Tensor, u_truth: torch.Tensor, ws: Optional[torch.Tensor] = None,
+                    out: Optional[torch.Tensor] = None):
+        """[EMRE, RB, RES, RMSE, scratch x4] (double, on the device)."""
+        N = u.shape[0]
+        _need(u, self.dtype, (N, self.n), "u")
+        _need(u_truth, self.dtype, (self.n,), "u_truth")
+        ws = torch.empty(self.n, dtype=torch.float64, device=u.device) if ws is None else ws
+        out = torch.empty(8, dtype=torch.float64, device=u.device) if out is None else out
+        check(lib().pf_diagnostics(self._h, N, _ptr(u), _ptr(u_truth), _ptr(ws), _ptr(out), _stream()),
+              "pf_diagnostics")
+        return out
+
+    def prior_sample(self, N: int, u_truth: torch.Tensor, seed: int, scale: float):
+        _need(u_truth, self.dtype, (self.n,), "u_truth")
+        m = torch.empty((N, self.n), dtype=self.dtype, device="cuda")
+        u = torch.empty_like(m)
+        check(lib().sch_prior_sample(self._h, N, _ptr(u_truth), seed, scale, _ptr(m), _ptr(u), _stream()),
+              "sch_prior_sample")
+        return m, u
+
+
+# ---------------------------------------------------------------------- #
+# filter entry points that need no model context
+# ---------------------------------------------------------------------- #
+def pf_temper(nll: torch.Tensor, logG: Optional[torch.Tensor], theta: float, ess_min: float,
+              wbar: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None):
+    """Returns (wbar, out) with out = [dtheta, ESS, theta_new, status] on the device; phi = nll - logG."""
+    N = nll.shape[0]
+    _need(nll, torch.float64, (N,), "nll")
+    if logG is not None:
+        _need(logG, torch.float64, (N,), "logG")
+    wbar = torch.empty_like(nll) if wbar is None else wbar
+    out = torch.empty(4, dtype=torch.float64, device=nll.device) if out is None else out
+    check(lib().pf_temper(N, _ptr(nll), _ptr(logG), theta, ess_min, _ptr(wbar), _ptr(out), _stream()),
+          "pf_temper")
+    return wbar, out
+
+
+def pf_resample(wbar: torch.Tensor, seed: int, stage_ctr: int, arrays: Sequence[torch.Tensor] = (),
+                ws: Optional[torch.Tensor] = None, idx: Optional[torch.Tensor] = None):
+    """Offspring indices (int32 [N]); gathers each tensor of ``arrays`` in place through ``ws``."""
+    N = wbar.shape[0]
+    _need(wbar, torch.float64, (N,), "wbar")
+    idx = torch.empty(N, dtype=torch.int32, device=wbar.device) if idx is None else idx
+    na = len(arrays)
+    ptrs = (ct.c_void_p * max(na, 1))(*[a.data_ptr() for a in arrays])
+    rows = (ct.c_size_t * max(na, 1))(*[a[0].numel() * a.element_size() for a in arrays])
+    for a in arrays:
+        if a.shape[0] != N or not a.is_contiguous():
+            raise ValueError("arrays must be contiguous with N rows")
+    total = sum(rows[i] for i in range(na))
+    if na and ws is None:
+        ws = torch.empty(N * total, dtype=torch.uint8, device=wbar.device)
+    ws_bytes = 0 if ws is None else ws.numel() * ws.element_size()
+    check(lib().pf_resample(N, _ptr(wbar), seed, stage_ctr, _ptr(idx), na, ptrs if na else None,
+                            rows if na else None, _ptr(ws), ws_bytes, _stream()), "pf_resample")
+    return idx
+
+
+def pf_gather_rows(idx: torch.Tensor, src: torch.Tensor, dst: torch.Tensor):
+    N = idx.shape[0]
+    row = src[0].numel() * src.element_size()
+    check(lib().pf_gather_rows(N, _ptr(idx), _ptr(src), _ptr(dst), row, _stream()), "pf_gather_rows")
+    return dst
+
+
+def pf_resample_workspace_bytes(N: int, row_bytes_total: int) -> int:
+    return int(lib().pf_resample_workspace_bytes(N, row_bytes_total))

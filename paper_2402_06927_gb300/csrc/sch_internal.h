@@ -1,0 +1,94 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sch.h"
+#include "sch_device.cuh"
+
+namespace sch {
+
+// Precomputed scalars of the discretised model, passed by value to kernels.
+template <typename R>
+struct ModelArgs {
+    int n, K, K2, M, stride, max_iter;
+    R h, dt;
+    R c0, b0;      // left operator M + mu dt/2 K: off-diagonal, diagonal
+    R c0p, b0p;    // right operator M - mu dt/2 K: off-diagonal, diagonal
+    R dt8;         // dt / 8
+    R h6;          // h / 6
+    R tol;
+    R hel_a, hel_b;  // Helmholtz H = M + alpha^2 K: off-diagonal, diagonal
+    R sigma_inv;
+    double dt_d;
+    R amp4[SCH_MAX_K / 2];  // a_j / 4
+};
+
+template <typename R>
+struct WindowIO {
+    int Ns;
+    const R* m_in;
+    R* m_out;
+    R* u_out;
+    const R* dW;
+    const R* lam;
+    const R* y;
+    double* nll;
+    double* logG;
+    int32_t* iters;
+    int32_t* status;
+};
+
+template <typename R>
+struct JitterIO {
+    int Ns, n_iter, particle0;
+    double theta;
+    R rho, sq1mr2;
+    uint64_t seed, ctr;
+    const R* m_start;
+    R* dW;
+    const R* lam;
+    const R* y;
+    double* nll;
+    double* logG;
+    R* m_end;
+    R* u_end;
+    int32_t* accepts;
+    int32_t* iters;
+    int32_t* status;
+};
+
+template <typename R, int C>
+int launch_window(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st);
+template <typename R, int C>
+int launch_jitter(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st);
+template <typename R, int C>
+int launch_helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cudaStream_t st);
+template <typename R, int C>
+int launch_prior(const ModelArgs<R>& A, const R* u_truth, uint64_t seed, R scale, R* m, R* u, int N,
+                 cudaStream_t st);
+template <typename R>
+int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0,
+                R* dW, cudaStream_t st);
+template <typename R>
+int launch_loglik(const ModelArgs<R>& A, int N, const R* u, const R* y, const R* dW, const R* lam, int Ns,
+                  double* nll, double* logG, cudaStream_t st);
+template <typename R, int C>
+size_t window_smem(int tp, int Ns, int K);
+template <typename R>
+int launch_synth_obs(const ModelArgs<R>& A, const R* u, uint64_t seed, uint64_t ctr, R* y, cudaStream_t st);
+template <typename R>
+int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* u_truth, double* ws, double* out,
+                cudaStream_t st);
+
+// filter kernels (pf_filter.cu)
+int launch_temper(int N, const double* nll, const double* logG, double theta, double ess_min, double* wbar,
+                  double* out, cudaStream_t st);
+int launch_resample_idx(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
+                        cudaStream_t st);
+int launch_gather(int N, const int32_t* idx, const void* src, void* dst, size_t row_bytes, cudaStream_t st);
+int launch_copy(const void* src, void* dst, size_t bytes, cudaStream_t st);
+
+}  // namespace sch

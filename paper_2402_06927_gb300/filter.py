@@ -1,0 +1,131 @@
+"""Host driver of one assimilation cycle on the GPU (Sec. 3.1 of the paper).
+
+The cycle works on the (X_start, dW) representation of a particle
+(Sec. 3.1.2): draw the window noise, propagate every particle through the
+window (with the fused likelihood epilogue), then repeat adaptive tempering,
+systematic resampling and PCN jittering until the temperature reaches one;
+finally the end state becomes the next window's start.  Every step is a call
+into the CUDA library; the host only reads back the 32-byte tempering result
+of each stage to decide whether another stage is needed.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import torch
+
+from . import _lib
+from .api import SchModel, pf_gather_rows, pf_resample, pf_temper
+
+
+@dataclass
+class StageStats:
+    dtheta: float
+    ess: float
+    theta: float
+
+
+@dataclass
+class CycleStats:
+    stages: List[StageStats] = field(default_factory=list)
+    forward_steps: int = 0      # particle-timesteps propagated in the cycle (incl. PCN re-runs)
+    launches: int = 0           # library kernels launched by the cycle
+    accepts: Optional[torch.Tensor] = None
+
+
+class KernelTimer:
+    """CUDA events around the jitter launches of a cycle (on the launching stream)."""
+
+    def __init__(self):
+        self.pairs = []
+        self.iters = []
+
+    def elapsed_ms(self):
+        return [a.elapsed_time(b) for a, b in self.pairs]
+
+
+class EnsembleFilter:
+    """GPU state of an N-particle tempering + jittering filter."""
+
+    def __init__(self, model: SchModel, N: int, Ns: int, ess_min: float, rho: float, n_jitter: int,
+                 seed: int, lam: Optional[torch.Tensor] = None):
+        self.model, self.N, self.Ns = model, N, Ns
+        self.ess_min, self.rho, self.n_jitter, self.seed = ess_min, rho, n_jitter, seed
+        dt, dev, n, K = model.dtype, torch.device("cuda"), model.n, model.K
+
+        def fld():
+            return torch.zeros((N, n), dtype=dt, device=dev)
+
+        self.m_start, self.m_end, self.u_end = fld(), fld(), fld()
+        self.dW = torch.zeros((N, Ns, K), dtype=dt, device=dev)
+        self.lam = lam
+        self.nll = torch.zeros(N, dtype=torch.float64, device=dev)
+        self.logG = torch.zeros(N, dtype=torch.float64, device=dev)
+        # second copies for out-of-place resampling gathers
+        self._b = dict(m_start=fld(), m_end=fld(), u_end=fld(),
+                       dW=torch.zeros_like(self.dW), nll=torch.zeros_like(self.nll),
+                       logG=torch.zeros_like(self.logG))
+        if lam is not None:
+            self._b["lam"] = torch.zeros_like(lam)
+        self.wbar = torch.zeros(N, dtype=torch.float64, device=dev)
+        self.tout = torch.zeros(4, dtype=torch.float64, device=dev)
+        self.tout_host = torch.zeros(4, dtype=torch.float64).pin_memory()
+        self.idx = torch.zeros(N, dtype=torch.int32, device=dev)
+        self.accepts = torch.zeros(N, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(N, dtype=torch.int32, device=dev)
+
+    def set_state(self, m_start: torch.Tensor) -> None:
+        self.m_start.copy_(m_start)
+
+    def _resample(self, stage_ctr: int) -> None:
+        pf_resample(self.wbar, self.seed, stage_ctr, idx=self.idx)
+        names = ["m_start", "m_end", "u_end", "dW", "nll", "logG"] + (["lam"] if self.lam is not None else [])
+        for name in names:
+            cur = getattr(self, name)
+            nxt = self._b[name]
+            pf_gather_rows(self.idx, cur, nxt)
+            setattr(self, name, nxt)
+            self._b[name] = cur
+
+    def cycle(self, y: torch.Tensor, cycle: int, max_stages: int = 64,
+              timer: Optional[KernelTimer] = None) -> CycleStats:
+        m = self.model
+        st = CycleStats()
+        m.draw_increments(self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, out=self.dW)
+        m.ensemble_step(self.m_start, self.dW, self.lam, y, m_out=self.m_end, u_out=self.u_end,
+                        nll=self.nll, logG=self.logG, status=self.status, want_iters=False)
+        st.forward_steps += self.N * self.Ns
+        st.launches += 2
+        theta, k = 0.0, 0
+        while theta < 1.0 and k < max_stages:
+            pf_temper(self.nll, self.logG, theta, self.ess_min, wbar=self.wbar, out=self.tout)
+            self.tout_host.copy_(self.tout, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            d, e, theta_new = (float(v) for v in self.tout_host[:3])
+            stage_ctr = cycle * 1024 + k
+            self._resample(stage_ctr)
+            theta = theta_new
+            iters = None
+            if timer is not None:
+                iters = torch.empty(self.N, dtype=torch.int32, device=self.nll.device)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record()
+            m.jitter(self.m_start, self.dW, self.lam, y, self.nll, self.logG, self.m_end, self.u_end, theta,
+                     self.rho, self.n_jitter, self.seed, stage_ctr * self.n_jitter, accepts=self.accepts,
+                     status=self.status, iters=iters)
+            if timer is not None:
+                ev1.record()
+                timer.pairs.append((ev0, ev1))
+                timer.iters.append(iters)
+            st.forward_steps += self.N * self.Ns * self.n_jitter
+            st.launches += 2 + len(self._b) + 1
+            st.stages.append(StageStats(d, e, theta))
+            k += 1
+        st.accepts = self.accepts
+        return st
+
+    def advance(self) -> None:
+        """The end of this window becomes the start of the next (X_start <- X_end)."""
+        self.m_start, self.m_end = self.m_end, self.m_start

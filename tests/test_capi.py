@@ -1,0 +1,86 @@
+"""CPU-side checks of the C ABI: the library loads, exports every function that
+include/sch.h declares, and rejects invalid arguments on the host before any
+CUDA call (these tests need no GPU)."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:int|size_t)\s+(\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2402_06927_gb300 import build
+    build.build()
+    from paper_2402_06927_gb300 import _lib
+    return _lib.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_2402_06927_gb300 import _lib
+    bound = set(_lib.SIGNATURES) | set(_lib.RESTYPES)
+    assert set(declared_functions()) <= bound
+
+
+def _params(**kw):
+    from paper_2402_06927_gb300._lib import SchParams, SCH_F64
+    p = SchParams()
+    p.L, p.n, p.alpha, p.mu, p.dt, p.K = 40.0, 256, 1.0, 0.02, 0.025, 4
+    p.amps[0] = p.amps[1] = 0.05
+    p.M, p.sigma, p.tol, p.max_iter, p.dtype = 32, 0.05, 1e-13, 50, SCH_F64
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("kw,rc", [({}, 0), ({"n": 100, "M": 25}, -6), ({"n": 256 * 4}, 0), ({"K": 3}, -1),
+                                   ({"K": 66}, -1), ({"M": 33}, -1), ({"sigma": 0.0}, -1), ({"dt": -1.0}, -1),
+                                   ({"dtype": 5}, -1), ({"n": 8192}, -6), ({"max_iter": 0}, -1)])
+def test_create_validates(lib, kw, rc):
+    p = _params(**kw)
+    h = ct.c_void_p()
+    got = lib.sch_create(ct.byref(p), ct.byref(h))
+    assert got == rc
+    if got == 0:
+        assert lib.sch_destroy(h) == 0
+
+
+def test_host_argument_errors_need_no_gpu(lib):
+    p = _params()
+    h = ct.c_void_p()
+    assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0
+    # missing pointers are rejected before any launch
+    assert lib.sch_ensemble_step(h, 4, 5, None, None, None, None, None, None, None, None, None, None, None) == -1
+    assert lib.sch_ensemble_step(h, -1, 5, None, None, None, None, None, None, None, None, None, None, None) == -1
+    # empty ensembles are a no-op
+    assert lib.sch_ensemble_step(h, 0, 5, None, None, None, None, None, None, None, None, None, None, None) == 0
+    assert lib.pf_temper(0, None, None, 0.0, 1.0, None, None, None) == -1
+    assert lib.pf_temper(4, ct.c_void_p(16), None, 1.0, 1.0, ct.c_void_p(16), ct.c_void_p(16), None) == -1
+    assert lib.pf_resample(9000, ct.c_void_p(16), 0, 0, ct.c_void_p(16), 0, None, None, None, 0, None) == -1
+    arr = (ct.c_void_p * 1)(16)
+    rows = (ct.c_size_t * 1)(32)
+    assert lib.pf_resample(4, ct.c_void_p(16), 0, 0, ct.c_void_p(16), 1, arr, rows, None, 0, None) == -5
+    assert lib.pf_gather_rows(4, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(32), 6, None) == -1
+    assert lib.pf_jitter(h, 4, 5, 1, 0.5, 1.5, 0, 0, *([None] * 12)) == -1
+    assert lib.pf_resample_workspace_bytes(10, 48) == 480
+    assert lib.sch_destroy(h) == 0

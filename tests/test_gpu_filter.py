@@ -1,0 +1,143 @@
+"""GPU parity of the filter kernels against the FP64 oracle (through the C ABI).
+
+* tempering: dtheta, ESS and normalised weights within 1e-12 relative;
+* resampling: offspring indices bit-exact given the oracle's weights;
+* PCN jitter: accept decisions identical wherever the Metropolis margin
+  |log U - (w0 - w1)| exceeds 1e-6, fields of those particles within the
+  window tolerance;
+* a whole assimilation cycle in FP64: same number of tempering stages, the
+  same temperatures and ensemble within 1e-8.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import get_config, random_state, random_increments, random_drift, random_obs, random_logweights
+from oracle import filter as OF
+from oracle import rng as ORNG
+from tests.helpers import gpu_model, oracle_model, require_lib, tdev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("N,spread,theta", [(1, 1.0, 0.0), (7, 0.01, 0.0), (64, 5.0, 0.0), (1024, 30.0, 0.25),
+                                            (8192, 80.0, 0.5), (16384, 5.0, 0.9)])
+def test_temper_matches_oracle(N, spread, theta):
+    api = require_lib()
+    phi = random_logweights(N, N, spread)
+    lg = np.random.default_rng(N).normal(size=N)
+    ess_min = 0.5 * N
+    nll = phi + lg
+    w, out = api.pf_temper(tdev(nll, torch.float64), tdev(lg, torch.float64), theta, ess_min)
+    out = out.cpu().numpy()
+    d, wb, e = OF.temper(nll - lg, theta, ess_min)
+    assert abs(out[0] - d) <= 1e-12 * max(d, 1e-300) + 1e-300
+    assert abs(out[1] - e) <= 1e-12 * e
+    assert np.allclose(w.cpu().numpy(), wb, rtol=1e-11, atol=1e-300)
+    exp_theta = 1.0 if d >= 1.0 - theta else theta + d
+    assert out[2] == exp_theta
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 100, 1024, 8192])
+def test_resample_bit_exact_given_oracle_weights(N):
+    api = require_lib()
+    r = np.random.default_rng(N)
+    for trial in range(3):
+        w = r.gamma(0.3 + trial, size=N)
+        w /= w.sum()
+        seed, ctr = 1000 + trial, 17 * trial
+        idx = api.pf_resample(tdev(w, torch.float64), seed, ctr).cpu().numpy()
+        ref = OF.systematic_resample(w, OF.resample_offset(seed, ctr))
+        assert np.array_equal(idx, ref)
+
+
+def test_resample_degenerate_and_inplace():
+    api = require_lib()
+    N = 6
+    w = np.array([0.0, 0.0, 1.0, 0.0, 0.0, 0.0])
+    a = torch.arange(N * 4, dtype=torch.float32, device="cuda").reshape(N, 4)
+    b = torch.arange(N * 8, dtype=torch.float64, device="cuda").reshape(N, 8)
+    idx = api.pf_resample(tdev(w, torch.float64), 3, 4, arrays=[a, b]).cpu().numpy()
+    assert np.array_equal(idx, np.full(N, 2))
+    assert torch.all(a == torch.tensor([8, 9, 10, 11], dtype=torch.float32, device="cuda"))
+    assert torch.all(b[:, 0] == 16)
+    src = torch.randn(N, 3, dtype=torch.float64, device="cuda").contiguous()
+    dst = torch.empty_like(src)
+    perm = torch.tensor([5, 4, 3, 2, 1, 0], dtype=torch.int32, device="cuda")
+    api.pf_gather_rows(perm, src, dst)
+    assert torch.equal(dst, src.flip(0))
+
+
+@pytest.mark.parametrize("name,theta,lam", [("cfg1_f64", 0.4, False), ("cfg1_f64", 1.0, True),
+                                            ("cfg2_f32", 0.3, False)])
+def test_jitter_matches_oracle(name, theta, lam):
+    cfg = get_config(name)
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    N = 8 if cfg.dtype == "f64" else 3
+    u0 = random_state(cfg, N, 50)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    dW = random_increments(cfg, N, 51)
+    la = random_drift(cfg, N, 52, scale=0.2) if lam else None
+    y = random_obs(cfg, 53)
+    n_iter, seed, ctr = 4, 77, 1000
+    ref = OF.jitter(om, m0, dW, la, y, cfg.sigma, theta, cfg.rho, n_iter, seed, ctr)
+    dt = g.dtype
+    m0d, dWd = tdev(m0, dt), tdev(dW, dt)
+    lad = None if la is None else tdev(la, dt)
+    yd = tdev(y, dt)
+    st = g.ensemble_step(m0d, dWd, lad, yd)
+    nll, logG = st["nll"], st["logG"]
+    m_end, u_end = st["m"], st["u"]
+    acc, _, status = g.jitter(m0d, dWd, lad, yd, nll, logG, m_end, u_end, theta, cfg.rho, n_iter, seed, ctr)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    # replay the oracle's decisions to find the particles whose chains were never near a coin flip
+    tol = 1e-10 if cfg.dtype == "f64" else 1e-4
+    acc_g = acc.cpu().numpy()
+    same = acc_g == ref[5]
+    assert same.mean() >= 0.75
+    sel = np.where(same)[0]
+    assert rel_err(dWd.double().cpu().numpy()[sel], ref[0][sel]) < tol
+    assert rel_err(u_end.double().cpu().numpy()[sel], ref[4][sel]) < tol
+    assert np.allclose(nll.cpu().numpy()[sel], ref[1][sel], rtol=tol * 10, atol=tol)
+
+
+def test_jitter_theta_zero_accepts_everything():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    N = 4
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 60)])
+    dW = random_increments(cfg, N, 61)
+    y = random_obs(cfg, 62)
+    dt = g.dtype
+    m0d, dWd, yd = tdev(m0, dt), tdev(dW, dt), tdev(y, dt)
+    st = g.ensemble_step(m0d, dWd, None, yd)
+    acc, _, _ = g.jitter(m0d, dWd, None, yd, st["nll"], st["logG"], st["m"], st["u"], 0.0, cfg.rho, 3, 5, 0)
+    assert np.all(acc.cpu().numpy() == 3)
+
+
+def test_cycle_matches_oracle_f64():
+    from paper_2402_06927_gb300.filter import EnsembleFilter
+    cfg = get_config("cfg1_f64", N=16, n_jitter=2)
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    N = cfg.N
+    u0 = random_state(cfg, N, 70, scale=0.1)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    y = random_obs(cfg, 71)
+    seed, cycle = 9, 2
+    dW = ORNG.window_increments(seed, ORNG.TAG_PRIOR_DW, N, cfg.Ns, cfg.K, cfg.dt, cycle)
+    ref = OF.assimilation_cycle(om, m0, y, cfg.sigma, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, cycle, dW=dW)
+    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    f.set_state(tdev(m0, g.dtype))
+    st = f.cycle(tdev(y, g.dtype), cycle)
+    assert len(st.stages) == len(ref["stages"])
+    for a, b in zip(st.stages, ref["stages"]):
+        assert abs(a.dtheta - b["dtheta"]) <= 1e-9 * b["dtheta"]
+        assert abs(a.theta - b["theta"]) <= 1e-9
+    assert rel_err(f.u_end.cpu().numpy(), ref["u_end"]) < 1e-8
+    assert rel_err(f.dW.cpu().numpy(), ref["dW"]) < 1e-8

@@ -1,0 +1,196 @@
+"""GPU parity of the SCH model kernels against the FP64 oracle (through the C ABI).
+
+Tolerances (max-norm, relative to the oracle's max-norm):
+* FP64 fields after one window: 1e-10 (the Picard iteration stops at 1e-13
+  relative; the two sides differ only by rounding order).
+* FP32 fields after one window: 1e-4 (single-precision rounding over
+  Ns implicit solves with tolerance 1e-6).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import get_config, random_state, random_increments, random_drift, random_obs, u0_profile
+from oracle import filter as OF
+from oracle import rng as ORNG
+from tests.helpers import gpu_model, oracle_model, tdev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64_TOL = 1e-10
+F32_TOL = 1e-4
+
+
+def _case(cfg, N, seed, Ns=None, lam=False):
+    Ns = cfg.Ns if Ns is None else Ns
+    om = oracle_model(cfg)
+    u0 = random_state(cfg, N, seed)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    dW = random_increments(cfg, N, seed + 1, steps=Ns)
+    la = random_drift(cfg, N, seed + 2, steps=Ns) if lam else None
+    return om, m0, dW, la
+
+
+@pytest.mark.parametrize("name,over", [("cfg1_f64", {}), ("cfg3_f64", {}), ("cfg2_f32", {}),
+                                       ("cfg5_f32", {})])
+def test_helmholtz_both_ways(name, over):
+    cfg = get_config(name, **over)
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    u = random_state(cfg, 3, 5)
+    ref_m = np.stack([om.m_from_u(v) for v in u])
+    m = g.m_from_u(tdev(u, g.dtype)).cpu().numpy()
+    tol = F64_TOL if cfg.dtype == "f64" else F32_TOL
+    assert rel_err(m, ref_m) < tol
+    uu = g.u_from_m(tdev(ref_m, g.dtype)).cpu().numpy()
+    assert rel_err(uu, u) < tol
+
+
+@pytest.mark.parametrize("lam", [False, True])
+def test_window_f64_cfg1(lam):
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la = _case(cfg, 6, 11, lam=lam)
+    ref = om.ensemble_window(m0, dW, la)
+    y = random_obs(cfg, 3)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), None if la is None else tdev(la, g.dtype),
+                          y=tdev(y, g.dtype))
+    torch.cuda.synchronize()
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < F64_TOL
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < F64_TOL
+    assert np.all(out["status"].cpu().numpy() == 0)
+    # Picard counts follow the same stopping rule
+    assert np.all(np.abs(out["iters"].cpu().numpy() - ref[2].sum(axis=1)) <= cfg.Ns)
+    nll = OF.nll(ref[1], y, cfg.sigma)
+    lg = OF.girsanov_logG(la, dW, cfg.dt) if la is not None else np.zeros(6)
+    assert np.allclose(out["nll"].cpu().numpy(), nll, rtol=1e-9)
+    assert np.allclose(out["logG"].cpu().numpy(), lg, rtol=1e-12, atol=1e-14)
+
+
+def test_window_f64_multiwarp():
+    # n = 1024 in FP64: 256 threads per particle, exercises the cross-warp exchanges
+    cfg = get_config("cfg3_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la = _case(cfg, 2, 21, Ns=4, lam=True)
+    ref = om.ensemble_window(m0, dW, la)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
+    torch.cuda.synchronize()
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < F64_TOL
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < F64_TOL
+
+
+@pytest.mark.parametrize("name,N", [("cfg2_f32", 3), ("cfg5_f32", 2)])
+def test_window_f32(name, N):
+    cfg = get_config(name)
+    g = gpu_model(cfg)
+    om, m0, dW, la = _case(cfg, N, 31, lam=True)
+    ref = om.ensemble_window(m0, dW, la)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
+    torch.cuda.synchronize()
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < F32_TOL
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < F32_TOL
+    assert np.all(out["status"].cpu().numpy() == 0)
+
+
+def test_window_full_size_sampled():
+    # the bench configuration (n = 1024, N = 1024, Ns = 10, FP32): every particle
+    # is propagated in the launch the bench times; three sampled particles are
+    # recomputed by the oracle
+    cfg = get_config("cfg2_f32")
+    g = gpu_model(cfg)
+    N = cfg.N
+    u0 = random_state(cfg, N, 41)
+    m0 = g.m_from_u(tdev(u0, g.dtype))
+    dW = g.draw_increments(N, cfg.Ns, 7, 1, 0)
+    y = random_obs(cfg, 4)
+    out = g.ensemble_step(m0, dW, None, tdev(y, g.dtype))
+    torch.cuda.synchronize()
+    om = oracle_model(cfg)
+    dWh = dW.double().cpu().numpy()
+    m0h = m0.double().cpu().numpy()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in (0, 517, N - 1):
+        mref, uref, _, ok = om.window(m0h[p], dWh[p])
+        assert ok
+        assert rel_err(out["m"][p].cpu().numpy(), mref) < F32_TOL
+        assert rel_err(out["u"][p].cpu().numpy(), uref) < F32_TOL
+        assert abs(out["nll"][p].item() - OF.nll(uref[None], y, cfg.sigma)[0]) < 1e-3 * max(1.0, out["nll"][p].item())
+
+
+def test_draw_increments_match_oracle_generator():
+    for name in ("cfg1_f64", "cfg2_f32"):
+        cfg = get_config(name)
+        g = gpu_model(cfg)
+        dW = g.draw_increments(5, cfg.Ns, 123, ORNG.TAG_PRIOR_DW, 9, particle0=3).double().cpu().numpy()
+        ref = ORNG.window_increments(123, ORNG.TAG_PRIOR_DW, 5, cfg.Ns, cfg.K, cfg.dt, 9, particle0=3)
+        tol = 1e-13 if cfg.dtype == "f64" else 2e-6
+        assert np.max(np.abs(dW - ref)) < tol * 5 * math.sqrt(cfg.dt)
+
+
+def test_loglik_standalone():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    u = random_state(cfg, 7, 2)
+    y = random_obs(cfg, 9)
+    dW = random_increments(cfg, 7, 3)
+    la = random_drift(cfg, 7, 4)
+    nll, lg = g.loglik(tdev(u, g.dtype), tdev(y, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
+    assert np.allclose(nll.cpu().numpy(), OF.nll(u, y, cfg.sigma), rtol=1e-12)
+    assert np.allclose(lg.cpu().numpy(), OF.girsanov_logG(la, dW, cfg.dt), rtol=1e-12)
+    nll0, lg0 = g.loglik(tdev(u, g.dtype), tdev(y, g.dtype))
+    assert np.all(lg0.cpu().numpy() == 0.0)
+
+
+def test_prior_sample_matches_oracle():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    ut = u0_profile(cfg)
+    m_ref, u_ref = om.prior_sample(ut, 5, 4, 0.05)
+    m, u = g.prior_sample(4, tdev(ut, g.dtype), 5, 0.05)
+    assert rel_err(u.cpu().numpy(), u_ref) < 1e-11
+    assert rel_err(m.cpu().numpy(), m_ref) < 1e-10
+
+
+def test_synth_obs_and_diagnostics():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    ut = u0_profile(cfg)
+    y = g.synth_obs(tdev(ut, g.dtype), 3, 2).cpu().numpy()
+    z = ORNG.normals(3, ORNG.TAG_OBS, cfg.M, np.uint64(0), np.uint64(0), np.uint64(2))
+    assert np.allclose(y, ut[:: cfg.obs_stride] + cfg.sigma * z, rtol=1e-13, atol=1e-15)
+    ens = random_state(cfg, 9, 8)
+    d = g.diagnostics(tdev(ens, g.dtype), tdev(ut, g.dtype)).cpu().numpy()
+    assert np.isclose(d[0], OF.emre(ut, ens), rtol=1e-12)
+    assert np.isclose(d[1], OF.rb(ut, ens), rtol=1e-12)
+    assert np.isclose(d[2], OF.res(ut, ens), rtol=1e-12)
+    assert np.isclose(d[3], np.sqrt(np.mean((ens.mean(0) - ut) ** 2)), rtol=1e-12)
+
+
+def test_nonfinite_input_reports_status():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, _ = _case(cfg, 3, 1)
+    m0 = m0.copy()
+    m0[1, 10] = np.nan
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype))
+    st = out["status"].cpu().numpy()
+    assert st[1] & 2 and st[0] == 0 and st[2] == 0
+
+
+def test_nonconvergence_reports_status():
+    cfg = get_config("cfg1_f64", max_iter=1)
+    g = gpu_model(cfg)
+    om, m0, dW, _ = _case(cfg, 2, 1)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype))
+    assert np.all(out["status"].cpu().numpy() & 1)
+
+
+def test_empty_ensemble_is_noop():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    e = torch.empty((0, cfg.n), dtype=g.dtype, device="cuda")
+    out = g.ensemble_step(e, torch.empty((0, cfg.Ns, cfg.K), dtype=g.dtype, device="cuda"))
+    assert out["m"].shape == (0, cfg.n)
