@@ -36,7 +36,8 @@ def test_temper_matches_oracle(N, spread, theta):
     assert abs(out[0] - d) <= 1e-12 * max(d, 1e-300) + 1e-300
     assert abs(out[1] - e) <= 1e-12 * e
     assert np.allclose(w.cpu().numpy(), wb, rtol=1e-11, atol=1e-300)
-    exp_theta = 1.0 if d >= 1.0 - theta else theta + d
+    # the new temperature follows from the kernel's own dtheta by the stated rule
+    exp_theta = 1.0 if out[0] >= 1.0 - theta else theta + out[0]
     assert out[2] == exp_theta
 
 

@@ -33,19 +33,29 @@ def _case(cfg, N, seed, Ns=None, lam=False):
     return om, m0, dW, la
 
 
-@pytest.mark.parametrize("name,over", [("cfg1_f64", {}), ("cfg3_f64", {}), ("cfg2_f32", {}),
-                                       ("cfg5_f32", {})])
-def test_helmholtz_both_ways(name, over):
-    cfg = get_config(name, **over)
+@pytest.mark.parametrize("name", ["cfg1_f64", "cfg3_f64", "cfg2_f32", "cfg5_f32"])
+def test_helmholtz_both_ways(name):
+    cfg = get_config(name)
     g = gpu_model(cfg)
     om = oracle_model(cfg)
     u = random_state(cfg, 3, 5)
+    if cfg.dtype == "f32":
+        u = u.astype(np.float32).astype(np.float64)
     ref_m = np.stack([om.m_from_u(v) for v in u])
     m = g.m_from_u(tdev(u, g.dtype)).cpu().numpy()
-    tol = F64_TOL if cfg.dtype == "f64" else F32_TOL
-    assert rel_err(m, ref_m) < tol
+    if cfg.dtype == "f64":
+        assert rel_err(m, ref_m) < F64_TOL
+    else:
+        # m = M^{-1} (M + alpha^2 K) u differentiates twice: the FP32 right-hand
+        # side carries ~3 eps (4 alpha^2 / h) |u| of rounding and M^{-1} has norm
+        # 3 / h, so |m - m_ref| <= 36 eps alpha^2 |u| / h^2 bounds the kernel's error
+        eps = np.finfo(np.float32).eps
+        bound = 36 * eps * cfg.alpha ** 2 * np.max(np.abs(u)) / cfg.h ** 2
+        assert np.max(np.abs(m - ref_m)) <= bound
+        assert np.max(np.abs(m - ref_m)) <= 1e-2 * np.max(np.abs(ref_m))
+    # u = H^{-1} M m smooths: well conditioned in both precisions
     uu = g.u_from_m(tdev(ref_m, g.dtype)).cpu().numpy()
-    assert rel_err(uu, u) < tol
+    assert rel_err(uu, u) < (F64_TOL if cfg.dtype == "f64" else F32_TOL)
 
 
 @pytest.mark.parametrize("lam", [False, True])
