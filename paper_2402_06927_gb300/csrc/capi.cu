@@ -18,8 +18,57 @@ struct sch_ctx {
 
 namespace {
 
+// Chunk-partition coefficients of the symmetric circulant tridiagonal matrix
+// with off-diagonal a and diagonal b, for chunks of C rows (double precision).
+void ctab_host(double a, double b, int C, CTab<double>& T) {
+    double al[8], ga[8];
+    memset(&T, 0, sizeof(T));
+    al[0] = -1.0;
+    ga[0] = 0.0;
+    for (int i = 1; i < C; ++i) {
+        const double r = 1.0 / (b - a * ga[i - 1]);
+        T.rden[i] = r;
+        ga[i] = a * r;
+        al[i] = -a * al[i - 1] * r;
+        T.gam[i] = ga[i];
+    }
+    double ap = 0.0, gp = -1.0;
+    T.alpp[C - 1] = ap;
+    T.gamp[C - 1] = gp;
+    for (int i = C - 2; i >= 1; --i) {
+        ap = al[i] - ga[i] * ap;
+        gp = -ga[i] * gp;
+        T.alpp[i] = ap;
+        T.gamp[i] = gp;
+    }
+    const double BF = (C == 2) ? b : b - a * T.alpp[1];
+    const double CF = (C == 2) ? a : -a * T.gamp[1];
+    T.a = a;
+    T.iBF = 1.0 / BF;
+    T.pa = a * T.iBF;
+    T.pc = CF * T.iBF;
+    T.ae = al[C - 1];
+    T.ge = ga[C - 1];
+}
+
 template <typename R>
-void fill_args(const sch_params& p, ModelArgs<R>& A) {
+void cast_tab(const CTab<double>& s, CTab<R>& d) {
+    for (int i = 0; i < 8; ++i) {
+        d.rden[i] = (R)s.rden[i];
+        d.gam[i] = (R)s.gam[i];
+        d.alpp[i] = (R)s.alpp[i];
+        d.gamp[i] = (R)s.gamp[i];
+    }
+    d.a = (R)s.a;
+    d.iBF = (R)s.iBF;
+    d.pa = (R)s.pa;
+    d.pc = (R)s.pc;
+    d.ae = (R)s.ae;
+    d.ge = (R)s.ge;
+}
+
+template <typename R>
+void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
     memset(&A, 0, sizeof(A));
     const double h = p.L / p.n;
     A.n = p.n;
@@ -43,6 +92,13 @@ void fill_args(const sch_params& p, ModelArgs<R>& A) {
     A.sigma_inv = (R)(1.0 / p.sigma);
     A.dt_d = p.dt;
     for (int j = 0; j < p.K / 2; ++j) A.amp4[j] = (R)(0.25 * p.amps[j]);
+    CTab<double> t;
+    ctab_host(h / 6.0 - a2 / h, 2.0 * h / 3.0 + 2.0 * a2 / h, C, t);
+    cast_tab(t, A.hel);
+    ctab_host(h / 6.0, 2.0 * h / 3.0, C, t);
+    cast_tab(t, A.mass);
+    ctab_host(h / 6.0 - 1.0 / h, 2.0 * h / 3.0 + 2.0 / h, C, t);
+    cast_tab(t, A.smooth);
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -70,8 +126,8 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     c->p = p;
     c->C = C;
     c->tp = tp;
-    fill_args(p, c->af);
-    fill_args(p, c->ad);
+    fill_args(p, C, c->af);
+    fill_args(p, C, c->ad);
     *ctx = c;
     return SCH_OK;
 }
@@ -211,8 +267,8 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
     if (N == 0 || n_iter == 0) return SCH_OK;
     if (!m_start || !dW || !y || !nll || !m_end || !u_end) return SCH_ERR_ARG;
     if (lambda && !logG) return SCH_ERR_ARG;
-    const size_t sm = (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
-                                                 : window_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
+    const size_t sm = (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
+                                                 : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
     const double sq = sqrt(1.0 - rho * rho);
     if (ctx->p.dtype == SCH_F32) {

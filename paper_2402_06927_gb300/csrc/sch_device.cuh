@@ -3,11 +3,7 @@
 // * Philox4x64-10 counter-based generator (Salmon et al., SC'11) and the
 //   Box-Muller transform, so that every draw is a pure function of
 //   (seed, purpose, block, step, particle, stream counter).
-// * CTA-wide helpers for the "one particle per CTA" layout: each of the TP
-//   threads owns C consecutive nodes of the periodic mesh in registers;
-//   neighbours at chunk ends are exchanged with warp shuffles plus a shared
-//   memory hop between warps.
-// * Cyclic parallel cyclic reduction (PCR) over one row per thread.
+// * Reciprocal and warp-reduction helpers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -81,81 +77,21 @@ __device__ __forceinline__ double uniform_open0(uint64_t seed, uint64_t tag, uin
 // --------------------------------------------------------------------------
 // arithmetic helpers
 // --------------------------------------------------------------------------
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// FP32: the hardware reciprocal approximation (relative error ~2^-23), ample
+// for the 1e-6 Picard tolerance of the FP32 path; FP64: correctly rounded.
+__device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
 template <typename R> __device__ __forceinline__ R rabs(R x) { return x < R(0) ? -x : x; }
 template <typename R> __device__ __forceinline__ bool finite_(R x) { return isfinite(x); }
 
 // --------------------------------------------------------------------------
-// CTA exchange helpers.  `base` holds two phases of EXCH_SLOTS 8-byte slots;
-// successive exchanges alternate phases, so a slot is rewritten only after a
-// later barrier that every reader of its previous value has passed.
+// warp reductions (every lane receives the result)
 // --------------------------------------------------------------------------
-constexpr int EXCH_SLOTS = 128;
-constexpr int EXCH_BYTES = 2 * EXCH_SLOTS * 8;
-
-struct Exch {
-    unsigned char* base;   // shared scratch for neighbour exchange (EXCH_BYTES)
-    int phase;
-    int tp;                // threads per particle (power of two, >= 32)
-
-    template <typename R>
-    __device__ __forceinline__ R* slots() const {
-        return reinterpret_cast<R*>(base + (phase & 1) * EXCH_SLOTS * 8);
-    }
-};
-
-// prev thread's `last` and next thread's `first` (cyclic over tp threads)
-template <typename R>
-__device__ __forceinline__ void halo(Exch& x, R first, R last, R& prev_last, R& next_first) {
-    const int lane = threadIdx.x & 31;
-    prev_last = __shfl_sync(FULL, last, (lane + 31) & 31);
-    next_first = __shfl_sync(FULL, first, (lane + 1) & 31);
-    if (x.tp > 32) {
-        const int nw = x.tp >> 5;
-        const int warp = threadIdx.x >> 5;
-        R* buf = x.slots<R>();
-        if (lane == 31) buf[warp] = last;
-        if (lane == 0) buf[32 + warp] = first;
-        __syncthreads();
-        if (lane == 0) prev_last = buf[(warp + nw - 1) & (nw - 1)];
-        if (lane == 31) next_first = buf[32 + ((warp + 1) & (nw - 1))];
-        x.phase++;
-    }
-}
-
-// next thread's values of a small tuple (cyclic)
-template <typename R, int V>
-__device__ __forceinline__ void from_next(Exch& x, const R (&mine)[V], R (&nxt)[V]) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int v = 0; v < V; ++v) nxt[v] = __shfl_sync(FULL, mine[v], (lane + 1) & 31);
-    if (x.tp > 32) {
-        const int nw = x.tp >> 5;
-        const int warp = threadIdx.x >> 5;
-        R* buf = x.slots<R>();
-        if (lane == 0) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) buf[warp * V + v] = mine[v];
-        }
-        __syncthreads();
-        if (lane == 31) {
-            const int w = (warp + 1) & (nw - 1);
-#pragma unroll
-            for (int v = 0; v < V; ++v) nxt[v] = buf[w * V + v];
-        }
-        x.phase++;
-    }
-}
-
-// prev and next thread's single value (cyclic)
-template <typename R>
-__device__ __forceinline__ void both_neighbours(Exch& x, R mine, R& prev, R& next) {
-    halo(x, mine, mine, prev, next);
-}
-
-// Block-wide reductions; all threads receive the result.
 template <typename R>
 __device__ __forceinline__ R warp_max(R v) {
 #pragma unroll
@@ -167,113 +103,6 @@ __device__ __forceinline__ R warp_sum(R v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
-}
-
-// max of two values across the tp threads of the CTA
-template <typename R>
-__device__ __forceinline__ void block_max2(Exch& x, R& a, R& b) {
-    a = warp_max(a);
-    b = warp_max(b);
-    if (x.tp > 32) {
-        const int nw = x.tp >> 5;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        R* buf = x.slots<R>();
-        if (lane == 0) { buf[warp] = a; buf[32 + warp] = b; }
-        __syncthreads();
-        a = buf[0]; b = buf[32];
-        for (int w = 1; w < nw; ++w) { a = fmax(a, buf[w]); b = fmax(b, buf[32 + w]); }
-        x.phase++;
-    }
-}
-
-// sum across the CTA in double
-__device__ __forceinline__ double block_sum(Exch& x, double v) {
-    v = warp_sum(v);
-    if (x.tp > 32) {
-        const int nw = x.tp >> 5;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        double* buf = x.slots<double>();
-        if (lane == 0) buf[warp] = v;
-        __syncthreads();
-        double s = 0.0;
-        for (int w = 0; w < nw; ++w) s += buf[w];
-        v = s;
-        x.phase++;
-    }
-    return v;
-}
-
-// --------------------------------------------------------------------------
-// Cyclic PCR on one row per thread: A_t E_{t-1} + B_t E_t + C_t E_{t+1} = D_t,
-// t = 0..tp-1 (indices mod tp, tp a power of two >= 32).  Levels with stride
-// s < tp/2 eliminate the neighbours at distance s; at stride tp/2 the two
-// neighbours coincide and a 2x2 system closes the solve.
-// `pbuf` holds 2 * tp rows of 4 values (double-buffered).
-// --------------------------------------------------------------------------
-template <typename R>
-struct Row4 { R a, c, d, rb; };
-
-template <typename R>
-__device__ __forceinline__ R pcr_cyclic(R A, R B, R Cc, R D, Row4<R>* pbuf, int tp) {
-    const int t = threadIdx.x;
-    int ph = 0;
-    for (int s = 1; s < (tp >> 1); s <<= 1) {
-        const R rb = rcp(B);
-        Row4<R>* buf = pbuf + ph * tp;
-        R Am, Cm, Dm, rbm, Ap, Cp, Dp, rbp;
-        buf[t] = Row4<R>{A, Cc, D, rb};
-        __syncthreads();
-        const Row4<R> lo = buf[(t - s) & (tp - 1)];
-        const Row4<R> hi = buf[(t + s) & (tp - 1)];
-        Am = lo.a; Cm = lo.c; Dm = lo.d; rbm = lo.rb;
-        Ap = hi.a; Cp = hi.c; Dp = hi.d; rbp = hi.rb;
-        const R k1 = A * rbm;
-        const R k2 = Cc * rbp;
-        // B' = B - C_{t-s} k1 - A_{t+s} k2
-        const R nB = B - Cm * k1 - Ap * k2;
-        const R nD = D - Dm * k1 - Dp * k2;
-        A = -Am * k1;
-        Cc = -Cp * k2;
-        B = nB;
-        D = nD;
-        ph ^= 1;
-    }
-    // closing 2x2 with the row half a period away
-    Row4<R>* buf = pbuf + ph * tp;
-    const R e = A + Cc;
-    buf[t] = Row4<R>{e, B, D, R(0)};
-    __syncthreads();
-    const Row4<R> o = buf[t ^ (tp >> 1)];
-    // rows: B E_t + e E_j = D ;  o.c E_j + o.a E_t = o.d   (o.a = e_j, o.c = B_j)
-    const R det = B * o.c - e * o.a;
-    const R E = (D * o.c - e * o.d) / det;
-    __syncthreads();   // pbuf may be reused right after
-    return E;
-}
-
-// Same for a circulant system whose A, B, C are the same on every row at every
-// level: only D travels.  k1[l], k2[l] are the level multipliers and
-// f1 E = f1 D + f2 D_{t + tp/2} closes the solve.
-template <typename R>
-__device__ __forceinline__ R pcr_cyclic_const(R D, const R* k1, const R* k2, R f1, R f2, R* dbuf,
-                                              int tp) {
-    const int t = threadIdx.x;
-    int ph = 0, l = 0;
-    for (int s = 1; s < (tp >> 1); s <<= 1, ++l) {
-        R* buf = dbuf + ph * tp;
-        buf[t] = D;
-        __syncthreads();
-        const R Dm = buf[(t - s) & (tp - 1)];
-        const R Dp = buf[(t + s) & (tp - 1)];
-        D = D - k1[l] * Dm - k2[l] * Dp;
-        ph ^= 1;
-    }
-    R* buf = dbuf + ph * tp;
-    buf[t] = D;
-    __syncthreads();
-    const R Dj = buf[t ^ (tp >> 1)];
-    __syncthreads();
-    return f1 * D + f2 * Dj;
 }
 
 }  // namespace sch

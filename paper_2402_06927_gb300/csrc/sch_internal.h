@@ -10,7 +10,18 @@
 
 namespace sch {
 
-// Precomputed scalars of the discretised model, passed by value to kernels.
+// A constant symmetric circulant tridiagonal matrix (off-diagonal a, diagonal b)
+// in chunk-partitioned form: the forward/backward sweep coefficients of a
+// chunk of C <= 8 rows and the coefficients of its reduced "first" and "last"
+// rows, identical in every chunk.  Computed on the host in double precision.
+template <typename R>
+struct CTab {
+    R rden[8], gam[8], alpp[8], gamp[8];
+    R a, iBF, pa, pc, ae, ge;
+};
+
+// Precomputed scalars of the discretised model, passed by value to kernels
+// (so that every thread reads them from the constant parameter bank).
 template <typename R>
 struct ModelArgs {
     int n, K, K2, M, stride, max_iter;
@@ -24,6 +35,9 @@ struct ModelArgs {
     R sigma_inv;
     double dt_d;
     R amp4[SCH_MAX_K / 2];  // a_j / 4
+    CTab<R> hel;            // M + alpha^2 K
+    CTab<R> mass;           // M
+    CTab<R> smooth;         // M + K (the (I - d_xx) smoothing of the prior)
 };
 
 template <typename R>
@@ -69,6 +83,8 @@ int launch_helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cud
 template <typename R, int C>
 int launch_prior(const ModelArgs<R>& A, const R* u_truth, uint64_t seed, R scale, R* m, R* u, int N,
                  cudaStream_t st);
+template <typename R, int C>
+size_t jitter_smem(int tp, int Ns, int K);
 template <typename R>
 int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0,
                 R* dW, cudaStream_t st);

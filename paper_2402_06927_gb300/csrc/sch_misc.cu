@@ -1,0 +1,179 @@
+// Small kernels around the propagation: Philox draws of the window noise,
+// the standalone likelihood / Girsanov weight, synthetic observations of a
+// truth trajectory and the EMRE / RB / RES diagnostics of Sec. 4.1.1.
+#include "sch_internal.h"
+
+namespace sch {
+
+// dW[p][s][k] = sqrt(dt) z, z from block (k/4, s, particle0 + p, ctr)
+template <typename R>
+__global__ void draw_kernel(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr,
+                            int particle0, R* dW) {
+    const int nblk = (K + 3) >> 2;
+    const long long tot = (long long)N * Ns * nblk;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(q % nblk);
+        const int s = (int)((q / nblk) % Ns);
+        const int p = (int)(q / ((long long)nblk * Ns));
+        R z[4];
+        normal4<R>(seed, tag, (uint64_t)b, (uint64_t)s, (uint64_t)(particle0 + p), ctr, z);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = 4 * b + e;
+            if (k < K) dW[((size_t)p * Ns + s) * K + k] = sqdt * z[e];
+        }
+    }
+}
+
+// one warp per particle: nll and logG of given end states
+template <typename R>
+__global__ void loglik_kernel(ModelArgs<R> A, int N, const R* u, const R* y, const R* dW,
+                              const R* lam, int Ns, double* nll, double* logG) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= N) return;
+    const R* up = u + (size_t)warp * A.n;
+    double acc = 0.0;
+    for (int j = lane; j < A.M; j += 32) {
+        const R r = (up[j * A.stride] - y[j]) * A.sigma_inv;
+        acc += (double)r * (double)r;
+    }
+    acc = warp_sum(acc);
+    double g = 0.0;
+    if (lam) {
+        const int NK = Ns * A.K;
+        for (int q = lane; q < NK; q += 32) {
+            const double l = lam[(size_t)warp * NK + q], w = dW[(size_t)warp * NK + q];
+            g += l * w + 0.5 * l * l * A.dt_d;
+        }
+    }
+    g = warp_sum(g);
+    if (lane == 0) {
+        nll[warp] = 0.5 * acc;
+        if (logG) logG[warp] = -g;
+    }
+}
+
+template <typename R>
+int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0,
+                R* dW, cudaStream_t st) {
+    const long long tot = (long long)N * Ns * ((K + 3) / 4);
+    const int threads = 256;
+    long long blocks = (tot + threads - 1) / threads;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    draw_kernel<R><<<(int)blocks, threads, 0, st>>>(N, Ns, K, sqdt, seed, tag, ctr, particle0, dW);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+template <typename R>
+int launch_loglik(const ModelArgs<R>& A, int N, const R* u, const R* y, const R* dW, const R* lam, int Ns,
+                  double* nll, double* logG, cudaStream_t st) {
+    const int threads = 256;
+    const int blocks = (N * 32 + threads - 1) / threads;
+    loglik_kernel<R><<<blocks, threads, 0, st>>>(A, N, u, y, dW, lam, Ns, nll, logG);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+template int launch_draw<float>(int, int, int, float, uint64_t, uint64_t, uint64_t, int, float*, cudaStream_t);
+template int launch_draw<double>(int, int, int, double, uint64_t, uint64_t, uint64_t, int, double*,
+                                 cudaStream_t);
+template int launch_loglik<float>(const ModelArgs<float>&, int, const float*, const float*, const float*,
+                                  const float*, int, double*, double*, cudaStream_t);
+template int launch_loglik<double>(const ModelArgs<double>&, int, const double*, const double*,
+                                   const double*, const double*, int, double*, double*, cudaStream_t);
+
+// y_j = u(x_j) + sigma z_j, z_j keyed (seed, SCH_TAG_OBS, (j / 4, 0, 0, ctr))
+template <typename R>
+__global__ void synth_obs_kernel(ModelArgs<R> A, const R* u, uint64_t seed, uint64_t ctr, R sigma, R* y) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= A.M) return;
+    R z[4];
+    normal4<R>(seed, SCH_TAG_OBS, (uint64_t)(j >> 2), 0, 0, ctr, z);
+    y[j] = u[j * A.stride] + sigma * z[j & 3];
+}
+
+// ensemble mean per node and the truth-based node sums:
+// ws[i] = mean_p u[p][i]; out[4] += u_a^2; out[5] += (u_a - mean)^2
+template <typename R>
+__global__ void diag_mean_kernel(ModelArgs<R> A, int N, const R* u, const R* ua, double* ws, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double a = 0.0, b = 0.0;
+    if (i < A.n) {
+        double s = 0.0;
+        for (int p = 0; p < N; ++p) s += (double)u[(size_t)p * A.n + i];
+        const double mean = s / N;
+        ws[i] = mean;
+        const double t = (double)ua[i];
+        a = t * t;
+        b = (t - mean) * (t - mean);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[4], a);
+        atomicAdd(&out[5], b);
+    }
+}
+
+// one warp per particle: out[6] += |u_p - u_a|, out[7] += |u_p - mean|
+template <typename R>
+__global__ void diag_particle_kernel(ModelArgs<R> A, int N, const R* u, const R* ua, const double* ws,
+                                     double* out) {
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (p >= N) return;
+    double e = 0.0, f = 0.0;
+    for (int i = lane; i < A.n; i += 32) {
+        const double v = (double)u[(size_t)p * A.n + i];
+        const double d1 = v - (double)ua[i], d2 = v - ws[i];
+        e += d1 * d1;
+        f += d2 * d2;
+    }
+    e = warp_sum(e);
+    f = warp_sum(f);
+    if (lane == 0) {
+        atomicAdd(&out[6], sqrt(e));
+        atomicAdd(&out[7], sqrt(f));
+    }
+}
+
+__global__ void diag_zero_kernel(double* out) {
+    if (threadIdx.x < 8) out[threadIdx.x] = 0.0;
+}
+
+template <typename R>
+__global__ void diag_final_kernel(ModelArgs<R> A, int N, double* out) {
+    if (threadIdx.x != 0) return;
+    const double na = sqrt(out[4]);
+    out[0] = out[6] / N / na;                 // EMRE
+    out[1] = sqrt(out[5]) / na;               // RB
+    out[2] = out[7] / (N - 1) / na;           // RES
+    out[3] = sqrt(out[5] / A.n);              // RMSE of the ensemble mean
+}
+
+template <typename R>
+int launch_synth_obs(const ModelArgs<R>& A, const R* u, uint64_t seed, uint64_t ctr, R* y, cudaStream_t st) {
+    synth_obs_kernel<R><<<(A.M + 127) / 128, 128, 0, st>>>(A, u, seed, ctr, R(1) / A.sigma_inv, y);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+template <typename R>
+int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* ua, double* ws, double* out, cudaStream_t st) {
+    diag_zero_kernel<<<1, 32, 0, st>>>(out);
+    diag_mean_kernel<R><<<(A.n + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
+    diag_particle_kernel<R><<<(N * 32 + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
+    diag_final_kernel<R><<<1, 32, 0, st>>>(A, N, out);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+template int launch_synth_obs<float>(const ModelArgs<float>&, const float*, uint64_t, uint64_t, float*, cudaStream_t);
+template int launch_synth_obs<double>(const ModelArgs<double>&, const double*, uint64_t, uint64_t, double*,
+                                      cudaStream_t);
+template int launch_diag<float>(const ModelArgs<float>&, int, const float*, const float*, double*, double*,
+                                cudaStream_t);
+template int launch_diag<double>(const ModelArgs<double>&, int, const double*, const double*, double*, double*,
+                                 cudaStream_t);
+
+}  // namespace sch
