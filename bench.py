@@ -31,10 +31,21 @@ if ROOT not in sys.path:
 
 WORKLOAD = "cfg2_f32"
 METRIC = "particle-timesteps/s"
-# algorithmic flops per node per Picard iteration of the linearly implicit
-# midpoint step: dv 3, left operator 7, right-hand side 8,
-# cyclic variable tridiagonal solve 14, Helmholtz 10, convergence 2
-FLOPS_PER_NODE_ITER = 44
+# Algorithmic flops per node of the implicit-midpoint step, counted on the plain
+# algorithm (each +, -, *, / is one flop).  Per Picard iteration:
+#  linearly implicit (LI): dv 3, left operator 7, right-hand side 8, cyclic
+#    variable tridiagonal solve 14 (Thomas 8 + Sherman-Morrison 6), Helmholtz 10
+#    (mass product 4 + factored cyclic solve 6), convergence 2 -> 44;
+#  explicit advection (EA): dv 3, mbar 2, advection 6, right-hand side 1,
+#    factored cyclic solve of M + mu dt/2 K 6, Helmholtz 10, convergence 2 -> 30.
+# Per step: noise synthesis 2K, and for EA the right operator (M - mu dt/2 K) m0 5.
+FLOPS_PER_NODE_ITER = {"li": 44, "ea": 30}
+FLOPS_PER_NODE_STEP_EXTRA = {"li": 0, "ea": 5}
+
+
+def step_flops(n, K, solver, iters, steps):
+    """Algorithmic flops of `steps` particle-steps that took `iters` Picard iterations in total."""
+    return n * (FLOPS_PER_NODE_ITER[solver] * iters + (2 * K + FLOPS_PER_NODE_STEP_EXTRA[solver]) * steps)
 
 
 def _peaks():
@@ -261,7 +272,8 @@ def run_ours(args):
     jit_ms = timer.elapsed_ms()
     it_sum = sum(int(t.sum().item()) for t in timer.iters)
     n_launch = len(jit_ms)
-    flops = cfg.n * (FLOPS_PER_NODE_ITER * it_sum + 2 * cfg.K * N * cfg.Ns * cfg.n_jitter * n_launch)
+    solver = "ea" if cfg.dtype == "f32" else "li"
+    flops = step_flops(cfg.n, cfg.K, solver, it_sum, N * cfg.Ns * cfg.n_jitter * n_launch)
     jit_s = sum(jit_ms) / 1000.0
     achieved = flops / jit_s / 1e12
     peak = fp32_peak_tflops()
@@ -313,9 +325,10 @@ def run_ours(args):
                        "l2": "flushed between timed steps (256 MB write)",
                        "cycles_per_s": args.steps * ws / dev_s_max,
                        "mean_tempering_stages": statistics.mean(stages),
-                       "mean_picard_iters_per_step": mean_iters,
+                       "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
-            "roofline": {"bound": "alu", "kernel": "jitter_kernel<float,8>", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": f"jitter_kernel<float,8,128,{solver.upper()}>",
+                         "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                          "peak_note": "FP32 FMA pipe 152 SMs x 128 lanes x 2 x max SM clock"},
             "gpu_launches": launches,

@@ -56,6 +56,17 @@ enum { SCH_DEV_NOCONVERGE = 1, SCH_DEV_NONFINITE = 2 };
 
 enum { SCH_F64 = 0, SCH_F32 = 1 };
 
+/* Picard iteration used to solve each implicit-midpoint step (the paper names
+ * none; both reach the same fixed point of Eq. fde1 to params.tol):
+ *   SCH_SOLVER_LI  linearly implicit: dv frozen at the last iterate, the cyclic
+ *                  tridiagonal (M + mu dt/2 K + 1/2 A_dv) solved each iteration;
+ *   SCH_SOLVER_EA  explicit advection: A(mbar, dv) at the last iterate moved to
+ *                  the right-hand side, so only the constant matrices
+ *                  M + mu dt/2 K and M + alpha^2 K are solved (cheaper
+ *                  iterations, slower contraction);
+ *   SCH_SOLVER_AUTO  EA for SCH_F32, LI for SCH_F64. */
+enum { SCH_SOLVER_AUTO = 0, SCH_SOLVER_LI = 1, SCH_SOLVER_EA = 2 };
+
 enum {
     SCH_TAG_PRIOR_DW = 1, SCH_TAG_PCN = 2, SCH_TAG_PCN_ACCEPT = 3, SCH_TAG_RESAMPLE = 4,
     SCH_TAG_TRUTH = 5, SCH_TAG_OBS = 6, SCH_TAG_INIT = 7, SCH_TAG_NUDGE = 8
@@ -78,6 +89,7 @@ typedef struct {
     double tol;          /* Picard stop: max|dm| <= tol * max(1, max|m|) */
     int32_t max_iter;    /* Picard iteration limit per step */
     int32_t dtype;       /* SCH_F64 or SCH_F32: precision of fields, dW, lambda */
+    int32_t solver;      /* SCH_SOLVER_* */
 } sch_params;
 
 typedef struct sch_ctx sch_ctx;

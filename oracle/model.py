@@ -20,12 +20,18 @@ cyclic tridiagonal triple (a, b, c): row i reads a_i x_{i-1} + b_i x_i +
 c_i x_{i+1}.  Cyclic systems are solved by Sherman-Morrison on top of LAPACK's
 banded solver (scipy.linalg.solve_banded), the textbook route.
 
-The nonlinear step (the paper names no solver) is solved by a linearly
-implicit Picard iteration: with dv frozen at iterate p, solve
-(M + mu dt/2 K + 1/2 A_dv) m^{p+1} = (M - mu dt/2 K - 1/2 A_dv) m0, then
-u^{p+1} = H^{-1} M m^{p+1}, until max|m^{p+1} - m^p| <= tol max(1, max|m^{p+1}|).
-Its fixed point is the solution of Eq. fde1, which ``residual_quadrature``
-checks independently with 3-point Gauss quadrature.
+The nonlinear step (the paper names no solver) is solved by a Picard
+iteration, stopped when max|m^{p+1} - m^p| <= tol max(1, max|m^{p+1}|).  Two
+iterations with the same fixed point (the solution of Eq. fde1, which
+``residual_quadrature`` checks independently with 3-point Gauss quadrature):
+
+* ``scheme="li"`` (linearly implicit): with dv frozen at iterate p, solve
+  (M + mu dt/2 K + 1/2 A_dv) m^{p+1} = (M - mu dt/2 K - 1/2 A_dv) m0;
+* ``scheme="ea"`` (explicit advection): with mbar and dv both taken at
+  iterate p, solve (M + mu dt/2 K) m^{p+1} = (M - mu dt/2 K) m0 - A(mbar^p, dv^p),
+  a constant matrix, at the price of a slower contraction;
+
+and in both u^{p+1} = H^{-1} M m^{p+1}.
 """
 from __future__ import annotations
 
@@ -52,13 +58,14 @@ class Model:
     amps: np.ndarray      # a_j, j = 1..K/2
     tol: float = 1e-13
     max_iter: int = 100
+    scheme: str = "li"
 
     @classmethod
-    def from_config(cls, cfg, tol=None, max_iter=None) -> "Model":
+    def from_config(cls, cfg, tol=None, max_iter=None, scheme="li") -> "Model":
         from workloads import mode_amplitudes
         return cls(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt,
                    amps=mode_amplitudes(cfg), tol=1e-13 if tol is None else tol,
-                   max_iter=100 if max_iter is None else max_iter)
+                   max_iter=100 if max_iter is None else max_iter, scheme=scheme)
 
     @property
     def h(self) -> float:
@@ -241,12 +248,18 @@ class Model:
         half_visc = 0.5 * self.mu * self.dt
         m_it = m0.copy()
         u_it = u0.copy()
+        if self.scheme == "ea":
+            lhs_c = tuple(Ma[j] + half_visc * Ka[j] for j in range(3))
+            rhs_c = self.apply(tuple(Ma[j] - half_visc * Ka[j] for j in range(3)), m0)
         for it in range(1, self.max_iter + 1):
             dv = 0.5 * self.dt * (u0 + u_it) + dU
             Aa = self.advection(dv)
-            lhs = tuple(Ma[j] + half_visc * Ka[j] + 0.5 * Aa[j] for j in range(3))
-            rop = tuple(Ma[j] - half_visc * Ka[j] - 0.5 * Aa[j] for j in range(3))
-            m_new = self.solve(lhs, self.apply(rop, m0))
+            if self.scheme == "ea":
+                m_new = self.solve(lhs_c, rhs_c - self.apply(Aa, 0.5 * (m0 + m_it)))
+            else:
+                lhs = tuple(Ma[j] + half_visc * Ka[j] + 0.5 * Aa[j] for j in range(3))
+                rop = tuple(Ma[j] - half_visc * Ka[j] - 0.5 * Aa[j] for j in range(3))
+                m_new = self.solve(lhs, self.apply(rop, m0))
             u_new = self.u_from_m(m_new)
             delta = np.max(np.abs(m_new - m_it))
             scale = max(1.0, np.max(np.abs(m_new)))

@@ -23,6 +23,7 @@ SCH_DEV_NOCONVERGE = 1
 SCH_DEV_NONFINITE = 2
 SCH_F64 = 0
 SCH_F32 = 1
+SCH_SOLVER_AUTO, SCH_SOLVER_LI, SCH_SOLVER_EA = 0, 1, 2
 
 TAG_PRIOR_DW, TAG_PCN, TAG_PCN_ACCEPT, TAG_RESAMPLE, TAG_TRUTH, TAG_OBS, TAG_INIT, TAG_NUDGE = range(1, 9)
 
@@ -32,7 +33,7 @@ class SchParams(ct.Structure):
         ("L", ct.c_double), ("n", ct.c_int32), ("alpha", ct.c_double), ("mu", ct.c_double),
         ("dt", ct.c_double), ("K", ct.c_int32), ("amps", ct.c_double * (SCH_MAX_K // 2)),
         ("M", ct.c_int32), ("sigma", ct.c_double), ("tol", ct.c_double), ("max_iter", ct.c_int32),
-        ("dtype", ct.c_int32),
+        ("dtype", ct.c_int32), ("solver", ct.c_int32),
     ]
 
 

@@ -39,7 +39,7 @@ class SchModel:
     """A library context for one set of model and observation parameters."""
 
     def __init__(self, L: float, n: int, alpha: float, mu: float, dt: float, amps: Sequence[float],
-                 M: int, sigma: float, tol: float, max_iter: int, dtype: str = "f32"):
+                 M: int, sigma: float, tol: float, max_iter: int, dtype: str = "f32", solver: str = "auto"):
         p = SchParams()
         p.L, p.n, p.alpha, p.mu, p.dt = L, n, alpha, mu, dt
         p.K = 2 * len(amps)
@@ -47,6 +47,7 @@ class SchModel:
             p.amps[j] = float(a)
         p.M, p.sigma, p.tol, p.max_iter = M, sigma, tol, max_iter
         p.dtype = SCH_F32 if dtype == "f32" else SCH_F64
+        p.solver = {"auto": 0, "li": 1, "ea": 2}[solver]
         self.params = p
         self.n, self.K, self.M, self.dt = n, p.K, M, dt
         self.dtype = torch.float32 if dtype == "f32" else torch.float64

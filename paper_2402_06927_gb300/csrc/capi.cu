@@ -51,6 +51,154 @@ void ctab_host(double a, double b, int C, CTab<double>& T) {
     T.ge = ga[C - 1];
 }
 
+// Reduced cyclic system of chunk table T for TP threads: lane-level sweep over
+// RR = TP/32 rows and the 32-lane PCR coefficients (double precision).
+void rtab_host(const CTab<double>& T, int TP, RTab<double>& Q) {
+    memset(&Q, 0, sizeof(Q));
+    const double A = -T.ae * T.pa, B = 1.0 - T.ae * T.pc - T.ge * T.pa, Cc = -T.ge * T.pc;
+    Q.A = A;
+    Q.B = B;
+    Q.Cc = Cc;
+    const int RR = TP / 32;
+    double LA = A, LB = B, LC = Cc;
+    if (RR > 1) {
+        double alf[16], gaf[16];
+        alf[0] = -1.0;
+        gaf[0] = 0.0;
+        for (int r = 1; r < RR; ++r) {
+            const double q = 1.0 / (B - A * gaf[r - 1]);
+            Q.q[r] = q;
+            gaf[r] = Cc * q;
+            alf[r] = -A * alf[r - 1] * q;
+            Q.ga[r] = gaf[r];
+        }
+        Q.aeL = alf[RR - 1];
+        Q.geL = gaf[RR - 1];
+        double ap = 0.0, gp = -1.0;
+        Q.alp[RR - 1] = ap;
+        Q.gap[RR - 1] = gp;
+        for (int r = RR - 2; r >= 1; --r) {
+            ap = alf[r] - gaf[r] * ap;
+            gp = -gaf[r] * gp;
+            Q.alp[r] = ap;
+            Q.gap[r] = gp;
+        }
+        const double BF = (RR == 2) ? B : B - Cc * Q.alp[1];
+        const double CF = (RR == 2) ? Cc : -Cc * Q.gap[1];
+        Q.iBF = 1.0 / BF;
+        Q.qa = A * Q.iBF;
+        Q.qc = CF * Q.iBF;
+        LA = -Q.aeL * Q.qa;
+        LB = 1.0 - Q.aeL * Q.qc - Q.geL * Q.qa;
+        LC = -Q.geL * Q.qc;
+    }
+    double a = LA, b = LB, c = LC;
+    for (int l = 0; l < 4; ++l) {
+        const double k1 = a / b, k2 = c / b;
+        Q.k1[l] = k1;
+        Q.k2[l] = k2;
+        const double nb = b - c * k1 - a * k2;
+        a = -a * k1;
+        c = -c * k2;
+        b = nb;
+    }
+    const double e = a + c, det = b * b - e * e;
+    Q.f1 = b / det;
+    Q.f2 = -e / det;
+}
+
+// chunk sweep of table T on a right-hand side r: the reduced "first" row value
+// pd, the "last" row value de and the interior particular solution dp
+void chunk_sweep(const CTab<double>& T, int C, const double* r, double& pd, double& de, double* dp) {
+    double d[8];
+    d[0] = 0.0;
+    for (int i = 1; i < C; ++i) d[i] = (r[i] - T.a * d[i - 1]) * T.rden[i];
+    for (int i = 0; i < C; ++i) dp[i] = 0.0;
+    for (int i = C - 2; i >= 1; --i) dp[i] = d[i] - T.gam[i] * dp[i + 1];
+    const double DF = (C == 2) ? r[0] : r[0] - T.a * dp[1];
+    pd = DF * T.iBF;
+    de = d[C - 1];
+}
+
+// the Helmholtz interface rows as linear functionals of the Picard chunk solution
+void hbasis_host(const CTab<double>& P, const CTab<double>& H, int C, double h6, HBasis<double>& B) {
+    memset(&B, 0, sizeof(B));
+    double wpd[8], wde[8], dp[8], r[8];
+    for (int j = 0; j < C; ++j) {
+        for (int i = 0; i < C; ++i) r[i] = (i == j) ? 1.0 : 0.0;
+        chunk_sweep(H, C, r, wpd[j], wde[j], dp);
+    }
+    auto mass_c = [&](const double* x, double* out) {
+        for (int j = 0; j < C; ++j) {
+            const double lo = (j > 0) ? x[j - 1] : 0.0, hi = (j < C - 1) ? x[j + 1] : 0.0;
+            out[j] = h6 * (lo + 4.0 * x[j] + hi);
+        }
+    };
+    for (int i = 1; i < C - 1; ++i) {
+        double e[8], me[8];
+        for (int j = 0; j < C; ++j) e[j] = (j == i) ? 1.0 : 0.0;
+        mass_c(e, me);
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < C; ++j) {
+            a += wpd[j] * me[j];
+            b += wde[j] * me[j];
+        }
+        B.apd[i] = a;
+        B.ade[i] = b;
+    }
+    double phF[8], phE[8], mF[8], mE[8];
+    for (int i = 0; i < C; ++i) {
+        phF[i] = (i == 0) ? 1.0 : (i == C - 1 ? 0.0 : -P.alpp[i]);
+        phE[i] = (i == C - 1) ? 1.0 : (i == 0 ? 0.0 : -P.gamp[i]);
+    }
+    mass_c(phF, mF);
+    mass_c(phE, mE);
+    for (int j = 0; j < C; ++j) {
+        B.cpF += wpd[j] * mF[j];
+        B.cpE += wpd[j] * mE[j];
+        B.cdF += wde[j] * mF[j];
+        B.cdE += wde[j] * mE[j];
+    }
+    B.cpEp = h6 * wpd[0];
+    B.cpFn = h6 * wpd[C - 1];
+    B.cdEp = h6 * wde[0];
+    B.cdFn = h6 * wde[C - 1];
+}
+
+template <typename R>
+void cast_rtab(const RTab<double>& s, RTab<R>& d) {
+    d.A = (R)s.A;
+    d.B = (R)s.B;
+    d.Cc = (R)s.Cc;
+    for (int i = 0; i < 16; ++i) {
+        d.q[i] = (R)s.q[i];
+        d.ga[i] = (R)s.ga[i];
+        d.alp[i] = (R)s.alp[i];
+        d.gap[i] = (R)s.gap[i];
+    }
+    d.qa = (R)s.qa;
+    d.qc = (R)s.qc;
+    d.iBF = (R)s.iBF;
+    d.aeL = (R)s.aeL;
+    d.geL = (R)s.geL;
+    for (int l = 0; l < 4; ++l) {
+        d.k1[l] = (R)s.k1[l];
+        d.k2[l] = (R)s.k2[l];
+    }
+    d.f1 = (R)s.f1;
+    d.f2 = (R)s.f2;
+}
+
+template <typename R>
+void cast_hb(const HBasis<double>& s, HBasis<R>& d) {
+    for (int i = 0; i < 8; ++i) {
+        d.apd[i] = (R)s.apd[i];
+        d.ade[i] = (R)s.ade[i];
+    }
+    d.cpF = (R)s.cpF; d.cpE = (R)s.cpE; d.cpEp = (R)s.cpEp; d.cpFn = (R)s.cpFn;
+    d.cdF = (R)s.cdF; d.cdE = (R)s.cdE; d.cdEp = (R)s.cdEp; d.cdFn = (R)s.cdFn;
+}
+
 template <typename R>
 void cast_tab(const CTab<double>& s, CTab<R>& d) {
     for (int i = 0; i < 8; ++i) {
@@ -77,6 +225,7 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
     A.M = p.M;
     A.stride = p.n / p.M;
     A.max_iter = p.max_iter;
+    A.solver = (p.solver != SCH_SOLVER_AUTO) ? p.solver : (p.dtype == SCH_F32 ? SCH_SOLVER_EA : SCH_SOLVER_LI);
     A.h = (R)h;
     A.dt = (R)p.dt;
     A.c0 = (R)(h / 6.0 - p.mu * p.dt / (2.0 * h));
@@ -91,14 +240,33 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
     A.hel_b = (R)(2.0 * h / 3.0 + 2.0 * a2 / h);
     A.sigma_inv = (R)(1.0 / p.sigma);
     A.dt_d = p.dt;
-    for (int j = 0; j < p.K / 2; ++j) A.amp4[j] = (R)(0.25 * p.amps[j]);
-    CTab<double> t;
-    ctab_host(h / 6.0 - a2 / h, 2.0 * h / 3.0 + 2.0 * a2 / h, C, t);
-    cast_tab(t, A.hel);
-    ctab_host(h / 6.0, 2.0 * h / 3.0, C, t);
-    cast_tab(t, A.mass);
-    ctab_host(h / 6.0 - 1.0 / h, 2.0 * h / 3.0 + 2.0 / h, C, t);
-    cast_tab(t, A.smooth);
+    for (int j = 0; j < p.K / 2; ++j) {
+        A.amp4[j] = (R)(0.25 * p.amps[j]);
+        A.rot_c[j] = (R)cos(2.0 * M_PI * (j + 1) / p.n);
+        A.rot_s[j] = (R)sin(2.0 * M_PI * (j + 1) / p.n);
+    }
+    const int TP = p.n / C;
+    CTab<double> th, tm, ts, tpic;
+    RTab<double> q;
+    ctab_host(h / 6.0 - a2 / h, 2.0 * h / 3.0 + 2.0 * a2 / h, C, th);
+    ctab_host(h / 6.0, 2.0 * h / 3.0, C, tm);
+    ctab_host(h / 6.0 - 1.0 / h, 2.0 * h / 3.0 + 2.0 / h, C, ts);
+    ctab_host(h / 6.0 - p.mu * p.dt / (2.0 * h), 2.0 * h / 3.0 + p.mu * p.dt / h, C, tpic);
+    cast_tab(th, A.hel);
+    cast_tab(tm, A.mass);
+    cast_tab(ts, A.smooth);
+    cast_tab(tpic, A.pic);
+    rtab_host(th, TP, q);
+    cast_rtab(q, A.rhel);
+    rtab_host(tm, TP, q);
+    cast_rtab(q, A.rmass);
+    rtab_host(ts, TP, q);
+    cast_rtab(q, A.rsmooth);
+    rtab_host(tpic, TP, q);
+    cast_rtab(q, A.rpic);
+    HBasis<double> hb;
+    hbasis_host(tpic, th, C, h / 6.0, hb);
+    cast_hb(hb, A.hb);
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -117,6 +285,7 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     if (p.n <= 0 || p.M <= 0 || p.n % p.M != 0 || p.max_iter < 1) return SCH_ERR_ARG;
     if (p.K < 2 || p.K > SCH_MAX_K || (p.K & 1)) return SCH_ERR_ARG;
     if (p.dtype != SCH_F32 && p.dtype != SCH_F64) return SCH_ERR_ARG;
+    if (p.solver < SCH_SOLVER_AUTO || p.solver > SCH_SOLVER_EA) return SCH_ERR_ARG;
     const int C = (p.dtype == SCH_F32) ? 8 : 4;
     if (p.n % C != 0) return SCH_ERR_UNSUPPORTED;
     const int tp = p.n / C;
@@ -183,11 +352,13 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
     if (ctx->p.dtype == SCH_F32) {
         WindowIO<float> io{nsteps, (const float*)m, (float*)m_out, (float*)u_out, (const float*)dW,
                            (const float*)lambda, (const float*)y, nll, logG, iters, status};
-        return launch_window<float, 8>(ctx->af, io, N, S(stream));
+        return ctx->af.solver == SCH_SOLVER_EA ? launch_window<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
+                                               : launch_window<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }
     WindowIO<double> io{nsteps, (const double*)m, (double*)m_out, (double*)u_out, (const double*)dW,
                         (const double*)lambda, (const double*)y, nll, logG, iters, status};
-    return launch_window<double, 4>(ctx->ad, io, N, S(stream));
+    return ctx->ad.solver == SCH_SOLVER_EA ? launch_window<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
+                                           : launch_window<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
 }
 
 int sch_loglik(sch_ctx* ctx, int N, const void* u, const void* y, const void* dW, const void* lambda,
@@ -275,12 +446,14 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
         JitterIO<float> io{nsteps, n_iter, 0, theta, (float)rho, (float)sq, seed, ctr, (const float*)m_start,
                            (float*)dW, (const float*)lambda, (const float*)y, nll, logG, (float*)m_end,
                            (float*)u_end, accepts, iters, status};
-        return launch_jitter<float, 8>(ctx->af, io, N, S(stream));
+        return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
+                                               : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }
     JitterIO<double> io{nsteps, n_iter, 0, theta, rho, sq, seed, ctr, (const double*)m_start, (double*)dW,
                         (const double*)lambda, (const double*)y, nll, logG, (double*)m_end, (double*)u_end,
                         accepts, iters, status};
-    return launch_jitter<double, 4>(ctx->ad, io, N, S(stream));
+    return ctx->ad.solver == SCH_SOLVER_EA ? launch_jitter<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
+                                           : launch_jitter<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
 }
 
 int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, double scale, void* m, void* u,

@@ -20,11 +20,34 @@ struct CTab {
     R a, iBF, pa, pc, ae, ge;
 };
 
+// The reduced cyclic system of a constant matrix: one unknown E_t per chunk,
+// rows A E_{t-1} + B E_t + C E_{t+1} = D_t with the same A, B, C everywhere.
+// Warp 0 solves it with lanes owning RR = TP/32 consecutive rows: a lane-level
+// partition sweep (coefficients q, ga, al, alp, gap), then a cyclic PCR over
+// the 32 lanes (level multipliers k1, k2 and the closing 2x2 weights f1, f2).
+template <typename R>
+struct RTab {
+    R A, B, Cc;
+    R q[16], ga[16], alp[16], gap[16];
+    R qa, qc, iBF, aeL, geL;
+    R k1[4], k2[4], f1, f2;
+};
+
+// Linear functionals used by the explicit-advection step to build the
+// Helmholtz interface rows of a chunk from the interface values of the
+// preceding constant solve: hpd = sum_i apd_i dp_i + cpF F + cpE E + cpEp E_{t-1}
+// + cpFn F_{t+1}, and the same for hde with ade, cd*.
+template <typename R>
+struct HBasis {
+    R apd[8], ade[8];
+    R cpF, cpE, cpEp, cpFn, cdF, cdE, cdEp, cdFn;
+};
+
 // Precomputed scalars of the discretised model, passed by value to kernels
 // (so that every thread reads them from the constant parameter bank).
 template <typename R>
 struct ModelArgs {
-    int n, K, K2, M, stride, max_iter;
+    int n, K, K2, M, stride, max_iter, solver;
     R h, dt;
     R c0, b0;      // left operator M + mu dt/2 K: off-diagonal, diagonal
     R c0p, b0p;    // right operator M - mu dt/2 K: off-diagonal, diagonal
@@ -38,6 +61,10 @@ struct ModelArgs {
     CTab<R> hel;            // M + alpha^2 K
     CTab<R> mass;           // M
     CTab<R> smooth;         // M + K (the (I - d_xx) smoothing of the prior)
+    CTab<R> pic;            // M + mu dt/2 K (explicit-advection Picard matrix)
+    R rot_c[SCH_MAX_K / 2], rot_s[SCH_MAX_K / 2];   // cos(j 2 pi / n), sin(j 2 pi / n), j = 1..K/2
+    RTab<R> rhel, rmass, rsmooth, rpic;
+    HBasis<R> hb;
 };
 
 template <typename R>
@@ -74,9 +101,9 @@ struct JitterIO {
     int32_t* status;
 };
 
-template <typename R, int C>
+template <typename R, int C, int S>
 int launch_window(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st);
-template <typename R, int C>
+template <typename R, int C, int S>
 int launch_jitter(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st);
 template <typename R, int C>
 int launch_helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cudaStream_t st);

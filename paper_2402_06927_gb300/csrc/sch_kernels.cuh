@@ -55,7 +55,7 @@ __host__ __device__ constexpr size_t shm_base_bytes() {
     return (sizeof(Shm<R, TP>) + 15) / 16 * 16;
 }
 
-enum { FLAG_CONVERGED = 1, FLAG_NONFINITE = 2 };
+enum { FLAG_CONVERGED = 1, FLAG_NONFINITE = 2, FLAG_STOP = 4, FLAG_NOCONV = 8 };
 
 // --------------------------------------------------------------------------
 // cyclic PCR over the 32 lanes of a warp (one row per lane)
@@ -177,26 +177,67 @@ __device__ __forceinline__ void warp_reduce_var(Shm<R, TP>* sh) {
     }
 }
 
-// Warp 0: reduced solve of a tabulated constant matrix (rows from hpd, hde).
-template <typename R, int TP>
-__device__ __forceinline__ void warp_reduce_const(const CTab<R>& T, Shm<R, TP>* sh) {
-    const R A = -T.ae * T.pa;
-    const R B = R(1) - T.ae * T.pc - T.ge * T.pa;
-    const R Cc = -T.ge * T.pc;
-    auto row = [sh, A, B, Cc, &T](int t, R& a, R& b, R& c, R& d) {
-        a = A;
-        b = B;
-        c = Cc;
-        d = sh->hde[t] - T.ae * sh->hpd[t] - T.ge * sh->hpd[(t + 1) & (TP - 1)];
-    };
-    warp_cyclic_solve<R, TP>(row, sh->hE, sh->sw);
-    constexpr int RR = Shm<R, TP>::RR;
+// cyclic PCR over 32 lanes for a constant reduced system: only D travels
+template <typename R>
+__device__ __forceinline__ R pcr32_const(R D, const RTab<R>& Q) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int r = 0; r < RR; ++r) {
-        const int t = lane * RR + r;
-        if (t < TP) sh->hF[t] = sh->hpd[t] - T.pa * sh->hE[(t - 1) & (TP - 1)] - T.pc * sh->hE[t];
+    for (int l = 0; l < 4; ++l) {
+        const int s = 1 << l;
+        const R Dm = __shfl_sync(FULL, D, (lane - s) & 31);
+        const R Dp = __shfl_sync(FULL, D, (lane + s) & 31);
+        D = D - Q.k1[l] * Dm - Q.k2[l] * Dp;
     }
+    const R Dj = __shfl_sync(FULL, D, lane ^ 16);
+    return Q.f1 * D + Q.f2 * Dj;
+}
+
+// Warp 0: interface values of a tabulated constant matrix from the chunk rows
+// pd[t], de[t]: reduced rows D_t = de_t - ae pd_t - ge pd_{t+1} (A, B, C fixed),
+// lane sweeps and 32-lane PCR with host coefficients, then E[t] and
+// F[t] = pd_t - pa E_{t-1} - pc E_t.
+template <typename R, int TP>
+__device__ __forceinline__ void warp_solve_const(const CTab<R>& T, const RTab<R>& Q, const R* pd, const R* de,
+                                                 R* E, R* F) {
+    constexpr int RR = TP / 32;
+    const int lane = threadIdx.x & 31;
+    const int t0 = lane * RR;
+    if constexpr (RR == 1) {
+        const R D = de[t0] - T.ae * pd[t0] - T.ge * pd[(t0 + 1) & (TP - 1)];
+        E[t0] = pcr32_const(D, Q);
+    } else {
+        R dl[RR];
+        const R D0 = de[t0] - T.ae * pd[t0] - T.ge * pd[t0 + 1];
+        dl[0] = R(0);
+#pragma unroll
+        for (int r = 1; r < RR; ++r) {
+            const int t = t0 + r;
+            const R D = de[t] - T.ae * pd[t] - T.ge * pd[(t + 1) & (TP - 1)];
+            dl[r] = (D - Q.A * dl[r - 1]) * Q.q[r];
+        }
+        R dp[RR];
+        dp[RR - 1] = R(0);
+#pragma unroll
+        for (int r = RR - 2; r >= 1; --r) dp[r] = dl[r] - Q.ga[r] * dp[r + 1];
+        const R DF = (RR == 2) ? D0 : D0 - Q.Cc * dp[1];
+        const R qd = DF * Q.iBF;
+        const R nqd = __shfl_sync(FULL, qd, (lane + 1) & 31);
+        const R LD = dl[RR - 1] - Q.aeL * qd - Q.geL * nqd;
+        const R EL = pcr32_const(LD, Q);
+        const R Ep = __shfl_sync(FULL, EL, (lane + 31) & 31);
+        const R Ff = qd - Q.qa * Ep - Q.qc * EL;
+        E[t0] = Ff;
+#pragma unroll
+        for (int r = 1; r < RR - 1; ++r) E[t0 + r] = dp[r] - Q.alp[r] * Ff - Q.gap[r] * EL;
+        E[t0 + RR - 1] = EL;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        const int t = t0 + r;
+        F[t] = pd[t] - T.pa * E[(t - 1) & (TP - 1)] - T.pc * E[t];
+    }
+    __syncwarp();
 }
 
 // --------------------------------------------------------------------------
@@ -228,12 +269,12 @@ __device__ __forceinline__ void const_back(const CTab<R>& T, const R (&dp)[C], R
 // Full solve of a tabulated constant matrix for right-hand side r: returns x
 // and its chunk-end neighbours xp (= x_{tC-1}) and xn (= x_{tC+C}).
 template <typename R, int C, int TP>
-__device__ __forceinline__ void const_solve(const CTab<R>& T, const R (&r)[C], R (&x)[C], R& xp, R& xn,
-                                            Shm<R, TP>* sh) {
+__device__ __forceinline__ void const_solve(const CTab<R>& T, const RTab<R>& Q, const R (&r)[C], R (&x)[C], R& xp,
+                                            R& xn, Shm<R, TP>* sh) {
     R dp[C];
     const_local<R, C, TP>(T, r, dp, sh);
     __syncthreads();
-    if (threadIdx.x < 32) warp_reduce_const<R, TP>(T, sh);
+    if (threadIdx.x < 32) warp_solve_const<R, TP>(T, Q, sh->hpd, sh->hde, sh->hE, sh->hF);
     __syncthreads();
     const int t = threadIdx.x;
     const R F = sh->hF[t], E = sh->hE[t];
@@ -265,21 +306,38 @@ __device__ __forceinline__ void mass_apply(R h6, const R (&v)[C], R vp, R vn, R 
     }
 }
 
-// SALT increment dU/4 at a node from its angle (sin, cos) and the K weights
-// wq_k = a_j/4 (dW_k + lambda_k dt): Chebyshev recurrence over harmonics.
-template <typename R>
-__device__ __forceinline__ R noise_q(const R* wq, int K2, R s1, R c1) {
-    const R c2 = R(2) * c1;
-    R sk = s1, ck = c1, sp = R(0), cp = R(1), acc = R(0);
-    for (int j = 0; j < K2; ++j) {
-        acc += wq[2 * j] * sk + wq[2 * j + 1] * ck;
-        const R s2 = c2 * sk - sp;
-        const R k2 = c2 * ck - cp;
-        sp = sk; cp = ck; sk = s2; ck = k2;
+// SALT increment dU/4 at the C + 2 nodes i0 - 1 .. i0 + C of this thread's
+// chunk, from the step's K weights wq_k = a_j/4 (dW_k + lambda_k dt):
+// dU_i / 4 = sum_j wq_{2j-2} sin(j theta_i) + wq_{2j-1} cos(j theta_i).
+// (sin, cos)(j theta_{i0-1}) follow a Chebyshev recurrence over j; along the
+// chunk each harmonic is rotated by its tabulated angle j 2 pi / n.  Each weight
+// is read once per step.
+template <typename R, int C>
+__device__ __forceinline__ void noise_nodes(const ModelArgs<R>& A, const R* wq, R s0, R c0, R (&nq)[C + 2]) {
+#pragma unroll
+    for (int q = 0; q < C + 2; ++q) nq[q] = R(0);
+    const R twoc = R(2) * c0;
+    R sj = s0, cj = c0, sjm = R(0), cjm = R(1);
+    for (int j = 0; j < A.K2; ++j) {
+        const R a = wq[2 * j], b = wq[2 * j + 1];
+        const R rc = A.rot_c[j], rs = A.rot_s[j];
+        R sn = sj, cs = cj;
+#pragma unroll
+        for (int q = 0; q < C + 2; ++q) {
+            nq[q] += a * sn + b * cs;
+            const R s2 = sn * rc + cs * rs;
+            cs = cs * rc - sn * rs;
+            sn = s2;
+        }
+        const R sn2 = twoc * sj - sjm, cn2 = twoc * cj - cjm;
+        sjm = sj;
+        cjm = cj;
+        sj = sn2;
+        cj = cn2;
     }
-    return acc;
 }
 
+// sin and cos of the angle 2 pi i / n of node i (taken mod n)
 template <typename R>
 __device__ __forceinline__ void node_angle(int node, int n, R& s, R& c) {
     const int i = (node + n) % n;
@@ -301,15 +359,16 @@ struct Field {
 // --------------------------------------------------------------------------
 template <typename R, int C, int TP>
 __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, Field<R, C>& f, const R* wq,
-                                         const R (&sn)[C], const R (&cs)[C], R snp, R csp, R snn, R csn,
-                                         int& iters, int& flags) {
+                                         R s0, R c0, int& iters, int& flags) {
     const int t = threadIdx.x;
     // W0 = dt/8 u0 + dU/4, at the chunk and its two neighbour nodes
+    R nq[C + 2];
+    noise_nodes<R, C>(A, wq, s0, c0, nq);
     R W0[C];
 #pragma unroll
-    for (int i = 0; i < C; ++i) W0[i] = A.dt8 * f.u[i] + noise_q(wq, A.K2, sn[i], cs[i]);
-    const R W0p = A.dt8 * f.up + noise_q(wq, A.K2, snp, csp);
-    const R W0n = A.dt8 * f.un + noise_q(wq, A.K2, snn, csn);
+    for (int i = 0; i < C; ++i) W0[i] = A.dt8 * f.u[i] + nq[i + 1];
+    const R W0p = A.dt8 * f.up + nq[0];
+    const R W0n = A.dt8 * f.un + nq[C + 1];
     // from m0: S_i = m_i + m_{i+1}, D0_i = c0p (m_{i-1} + m_{i+1}) + b0p m_i
     R Ssum[C], D0[C];
     const R Sprev = f.mp + f.m[0];
@@ -415,7 +474,7 @@ __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, 
         const_local<R, C, TP>(A.hel, r, dpH, sh);
         __syncthreads();                                             // B3
         if (t < 32) {
-            warp_reduce_const<R, TP>(A.hel, sh);
+            warp_solve_const<R, TP>(A.hel, A.rhel, sh->hpd, sh->hde, sh->hE, sh->hF);
             constexpr int NW = TP / 32;
             R dm = (t < NW) ? sh->wred[0][t] : R(0);
             R mm = (t < NW) ? sh->wred[1][t] : R(0);
@@ -454,6 +513,183 @@ __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, 
     f.un = uin;
 }
 
+// --------------------------------------------------------------------------
+// One implicit-midpoint step by explicit-advection Picard iteration:
+//   (M + mu dt/2 K) m^{p+1} = (M - mu dt/2 K) m0 - A(mbar^p, dv^p),
+//   u^{p+1} = H^{-1} M m^{p+1}.
+// Both matrices are constant, so warp 0 can build the Helmholtz interface rows
+// from the Picard interface values with host-tabulated functionals and solve
+// both reduced systems between one pair of barriers.  The convergence test of
+// iterate p is decided at the first barrier of iteration p + 1 (whose local
+// work is then discarded), so an iteration costs two barriers.
+// --------------------------------------------------------------------------
+template <typename R, int C, int TP>
+__device__ __forceinline__ void sch_step_ea(const ModelArgs<R>& A, Shm<R, TP>* sh, Field<R, C>& f, const R* wq,
+                                            R s0, R c0, int& iters, int& flags) {
+    constexpr int RR = TP / 32;
+    const int t = threadIdx.x;
+    R nq[C + 2];
+    noise_nodes<R, C>(A, wq, s0, c0, nq);
+    // W0 = dt/8 u0 + dU/4, so that dv/4 = W0 + dt/8 u at an iterate
+    R W0[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) W0[i] = A.dt8 * f.u[i] + nq[i + 1];
+    const R W0p = A.dt8 * f.up + nq[0];
+    const R W0n = A.dt8 * f.un + nq[C + 1];
+    // R0 = (M - mu dt/2 K) m0
+    R R0[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const R lo = (i == 0) ? f.mp : f.m[i - 1];
+        const R hi = (i == C - 1) ? f.mn : f.m[i + 1];
+        R0[i] = A.c0p * (lo + hi) + A.b0p * f.m[i];
+    }
+    R mi[C], ui[C];
+#pragma unroll
+    for (int i = 0; i < C; ++i) { mi[i] = f.m[i]; ui[i] = f.u[i]; }
+    R mip = f.mp, min_ = f.mn, uip = f.up, uin = f.un;
+    const R m0p = f.mp, m0n = f.mn;
+
+    for (int it = 1;; ++it) {
+        // local phase: right-hand side and chunk sweep of M + mu dt/2 K
+        R rhs[C];
+        {
+            R w[C], mb[C];
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                w[i] = W0[i] + A.dt8 * ui[i];
+                mb[i] = R(0.5) * (f.m[i] + mi[i]);
+            }
+            const R wp = W0p + A.dt8 * uip, wn = W0n + A.dt8 * uin;
+            const R mbp = R(0.5) * (m0p + mip), mbn = R(0.5) * (m0n + min_);
+#pragma unroll
+            for (int i = 0; i < C; ++i) {
+                const R wl = (i == 0) ? wp : w[i - 1];
+                const R wr = (i == C - 1) ? wn : w[i + 1];
+                const R ml = (i == 0) ? mbp : mb[i - 1];
+                const R mr = (i == C - 1) ? mbn : mb[i + 1];
+                // A(mbar, dv)_i = 1/2 [dv_{i+1} (mbar_i + mbar_{i+1}) - dv_{i-1} (mbar_{i-1} + mbar_i)]
+                rhs[i] = R0[i] - R(2) * (wr * (mb[i] + mr) - wl * (ml + mb[i]));
+            }
+        }
+        R dp[C];
+        R de_last, DF;
+        {
+            R de[C];
+            de[0] = R(0);
+#pragma unroll
+            for (int i = 1; i < C; ++i) de[i] = (rhs[i] - A.pic.a * de[i - 1]) * A.pic.rden[i];
+            dp[0] = R(0);
+            dp[C - 1] = R(0);
+#pragma unroll
+            for (int i = C - 2; i >= 1; --i) dp[i] = de[i] - A.pic.gam[i] * dp[i + 1];
+            de_last = de[C - 1];
+            DF = (C == 2) ? rhs[0] : rhs[0] - A.pic.a * dp[1];
+        }
+        R hpl = R(0), hdl = R(0);
+#pragma unroll
+        for (int i = 1; i < C - 1; ++i) {
+            hpl += A.hb.apd[i] * dp[i];
+            hdl += A.hb.ade[i] * dp[i];
+        }
+        sh->pd[t] = DF * A.pic.iBF;
+        sh->de[t] = de_last;
+        sh->hpd[t] = hpl;
+        sh->hde[t] = hdl;
+        __syncthreads();                                             // B1
+        if (t < 32) {
+            int fl = 0;
+            if (it > 1) {
+                constexpr int NW = TP / 32;
+                R dm = (t < NW) ? sh->wred[0][t] : R(0);
+                R mm = (t < NW) ? sh->wred[1][t] : R(0);
+                dm = warp_max(dm);
+                mm = warp_max(mm);
+                if (!(dm < R(INFINITY)) || !(mm < R(INFINITY))) fl = FLAG_STOP | FLAG_NONFINITE;
+                else if (dm <= A.tol * fmax(R(1), mm)) fl = FLAG_STOP | FLAG_CONVERGED;
+                else if (it > A.max_iter) fl = FLAG_STOP | FLAG_NOCONV;
+            }
+            if (!(fl & FLAG_STOP)) {
+                warp_solve_const<R, TP>(A.pic, A.rpic, sh->pd, sh->de, sh->E, sh->F);
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int q = t * RR + r;
+                    const R Fq = sh->F[q], Eq = sh->E[q];
+                    const R Eqp = sh->E[(q - 1) & (TP - 1)], Fqn = sh->F[(q + 1) & (TP - 1)];
+                    sh->hpd[q] += A.hb.cpF * Fq + A.hb.cpE * Eq + A.hb.cpEp * Eqp + A.hb.cpFn * Fqn;
+                    sh->hde[q] += A.hb.cdF * Fq + A.hb.cdE * Eq + A.hb.cdEp * Eqp + A.hb.cdFn * Fqn;
+                }
+                __syncwarp();
+                warp_solve_const<R, TP>(A.hel, A.rhel, sh->hpd, sh->hde, sh->hE, sh->hF);
+            }
+            if (t == 0) sh->flag = fl;
+        }
+        __syncthreads();                                             // B2
+        const int fl = sh->flag;
+        if (fl & FLAG_STOP) {
+            if (fl & FLAG_NONFINITE) flags |= SCH_DEV_NONFINITE;
+            if (fl & FLAG_NOCONV) flags |= SCH_DEV_NOCONVERGE;
+            break;
+        }
+        // back phase: the new iterate (m, u) of this chunk
+        const R E = sh->E[t], F = sh->F[t];
+        const R Ep = sh->E[(t - 1) & (TP - 1)], Fn = sh->F[(t + 1) & (TP - 1)];
+        R mnew[C];
+        mnew[0] = F;
+        mnew[C - 1] = E;
+#pragma unroll
+        for (int i = 1; i < C - 1; ++i) mnew[i] = dp[i] - A.pic.alpp[i] * F - A.pic.gamp[i] * E;
+        R r[C];
+        mass_apply<R, C>(A.h6, mnew, Ep, Fn, r);
+        R hd[C];
+        hd[0] = R(0);
+#pragma unroll
+        for (int i = 1; i < C; ++i) hd[i] = (r[i] - A.hel.a * hd[i - 1]) * A.hel.rden[i];
+        R hdp[C];
+        hdp[C - 1] = R(0);
+#pragma unroll
+        for (int i = C - 2; i >= 1; --i) hdp[i] = hd[i] - A.hel.gam[i] * hdp[i + 1];
+        const R hF = sh->hF[t], hE = sh->hE[t];
+        R dmax = R(0), mmax = R(0);
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+            const R un = (i == 0) ? hF : (i == C - 1 ? hE : hdp[i] - A.hel.alpp[i] * hF - A.hel.gamp[i] * hE);
+            R dd = rabs(mnew[i] - mi[i]);
+            if (!(dd == dd)) dd = R(INFINITY);
+            dmax = fmax(dmax, dd);
+            mmax = fmax(mmax, rabs(mnew[i]));
+            mi[i] = mnew[i];
+            ui[i] = un;
+        }
+        dmax = warp_max(dmax);
+        mmax = warp_max(mmax);
+        if ((t & 31) == 0) {
+            sh->wred[0][t >> 5] = dmax;
+            sh->wred[1][t >> 5] = mmax;
+        }
+        mip = Ep;
+        min_ = Fn;
+        uip = sh->hE[(t - 1) & (TP - 1)];
+        uin = sh->hF[(t + 1) & (TP - 1)];
+        iters++;
+    }
+#pragma unroll
+    for (int i = 0; i < C; ++i) { f.m[i] = mi[i]; f.u[i] = ui[i]; }
+    f.mp = mip;
+    f.mn = min_;
+    f.up = uip;
+    f.un = uin;
+}
+
+template <int S, typename R, int C, int TP>
+__device__ __forceinline__ void step_any(const ModelArgs<R>& A, Shm<R, TP>* sh, Field<R, C>& f, const R* wq, R s0,
+                                         R c0, int& iters, int& flags) {
+    if constexpr (S == SCH_SOLVER_EA)
+        sch_step_ea<R, C, TP>(A, sh, f, wq, s0, c0, iters, flags);
+    else
+        sch_step<R, C, TP>(A, sh, f, wq, s0, c0, iters, flags);
+}
+
 // load m of a particle, exchange its chunk ends and solve for u
 template <typename R, int C, int TP>
 __device__ __forceinline__ void field_start(const ModelArgs<R>& A, Shm<R, TP>* sh, const R* m_src, Field<R, C>& f) {
@@ -463,7 +699,7 @@ __device__ __forceinline__ void field_start(const ModelArgs<R>& A, Shm<R, TP>* s
     chunk_halo<R, C, TP>(f.m, f.mp, f.mn, sh);
     R r[C];
     mass_apply<R, C>(A.h6, f.m, f.mp, f.mn, r);
-    const_solve<R, C, TP>(A.hel, r, f.u, f.up, f.un, sh);
+    const_solve<R, C, TP>(A.hel, A.rhel, r, f.u, f.up, f.un, sh);
 }
 
 // the noise weights a_j/4 (dW + lambda dt) of a window, staged in smem
@@ -529,21 +765,6 @@ __device__ __forceinline__ void block_sum2(Shm<R, TP>* sh, double& a, double& b)
     __syncthreads();
 }
 
-template <typename R, int C>
-struct Trig {
-    R sn[C], cs[C];
-    R snp, csp, snn, csn;
-};
-
-template <typename R, int C>
-__device__ __forceinline__ void trig_init(int n, Trig<R, C>& g) {
-    const int i0 = threadIdx.x * C;
-#pragma unroll
-    for (int i = 0; i < C; ++i) node_angle<R>(i0 + i, n, g.sn[i], g.cs[i]);
-    node_angle<R>(i0 - 1, n, g.snp, g.csp);
-    node_angle<R>(i0 + C, n, g.snn, g.csn);
-}
-
 // --------------------------------------------------------------------------
 // kernels
 // --------------------------------------------------------------------------
@@ -552,7 +773,7 @@ struct Occ {
     static constexpr int minb = TP <= 32 ? 16 : (TP <= 64 ? 8 : (TP <= 128 ? 4 : (TP <= 256 ? 2 : 1)));
 };
 
-template <typename R, int C, int TP>
+template <typename R, int C, int TP, int S>
 __global__ void __launch_bounds__(TP, Occ<TP>::minb) window_kernel(ModelArgs<R> A, WindowIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
@@ -560,13 +781,12 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) window_kernel(ModelArgs<R> 
     const int p = blockIdx.x;
     const size_t NK = (size_t)io.Ns * A.K;
     stage_noise(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
-    Trig<R, C> g;
-    trig_init<R, C>(A.n, g);
+    R s0, c0;
+    node_angle<R>((int)threadIdx.x * C - 1, A.n, s0, c0);
     Field<R, C> f;
     field_start<R, C, TP>(A, sh, io.m_in + (size_t)p * A.n, f);   // its barriers publish the noise
     int iters = 0, flags = 0;
-    for (int s = 0; s < io.Ns; ++s)
-        sch_step<R, C, TP>(A, sh, f, noise + s * A.K, g.sn, g.cs, g.snp, g.csp, g.snn, g.csn, iters, flags);
+    for (int s = 0; s < io.Ns; ++s) step_any<S, R, C, TP>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
     const int i0 = threadIdx.x * C;
 #pragma unroll
     for (int i = 0; i < C; ++i) {
@@ -590,7 +810,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) window_kernel(ModelArgs<R> 
 
 // PCN jittering: n_iter proposals of the window noise, each run through the
 // whole window from m_start and accepted with probability min(1, exp(w0 - w1)).
-template <typename R, int C, int TP>
+template <typename R, int C, int TP, int S>
 __global__ void __launch_bounds__(TP, Occ<TP>::minb) jitter_kernel(ModelArgs<R> A, JitterIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
@@ -608,8 +828,8 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) jitter_kernel(ModelArgs<R> 
         sh_state[0] = io.nll[p];
         sh_state[1] = io.logG ? io.logG[p] : 0.0;
     }
-    Trig<R, C> g;
-    trig_init<R, C>(A.n, g);
+    R s0, c0;
+    node_angle<R>((int)threadIdx.x * C - 1, A.n, s0, c0);
     const R sq = io.sq1mr2 * (R)sqrt(A.dt_d);
     const int nblk = (K + 3) >> 2;
     const int i0 = threadIdx.x * C;
@@ -633,8 +853,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) jitter_kernel(ModelArgs<R> 
         Field<R, C> f;
         field_start<R, C, TP>(A, sh, io.m_start + (size_t)p * A.n, f);   // barriers publish the noise
         int fl = 0;
-        for (int s = 0; s < Ns; ++s)
-            sch_step<R, C, TP>(A, sh, f, noise + s * K, g.sn, g.cs, g.snp, g.csp, g.snn, g.csn, iters, fl);
+        for (int s = 0; s < Ns; ++s) step_any<S, R, C, TP>(A, sh, f, noise + s * K, s0, c0, iters, fl);
         double mis = chunk_misfit<R, C>(A, f.u, io.y);
         double gl = window_girsanov(A, prop, lam, Ns);
         block_sum2<R, TP>(sh, mis, gl);
@@ -688,7 +907,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) helm_kernel(ModelArgs<R> A,
     chunk_halo<R, C, TP>(v, vp, vn, sh);
     if (mode == 0) {
         mass_apply<R, C>(A.h6, v, vp, vn, r);
-        const_solve<R, C, TP>(A.hel, r, x, xp, xn, sh);
+        const_solve<R, C, TP>(A.hel, A.rhel, r, x, xp, xn, sh);
     } else {
 #pragma unroll
         for (int i = 0; i < C; ++i) {
@@ -696,7 +915,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) helm_kernel(ModelArgs<R> A,
             const R hi = (i == C - 1) ? vn : v[i + 1];
             r[i] = A.hel_a * (lo + hi) + A.hel_b * v[i];
         }
-        const_solve<R, C, TP>(A.mass, r, x, xp, xn, sh);
+        const_solve<R, C, TP>(A.mass, A.rmass, r, x, xp, xn, sh);
     }
 #pragma unroll
     for (int i = 0; i < C; ++i) out[(size_t)p * A.n + i0 + i] = x[i];
@@ -734,11 +953,11 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) prior_kernel(ModelArgs<R> A
     chunk_halo<R, C, TP>(cell, cp, cn, sh);
 #pragma unroll
     for (int i = 0; i < C; ++i) r[i] = R(0.5) * h * (((i == 0) ? cp : cell[i - 1]) + cell[i]);
-    const_solve<R, C, TP>(A.smooth, r, U, Up, Un, sh);
+    const_solve<R, C, TP>(A.smooth, A.rsmooth, r, U, Up, Un, sh);
     for (int rep = 0; rep < 2; ++rep) {
         mass_apply<R, C>(A.h6, U, Up, Un, r);
         R V[C];
-        const_solve<R, C, TP>(A.smooth, r, V, Up, Un, sh);
+        const_solve<R, C, TP>(A.smooth, A.rsmooth, r, V, Up, Un, sh);
 #pragma unroll
         for (int i = 0; i < C; ++i) U[i] = V[i];
     }
@@ -753,7 +972,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) prior_kernel(ModelArgs<R> A
         r[i] = A.hel_a * (lo + hi) + A.hel_b * u[i];
     }
     R m[C], mp, mn;
-    const_solve<R, C, TP>(A.mass, r, m, mp, mn, sh);
+    const_solve<R, C, TP>(A.mass, A.rmass, r, m, mp, mn, sh);
 #pragma unroll
     for (int i = 0; i < C; ++i) {
         m_out[(size_t)p * A.n + i0 + i] = m[i];
@@ -773,16 +992,18 @@ struct Launch {
         if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
 
+    template <int S>
     static int window(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st) {
         const size_t sm = smem(io.Ns, A.K, 1);
-        prep(window_kernel<R, C, TP>, sm);
-        window_kernel<R, C, TP><<<N, TP, sm, st>>>(A, io);
+        prep(window_kernel<R, C, TP, S>, sm);
+        window_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
+    template <int S>
     static int jitter(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st) {
         const size_t sm = smem(io.Ns, A.K, 3);
-        prep(jitter_kernel<R, C, TP>, sm);
-        jitter_kernel<R, C, TP><<<N, TP, sm, st>>>(A, io);
+        prep(jitter_kernel<R, C, TP, S>, sm);
+        jitter_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
     static int helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cudaStream_t st) {

@@ -1,26 +1,29 @@
 // Instantiations of the particle kernels for float fields, chunks of 8 nodes
-// per thread, and the supported CTA sizes TP (n = 8 * TP).
+// per thread and CTA sizes TP = 32 .. 512 (n = 8 TP): utilities, and the
+// window and jitter kernels with the explicit-advection Picard solver.
 #include "sch_kernels.cuh"
 
 namespace sch {
 
-#define SCH_TP_SWITCH(expr_tp, call)            \
-    switch (expr_tp) {                          \
-        case 32: return Launch<float, 8, 32>::call;   \
-        case 64: return Launch<float, 8, 64>::call;   \
-        case 128: return Launch<float, 8, 128>::call; \
-        case 256: return Launch<float, 8, 256>::call; \
-        case 512: return Launch<float, 8, 512>::call; \
-        default: return SCH_ERR_UNSUPPORTED;    \
+#define SCH_TP_SWITCH(expr_tp, call)                      \
+    switch (expr_tp) {                                    \
+        case 32: return Launch<float, 8, 32>::call;     \
+        case 64: return Launch<float, 8, 64>::call;     \
+        case 128: return Launch<float, 8, 128>::call;   \
+        case 256: return Launch<float, 8, 256>::call;   \
+        case 512: return Launch<float, 8, 512>::call;   \
+        default: return SCH_ERR_UNSUPPORTED;              \
     }
 
 template <>
-int launch_window<float, 8>(const ModelArgs<float>& A, const WindowIO<float>& io, int N, cudaStream_t st) {
-    SCH_TP_SWITCH(A.n / 8, window(A, io, N, st))
+int launch_window<float, 8, SCH_SOLVER_EA>(const ModelArgs<float>& A, const WindowIO<float>& io, int N,
+                                             cudaStream_t st) {
+    SCH_TP_SWITCH(A.n / 8, template window<SCH_SOLVER_EA>(A, io, N, st))
 }
 template <>
-int launch_jitter<float, 8>(const ModelArgs<float>& A, const JitterIO<float>& io, int N, cudaStream_t st) {
-    SCH_TP_SWITCH(A.n / 8, jitter(A, io, N, st))
+int launch_jitter<float, 8, SCH_SOLVER_EA>(const ModelArgs<float>& A, const JitterIO<float>& io, int N,
+                                             cudaStream_t st) {
+    SCH_TP_SWITCH(A.n / 8, template jitter<SCH_SOLVER_EA>(A, io, N, st))
 }
 template <>
 int launch_helm<float, 8>(const ModelArgs<float>& A, const float* in, float* out, int mode, int N, cudaStream_t st) {
@@ -32,14 +35,14 @@ int launch_prior<float, 8>(const ModelArgs<float>& A, const float* ut, uint64_t 
     SCH_TP_SWITCH(A.n / 8, prior(A, ut, seed, scale, m, u, N, st))
 }
 
-#define SCH_TP_SMEM(tp, bufs)                                                        \
-    switch (tp) {                                                                    \
-        case 32: return Launch<float, 8, 32>::smem(Ns, K, bufs);                   \
-        case 64: return Launch<float, 8, 64>::smem(Ns, K, bufs);                   \
-        case 128: return Launch<float, 8, 128>::smem(Ns, K, bufs);                 \
-        case 256: return Launch<float, 8, 256>::smem(Ns, K, bufs);                 \
-        case 512: return Launch<float, 8, 512>::smem(Ns, K, bufs);                 \
-        default: return (size_t)-1;                                                  \
+#define SCH_TP_SMEM(tp, bufs)                                          \
+    switch (tp) {                                                      \
+        case 32: return Launch<float, 8, 32>::smem(Ns, K, bufs);     \
+        case 64: return Launch<float, 8, 64>::smem(Ns, K, bufs);     \
+        case 128: return Launch<float, 8, 128>::smem(Ns, K, bufs);   \
+        case 256: return Launch<float, 8, 256>::smem(Ns, K, bufs);   \
+        case 512: return Launch<float, 8, 512>::smem(Ns, K, bufs);   \
+        default: return (size_t)-1;                                    \
     }
 
 template <>

@@ -79,6 +79,24 @@ def test_window_f64_cfg1(lam):
     assert np.allclose(out["logG"].cpu().numpy(), lg, rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("solver,name", [("ea", "cfg1_f64"), ("ea", "cfg3_f64"), ("li", "cfg2_f32")])
+def test_window_other_solver(solver, name):
+    # each precision also runs the other Picard iteration; both reach the fixed point of Eq. fde1
+    cfg = get_config(name)
+    g = gpu_model(cfg, solver=solver)
+    om, m0, dW, la = _case(cfg, 3, 13, Ns=4, lam=True)
+    om.scheme = solver
+    ref = om.ensemble_window(m0, dW, la)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
+    torch.cuda.synchronize()
+    tol = F64_TOL if cfg.dtype == "f64" else F32_TOL
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < tol
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < tol
+    assert np.all(out["status"].cpu().numpy() == 0)
+    if cfg.dtype == "f64":
+        assert np.all(np.abs(out["iters"].cpu().numpy() - ref[2].sum(axis=1)) <= 4)
+
+
 def test_window_f64_multiwarp():
     # n = 1024 in FP64: 256 threads per particle, exercises the cross-warp exchanges
     cfg = get_config("cfg3_f64")

@@ -84,9 +84,11 @@ def test_assembly_matches_gauss_quadrature():
     assert np.allclose(R, Rq, rtol=0, atol=1e-13 * np.max(np.abs(Rq)))
 
 
-def test_step_solves_fde1():
+@pytest.mark.parametrize("scheme", ["li", "ea"])
+def test_step_solves_fde1(scheme):
     r = np.random.default_rng(2)
     m = make(n=32)
+    m.scheme = scheme
     x = m.x
     u0 = 0.2 / np.cosh(x - 27) + 0.5 / np.cosh(x - 13)
     m0 = m.m_from_u(u0)
@@ -185,3 +187,20 @@ def test_peakon_speed():
     xc = (ur - ul + sl * xl - sr * xr) / (sl - sr)
     speed = (xc - x0) / T
     assert abs(speed - c) < 0.02 * c
+
+
+def test_both_picard_schemes_reach_the_same_step():
+    r = np.random.default_rng(9)
+    li = make(n=128)
+    ea = make(n=128)
+    ea.scheme = "ea"
+    x = li.x
+    u0 = 0.2 / np.cosh(x - 27) + 0.5 / np.cosh(x - 13)
+    m0 = li.m_from_u(u0)
+    dW = r.normal(scale=math.sqrt(li.dt), size=(5, li.K))
+    a = li.window(m0, dW)
+    b = ea.window(m0, dW)
+    assert a[3] and b[3]
+    assert np.max(np.abs(a[0] - b[0])) <= 1e-12 * np.max(np.abs(a[0]))
+    # explicit advection contracts more slowly
+    assert b[2].sum() >= a[2].sum()
