@@ -196,6 +196,55 @@ int sch_synth_obs(sch_ctx* ctx, const void* u, uint64_t seed, uint64_t ctr, void
 int pf_diagnostics(sch_ctx* ctx, int N, const void* u, const void* u_truth, double* ws, double* out,
                    void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Nudging (Sec. 3.1.3): drifts lambda that lower the window cost
+ *   J(lambda) = NLL(u_end) + 1/2 sum_{s,k} lambda_{s,k}^2 dt,
+ * with gradients from a hand-written reverse-mode adjoint of the converged
+ * implicit-midpoint steps (the paper computes them with an automated adjoint).
+ * The adjoint and the optimiser run in the context's default Picard solver
+ * (SCH_SOLVER_LI for SCH_F64, SCH_SOLVER_EA for SCH_F32); a context created
+ * with the other solver gets SCH_ERR_UNSUPPORTED.
+ * ------------------------------------------------------------------------- */
+
+/* Workspace for sch_adjoint_window: per particle, the states at every ckpt-th
+ * step plus 2 (ckpt + 1) recomputed states of n reals. */
+size_t sch_adjoint_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt);
+
+/* J, dJ/dlambda, dJ/d dW and dJ/dm_start of the window cost for every particle:
+ * a forward pass storing the state every ckpt steps, then per segment a
+ * forward recomputation and the adjoint steps in reverse order.  The adjoint
+ * of a step solves J1^T psi = g by the transposed Picard fixed point to
+ * params.tol (Eq. fde1 differentiated at its solution).
+ *   m_start real [N][n]; dW, lambda real [N][nsteps][K] (lambda may be NULL);
+ *   y real [M]; J double [N] out; g_lambda real [N][nsteps][K] out;
+ *   g_dW real [N][nsteps][K] out (optional); g_m0 real [N][n] out (optional);
+ *   iters int32 [N] optional (Picard + adjoint iterations); status optional.
+ *   ws: device workspace of ws_bytes >= sch_adjoint_workspace_bytes. */
+int sch_adjoint_window(sch_ctx* ctx, int N, int nsteps, int ckpt, const void* m_start, const void* dW,
+                       const void* lambda, const void* y, double* J, void* g_lambda, void* g_dW, void* g_m0,
+                       int32_t* iters, int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+enum { PF_NUDGE_SEQUENTIAL = 0, PF_NUDGE_OPEN_LOOP = 1 };
+
+/* Workspace for pf_nudge: the adjoint's plus one start state per particle. */
+size_t pf_nudge_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt);
+
+/* Per-particle nudging by L-BFGS (two-loop recursion, memory 6, Armijo
+ * backtracking) on J with the adjoint gradient, stopping when
+ * max |dJ/dlambda| <= gtol or after max_iter iterations (per stage).
+ *   mode PF_NUDGE_SEQUENTIAL: the adapted schedule of Sec. 3.1.3 -- for
+ *     n = 0..nsteps-1 optimise lambda^n with later increments and drifts zero,
+ *     then reveal dW^n = sqrt(dt) z, z keyed (seed, SCH_TAG_NUDGE,
+ *     (k / 4, n, particle, ctr)), and advance the start state one step;
+ *   mode PF_NUDGE_OPEN_LOOP: optimise all drifts at once with every increment
+ *     zero (lambda in: the starting guess), then reveal every increment with
+ *     the same keys.
+ * Out: lambda, dW real [N][nsteps][K]; J double [N] (cost at the last
+ * optimisation); iters int32 [N] (L-BFGS iterations, optional); status. */
+int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gtol, int ckpt, uint64_t seed,
+             uint64_t ctr, const void* m_start, const void* y, void* lambda, void* dW, double* J, int32_t* iters,
+             int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
 /* Prior ensemble about a truth velocity (a reading of Eq. init_solve): for
  * particle p, W_p is a DG0 field with cell values sqrt(h) z (z keyed
  * (seed, SCH_TAG_INIT, (b, 0, p, 0))), S = (M + K)^{-1} M-type P1 smoothing

@@ -60,8 +60,12 @@ SIGNATURES = {
     "pf_gather_rows": [I, P, P, P, SZ, P],
     "pf_jitter": [P, I, I, I, D, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
     "sch_prior_sample": [P, I, P, U64, D, P, P, P],
+    "sch_adjoint_window": [P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, SZ, P],
+    "pf_nudge": [P, I, I, I, I, D, I, U64, U64, P, P, P, P, P, P, P, P, SZ, P],
 }
-RESTYPES = {"pf_resample_workspace_bytes": (SZ, [I, SZ])}
+RESTYPES = {"pf_resample_workspace_bytes": (SZ, [I, SZ]),
+            "sch_adjoint_workspace_bytes": (SZ, [P, I, I, I]),
+            "pf_nudge_workspace_bytes": (SZ, [P, I, I, I])}
 
 _LIB = None
 

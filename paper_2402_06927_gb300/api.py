@@ -185,6 +185,54 @@ class SchModel:
               "pf_diagnostics")
         return out
 
+    def adjoint_window(self, m_start: torch.Tensor, dW: torch.Tensor, lam: Optional[torch.Tensor],
+                       y: torch.Tensor, ckpt: int = 5, want_dW: bool = True, want_m0: bool = True,
+                       ws: Optional[torch.Tensor] = None):
+        """sch_adjoint_window: J and its gradients for every particle."""
+        N, nsteps, K = dW.shape
+        _need(m_start, self.dtype, (N, self.n), "m_start")
+        _need(dW, self.dtype, (N, nsteps, self.K), "dW")
+        _need(y, self.dtype, (self.M,), "y")
+        if lam is not None:
+            _need(lam, self.dtype, (N, nsteps, self.K), "lambda")
+        dev = dW.device
+        J = torch.empty(N, dtype=torch.float64, device=dev)
+        g_lam = torch.empty_like(dW)
+        g_dW = torch.empty_like(dW) if want_dW else None
+        g_m0 = torch.empty_like(m_start) if want_m0 else None
+        iters = torch.empty(N, dtype=torch.int32, device=dev)
+        status = torch.empty(N, dtype=torch.int32, device=dev)
+        need = int(lib().sch_adjoint_workspace_bytes(self._h, N, nsteps, ckpt))
+        if ws is None:
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        check(lib().sch_adjoint_window(self._h, N, nsteps, ckpt, _ptr(m_start), _ptr(dW), _ptr(lam), _ptr(y),
+                                       _ptr(J), _ptr(g_lam), _ptr(g_dW), _ptr(g_m0), _ptr(iters), _ptr(status),
+                                       _ptr(ws), ws.numel() * ws.element_size(), _stream()), "sch_adjoint_window")
+        return dict(J=J, g_lam=g_lam, g_dW=g_dW, g_m0=g_m0, iters=iters, status=status)
+
+    def nudge(self, m_start: torch.Tensor, y: torch.Tensor, nsteps: int, mode: str = "sequential",
+              max_iter: int = 50, gtol: float = 1e-8, ckpt: int = 5, seed: int = 0, ctr: int = 0,
+              lam0: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None):
+        """pf_nudge: L-BFGS nudging drifts and the revealed increments for every particle."""
+        N = m_start.shape[0]
+        _need(m_start, self.dtype, (N, self.n), "m_start")
+        _need(y, self.dtype, (self.M,), "y")
+        dev = m_start.device
+        lam = torch.zeros((N, nsteps, self.K), dtype=self.dtype, device=dev) if lam0 is None else lam0.clone()
+        _need(lam, self.dtype, (N, nsteps, self.K), "lambda")
+        dW = torch.empty_like(lam)
+        J = torch.empty(N, dtype=torch.float64, device=dev)
+        iters = torch.empty(N, dtype=torch.int32, device=dev)
+        status = torch.empty(N, dtype=torch.int32, device=dev)
+        need = int(lib().pf_nudge_workspace_bytes(self._h, N, nsteps, ckpt))
+        if ws is None:
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        m = {"sequential": 0, "open_loop": 1}[mode]
+        check(lib().pf_nudge(self._h, N, nsteps, m, max_iter, gtol, ckpt, seed, ctr, _ptr(m_start), _ptr(y),
+                             _ptr(lam), _ptr(dW), _ptr(J), _ptr(iters), _ptr(status), _ptr(ws),
+                             ws.numel() * ws.element_size(), _stream()), "pf_nudge")
+        return dict(lam=lam, dW=dW, J=J, iters=iters, status=status)
+
     def prior_sample(self, N: int, u_truth: torch.Tensor, seed: int, scale: float):
         _need(u_truth, self.dtype, (self.n,), "u_truth")
         m = torch.empty((N, self.n), dtype=self.dtype, device="cuda")
@@ -241,3 +289,25 @@ def pf_gather_rows(idx: torch.Tensor, src: torch.Tensor, dst: torch.Tensor):
 
 def pf_resample_workspace_bytes(N: int, row_bytes_total: int) -> int:
     return int(lib().pf_resample_workspace_bytes(N, row_bytes_total))
+
+
+class NudgingCost(torch.autograd.Function):
+    """J(m_start, dW, lambda) = NLL(u_end) + 1/2 dt sum lambda^2 per particle, with the
+    hand-written adjoint (sch_adjoint_window) as its backward.
+
+    forward(model, m_start, dW, lam, y, ckpt) -> J [N] (double).  The backward
+    returns the adjoint's gradients, scaled per particle by the incoming
+    gradient of J (autograd's chain rule).
+    """
+
+    @staticmethod
+    def forward(ctx, model: SchModel, m_start, dW, lam, y, ckpt: int = 5):
+        out = model.adjoint_window(m_start.contiguous(), dW.contiguous(), lam.contiguous(), y.contiguous(), ckpt)
+        ctx.save_for_backward(out["g_m0"], out["g_dW"], out["g_lam"])
+        return out["J"]
+
+    @staticmethod
+    def backward(ctx, gJ):
+        g_m0, g_dW, g_lam = ctx.saved_tensors
+        s = gJ.to(g_lam.dtype)
+        return (None, g_m0 * s[:, None], g_dW * s[:, None, None], g_lam * s[:, None, None], None, None)

@@ -468,4 +468,70 @@ int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, do
                                    S(stream));
 }
 
+static size_t adjoint_ws_per(const sch_ctx* ctx, int nsteps, int ckpt) {
+    const size_t ncp = (size_t)((nsteps + ckpt - 1) / ckpt);
+    const size_t b = (ctx->p.dtype == SCH_F32) ? sizeof(float) : sizeof(double);
+    return (ncp + 2 * (size_t)(ckpt + 1)) * (size_t)ctx->p.n * b;
+}
+
+size_t sch_adjoint_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt) {
+    if (!ctx || N <= 0 || nsteps <= 0 || ckpt <= 0) return 0;
+    return (size_t)N * adjoint_ws_per(ctx, nsteps, ckpt);
+}
+
+size_t pf_nudge_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt) {
+    if (!ctx || N <= 0 || nsteps <= 0 || ckpt <= 0) return 0;
+    const size_t b = (ctx->p.dtype == SCH_F32) ? sizeof(float) : sizeof(double);
+    return (size_t)N * (adjoint_ws_per(ctx, nsteps, ckpt) + (size_t)ctx->p.n * b);
+}
+
+int sch_adjoint_window(sch_ctx* ctx, int N, int nsteps, int ckpt, const void* m_start, const void* dW,
+                       const void* lambda, const void* y, double* J, void* g_lambda, void* g_dW, void* g_m0,
+                       int32_t* iters, int32_t* status, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx || N < 0 || nsteps <= 0 || ckpt <= 0 || nsteps > 4096) return SCH_ERR_ARG;
+    if (N == 0) return SCH_OK;
+    if (!m_start || !dW || !y || !J || !g_lambda) return SCH_ERR_ARG;
+    if (!ws || ws_bytes < sch_adjoint_workspace_bytes(ctx, N, nsteps, ckpt)) return SCH_ERR_WORKSPACE;
+    const size_t per = adjoint_ws_per(ctx, nsteps, ckpt);
+    if (ctx->p.dtype == SCH_F32) {
+        if (adjoint_smem<float, 8>(ctx->tp, nsteps, ctx->p.K) > 200 * 1024) return SCH_ERR_UNSUPPORTED;
+        AdjointIO<float> io{nsteps, ckpt, (const float*)m_start, (const float*)dW, (const float*)lambda,
+                            (const float*)y, J, (float*)g_lambda, (float*)g_dW, (float*)g_m0, (float*)ws,
+                            per / sizeof(float), iters, status};
+        return ctx->af.solver == SCH_SOLVER_EA ? launch_adjoint<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
+                                               : launch_adjoint<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
+    }
+    if (adjoint_smem<double, 4>(ctx->tp, nsteps, ctx->p.K) > 200 * 1024) return SCH_ERR_UNSUPPORTED;
+    AdjointIO<double> io{nsteps, ckpt, (const double*)m_start, (const double*)dW, (const double*)lambda,
+                         (const double*)y, J, (double*)g_lambda, (double*)g_dW, (double*)g_m0, (double*)ws,
+                         per / sizeof(double), iters, status};
+    return ctx->ad.solver == SCH_SOLVER_EA ? launch_adjoint<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
+                                           : launch_adjoint<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
+}
+
+int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gtol, int ckpt, uint64_t seed,
+             uint64_t ctr, const void* m_start, const void* y, void* lambda, void* dW, double* J, int32_t* iters,
+             int32_t* status, void* ws, size_t ws_bytes, void* stream) {
+    if (!ctx || N < 0 || nsteps <= 0 || ckpt <= 0 || max_iter < 0 || nsteps > 4096) return SCH_ERR_ARG;
+    if (mode != PF_NUDGE_SEQUENTIAL && mode != PF_NUDGE_OPEN_LOOP) return SCH_ERR_ARG;
+    if (!(gtol >= 0.0)) return SCH_ERR_ARG;
+    if (N == 0) return SCH_OK;
+    if (!m_start || !y || !lambda || !dW || !J) return SCH_ERR_ARG;
+    if (!ws || ws_bytes < pf_nudge_workspace_bytes(ctx, N, nsteps, ckpt)) return SCH_ERR_WORKSPACE;
+    const size_t b = (ctx->p.dtype == SCH_F32) ? sizeof(float) : sizeof(double);
+    const size_t per = (adjoint_ws_per(ctx, nsteps, ckpt) + (size_t)ctx->p.n * b) / b;
+    if (ctx->p.dtype == SCH_F32) {
+        if (nudge_smem<float, 8>(ctx->tp, nsteps, ctx->p.K) > 200 * 1024) return SCH_ERR_UNSUPPORTED;
+        NudgeIO<float> io{nsteps, ckpt, mode, max_iter, 0, gtol, seed, ctr, (const float*)m_start,
+                          (const float*)y, (float*)lambda, (float*)dW, J, (float*)ws, per, iters, status};
+        return ctx->af.solver == SCH_SOLVER_EA ? launch_nudge<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
+                                               : launch_nudge<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
+    }
+    if (nudge_smem<double, 4>(ctx->tp, nsteps, ctx->p.K) > 200 * 1024) return SCH_ERR_UNSUPPORTED;
+    NudgeIO<double> io{nsteps, ckpt, mode, max_iter, 0, gtol, seed, ctr, (const double*)m_start,
+                       (const double*)y, (double*)lambda, (double*)dW, J, (double*)ws, per, iters, status};
+    return ctx->ad.solver == SCH_SOLVER_EA ? launch_nudge<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
+                                           : launch_nudge<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
+}
+
 }  // extern "C"

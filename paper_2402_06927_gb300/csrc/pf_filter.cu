@@ -2,42 +2,46 @@
 // resampling on exact integers, and the row gather that copies resampled
 // particles (Sec. 3.1.1 and 3.1.2 of the paper).  Weights and cumulative sums
 // are FP64 / uint64 regardless of the field precision.
+#include <cooperative_groups.h>
+
 #include "sch_internal.h"
 
 namespace sch {
 
-constexpr int TEMPER_THREADS = 1024;
-constexpr int TEMPER_PER_THREAD = 16;   // N <= 16384
+constexpr int TEMPER_CTAS = 8;          // one thread-block cluster
+constexpr int TEMPER_THREADS = 256;
+constexpr int TEMPER_PER_THREAD = 8;    // N <= 8 * 256 * 8 = 16384
 constexpr int RESAMPLE_THREADS = 1024;
 
-__device__ __forceinline__ double block_reduce_sum1024(double v, double* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
-    s = warp_sum(s);
-    return s;
-}
+// Adaptive tempering on one cluster of TEMPER_CTAS CTAs: every CTA holds a
+// slice of the particles, ESS evaluations reduce (sum w, sum w^2) in the CTA,
+// then across the cluster through distributed shared memory.  Every CTA sums
+// the partials in the same order, so all CTAs take identical bisection
+// decisions.  Partials are double-buffered by evaluation parity, so one
+// cluster barrier per evaluation suffices.
+struct TemperShm {
+    double part[2][2];      // [parity][s1, s2] of this CTA
+    double warp[2][8];      // per-warp partials (s1, s2)
+    double minw[8];
+};
 
-__device__ __forceinline__ double block_reduce_min1024(double v, double* sh) {
+__device__ __forceinline__ double cta_min(double v, TemperShm* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
+    if (lane == 0) sh->minw[warp] = v;
     __syncthreads();
-    if (lane == 0) sh[warp] = v;
+    double m = sh->minw[0];
+    for (int w = 1; w < TEMPER_THREADS / 32; ++w) m = fmin(m, sh->minw[w]);
     __syncthreads();
-    double s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : INFINITY;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = fmin(s, __shfl_xor_sync(FULL, s, o));
-    return s;
+    return m;
 }
 
-// ESS of the weights exp(-d phi_i) (shifted by their maximum -d phi_min):
-// ESS = (sum w)^2 / sum w^2  (Eq. ess).
-__device__ __forceinline__ double ess_at(double d, const double (&phi)[TEMPER_PER_THREAD], int cnt,
-                                         double phimin, double* sh1, double* sh2, double& s1out) {
+// ESS (Eq. ess) of the weights exp(-d phi_i - max), max = -d phi_min
+__device__ __forceinline__ double ess_eval(double d, const double (&phi)[TEMPER_PER_THREAD], int cnt, double phimin,
+                                           TemperShm* sh, int& parity, double& s1_out) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
     const double mx = -d * phimin;
     double s1 = 0.0, s2 = 0.0;
 #pragma unroll
@@ -48,26 +52,52 @@ __device__ __forceinline__ double ess_at(double d, const double (&phi)[TEMPER_PE
             s2 += w * w;
         }
     }
-    s1 = block_reduce_sum1024(s1, sh1);
-    s2 = block_reduce_sum1024(s2, sh2);
-    s1out = s1;
-    return s1 * s1 / s2;
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh->warp[0][warp] = s1;
+        sh->warp[1][warp] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < TEMPER_THREADS / 32; ++w) {
+            a += sh->warp[0][w];
+            b += sh->warp[1][w];
+        }
+        sh->part[parity][0] = a;
+        sh->part[parity][1] = b;
+    }
+    cl.sync();
+    double t1 = 0.0, t2 = 0.0;
+    for (int r = 0; r < TEMPER_CTAS; ++r) {
+        const TemperShm* o = cl.map_shared_rank(sh, r);
+        t1 += o->part[parity][0];
+        t2 += o->part[parity][1];
+    }
+    parity ^= 1;
+    s1_out = t1;
+    return t1 * t1 / t2;
 }
 
-__global__ void __launch_bounds__(TEMPER_THREADS) temper_kernel(int N, const double* __restrict__ nll,
-                                                                const double* __restrict__ logG,
-                                                                double theta, double ess_min,
-                                                                double* __restrict__ wbar,
-                                                                double* __restrict__ out) {
-    __shared__ double sh1[32], sh2[32];
-    const int t = threadIdx.x;
-    // thread t owns particles t, t + 1024, ... (strided for coalescing)
+__global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THREADS)
+    temper_kernel(int N, const double* __restrict__ nll, const double* __restrict__ logG, double theta,
+                  double ess_min, double* __restrict__ wbar, double* __restrict__ out) {
+    namespace cg = cooperative_groups;
+    __shared__ TemperShm shm;
+    TemperShm* sh = &shm;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int gt = rank * TEMPER_THREADS + threadIdx.x;      // global thread index in the cluster
+    constexpr int STRIDE = TEMPER_CTAS * TEMPER_THREADS;
+    // thread gt owns particles gt, gt + STRIDE, ... (coalesced)
     double phi[TEMPER_PER_THREAD];
     int cnt = 0;
     double lmin = INFINITY;
 #pragma unroll
     for (int e = 0; e < TEMPER_PER_THREAD; ++e) {
-        const int i = t + e * TEMPER_THREADS;
+        const int i = gt + e * STRIDE;
         if (i < N) {
             phi[e] = logG ? nll[i] - logG[i] : nll[i];
             lmin = fmin(lmin, phi[e]);
@@ -76,35 +106,42 @@ __global__ void __launch_bounds__(TEMPER_THREADS) temper_kernel(int N, const dou
             phi[e] = 0.0;
         }
     }
-    const double phimin = block_reduce_min1024(lmin, sh1);
+    // cluster-wide minimum of phi
+    double cmin = cta_min(lmin, sh);
+    if (threadIdx.x == 0) sh->part[1][0] = cmin;
+    cl.sync();
+    double phimin = INFINITY;
+    for (int r = 0; r < TEMPER_CTAS; ++r) phimin = fmin(phimin, cl.map_shared_rank(sh, r)->part[1][0]);
+    int parity = 0;   // the next evaluation writes parity 0; parity 1 is free again after its barrier
     const double rest = 1.0 - theta;
     double s1;
+    double ess = ess_eval(rest, phi, cnt, phimin, sh, parity, s1);
     double d;
-    double ess = ess_at(rest, phi, cnt, phimin, sh1, sh2, s1);
     if (ess >= ess_min) {
         d = rest;
     } else {
         double lo = 0.0, hi = rest;
         for (int it = 0; it < 60; ++it) {
             const double mid = 0.5 * (lo + hi);
-            const double e_mid = ess_at(mid, phi, cnt, phimin, sh1, sh2, s1);
+            const double e_mid = ess_eval(mid, phi, cnt, phimin, sh, parity, s1);
             if (e_mid >= ess_min) lo = mid; else hi = mid;
         }
         d = (lo > 0.0) ? lo : hi;
     }
-    ess = ess_at(d, phi, cnt, phimin, sh1, sh2, s1);
+    ess = ess_eval(d, phi, cnt, phimin, sh, parity, s1);
     const double mx = -d * phimin;
 #pragma unroll
     for (int e = 0; e < TEMPER_PER_THREAD; ++e) {
-        const int i = t + e * TEMPER_THREADS;
+        const int i = gt + e * STRIDE;
         if (i < N) wbar[i] = exp(-d * phi[e] - mx) / s1;
     }
-    if (t == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         out[0] = d;
         out[1] = ess;
         out[2] = (d >= 1.0 - theta) ? 1.0 : theta + d;
         out[3] = (ess == ess) ? 0.0 : 1.0;
     }
+    cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
 // Offspring indices of systematic resampling on integers:
@@ -181,7 +218,7 @@ __global__ void copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ d
 
 int launch_temper(int N, const double* nll, const double* logG, double theta, double ess_min, double* wbar,
                   double* out, cudaStream_t st) {
-    temper_kernel<<<1, TEMPER_THREADS, 0, st>>>(N, nll, logG, theta, ess_min, wbar, out);
+    temper_kernel<<<TEMPER_CTAS, TEMPER_THREADS, 0, st>>>(N, nll, logG, theta, ess_min, wbar, out);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 

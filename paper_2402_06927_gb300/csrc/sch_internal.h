@@ -101,6 +101,48 @@ struct JitterIO {
     int32_t* status;
 };
 
+template <typename R>
+struct AdjointIO {
+    int Ns, ck;
+    const R* m_start;
+    const R* dW;
+    const R* lam;
+    const R* y;
+    double* J;
+    R* g_lam;     // [N][Ns][K]
+    R* g_dW;      // [N][Ns][K] or null
+    R* g_m0;      // [N][n] or null
+    R* ws;        // per-particle scratch: ncp checkpoints + 2 (ck + 1) states of n values
+    size_t ws_per;
+    int32_t* iters;
+    int32_t* status;
+};
+
+template <typename R>
+struct NudgeIO {
+    int Ns, ck, mode, max_iter, particle0;
+    double gtol;
+    uint64_t seed, ctr;
+    const R* m_start;
+    const R* y;
+    R* lam;       // [N][Ns][K] in: start (open loop), out: drift
+    R* dW;        // [N][Ns][K] out: the revealed increments
+    double* J;    // [N] out: final cost
+    R* ws;
+    size_t ws_per;
+    int32_t* iters;   // [N] out: L-BFGS iterations
+    int32_t* status;
+};
+
+template <typename R, int C, int S>
+int launch_adjoint(const ModelArgs<R>& A, const AdjointIO<R>& io, int N, cudaStream_t st);
+template <typename R, int C, int S>
+int launch_nudge(const ModelArgs<R>& A, const NudgeIO<R>& io, int N, cudaStream_t st);
+template <typename R, int C>
+size_t adjoint_smem(int tp, int Ns, int K);
+template <typename R, int C>
+size_t nudge_smem(int tp, int Ns, int K);
+
 template <typename R, int C, int S>
 int launch_window(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st);
 template <typename R, int C, int S>

@@ -94,16 +94,24 @@ __global__ void synth_obs_kernel(ModelArgs<R> A, const R* u, uint64_t seed, uint
     y[j] = u[j * A.stride] + sigma * z[j & 3];
 }
 
-// ensemble mean per node and the truth-based node sums:
-// ws[i] = mean_p u[p][i]; out[4] += u_a^2; out[5] += (u_a - mean)^2
+// ensemble sum per node, particles split over gridDim.y groups: ws[i] += sum_p u[p][i]
 template <typename R>
-__global__ void diag_mean_kernel(ModelArgs<R> A, int N, const R* u, const R* ua, double* ws, double* out) {
+__global__ void diag_sum_kernel(ModelArgs<R> A, int N, const R* u, double* ws) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.n) return;
+    double s = 0.0;
+    for (int p = blockIdx.y; p < N; p += gridDim.y) s += (double)u[(size_t)p * A.n + i];
+    atomicAdd(&ws[i], s);
+}
+
+// ensemble mean per node and the truth-based node sums:
+// ws[i] <- mean_p u[p][i]; out[4] += u_a^2; out[5] += (u_a - mean)^2
+template <typename R>
+__global__ void diag_mean_kernel(ModelArgs<R> A, int N, const R* ua, double* ws, double* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     double a = 0.0, b = 0.0;
     if (i < A.n) {
-        double s = 0.0;
-        for (int p = 0; p < N; ++p) s += (double)u[(size_t)p * A.n + i];
-        const double mean = s / N;
+        const double mean = ws[i] / N;
         ws[i] = mean;
         const double t = (double)ua[i];
         a = t * t;
@@ -139,8 +147,10 @@ __global__ void diag_particle_kernel(ModelArgs<R> A, int N, const R* u, const R*
     }
 }
 
-__global__ void diag_zero_kernel(double* out) {
-    if (threadIdx.x < 8) out[threadIdx.x] = 0.0;
+__global__ void diag_zero_kernel(int n, double* ws, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 8) out[i] = 0.0;
+    if (i < n) ws[i] = 0.0;
 }
 
 template <typename R>
@@ -161,8 +171,10 @@ int launch_synth_obs(const ModelArgs<R>& A, const R* u, uint64_t seed, uint64_t 
 
 template <typename R>
 int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* ua, double* ws, double* out, cudaStream_t st) {
-    diag_zero_kernel<<<1, 32, 0, st>>>(out);
-    diag_mean_kernel<R><<<(A.n + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
+    const int nb = (A.n + 255) / 256;
+    diag_zero_kernel<<<nb, 256, 0, st>>>(A.n, ws, out);
+    diag_sum_kernel<R><<<dim3(nb, N < 64 ? N : 64), 256, 0, st>>>(A, N, u, ws);
+    diag_mean_kernel<R><<<nb, 256, 0, st>>>(A, N, ua, ws, out);
     diag_particle_kernel<R><<<(N * 32 + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
     diag_final_kernel<R><<<1, 32, 0, st>>>(A, N, out);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;

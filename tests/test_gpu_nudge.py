@@ -1,0 +1,137 @@
+"""GPU parity of the adjoint and the nudging optimiser (through the C ABI).
+
+* dJ/dlambda from the reverse-mode adjoint against the oracle's forward
+  tangent-linear gradient (independent code) to 1e-8 relative, FP64;
+* dJ/dlambda, dJ/ddW, dJ/dm0 against central finite differences of the GPU
+  window cost on 16 random directions at the nudging workload size
+  (n = 1024, 8 modes, 20-step window, checkpoints every 5 steps);
+* gradients independent of the checkpoint interval;
+* the L-BFGS drift of both schedules against the oracle's (scipy L-BFGS-B)
+  minimiser, and the revealed increments bit-for-bit keyed draws;
+* the torch.autograd.Function wrapper returns the adjoint's gradients.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import get_config, random_state, random_increments, random_drift, random_obs
+from oracle import filter as OF
+from oracle import nudge as ON
+from oracle import rng as ORNG
+from tests.helpers import gpu_model, oracle_model, tdev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(cfg, N, seed, Ns=None, lam_scale=0.3):
+    Ns = cfg.Ns if Ns is None else Ns
+    om = oracle_model(cfg)
+    u0 = random_state(cfg, N, seed)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    dW = random_increments(cfg, N, seed + 1, steps=Ns)
+    la = random_drift(cfg, N, seed + 2, scale=lam_scale, steps=Ns)
+    y = random_obs(cfg, seed + 3)
+    return om, m0, dW, la, y
+
+
+def test_adjoint_matches_oracle_tangent_linear():
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la, y = _setup(cfg, 2, 5, Ns=4)
+    out = g.adjoint_window(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype), ckpt=2)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in range(2):
+        J, grad = ON.cost_and_gradient(om, m0[p], dW[p], la[p], y, cfg.sigma)
+        assert abs(out["J"][p].item() - J) <= 1e-10 * J
+        assert rel_err(out["g_lam"][p].cpu().numpy(), grad) < 1e-8
+
+
+@pytest.mark.parametrize("ck", [1, 3, 5])
+def test_adjoint_independent_of_checkpoint_interval(ck):
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la, y = _setup(cfg, 2, 6, Ns=5)
+    args = (tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype))
+    ref = g.adjoint_window(*args, ckpt=5)
+    out = g.adjoint_window(*args, ckpt=ck)
+    for k in ("J", "g_lam", "g_dW", "g_m0"):
+        assert torch.allclose(out[k], ref[k], rtol=1e-12, atol=1e-14), k
+
+
+def test_adjoint_finite_differences_16_directions_nudging_workload():
+    cfg = get_config("cfg3_f64")     # n = 1024, 8 modes, 20-step window, FP64
+    g = gpu_model(cfg)
+    N = 2
+    om, m0, dW, la, y = _setup(cfg, N, 7, lam_scale=0.5)
+    md, dWd, lad, yd = (tdev(a, g.dtype) for a in (m0, dW, la, y))
+    out = g.adjoint_window(md, dWd, lad, yd, ckpt=5)
+    r = np.random.default_rng(8)
+
+    def J(m, w, l):
+        return g.adjoint_window(m, w, l, yd, ckpt=5, want_dW=False, want_m0=False)["J"].cpu().numpy()
+
+    for _ in range(16):
+        dl = tdev(r.normal(size=la.shape), g.dtype)
+        dw = tdev(r.normal(scale=math.sqrt(cfg.dt), size=dW.shape), g.dtype)
+        dm = tdev(0.01 * r.normal(size=m0.shape), g.dtype)
+        eps = 1e-6
+        fd = (J(md + eps * dm, dWd + eps * dw, lad + eps * dl) - J(md - eps * dm, dWd - eps * dw, lad - eps * dl)) / (2 * eps)
+        an = ((out["g_lam"] * dl).sum(dim=(1, 2)) + (out["g_dW"] * dw).sum(dim=(1, 2)) + (out["g_m0"] * dm).sum(dim=1))
+        an = an.cpu().numpy()
+        assert np.all(np.abs(fd - an) <= 1e-6 * np.maximum(1.0, np.abs(fd)))
+
+
+def test_autograd_function_returns_adjoint_gradients():
+    from paper_2402_06927_gb300.api import NudgingCost
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la, y = _setup(cfg, 3, 9, Ns=3)
+    md, dWd, lad, yd = (tdev(a, g.dtype) for a in (m0, dW, la, y))
+    lad.requires_grad_(True)
+    dWd.requires_grad_(True)
+    J = NudgingCost.apply(g, md, dWd, lad, yd, 2)
+    (2.0 * J).sum().backward()
+    ref = g.adjoint_window(md, dWd.detach(), lad.detach(), yd, ckpt=2)
+    assert torch.allclose(lad.grad, 2.0 * ref["g_lam"], rtol=1e-13)
+    assert torch.allclose(dWd.grad, 2.0 * ref["g_dW"], rtol=1e-13)
+
+
+def _nudge_case():
+    cfg = get_config("cfg1_f64", n=128, M=16, Ns=3)
+    om = oracle_model(cfg)
+    u0 = random_state(cfg, 2, 11)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    y = random_obs(cfg, 12)
+    return cfg, om, m0, y
+
+
+def test_nudge_open_loop_matches_oracle():
+    cfg, om, m0, y = _nudge_case()
+    g = gpu_model(cfg)
+    out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="open_loop", max_iter=200, gtol=1e-10,
+                  ckpt=2, seed=4, ctr=1)
+    torch.cuda.synchronize()
+    lam = out["lam"].cpu().numpy()
+    for p in range(2):
+        ref, res = ON.nudge_open_loop(om, m0[p], y, cfg.sigma, cfg.Ns, cfg.K, gtol=1e-12)
+        assert rel_err(lam[p], ref) < 1e-5
+        assert abs(out["J"][p].item() - res.fun) <= 1e-9 * res.fun
+        z = ORNG.normals(4, ORNG.TAG_NUDGE, cfg.K, np.arange(cfg.Ns, dtype=np.uint64), np.uint64(p), np.uint64(1))
+        assert np.allclose(out["dW"][p].cpu().numpy(), math.sqrt(cfg.dt) * z, rtol=1e-13, atol=1e-15)
+
+
+def test_nudge_sequential_matches_oracle():
+    cfg, om, m0, y = _nudge_case()
+    g = gpu_model(cfg)
+    out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="sequential", max_iter=100, gtol=1e-10,
+                  ckpt=2, seed=3, ctr=7)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in range(2):
+        lam, dW = ON.nudge_sequential(om, m0[p], y, cfg.sigma, cfg.Ns, cfg.K, seed=3, particle=p, ctr=7,
+                                      gtol=1e-12)
+        assert np.allclose(out["dW"][p].cpu().numpy(), dW, rtol=1e-13, atol=1e-15)
+        assert rel_err(out["lam"][p].cpu().numpy(), lam) < 1e-5
