@@ -167,6 +167,37 @@ int pf_resample(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, in
                 int n_arrays, void* const* arrays, const size_t* row_bytes, void* ws,
                 size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of pf_resample (the paper has no counterpart; it
+ * exists for the way some programs are built, not for the method).
+ *
+ * Some callers cannot call cudaMalloc, or pass in device scratch, at the point
+ * where they resample: a host application that fixes its device memory
+ * budget at start-up and forbids later allocations, a plugin running inside a
+ * framework that owns every device allocation through its own allocator, or a
+ * latency-critical loop that cannot afford cudaMalloc's possible implicit
+ * device synchronisation.  This entry point computes the same offspring
+ * indices as pf_resample and gathers the arrays in place, but stages each
+ * array in a scratch buffer that the library itself holds: a file-scope
+ * __device__ array of PF_RESAMPLE_STATIC_BYTES (16 MiB), which every GPU that
+ * loads the library keeps until the process exits.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *
+ * Limits and rules:
+ *  - each array must satisfy N * row_bytes[a] <= PF_RESAMPLE_STATIC_BYTES,
+ *    otherwise the call returns SCH_ERR_WORKSPACE before launching anything;
+ *    other arguments as for pf_resample (N <= 8192, 16-byte rows);
+ *  - the first call on a device (with that device current) looks up the
+ *    scratch's device address with cudaGetSymbolAddress and caches it; make
+ *    that first call before any stream capture;
+ *  - every call on a device shares the one scratch buffer, which keeps the
+ *    last call's contents (nothing in it needs to start at zero: each array is
+ *    fully written before it is read back).  Calls whose execution overlaps on
+ *    the GPU (on different streams, or from several host threads) race on the
+ *    scratch and must be serialised by the caller. */
+#define PF_RESAMPLE_STATIC_BYTES (16u * 1024u * 1024u)
+int pf_resample_static(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
+                       int n_arrays, void* const* arrays, const size_t* row_bytes, void* stream);
+
 /* Out-of-place row gather: dst row i = src row idx[i]; rows of row_bytes
  * bytes (a multiple of 4; src and dst aligned to the largest of 16, 8, 4 that
  * divides row_bytes). */

@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libsch.so")
 
 SCH_MAX_K = 64
+PF_RESAMPLE_STATIC_BYTES = 16 * 1024 * 1024
 
 SCH_OK = 0
 ERRORS = {
@@ -58,6 +59,7 @@ SIGNATURES = {
     "pf_diagnostics": [P, I, P, P, P, P, P],
     "pf_resample": [I, P, U64, U64, P, I, P, P, P, SZ, P],
     "pf_gather_rows": [I, P, P, P, SZ, P],
+    "pf_resample_static": [I, P, U64, U64, P, I, P, P, P],
     "pf_jitter": [P, I, I, I, D, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
     "sch_prior_sample": [P, I, P, U64, D, P, P, P],
     "sch_adjoint_window": [P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, SZ, P],

@@ -280,6 +280,25 @@ def pf_resample(wbar: torch.Tensor, seed: int, stage_ctr: int, arrays: Sequence[
     return idx
 
 
+def pf_resample_static(wbar: torch.Tensor, seed: int, stage_ctr: int, arrays: Sequence[torch.Tensor] = (),
+                       idx: Optional[torch.Tensor] = None):
+    """As pf_resample, but the in-place gathers are staged in the library's own
+    device scratch (no allocation, no workspace argument; each array at most
+    PF_RESAMPLE_STATIC_BYTES).  Calls that overlap on the GPU share that scratch."""
+    N = wbar.shape[0]
+    _need(wbar, torch.float64, (N,), "wbar")
+    idx = torch.empty(N, dtype=torch.int32, device=wbar.device) if idx is None else idx
+    na = len(arrays)
+    for a in arrays:
+        if a.shape[0] != N or not a.is_contiguous():
+            raise ValueError("arrays must be contiguous with N rows")
+    ptrs = (ct.c_void_p * max(na, 1))(*[a.data_ptr() for a in arrays])
+    rows = (ct.c_size_t * max(na, 1))(*[a[0].numel() * a.element_size() for a in arrays])
+    check(lib().pf_resample_static(N, _ptr(wbar), seed, stage_ctr, _ptr(idx), na, ptrs if na else None,
+                                   rows if na else None, _stream()), "pf_resample_static")
+    return idx
+
+
 def pf_gather_rows(idx: torch.Tensor, src: torch.Tensor, dst: torch.Tensor):
     N = idx.shape[0]
     row = src[0].numel() * src.element_size()
