@@ -1,0 +1,151 @@
+"""FP64 oracle of the learned drift proposal (test infrastructure only).
+
+The proposal replaces the nudging optimiser of Sec. 3.1.3 by a network that
+maps a particle's state at the window start and the innovation of the window's
+observations to the drifts lambda [Ns][K]; any lambda keeps the particle
+weights consistent through the Girsanov factor, so the network only affects
+how close the proposal lands to the observations.  Not in the paper.
+
+Network (all convolutions circular, kernel 5, stride 2, padding 2):
+    features  x0[0] = u_start,  x0[1] = (y_j - u_start(x_j)) / sigma at node j n/M, 0 elsewhere
+    conv1     2 -> C channels,  n -> n/2,   ReLU
+    conv2     C -> C,           n/2 -> n/4, ReLU
+    conv3     C -> C,           n/4 -> n/8, ReLU
+    conv4     C -> C,           n/8 -> n/16, ReLU
+    modes     F[c, 2(j-1)] = (1/P) sum_q h[c, q] sin(2 pi j q / P),
+              F[c, 2(j-1)+1] = (1/P) sum_q h[c, q] cos(2 pi j q / P),   P = n/16, j = 1..K/2
+    head      lambda = Wh F + bh,  F flattened channel-major to C K values
+Loss: L = 1/(2B) sum_b sum_o (lambda_bo - target_bo)^2.  Adam (Kingma & Ba):
+m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, p <- p - lr mhat / (sqrt(vhat) + eps).
+
+Pinned by tests/test_oracle_convnet.py against torch's CPU conv1d (circular
+padding), autograd and torch.optim.Adam in FP64, and central differences.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+KSIZE = 5
+STRIDE = 2
+PAD = 2
+NLAYER = 4
+
+
+def init_params(C: int, K: int, Ns: int, n: int, seed: int):
+    """He-style initialisation from a seeded numpy generator."""
+    r = np.random.default_rng(seed)
+    p = {}
+    cin = 2
+    for l in range(NLAYER):
+        fan = cin * KSIZE
+        p[f"w{l}"] = r.normal(scale=math.sqrt(2.0 / fan), size=(C, cin, KSIZE))
+        p[f"b{l}"] = np.zeros(C)
+        cin = C
+    p["wh"] = r.normal(scale=math.sqrt(1.0 / (C * K)), size=(K * Ns, C * K))
+    p["bh"] = np.zeros(K * Ns)
+    return p
+
+
+def features(u_start: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:
+    """x0 [B, 2, n] from the start velocities [B, n] and the window observations [M]."""
+    u = np.atleast_2d(np.asarray(u_start, dtype=np.float64))
+    B, n = u.shape
+    M = len(y)
+    stride = n // M
+    x = np.zeros((B, 2, n))
+    x[:, 0] = u
+    x[:, 1, ::stride] = (np.asarray(y)[None, :] - u[:, ::stride]) / sigma
+    return x
+
+
+def conv_forward(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """out[b, co, q] = b[co] + sum_ci sum_j w[co, ci, j] x[b, ci, (2q + j - 2) mod L]."""
+    B, Ci, L = x.shape
+    Lo = L // STRIDE
+    idx = (STRIDE * np.arange(Lo)[:, None] + np.arange(KSIZE)[None, :] - PAD) % L   # [Lo, k]
+    cols = x[:, :, idx]                                                               # [B, Ci, Lo, k]
+    return np.einsum("bcqj,ocj->boq", cols, w) + b[None, :, None]
+
+
+def conv_backward(x: np.ndarray, w: np.ndarray, gout: np.ndarray):
+    """Gradients of conv_forward: (dx, dw, db) given dL/dout."""
+    B, Ci, L = x.shape
+    Lo = L // STRIDE
+    idx = (STRIDE * np.arange(Lo)[:, None] + np.arange(KSIZE)[None, :] - PAD) % L
+    cols = x[:, :, idx]
+    dw = np.einsum("boq,bcqj->ocj", gout, cols)
+    db = gout.sum(axis=(0, 2))
+    dcols = np.einsum("boq,ocj->bcqj", gout, w)
+    dx = np.zeros_like(x)
+    for q in range(Lo):
+        for j in range(KSIZE):
+            dx[:, :, idx[q, j]] += dcols[:, :, q, j]
+    return dx, dw, db
+
+
+def mode_matrix(P: int, K: int) -> np.ndarray:
+    """S[q, 2(j-1)] = sin(2 pi j q / P) / P, S[q, 2(j-1)+1] = cos(2 pi j q / P) / P."""
+    q = np.arange(P)
+    S = np.empty((P, K))
+    for jj in range(K // 2):
+        j = jj + 1
+        S[:, 2 * jj] = np.sin(2 * math.pi * j * q / P) / P
+        S[:, 2 * jj + 1] = np.cos(2 * math.pi * j * q / P) / P
+    return S
+
+
+def forward(params, x0: np.ndarray, K: int, Ns: int):
+    """lambda [B, Ns, K] and the cache of activations."""
+    acts = [x0]
+    h = x0
+    for l in range(NLAYER):
+        z = conv_forward(h, params[f"w{l}"], params[f"b{l}"])
+        h = np.maximum(z, 0.0)
+        acts.append(h)
+    B, C, P = h.shape
+    S = mode_matrix(P, K)
+    F = np.einsum("bcq,qk->bck", h, S).reshape(B, C * K)
+    lam = F @ params["wh"].T + params["bh"][None, :]
+    return lam.reshape(B, Ns, K), (acts, F, S)
+
+
+def loss_and_grad(params, x0: np.ndarray, target: np.ndarray, K: int, Ns: int):
+    """L = 1/(2B) sum (lambda - target)^2 and dL/dparams (manual backward)."""
+    lam, (acts, F, S) = forward(params, x0, K, Ns)
+    B = x0.shape[0]
+    diff = (lam - target).reshape(B, Ns * K)
+    L = 0.5 * float(np.sum(diff * diff)) / B
+    g = {}
+    glam = diff / B                                   # [B, Ns K]
+    g["wh"] = glam.T @ F
+    g["bh"] = glam.sum(axis=0)
+    gF = (glam @ params["wh"]).reshape(B, -1, K)      # [B, C, K]
+    gh = np.einsum("bck,qk->bcq", gF, S)
+    for l in reversed(range(NLAYER)):
+        gz = gh * (acts[l + 1] > 0.0)
+        dx, dw, db = conv_backward(acts[l], params[f"w{l}"], gz)
+        g[f"w{l}"] = dw
+        g[f"b{l}"] = db
+        gh = dx
+    return L, g
+
+
+class Adam:
+    def __init__(self, params, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        self.lr, self.b1, self.b2, self.eps = lr, b1, b2, eps
+        self.m = {k: np.zeros_like(v) for k, v in params.items()}
+        self.v = {k: np.zeros_like(v) for k, v in params.items()}
+        self.t = 0
+
+    def step(self, params, grads):
+        self.t += 1
+        for k in params:
+            g = grads[k]
+            self.m[k] = self.b1 * self.m[k] + (1 - self.b1) * g
+            self.v[k] = self.b2 * self.v[k] + (1 - self.b2) * g * g
+            mhat = self.m[k] / (1 - self.b1 ** self.t)
+            vhat = self.v[k] / (1 - self.b2 ** self.t)
+            params[k] = params[k] - self.lr * mhat / (np.sqrt(vhat) + self.eps)
+        return params
