@@ -22,6 +22,12 @@
 
 namespace sch {
 
+// the adjoint and optimiser kernels keep more live state: no occupancy push
+template <int TP>
+struct OccAdj {
+    static constexpr int minb = TP <= 32 ? 16 : (TP <= 64 ? 8 : (TP <= 128 ? 4 : (TP <= 256 ? 2 : 1)));
+};
+
 // --------------------------------------------------------------------------
 // generic variable cyclic tridiagonal solve: row i reads
 // a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i.  Two CTA barriers.
@@ -367,7 +373,7 @@ __host__ __device__ inline size_t adj_smem_bytes(int Ns, int K) {
 
 // J and dJ/dlambda, dJ/ddW, dJ/dm0 of a whole window for every particle
 template <typename R, int C, int TP, int S>
-__global__ void __launch_bounds__(TP, Occ<TP>::minb) adjoint_kernel(ModelArgs<R> A, AdjointIO<R> io) {
+__global__ void __launch_bounds__(TP, OccAdj<TP>::minb) adjoint_kernel(ModelArgs<R> A, AdjointIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     R* noise = reinterpret_cast<R*>(smem_raw + shm_base_bytes<R, TP>());
@@ -445,7 +451,7 @@ __device__ __forceinline__ double block_absmax(Shm<R, TP>* sh, const double* a, 
 // (k/4, n, particle, ctr)) and advance the start state one step.
 // Open loop: optimise all drifts with every increment zero, then reveal all.
 template <typename R, int C, int TP, int S>
-__global__ void __launch_bounds__(TP, Occ<TP>::minb) nudge_kernel(ModelArgs<R> A, NudgeIO<R> io) {
+__global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R> A, NudgeIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     const int Ns = io.Ns, K = A.K, NK = Ns * K;

@@ -768,13 +768,19 @@ __device__ __forceinline__ void block_sum2(Shm<R, TP>* sh, double& a, double& b)
 // --------------------------------------------------------------------------
 // kernels
 // --------------------------------------------------------------------------
-template <int TP>
+// Minimum resident CTAs per SM requested from the compiler.  FP32 with 128
+// threads per particle (n = 1024) asks for 7, so that 7 x 152 SMs hold a
+// 1024-particle ensemble in one wave (72 registers, a few spilled); otherwise
+// the register file allows up to 128 registers per thread.
+template <typename R, int TP>
 struct Occ {
-    static constexpr int minb = TP <= 32 ? 16 : (TP <= 64 ? 8 : (TP <= 128 ? 4 : (TP <= 256 ? 2 : 1)));
+    static constexpr int minb = (sizeof(R) == 4 && TP == 128)
+                                    ? 7
+                                    : (TP <= 32 ? 16 : (TP <= 64 ? 8 : (TP <= 128 ? 4 : (TP <= 256 ? 2 : 1))));
 };
 
 template <typename R, int C, int TP, int S>
-__global__ void __launch_bounds__(TP, Occ<TP>::minb) window_kernel(ModelArgs<R> A, WindowIO<R> io) {
+__global__ void __launch_bounds__(TP, Occ<R, TP>::minb) window_kernel(ModelArgs<R> A, WindowIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     R* noise = reinterpret_cast<R*>(smem_raw + shm_base_bytes<R, TP>());
@@ -811,7 +817,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) window_kernel(ModelArgs<R> 
 // PCN jittering: n_iter proposals of the window noise, each run through the
 // whole window from m_start and accepted with probability min(1, exp(w0 - w1)).
 template <typename R, int C, int TP, int S>
-__global__ void __launch_bounds__(TP, Occ<TP>::minb) jitter_kernel(ModelArgs<R> A, JitterIO<R> io) {
+__global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<R> A, JitterIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     const int p = blockIdx.x;
@@ -896,7 +902,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) jitter_kernel(ModelArgs<R> 
 
 // Helmholtz utilities: mode 0: u = H^{-1} M m ; mode 1: m = M^{-1} H u
 template <typename R, int C, int TP>
-__global__ void __launch_bounds__(TP, Occ<TP>::minb) helm_kernel(ModelArgs<R> A, const R* in, R* out, int mode) {
+__global__ void __launch_bounds__(TP, Occ<R, TP>::minb) helm_kernel(ModelArgs<R> A, const R* in, R* out, int mode) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     const int p = blockIdx.x;
@@ -924,7 +930,7 @@ __global__ void __launch_bounds__(TP, Occ<TP>::minb) helm_kernel(ModelArgs<R> A,
 // Prior ensemble: u = u_truth + scale (a_p S^3 W_p + b_p), S the P1 solve of
 // (U, v) + (U_x, v_x) = (f, v); then m = M^{-1} H u.
 template <typename R, int C, int TP>
-__global__ void __launch_bounds__(TP, Occ<TP>::minb) prior_kernel(ModelArgs<R> A, const R* u_truth, uint64_t seed,
+__global__ void __launch_bounds__(TP, Occ<R, TP>::minb) prior_kernel(ModelArgs<R> A, const R* u_truth, uint64_t seed,
                                                                  R scale, R* m_out, R* u_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
