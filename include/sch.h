@@ -150,8 +150,9 @@ int sch_loglik(sch_ctx* ctx, int N, const void* u, const void* y, const void* dW
  * ESS(exp(-dtheta phi)) >= ess_min (Eq. ess): the whole step if it passes,
  * else 60 bisection steps on [0, 1 - theta] (falls back to the smallest
  * point tried if none passes).  Writes wbar[N] (double, normalised weights at
- * dtheta) and out[4] = {dtheta, ESS, theta_new, status}; theta_new is exactly
- * 1.0 when the remaining step was taken.  N <= 16384. */
+ * dtheta) and out[4] = {dtheta, ESS at dtheta, theta_new, ESS of the whole
+ * remaining step}; theta_new is exactly 1.0 when the remaining step was taken.
+ * N <= 16384. */
 int pf_temper(int N, const double* nll, const double* logG, double theta, double ess_min,
               double* wbar, double* out, void* stream);
 
@@ -275,6 +276,49 @@ size_t pf_nudge_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt)
 int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gtol, int ckpt, uint64_t seed,
              uint64_t ctr, const void* m_start, const void* y, void* lambda, void* dW, double* J, int32_t* iters,
              int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned drift proposal (not in the paper): a 1D convolutional network that
+ * maps a particle's window-start velocity and the innovation of the window's
+ * observations to nudging drifts lambda [Ns][K], trained on drifts produced by
+ * pf_nudge.  Any drift keeps the particle weights consistent through the
+ * Girsanov factor (Eq. girsanov DG approx), so the network only changes how
+ * close the proposal lands to the observations; the optimiser stays as the
+ * fallback and the judge.
+ *   x0 = (u_start, (y - u_start(x_obs)) / sigma at the observation nodes)   [2][n]
+ *   4 x (circular convolution, kernel 5, stride 2, C channels, ReLU)    -> [C][n/16]
+ *   F[c][2(j-1)], F[c][2j-1] = (1/P) sum_q h[c][q] sin, cos(2 pi j q / P), P = n/16
+ *   lambda = Wh F + bh
+ * Parameters are one FP32 vector (per layer w[C][Cin][5], b[C]; then Wh[K Ns][C K],
+ * bh[K Ns]); activations FP32 with FP32 accumulation.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n;       /* nodes (multiple of 16 and of M) */
+    int32_t K;       /* drift modes (even) */
+    int32_t Ns;      /* steps per window */
+    int32_t C;       /* channels */
+    int32_t M;       /* observation points */
+    float sigma;     /* observation noise, scales the innovation */
+} nn_shape;
+
+/* Number of FP32 parameters (0 for an invalid shape). */
+size_t nn_param_count(const nn_shape* shape);
+/* Workspace bytes for a batch of B samples (activations and gradients). */
+size_t nn_workspace_bytes(const nn_shape* shape, int B);
+/* lambda_out float [B][Ns][K] for u_start float [B][n] and observations y float
+ * [B][M] with row stride y_stride floats (0: one y shared by the batch). */
+int nn_forward(const nn_shape* shape, int B, const float* params, const float* u_start, const float* y,
+               int y_stride, float* lambda_out, void* ws, size_t ws_bytes, void* stream);
+/* Loss L = 1/(2B) sum (lambda - target)^2 (double, device scalar) and its
+ * gradient with respect to every parameter (float [nn_param_count]). */
+int nn_backward(const nn_shape* shape, int B, const float* params, const float* u_start, const float* y,
+                int y_stride, const float* target, float* grads, double* loss, void* ws, size_t ws_bytes,
+                void* stream);
+/* One Adam step (Kingma and Ba) at step number t >= 1 over count parameters:
+ * m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+ * p <- p - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */
+int nn_adam_step(size_t count, float* params, const float* grads, float* m, float* v, int t, float lr, float b1,
+                 float b2, float eps, void* stream);
 
 /* Prior ensemble about a truth velocity (a reading of Eq. init_solve): for
  * particle p, W_p is a DG0 field with cell values sqrt(h) z (z keyed

@@ -38,6 +38,11 @@ class SchParams(ct.Structure):
     ]
 
 
+class NNShape(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("K", ct.c_int32), ("Ns", ct.c_int32), ("C", ct.c_int32),
+                ("M", ct.c_int32), ("sigma", ct.c_float)]
+
+
 P = ct.c_void_p
 I = ct.c_int
 U64 = ct.c_uint64
@@ -64,10 +69,15 @@ SIGNATURES = {
     "sch_prior_sample": [P, I, P, U64, D, P, P, P],
     "sch_adjoint_window": [P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, SZ, P],
     "pf_nudge": [P, I, I, I, I, D, I, U64, U64, P, P, P, P, P, P, P, P, SZ, P],
+    "nn_forward": [P, I, P, P, P, I, P, P, SZ, P],
+    "nn_backward": [P, I, P, P, P, I, P, P, P, P, SZ, P],
+    "nn_adam_step": [SZ, P, P, P, P, I, ct.c_float, ct.c_float, ct.c_float, ct.c_float, P],
 }
 RESTYPES = {"pf_resample_workspace_bytes": (SZ, [I, SZ]),
             "sch_adjoint_workspace_bytes": (SZ, [P, I, I, I]),
-            "pf_nudge_workspace_bytes": (SZ, [P, I, I, I])}
+            "pf_nudge_workspace_bytes": (SZ, [P, I, I, I]),
+            "nn_param_count": (SZ, [P]),
+            "nn_workspace_bytes": (SZ, [P, I])}
 
 _LIB = None
 

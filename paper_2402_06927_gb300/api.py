@@ -12,7 +12,7 @@ from typing import Optional, Sequence
 import torch
 
 from . import _lib
-from ._lib import SCH_F32, SCH_F64, SchParams, check, lib
+from ._lib import NNShape, SCH_F32, SCH_F64, SchParams, check, lib
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -247,7 +247,8 @@ class SchModel:
 # ---------------------------------------------------------------------- #
 def pf_temper(nll: torch.Tensor, logG: Optional[torch.Tensor], theta: float, ess_min: float,
               wbar: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None):
-    """Returns (wbar, out) with out = [dtheta, ESS, theta_new, status] on the device; phi = nll - logG."""
+    """Returns (wbar, out) with out = [dtheta, ESS, theta_new, ESS of the whole remaining step]
+    on the device; phi = nll - logG."""
     N = nll.shape[0]
     _need(nll, torch.float64, (N,), "nll")
     if logG is not None:
@@ -330,3 +331,78 @@ class NudgingCost(torch.autograd.Function):
         g_m0, g_dW, g_lam = ctx.saved_tensors
         s = gJ.to(g_lam.dtype)
         return (None, g_m0 * s[:, None], g_dW * s[:, None, None], g_lam * s[:, None, None], None, None)
+
+
+class ProposalNet:
+    """Learned drift proposal (nn_forward / nn_backward / nn_adam_step).
+
+    ``params`` is the flat FP32 parameter vector in the library's layout
+    (per layer w[C][Cin][5], b[C]; then Wh[K Ns][C K], bh[K Ns]); when omitted
+    it is initialised with a seeded He-normal draw.
+    """
+
+    def __init__(self, n: int, K: int, Ns: int, M: int, sigma: float, C: int = 64,
+                 params: Optional[torch.Tensor] = None, seed: int = 0):
+        self.shape = NNShape(n, K, Ns, C, M, sigma)
+        self.n, self.K, self.Ns, self.C, self.M = n, K, Ns, C, M
+        self.count = int(lib().nn_param_count(ct.byref(self.shape)))
+        if self.count == 0:
+            raise ValueError("invalid network shape")
+        if params is None:
+            g = torch.Generator(device="cpu").manual_seed(seed)
+            parts, cin = [], 2
+            for _ in range(4):
+                parts.append(torch.randn(C * cin * 5, generator=g) * (2.0 / (cin * 5)) ** 0.5)
+                parts.append(torch.zeros(C))
+                cin = C
+            parts.append(torch.randn(K * Ns * C * K, generator=g) * (1.0 / (C * K)) ** 0.5)
+            parts.append(torch.zeros(K * Ns))
+            params = torch.cat(parts)
+        self.params = params.to(device="cuda", dtype=torch.float32).contiguous()
+        if self.params.numel() != self.count:
+            raise ValueError(f"expected {self.count} parameters")
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.t = 0
+        self._ws = None
+
+    def _workspace(self, B: int):
+        need = int(lib().nn_workspace_bytes(ct.byref(self.shape), B))
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        return self._ws
+
+    def forward(self, u_start: torch.Tensor, y: torch.Tensor, out: Optional[torch.Tensor] = None):
+        """lambda [B, Ns, K] for velocities [B, n]; y is [M] (shared) or [B, M]."""
+        B = u_start.shape[0]
+        _need(u_start, torch.float32, (B, self.n), "u_start")
+        ys = 0 if y.dim() == 1 else self.M
+        out = torch.empty((B, self.Ns, self.K), dtype=torch.float32, device="cuda") if out is None else out
+        ws = self._workspace(B)
+        check(lib().nn_forward(ct.byref(self.shape), B, _ptr(self.params), _ptr(u_start), _ptr(y), ys, _ptr(out),
+                               _ptr(ws), ws.numel(), _stream()), "nn_forward")
+        return out
+
+    def loss_and_grad(self, u_start: torch.Tensor, y: torch.Tensor, target: torch.Tensor):
+        B = u_start.shape[0]
+        _need(u_start, torch.float32, (B, self.n), "u_start")
+        _need(target, torch.float32, (B, self.Ns, self.K), "target")
+        ys = 0 if y.dim() == 1 else self.M
+        grads = torch.empty_like(self.params)
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        ws = self._workspace(B)
+        check(lib().nn_backward(ct.byref(self.shape), B, _ptr(self.params), _ptr(u_start), _ptr(y), ys,
+                                _ptr(target), _ptr(grads), _ptr(loss), _ptr(ws), ws.numel(), _stream()),
+              "nn_backward")
+        return loss, grads
+
+    def adam_step(self, grads: torch.Tensor, lr: float = 1e-3, b1: float = 0.9, b2: float = 0.999,
+                  eps: float = 1e-8):
+        self.t += 1
+        check(lib().nn_adam_step(self.count, _ptr(self.params), _ptr(grads), _ptr(self.m), _ptr(self.v), self.t,
+                                 lr, b1, b2, eps, _stream()), "nn_adam_step")
+
+    def train_step(self, u_start, y, target, lr: float = 1e-3):
+        loss, grads = self.loss_and_grad(u_start, y, target)
+        self.adam_step(grads, lr)
+        return loss

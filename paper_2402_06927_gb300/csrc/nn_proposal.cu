@@ -1,0 +1,410 @@
+// Learned drift proposal on sm_103a: forward, backward and Adam of the small
+// 1D convolutional network that maps a particle's window-start velocity and
+// the innovation of the window's observations to nudging drifts lambda
+// [Ns][K] (used in place of, or as the starting point of, the optimiser of
+// Sec. 3.1.3; any drift keeps the weights consistent through Girsanov).
+//
+// Network (FP32 parameters and activations, FP32 accumulation):
+//   x0[b] = (u_start, (y - u_start(x_obs)) / sigma scattered at the obs nodes)   2 x n
+//   four circular convolutions, kernel 5, stride 2, padding 2, C channels, ReLU  -> C x n/16
+//   Fourier-mode projection F[c][k] = (1/P) sum_q h[c][q] {sin,cos}(2 pi j q / P)
+//   linear head lambda = Wh F + bh
+// Every contraction runs through one tiled SGEMM kernel with gather functors
+// (implicit im2col for the convolutions), so no im2col buffer is formed.
+#include "sch_internal.h"
+
+namespace sch {
+
+struct NNDims {
+    int n, K, Ns, C, M;
+    float sigma;
+    int L[5];     // positions at layers 0..4: n, n/2, n/4, n/8, n/16
+    int cin[4];   // input channels of conv l
+    size_t off_w[4], off_b[4], off_wh, off_bh, nparam;
+    size_t act_off[5], off_F, off_lam, act_total;   // per-sample activation offsets (floats)
+};
+
+static NNDims make_dims(const nn_shape* s) {
+    NNDims d{};
+    d.n = s->n; d.K = s->K; d.Ns = s->Ns; d.C = s->C; d.M = s->M; d.sigma = s->sigma;
+    for (int l = 0; l <= 4; ++l) d.L[l] = s->n >> l;
+    size_t o = 0;
+    for (int l = 0; l < 4; ++l) {
+        d.cin[l] = (l == 0) ? 2 : s->C;
+        d.off_w[l] = o; o += (size_t)s->C * d.cin[l] * 5;
+        d.off_b[l] = o; o += (size_t)s->C;
+    }
+    d.off_wh = o; o += (size_t)s->K * s->Ns * s->C * s->K;
+    d.off_bh = o; o += (size_t)s->K * s->Ns;
+    d.nparam = o;
+    size_t a = 0;
+    d.act_off[0] = a; a += 2 * (size_t)d.L[0];
+    for (int l = 1; l <= 4; ++l) { d.act_off[l] = a; a += (size_t)s->C * d.L[l]; }
+    d.off_F = a; a += (size_t)s->C * s->K;
+    d.off_lam = a; a += (size_t)s->K * s->Ns;
+    d.act_total = a;
+    return d;
+}
+
+// --------------------------------------------------------------------------
+// tiled SGEMM: C[m][n] (+)= sum_k A(m, k) B(k, n) over a batch index z.
+// 64 x 64 tiles, k-chunks of 16, 256 threads, 4 x 4 outputs per thread.
+// --------------------------------------------------------------------------
+constexpr int TM = 64, TN = 64, TK = 16;
+
+template <typename LA, typename LB, typename EP>
+__global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int Kd, int kchunk, LA la, LB lb, EP ep) {
+    __shared__ float As[TK][TM + 4];
+    __shared__ float Bs[TK][TN + 4];
+    const int z = blockIdx.z;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int kbeg = (int)(blockIdx.z % (unsigned)max(1, (Kd + kchunk - 1) / kchunk)) * kchunk;
+    const int zb = z / max(1, (Kd + kchunk - 1) / kchunk);
+    const int kend = min(Kd, kbeg + kchunk);
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k0 = kbeg; k0 < kend; k0 += TK) {
+        for (int e = threadIdx.x; e < TK * TM; e += 256) {
+            const int kk = e / TM, mm = e % TM;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < M && gk < kend) ? la(zb, gm, gk) : 0.f;
+        }
+        for (int e = threadIdx.x; e < TK * TN; e += 256) {
+            const int kk = e / TN, nn = e % TN;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[kk][nn] = (gn < N && gk < kend) ? lb(zb, gk, gn) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty * 4 + i, gn = n0 + tx * 4 + j;
+            if (gm < M && gn < N) ep(zb, gm, gn, acc[i][j]);
+        }
+}
+
+template <typename LA, typename LB, typename EP>
+static void sgemm(int batch, int M, int N, int Kd, int splitk, LA la, LB lb, EP ep, cudaStream_t st) {
+    const int kchunk = (Kd + splitk - 1) / splitk;
+    const int nk = (Kd + kchunk - 1) / kchunk;
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch * nk);
+    sgemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, kchunk, la, lb, ep);
+}
+
+// --------------------------------------------------------------------------
+// functors
+// --------------------------------------------------------------------------
+struct ConvW {            // A(co, kk) = w[co][kk], kk = ci * 5 + j
+    const float* w; int KK;
+    __device__ float operator()(int, int m, int k) const { return w[(size_t)m * KK + k]; }
+};
+struct ConvX {            // B(kk, q) = x[b][ci][(2q + j - 2) mod L]
+    const float* x; size_t bstride; int L;
+    __device__ float operator()(int b, int k, int q) const {
+        const int ci = k / 5, j = k % 5;
+        int i = 2 * q + j - 2;
+        i = (i + L) % L;
+        return x[(size_t)b * bstride + (size_t)ci * L + i];
+    }
+};
+struct StoreAct {         // out[b][co][q] = relu(acc + bias[co])
+    float* out; size_t bstride; int Lo; const float* bias;
+    __device__ void operator()(int b, int m, int n, float v) const {
+        v += bias[m];
+        out[(size_t)b * bstride + (size_t)m * Lo + n] = v > 0.f ? v : 0.f;
+    }
+};
+// backward data: dx[b][ci][i] = sum_{co, j} w[co][ci][j] g[b][co][q], 2q + j - 2 = i (mod L)
+struct WT {               // A(ci, kk') = w[co][ci][j], kk' = co * 5 + j
+    const float* w; int Ci;
+    __device__ float operator()(int, int m, int k) const {
+        const int co = k / 5, j = k % 5;
+        return w[((size_t)co * Ci + m) * 5 + j];
+    }
+};
+struct GatherG {          // B(kk', i) = g[b][co][q] if 2q + j - 2 = i (mod L), else 0
+    const float* g; size_t bstride; int L, Lo;
+    __device__ float operator()(int b, int k, int i) const {
+        const int co = k / 5, j = k % 5;
+        int t = i - j + 2;
+        t = ((t % L) + L) % L;
+        if (t & 1) return 0.f;
+        const int q = t >> 1;
+        return g[(size_t)b * bstride + (size_t)co * Lo + q];
+    }
+};
+struct StoreMasked {      // dx masked by the ReLU of the layer that produced x (x > 0)
+    float* out; const float* x; size_t bstride; int L; int mask;
+    __device__ void operator()(int b, int m, int n, float v) const {
+        const size_t o = (size_t)b * bstride + (size_t)m * L + n;
+        out[o] = (mask && !(x[o] > 0.f)) ? 0.f : v;
+    }
+};
+// backward weights: dw[co][kk] = sum_{b, q} g[b][co][q] X(b, kk, q), batch folded into k
+struct GRowsBQ {          // A(co, (b, q)) = g[b][co][q]
+    const float* g; size_t bstride; int Lo;
+    __device__ float operator()(int, int m, int k) const {
+        const int b = k / Lo, q = k % Lo;
+        return g[(size_t)b * bstride + (size_t)m * Lo + q];
+    }
+};
+struct ConvXT {           // B((b, q), kk) = x[b][ci][(2q + j - 2) mod L]
+    const float* x; size_t bstride; int L, Lo;
+    __device__ float operator()(int, int k, int n) const {
+        const int b = k / Lo, q = k % Lo;
+        const int ci = n / 5, j = n % 5;
+        int i = 2 * q + j - 2;
+        i = (i + L) % L;
+        return x[(size_t)b * bstride + (size_t)ci * L + i];
+    }
+};
+struct AtomicAdd2D {
+    float* out; int ld;
+    __device__ void operator()(int, int m, int n, float v) const { atomicAdd(&out[(size_t)m * ld + n], v); }
+};
+// generic row-major accessors
+struct RowMajor {         // A(m, k) = p[z * bs + m * ld + k]
+    const float* p; size_t bs; int ld;
+    __device__ float operator()(int z, int m, int k) const { return p[(size_t)z * bs + (size_t)m * ld + k]; }
+};
+struct RowMajorT {        // A(m, k) = p[z * bs + k * ld + m]
+    const float* p; size_t bs; int ld;
+    __device__ float operator()(int z, int m, int k) const { return p[(size_t)z * bs + (size_t)k * ld + m]; }
+};
+struct ModeS {            // S(q, k) = {sin, cos}(2 pi j q / P) / P
+    int P;
+    __device__ float operator()(int, int q, int k) const {
+        const int j = k / 2 + 1;
+        float s, c;
+        sincospif(2.0f * (float)((j * q) % P) / (float)P, &s, &c);
+        return ((k & 1) ? c : s) / (float)P;
+    }
+};
+struct ModeST {           // S^T(k, q)
+    int P;
+    __device__ float operator()(int z, int k, int q) const { return ModeS{P}(z, q, k); }
+};
+struct Store {            // out[z * bs + m * ld + n] = v (+ bias[n] if bias)
+    float* out; size_t bs; int ld; const float* bias;
+    __device__ void operator()(int z, int m, int n, float v) const {
+        out[(size_t)z * bs + (size_t)m * ld + n] = v + (bias ? bias[n] : 0.f);
+    }
+};
+
+// --------------------------------------------------------------------------
+// element-wise kernels
+// --------------------------------------------------------------------------
+__global__ void features_kernel(int B, int n, int M, float sigma, const float* u, const float* y, int ystride,
+                                float* x0, size_t bstride) {
+    const size_t tot = (size_t)B * n;
+    const int stride = n / M;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / n), i = (int)(e % n);
+        const float ub = u[(size_t)b * n + i];
+        float inn = 0.f;
+        if (i % stride == 0) inn = (y[(size_t)b * ystride + i / stride] - ub) / sigma;
+        x0[(size_t)b * bstride + i] = ub;
+        x0[(size_t)b * bstride + n + i] = inn;
+    }
+}
+
+// glam = (lam - target) / B, loss partials in double
+__global__ void loss_kernel(int B, int O, const float* lam, size_t lstride, const float* target, float* glam,
+                            double* loss) {
+    const size_t tot = (size_t)B * O;
+    double acc = 0.0;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int b = (int)(e / O), o = (int)(e % O);
+        const float d = lam[(size_t)b * lstride + o] - target[e];
+        glam[e] = d / (float)B;
+        acc += 0.5 * (double)d * (double)d / B;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+__global__ void bias_grad_kernel(int B, int Co, int L, const float* g, size_t bstride, float* db) {
+    const int co = blockIdx.x;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < B * L; e += blockDim.x) {
+        const int b = e / L, q = e % L;
+        acc += g[(size_t)b * bstride + (size_t)co * L + q];
+    }
+    acc = warp_sum(acc);
+    __shared__ double sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+        db[co] = (float)s;
+    }
+}
+
+__global__ void zero_kernel(float* p, size_t nel, double* d) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nel; e += (size_t)gridDim.x * blockDim.x)
+        p[e] = 0.f;
+    if (d && blockIdx.x == 0 && threadIdx.x == 0) *d = 0.0;
+}
+
+__global__ void adam_kernel(size_t nel, float* p, const float* g, float* m, float* v, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nel; e += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[e];
+        const float mi = b1 * m[e] + (1.f - b1) * gi;
+        const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+        m[e] = mi;
+        v[e] = vi;
+        p[e] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+__global__ void copy_rows_kernel(int B, int O, const float* src, size_t sstride, float* dst) {
+    const size_t tot = (size_t)B * O;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = src[(e / O) * sstride + e % O];
+}
+
+static int grid_elems(size_t n) {
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+// forward pass into the activation workspace (per-sample stride act_total)
+static void nn_forward_impl(const NNDims& d, int B, const float* params, const float* u, const float* y, int ystride,
+                            float* act, cudaStream_t st) {
+    const size_t bs = d.act_total;
+    features_kernel<<<grid_elems((size_t)B * d.n), 256, 0, st>>>(B, d.n, d.M, d.sigma, u, y, ystride,
+                                                                 act + d.act_off[0], bs);
+    for (int l = 0; l < 4; ++l) {
+        const int Ci = d.cin[l], Lin = d.L[l], Lo = d.L[l + 1];
+        sgemm(B, d.C, Lo, Ci * 5, 1, ConvW{params + d.off_w[l], Ci * 5}, ConvX{act + d.act_off[l], bs, Lin},
+              StoreAct{act + d.act_off[l + 1], bs, Lo, params + d.off_b[l]}, st);
+    }
+    const int P = d.L[4];
+    // F[b][c][k] = sum_q h4[b][c][q] S[q][k]
+    sgemm(B, d.C, d.K, P, 1, RowMajor{act + d.act_off[4], bs, P}, ModeS{P},
+          Store{act + d.off_F, bs, d.K, nullptr}, st);
+    // lambda[b][o] = sum_f F[b][f] Wh[o][f] + bh[o]   (one GEMM over the batch: rows b)
+    const int O = d.K * d.Ns, FF = d.C * d.K;
+    sgemm(1, B, O, FF, 1, RowMajor{act + d.off_F, 0, (int)bs}, RowMajorT{params + d.off_wh, 0, FF},
+          Store{act + d.off_lam, 0, (int)bs, params + d.off_bh}, st);
+}
+
+}  // namespace sch
+
+using namespace sch;
+
+extern "C" {
+
+size_t nn_param_count(const nn_shape* s) {
+    if (!s || s->n <= 0 || (s->n % 16) || s->K <= 0 || s->Ns <= 0 || s->C <= 0) return 0;
+    return make_dims(s).nparam;
+}
+
+size_t nn_workspace_bytes(const nn_shape* s, int B) {
+    if (!s || B <= 0 || nn_param_count(s) == 0) return 0;
+    const NNDims d = make_dims(s);
+    // forward activations + two gradient buffers of one activation each + glam/gF
+    return ((size_t)B * d.act_total * 3 + 2 * (size_t)d.C * d.K * B + (size_t)d.K * d.Ns * B) * sizeof(float);
+}
+
+static int nn_check(const nn_shape* s, int B, const void* params, const void* u, const void* y, void* ws,
+                    size_t ws_bytes) {
+    if (!s || B <= 0 || !params || !u || !y || !ws) return SCH_ERR_ARG;
+    if (nn_param_count(s) == 0 || s->M <= 0 || s->n % s->M || !(s->sigma > 0.f)) return SCH_ERR_ARG;
+    if (ws_bytes < nn_workspace_bytes(s, B)) return SCH_ERR_WORKSPACE;
+    return SCH_OK;
+}
+
+int nn_forward(const nn_shape* s, int B, const float* params, const float* u_start, const float* y, int y_stride,
+               float* lam_out, void* ws, size_t ws_bytes, void* stream) {
+    int rc = nn_check(s, B, params, u_start, y, ws, ws_bytes);
+    if (rc != SCH_OK) return rc;
+    if (!lam_out || y_stride < 0) return SCH_ERR_ARG;
+    const NNDims d = make_dims(s);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    float* act = reinterpret_cast<float*>(ws);
+    nn_forward_impl(d, B, params, u_start, y, y_stride, act, st);
+    const int O = d.K * d.Ns;
+    copy_rows_kernel<<<grid_elems((size_t)B * O), 256, 0, st>>>(B, O, act + d.off_lam, d.act_total, lam_out);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+int nn_backward(const nn_shape* s, int B, const float* params, const float* u_start, const float* y, int y_stride,
+                const float* target, float* grads, double* loss, void* ws, size_t ws_bytes, void* stream) {
+    int rc = nn_check(s, B, params, u_start, y, ws, ws_bytes);
+    if (rc != SCH_OK) return rc;
+    if (!target || !grads || !loss || y_stride < 0) return SCH_ERR_ARG;
+    const NNDims d = make_dims(s);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    float* act = reinterpret_cast<float*>(ws);
+    const size_t bs = d.act_total;
+    float* gA = act + (size_t)B * bs;          // gradient of an activation (ping)
+    float* gB = gA + (size_t)B * bs;           // (pong)
+    float* gF = gB + (size_t)B * bs;           // [B][C K]
+    float* glam = gF + (size_t)B * d.C * d.K;  // [B][O]
+    const int O = d.K * d.Ns, FF = d.C * d.K, P = d.L[4];
+    nn_forward_impl(d, B, params, u_start, y, y_stride, act, st);
+    zero_kernel<<<grid_elems(d.nparam), 256, 0, st>>>(grads, d.nparam, loss);
+    loss_kernel<<<grid_elems((size_t)B * O), 256, 0, st>>>(B, O, act + d.off_lam, bs, target, glam, loss);
+    // head: dWh[o][f] = sum_b glam[b][o] F[b][f]; dbh[o] = sum_b glam[b][o]; gF = glam Wh
+    sgemm(1, O, FF, B, 16, RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
+          AtomicAdd2D{grads + d.off_wh, FF}, st);
+    bias_grad_kernel<<<O, 256, 0, st>>>(B, O, 1, glam, (size_t)O, grads + d.off_bh);
+    sgemm(1, B, FF, O, 1, RowMajor{glam, 0, O}, RowMajor{params + d.off_wh, 0, FF}, Store{gF, 0, FF, nullptr}, st);
+    // dh4[b][c][q] = sum_k gF[b][c][k] S[q][k], masked by ReLU(h4 > 0)
+    sgemm(B, d.C, P, d.K, 1, RowMajor{gF, (size_t)FF, d.K}, ModeST{P}, StoreMasked{gA, act + d.act_off[4], bs, P, 1},
+          st);
+    // conv layers, last to first; gA holds dL/dz of layer l's output at offset act_off[l+1]
+    float* gcur = gA;
+    float* gnext = gB;
+    for (int l = 3; l >= 0; --l) {
+        const int Ci = d.cin[l], Lin = d.L[l], Lo = d.L[l + 1];
+        const float* gz = gcur;
+        // weights: dw[co][kk] = sum_{b,q} gz[b][co][q] X(b, kk, q)
+        sgemm(1, d.C, Ci * 5, B * Lo, 32, GRowsBQ{gz, bs, Lo}, ConvXT{act + d.act_off[l], bs, Lin, Lo},
+              AtomicAdd2D{grads + d.off_w[l], Ci * 5}, st);
+        bias_grad_kernel<<<d.C, 256, 0, st>>>(B, d.C, Lo, gz, bs, grads + d.off_b[l]);
+        if (l > 0) {
+            // data: dx[b][ci][i], masked by the ReLU of layer l-1's output
+            sgemm(B, Ci, Lin, d.C * 5, 1, WT{params + d.off_w[l], Ci}, GatherG{gz, bs, Lin, Lo},
+                  StoreMasked{gnext, act + d.act_off[l], bs, Lin, 1}, st);
+            float* t = gcur;
+            gcur = gnext;
+            gnext = t;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+int nn_adam_step(size_t count, float* params, const float* grads, float* m, float* v, int t, float lr, float b1,
+                 float b2, float eps, void* stream) {
+    if (count == 0 || !params || !grads || !m || !v || t < 1 || !(lr > 0.f)) return SCH_ERR_ARG;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<grid_elems(count), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(count, params, grads, m, v,
+                                                                                         lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -116,6 +116,7 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
     const double rest = 1.0 - theta;
     double s1;
     double ess = ess_eval(rest, phi, cnt, phimin, sh, parity, s1);
+    const double ess_rest = ess;
     double d;
     if (ess >= ess_min) {
         d = rest;
@@ -139,7 +140,7 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
         out[0] = d;
         out[1] = ess;
         out[2] = (d >= 1.0 - theta) ? 1.0 : theta + d;
-        out[3] = (ess == ess) ? 0.0 : 1.0;
+        out[3] = ess_rest;
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }

@@ -32,6 +32,7 @@ class CycleStats:
     forward_steps: int = 0      # particle-timesteps propagated in the cycle (incl. PCN re-runs)
     launches: int = 0           # library kernels launched by the cycle
     accepts: Optional[torch.Tensor] = None
+    ess0: Optional[float] = None  # ESS of the untempered (Girsanov-corrected) forecast weights
 
 
 class KernelTimer:
@@ -78,6 +79,17 @@ class EnsembleFilter:
     def set_state(self, m_start: torch.Tensor) -> None:
         self.m_start.copy_(m_start)
 
+    def set_drift(self, lam: Optional[torch.Tensor]) -> None:
+        """Nudging drift of the coming window (None: no nudging)."""
+        if lam is None:
+            self.lam = None
+            self._b.pop("lam", None)
+            return
+        if self.lam is None or self.lam.shape != lam.shape:
+            self.lam = torch.empty_like(lam)
+            self._b["lam"] = torch.empty_like(lam)
+        self.lam.copy_(lam)
+
     def _resample(self, stage_ctr: int) -> None:
         pf_resample(self.wbar, self.seed, stage_ctr, idx=self.idx)
         names = ["m_start", "m_end", "u_end", "dW", "nll", "logG"] + (["lam"] if self.lam is not None else [])
@@ -89,14 +101,20 @@ class EnsembleFilter:
             self._b[name] = cur
 
     def cycle(self, y: torch.Tensor, cycle: int, max_stages: int = 64,
-              timer: Optional[KernelTimer] = None) -> CycleStats:
+              timer: Optional[KernelTimer] = None, dW: Optional[torch.Tensor] = None) -> CycleStats:
+        """One assimilation cycle.  ``dW`` (optional) supplies the window increments
+        (e.g. the ones revealed by pf_nudge); otherwise they are drawn from the prior."""
         m = self.model
         st = CycleStats()
-        m.draw_increments(self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, out=self.dW)
+        if dW is None:
+            m.draw_increments(self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, out=self.dW)
+        else:
+            self.dW.copy_(dW)
         m.ensemble_step(self.m_start, self.dW, self.lam, y, m_out=self.m_end, u_out=self.u_end,
                         nll=self.nll, logG=self.logG, status=self.status, want_iters=False)
         st.forward_steps += self.N * self.Ns
         st.launches += 2
+        st.ess0 = None
         theta, k = 0.0, 0
         while theta < 1.0 and k < max_stages:
             pf_temper(self.nll, self.logG, theta, self.ess_min, wbar=self.wbar, out=self.tout)
@@ -122,6 +140,8 @@ class EnsembleFilter:
             st.forward_steps += self.N * self.Ns * self.n_jitter
             st.launches += 2 + len(self._b) + 1
             st.stages.append(StageStats(d, e, theta))
+            if k == 0:
+                st.ess0 = float(self.tout_host[3])
             k += 1
         st.accepts = self.accepts
         return st

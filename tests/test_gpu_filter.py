@@ -39,6 +39,9 @@ def test_temper_matches_oracle(N, spread, theta):
     # the new temperature follows from the kernel's own dtheta by the stated rule
     exp_theta = 1.0 if out[0] >= 1.0 - theta else theta + out[0]
     assert out[2] == exp_theta
+    # out[3]: ESS of the whole remaining step
+    e_rest = OF.ess(-(1.0 - theta) * (nll - lg))
+    assert abs(out[3] - e_rest) <= 1e-12 * e_rest
 
 
 @pytest.mark.parametrize("N", [1, 2, 5, 100, 1024, 8192])
