@@ -344,6 +344,47 @@ def run_ours(args):
     return 0
 
 
+def run_nudging(args):
+    """--nudging: learned vs optimiser nudging on the learned-proposal workload.
+
+    n = 1024, K = 16 modes, 20-step windows, N = 1024, M = 64, sigma = 0.05,
+    FP32 fields.  Training pairs: pf_nudge (open loop, L-BFGS to max|grad| <=
+    1e-6) on `--train-cycles` cycles of a twin experiment x 1024 particles;
+    the network is trained with its own GPU kernels; then the same evaluation
+    twin is assimilated `--steps` cycles with learned, optimiser and no
+    nudging (tempering + 10 jitter steps each).
+    """
+    import torch
+    from workloads import get_config, u0_profile
+    from paper_2402_06927_gb300.api import ProposalNet, SchModel
+    from paper_2402_06927_gb300 import proposal as PR
+
+    torch.cuda.set_device(0)
+    cfg = get_config("cfg4_f32")
+    g = SchModel.from_config(cfg)
+    u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
+    U, Y, T, gst = PR.generate_pairs(g, cfg.N, cfg.Ns, args.train_cycles, 7, u0, cfg.ess_min, cfg.rho,
+                                     cfg.n_jitter, cfg.prior_scale, max_iter=60, gtol=1e-6)
+    net = ProposalNet(cfg.n, cfg.K, cfg.Ns, cfg.M, cfg.sigma, C=64, seed=1)
+    tst = PR.train(net, U, Y, T, epochs=args.epochs, batch=256, lr=1e-3)
+    twin = PR.make_twin(g, cfg.Ns, args.steps, 99, u0)
+    res = {}
+    for src in ("none", "learned", "optimiser"):
+        res[src] = PR.run_nudged(g, src, net, cfg.N, cfg.Ns, args.steps, 99, u0, cfg.ess_min, cfg.rho,
+                                 cfg.n_jitter, cfg.prior_scale, twin, max_iter=60, gtol=1e-6)
+    line = {
+        "metric": "assim. cycles/s (learned nudging)", "value": res["learned"]["cycles_per_s"], "unit": "cycles/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "SCH twin experiment n=1024 K=16 Ns=20 N=1024 M=64 sigma=0.05, learned vs "
+                               "optimiser nudging + tempering + 10 jitter steps",
+                   "train_pairs": int(U.shape[0]), "generation": gst, "training": tst},
+        "comparison": res,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -351,7 +392,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--nudging", action="store_true",
+                    help="learned vs optimiser nudging comparison instead of the default workload")
+    ap.add_argument("--train-cycles", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=10)
     args = ap.parse_args()
+    if args.nudging:
+        if args.steps == 100:
+            args.steps = 20
+        return run_nudging(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

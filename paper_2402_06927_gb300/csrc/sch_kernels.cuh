@@ -192,50 +192,72 @@ __device__ __forceinline__ R pcr32_const(R D, const RTab<R>& Q) {
     return Q.f1 * D + Q.f2 * Dj;
 }
 
-// Warp 0: interface values of a tabulated constant matrix from the chunk rows
-// pd[t], de[t]: reduced rows D_t = de_t - ae pd_t - ge pd_{t+1} (A, B, C fixed),
-// lane sweeps and 32-lane PCR with host coefficients, then E[t] and
-// F[t] = pd_t - pa E_{t-1} - pc E_t.
+// Warp 0, registers only: interface values of a tabulated constant matrix.
+// Lane l holds the reduced-row inputs pd, de of rows t = l RR + r (RR = TP/32)
+// and gets back E_t and F_t = pd_t - pa E_{t-1} - pc E_t.  Rows read
+// D_t = de_t - ae pd_t - ge pd_{t+1} (A, B, C fixed); the next row's pd and the
+// previous row's E cross lanes by shuffle.
 template <typename R, int TP>
-__device__ __forceinline__ void warp_solve_const(const CTab<R>& T, const RTab<R>& Q, const R* pd, const R* de,
-                                                 R* E, R* F) {
+__device__ __forceinline__ void lane_solve_const(const CTab<R>& T, const RTab<R>& Q, const R (&pd)[TP / 32],
+                                                 const R (&de)[TP / 32], R (&E)[TP / 32], R (&F)[TP / 32]) {
     constexpr int RR = TP / 32;
     const int lane = threadIdx.x & 31;
-    const int t0 = lane * RR;
+    const R pd_next = __shfl_sync(FULL, pd[0], (lane + 1) & 31);
+    R D[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        const R pn = (r == RR - 1) ? pd_next : pd[(r + 1) % RR];
+        D[r] = de[r] - T.ae * pd[r] - T.ge * pn;
+    }
     if constexpr (RR == 1) {
-        const R D = de[t0] - T.ae * pd[t0] - T.ge * pd[(t0 + 1) & (TP - 1)];
-        E[t0] = pcr32_const(D, Q);
+        E[0] = pcr32_const(D[0], Q);
     } else {
         R dl[RR];
-        const R D0 = de[t0] - T.ae * pd[t0] - T.ge * pd[t0 + 1];
         dl[0] = R(0);
 #pragma unroll
-        for (int r = 1; r < RR; ++r) {
-            const int t = t0 + r;
-            const R D = de[t] - T.ae * pd[t] - T.ge * pd[(t + 1) & (TP - 1)];
-            dl[r] = (D - Q.A * dl[r - 1]) * Q.q[r];
-        }
+        for (int r = 1; r < RR; ++r) dl[r] = (D[r] - Q.A * dl[r - 1]) * Q.q[r];
         R dp[RR];
         dp[RR - 1] = R(0);
+        dp[0] = R(0);
 #pragma unroll
         for (int r = RR - 2; r >= 1; --r) dp[r] = dl[r] - Q.ga[r] * dp[r + 1];
-        const R DF = (RR == 2) ? D0 : D0 - Q.Cc * dp[1];
+        const R DF = (RR == 2) ? D[0] : D[0] - Q.Cc * dp[1];
         const R qd = DF * Q.iBF;
         const R nqd = __shfl_sync(FULL, qd, (lane + 1) & 31);
         const R LD = dl[RR - 1] - Q.aeL * qd - Q.geL * nqd;
         const R EL = pcr32_const(LD, Q);
         const R Ep = __shfl_sync(FULL, EL, (lane + 31) & 31);
         const R Ff = qd - Q.qa * Ep - Q.qc * EL;
-        E[t0] = Ff;
+        E[0] = Ff;
 #pragma unroll
-        for (int r = 1; r < RR - 1; ++r) E[t0 + r] = dp[r] - Q.alp[r] * Ff - Q.gap[r] * EL;
-        E[t0 + RR - 1] = EL;
+        for (int r = 1; r < RR - 1; ++r) E[r] = dp[r] - Q.alp[r] * Ff - Q.gap[r] * EL;
+        E[RR - 1] = EL;
     }
-    __syncwarp();
+    const R Eprev = __shfl_sync(FULL, E[RR - 1], (lane + 31) & 31);
 #pragma unroll
     for (int r = 0; r < RR; ++r) {
-        const int t = t0 + r;
-        F[t] = pd[t] - T.pa * E[(t - 1) & (TP - 1)] - T.pc * E[t];
+        const R em1 = (r == 0) ? Eprev : E[(r + RR - 1) % RR];
+        F[r] = pd[r] - T.pa * em1 - T.pc * E[r];
+    }
+}
+
+// Warp 0: the same from shared-memory rows pd[t], de[t] into E[t], F[t].
+template <typename R, int TP>
+__device__ __forceinline__ void warp_solve_const(const CTab<R>& T, const RTab<R>& Q, const R* pd, const R* de,
+                                                 R* E, R* F) {
+    constexpr int RR = TP / 32;
+    const int t0 = (threadIdx.x & 31) * RR;
+    R p[RR], d[RR], e[RR], f[RR];
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        p[r] = pd[t0 + r];
+        d[r] = de[t0 + r];
+    }
+    lane_solve_const<R, TP>(T, Q, p, d, e, f);
+#pragma unroll
+    for (int r = 0; r < RR; ++r) {
+        E[t0 + r] = e[r];
+        F[t0 + r] = f[r];
     }
     __syncwarp();
 }
@@ -610,17 +632,36 @@ __device__ __forceinline__ void sch_step_ea(const ModelArgs<R>& A, Shm<R, TP>* s
                 else if (it > A.max_iter) fl = FLAG_STOP | FLAG_NOCONV;
             }
             if (!(fl & FLAG_STOP)) {
-                warp_solve_const<R, TP>(A.pic, A.rpic, sh->pd, sh->de, sh->E, sh->F);
+                R pdr[RR], der[RR], hpr[RR], hdr[RR], Er[RR], Fr[RR];
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     const int q = t * RR + r;
-                    const R Fq = sh->F[q], Eq = sh->E[q];
-                    const R Eqp = sh->E[(q - 1) & (TP - 1)], Fqn = sh->F[(q + 1) & (TP - 1)];
-                    sh->hpd[q] += A.hb.cpF * Fq + A.hb.cpE * Eq + A.hb.cpEp * Eqp + A.hb.cpFn * Fqn;
-                    sh->hde[q] += A.hb.cdF * Fq + A.hb.cdE * Eq + A.hb.cdEp * Eqp + A.hb.cdFn * Fqn;
+                    pdr[r] = sh->pd[q];
+                    der[r] = sh->de[q];
+                    hpr[r] = sh->hpd[q];
+                    hdr[r] = sh->hde[q];
                 }
-                __syncwarp();
-                warp_solve_const<R, TP>(A.hel, A.rhel, sh->hpd, sh->hde, sh->hE, sh->hF);
+                lane_solve_const<R, TP>(A.pic, A.rpic, pdr, der, Er, Fr);
+                // Helmholtz rows from the Picard interface values
+                const R Ep = __shfl_sync(FULL, Er[RR - 1], (t + 31) & 31);
+                const R Fn = __shfl_sync(FULL, Fr[0], (t + 1) & 31);
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const R em1 = (r == 0) ? Ep : Er[(r + RR - 1) % RR];
+                    const R fp1 = (r == RR - 1) ? Fn : Fr[(r + 1) % RR];
+                    hpr[r] += A.hb.cpF * Fr[r] + A.hb.cpE * Er[r] + A.hb.cpEp * em1 + A.hb.cpFn * fp1;
+                    hdr[r] += A.hb.cdF * Fr[r] + A.hb.cdE * Er[r] + A.hb.cdEp * em1 + A.hb.cdFn * fp1;
+                }
+                R hEr[RR], hFr[RR];
+                lane_solve_const<R, TP>(A.hel, A.rhel, hpr, hdr, hEr, hFr);
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int q = t * RR + r;
+                    sh->E[q] = Er[r];
+                    sh->F[q] = Fr[r];
+                    sh->hE[q] = hEr[r];
+                    sh->hF[q] = hFr[r];
+                }
             }
             if (t == 0) sh->flag = fl;
         }
