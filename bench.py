@@ -351,8 +351,9 @@ def run_nudging(args):
     FP32 fields.  Training pairs: pf_nudge (open loop, L-BFGS to max|grad| <=
     1e-6) on `--train-cycles` cycles of a twin experiment x 1024 particles;
     the network is trained with its own GPU kernels; then the same evaluation
-    twin is assimilated `--steps` cycles with learned, optimiser and no
-    nudging (tempering + 10 jitter steps each).
+    twin is assimilated `--steps` cycles with learned, hybrid (the network's
+    drift refined by one L-BFGS iteration), optimiser and no nudging
+    (tempering + 10 jitter steps each).
     """
     import torch
     from workloads import get_config, u0_profile
@@ -369,9 +370,9 @@ def run_nudging(args):
     tst = PR.train(net, U, Y, T, epochs=args.epochs, batch=256, lr=1e-3)
     twin = PR.make_twin(g, cfg.Ns, args.steps, 99, u0)
     res = {}
-    for src in ("none", "learned", "optimiser"):
+    for src in ("none", "learned", "hybrid", "optimiser"):
         res[src] = PR.run_nudged(g, src, net, cfg.N, cfg.Ns, args.steps, 99, u0, cfg.ess_min, cfg.rho,
-                                 cfg.n_jitter, cfg.prior_scale, twin, max_iter=60, gtol=1e-6)
+                                 cfg.n_jitter, cfg.prior_scale, twin, max_iter=60, gtol=1e-6, refine=1)
     line = {
         "metric": "assim. cycles/s (learned nudging)", "value": res["learned"]["cycles_per_s"], "unit": "cycles/s",
         "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": True, "dtype": "f32",

@@ -99,8 +99,13 @@ def train(net: ProposalNet, U, Y, T, epochs: int = 20, batch: int = 256, lr: flo
 
 def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycles: int, seed: int,
                u0: torch.Tensor, ess_min: float, rho: float, n_jitter: int, prior_scale: float,
-               twin: Twin, max_iter: int = 30, gtol: float = 1e-4):
-    """Cycles of a nudged tempering + jittering filter; source is 'learned', 'optimiser' or 'none'."""
+               twin: Twin, max_iter: int = 30, gtol: float = 1e-4, refine: int = 1):
+    """Cycles of a nudged tempering + jittering filter.
+
+    source: 'learned' (network drift), 'optimiser' (pf_nudge from zero),
+    'hybrid' (pf_nudge started from the network's drift, `refine` L-BFGS
+    iterations) or 'none'.
+    """
     f = EnsembleFilter(g, N, Ns, ess_min, rho, n_jitter, seed)
     m0, _ = g.prior_sample(N, u0, seed, prior_scale)
     f.set_state(m0)
@@ -117,9 +122,12 @@ def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycl
             lam = net.forward(u_start, y)
             f.set_drift(lam.to(g.dtype))
             dW = g.draw_increments(N, Ns, seed, _lib.TAG_NUDGE, 1_000_000 + c)
-        elif source == "optimiser":
-            nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter, gtol=gtol, ckpt=5, seed=seed,
-                         ctr=1_000_000 + c)
+        elif source in ("optimiser", "hybrid"):
+            lam0 = None
+            if source == "hybrid":
+                lam0 = net.forward(g.u_from_m(f.m_start), y).to(g.dtype)
+            nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter if source == "optimiser" else refine,
+                         gtol=gtol, ckpt=5, seed=seed, ctr=1_000_000 + c, lam0=lam0)
             f.set_drift(nd["lam"])
             dW = nd["dW"]
         else:
