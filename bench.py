@@ -48,6 +48,28 @@ def step_flops(n, K, solver, iters, steps):
     return n * (FLOPS_PER_NODE_ITER[solver] * iters + (2 * K + FLOPS_PER_NODE_STEP_EXTRA[solver]) * steps)
 
 
+# DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# per launch) from one ncu capture of the bench workload (profiles/
+# jitter_kernel_cfg2_n1024_N1024.md).  It describes only the kernel sources it was
+# taken on: when those change, the bench reports null until it is re-measured.
+JITTER_TRAFFIC_BYTES = 4602880 + 372224
+JITTER_SOURCES = ["paper_2402_06927_gb300/csrc/sch_kernels.cuh", "paper_2402_06927_gb300/csrc/sch_internal.h",
+                  "paper_2402_06927_gb300/csrc/sch_device.cuh", "paper_2402_06927_gb300/csrc/sch_window_f32.cu"]
+JITTER_SOURCES_SHA1 = "938d11038f996d6fbf153de2a02df5f243d412ce"
+
+
+def jitter_traffic():
+    import hashlib
+    h = hashlib.sha1()
+    try:
+        for f in JITTER_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(hashlib.sha1(fh.read()).digest())
+    except OSError:
+        return None
+    return JITTER_TRAFFIC_BYTES if h.hexdigest() == JITTER_SOURCES_SHA1 else None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -275,6 +297,10 @@ def run_ours(args):
     solver = "ea" if cfg.dtype == "f32" else "li"
     flops = step_flops(cfg.n, cfg.K, solver, it_sum, N * cfg.Ns * cfg.n_jitter * n_launch)
     jit_s = sum(jit_ms) / 1000.0
+    # bytes a jitter launch must move: read m_start and dW, write dW, nll, logG and the
+    # accepted end states (m_end, u_end); lower bound assumes the end states of each
+    # particle are written once
+    algo_bytes = N * (cfg.n * 4 + 2 * cfg.Ns * cfg.K * 4 + 2 * 8 + 2 * cfg.n * 4)
     achieved = flops / jit_s / 1e12
     peak = fp32_peak_tflops()
     mean_iters = it_sum / (N * cfg.Ns * cfg.n_jitter * n_launch)
@@ -329,7 +355,8 @@ def run_ours(args):
                        "analysis_emre_rb_res_rmse": diag},
             "roofline": {"bound": "alu", "kernel": f"jitter_kernel<float,8,128,{solver.upper()}>",
                          "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": jitter_traffic(),
+                         "algorithmic_bytes_per_launch": algo_bytes,
                          "peak_note": "FP32 FMA pipe 152 SMs x 128 lanes x 2 x max SM clock"},
             "gpu_launches": launches,
             "e2e": {"value": e2e_val, "unit": METRIC, "h2d_bytes_per_step": cfg.M * 4,
