@@ -49,13 +49,13 @@ def step_flops(n, K, solver, iters, steps):
 
 
 # DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
-# per launch) from one ncu capture of the bench workload (profiles/
-# jitter_kernel_cfg2_n1024_N1024.md).  It describes only the kernel sources it was
-# taken on: when those change, the bench reports null until it is re-measured.
-JITTER_TRAFFIC_BYTES = 4602880 + 372224
-JITTER_SOURCES = ["paper_2402_06927_gb300/csrc/sch_kernels.cuh", "paper_2402_06927_gb300/csrc/sch_internal.h",
-                  "paper_2402_06927_gb300/csrc/sch_device.cuh", "paper_2402_06927_gb300/csrc/sch_window_f32.cu"]
-JITTER_SOURCES_SHA1 = "938d11038f996d6fbf153de2a02df5f243d412ce"
+# per launch) from one ncu capture of the bench workload, keyed by the sha1 of the
+# kernel's sources: a capture describes only the sources it was taken on, so the
+# bench reports null once they change, until the kernel is captured again.
+JITTER_SOURCES = ["paper_2402_06927_gb300/csrc/sch_warp.cuh", "paper_2402_06927_gb300/csrc/sch_kernels.cuh",
+                  "paper_2402_06927_gb300/csrc/sch_internal.h", "paper_2402_06927_gb300/csrc/sch_device.cuh",
+                  "paper_2402_06927_gb300/csrc/sch_window_warp.cu"]
+JITTER_TRAFFIC_BYTES = {}
 
 
 def jitter_traffic():
@@ -67,7 +67,7 @@ def jitter_traffic():
                 h.update(hashlib.sha1(fh.read()).digest())
     except OSError:
         return None
-    return JITTER_TRAFFIC_BYTES if h.hexdigest() == JITTER_SOURCES_SHA1 else None
+    return JITTER_TRAFFIC_BYTES.get(h.hexdigest())
 
 
 def _peaks():
@@ -353,7 +353,8 @@ def run_ours(args):
                        "mean_tempering_stages": statistics.mean(stages),
                        "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
-            "roofline": {"bound": "alu", "kernel": f"jitter_kernel<float,8,128,{solver.upper()}>",
+            "roofline": {"bound": "alu", "kernel": ("wjitter_kernel<16> (one warp per particle, EA)" if g.layout == "warp"
+                                    else f"jitter_kernel<float,8,128,{solver.upper()}>"),
                          "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": jitter_traffic(),
                          "algorithmic_bytes_per_launch": algo_bytes,

@@ -67,6 +67,15 @@ enum { SCH_F64 = 0, SCH_F32 = 1 };
  *   SCH_SOLVER_AUTO  EA for SCH_F32, LI for SCH_F64. */
 enum { SCH_SOLVER_AUTO = 0, SCH_SOLVER_LI = 1, SCH_SOLVER_EA = 2 };
 
+/* Kernel layout of sch_ensemble_step and pf_jitter:
+ *   SCH_LAYOUT_CTA   one CTA of n/8 (float) or n/4 (double) threads per particle;
+ *   SCH_LAYOUT_WARP  one warp per particle, packed f32x2 arithmetic: float
+ *                    fields, the SCH_SOLVER_EA solver and n = 256, 512 or 1024
+ *                    only (sch_create returns SCH_ERR_UNSUPPORTED otherwise);
+ *   SCH_LAYOUT_AUTO  WARP where it applies, else CTA.
+ * Both compute the same iteration; results agree to rounding. */
+enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
+
 enum {
     SCH_TAG_PRIOR_DW = 1, SCH_TAG_PCN = 2, SCH_TAG_PCN_ACCEPT = 3, SCH_TAG_RESAMPLE = 4,
     SCH_TAG_TRUTH = 5, SCH_TAG_OBS = 6, SCH_TAG_INIT = 7, SCH_TAG_NUDGE = 8
@@ -90,6 +99,7 @@ typedef struct {
     int32_t max_iter;    /* Picard iteration limit per step */
     int32_t dtype;       /* SCH_F64 or SCH_F32: precision of fields, dW, lambda */
     int32_t solver;      /* SCH_SOLVER_* */
+    int32_t layout;      /* SCH_LAYOUT_* */
 } sch_params;
 
 typedef struct sch_ctx sch_ctx;
@@ -99,6 +109,11 @@ typedef struct sch_ctx sch_ctx;
  * Returns SCH_ERR_ARG / SCH_ERR_UNSUPPORTED for invalid or uncompiled sizes. */
 int sch_create(const sch_params* params, sch_ctx** ctx);
 int sch_destroy(sch_ctx* ctx);
+
+/* The kernel layout a context runs sch_ensemble_step and pf_jitter with:
+ * SCH_LAYOUT_CTA or SCH_LAYOUT_WARP (SCH_LAYOUT_AUTO resolved); SCH_ERR_ARG
+ * for a NULL context.  Host only. */
+int sch_layout(const sch_ctx* ctx);
 
 /* Workspace bytes pf_resample needs to gather `row_bytes_total` bytes per
  * particle in place for N particles. */

@@ -34,7 +34,7 @@ class SchParams(ct.Structure):
         ("L", ct.c_double), ("n", ct.c_int32), ("alpha", ct.c_double), ("mu", ct.c_double),
         ("dt", ct.c_double), ("K", ct.c_int32), ("amps", ct.c_double * (SCH_MAX_K // 2)),
         ("M", ct.c_int32), ("sigma", ct.c_double), ("tol", ct.c_double), ("max_iter", ct.c_int32),
-        ("dtype", ct.c_int32), ("solver", ct.c_int32),
+        ("dtype", ct.c_int32), ("solver", ct.c_int32), ("layout", ct.c_int32),
     ]
 
 
@@ -54,6 +54,7 @@ DP = ct.POINTER(ct.c_double)
 SIGNATURES = {
     "sch_create": [ct.POINTER(SchParams), ct.POINTER(P)],
     "sch_destroy": [P],
+    "sch_layout": [P],
     "sch_u_from_m": [P, I, P, P, P],
     "sch_m_from_u": [P, I, P, P, P],
     "sch_draw_increments": [P, I, I, U64, U64, U64, I, P, P],

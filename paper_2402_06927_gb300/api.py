@@ -39,7 +39,8 @@ class SchModel:
     """A library context for one set of model and observation parameters."""
 
     def __init__(self, L: float, n: int, alpha: float, mu: float, dt: float, amps: Sequence[float],
-                 M: int, sigma: float, tol: float, max_iter: int, dtype: str = "f32", solver: str = "auto"):
+                 M: int, sigma: float, tol: float, max_iter: int, dtype: str = "f32", solver: str = "auto",
+                 layout: str = "auto"):
         p = SchParams()
         p.L, p.n, p.alpha, p.mu, p.dt = L, n, alpha, mu, dt
         p.K = 2 * len(amps)
@@ -48,12 +49,15 @@ class SchModel:
         p.M, p.sigma, p.tol, p.max_iter = M, sigma, tol, max_iter
         p.dtype = SCH_F32 if dtype == "f32" else SCH_F64
         p.solver = {"auto": 0, "li": 1, "ea": 2}[solver]
+        p.layout = {"auto": 0, "cta": 1, "warp": 2}[layout]
         self.params = p
         self.n, self.K, self.M, self.dt = n, p.K, M, dt
         self.dtype = torch.float32 if dtype == "f32" else torch.float64
         h = ct.c_void_p()
         check(lib().sch_create(ct.byref(p), ct.byref(h)), "sch_create")
         self._h = h
+        # the kernel layout the library chose: "warp" (one warp per particle) or "cta"
+        self.layout = {1: "cta", 2: "warp"}[lib().sch_layout(h)]
 
     @classmethod
     def from_config(cls, cfg, **over):

@@ -12,16 +12,27 @@ using namespace sch;
 struct sch_ctx {
     sch_params p;
     int C, tp;
+    int wcs;          // sub-chunk length of the warp-per-particle kernels, 0 = CTA kernels
+    WArgs wa;
     ModelArgs<float> af;
     ModelArgs<double> ad;
 };
 
 namespace {
 
+// Chunk-partition coefficients of a constant symmetric tridiagonal matrix for
+// chunks of up to HMAX rows, in double precision (the kernels' CTab and WTab
+// are casts of it).
+constexpr int HMAX = 32;
+struct HTab {
+    double rden[HMAX], gam[HMAX], alpp[HMAX], gamp[HMAX];
+    double a, iBF, pa, pc, ae, ge;
+};
+
 // Chunk-partition coefficients of the symmetric circulant tridiagonal matrix
 // with off-diagonal a and diagonal b, for chunks of C rows (double precision).
-void ctab_host(double a, double b, int C, CTab<double>& T) {
-    double al[8], ga[8];
+void ctab_host(double a, double b, int C, HTab& T) {
+    double al[HMAX], ga[HMAX];
     memset(&T, 0, sizeof(T));
     al[0] = -1.0;
     ga[0] = 0.0;
@@ -53,7 +64,7 @@ void ctab_host(double a, double b, int C, CTab<double>& T) {
 
 // Reduced cyclic system of chunk table T for TP threads: lane-level sweep over
 // RR = TP/32 rows and the 32-lane PCR coefficients (double precision).
-void rtab_host(const CTab<double>& T, int TP, RTab<double>& Q) {
+void rtab_host(const HTab& T, int TP, RTab<double>& Q) {
     memset(&Q, 0, sizeof(Q));
     const double A = -T.ae * T.pa, B = 1.0 - T.ae * T.pc - T.ge * T.pa, Cc = -T.ge * T.pc;
     Q.A = A;
@@ -109,7 +120,7 @@ void rtab_host(const CTab<double>& T, int TP, RTab<double>& Q) {
 
 // chunk sweep of table T on a right-hand side r: the reduced "first" row value
 // pd, the "last" row value de and the interior particular solution dp
-void chunk_sweep(const CTab<double>& T, int C, const double* r, double& pd, double& de, double* dp) {
+void chunk_sweep(const HTab& T, int C, const double* r, double& pd, double& de, double* dp) {
     double d[8];
     d[0] = 0.0;
     for (int i = 1; i < C; ++i) d[i] = (r[i] - T.a * d[i - 1]) * T.rden[i];
@@ -121,7 +132,7 @@ void chunk_sweep(const CTab<double>& T, int C, const double* r, double& pd, doub
 }
 
 // the Helmholtz interface rows as linear functionals of the Picard chunk solution
-void hbasis_host(const CTab<double>& P, const CTab<double>& H, int C, double h6, HBasis<double>& B) {
+void hbasis_host(const HTab& P, const HTab& H, int C, double h6, HBasis<double>& B) {
     memset(&B, 0, sizeof(B));
     double wpd[8], wde[8], dp[8], r[8];
     for (int j = 0; j < C; ++j) {
@@ -200,7 +211,7 @@ void cast_hb(const HBasis<double>& s, HBasis<R>& d) {
 }
 
 template <typename R>
-void cast_tab(const CTab<double>& s, CTab<R>& d) {
+void cast_tab(const HTab& s, CTab<R>& d) {
     for (int i = 0; i < 8; ++i) {
         d.rden[i] = (R)s.rden[i];
         d.gam[i] = (R)s.gam[i];
@@ -246,7 +257,7 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
         A.rot_s[j] = (R)sin(2.0 * M_PI * (j + 1) / p.n);
     }
     const int TP = p.n / C;
-    CTab<double> th, tm, ts, tpic;
+    HTab th, tm, ts, tpic;
     RTab<double> q;
     ctab_host(h / 6.0 - a2 / h, 2.0 * h / 3.0 + 2.0 * a2 / h, C, th);
     ctab_host(h / 6.0, 2.0 * h / 3.0, C, tm);
@@ -267,6 +278,42 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
     HBasis<double> hb;
     hbasis_host(tpic, th, C, h / 6.0, hb);
     cast_hb(hb, A.hb);
+}
+
+// the warp-per-particle tables: sub-chunks of CS nodes, 64-row reduced systems
+void wtab_cast(const HTab& s, int CS, WTab& d) {
+    memset(&d, 0, sizeof(d));
+    auto pr = [](double v) { return make_float2((float)v, (float)v); };
+    for (int i = 0; i < CS; ++i) {
+        d.rden[i] = pr(s.rden[i]);
+        d.nar[i] = pr(-s.a * s.rden[i]);
+        d.ngam[i] = pr(-s.gam[i]);
+        d.nalpp[i] = pr(-s.alpp[i]);
+        d.ngamp[i] = pr(-s.gamp[i]);
+    }
+    d.na = pr(-s.a);
+    d.iBF = pr(s.iBF);
+    d.pa = (float)s.pa;
+    d.pc = (float)s.pc;
+    d.ae = (float)s.ae;
+    d.ge = (float)s.ge;
+}
+
+void fill_wargs(const sch_params& p, int CS, WArgs& W) {
+    memset(&W, 0, sizeof(W));
+    const double h = p.L / p.n;
+    const double a2 = p.alpha * p.alpha;
+    HTab tp, th;
+    RTab<double> q;
+    ctab_host(h / 6.0 - p.mu * p.dt / (2.0 * h), 2.0 * h / 3.0 + p.mu * p.dt / h, CS, tp);
+    // the Helmholtz matrix scaled by 6/h: its right-hand side is m_{i-1} + 4 m_i + m_{i+1}
+    ctab_host((h / 6.0 - a2 / h) * 6.0 / h, (2.0 * h / 3.0 + 2.0 * a2 / h) * 6.0 / h, CS, th);
+    wtab_cast(tp, CS, W.pic);
+    wtab_cast(th, CS, W.hel);
+    rtab_host(tp, 64, q);
+    cast_rtab(q, W.rpic);
+    rtab_host(th, 64, q);
+    cast_rtab(q, W.rhel);
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -290,6 +337,11 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     if (p.n % C != 0) return SCH_ERR_UNSUPPORTED;
     const int tp = p.n / C;
     if (!pow2(tp) || tp < 32 || tp > 512) return SCH_ERR_UNSUPPORTED;
+    if (p.layout < SCH_LAYOUT_AUTO || p.layout > SCH_LAYOUT_WARP) return SCH_ERR_ARG;
+    const int solver = (p.solver != SCH_SOLVER_AUTO) ? p.solver : (p.dtype == SCH_F32 ? SCH_SOLVER_EA : SCH_SOLVER_LI);
+    const bool warp_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && (p.n == 256 || p.n == 512 || p.n == 1024);
+    if (p.layout == SCH_LAYOUT_WARP && !warp_fits) return SCH_ERR_UNSUPPORTED;
+    const bool warp_ok = warp_fits && p.layout != SCH_LAYOUT_CTA;
     sch_ctx* c = (sch_ctx*)calloc(1, sizeof(sch_ctx));
     if (!c) return SCH_ERR_ARG;
     c->p = p;
@@ -297,6 +349,10 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     c->tp = tp;
     fill_args(p, C, c->af);
     fill_args(p, C, c->ad);
+    if (warp_ok) {
+        c->wcs = p.n / 64;
+        fill_wargs(p, c->wcs, c->wa);
+    }
     *ctx = c;
     return SCH_OK;
 }
@@ -304,6 +360,11 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
 int sch_destroy(sch_ctx* ctx) {
     free(ctx);
     return SCH_OK;
+}
+
+int sch_layout(const sch_ctx* ctx) {
+    if (!ctx) return SCH_ERR_ARG;
+    return ctx->wcs ? SCH_LAYOUT_WARP : SCH_LAYOUT_CTA;
 }
 
 size_t pf_resample_workspace_bytes(int N, size_t row_bytes_total) {
@@ -346,12 +407,14 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
     if (!m || !m_out || !u_out || (nsteps > 0 && !dW)) return SCH_ERR_ARG;
     if (y && !nll) return SCH_ERR_ARG;
     if (nsteps > 4096) return SCH_ERR_ARG;
-    const size_t sm = (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
-                                                 : window_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
+    const size_t sm = ctx->wcs ? wwindow_smem(ctx->wcs, nsteps, ctx->p.K)
+                      : (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
+                                                  : window_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
     if (ctx->p.dtype == SCH_F32) {
         WindowIO<float> io{nsteps, (const float*)m, (float*)m_out, (float*)u_out, (const float*)dW,
                            (const float*)lambda, (const float*)y, nll, logG, iters, status};
+        if (ctx->wcs) return launch_wwindow(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_window<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_window<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }
@@ -438,14 +501,16 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
     if (N == 0 || n_iter == 0) return SCH_OK;
     if (!m_start || !dW || !y || !nll || !m_end || !u_end) return SCH_ERR_ARG;
     if (lambda && !logG) return SCH_ERR_ARG;
-    const size_t sm = (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
-                                                 : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
+    const size_t sm = ctx->wcs ? wjitter_smem(ctx->wcs, nsteps, ctx->p.K)
+                      : (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
+                                                  : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
     const double sq = sqrt(1.0 - rho * rho);
     if (ctx->p.dtype == SCH_F32) {
         JitterIO<float> io{nsteps, n_iter, 0, theta, (float)rho, (float)sq, seed, ctr, (const float*)m_start,
                            (float*)dW, (const float*)lambda, (const float*)y, nll, logG, (float*)m_end,
                            (float*)u_end, accepts, iters, status};
+        if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }

@@ -67,6 +67,28 @@ struct ModelArgs {
     HBasis<R> hb;
 };
 
+// Sub-chunk coefficients of a constant symmetric circulant tridiagonal matrix
+// (off-diagonal a) for the warp-per-particle kernels, whose lanes hold two
+// sub-chunks of CS <= WCS_MAX nodes as float pairs: every coefficient is
+// stored as a (c, c) pair so that the packed f32x2 instructions read it
+// straight from the parameter bank.
+constexpr int WCS_MAX = 16;
+
+struct WTab {
+    float2 rden[WCS_MAX];    // 1 / pivot of row i (i >= 1)
+    float2 nar[WCS_MAX];     // -a / pivot of row i
+    float2 ngam[WCS_MAX];    // -gam_i: back-sweep coefficient
+    float2 nalpp[WCS_MAX];   // -alpp_i: weight of the sub-chunk's first value
+    float2 ngamp[WCS_MAX];   // -gamp_i: weight of the sub-chunk's last value
+    float2 na, iBF;          // -a, 1 / pivot of the reduced first row
+    float pa, pc, ae, ge;    // reduced-row coupling coefficients
+};
+
+struct WArgs {
+    WTab pic, hel;           // M + mu dt/2 K ;  (6/h)(M + alpha^2 K)
+    RTab<float> rpic, rhel;  // their 64-row reduced systems (two rows per lane)
+};
+
 template <typename R>
 struct WindowIO {
     int Ns;
@@ -167,6 +189,14 @@ int launch_synth_obs(const ModelArgs<R>& A, const R* u, uint64_t seed, uint64_t 
 template <typename R>
 int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* u_truth, double* ws, double* out,
                 cudaStream_t st);
+
+// warp-per-particle kernels for float fields, n = 64 cs (sch_window_warp.cu)
+int launch_wwindow(int cs, const ModelArgs<float>& A, const WArgs& W, const WindowIO<float>& io, int N,
+                   cudaStream_t st);
+int launch_wjitter(int cs, const ModelArgs<float>& A, const WArgs& W, const JitterIO<float>& io, int N,
+                   cudaStream_t st);
+size_t wwindow_smem(int cs, int Ns, int K);
+size_t wjitter_smem(int cs, int Ns, int K);
 
 // filter kernels (pf_filter.cu)
 int launch_temper(int N, const double* nll, const double* logG, double theta, double ess_min, double* wbar,

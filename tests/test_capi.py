@@ -55,13 +55,21 @@ def _params(**kw):
 
 @pytest.mark.parametrize("kw,rc", [({}, 0), ({"n": 100, "M": 25}, -6), ({"n": 256 * 4}, 0), ({"K": 3}, -1),
                                    ({"K": 66}, -1), ({"M": 33}, -1), ({"sigma": 0.0}, -1), ({"dt": -1.0}, -1),
-                                   ({"dtype": 5}, -1), ({"n": 8192}, -6), ({"max_iter": 0}, -1)])
+                                   ({"dtype": 5}, -1), ({"n": 8192}, -6), ({"max_iter": 0}, -1),
+                                   # kernel layouts: the warp-per-particle layout takes float fields, the
+                                   # explicit-advection solver and n = 256, 512 or 1024 only
+                                   ({"layout": 3}, -1), ({"layout": 2}, -6), ({"layout": 1}, 0),
+                                   ({"layout": 2, "dtype": 1}, 0), ({"layout": 2, "dtype": 1, "n": 1024, "M": 64}, 0),
+                                   ({"layout": 2, "dtype": 1, "solver": 1}, -6),
+                                   ({"layout": 2, "dtype": 1, "n": 2048, "M": 64}, -6)])
 def test_create_validates(lib, kw, rc):
     p = _params(**kw)
     h = ct.c_void_p()
     got = lib.sch_create(ct.byref(p), ct.byref(h))
     assert got == rc
     if got == 0:
+        want = kw.get("layout", 0) or (2 if (p.dtype == 1 and p.solver != 1 and p.n in (256, 512, 1024)) else 1)
+        assert lib.sch_layout(h) == want
         assert lib.sch_destroy(h) == 0
 
 

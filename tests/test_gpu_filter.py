@@ -74,11 +74,11 @@ def test_resample_degenerate_and_inplace():
     assert torch.equal(dst, src.flip(0))
 
 
-@pytest.mark.parametrize("name,theta,lam", [("cfg1_f64", 0.4, False), ("cfg1_f64", 1.0, True),
-                                            ("cfg2_f32", 0.3, False)])
-def test_jitter_matches_oracle(name, theta, lam):
+@pytest.mark.parametrize("name,theta,lam,layout", [("cfg1_f64", 0.4, False, "auto"), ("cfg1_f64", 1.0, True, "auto"),
+                                                   ("cfg2_f32", 0.3, False, "warp"), ("cfg2_f32", 0.3, True, "cta")])
+def test_jitter_matches_oracle(name, theta, lam, layout):
     cfg = get_config(name)
-    g = gpu_model(cfg)
+    g = gpu_model(cfg, layout=layout)
     om = oracle_model(cfg)
     N = 8 if cfg.dtype == "f64" else 3
     u0 = random_state(cfg, N, 50)

@@ -6,6 +6,7 @@ Tolerances (max-norm, relative to the oracle's max-norm):
 * FP32 fields after one window: 1e-4 (single-precision rounding over
   Ns implicit solves with tolerance 1e-6).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -109,10 +110,16 @@ def test_window_f64_multiwarp():
     assert rel_err(out["u"].cpu().numpy(), ref[1]) < F64_TOL
 
 
-@pytest.mark.parametrize("name,N", [("cfg2_f32", 3), ("cfg5_f32", 2)])
-def test_window_f32(name, N):
-    cfg = get_config(name)
-    g = gpu_model(cfg)
+@pytest.mark.parametrize("name,N,layout", [("cfg2_f32", 3, "warp"), ("cfg2_f32", 3, "cta"), ("cfg5_f32", 2, "auto"),
+                                           ("cfg2_f32@n256", 3, "warp"), ("cfg2_f32@n512", 4, "warp")])
+def test_window_f32(name, N, layout):
+    # both kernel layouts against the oracle; the warp-per-particle kernels at
+    # every sub-chunk length they are built for (n = 256, 512, 1024)
+    base, _, size = name.partition("@n")
+    cfg = get_config(base)
+    if size:
+        cfg = dataclasses.replace(cfg, n=int(size))
+    g = gpu_model(cfg, layout=layout)
     om, m0, dW, la = _case(cfg, N, 31, lam=True)
     ref = om.ensemble_window(m0, dW, la)
     out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
@@ -222,3 +229,24 @@ def test_empty_ensemble_is_noop():
     e = torch.empty((0, cfg.n), dtype=g.dtype, device="cuda")
     out = g.ensemble_step(e, torch.empty((0, cfg.Ns, cfg.K), dtype=g.dtype, device="cuda"))
     assert out["m"].shape == (0, cfg.n)
+
+
+def test_layouts_agree_at_full_ensemble_size():
+    # the two kernel layouts on the same 1024-particle window: equal to rounding,
+    # with the same Picard iteration counts up to one per step
+    cfg = get_config("cfg2_f32")
+    gw, gc = gpu_model(cfg, layout="warp"), gpu_model(cfg, layout="cta")
+    N = cfg.N
+    u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
+    m0, _ = gw.prior_sample(N, u0, 5, 0.05)
+    dW = gw.draw_increments(N, cfg.Ns, 9, 1, 0)
+    y = gw.synth_obs(u0, 2, 1)
+    a = gw.ensemble_step(m0, dW, None, y)
+    b = gc.ensemble_step(m0, dW, None, y)
+    torch.cuda.synchronize()
+    scale = b["u"].abs().max().item()
+    assert (a["u"] - b["u"]).abs().max().item() < F32_TOL * scale
+    assert (a["m"] - b["m"]).abs().max().item() < F32_TOL * b["m"].abs().max().item()
+    assert torch.all(a["status"] == 0) and torch.all(b["status"] == 0)
+    assert (a["iters"] - b["iters"]).abs().max().item() <= cfg.Ns
+    assert torch.allclose(a["nll"], b["nll"], rtol=1e-3)
