@@ -163,8 +163,10 @@ int sch_loglik(sch_ctx* ctx, int N, const void* u, const void* y, const void* dW
  * be NULL for zero), phi = nll - logG = -log W~, and the current temperature
  * theta, find the largest dtheta in (0, 1 - theta] with
  * ESS(exp(-dtheta phi)) >= ess_min (Eq. ess): the whole step if it passes,
- * else 60 bisection steps on [0, 1 - theta] (falls back to the smallest
- * point tried if none passes).  Writes wbar[N] (double, normalised weights at
+ * else the root of the monotone ESS(dtheta) - ess_min on [0, 1 - theta],
+ * bracketed to a relative width of 2^-46 (Illinois regula falsi with
+ * bisection safeguards) and taken from the passing side; a root below
+ * (1 - theta) 2^-60 gives (1 - theta) 2^-60.  Writes wbar[N] (double, normalised weights at
  * dtheta) and out[4] = {dtheta, ESS at dtheta, theta_new, ESS of the whole
  * remaining step}; theta_new is exactly 1.0 when the remaining step was taken.
  * N <= 16384. */

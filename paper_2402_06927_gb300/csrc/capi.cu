@@ -281,22 +281,23 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
 }
 
 // the warp-per-particle tables: sub-chunks of CS nodes, 64-row reduced systems
-void wtab_cast(const HTab& s, int CS, WTab& d) {
+void wtab_cast(const HTab& s, const RTab<double>& q, int CS, WTab& d) {
     memset(&d, 0, sizeof(d));
-    auto pr = [](double v) { return make_float2((float)v, (float)v); };
     for (int i = 0; i < CS; ++i) {
-        d.rden[i] = pr(s.rden[i]);
-        d.nar[i] = pr(-s.a * s.rden[i]);
-        d.ngam[i] = pr(-s.gam[i]);
-        d.nalpp[i] = pr(-s.alpp[i]);
-        d.ngamp[i] = pr(-s.gamp[i]);
+        d.rden[i] = (float)s.rden[i];
+        d.nar[i] = (float)(-s.a * s.rden[i]);
+        d.ngam[i] = (float)(-s.gam[i]);
+        d.nalpp[i] = (float)(-s.alpp[i]);
+        d.ngamp[i] = (float)(-s.gamp[i]);
     }
-    d.na = pr(-s.a);
-    d.iBF = pr(s.iBF);
+    d.na = (float)(-s.a);
+    d.iBF = (float)s.iBF;
     d.pa = (float)s.pa;
     d.pc = (float)s.pc;
     d.ae = (float)s.ae;
     d.ge = (float)s.ge;
+    d.diag = fmax(fabs(q.A), fabs(q.Cc)) <= ldexp(fabs(q.B), -30) ? 1 : 0;
+    d.iB = (float)(1.0 / q.B);
 }
 
 void fill_wargs(const sch_params& p, int CS, WArgs& W) {
@@ -308,12 +309,12 @@ void fill_wargs(const sch_params& p, int CS, WArgs& W) {
     ctab_host(h / 6.0 - p.mu * p.dt / (2.0 * h), 2.0 * h / 3.0 + p.mu * p.dt / h, CS, tp);
     // the Helmholtz matrix scaled by 6/h: its right-hand side is m_{i-1} + 4 m_i + m_{i+1}
     ctab_host((h / 6.0 - a2 / h) * 6.0 / h, (2.0 * h / 3.0 + 2.0 * a2 / h) * 6.0 / h, CS, th);
-    wtab_cast(tp, CS, W.pic);
-    wtab_cast(th, CS, W.hel);
     rtab_host(tp, 64, q);
     cast_rtab(q, W.rpic);
+    wtab_cast(tp, q, CS, W.pic);
     rtab_host(th, 64, q);
     cast_rtab(q, W.rhel);
+    wtab_cast(th, q, CS, W.hel);
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }

@@ -1,4 +1,4 @@
-// Filter kernels on sm_103a: adaptive tempering by ESS bisection, systematic
+// Filter kernels on sm_103a: adaptive tempering by an ESS root search, systematic
 // resampling on exact integers, and the row gather that copies resampled
 // particles (Sec. 3.1.1 and 3.1.2 of the paper).  Weights and cumulative sums
 // are FP64 / uint64 regardless of the field precision.
@@ -16,7 +16,7 @@ constexpr int RESAMPLE_THREADS = 1024;
 // Adaptive tempering on one cluster of TEMPER_CTAS CTAs: every CTA holds a
 // slice of the particles, ESS evaluations reduce (sum w, sum w^2) in the CTA,
 // then across the cluster through distributed shared memory.  Every CTA sums
-// the partials in the same order, so all CTAs take identical bisection
+// the partials in the same order, so all CTAs take identical root-search
 // decisions.  Partials are double-buffered by evaluation parity, so one
 // cluster barrier per evaluation suffices.
 struct TemperShm {
@@ -117,17 +117,43 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
     double s1;
     double ess = ess_eval(rest, phi, cnt, phimin, sh, parity, s1);
     const double ess_rest = ess;
+    // The largest dtheta with ESS >= ess_min.  ESS(d) falls monotonically in d
+    // (its log-derivative is 2 (E_{w^2}[phi] - E_w[phi]) <= 0), so the root of
+    // g(d) = ESS(d) - ess_min is bracketed by [0, rest] (g(0) = N - ess_min >= 0)
+    // and found by the Illinois variant of regula falsi: the secant point of the
+    // bracket, with the function value at an end kept twice in a row halved,
+    // and a midpoint whenever the bracket failed to halve over three steps.  It
+    // stops at a relative width of 2^-46 and returns the passing end.  A root
+    // below rest 2^-60 (astronomically spread phi) gives rest 2^-60, the
+    // smallest point 60 bisection steps would try.
     double d;
     if (ess >= ess_min) {
         d = rest;
     } else {
-        double lo = 0.0, hi = rest;
-        for (int it = 0; it < 60; ++it) {
-            const double mid = 0.5 * (lo + hi);
-            const double e_mid = ess_eval(mid, phi, cnt, phimin, sh, parity, s1);
-            if (e_mid >= ess_min) lo = mid; else hi = mid;
+        const double dmin = ldexp(rest, -60);
+        double lo = 0.0, glo = (double)N - ess_min, hi = rest, ghi = ess - ess_min;
+        double wid[3] = {rest, rest, rest};
+        int side = 0;
+        for (int it = 0; it < 200; ++it) {
+            const double w = hi - lo;
+            if (w <= ldexp(hi, -46) || hi < dmin) break;
+            double c = (lo * ghi - hi * glo) / (ghi - glo);
+            if (!(c > lo && c < hi) || w > 0.5 * wid[it % 3]) c = 0.5 * (lo + hi);
+            wid[it % 3] = w;
+            const double gc = ess_eval(c, phi, cnt, phimin, sh, parity, s1) - ess_min;
+            if (gc >= 0.0) {
+                lo = c;
+                glo = gc;
+                if (side == 1) ghi *= 0.5;
+                side = 1;
+            } else {
+                hi = c;
+                ghi = gc;
+                if (side == -1) glo *= 0.5;
+                side = -1;
+            }
         }
-        d = (lo > 0.0) ? lo : hi;
+        d = (lo > 0.0) ? lo : fmax(hi, dmin);
     }
     ess = ess_eval(d, phi, cnt, phimin, sh, parity, s1);
     const double mx = -d * phimin;

@@ -69,19 +69,24 @@ struct ModelArgs {
 
 // Sub-chunk coefficients of a constant symmetric circulant tridiagonal matrix
 // (off-diagonal a) for the warp-per-particle kernels, whose lanes hold two
-// sub-chunks of CS <= WCS_MAX nodes as float pairs: every coefficient is
-// stored as a (c, c) pair so that the packed f32x2 instructions read it
-// straight from the parameter bank.
+// sub-chunks of CS <= WCS_MAX nodes as float pairs.  The coefficients are
+// scalars: each multiplies both halves of a pair through two scalar FMAs that
+// read it straight from the parameter bank.
 constexpr int WCS_MAX = 16;
 
 struct WTab {
-    float2 rden[WCS_MAX];    // 1 / pivot of row i (i >= 1)
-    float2 nar[WCS_MAX];     // -a / pivot of row i
-    float2 ngam[WCS_MAX];    // -gam_i: back-sweep coefficient
-    float2 nalpp[WCS_MAX];   // -alpp_i: weight of the sub-chunk's first value
-    float2 ngamp[WCS_MAX];   // -gamp_i: weight of the sub-chunk's last value
-    float2 na, iBF;          // -a, 1 / pivot of the reduced first row
+    float rden[WCS_MAX];     // 1 / pivot of row i (i >= 1)
+    float nar[WCS_MAX];      // -a / pivot of row i
+    float ngam[WCS_MAX];     // -gam_i: back-sweep coefficient
+    float nalpp[WCS_MAX];    // -alpp_i: weight of the sub-chunk's first value
+    float ngamp[WCS_MAX];    // -gamp_i: weight of the sub-chunk's last value
+    float na, iBF;           // -a, 1 / pivot of the reduced first row
     float pa, pc, ae, ge;    // reduced-row coupling coefficients
+    // 1 when the 64-row reduced system A E_{t-1} + B E_t + C E_{t+1} = D_t is
+    // diagonal to 2^-30 (|A|, |C| <= 2^-30 |B|): then E_t = D_t / B to well
+    // below float rounding and the kernels skip the cross-lane PCR
+    int diag;
+    float iB;                // 1 / B
 };
 
 struct WArgs {

@@ -30,6 +30,13 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return _
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return *reinterpret_cast<float2*>(&r);
+}
 
 // max(a, b, c), NaN if any input is NaN
 __device__ __forceinline__ float fmax3_nan(float a, float b, float c) {
@@ -58,46 +65,54 @@ __device__ __forceinline__ void whalo(const float2 (&v)[CS], float2& lo, float2&
 // Forward and backward sweep of both sub-chunks.  x holds the right-hand side
 // on entry and the interior particular solution dp_1 .. dp_{CS-2} on exit (x[0]
 // keeps rhs_0); pd = (rhs_0 - a dp_1) / BF and de = the last forward value,
-// the two reduced-row inputs of each sub-chunk.
+// the two reduced-row inputs of each sub-chunk.  The X and Y halves run as two
+// independent scalar recurrences whose coefficients come from the parameter bank.
 template <int CS>
 __device__ __forceinline__ void wsweep(const WTab& T, float2 (&x)[CS], float2& pd, float2& de) {
-    float2 d = f2mul(T.rden[1], x[1]);
-    x[1] = d;
+    float dx = T.rden[1] * x[1].x, dy = T.rden[1] * x[1].y;
+    x[1] = make_float2(dx, dy);
 #pragma unroll
     for (int i = 2; i < CS; ++i) {
-        d = f2fma(T.nar[i], d, f2mul(T.rden[i], x[i]));
-        x[i] = d;
+        dx = fmaf(T.nar[i], dx, T.rden[i] * x[i].x);
+        dy = fmaf(T.nar[i], dy, T.rden[i] * x[i].y);
+        x[i] = make_float2(dx, dy);
     }
-    de = d;
-    float2 p = x[CS - 2];
+    de = make_float2(dx, dy);
+    float px = x[CS - 2].x, py = x[CS - 2].y;
 #pragma unroll
     for (int i = CS - 3; i >= 1; --i) {
-        p = f2fma(T.ngam[i], p, x[i]);
-        x[i] = p;
+        px = fmaf(T.ngam[i], px, x[i].x);
+        py = fmaf(T.ngam[i], py, x[i].y);
+        x[i] = make_float2(px, py);
     }
-    pd = f2mul(T.iBF, f2fma(T.na, x[1], x[0]));
+    pd = make_float2(T.iBF * fmaf(T.na, x[1].x, x[0].x), T.iBF * fmaf(T.na, x[1].y, x[0].y));
 }
 
 // The 64-row reduced cyclic system E_t of a constant matrix.  Row t of lane l:
-// t = 2l (sub-chunk X) and 2l + 1 (Y).  Returns E = (E_2l, E_2l+1) and
-// F = (F_2l, F_2l+1), the last and first values of the two sub-chunks, and the
-// neighbours Ep = E_{2l-1} (previous lane's Y last value) and Fn = F_{2l+2}.
+// t = 2l (sub-chunk X) and 2l + 1 (Y), D_t = de_t - ae pd_t - ge pd_{t+1}.
+// Returns E = (E_2l, E_2l+1) and F = (F_2l, F_2l+1), the last and first values
+// of the two sub-chunks, and the neighbours Ep = E_{2l-1} (previous lane's Y
+// last value) and Fn = F_{2l+2}.  A system flagged diagonal (T.diag) is solved
+// as E_t = D_t / B; otherwise a two-row lane partition feeds a cyclic PCR over
+// the lanes' last rows.
 __device__ __forceinline__ void wreduced(const WTab& T, const RTab<float>& Q, float2 pd, float2 de, float2& E,
                                          float2& F, float& Ep, float& Fn) {
     const int lane = threadIdx.x & 31;
     const float pdn = __shfl_sync(FULL, pd.x, (lane + 1) & 31);
-    // D_t = de_t - ae pd_t - ge pd_{t+1}
     const float D0 = de.x - T.ae * pd.x - T.ge * pd.y;
     const float D1 = de.y - T.ae * pd.y - T.ge * pdn;
-    // two-row lane partition, then the 32-lane cyclic PCR on the lanes' last rows
-    const float qd = D0 * Q.iBF;
-    const float nqd = __shfl_sync(FULL, qd, (lane + 1) & 31);
-    const float LD = D1 * Q.q[1] - Q.aeL * qd - Q.geL * nqd;
-    const float EL = pcr32_const(LD, Q);
-    Ep = __shfl_sync(FULL, EL, (lane + 31) & 31);
-    const float Ef = qd - Q.qa * Ep - Q.qc * EL;
-    E = make_float2(Ef, EL);
-    F = make_float2(pd.x - T.pa * Ep - T.pc * Ef, pd.y - T.pa * Ef - T.pc * EL);
+    if (T.diag) {
+        E = make_float2(D0 * T.iB, D1 * T.iB);
+        Ep = __shfl_sync(FULL, E.y, (lane + 31) & 31);
+    } else {
+        const float qd = D0 * Q.iBF;
+        const float nqd = __shfl_sync(FULL, qd, (lane + 1) & 31);
+        const float LD = D1 * Q.q[1] - Q.aeL * qd - Q.geL * nqd;
+        const float EL = pcr32_const(LD, Q);
+        Ep = __shfl_sync(FULL, EL, (lane + 31) & 31);
+        E = make_float2(qd - Q.qa * Ep - Q.qc * EL, EL);
+    }
+    F = make_float2(pd.x - T.pa * Ep - T.pc * E.x, pd.y - T.pa * E.x - T.pc * E.y);
     Fn = __shfl_sync(FULL, F.x, (lane + 1) & 31);
 }
 
@@ -107,7 +122,9 @@ __device__ __forceinline__ void wback(const WTab& T, const float2 (&dp)[CS], flo
     x[0] = F;
     x[CS - 1] = E;
 #pragma unroll
-    for (int i = 1; i < CS - 1; ++i) x[i] = f2fma(T.nalpp[i], F, f2fma(T.ngamp[i], E, dp[i]));
+    for (int i = 1; i < CS - 1; ++i)
+        x[i] = make_float2(fmaf(T.nalpp[i], F.x, fmaf(T.ngamp[i], E.x, dp[i].x)),
+                           fmaf(T.nalpp[i], F.y, fmaf(T.ngamp[i], E.y, dp[i].y)));
 }
 
 // u = H^{-1} M m for this lane's nodes
@@ -132,25 +149,26 @@ __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[CS],
 // wq_k = a_j/4 (dW_k + lambda_k dt): dU_i/4 = sum_j wq_{2j-2} sin(j theta_i) +
 // wq_{2j-1} cos(j theta_i).  s1, c1: sin and cos of the angles of the first
 // X and Y nodes; the harmonics' start values follow the Chebyshev recurrence
-// in j, and along the sub-chunk each harmonic is rotated by j 2 pi / n.
+// in j.  Along a sub-chunk each harmonic's value v = a sin(j theta) + b cos(j theta)
+// and its quadrature q = a cos(j theta) - b sin(j theta) are rotated together by
+// the angle j 2 pi / n, so a node costs one rotation and one add per harmonic.
 template <int CS>
 __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* wq, float2 s1, float2 c1,
                                        float2 (&nq)[CS]) {
-#pragma unroll
-    for (int i = 0; i < CS; ++i) nq[i] = f2b(0.f);
     const float2 twoc = f2add(c1, c1);
     float2 sj = s1, cj = c1, nsjm = f2b(0.f), ncjm = f2b(-1.f);   // nsjm = -sin((j-1) theta)
     for (int j = 0; j < A.K2; ++j) {
-        const float2 a = f2b(wq[2 * j]), b = f2b(wq[2 * j + 1]);
+        const float a = wq[2 * j], b = wq[2 * j + 1];
         const float2 rc = f2b(A.rot_c[j]), rs = f2b(A.rot_s[j]), nrs = f2b(-A.rot_s[j]);
-        float2 sn = sj, cs = cj;
+        float2 v = f2fma(f2b(a), sj, f2mul(f2b(b), cj));
+        float2 q = f2fma(f2b(a), cj, f2mul(f2b(-b), sj));
 #pragma unroll
         for (int i = 0; i < CS; ++i) {
-            nq[i] = f2fma(a, sn, f2fma(b, cs, nq[i]));
+            nq[i] = (j == 0) ? v : f2add(nq[i], v);
             if (i < CS - 1) {
-                const float2 s2 = f2fma(sn, rc, f2mul(cs, rs));
-                cs = f2fma(cs, rc, f2mul(sn, nrs));
-                sn = s2;
+                const float2 v2 = f2fma(v, rc, f2mul(q, rs));
+                q = f2fma(q, rc, f2mul(v, nrs));
+                v = v2;
             }
         }
         const float2 sn2 = f2fma(twoc, sj, nsjm), cn2 = f2fma(twoc, cj, ncjm);
@@ -162,18 +180,18 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* w
 }
 
 // One implicit-midpoint step of this warp's particle: (m, u) in/out.
-// R0sm: this warp's [CS][32] float2 scratch for R0.
+// R0sm: this warp's [CS][32] float2 scratch for R0 = (M - mu dt/2 K) m0.
 template <int CS>
 __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[CS], float2 (&u)[CS],
                                       float2* R0sm, const float* wq, float2 s1, float2 c1, int& iters, int& flags) {
     const int lane = threadIdx.x & 31;
+    // W0 = dt/8 u0 + dU/4 (registers) and R0 (shared memory), fixed for the step
     float2 W0[CS];
     {
-        float2 nq[CS];
-        wnoise<CS>(A, wq, s1, c1, nq);
+        wnoise<CS>(A, wq, s1, c1, W0);
         const float2 dt8 = f2b(A.dt8);
 #pragma unroll
-        for (int i = 0; i < CS; ++i) W0[i] = f2fma(dt8, u[i], nq[i]);
+        for (int i = 0; i < CS; ++i) W0[i] = f2fma(dt8, u[i], W0[i]);
         float2 lo, hi;
         whalo<CS>(m, lo, hi);
         const float2 c0p = f2b(A.c0p), b0p = f2b(A.b0p);
@@ -184,36 +202,34 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
             R0sm[i * 32 + lane] = f2fma(c0p, f2add(l, r), f2mul(b0p, m[i]));
         }
     }
-    float2 mi[CS], ui[CS];
+    float2 mi[CS];
 #pragma unroll
-    for (int i = 0; i < CS; ++i) {
-        mi[i] = m[i];
-        ui[i] = u[i];
-    }
-    const float2 dt8 = f2b(A.dt8), mone = f2b(-1.f);
+    for (int i = 0; i < CS; ++i) mi[i] = m[i];
+    const float2 dt8 = f2b(A.dt8);
     for (int it = 1;; ++it) {
+        // rhs_i = R0_i + w_{i-1} g_{i-1} - w_{i+1} g_i,  w = W0 + dt/8 u_it,  g_i = mb2_i + mb2_{i+1}
         float2 x[CS];
         {
             float2 w[CS], mb[CS];
 #pragma unroll
             for (int i = 0; i < CS; ++i) {
-                w[i] = f2fma(dt8, ui[i], W0[i]);
+                w[i] = f2fma(dt8, u[i], W0[i]);
                 mb[i] = f2add(m[i], mi[i]);
             }
             float2 wl, wr, ml, mr;
             whalo<CS>(w, wl, wr);
             whalo<CS>(mb, ml, mr);
-            float2 gp = f2add(ml, mb[0]);   // mb2_{i-1} + mb2_i at i = 0
+            float2 gp = f2add(ml, mb[0]);
 #pragma unroll
             for (int i = 0; i < CS; ++i) {
                 const float2 wprev = (i == 0) ? wl : w[i - 1];
                 const float2 wnext = (i == CS - 1) ? wr : w[i + 1];
                 const float2 g = f2add(mb[i], (i == CS - 1) ? mr : mb[i + 1]);
-                const float2 t = f2fma(wprev, gp, R0sm[i * 32 + lane]);
-                x[i] = f2fma(f2mul(wnext, mone), g, t);
+                x[i] = f2sub(f2fma(wprev, gp, R0sm[i * 32 + lane]), f2mul(wnext, g));
                 gp = g;
             }
         }
+        // (M + mu dt/2 K) m_new = rhs
         float2 pd, de, E, F;
         float Ep, Fn;
         wsweep<CS>(W.pic, x, pd, de);
@@ -223,7 +239,7 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
         float dmax = 0.f, mmax = 0.f;
 #pragma unroll
         for (int i = 0; i < CS; ++i) {
-            const float2 d = f2fma(mi[i], mone, mn[i]);
+            const float2 d = f2sub(mn[i], mi[i]);
             dmax = fmax3_nan(dmax, fabsf(d.x), fabsf(d.y));
             mmax = fmaxf(mmax, fmaxf(fabsf(mn[i].x), fabsf(mn[i].y)));
             mi[i] = mn[i];
@@ -231,17 +247,18 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
         // u_new = H^{-1} M m_new, the mass product's chunk ends from the reduced solve
         {
             const float2 lo = make_float2(Ep, E.x), hi = make_float2(F.y, Fn);
+            const float2 four = f2b(4.f);
 #pragma unroll
             for (int i = 0; i < CS; ++i) {
                 const float2 l = (i == 0) ? lo : mn[i - 1];
                 const float2 r = (i == CS - 1) ? hi : mn[i + 1];
-                x[i] = f2fma(f2b(4.f), mn[i], f2add(l, r));
+                x[i] = f2fma(four, mn[i], f2add(l, r));
             }
             float2 hpd, hde, hE, hF;
             float hEp, hFn;
             wsweep<CS>(W.hel, x, hpd, hde);
             wreduced(W.hel, W.rhel, hpd, hde, hE, hF, hEp, hFn);
-            wback<CS>(W.hel, x, hF, hE, ui);
+            wback<CS>(W.hel, x, hF, hE, u);
         }
         iters++;
         const float dm = warp_max_nan(dmax);
@@ -257,10 +274,7 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
         }
     }
 #pragma unroll
-    for (int i = 0; i < CS; ++i) {
-        m[i] = mi[i];
-        u[i] = ui[i];
-    }
+    for (int i = 0; i < CS; ++i) m[i] = mi[i];
 }
 
 // this lane's 2 CS nodes of a particle row <-> the paired registers
@@ -287,20 +301,24 @@ __device__ __forceinline__ void wstore(float* row, const float2 (&v)[CS]) {
     }
 }
 
-// observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this lane's nodes
+// observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this lane's nodes;
+// node mod stride and the observation index advance node by node
 template <int CS>
 __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float2 (&u)[CS], const float* y) {
     const int base = (threadIdx.x & 31) * 2 * CS;
     double acc = 0.0;
+    int rem = base % A.stride;
+    int j = base / A.stride + (rem != 0);
 #pragma unroll
-    for (int i = 0; i < CS; ++i) {
+    for (int c = 0; c < 2; ++c) {
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int node = base + c * CS + i;
-            if (node % A.stride == 0) {
-                const float r = ((c ? u[i].y : u[i].x) - y[node / A.stride]) * A.sigma_inv;
+        for (int i = 0; i < CS; ++i) {
+            if (rem == 0) {
+                const float r = ((c ? u[i].y : u[i].x) - y[j]) * A.sigma_inv;
                 acc += (double)r * (double)r;
+                ++j;
             }
+            rem = (rem + 1 == A.stride) ? 0 : rem + 1;
         }
     }
     return acc;

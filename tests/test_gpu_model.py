@@ -111,14 +111,18 @@ def test_window_f64_multiwarp():
 
 
 @pytest.mark.parametrize("name,N,layout", [("cfg2_f32", 3, "warp"), ("cfg2_f32", 3, "cta"), ("cfg5_f32", 2, "auto"),
-                                           ("cfg2_f32@n256", 3, "warp"), ("cfg2_f32@n512", 4, "warp")])
+                                           ("cfg2_f32@n=256", 3, "warp"), ("cfg2_f32@n=512", 4, "warp"),
+                                           ("cfg2_f32@mu=2.0", 3, "warp"), ("cfg2_f32@mu=2.0", 2, "cta")])
 def test_window_f32(name, N, layout):
     # both kernel layouts against the oracle; the warp-per-particle kernels at
-    # every sub-chunk length they are built for (n = 256, 512, 1024)
-    base, _, size = name.partition("@n")
+    # every sub-chunk length they are built for (n = 256, 512, 1024), and with a
+    # viscosity large enough that the Picard matrix's reduced system is coupled
+    # (at mu = 0.02 it is diagonal to 2^-30 and solved without the lane PCR)
+    base, _, over = name.partition("@")
     cfg = get_config(base)
-    if size:
-        cfg = dataclasses.replace(cfg, n=int(size))
+    if over:
+        key, val = over.split("=")
+        cfg = dataclasses.replace(cfg, **{key: type(getattr(cfg, key))(val)})
     g = gpu_model(cfg, layout=layout)
     om, m0, dW, la = _case(cfg, N, 31, lam=True)
     ref = om.ensemble_window(m0, dW, la)
