@@ -55,7 +55,10 @@ def step_flops(n, K, solver, iters, steps):
 JITTER_SOURCES = ["paper_2402_06927_gb300/csrc/sch_warp.cuh", "paper_2402_06927_gb300/csrc/sch_kernels.cuh",
                   "paper_2402_06927_gb300/csrc/sch_internal.h", "paper_2402_06927_gb300/csrc/sch_device.cuh",
                   "paper_2402_06927_gb300/csrc/sch_window_warp.cu"]
-JITTER_TRAFFIC_BYTES = {}
+JITTER_TRAFFIC_BYTES = {
+    # wjitter_kernel<16>, profiles/wjitter_kernel_cfg2_n1024_N1024.md: 4.625408 MB read, 0 written
+    "03603b1da549b2a07e5b107c4f72f79b833396ee": 4625408,
+}
 
 
 def jitter_traffic():

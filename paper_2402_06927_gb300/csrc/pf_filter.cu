@@ -37,19 +37,22 @@ __device__ __forceinline__ double cta_min(double v, TemperShm* sh) {
     return m;
 }
 
-// ESS (Eq. ess) of the weights exp(-d phi_i - max), max = -d phi_min
+// ESS (Eq. ess) of the weights w_e = exp(-d phi_e - max), max = -d phi_min;
+// the thread's weights are returned in w, their cluster-wide sum in s1_out
 __device__ __forceinline__ double ess_eval(double d, const double (&phi)[TEMPER_PER_THREAD], int cnt, double phimin,
-                                           TemperShm* sh, int& parity, double& s1_out) {
+                                           TemperShm* sh, int& parity, double& s1_out,
+                                           double (&w)[TEMPER_PER_THREAD]) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const double mx = -d * phimin;
     double s1 = 0.0, s2 = 0.0;
 #pragma unroll
     for (int e = 0; e < TEMPER_PER_THREAD; ++e) {
+        w[e] = 0.0;
         if (e < cnt) {
-            const double w = exp(-d * phi[e] - mx);
-            s1 += w;
-            s2 += w * w;
+            w[e] = exp(-d * phi[e] - mx);
+            s1 += w[e];
+            s2 += w[e] * w[e];
         }
     }
     s1 = warp_sum(s1);
@@ -114,8 +117,10 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
     for (int r = 0; r < TEMPER_CTAS; ++r) phimin = fmin(phimin, cl.map_shared_rank(sh, r)->part[1][0]);
     int parity = 0;   // the next evaluation writes parity 0; parity 1 is free again after its barrier
     const double rest = 1.0 - theta;
-    double s1;
-    double ess = ess_eval(rest, phi, cnt, phimin, sh, parity, s1);
+    // (ess, s1, wk): the ESS, weight sum and this thread's weights at the
+    // current answer, so that the normalised weights need no further pass
+    double s1, wk[TEMPER_PER_THREAD], wc[TEMPER_PER_THREAD];
+    double ess = ess_eval(rest, phi, cnt, phimin, sh, parity, s1, wk);
     const double ess_rest = ess;
     // The largest dtheta with ESS >= ess_min.  ESS(d) falls monotonically in d
     // (its log-derivative is 2 (E_{w^2}[phi] - E_w[phi]) <= 0), so the root of
@@ -132,18 +137,26 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
     } else {
         const double dmin = ldexp(rest, -60);
         double lo = 0.0, glo = (double)N - ess_min, hi = rest, ghi = ess - ess_min;
-        double wid[3] = {rest, rest, rest};
+        double w3 = rest, w2 = rest, w1 = rest;   // bracket widths of the last three steps
         int side = 0;
         for (int it = 0; it < 200; ++it) {
             const double w = hi - lo;
             if (w <= ldexp(hi, -46) || hi < dmin) break;
             double c = (lo * ghi - hi * glo) / (ghi - glo);
-            if (!(c > lo && c < hi) || w > 0.5 * wid[it % 3]) c = 0.5 * (lo + hi);
-            wid[it % 3] = w;
-            const double gc = ess_eval(c, phi, cnt, phimin, sh, parity, s1) - ess_min;
+            if (!(c > lo && c < hi) || w > 0.5 * w3) c = 0.5 * (lo + hi);
+            w3 = w2;
+            w2 = w1;
+            w1 = w;
+            double sc;
+            const double ec = ess_eval(c, phi, cnt, phimin, sh, parity, sc, wc);
+            const double gc = ec - ess_min;
             if (gc >= 0.0) {
                 lo = c;
                 glo = gc;
+                ess = ec;
+                s1 = sc;
+#pragma unroll
+                for (int e = 0; e < TEMPER_PER_THREAD; ++e) wk[e] = wc[e];
                 if (side == 1) ghi *= 0.5;
                 side = 1;
             } else {
@@ -153,14 +166,17 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
                 side = -1;
             }
         }
-        d = (lo > 0.0) ? lo : fmax(hi, dmin);
+        if (lo > 0.0) {
+            d = lo;
+        } else {
+            d = fmax(hi, dmin);
+            ess = ess_eval(d, phi, cnt, phimin, sh, parity, s1, wk);
+        }
     }
-    ess = ess_eval(d, phi, cnt, phimin, sh, parity, s1);
-    const double mx = -d * phimin;
 #pragma unroll
     for (int e = 0; e < TEMPER_PER_THREAD; ++e) {
         const int i = gt + e * STRIDE;
-        if (i < N) wbar[i] = exp(-d * phi[e] - mx) / s1;
+        if (i < N) wbar[i] = wk[e] / s1;
     }
     if (rank == 0 && threadIdx.x == 0) {
         out[0] = d;
