@@ -300,7 +300,7 @@ void wtab_cast(const HTab& s, const RTab<double>& q, int CS, WTab& d) {
     d.iB = (float)(1.0 / q.B);
 }
 
-void fill_wargs(const sch_params& p, int CS, WArgs& W) {
+void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
     memset(&W, 0, sizeof(W));
     const double h = p.L / p.n;
     const double a2 = p.alpha * p.alpha;
@@ -309,10 +309,10 @@ void fill_wargs(const sch_params& p, int CS, WArgs& W) {
     ctab_host(h / 6.0 - p.mu * p.dt / (2.0 * h), 2.0 * h / 3.0 + p.mu * p.dt / h, CS, tp);
     // the Helmholtz matrix scaled by 6/h: its right-hand side is m_{i-1} + 4 m_i + m_{i+1}
     ctab_host((h / 6.0 - a2 / h) * 6.0 / h, (2.0 * h / 3.0 + 2.0 * a2 / h) * 6.0 / h, CS, th);
-    rtab_host(tp, 64, q);
+    rtab_host(tp, rows, q);
     cast_rtab(q, W.rpic);
     wtab_cast(tp, q, CS, W.pic);
-    rtab_host(th, 64, q);
+    rtab_host(th, rows, q);
     cast_rtab(q, W.rhel);
     wtab_cast(th, q, CS, W.hel);
 }
@@ -351,8 +351,10 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     fill_args(p, C, c->af);
     fill_args(p, C, c->ad);
     if (warp_ok) {
-        c->wcs = p.n / 64;
-        fill_wargs(p, c->wcs, c->wa);
+        // one warp per particle: 32 lanes x 2P sub-chunks of wcs nodes, a reduced system of 64 P rows
+        const int P = warp_streams(p.n);
+        c->wcs = p.n / (64 * P);
+        fill_wargs(p, c->wcs, 64 * P, c->wa);
     }
     *ctx = c;
     return SCH_OK;

@@ -195,7 +195,9 @@ template <typename R>
 int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* u_truth, double* ws, double* out,
                 cudaStream_t st);
 
-// warp-per-particle kernels for float fields, n = 64 cs (sch_window_warp.cu)
+// warp-per-particle kernels for float fields, n = 64 P cs with P = warp_streams(n)
+// float-pair streams of two sub-chunks each (sch_window_warp.cu)
+int warp_streams(int n);
 int launch_wwindow(int cs, const ModelArgs<float>& A, const WArgs& W, const WindowIO<float>& io, int N,
                    cudaStream_t st);
 int launch_wjitter(int cs, const ModelArgs<float>& A, const WArgs& W, const JitterIO<float>& io, int N,

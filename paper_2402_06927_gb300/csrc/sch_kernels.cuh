@@ -196,10 +196,12 @@ __device__ __forceinline__ R pcr32_const(R D, const RTab<R>& Q) {
 // Lane l holds the reduced-row inputs pd, de of rows t = l RR + r (RR = TP/32)
 // and gets back E_t and F_t = pd_t - pa E_{t-1} - pc E_t.  Rows read
 // D_t = de_t - ae pd_t - ge pd_{t+1} (A, B, C fixed); the next row's pd and the
-// previous row's E cross lanes by shuffle.
-template <typename R, int TP>
-__device__ __forceinline__ void lane_solve_const(const CTab<R>& T, const RTab<R>& Q, const R (&pd)[TP / 32],
-                                                 const R (&de)[TP / 32], R (&E)[TP / 32], R (&F)[TP / 32]) {
+// previous row's E cross lanes by shuffle.  T: any table with the reduced-row
+// couplings ae, ge, pa, pc; Eprev_out, if given, receives E_{l RR - 1}.
+template <typename R, int TP, typename Tab>
+__device__ __forceinline__ void lane_solve_const(const Tab& T, const RTab<R>& Q, const R (&pd)[TP / 32],
+                                                 const R (&de)[TP / 32], R (&E)[TP / 32], R (&F)[TP / 32],
+                                                 R* Eprev_out = nullptr) {
     constexpr int RR = TP / 32;
     const int lane = threadIdx.x & 31;
     const R pd_next = __shfl_sync(FULL, pd[0], (lane + 1) & 31);
@@ -239,6 +241,7 @@ __device__ __forceinline__ void lane_solve_const(const CTab<R>& T, const RTab<R>
         const R em1 = (r == 0) ? Eprev : E[(r + RR - 1) % RR];
         F[r] = pd[r] - T.pa * em1 - T.pc * E[r];
     }
+    if (Eprev_out) *Eprev_out = Eprev;
 }
 
 // Warp 0: the same from shared-memory rows pd[t], de[t] into E[t], F[t].

@@ -1,14 +1,17 @@
 // Warp-per-particle propagation for float fields (explicit-advection Picard
-// solver of the implicit midpoint step, Eq. fde1), n = 64 CS nodes, CS <= 16.
+// solver of the implicit midpoint step, Eq. fde1), n = 64 P CS nodes.
 //
 // One warp carries one particle and needs no CTA barrier.  Lane l owns the
-// 2 CS consecutive nodes [2 CS l, 2 CS (l + 1)) as two sub-chunks X (first CS
-// nodes) and Y (last CS), and keeps node i of X and node i of Y in one float2.
-// Every stencil operation and every chunk sweep then runs on both sub-chunks at
-// once with the packed f32x2 instructions (fma.rn.f32x2 and friends).  The
-// 64 sub-chunks of a particle leave a cyclic reduced system of 64 interface
-// rows (two per lane, rows 2l and 2l + 1), solved by every lane at once: a
-// two-row lane sweep and a cyclic PCR across the 32 lanes with shuffles.
+// LN = 2 P CS consecutive nodes [LN l, LN (l + 1)) as S = 2P sub-chunks of CS
+// nodes, s = 0 .. S-1 in node order.  Stream p (p < P) keeps node i of
+// sub-chunk p and node i of sub-chunk p + P in one float2, so stencil work on
+// a stream runs on two sub-chunks at once, and a stream's chunk-end neighbours
+// are whole pairs of the adjacent streams (only the lane's first and last
+// nodes cross lanes).  The sub-chunk sweeps run as 2P interleaved scalar
+// recurrences.  The 32 S sub-chunks of a particle leave a cyclic reduced
+// system of 32 S interface rows (S per lane, rows S l + s), solved by every
+// lane at once: an S-row lane partition and a cyclic PCR across the 32 lanes
+// with shuffles.
 //
 // One Picard iteration (the step's right-hand sides R0 = (M - mu dt/2 K) m0 and
 // W0 = dt/8 u0 + dU/4 fixed):
@@ -52,213 +55,285 @@ __device__ __forceinline__ float warp_max_nan(float v) {
     return r;
 }
 
-// chunk-end neighbours of a paired field: lo = (x_{-1}, y_{-1}) of pair 0 and
-// hi = (x_CS, y_CS) of pair CS - 1, i.e. (previous lane's last Y node, own
-// last X node) and (own first Y node, next lane's first X node)
-template <int CS>
-__device__ __forceinline__ void whalo(const float2 (&v)[CS], float2& lo, float2& hi) {
+// The lane's outer chunk-end neighbours of a paired field: lo, left of pair 0
+// of stream 0 = (previous lane's last node, last node of sub-chunk P-1), and
+// hi, right of the last pair of stream P-1 = (first node of sub-chunk P, next
+// lane's first node).  Every other stream boundary is an adjacent stream's pair.
+template <int CS, int P>
+__device__ __forceinline__ void whalo(const float2 (&v)[P][CS], float2& lo, float2& hi) {
     const int lane = threadIdx.x & 31;
-    lo = make_float2(__shfl_sync(FULL, v[CS - 1].y, (lane + 31) & 31), v[CS - 1].x);
-    hi = make_float2(v[0].y, __shfl_sync(FULL, v[0].x, (lane + 1) & 31));
+    lo = make_float2(__shfl_sync(FULL, v[P - 1][CS - 1].y, (lane + 31) & 31), v[P - 1][CS - 1].x);
+    hi = make_float2(v[0][0].y, __shfl_sync(FULL, v[0][0].x, (lane + 1) & 31));
 }
 
-// Forward and backward sweep of both sub-chunks.  x holds the right-hand side
-// on entry and the interior particular solution dp_1 .. dp_{CS-2} on exit (x[0]
+// stencil neighbours of pair i of stream p
+template <int CS, int P>
+__device__ __forceinline__ float2 wleft(const float2 (&v)[P][CS], int p, int i, float2 lo) {
+    return (i > 0) ? v[p][i - 1] : ((p == 0) ? lo : v[p - 1][CS - 1]);
+}
+template <int CS, int P>
+__device__ __forceinline__ float2 wright(const float2 (&v)[P][CS], int p, int i, float2 hi) {
+    return (i < CS - 1) ? v[p][i + 1] : ((p == P - 1) ? hi : v[p + 1][0]);
+}
+
+// Forward and backward sweep of every sub-chunk.  x holds the right-hand side
+// on entry and the interior particular solution dp_1 .. dp_{CS-2} on exit (x[.][0]
 // keeps rhs_0); pd = (rhs_0 - a dp_1) / BF and de = the last forward value,
-// the two reduced-row inputs of each sub-chunk.  The X and Y halves run as two
-// independent scalar recurrences whose coefficients come from the parameter bank.
-template <int CS>
-__device__ __forceinline__ void wsweep(const WTab& T, float2 (&x)[CS], float2& pd, float2& de) {
-    float dx = T.rden[1] * x[1].x, dy = T.rden[1] * x[1].y;
-    x[1] = make_float2(dx, dy);
+// the two reduced-row inputs of each sub-chunk.  The 2P recurrences are
+// interleaved; their coefficients come from the parameter bank.
+template <int CS, int P>
+__device__ __forceinline__ void wsweep(const WTab& T, float2 (&x)[P][CS], float2 (&pd)[P], float2 (&de)[P]) {
+    float dx[P], dy[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        dx[p] = T.rden[1] * x[p][1].x;
+        dy[p] = T.rden[1] * x[p][1].y;
+        x[p][1] = make_float2(dx[p], dy[p]);
+    }
 #pragma unroll
     for (int i = 2; i < CS; ++i) {
-        dx = fmaf(T.nar[i], dx, T.rden[i] * x[i].x);
-        dy = fmaf(T.nar[i], dy, T.rden[i] * x[i].y);
-        x[i] = make_float2(dx, dy);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            dx[p] = fmaf(T.nar[i], dx[p], T.rden[i] * x[p][i].x);
+            dy[p] = fmaf(T.nar[i], dy[p], T.rden[i] * x[p][i].y);
+            x[p][i] = make_float2(dx[p], dy[p]);
+        }
     }
-    de = make_float2(dx, dy);
-    float px = x[CS - 2].x, py = x[CS - 2].y;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        de[p] = make_float2(dx[p], dy[p]);
+        dx[p] = x[p][CS - 2].x;
+        dy[p] = x[p][CS - 2].y;
+    }
 #pragma unroll
     for (int i = CS - 3; i >= 1; --i) {
-        px = fmaf(T.ngam[i], px, x[i].x);
-        py = fmaf(T.ngam[i], py, x[i].y);
-        x[i] = make_float2(px, py);
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            dx[p] = fmaf(T.ngam[i], dx[p], x[p][i].x);
+            dy[p] = fmaf(T.ngam[i], dy[p], x[p][i].y);
+            x[p][i] = make_float2(dx[p], dy[p]);
+        }
     }
-    pd = make_float2(T.iBF * fmaf(T.na, x[1].x, x[0].x), T.iBF * fmaf(T.na, x[1].y, x[0].y));
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        pd[p] = make_float2(T.iBF * fmaf(T.na, x[p][1].x, x[p][0].x), T.iBF * fmaf(T.na, x[p][1].y, x[p][0].y));
 }
 
-// The 64-row reduced cyclic system E_t of a constant matrix.  Row t of lane l:
-// t = 2l (sub-chunk X) and 2l + 1 (Y), D_t = de_t - ae pd_t - ge pd_{t+1}.
-// Returns E = (E_2l, E_2l+1) and F = (F_2l, F_2l+1), the last and first values
-// of the two sub-chunks, and the neighbours Ep = E_{2l-1} (previous lane's Y
-// last value) and Fn = F_{2l+2}.  A system flagged diagonal (T.diag) is solved
-// as E_t = D_t / B; otherwise a two-row lane partition feeds a cyclic PCR over
-// the lanes' last rows.
-__device__ __forceinline__ void wreduced(const WTab& T, const RTab<float>& Q, float2 pd, float2 de, float2& E,
-                                         float2& F, float& Ep, float& Fn) {
+// The cyclic reduced system E_t (t = S l + s) of a constant matrix,
+// D_t = de_t - ae pd_t - ge pd_{t+1}.  Returns the pairs E[p] = (E of sub-chunk
+// p, of p + P) and F[p] likewise (the last and first values of the sub-chunks),
+// and the lane's outer neighbours Ep = E_{S l - 1}, Fn = F_{S (l + 1)}.  A system
+// flagged diagonal (T.diag) is solved as E_t = D_t / B; otherwise an S-row lane
+// partition feeds a cyclic PCR over the lanes.
+template <int P>
+__device__ __forceinline__ void wreduced(const WTab& T, const RTab<float>& Q, const float2 (&pd)[P],
+                                         const float2 (&de)[P], float2 (&E)[P], float2 (&F)[P], float& Ep,
+                                         float& Fn) {
+    constexpr int S = 2 * P;
     const int lane = threadIdx.x & 31;
-    const float pdn = __shfl_sync(FULL, pd.x, (lane + 1) & 31);
-    const float D0 = de.x - T.ae * pd.x - T.ge * pd.y;
-    const float D1 = de.y - T.ae * pd.y - T.ge * pdn;
-    if (T.diag) {
-        E = make_float2(D0 * T.iB, D1 * T.iB);
-        Ep = __shfl_sync(FULL, E.y, (lane + 31) & 31);
-    } else {
-        const float qd = D0 * Q.iBF;
-        const float nqd = __shfl_sync(FULL, qd, (lane + 1) & 31);
-        const float LD = D1 * Q.q[1] - Q.aeL * qd - Q.geL * nqd;
-        const float EL = pcr32_const(LD, Q);
-        Ep = __shfl_sync(FULL, EL, (lane + 31) & 31);
-        E = make_float2(qd - Q.qa * Ep - Q.qc * EL, EL);
+    float pr[S], dr[S], Er[S], Fr[S];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        pr[p] = pd[p].x;
+        pr[p + P] = pd[p].y;
+        dr[p] = de[p].x;
+        dr[p + P] = de[p].y;
     }
-    F = make_float2(pd.x - T.pa * Ep - T.pc * E.x, pd.y - T.pa * E.x - T.pc * E.y);
-    Fn = __shfl_sync(FULL, F.x, (lane + 1) & 31);
+    if (T.diag) {
+        const float pdn = __shfl_sync(FULL, pr[0], (lane + 1) & 31);
+#pragma unroll
+        for (int r = 0; r < S; ++r)
+            Er[r] = (dr[r] - T.ae * pr[r] - T.ge * ((r == S - 1) ? pdn : pr[r + 1])) * T.iB;
+        Ep = __shfl_sync(FULL, Er[S - 1], (lane + 31) & 31);
+#pragma unroll
+        for (int r = 0; r < S; ++r) Fr[r] = pr[r] - T.pa * ((r == 0) ? Ep : Er[r - 1]) - T.pc * Er[r];
+    } else {
+        lane_solve_const<float, 32 * S>(T, Q, pr, dr, Er, Fr, &Ep);
+    }
+    Fn = __shfl_sync(FULL, Fr[0], (lane + 1) & 31);
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        E[p] = make_float2(Er[p], Er[p + P]);
+        F[p] = make_float2(Fr[p], Fr[p + P]);
+    }
 }
 
 // back substitution: x_i = dp_i - alpp_i F - gamp_i E, x_0 = F, x_{CS-1} = E
-template <int CS>
-__device__ __forceinline__ void wback(const WTab& T, const float2 (&dp)[CS], float2 F, float2 E, float2 (&x)[CS]) {
-    x[0] = F;
-    x[CS - 1] = E;
+template <int CS, int P>
+__device__ __forceinline__ void wback(const WTab& T, const float2 (&dp)[P][CS], const float2 (&F)[P],
+                                      const float2 (&E)[P], float2 (&x)[P][CS]) {
 #pragma unroll
-    for (int i = 1; i < CS - 1; ++i)
-        x[i] = make_float2(fmaf(T.nalpp[i], F.x, fmaf(T.ngamp[i], E.x, dp[i].x)),
-                           fmaf(T.nalpp[i], F.y, fmaf(T.ngamp[i], E.y, dp[i].y)));
+    for (int p = 0; p < P; ++p) {
+        x[p][0] = F[p];
+        x[p][CS - 1] = E[p];
+#pragma unroll
+        for (int i = 1; i < CS - 1; ++i)
+            x[p][i] = make_float2(fmaf(T.nalpp[i], F[p].x, fmaf(T.ngamp[i], E[p].x, dp[p][i].x)),
+                                  fmaf(T.nalpp[i], F[p].y, fmaf(T.ngamp[i], E[p].y, dp[p][i].y)));
+    }
+}
+
+// the lane's outer chunk-end neighbours of a field just solved for, from its
+// reduced solve (see whalo)
+template <int P>
+__device__ __forceinline__ void wsolved_halo(const float2 (&E)[P], const float2 (&F)[P], float Ep, float Fn,
+                                             float2& lo, float2& hi) {
+    lo = make_float2(Ep, E[P - 1].x);
+    hi = make_float2(F[0].y, Fn);
 }
 
 // u = H^{-1} M m for this lane's nodes
-template <int CS>
-__device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[CS], float2 (&u)[CS]) {
-    float2 lo, hi, x[CS];
-    whalo<CS>(m, lo, hi);
+template <int CS, int P>
+__device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][CS], float2 (&u)[P][CS]) {
+    float2 lo, hi, x[P][CS];
+    whalo<CS, P>(m, lo, hi);
+    const float2 four = f2b(4.f);
 #pragma unroll
-    for (int i = 0; i < CS; ++i) {
-        const float2 l = (i == 0) ? lo : m[i - 1];
-        const float2 r = (i == CS - 1) ? hi : m[i + 1];
-        x[i] = f2fma(f2b(4.f), m[i], f2add(l, r));
-    }
-    float2 pd, de, E, F;
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int i = 0; i < CS; ++i)
+            x[p][i] = f2fma(four, m[p][i], f2add(wleft<CS, P>(m, p, i, lo), wright<CS, P>(m, p, i, hi)));
+    float2 pd[P], de[P], E[P], F[P];
     float Ep, Fn;
-    wsweep<CS>(W.hel, x, pd, de);
-    wreduced(W.hel, W.rhel, pd, de, E, F, Ep, Fn);
-    wback<CS>(W.hel, x, F, E, u);
+    wsweep<CS, P>(W.hel, x, pd, de);
+    wreduced<P>(W.hel, W.rhel, pd, de, E, F, Ep, Fn);
+    wback<CS, P>(W.hel, x, F, E, u);
 }
 
 // SALT increment dU/4 at this lane's nodes from the step's K weights
 // wq_k = a_j/4 (dW_k + lambda_k dt): dU_i/4 = sum_j wq_{2j-2} sin(j theta_i) +
-// wq_{2j-1} cos(j theta_i).  s1, c1: sin and cos of the angles of the first
-// X and Y nodes; the harmonics' start values follow the Chebyshev recurrence
-// in j.  Along a sub-chunk each harmonic's value v = a sin(j theta) + b cos(j theta)
-// and its quadrature q = a cos(j theta) - b sin(j theta) are rotated together by
-// the angle j 2 pi / n, so a node costs one rotation and one add per harmonic.
-template <int CS>
-__device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* wq, float2 s1, float2 c1,
-                                       float2 (&nq)[CS]) {
-    const float2 twoc = f2add(c1, c1);
-    float2 sj = s1, cj = c1, nsjm = f2b(0.f), ncjm = f2b(-1.f);   // nsjm = -sin((j-1) theta)
+// wq_{2j-1} cos(j theta_i).  s1[p], c1[p]: sin and cos of the angles of the
+// first nodes of stream p's two sub-chunks; the harmonics' start values follow
+// the Chebyshev recurrence in j.  Along a sub-chunk each harmonic's value
+// v = a sin(j theta) + b cos(j theta) and its quadrature q = a cos(j theta) -
+// b sin(j theta) are rotated together by the angle j 2 pi / n, so a node costs
+// one rotation and one add per harmonic.
+template <int CS, int P>
+__device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* wq, const float2 (&s1)[P],
+                                       const float2 (&c1)[P], float2 (&nq)[P][CS]) {
+    float2 sj[P], cj[P], nsjm[P], ncjm[P];   // nsjm = -sin((j-1) theta)
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        sj[p] = s1[p];
+        cj[p] = c1[p];
+        nsjm[p] = f2b(0.f);
+        ncjm[p] = f2b(-1.f);
+    }
     for (int j = 0; j < A.K2; ++j) {
         const float a = wq[2 * j], b = wq[2 * j + 1];
         const float2 rc = f2b(A.rot_c[j]), rs = f2b(A.rot_s[j]), nrs = f2b(-A.rot_s[j]);
-        float2 v = f2fma(f2b(a), sj, f2mul(f2b(b), cj));
-        float2 q = f2fma(f2b(a), cj, f2mul(f2b(-b), sj));
 #pragma unroll
-        for (int i = 0; i < CS; ++i) {
-            nq[i] = (j == 0) ? v : f2add(nq[i], v);
-            if (i < CS - 1) {
-                const float2 v2 = f2fma(v, rc, f2mul(q, rs));
-                q = f2fma(q, rc, f2mul(v, nrs));
-                v = v2;
+        for (int p = 0; p < P; ++p) {
+            float2 v = f2fma(f2b(a), sj[p], f2mul(f2b(b), cj[p]));
+            float2 q = f2fma(f2b(a), cj[p], f2mul(f2b(-b), sj[p]));
+#pragma unroll
+            for (int i = 0; i < CS; ++i) {
+                nq[p][i] = (j == 0) ? v : f2add(nq[p][i], v);
+                if (i < CS - 1) {
+                    const float2 v2 = f2fma(v, rc, f2mul(q, rs));
+                    q = f2fma(q, rc, f2mul(v, nrs));
+                    v = v2;
+                }
             }
+            const float2 twoc = f2add(c1[p], c1[p]);
+            const float2 sn2 = f2fma(twoc, sj[p], nsjm[p]), cn2 = f2fma(twoc, cj[p], ncjm[p]);
+            nsjm[p] = f2mul(sj[p], f2b(-1.f));
+            ncjm[p] = f2mul(cj[p], f2b(-1.f));
+            sj[p] = sn2;
+            cj[p] = cn2;
         }
-        const float2 sn2 = f2fma(twoc, sj, nsjm), cn2 = f2fma(twoc, cj, ncjm);
-        nsjm = f2mul(sj, f2b(-1.f));
-        ncjm = f2mul(cj, f2b(-1.f));
-        sj = sn2;
-        cj = cn2;
     }
 }
 
 // One implicit-midpoint step of this warp's particle: (m, u) in/out.
-// R0sm: this warp's [CS][32] float2 scratch for R0 = (M - mu dt/2 K) m0.
-template <int CS>
-__device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[CS], float2 (&u)[CS],
-                                      float2* R0sm, const float* wq, float2 s1, float2 c1, int& iters, int& flags) {
+// R0sm: this warp's [P][CS][32] float2 scratch for R0 = (M - mu dt/2 K) m0.
+template <int CS, int P>
+__device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
+                                      float2 (&u)[P][CS], float2* R0sm, const float* wq, const float2 (&s1)[P],
+                                      const float2 (&c1)[P], int& iters, int& flags) {
     const int lane = threadIdx.x & 31;
     // W0 = dt/8 u0 + dU/4 (registers) and R0 (shared memory), fixed for the step
-    float2 W0[CS];
+    float2 W0[P][CS];
     {
-        wnoise<CS>(A, wq, s1, c1, W0);
+        wnoise<CS, P>(A, wq, s1, c1, W0);
         const float2 dt8 = f2b(A.dt8);
-#pragma unroll
-        for (int i = 0; i < CS; ++i) W0[i] = f2fma(dt8, u[i], W0[i]);
         float2 lo, hi;
-        whalo<CS>(m, lo, hi);
+        whalo<CS, P>(m, lo, hi);
         const float2 c0p = f2b(A.c0p), b0p = f2b(A.b0p);
 #pragma unroll
-        for (int i = 0; i < CS; ++i) {
-            const float2 l = (i == 0) ? lo : m[i - 1];
-            const float2 r = (i == CS - 1) ? hi : m[i + 1];
-            R0sm[i * 32 + lane] = f2fma(c0p, f2add(l, r), f2mul(b0p, m[i]));
-        }
-    }
-    float2 mi[CS];
+        for (int p = 0; p < P; ++p)
 #pragma unroll
-    for (int i = 0; i < CS; ++i) mi[i] = m[i];
+            for (int i = 0; i < CS; ++i) {
+                W0[p][i] = f2fma(dt8, u[p][i], W0[p][i]);
+                R0sm[(p * CS + i) * 32 + lane] =
+                    f2fma(c0p, f2add(wleft<CS, P>(m, p, i, lo), wright<CS, P>(m, p, i, hi)), f2mul(b0p, m[p][i]));
+            }
+    }
+    float2 mi[P][CS];
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int i = 0; i < CS; ++i) mi[p][i] = m[p][i];
     const float2 dt8 = f2b(A.dt8);
     for (int it = 1;; ++it) {
         // rhs_i = R0_i + w_{i-1} g_{i-1} - w_{i+1} g_i,  w = W0 + dt/8 u_it,  g_i = mb2_i + mb2_{i+1}
-        float2 x[CS];
+        float2 x[P][CS];
         {
-            float2 w[CS], mb[CS];
+            float2 w[P][CS], mb[P][CS];
 #pragma unroll
-            for (int i = 0; i < CS; ++i) {
-                w[i] = f2fma(dt8, u[i], W0[i]);
-                mb[i] = f2add(m[i], mi[i]);
-            }
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int i = 0; i < CS; ++i) {
+                    w[p][i] = f2fma(dt8, u[p][i], W0[p][i]);
+                    mb[p][i] = f2add(m[p][i], mi[p][i]);
+                }
             float2 wl, wr, ml, mr;
-            whalo<CS>(w, wl, wr);
-            whalo<CS>(mb, ml, mr);
-            float2 gp = f2add(ml, mb[0]);
+            whalo<CS, P>(w, wl, wr);
+            whalo<CS, P>(mb, ml, mr);
 #pragma unroll
-            for (int i = 0; i < CS; ++i) {
-                const float2 wprev = (i == 0) ? wl : w[i - 1];
-                const float2 wnext = (i == CS - 1) ? wr : w[i + 1];
-                const float2 g = f2add(mb[i], (i == CS - 1) ? mr : mb[i + 1]);
-                x[i] = f2sub(f2fma(wprev, gp, R0sm[i * 32 + lane]), f2mul(wnext, g));
-                gp = g;
+            for (int p = 0; p < P; ++p) {
+                float2 gp = f2add(wleft<CS, P>(mb, p, 0, ml), mb[p][0]);
+#pragma unroll
+                for (int i = 0; i < CS; ++i) {
+                    const float2 g = f2add(mb[p][i], wright<CS, P>(mb, p, i, mr));
+                    x[p][i] = f2sub(f2fma(wleft<CS, P>(w, p, i, wl), gp, R0sm[(p * CS + i) * 32 + lane]),
+                                    f2mul(wright<CS, P>(w, p, i, wr), g));
+                    gp = g;
+                }
             }
         }
         // (M + mu dt/2 K) m_new = rhs
-        float2 pd, de, E, F;
+        float2 pd[P], de[P], E[P], F[P];
         float Ep, Fn;
-        wsweep<CS>(W.pic, x, pd, de);
-        wreduced(W.pic, W.rpic, pd, de, E, F, Ep, Fn);
-        float2 mn[CS];
-        wback<CS>(W.pic, x, F, E, mn);
+        wsweep<CS, P>(W.pic, x, pd, de);
+        wreduced<P>(W.pic, W.rpic, pd, de, E, F, Ep, Fn);
+        float2 mn[P][CS];
+        wback<CS, P>(W.pic, x, F, E, mn);
         float dmax = 0.f, mmax = 0.f;
 #pragma unroll
-        for (int i = 0; i < CS; ++i) {
-            const float2 d = f2sub(mn[i], mi[i]);
-            dmax = fmax3_nan(dmax, fabsf(d.x), fabsf(d.y));
-            mmax = fmaxf(mmax, fmaxf(fabsf(mn[i].x), fabsf(mn[i].y)));
-            mi[i] = mn[i];
-        }
-        // u_new = H^{-1} M m_new, the mass product's chunk ends from the reduced solve
-        {
-            const float2 lo = make_float2(Ep, E.x), hi = make_float2(F.y, Fn);
-            const float2 four = f2b(4.f);
+        for (int p = 0; p < P; ++p)
 #pragma unroll
             for (int i = 0; i < CS; ++i) {
-                const float2 l = (i == 0) ? lo : mn[i - 1];
-                const float2 r = (i == CS - 1) ? hi : mn[i + 1];
-                x[i] = f2fma(four, mn[i], f2add(l, r));
+                const float2 d = f2sub(mn[p][i], mi[p][i]);
+                dmax = fmax3_nan(dmax, fabsf(d.x), fabsf(d.y));
+                mmax = fmaxf(mmax, fmaxf(fabsf(mn[p][i].x), fabsf(mn[p][i].y)));
+                mi[p][i] = mn[p][i];
             }
-            float2 hpd, hde, hE, hF;
+        // u_new = H^{-1} M m_new, the mass product's chunk ends from the reduced solve
+        {
+            float2 lo, hi;
+            wsolved_halo<P>(E, F, Ep, Fn, lo, hi);
+            const float2 four = f2b(4.f);
+#pragma unroll
+            for (int p = 0; p < P; ++p)
+#pragma unroll
+                for (int i = 0; i < CS; ++i)
+                    x[p][i] = f2fma(four, mn[p][i], f2add(wleft<CS, P>(mn, p, i, lo), wright<CS, P>(mn, p, i, hi)));
+            float2 hpd[P], hde[P], hE[P], hF[P];
             float hEp, hFn;
-            wsweep<CS>(W.hel, x, hpd, hde);
-            wreduced(W.hel, W.rhel, hpd, hde, hE, hF, hEp, hFn);
-            wback<CS>(W.hel, x, hF, hE, u);
+            wsweep<CS, P>(W.hel, x, hpd, hde);
+            wreduced<P>(W.hel, W.rhel, hpd, hde, hE, hF, hEp, hFn);
+            wback<CS, P>(W.hel, x, hF, hE, u);
         }
         iters++;
         const float dm = warp_max_nan(dmax);
@@ -274,47 +349,58 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
         }
     }
 #pragma unroll
-    for (int i = 0; i < CS; ++i) m[i] = mi[i];
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int i = 0; i < CS; ++i) m[p][i] = mi[p][i];
 }
 
-// this lane's 2 CS nodes of a particle row <-> the paired registers
-template <int CS>
-__device__ __forceinline__ void wload(const float* row, float2 (&v)[CS]) {
-    const float4* p = reinterpret_cast<const float4*>(row + (threadIdx.x & 31) * 2 * CS);
+// this lane's LN = 2 P CS nodes of a particle row <-> the paired registers:
+// sub-chunk s < P is stream s's .x, sub-chunk s >= P is stream s - P's .y
+template <int CS, int P>
+__device__ __forceinline__ void wload(const float* row, float2 (&v)[P][CS]) {
+    const float4* q4 = reinterpret_cast<const float4*>(row + (threadIdx.x & 31) * 2 * P * CS);
 #pragma unroll
-    for (int q = 0; q < CS / 4; ++q) {
-        const float4 a = p[q], b = p[CS / 4 + q];
-        v[4 * q + 0] = make_float2(a.x, b.x);
-        v[4 * q + 1] = make_float2(a.y, b.y);
-        v[4 * q + 2] = make_float2(a.z, b.z);
-        v[4 * q + 3] = make_float2(a.w, b.w);
-    }
+    for (int s = 0; s < 2 * P; ++s)
+#pragma unroll
+        for (int q = 0; q < CS / 4; ++q) {
+            const float4 a = q4[s * (CS / 4) + q];
+            const float e[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (s < P) v[s][4 * q + k].x = e[k];
+                else v[s - P][4 * q + k].y = e[k];
+            }
+        }
 }
 
-template <int CS>
-__device__ __forceinline__ void wstore(float* row, const float2 (&v)[CS]) {
-    float4* p = reinterpret_cast<float4*>(row + (threadIdx.x & 31) * 2 * CS);
+template <int CS, int P>
+__device__ __forceinline__ void wstore(float* row, const float2 (&v)[P][CS]) {
+    float4* q4 = reinterpret_cast<float4*>(row + (threadIdx.x & 31) * 2 * P * CS);
 #pragma unroll
-    for (int q = 0; q < CS / 4; ++q) {
-        p[q] = make_float4(v[4 * q].x, v[4 * q + 1].x, v[4 * q + 2].x, v[4 * q + 3].x);
-        p[CS / 4 + q] = make_float4(v[4 * q].y, v[4 * q + 1].y, v[4 * q + 2].y, v[4 * q + 3].y);
-    }
+    for (int s = 0; s < 2 * P; ++s)
+#pragma unroll
+        for (int q = 0; q < CS / 4; ++q) {
+            float e[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e[k] = (s < P) ? v[s][4 * q + k].x : v[s - P][4 * q + k].y;
+            q4[s * (CS / 4) + q] = make_float4(e[0], e[1], e[2], e[3]);
+        }
 }
 
 // observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this lane's nodes;
 // node mod stride and the observation index advance node by node
-template <int CS>
-__device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float2 (&u)[CS], const float* y) {
-    const int base = (threadIdx.x & 31) * 2 * CS;
+template <int CS, int P>
+__device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float2 (&u)[P][CS], const float* y) {
+    const int base = (threadIdx.x & 31) * 2 * P * CS;
     double acc = 0.0;
     int rem = base % A.stride;
     int j = base / A.stride + (rem != 0);
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int s = 0; s < 2 * P; ++s) {
 #pragma unroll
         for (int i = 0; i < CS; ++i) {
             if (rem == 0) {
-                const float r = ((c ? u[i].y : u[i].x) - y[j]) * A.sigma_inv;
+                const float r = (((s < P) ? u[s][i].x : u[s - P][i].y) - y[j]) * A.sigma_inv;
                 acc += (double)r * (double)r;
                 ++j;
             }
@@ -324,45 +410,48 @@ __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float
     return acc;
 }
 
-// sin and cos of the angles of this lane's first X and Y nodes
-template <int CS>
-__device__ __forceinline__ void wangles(int n, float2& s1, float2& c1) {
-    const int base = (threadIdx.x & 31) * 2 * CS;
-    float sx, cx, sy, cy;
-    node_angle<float>(base, n, sx, cx);
-    node_angle<float>(base + CS, n, sy, cy);
-    s1 = make_float2(sx, sy);
-    c1 = make_float2(cx, cy);
+// sin and cos of the angles of the first nodes of stream p's sub-chunks p and p + P
+template <int CS, int P>
+__device__ __forceinline__ void wangles(int n, float2 (&s1)[P], float2 (&c1)[P]) {
+    const int base = (threadIdx.x & 31) * 2 * P * CS;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        float sx, cx, sy, cy;
+        node_angle<float>(base + p * CS, n, sx, cx);
+        node_angle<float>(base + (p + P) * CS, n, sy, cy);
+        s1[p] = make_float2(sx, sy);
+        c1[p] = make_float2(cx, cy);
+    }
 }
 
-template <int CS>
+template <int CS, int P>
 __host__ __device__ constexpr size_t wsmem_base() {
-    return (size_t)CS * 32 * sizeof(float2);
+    return (size_t)P * CS * 32 * sizeof(float2);
 }
 
 // Occupancy: 8 one-warp CTAs per SM (255 registers a thread)
 constexpr int WMINB = 8;
 
-template <int CS>
+template <int CS, int P>
 __global__ void __launch_bounds__(32, WMINB) wwindow_kernel(ModelArgs<float> A, WArgs W, WindowIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* R0sm = reinterpret_cast<float2*>(smem_raw);
-    float* noise = reinterpret_cast<float*>(smem_raw + wsmem_base<CS>());
+    float* noise = reinterpret_cast<float*>(smem_raw + wsmem_base<CS, P>());
     const int p = blockIdx.x;
     const size_t NK = (size_t)io.Ns * A.K;
     stage_noise(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
-    float2 s1, c1;
-    wangles<CS>(A.n, s1, c1);
-    float2 m[CS], u[CS];
-    wload<CS>(io.m_in + (size_t)p * A.n, m);
-    wu_from_m<CS>(W, m, u);
+    float2 s1[P], c1[P];
+    wangles<CS, P>(A.n, s1, c1);
+    float2 m[P][CS], u[P][CS];
+    wload<CS, P>(io.m_in + (size_t)p * A.n, m);
+    wu_from_m<CS, P>(W, m, u);
     __syncwarp();
     int iters = 0, flags = 0;
-    for (int s = 0; s < io.Ns; ++s) wstep<CS>(A, W, m, u, R0sm, noise + s * A.K, s1, c1, iters, flags);
-    wstore<CS>(io.m_out + (size_t)p * A.n, m);
-    wstore<CS>(io.u_out + (size_t)p * A.n, u);
+    for (int s = 0; s < io.Ns; ++s) wstep<CS, P>(A, W, m, u, R0sm, noise + s * A.K, s1, c1, iters, flags);
+    wstore<CS, P>(io.m_out + (size_t)p * A.n, m);
+    wstore<CS, P>(io.u_out + (size_t)p * A.n, u);
     if (io.y) {
-        double mis = warp_sum(wmisfit<CS>(A, u, io.y));
+        double mis = warp_sum(wmisfit<CS, P>(A, u, io.y));
         double gl = warp_sum(window_girsanov(A, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns));
         if (threadIdx.x == 0) {
             io.nll[p] = 0.5 * mis;
@@ -378,22 +467,22 @@ __global__ void __launch_bounds__(32, WMINB) wwindow_kernel(ModelArgs<float> A, 
 // PCN jittering (Sec. 3.1.2): n_iter proposals dW' = rho dW + sqrt(1 - rho^2)
 // sqrt(dt) z of the window noise, each run through the window from m_start
 // and accepted with probability min(1, exp(w0 - w1)), w = theta (NLL - log G).
-template <int CS>
+template <int CS, int P>
 __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, WArgs W, JitterIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* R0sm = reinterpret_cast<float2*>(smem_raw);
     const int p = blockIdx.x;
     const int lane = threadIdx.x;
     const int Ns = io.Ns, K = A.K, NK = Ns * K;
-    float* noise = reinterpret_cast<float*>(smem_raw + wsmem_base<CS>());
+    float* noise = reinterpret_cast<float*>(smem_raw + wsmem_base<CS, P>());
     float* cur = noise + NK;
     float* prop = noise + 2 * NK;
     float* dW = io.dW + (size_t)p * NK;
     const float* lam = io.lam ? io.lam + (size_t)p * NK : nullptr;
     for (int q = lane; q < NK; q += 32) cur[q] = dW[q];
     double nll0 = io.nll[p], lg0 = io.logG ? io.logG[p] : 0.0;
-    float2 s1, c1;
-    wangles<CS>(A.n, s1, c1);
+    float2 s1[P], c1[P];
+    wangles<CS, P>(A.n, s1, c1);
     const float sq = io.sq1mr2 * (float)sqrt(A.dt_d);
     const int nblk = (K + 3) >> 2;
     int iters = 0, flags = 0, n_acc = 0, changed = 0;
@@ -412,13 +501,13 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
         }
         __syncwarp();
         stage_noise(A, noise, prop, lam, Ns);
-        float2 m[CS], u[CS];
-        wload<CS>(io.m_start + (size_t)p * A.n, m);
-        wu_from_m<CS>(W, m, u);
+        float2 m[P][CS], u[P][CS];
+        wload<CS, P>(io.m_start + (size_t)p * A.n, m);
+        wu_from_m<CS, P>(W, m, u);
         __syncwarp();
         int fl = 0;
-        for (int s = 0; s < Ns; ++s) wstep<CS>(A, W, m, u, R0sm, noise + s * K, s1, c1, iters, fl);
-        const double mis = warp_sum(wmisfit<CS>(A, u, io.y));
+        for (int s = 0; s < Ns; ++s) wstep<CS, P>(A, W, m, u, R0sm, noise + s * K, s1, c1, iters, fl);
+        const double mis = warp_sum(wmisfit<CS, P>(A, u, io.y));
         const double gl = warp_sum(window_girsanov(A, prop, lam, Ns));
         const double nll1 = 0.5 * mis, lg1 = -gl;
         int acc = 0;
@@ -433,8 +522,8 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
             nll0 = nll1;
             lg0 = lg1;
             for (int q = lane; q < NK; q += 32) cur[q] = prop[q];
-            wstore<CS>(io.m_end + (size_t)p * A.n, m);
-            wstore<CS>(io.u_end + (size_t)p * A.n, u);
+            wstore<CS, P>(io.m_end + (size_t)p * A.n, m);
+            wstore<CS, P>(io.u_end + (size_t)p * A.n, u);
             n_acc++;
             changed = 1;
         }
