@@ -179,21 +179,48 @@ def barrier(ws: int):
 # ---------------------------------------------------------------------- #
 # CPU baseline: the FP64 oracle, as it stands, on a bounded sample
 # ---------------------------------------------------------------------- #
-def oracle_sample(cfg, budget_s: float = 12.0, min_particles: int = 1):
+def oracle_sample(cfg, budget_s: float = 12.0, min_particles: int = 1, first: int = 0, count: int = 64):
+    """The oracle's window propagation (FP64, one thread) of particles first .. first+count-1
+    of a seeded sample, for about budget_s seconds.  Returns (steps/s, description, seconds, steps)."""
     import numpy as np
     from oracle.model import Model
     from workloads import mode_amplitudes, random_increments, random_state
     om = Model(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg))
-    u0 = random_state(cfg, 64, 123)
-    dW = random_increments(cfg, 64, 124)
+    u0 = random_state(cfg, first + count, 123)
+    dW = random_increments(cfg, first + count, 124)
     t0 = time.perf_counter()
     done = 0
-    while done < 64 and (done < min_particles or time.perf_counter() - t0 < budget_s):
-        m0 = om.m_from_u(u0[done])
-        om.window(m0, dW[done])
+    while done < count and (done < min_particles or time.perf_counter() - t0 < budget_s):
+        m0 = om.m_from_u(u0[first + done])
+        om.window(m0, dW[first + done])
         done += 1
     el = time.perf_counter() - t0
-    return done * cfg.Ns / el, f"oracle window propagation (FP64, one thread) of {done} particles x {cfg.Ns} steps of the n={cfg.n} workload", el
+    return done * cfg.Ns / el, (f"oracle window propagation (FP64, one thread) of {done} particles x {cfg.Ns} "
+                                f"steps of the n={cfg.n} workload"), el, done * cfg.Ns
+
+
+def _oracle_worker(job):
+    name, budget_s, first, count = job
+    from workloads import get_config
+    _, _, el, steps = oracle_sample(get_config(name), budget_s=budget_s, min_particles=1, first=first, count=count)
+    return steps, el
+
+
+def oracle_parallel(name, budget_s: float = 10.0, per_core: int = 512):
+    """The oracle on every host core: particles split across processes (started with spawn),
+    as the paper splits its ensemble across ranks.  Returns (steps/s, cores, description)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    # one thread per process: the processes are the parallelism
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    jobs = [(name, budget_s, c * per_core, per_core) for c in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    steps = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return steps / wall, cores, (f"oracle window propagation (FP64) on {cores} processes, particles split across "
+                                 f"them, {steps} particle-steps of the n=1024 workload in {wall:.1f} s")
 
 
 def run_reference(args):
@@ -208,17 +235,19 @@ def run_reference(args):
     rates = []
     t_all = 0.0
     sample = ""
+    cores = 1
     for _ in range(args.steps):
-        r, sample, el = oracle_sample(cfg, budget_s=8.0, min_particles=1)
+        t0 = time.perf_counter()
+        r, cores, sample = oracle_parallel(WORKLOAD, budget_s=6.0)
         rates.append(r)
-        t_all += el
+        t_all += time.perf_counter() - t0
     value = statistics.mean(rates)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n": cfg.n, "N": cfg.N, "Ns": cfg.Ns, "K": cfg.K},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -339,8 +368,10 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, sample, _ = oracle_sample(cfg, budget_s=12.0)
-        cpu = {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": sample}
+        v1, sample1, _, _ = oracle_sample(cfg, budget_s=8.0)
+        v, cores, sample = oracle_parallel(WORKLOAD, budget_s=8.0)
+        cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
+               "single_core": {"value": v1, "sample": sample1}}
 
     if rank == 0:
         line = {
@@ -356,7 +387,7 @@ def run_ours(args):
                        "mean_tempering_stages": statistics.mean(stages),
                        "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
-            "roofline": {"bound": "alu", "kernel": ("wjitter_kernel<16> (one warp per particle, EA)" if g.layout == "warp"
+            "roofline": {"bound": "alu", "kernel": ("wjitter_kernel<8,2> (one warp per particle, EA)" if g.layout == "warp"
                                     else f"jitter_kernel<float,8,128,{solver.upper()}>"),
                          "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": jitter_traffic(),
@@ -417,6 +448,96 @@ def run_nudging(args):
     return 0
 
 
+# Algorithmic flops per node of the reverse-mode adjoint of one converged step
+# (the transpose of the linearised Eq. fde1 solved by a fixed point):
+# per adjoint iteration: right-hand side 1, variable cyclic tridiagonal solve 14,
+# B^T psi 4, Helmholtz solve 6 and mass product 4 of the correction, its scaling 1,
+# convergence 2 -> 32; per step: dv 3, mbar 2, its edge sums 1, the transposed
+# rows 4, dJ/dm of the previous state 6, and the projection on the K modes 2K.
+ADJ_FLOPS_PER_NODE_ITER = 32
+ADJ_FLOPS_PER_NODE_STEP = 16
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12   # 2 DFMA lanes per SM per cycle, max SM clock
+
+
+def run_adjoint(args):
+    """--adjoint: gradient evaluations on the nudging workload (n = 1024, K = 8,
+    20-step windows, N = 256, FP64, checkpoints every 5 steps).  One evaluation is
+    sch_adjoint_window on one particle: the forward window and its reverse-mode
+    adjoint, J and dJ/dlambda, dJ/ddW, dJ/dm0.  Inputs resident, L2 flushed
+    between timed calls, CUDA events; the oracle's gradient (tangent linear,
+    dense Jacobians) is timed on the host beside it."""
+    import torch
+    from workloads import get_config, u0_profile, random_drift
+    from paper_2402_06927_gb300.api import SchModel
+    torch.cuda.set_device(0)
+    cfg = get_config("cfg3_f64")
+    g = SchModel.from_config(cfg)
+    N, Ns, K, n = cfg.N, cfg.Ns, cfg.K, cfg.n
+    u0 = torch.tensor(u0_profile(cfg), dtype=g.dtype, device="cuda")
+    # twin: the truth runs one window from u0; the particles start from the prior around u0
+    mt = g.m_from_u(u0[None].contiguous())
+    tr = g.ensemble_step(mt, g.draw_increments(1, Ns, 21, 5, 0), None)
+    y = g.synth_obs(tr["u"][0].contiguous(), 22, 1)
+    m0, _ = g.prior_sample(N, u0, 23, cfg.prior_scale)
+    dW = g.draw_increments(N, Ns, 24, 1, 0)
+    lam = torch.tensor(random_drift(cfg, N, 25, steps=Ns, scale=0.2), dtype=g.dtype, device="cuda")
+    fwd = g.ensemble_step(m0, dW, lam, y)
+    ws = None
+    for _ in range(max(3, args.warmup)):
+        out = g.adjoint_window(m0, dW, lam, y, ckpt=5)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    times = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        out = g.adjoint_window(m0, dW, lam, y, ckpt=5)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.median(times)
+    assert int(out["status"].abs().sum().item()) == 0, "adjoint status flags"
+    it_fwd = int(fwd["iters"].sum().item())
+    it_adj = int(out["iters"].sum().item()) - it_fwd
+    flops = (step_flops(n, K, "li", it_fwd, N * Ns)
+             + n * (ADJ_FLOPS_PER_NODE_ITER * it_adj + (ADJ_FLOPS_PER_NODE_STEP + 2 * K) * N * Ns))
+    achieved = flops / t / 1e12
+    cpu = None
+    if not args.no_cpu:
+        import numpy as np
+        from oracle.model import Model
+        from oracle import nudge as ON
+        from workloads import mode_amplitudes
+        om = Model(L=cfg.L, n=n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg))
+        m0h, dWh, lamh, yh = (x.double().cpu().numpy() for x in (m0[:4], dW[:4], lam[:4], y))
+        t0 = time.perf_counter()
+        done = 0
+        while done < 4 and (done < 1 or time.perf_counter() - t0 < 20.0):
+            ON.cost_and_gradient(om, m0h[done], dWh[done], lamh[done], yh, cfg.sigma)
+            done += 1
+        el = time.perf_counter() - t0
+        cpu = {"value": done / el, "unit": "gradient evaluations/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle J and dJ/dlambda by tangent linearisation (dense Jacobians, FP64, one thread) "
+                         f"for {done} particles of the same inputs"}
+    line = {
+        "metric": "gradient evaluations/s", "value": N / t, "unit": "gradient evaluations/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "adjoint window: n=1024 K=8 Ns=20 N=256 (FP64, LI Picard, checkpoints every 5 steps)",
+                   "l2": "flushed between timed calls (256 MB write)",
+                   "forward_picard_iters_per_step": it_fwd / (N * Ns), "adjoint_iters_per_step": it_adj / (N * Ns)},
+        "roofline": {"bound": "alu", "kernel": "adjoint_kernel<double,4,256,LI>", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_note": "FP64 pipe 152 SMs x 2 DFMA lanes x 2 x max SM clock; recomputation from "
+                                  "checkpoints is not credited"},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,6 +547,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--nudging", action="store_true",
                     help="learned vs optimiser nudging comparison instead of the default workload")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the reverse-mode adjoint (gradient evaluations) on the nudging workload")
     ap.add_argument("--train-cycles", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=10)
     args = ap.parse_args()
@@ -433,6 +556,10 @@ def main():
         if args.steps == 100:
             args.steps = 20
         return run_nudging(args)
+    if args.adjoint:
+        if args.steps == 100:
+            args.steps = 10
+        return run_adjoint(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
