@@ -56,8 +56,8 @@ JITTER_SOURCES = ["paper_2402_06927_gb300/csrc/sch_warp.cuh", "paper_2402_06927_
                   "paper_2402_06927_gb300/csrc/sch_internal.h", "paper_2402_06927_gb300/csrc/sch_device.cuh",
                   "paper_2402_06927_gb300/csrc/sch_window_warp.cu"]
 JITTER_TRAFFIC_BYTES = {
-    # wjitter_kernel<16>, profiles/wjitter_kernel_cfg2_n1024_N1024.md: 4.625408 MB read, 0 written
-    "03603b1da549b2a07e5b107c4f72f79b833396ee": 4625408,
+    # wjitter_kernel<8,2>, profiles/wjitter_kernel_cfg2_n1024_N1024.md: 4.609536 MB read, 0 written
+    "046260e88682dedabd37446960a1bf9d4d68bbc1": 4609536,
 }
 
 
@@ -538,6 +538,39 @@ def run_adjoint(args):
     return 0
 
 
+def run_occupancy(args):
+    """--occupancy: one jitter launch of the bench workload (10 PCN proposals of a
+    10-step window, n = 1024, K = 8, FP32) at N = 152 .. 2432 particles, i.e. 1 .. 16
+    warps per SM in the warp layout; best of --steps timed launches (CUDA events) each."""
+    import torch
+    from workloads import get_config, u0_profile
+    from paper_2402_06927_gb300.api import SchModel
+    torch.cuda.set_device(0)
+    cfg = get_config(WORKLOAD)
+    g = SchModel.from_config(cfg)
+    u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
+    y = g.synth_obs(u0, 1, 1)
+    rows = []
+    for N in (152, 304, 608, 912, 1216, 1824, 2432):
+        m0, _ = g.prior_sample(N, u0, 3, cfg.prior_scale)
+        dW = g.draw_increments(N, cfg.Ns, 5, 1, 0)
+        st = g.ensemble_step(m0, dW, None, y)
+        nll, logG = st["nll"].clone(), st["logG"].clone()
+        ms = []
+        for rep in range(max(2, args.steps) + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, it, _ = g.jitter(m0, dW, None, y, nll, logG, st["m"], st["u"], 0.5, cfg.rho, 10, 9, rep * 10,
+                                want_iters=True)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        rows.append({"N": N, "warps_per_sm": N / 152, "ms_per_launch": min(ms[1:]),
+                     "picard_iters_per_step": it.float().mean().item() / (10 * cfg.Ns)})
+    print(json.dumps({"occupancy_sweep": rows, "kernel": f"wjitter ({g.layout} layout)"}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -549,6 +582,8 @@ def main():
                     help="learned vs optimiser nudging comparison instead of the default workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the reverse-mode adjoint (gradient evaluations) on the nudging workload")
+    ap.add_argument("--occupancy", action="store_true",
+                    help="jitter launch time at 1 .. 16 warps per SM (occupancy sweep)")
     ap.add_argument("--train-cycles", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=10)
     args = ap.parse_args()
@@ -556,6 +591,10 @@ def main():
         if args.steps == 100:
             args.steps = 20
         return run_nudging(args)
+    if args.occupancy:
+        if args.steps == 100:
+            args.steps = 4
+        return run_occupancy(args)
     if args.adjoint:
         if args.steps == 100:
             args.steps = 10
