@@ -538,6 +538,140 @@ def run_adjoint(args):
     return 0
 
 
+def _event_time(fn, reps, flush=None):
+    """Median device time of fn() over reps calls (CUDA events; L2 flushed before each if given)."""
+    import torch
+    st = torch.cuda.current_stream()
+    ts = []
+    for k in range(reps):
+        if flush is not None:
+            flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        fn()
+        e1.record(st)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return statistics.median(ts)
+
+
+def _host_time(fn, budget_s=3.0, min_reps=1):
+    t0 = time.perf_counter()
+    reps = 0
+    while reps < min_reps or time.perf_counter() - t0 < budget_s:
+        fn()
+        reps += 1
+    return (time.perf_counter() - t0) / reps
+
+
+def run_filter_kernels(args):
+    """--filter-kernels: the filter steps between the model runs, at the bench ensemble
+    size (N = 1024) and the large one (N = 8192, n = 4096): adaptive tempering (a search
+    and a whole-step call), systematic resampling, and the row gather that copies the
+    resampled particles (HBM-bound, against the measured copy bandwidth).  Device times
+    by CUDA events (median, L2 flushed before each call); the oracle's steps timed on one
+    host core beside them."""
+    import numpy as np
+    import torch
+    from oracle import filter as OF
+    from workloads import random_logweights
+    from paper_2402_06927_gb300 import api
+    torch.cuda.set_device(0)
+    hbm = _peaks().get("hbm_gbs", 6800.0)   # measured copy bandwidth, else the earlier GB300 measurement
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    reps = max(5, args.steps)
+    out = []
+    for N, n in ((1024, 1024), (8192, 4096)):
+        for label, spread in (("search", 40.0), ("whole step", 0.002)):
+            phi = random_logweights(N, N + 1, spread)
+            nll = torch.tensor(phi, dtype=torch.float64, device="cuda")
+            wbar, res = api.pf_temper(nll, None, 0.0, 0.5 * N)
+            t = _event_time(lambda: api.pf_temper(nll, None, 0.0, 0.5 * N, wbar, res), reps, flush)
+            th = _host_time(lambda: OF.temper(phi, 0.0, 0.5 * N), 2.0)
+            out.append({"step": f"temper ({label})", "N": N, "device_us": 1e6 * t, "oracle_us": 1e6 * th,
+                        "dtheta": float(res[0].item()), "bound": "FP64 exp and cluster-barrier latency"})
+        wb = wbar.double()
+        idx = torch.empty(N, dtype=torch.int32, device="cuda")
+        t = _event_time(lambda: api.pf_resample(wb, 7, 3, idx=idx), reps, flush)
+        wh = wb.cpu().numpy()
+        u53 = OF.resample_offset(7, 3)
+        th = _host_time(lambda: OF.systematic_resample(wh, u53), 2.0)
+        out.append({"step": "systematic resampling (indices)", "N": N, "device_us": 1e6 * t, "oracle_us": 1e6 * th,
+                    "bound": "latency (one CTA: integer scan and N searches)"})
+        src = torch.randn(N, n, device="cuda")
+        dst = torch.empty_like(src)
+        t = _event_time(lambda: api.pf_gather_rows(idx, src, dst), reps, flush)
+        nbytes = 2 * N * n * 4
+        srch = src.cpu().numpy()
+        ih = idx.cpu().numpy()
+        th = _host_time(lambda: srch[ih], 2.0)
+        out.append({"step": "row gather (m rows)", "N": N, "row_bytes": n * 4, "device_us": 1e6 * t,
+                    "oracle_us": 1e6 * th, "bound": "hbm", "achieved_gbs": nbytes / t / 1e9, "peak_gbs": hbm,
+                    "frac": nbytes / t / 1e9 / hbm})
+    print(json.dumps({"filter_kernels": out, "peak_note": "peak_gbs: measured copy bandwidth (MEASURED_PEAKS.json)",
+                      "oracle_cores": 1}))
+    return 0
+
+
+def run_proposal(args):
+    """--proposal: the learned proposal network at the learned-proposal workload's size
+    (n = 1024, K = 16, Ns = 20, M = 64, 64 channels) on a batch of B = 1024 particles:
+    nn_forward, nn_backward (loss and all gradients) and nn_adam_step.  Algorithmic flops
+    are the multiply-adds of the convolutions, the Fourier-mode projection and the head
+    (2 per multiply-add); the kernels are FP32 SGEMMs on the FMA pipe.  The FP64 oracle
+    network is timed on one host core beside them."""
+    import numpy as np
+    import torch
+    from workloads import get_config
+    from oracle import convnet as OC
+    from paper_2402_06927_gb300.api import ProposalNet
+    torch.cuda.set_device(0)
+    cfg = get_config("cfg4_f32")
+    n, K, Ns, M, C, B = cfg.n, cfg.K, cfg.Ns, cfg.M, 64, 1024
+    net = ProposalNet(n, K, Ns, M, cfg.sigma, C=C, seed=1)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    u = (0.3 * torch.randn(B, n, generator=g)).cuda()
+    y = (0.3 * torch.randn(M, generator=g)).cuda()
+    tgt = (0.1 * torch.randn(B, Ns, K, generator=g)).cuda()
+    P = n // 16
+    conv = sum(2 * (n >> (l + 1)) * C * (2 if l == 0 else C) * 5 for l in range(4))
+    fwd = B * (conv + 2 * C * P * K + 2 * (C * K) * (K * Ns))
+    # backward: dW of every layer, dX of layers 2..4, the mode projection and the head twice
+    conv_dx = sum(2 * (n >> (l + 1)) * C * C * 5 for l in range(1, 4))
+    bwd = B * (conv + conv_dx + 2 * C * P * K + 2 * 2 * (C * K) * (K * Ns))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        net.forward(u, y)
+        net.loss_and_grad(u, y, tgt)
+    reps = max(5, args.steps)
+    tf = _event_time(lambda: net.forward(u, y), reps, flush)
+    tb = _event_time(lambda: net.loss_and_grad(u, y, tgt), reps, flush)
+    _, gr = net.loss_and_grad(u, y, tgt)
+    ta = _event_time(lambda: net.adam_step(gr), reps, flush)
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    p_np = OC.init_params(C, K, Ns, n, 1)
+    x0 = OC.features(u[:4].double().cpu().numpy(), y.double().cpu().numpy(), cfg.sigma)
+    tho_f = _host_time(lambda: OC.forward(p_np, x0, K, Ns), 2.0) / 4
+    tho_b = _host_time(lambda: OC.loss_and_grad(p_np, x0, tgt[:4].double().cpu().numpy(), K, Ns), 2.0) / 4
+    line = {
+        "metric": "network samples/s (forward)", "value": B / tf, "unit": "samples/s", "n_gpus": 1, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"learned proposal: n={n} K={K} Ns={Ns} M={M} C={C}, batch {B}",
+                   "l2": "flushed before each timed call (256 MB write)"},
+        "forward": {"ms": 1e3 * tf, "tflops": fwd / tf / 1e12, "frac": fwd / tf / 1e12 / peak},
+        "backward": {"ms": 1e3 * tb, "tflops": bwd / tb / 1e12, "frac": bwd / tb / 1e12 / peak},
+        "adam_ms": 1e3 * ta,
+        "roofline": {"bound": "alu", "kernel": "sgemm_kernel (nn_forward)", "achieved": fwd / tf / 1e12,
+                     "peak": peak, "unit": "TFLOP/s", "frac": fwd / tf / 1e12 / peak, "traffic": None,
+                     "peak_note": "FP32 FMA pipe 152 SMs x 128 lanes x 2 x max SM clock"},
+        "cpu_baseline": {"value": 1.0 / tho_f, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                         "sample": "FP64 oracle network forward on 4 samples (one thread); backward "
+                                   f"{1.0 / tho_b:.1f} samples/s"},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_occupancy(args):
     """--occupancy: one jitter launch of the bench workload (10 PCN proposals of a
     10-step window, n = 1024, K = 8, FP32) at N = 152 .. 2432 particles, i.e. 1 .. 16
@@ -582,6 +716,10 @@ def main():
                     help="learned vs optimiser nudging comparison instead of the default workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the reverse-mode adjoint (gradient evaluations) on the nudging workload")
+    ap.add_argument("--filter-kernels", action="store_true",
+                    help="time tempering, resampling and the row gather against their bounds")
+    ap.add_argument("--proposal", action="store_true",
+                    help="time the learned proposal network (forward, backward, Adam)")
     ap.add_argument("--occupancy", action="store_true",
                     help="jitter launch time at 1 .. 16 warps per SM (occupancy sweep)")
     ap.add_argument("--train-cycles", type=int, default=200)
@@ -591,6 +729,14 @@ def main():
         if args.steps == 100:
             args.steps = 20
         return run_nudging(args)
+    if args.filter_kernels:
+        if args.steps == 100:
+            args.steps = 20
+        return run_filter_kernels(args)
+    if args.proposal:
+        if args.steps == 100:
+            args.steps = 20
+        return run_proposal(args)
     if args.occupancy:
         if args.steps == 100:
             args.steps = 4

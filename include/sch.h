@@ -93,7 +93,9 @@ typedef struct {
     int32_t K;           /* number of SALT mode functions (even) */
     double amps[SCH_MAX_K / 2];  /* a_j, j = 1..K/2: xi_{2j-2} = a_j sin(2 pi j x/L),
                                     xi_{2j-1} = a_j cos(2 pi j x/L) */
-    int32_t M;           /* observation points x_j = j L / M (on nodes) */
+    int32_t M;           /* observation points x_j = j L / M (on nodes); in every
+                            observation vector y [M] an entry that is NaN is not
+                            observed (e.g. Exp 2's half domain, Sec. 4) */
     double sigma;        /* observation noise standard deviation */
     double tol;          /* Picard stop: max|dm| <= tol * max(1, max|m|) */
     int32_t max_iter;    /* Picard iteration limit per step */

@@ -8,6 +8,7 @@ how close the proposal lands to the observations.  Not in the paper.
 
 Network (all convolutions circular, kernel 5, stride 2, padding 2):
     features  x0[0] = u_start,  x0[1] = (y_j - u_start(x_j)) / sigma at node j n/M, 0 elsewhere
+              and at unobserved points (y_j NaN)
     conv1     2 -> C channels,  n -> n/2,   ReLU
     conv2     C -> C,           n/2 -> n/4, ReLU
     conv3     C -> C,           n/4 -> n/8, ReLU
@@ -49,14 +50,17 @@ def init_params(C: int, K: int, Ns: int, n: int, seed: int):
 
 
 def features(u_start: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:
-    """x0 [B, 2, n] from the start velocities [B, n] and the window observations [M]."""
+    """x0 [B, 2, n] from the start velocities [B, n] and the window observations [M]
+    (an unobserved point, y_j NaN, has innovation 0)."""
     u = np.atleast_2d(np.asarray(u_start, dtype=np.float64))
     B, n = u.shape
+    y = np.asarray(y, dtype=np.float64)
     M = len(y)
     stride = n // M
     x = np.zeros((B, 2, n))
     x[:, 0] = u
-    x[:, 1, ::stride] = (np.asarray(y)[None, :] - u[:, ::stride]) / sigma
+    inn = (y[None, :] - u[:, ::stride]) / sigma
+    x[:, 1, ::stride] = np.where(np.isnan(y)[None, :], 0.0, inn)
     return x
 
 

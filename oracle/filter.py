@@ -7,7 +7,8 @@ Sec. 3 of the paper: likelihood weights (Eq. loglikeq), effective sample size
 (Eq. girsanov DG approx) and the diagnostics EMRE, RB, RES (Sec. 4.1.1).
 
 Readings of the text that the code fixes:
-* observation points are the M distinct nodes x_j = j L / M, j = 0..M-1;
+* observation points are the M distinct nodes x_j = j L / M, j = 0..M-1; an
+  entry of y that is NaN is not observed;
 * the Girsanov log-weight of increments dW drawn under drift lambda is
   logG = -sum_{n<Ns} sum_k (lambda_k^n dW_k^n + 1/2 (lambda_k^n)^2 dt), the
   ratio of the N(0, dt) prior density to the proposal density of the increment
@@ -36,12 +37,21 @@ def obs_indices(n: int, M: int) -> np.ndarray:
     return np.arange(M) * (n // M)
 
 
+def observed(y: np.ndarray) -> np.ndarray:
+    """Mask of the observed points: an entry of y that is NaN is not observed (Exp 2
+    of Sec. 4 observes only [0, L/2])."""
+    return ~np.isnan(np.asarray(y, dtype=np.float64))
+
+
 def nll(u: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:
-    """Negative log of Eq. loglikeq: 1/2 sum_j ((u(x_j) - y_j) / sigma)^2 for each particle."""
+    """Negative log of Eq. loglikeq: 1/2 sum_j ((u(x_j) - y_j) / sigma)^2 for each particle,
+    over the observed points j (y_j not NaN)."""
     u = np.atleast_2d(np.asarray(u, dtype=np.float64))
+    y = np.asarray(y, dtype=np.float64)
     M = len(y)
-    idx = obs_indices(u.shape[1], M)
-    r = (u[:, idx] - np.asarray(y, dtype=np.float64)[None, :]) / sigma
+    obs = observed(y)
+    idx = obs_indices(u.shape[1], M)[obs]
+    r = (u[:, idx] - y[obs][None, :]) / sigma
     return 0.5 * np.sum(r * r, axis=1)
 
 

@@ -32,11 +32,13 @@ from oracle import rng as _rng
 
 
 def obs_grad_u(u_end: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:
-    """d NLL / d u_end: (u(x_j) - y_j) / sigma^2 at the observation nodes, zero elsewhere."""
+    """d NLL / d u_end: (u(x_j) - y_j) / sigma^2 at the observed nodes, zero elsewhere."""
     n = len(u_end)
-    idx = _F.obs_indices(n, len(y))
+    y = np.asarray(y, dtype=np.float64)
+    obs = _F.observed(y)
+    idx = _F.obs_indices(n, len(y))[obs]
     g = np.zeros(n)
-    g[idx] = (u_end[idx] - y) / sigma ** 2
+    g[idx] = (u_end[idx] - y[obs]) / sigma ** 2
     return g
 
 

@@ -102,6 +102,13 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int Kd, int kc
         }
 }
 
+// k-splits for a reduction with few output tiles (weight gradients: the sum runs over
+// batch x positions): about 8 CTAs per SM of 152, chunks of at least 256 k-values
+static int splitk_for(int M, int N, int Kd) {
+    const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    return max(1, min(Kd / 256, 8 * 152 / tiles));
+}
+
 template <typename LA, typename LB, typename EP>
 static void sgemm(int batch, int M, int N, int Kd, int splitk, LA la, LB lb, EP ep, cudaStream_t st) {
     const int kchunk = (Kd + splitk - 1) / splitk;
@@ -221,7 +228,10 @@ __global__ void features_kernel(int B, int n, int M, float sigma, const float* u
         const int b = (int)(e / n), i = (int)(e % n);
         const float ub = u[(size_t)b * n + i];
         float inn = 0.f;
-        if (i % stride == 0) inn = (y[(size_t)b * ystride + i / stride] - ub) / sigma;
+        if (i % stride == 0) {
+            const float yj = y[(size_t)b * ystride + i / stride];
+            if (yj == yj) inn = (yj - ub) / sigma;   // NaN: not observed
+        }
         x0[(size_t)b * bstride + i] = ub;
         x0[(size_t)b * bstride + n + i] = inn;
     }
@@ -242,14 +252,27 @@ __global__ void loss_kernel(int B, int O, const float* lam, size_t lstride, cons
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
 }
 
+// db[co] = sum over samples b and positions q of g[b][co][q].  Per-thread partial
+// sums in FP32 (two interleaved accumulators; GB300's FP64 rate would make this
+// the slowest step of the backward pass), the final reduction in FP64.  With
+// L >= 32 positions the threads stride over q inside each sample; otherwise over
+// the flattened (b, q).
 __global__ void bias_grad_kernel(int B, int Co, int L, const float* g, size_t bstride, float* db) {
     const int co = blockIdx.x;
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < B * L; e += blockDim.x) {
-        const int b = e / L, q = e % L;
-        acc += g[(size_t)b * bstride + (size_t)co * L + q];
+    float a0 = 0.f, a1 = 0.f;
+    if (L >= 32) {
+        const float* row = g + (size_t)co * L;
+        for (int b = 0; b < B; b += 2) {
+            for (int q = threadIdx.x; q < L; q += blockDim.x) {
+                a0 += row[(size_t)b * bstride + q];
+                if (b + 1 < B) a1 += row[(size_t)(b + 1) * bstride + q];
+            }
+        }
+    } else {
+        for (int e = threadIdx.x; e < B * L; e += blockDim.x)
+            a0 += g[(size_t)(e / L) * bstride + (size_t)co * L + e % L];
     }
-    acc = warp_sum(acc);
+    double acc = warp_sum((double)a0 + (double)a1);
     __shared__ double sh[32];
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -369,7 +392,7 @@ int nn_backward(const nn_shape* s, int B, const float* params, const float* u_st
     zero_kernel<<<grid_elems(d.nparam), 256, 0, st>>>(grads, d.nparam, loss);
     loss_kernel<<<grid_elems((size_t)B * O), 256, 0, st>>>(B, O, act + d.off_lam, bs, target, glam, loss);
     // head: dWh[o][f] = sum_b glam[b][o] F[b][f]; dbh[o] = sum_b glam[b][o]; gF = glam Wh
-    sgemm(1, O, FF, B, 16, RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
+    sgemm(1, O, FF, B, splitk_for(O, FF, B), RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
           AtomicAdd2D{grads + d.off_wh, FF}, st);
     bias_grad_kernel<<<O, 256, 0, st>>>(B, O, 1, glam, (size_t)O, grads + d.off_bh);
     sgemm(1, B, FF, O, 1, RowMajor{glam, 0, O}, RowMajor{params + d.off_wh, 0, FF}, Store{gF, 0, FF, nullptr}, st);
@@ -383,8 +406,8 @@ int nn_backward(const nn_shape* s, int B, const float* params, const float* u_st
         const int Ci = d.cin[l], Lin = d.L[l], Lo = d.L[l + 1];
         const float* gz = gcur;
         // weights: dw[co][kk] = sum_{b,q} gz[b][co][q] X(b, kk, q)
-        sgemm(1, d.C, Ci * 5, B * Lo, 32, GRowsBQ{gz, bs, Lo}, ConvXT{act + d.act_off[l], bs, Lin, Lo},
-              AtomicAdd2D{grads + d.off_w[l], Ci * 5}, st);
+        sgemm(1, d.C, Ci * 5, B * Lo, splitk_for(d.C, Ci * 5, B * Lo), GRowsBQ{gz, bs, Lo},
+              ConvXT{act + d.act_off[l], bs, Lin, Lo}, AtomicAdd2D{grads + d.off_w[l], Ci * 5}, st);
         bias_grad_kernel<<<d.C, 256, 0, st>>>(B, d.C, Lo, gz, bs, grads + d.off_b[l]);
         if (l > 0) {
             // data: dx[b][ci][i], masked by the ReLU of layer l-1's output

@@ -309,7 +309,8 @@ __device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* s
 #pragma unroll
     for (int i = 0; i < C; ++i) {
         const int node = i0 + i;
-        gu[i] = (node % A.stride == 0) ? (fend.u[i] - y[node / A.stride]) * A.sigma_inv * A.sigma_inv : R(0);
+        const R yj = (node % A.stride == 0) ? y[node / A.stride] : R(NAN);
+        gu[i] = (yj == yj) ? (fend.u[i] - yj) * A.sigma_inv * A.sigma_inv : R(0);   // NaN: not observed
     }
     R q[C], qp, qn, gp, gn;
     const_solve<R, C, TP>(A.hel, A.rhel, gu, q, qp, qn, sh);

@@ -766,8 +766,11 @@ __device__ __forceinline__ double chunk_misfit(const ModelArgs<R>& A, const R (&
     for (int i = 0; i < C; ++i) {
         const int node = i0 + i;
         if (node % A.stride == 0) {
-            const R r = (u[i] - y[node / A.stride]) * A.sigma_inv;
-            acc += (double)r * (double)r;
+            const R yj = y[node / A.stride];
+            if (yj == yj) {   // NaN: not observed
+                const R r = (u[i] - yj) * A.sigma_inv;
+                acc += (double)r * (double)r;
+            }
         }
     }
     return acc;

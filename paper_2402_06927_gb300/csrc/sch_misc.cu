@@ -36,7 +36,9 @@ __global__ void loglik_kernel(ModelArgs<R> A, int N, const R* u, const R* y, con
     const R* up = u + (size_t)warp * A.n;
     double acc = 0.0;
     for (int j = lane; j < A.M; j += 32) {
-        const R r = (up[j * A.stride] - y[j]) * A.sigma_inv;
+        const R yj = y[j];
+        if (yj != yj) continue;   // NaN: not observed
+        const R r = (up[j * A.stride] - yj) * A.sigma_inv;
         acc += (double)r * (double)r;
     }
     acc = warp_sum(acc);

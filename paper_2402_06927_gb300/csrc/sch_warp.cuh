@@ -387,8 +387,8 @@ __device__ __forceinline__ void wstore(float* row, const float2 (&v)[P][CS]) {
         }
 }
 
-// observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this lane's nodes;
-// node mod stride and the observation index advance node by node
+// observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this lane's observed
+// nodes (y_j not NaN); node mod stride and the observation index advance node by node
 template <int CS, int P>
 __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float2 (&u)[P][CS], const float* y) {
     const int base = (threadIdx.x & 31) * 2 * P * CS;
@@ -400,8 +400,11 @@ __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float
 #pragma unroll
         for (int i = 0; i < CS; ++i) {
             if (rem == 0) {
-                const float r = (((s < P) ? u[s][i].x : u[s - P][i].y) - y[j]) * A.sigma_inv;
-                acc += (double)r * (double)r;
+                const float yj = y[j];
+                if (yj == yj) {   // NaN: not observed
+                    const float r = (((s < P) ? u[s][i].x : u[s - P][i].y) - yj) * A.sigma_inv;
+                    acc += (double)r * (double)r;
+                }
                 ++j;
             }
             rem = (rem + 1 == A.stride) ? 0 : rem + 1;

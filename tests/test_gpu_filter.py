@@ -74,9 +74,12 @@ def test_resample_degenerate_and_inplace():
     assert torch.equal(dst, src.flip(0))
 
 
-@pytest.mark.parametrize("name,theta,lam,layout", [("cfg1_f64", 0.4, False, "auto"), ("cfg1_f64", 1.0, True, "auto"),
-                                                   ("cfg2_f32", 0.3, False, "warp"), ("cfg2_f32", 0.3, True, "cta")])
-def test_jitter_matches_oracle(name, theta, lam, layout):
+@pytest.mark.parametrize("name,theta,lam,layout,upto", [("cfg1_f64", 0.4, False, "auto", None),
+                                                        ("cfg1_f64", 1.0, True, "auto", None),
+                                                        ("cfg2_f32", 0.3, False, "warp", None),
+                                                        ("cfg2_f32", 0.3, True, "cta", None),
+                                                        ("cfg2_f32", 0.3, False, "warp", 0.5)])
+def test_jitter_matches_oracle(name, theta, lam, layout, upto):
     cfg = get_config(name)
     g = gpu_model(cfg, layout=layout)
     om = oracle_model(cfg)
@@ -85,7 +88,7 @@ def test_jitter_matches_oracle(name, theta, lam, layout):
     m0 = np.stack([om.m_from_u(u) for u in u0])
     dW = random_increments(cfg, N, 51)
     la = random_drift(cfg, N, 52, scale=0.2) if lam else None
-    y = random_obs(cfg, 53)
+    y = random_obs(cfg, 53, upto=upto)   # upto = 0.5: Exp 2's half-domain observations
     n_iter, seed, ctr = 4, 77, 1000
     ref = OF.jitter(om, m0, dW, la, y, cfg.sigma, theta, cfg.rho, n_iter, seed, ctr)
     dt = g.dtype

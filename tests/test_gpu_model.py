@@ -254,3 +254,27 @@ def test_layouts_agree_at_full_ensemble_size():
     assert torch.all(a["status"] == 0) and torch.all(b["status"] == 0)
     assert (a["iters"] - b["iters"]).abs().max().item() <= cfg.Ns
     assert torch.allclose(a["nll"], b["nll"], rtol=1e-3)
+
+
+@pytest.mark.parametrize("name,layout", [("cfg1_f64", "auto"), ("cfg2_f32", "warp"), ("cfg2_f32", "cta")])
+def test_half_domain_observations(name, layout):
+    # Exp 2: only the points of [0, L/2] are observed (NaN elsewhere); the fused window
+    # likelihood and sch_loglik sum over the observed points only
+    cfg = get_config(name)
+    g = gpu_model(cfg, layout=layout)
+    om, m0, dW, la = _case(cfg, 3, 61, lam=True)
+    y = random_obs(cfg, 62, upto=0.5)
+    assert np.isnan(y).sum() == cfg.M - (cfg.M // 2 + 1)
+    ref = om.ensemble_window(m0, dW, la)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype))
+    nll_ref = OF.nll(ref[1], y, cfg.sigma)
+    tol = 1e-9 if cfg.dtype == "f64" else 1e-4
+    assert np.allclose(out["nll"].cpu().numpy(), nll_ref, rtol=tol)
+    yd = tdev(y, g.dtype)
+    ll, _ = g.loglik(out["u"], yd)
+    # the residuals are formed in the field precision, the sums in FP64
+    tol_ll = 1e-9 if cfg.dtype == "f64" else 1e-6
+    assert np.allclose(ll.cpu().numpy(), OF.nll(out["u"].double().cpu().numpy(), yd.double().cpu().numpy(),
+                                                cfg.sigma), rtol=tol_ll)
+    # the unobserved half carries no weight: the full-domain NLL is larger
+    assert np.all(OF.nll(ref[1], random_obs(cfg, 62), cfg.sigma) > nll_ref)

@@ -36,10 +36,13 @@ def _setup(cfg, N, seed, Ns=None, lam_scale=0.3):
     return om, m0, dW, la, y
 
 
-def test_adjoint_matches_oracle_tangent_linear():
+@pytest.mark.parametrize("upto", [None, 0.5])
+def test_adjoint_matches_oracle_tangent_linear(upto):
     cfg = get_config("cfg1_f64")
     g = gpu_model(cfg)
     om, m0, dW, la, y = _setup(cfg, 2, 5, Ns=4)
+    if upto is not None:   # Exp 2: observations on [0, L/2] only
+        y = random_obs(cfg, 8, upto=upto)
     out = g.adjoint_window(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype), ckpt=2)
     torch.cuda.synchronize()
     assert np.all(out["status"].cpu().numpy() == 0)

@@ -43,10 +43,13 @@ def _case(n=256, K=4, Ns=3, C=16, M=32, B=6, seed=0):
     return p, u, y, target
 
 
-def test_forward_and_gradients_match_oracle():
+@pytest.mark.parametrize("masked", [False, True])
+def test_forward_and_gradients_match_oracle(masked):
     api = require_lib()
     n, K, Ns, C, M, sigma = 256, 4, 3, 16, 32, 0.05
     p, u, y, target = _case(n, K, Ns, C, M)
+    if masked:   # unobserved points (NaN) carry zero innovation
+        y[:, M // 2 + 1:] = np.nan
     net = api.ProposalNet(n, K, Ns, M, sigma, C=C, params=torch.tensor(_flat(p), dtype=torch.float32))
     ud = torch.tensor(u, dtype=torch.float32, device="cuda")
     yd = torch.tensor(y, dtype=torch.float32, device="cuda")
@@ -64,6 +67,7 @@ def test_forward_and_gradients_match_oracle():
     lam_shared = net.forward(ud, yd[0].contiguous()).cpu().numpy()
     lam_bcast = net.forward(ud, yd[0:1].expand(u.shape[0], M).contiguous()).cpu().numpy()
     assert np.array_equal(lam_shared, lam_bcast)
+    assert np.all(np.isfinite(lam))
 
 
 def test_adam_matches_oracle():

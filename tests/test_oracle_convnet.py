@@ -79,3 +79,9 @@ def test_features_scatter_innovation():
     assert np.allclose(x[0, 0], u[0])
     assert np.allclose(x[0, 1, ::4], (y - u[0, ::4]) / 0.5)
     assert np.all(x[0, 1, 1::4] == 0)
+    # an unobserved point (NaN) has innovation zero
+    ym = y.copy()
+    ym[2:] = np.nan
+    xm = CN.features(u, ym, 0.5)
+    assert np.allclose(xm[0, 1, 0:8:4], (y[:2] - u[0, 0:8:4]) / 0.5)
+    assert np.all(xm[0, 1, 8::4] == 0) and np.all(np.isfinite(xm))

@@ -56,6 +56,29 @@ def test_nll_definition_and_girsanov_density_ratio():
     assert np.all(F.girsanov_logG(np.zeros_like(lam), dW, dt) == 0.0)
 
 
+def test_nll_observation_mask():
+    # Exp 2 observes [0, L/2] only: entries of y that are NaN are not observed.  The masked
+    # NLL is the sum over the observed points alone, written out by hand here.
+    r = np.random.default_rng(7)
+    n, M, sigma = 64, 16, 0.1
+    u = r.normal(size=(2, n))
+    y = r.normal(size=M)
+    ym = y.copy()
+    ym[M // 2 + 1:] = np.nan
+    v = F.nll(u, ym, sigma)
+    for p in range(2):
+        ref = sum(0.5 * ((u[p, j * (n // M)] - y[j]) / sigma) ** 2 for j in range(M // 2 + 1))
+        assert abs(v[p] - ref) < 1e-12 * ref
+    # nothing observed: likelihood one; every point observed: the unmasked NLL
+    assert np.all(F.nll(u, np.full(M, np.nan), sigma) == 0.0)
+    assert np.array_equal(F.nll(u, y, sigma), F.nll(u, np.where(F.observed(y), y, np.nan), sigma))
+    # a mask that is not a prefix
+    ym2 = y.copy()
+    ym2[::3] = np.nan
+    ref = 0.5 * sum(((u[0, j * (n // M)] - y[j]) / sigma) ** 2 for j in range(M) if j % 3)
+    assert abs(F.nll(u, ym2, sigma)[0] - ref) < 1e-12 * ref
+
+
 def test_temper_against_dense_scan():
     r = np.random.default_rng(2)
     for trial in range(5):

@@ -78,6 +78,28 @@ def test_gradient_matches_finite_differences_16_directions():
         assert abs(fd - np.sum(g * d)) <= 1e-6 * max(1.0, abs(fd))
 
 
+def test_gradient_with_half_domain_observations():
+    # Exp 2: observations on [0, L/2] only (y NaN elsewhere); the gradient still matches
+    # central differences of the masked cost, and observations outside the mask do not matter
+    m, m0, dW, lam, y = _problem()
+    sigma = 0.05
+    ym = y.copy()
+    ym[len(y) // 2 + 1:] = np.nan
+    J, g = ON.cost_and_gradient(m, m0, dW, lam, ym, sigma)
+    assert np.isfinite(J) and np.all(np.isfinite(g))
+    r = np.random.default_rng(4)
+    for _ in range(4):
+        d = r.normal(size=lam.shape)
+        eps = 1e-5
+        fd = (ON.cost(m, m0, dW, lam + eps * d, ym, sigma) - ON.cost(m, m0, dW, lam - eps * d, ym, sigma)) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) <= 1e-6 * max(1.0, abs(fd))
+    # the terminal sensitivity vanishes at the unobserved nodes and is unchanged at the observed ones
+    gm, gf = ON.obs_grad_u(m0, ym, sigma), ON.obs_grad_u(m0, y, sigma)
+    stride = m.n // len(y)
+    half = (len(y) // 2 + 1) * stride
+    assert np.all(gm[half:] == 0.0) and np.array_equal(gm[:half], gf[:half])
+
+
 def test_taylor_remainder_is_second_order():
     m, m0, dW, lam, y = _problem(4)
     sigma = 0.05

@@ -168,11 +168,16 @@ def random_drift(cfg: Config, N: int, seed: int, scale: float = 0.3,
     return rng.normal(scale=scale, size=(N, steps, cfg.K))
 
 
-def random_obs(cfg: Config, seed: int, noise: Optional[float] = None) -> np.ndarray:
-    """Synthetic observation vector y [M]: u0 at the observation nodes plus noise."""
+def random_obs(cfg: Config, seed: int, noise: Optional[float] = None, upto: Optional[float] = None) -> np.ndarray:
+    """Synthetic observation vector y [M]: u0 at the observation nodes plus noise.
+    With ``upto`` only the points x_j <= upto L are observed (the rest NaN): upto = 0.5
+    is Exp 2's half-domain observation of Sec. 4."""
     rng = np.random.default_rng(seed)
     noise = cfg.sigma if noise is None else noise
-    return u0_profile(cfg)[:: cfg.obs_stride][: cfg.M] + rng.normal(scale=noise, size=cfg.M)
+    y = u0_profile(cfg)[:: cfg.obs_stride][: cfg.M] + rng.normal(scale=noise, size=cfg.M)
+    if upto is not None:
+        y[np.arange(cfg.M) > upto * cfg.M] = np.nan
+    return y
 
 
 def random_logweights(N: int, seed: int, spread: float = 5.0) -> np.ndarray:
