@@ -283,7 +283,7 @@ def run_ours(args):
         m_truth = out["m"]
         truths.append(out["u"][0].clone())
         ys.append(g.synth_obs(out["u"][0].contiguous(), seed, c))
-    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
     m0, _ = g.prior_sample(N, u_truth, seed, cfg.prior_scale)
     f.set_state(m0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -348,7 +348,7 @@ def run_ours(args):
     dg_host = torch.empty(8, dtype=torch.float64).pin_memory()
     y_dev = torch.empty_like(ys[0])
     e2e_steps = min(args.steps, 3)
-    f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
     f2.set_state(m0)
     torch.cuda.synchronize()
     barrier(ws)
@@ -712,6 +712,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--eager-stages", type=int, default=2,
+                    help="tempering stages enqueued at once as device-gated stages (0: stage by stage)")
     ap.add_argument("--nudging", action="store_true",
                     help="learned vs optimiser nudging comparison instead of the default workload")
     ap.add_argument("--adjoint", action="store_true",

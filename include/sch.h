@@ -175,6 +175,24 @@ int sch_loglik(sch_ctx* ctx, int N, const void* u, const void* y, const void* dW
 int pf_temper(int N, const double* nll, const double* logG, double theta, double ess_min,
               double* wbar, double* out, void* stream);
 
+/* Adaptive tempering by halving (Sec. 3.1.2, "repeatedly reduces dtheta until the
+ * condition holds", read literally): the first of dtheta = (1 - theta) 2^-k,
+ * k = 0, 1, .., 60, with ESS >= ess_min; if none passes, (1 - theta) 2^-60.
+ * Arguments, outputs and errors as pf_temper. */
+int pf_temper_halving(int N, const double* nll, const double* logG, double theta, double ess_min,
+                      double* wbar, double* out, void* stream);
+
+/* Device-gated tempering stage, for a cycle whose stages are all enqueued without a
+ * host round trip.  The temperature is read from the device scalar theta_dev (the
+ * previous stage's out[2], or a device 0.0 for the first stage).  mode:
+ * PF_TEMPER_LARGEST (as pf_temper) or PF_TEMPER_HALVING (as pf_temper_halving).
+ * Writes out[5]: out[0..3] as pf_temper, out[4] = 1 when the stage is active.  A
+ * stage that starts at theta >= 1 is inactive: it writes {0, 0, 1, 0, 0} and leaves
+ * wbar untouched. */
+enum { PF_TEMPER_LARGEST = 0, PF_TEMPER_HALVING = 1 };
+int pf_temper_dev(int N, const double* nll, const double* logG, const double* theta_dev, double ess_min,
+                  int mode, double* wbar, double* out, void* stream);
+
 /* Systematic resampling (Sec. 3.1.1) on exact integers: q_i = floor(wbar_i 2^50),
  * C_j = q_0 + .. + q_j, T = C_{N-1}; slot i takes the smallest j with
  * C_j > floor((i 2^53 + U) T / (N 2^53)), U = (Philox (seed, SCH_TAG_RESAMPLE,
@@ -224,6 +242,12 @@ int pf_resample_static(int N, const double* wbar, uint64_t seed, uint64_t stage_
 int pf_gather_rows(int N, const int32_t* idx, const void* src, void* dst, size_t row_bytes,
                    void* stream);
 
+/* Offspring indices of a device-gated stage: as pf_resample without arrays when
+ * *gate != 0 (gate: device pointer to the stage's out[4] of pf_temper_dev); the
+ * identity idx[i] = i when the stage is inactive, so row gathers stay valid. */
+int pf_resample_gated(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, const double* gate,
+                      int32_t* idx, void* stream);
+
 /* PCN jittering at temperature theta (Sec. 3.1.2): n_iter Metropolis moves of
  * each particle's window noise.  Iteration j proposes
  *   dW' = rho dW + sqrt(1 - rho^2) sqrt(dt) z,  z keyed (seed, SCH_TAG_PCN, ctr + j),
@@ -235,6 +259,34 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
               uint64_t seed, uint64_t ctr, const void* m_start, void* dW, const void* lambda,
               const void* y, double* nll, double* logG, void* m_end, void* u_end,
               int32_t* accepts, int32_t* iters, int32_t* status, void* stream);
+
+/* pf_jitter for a device-gated stage: theta = tstate[2] and nothing is done when
+ * tstate[4] == 0 (tstate: device pointer to the stage's out[5] of pf_temper_dev). */
+int pf_jitter_dev(sch_ctx* ctx, int N, int nsteps, int n_iter, const double* tstate, double rho,
+                  uint64_t seed, uint64_t ctr, const void* m_start, void* dW, const void* lambda,
+                  const void* y, double* nll, double* logG, void* m_end, void* u_end,
+                  int32_t* accepts, int32_t* iters, int32_t* status, void* stream);
+
+/* n_stages device-gated stages of an assimilation cycle (Sec. 3.1.2) enqueued in one
+ * call, with no host round trip: for stage k, pf_temper_dev (temperature from
+ * theta0 for k = 0, else from stage k-1), pf_resample_gated with counter
+ * cycle * 1024 + first_stage + k, out-of-place row gathers of every state array
+ * from bufs_a to bufs_b, then pf_jitter_dev (jitter counter stage counter x
+ * n_jitter).  A stage reached at temperature one does nothing but copy the rows.
+ * bufs_a[PF_STAGE_ARRAYS], bufs_b[PF_STAGE_ARRAYS]: device pointers in the order
+ * PF_M_START, PF_M_END, PF_U_END, PF_DW, PF_NLL, PF_LOGG, PF_LAMBDA (the last may be
+ * NULL in both); every stage gathers a -> b and swaps the roles, so after n_stages
+ * stages the state is in bufs_a if n_stages is even, else in bufs_b.
+ *   touts   double [n_stages][5]: each stage's pf_temper_dev result
+ *   iters   int32 [n_stages][N] or NULL; accepts, status as pf_jitter
+ *   events  NULL or 2 n_stages cudaEvent_t recorded around each jitter launch
+ * Argument errors are caught before the first launch. */
+enum { PF_M_START = 0, PF_M_END, PF_U_END, PF_DW, PF_NLL, PF_LOGG, PF_LAMBDA, PF_STAGE_ARRAYS };
+int pf_gated_stages(sch_ctx* ctx, int N, int nsteps, int n_stages, int first_stage, double ess_min,
+                    int mode, double rho, int n_jitter, uint64_t seed, uint64_t cycle, const void* y,
+                    void* const* bufs_a, void* const* bufs_b, const double* theta0, double* wbar,
+                    int32_t* idx, double* touts, int32_t* accepts, int32_t* iters, int32_t* status,
+                    void* const* events, void* stream);
 
 /* Synthetic observations of a truth velocity: y_j = u(x_j) + sigma z_j with
  * z_j keyed (seed, SCH_TAG_OBS, (j / 4, 0, 0, ctr)).  u real [n], y real [M]. */

@@ -76,20 +76,29 @@ def ess(logw: np.ndarray) -> float:
     return float(1.0 / np.sum(wb * wb))
 
 
-def temper(phi: np.ndarray, theta: float, ess_min: float, iters: int = 60):
+def temper(phi: np.ndarray, theta: float, ess_min: float, iters: int = 60, mode: str = "largest"):
     """Adaptive tempering step (Sec. 3.1.2).
 
-    Largest dtheta in (0, 1 - theta] with ESS(exp(-dtheta phi)) >= ess_min.
-    If the whole remaining step passes it is taken; otherwise bisection on
-    [0, 1 - theta] for ``iters`` steps keeps the largest passing point.  If
-    even the smallest point tried fails (only possible for astronomically
-    spread phi), the smallest point tried is returned, so tempering always
-    advances.  Returns (dtheta, w_bar at dtheta, ESS at dtheta).
+    mode "largest": the largest dtheta in (0, 1 - theta] with
+    ESS(exp(-dtheta phi)) >= ess_min.  If the whole remaining step passes it is
+    taken; otherwise bisection on [0, 1 - theta] for ``iters`` steps keeps the
+    largest passing point.  mode "halving": the first of (1 - theta) 2^-k,
+    k = 0 .. iters, that passes.  In both, if even the smallest point tried
+    fails (only possible for astronomically spread phi), the smallest point
+    tried is returned, so tempering always advances.  Returns (dtheta, w_bar at
+    dtheta, ESS at dtheta).
     """
     phi = np.asarray(phi, dtype=np.float64)
     rest = 1.0 - theta
     if ess(-rest * phi) >= ess_min:
         d = rest
+    elif mode == "halving":
+        # Sec. 3.1.2 read literally ("repeatedly reduces dtheta until the condition
+        # holds"): the first of rest 2^-k, k = 1 .. iters, that passes, else the last tried
+        for k in range(1, iters + 1):
+            d = rest * 2.0 ** -k
+            if ess(-d * phi) >= ess_min:
+                break
     else:
         lo, hi = 0.0, rest
         for _ in range(iters):
@@ -227,7 +236,7 @@ def res(u_truth, u_ens) -> float:
 # one assimilation cycle (bootstrap forecast, then temper + resample + jitter)
 # ---------------------------------------------------------------------- #
 def assimilation_cycle(model, m_start, y, sigma, ess_min, rho, n_jitter, seed, cycle,
-                       lam=None, dW=None, max_stages=64):
+                       lam=None, dW=None, max_stages=64, temper_mode="largest"):
     """One cycle of Sec. 3.1.2 on the (X_start, dW) representation.
 
     dW is drawn from (seed, TAG_PRIOR_DW, cycle) unless given.  Stage k tempers
@@ -251,7 +260,7 @@ def assimilation_cycle(model, m_start, y, sigma, ess_min, rho, n_jitter, seed, c
     k = 0
     while theta < 1.0 and k < max_stages:
         phi = cur_nll - cur_logG
-        d, wbar, e = temper(phi, theta, ess_min)
+        d, wbar, e = temper(phi, theta, ess_min, mode=temper_mode)
         stage_ctr = cycle * 1024 + k
         idx = systematic_resample(wbar, resample_offset(seed, stage_ctr))
         m_start, dW, lam_arr = m_start[idx], dW[idx], lam_arr[idx]

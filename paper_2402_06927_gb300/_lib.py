@@ -61,12 +61,17 @@ SIGNATURES = {
     "sch_ensemble_step": [P, I, I, P, P, P, P, P, P, P, P, P, P, P],
     "sch_loglik": [P, I, P, P, P, P, I, P, P, P],
     "pf_temper": [I, P, P, D, D, P, P, P],
+    "pf_temper_halving": [I, P, P, D, D, P, P, P],
     "sch_synth_obs": [P, P, U64, U64, P, P],
     "pf_diagnostics": [P, I, P, P, P, P, P],
     "pf_resample": [I, P, U64, U64, P, I, P, P, P, SZ, P],
     "pf_gather_rows": [I, P, P, P, SZ, P],
+    "pf_temper_dev": [I, P, P, P, D, I, P, P, P],
+    "pf_resample_gated": [I, P, U64, U64, P, P, P],
     "pf_resample_static": [I, P, U64, U64, P, I, P, P, P],
     "pf_jitter": [P, I, I, I, D, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
+    "pf_jitter_dev": [P, I, I, I, P, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
+    "pf_gated_stages": [P, I, I, I, I, D, I, D, I, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
     "sch_prior_sample": [P, I, P, U64, D, P, P, P],
     "sch_adjoint_window": [P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, SZ, P],
     "pf_nudge": [P, I, I, I, I, D, I, U64, U64, P, P, P, P, P, P, P, P, SZ, P],

@@ -150,7 +150,8 @@ class SchModel:
         return nll, logG
 
     def jitter(self, m_start, dW, lam, y, nll, logG, m_end, u_end, theta: float, rho: float, n_iter: int,
-               seed: int, ctr: int, want_iters: bool = False, accepts=None, iters=None, status=None):
+               seed: int, ctr: int, want_iters: bool = False, accepts=None, iters=None, status=None,
+               tstate: Optional[torch.Tensor] = None):
         """pf_jitter: updates dW, nll, logG, m_end, u_end in place; returns (accepts, iters, status)."""
         N, nsteps, K = dW.shape
         _need(m_start, self.dtype, (N, self.n), "m_start")
@@ -166,9 +167,16 @@ class SchModel:
         if iters is None and want_iters:
             iters = torch.empty(N, dtype=torch.int32, device=dW.device)
         status = torch.empty(N, dtype=torch.int32, device=dW.device) if status is None else status
-        check(lib().pf_jitter(self._h, N, nsteps, n_iter, theta, rho, seed, ctr, _ptr(m_start), _ptr(dW),
-                              _ptr(lam), _ptr(y), _ptr(nll), _ptr(logG), _ptr(m_end), _ptr(u_end), _ptr(acc),
-                              _ptr(iters), _ptr(status), _stream()), "pf_jitter")
+        if tstate is not None:
+            # device-gated stage: theta = tstate[2], nothing done when tstate[4] == 0
+            check(lib().pf_jitter_dev(self._h, N, nsteps, n_iter, _ptr(tstate), rho, seed, ctr, _ptr(m_start),
+                                      _ptr(dW), _ptr(lam), _ptr(y), _ptr(nll), _ptr(logG), _ptr(m_end),
+                                      _ptr(u_end), _ptr(acc), _ptr(iters), _ptr(status), _stream()),
+                  "pf_jitter_dev")
+        else:
+            check(lib().pf_jitter(self._h, N, nsteps, n_iter, theta, rho, seed, ctr, _ptr(m_start), _ptr(dW),
+                                  _ptr(lam), _ptr(y), _ptr(nll), _ptr(logG), _ptr(m_end), _ptr(u_end), _ptr(acc),
+                                  _ptr(iters), _ptr(status), _stream()), "pf_jitter")
         return acc, iters, status
 
     def synth_obs(self, u: torch.Tensor, seed: int, ctr: int, y: Optional[torch.Tensor] = None):
@@ -250,17 +258,18 @@ class SchModel:
 # filter entry points that need no model context
 # ---------------------------------------------------------------------- #
 def pf_temper(nll: torch.Tensor, logG: Optional[torch.Tensor], theta: float, ess_min: float,
-              wbar: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None):
+              wbar: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None, mode: str = "largest"):
     """Returns (wbar, out) with out = [dtheta, ESS, theta_new, ESS of the whole remaining step]
-    on the device; phi = nll - logG."""
+    on the device; phi = nll - logG.  mode "largest": the largest passing dtheta
+    (pf_temper); "halving": the first passing (1 - theta) 2^-k (pf_temper_halving)."""
     N = nll.shape[0]
     _need(nll, torch.float64, (N,), "nll")
     if logG is not None:
         _need(logG, torch.float64, (N,), "logG")
     wbar = torch.empty_like(nll) if wbar is None else wbar
     out = torch.empty(4, dtype=torch.float64, device=nll.device) if out is None else out
-    check(lib().pf_temper(N, _ptr(nll), _ptr(logG), theta, ess_min, _ptr(wbar), _ptr(out), _stream()),
-          "pf_temper")
+    fn = {"largest": lib().pf_temper, "halving": lib().pf_temper_halving}[mode]
+    check(fn(N, _ptr(nll), _ptr(logG), theta, ess_min, _ptr(wbar), _ptr(out), _stream()), "pf_temper")
     return wbar, out
 
 
@@ -301,6 +310,27 @@ def pf_resample_static(wbar: torch.Tensor, seed: int, stage_ctr: int, arrays: Se
     rows = (ct.c_size_t * max(na, 1))(*[a[0].numel() * a.element_size() for a in arrays])
     check(lib().pf_resample_static(N, _ptr(wbar), seed, stage_ctr, _ptr(idx), na, ptrs if na else None,
                                    rows if na else None, _stream()), "pf_resample_static")
+    return idx
+
+
+def pf_temper_dev(nll: torch.Tensor, logG: Optional[torch.Tensor], theta_dev: torch.Tensor, ess_min: float,
+                  wbar: torch.Tensor, out: torch.Tensor, mode: str = "largest"):
+    """Device-gated tempering stage: theta read from the device scalar theta_dev; writes
+    out[5] = [dtheta, ESS, theta_new, ESS of the whole remaining step, active]."""
+    N = nll.shape[0]
+    _need(nll, torch.float64, (N,), "nll")
+    _need(out, torch.float64, (5,), "out")
+    md = {"largest": 0, "halving": 1}[mode]
+    check(lib().pf_temper_dev(N, _ptr(nll), _ptr(logG), _ptr(theta_dev), ess_min, md, _ptr(wbar), _ptr(out),
+                              _stream()), "pf_temper_dev")
+    return wbar, out
+
+
+def pf_resample_gated(wbar: torch.Tensor, seed: int, stage_ctr: int, gate: torch.Tensor, idx: torch.Tensor):
+    """Offspring indices of a device-gated stage (identity when *gate == 0)."""
+    N = wbar.shape[0]
+    check(lib().pf_resample_gated(N, _ptr(wbar), seed, stage_ctr, _ptr(gate), _ptr(idx), _stream()),
+          "pf_resample_gated")
     return idx
 
 

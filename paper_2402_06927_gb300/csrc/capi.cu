@@ -444,7 +444,27 @@ int pf_temper(int N, const double* nll, const double* logG, double theta, double
               double* out, void* stream) {
     if (N <= 0 || N > 16384 || !nll || !wbar || !out) return SCH_ERR_ARG;
     if (!(theta >= 0.0 && theta < 1.0) || !(ess_min > 0.0) || ess_min > N) return SCH_ERR_ARG;
-    return launch_temper(N, nll, logG, theta, ess_min, wbar, out, S(stream));
+    return launch_temper(N, nll, logG, theta, nullptr, ess_min, 0, wbar, out, S(stream));
+}
+
+int pf_temper_halving(int N, const double* nll, const double* logG, double theta, double ess_min, double* wbar,
+                      double* out, void* stream) {
+    if (N <= 0 || N > 16384 || !nll || !wbar || !out) return SCH_ERR_ARG;
+    if (!(theta >= 0.0 && theta < 1.0) || !(ess_min > 0.0) || ess_min > N) return SCH_ERR_ARG;
+    return launch_temper(N, nll, logG, theta, nullptr, ess_min, 1, wbar, out, S(stream));
+}
+
+int pf_temper_dev(int N, const double* nll, const double* logG, const double* theta_dev, double ess_min, int mode,
+                  double* wbar, double* out, void* stream) {
+    if (N <= 0 || N > 16384 || !nll || !theta_dev || !wbar || !out) return SCH_ERR_ARG;
+    if (!(ess_min > 0.0) || ess_min > N || (mode != PF_TEMPER_LARGEST && mode != PF_TEMPER_HALVING)) return SCH_ERR_ARG;
+    return launch_temper(N, nll, logG, 0.0, theta_dev, ess_min, mode == PF_TEMPER_HALVING, wbar, out, S(stream));
+}
+
+int pf_resample_gated(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, const double* gate,
+                      int32_t* idx, void* stream) {
+    if (N <= 0 || N > 8192 || !wbar || !gate || !idx) return SCH_ERR_ARG;
+    return launch_resample_idx(N, wbar, seed, stage_ctr, gate, idx, S(stream));
 }
 
 int pf_resample(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx, int n_arrays,
@@ -460,7 +480,7 @@ int pf_resample(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, in
     // every array's slice of the workspace starts on a 16-byte boundary: N * row_bytes[a] is a multiple of 16
     if (n_arrays > 0 && (!ws || ((uintptr_t)ws & 15) || ws_bytes < pf_resample_workspace_bytes(N, total)))
         return SCH_ERR_WORKSPACE;
-    int rc = launch_resample_idx(N, wbar, seed, stage_ctr, idx, S(stream));
+    int rc = launch_resample_idx(N, wbar, seed, stage_ctr, nullptr, idx, S(stream));
     if (rc != SCH_OK) return rc;
     unsigned char* w = (unsigned char*)ws;
     for (int a = 0; a < n_arrays; ++a) {
@@ -495,10 +515,12 @@ int pf_diagnostics(sch_ctx* ctx, int N, const void* u, const void* u_truth, doub
     return launch_diag<double>(ctx->ad, N, (const double*)u, (const double*)u_truth, ws, out, S(stream));
 }
 
-int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double rho, uint64_t seed,
-              uint64_t ctr, const void* m_start, void* dW, const void* lambda, const void* y, double* nll,
-              double* logG, void* m_end, void* u_end, int32_t* accepts, int32_t* iters, int32_t* status,
-              void* stream) {
+namespace {
+
+int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const double* tstate, double rho,
+                uint64_t seed, uint64_t ctr, const void* m_start, void* dW, const void* lambda, const void* y,
+                double* nll, double* logG, void* m_end, void* u_end, int32_t* accepts, int32_t* iters,
+                int32_t* status, void* stream) {
     if (!ctx || N < 0 || nsteps <= 0 || n_iter < 0) return SCH_ERR_ARG;
     if (!(rho >= 0.0 && rho <= 1.0) || !(theta >= 0.0 && theta <= 1.0)) return SCH_ERR_ARG;
     if (N == 0 || n_iter == 0) return SCH_OK;
@@ -510,18 +532,93 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
     const double sq = sqrt(1.0 - rho * rho);
     if (ctx->p.dtype == SCH_F32) {
-        JitterIO<float> io{nsteps, n_iter, 0, theta, (float)rho, (float)sq, seed, ctr, (const float*)m_start,
-                           (float*)dW, (const float*)lambda, (const float*)y, nll, logG, (float*)m_end,
-                           (float*)u_end, accepts, iters, status};
+        JitterIO<float> io{nsteps, n_iter, 0, theta, tstate, (float)rho, (float)sq, seed, ctr,
+                           (const float*)m_start, (float*)dW, (const float*)lambda, (const float*)y, nll, logG,
+                           (float*)m_end, (float*)u_end, accepts, iters, status};
         if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }
-    JitterIO<double> io{nsteps, n_iter, 0, theta, rho, sq, seed, ctr, (const double*)m_start, (double*)dW,
-                        (const double*)lambda, (const double*)y, nll, logG, (double*)m_end, (double*)u_end,
-                        accepts, iters, status};
+    JitterIO<double> io{nsteps, n_iter, 0, theta, tstate, rho, sq, seed, ctr, (const double*)m_start,
+                        (double*)dW, (const double*)lambda, (const double*)y, nll, logG, (double*)m_end,
+                        (double*)u_end, accepts, iters, status};
     return ctx->ad.solver == SCH_SOLVER_EA ? launch_jitter<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
                                            : launch_jitter<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
+}
+
+}  // namespace
+
+int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double rho, uint64_t seed,
+              uint64_t ctr, const void* m_start, void* dW, const void* lambda, const void* y, double* nll,
+              double* logG, void* m_end, void* u_end, int32_t* accepts, int32_t* iters, int32_t* status,
+              void* stream) {
+    return jitter_impl(ctx, N, nsteps, n_iter, theta, nullptr, rho, seed, ctr, m_start, dW, lambda, y, nll, logG,
+                       m_end, u_end, accepts, iters, status, stream);
+}
+
+int pf_jitter_dev(sch_ctx* ctx, int N, int nsteps, int n_iter, const double* tstate, double rho, uint64_t seed,
+                  uint64_t ctr, const void* m_start, void* dW, const void* lambda, const void* y, double* nll,
+                  double* logG, void* m_end, void* u_end, int32_t* accepts, int32_t* iters, int32_t* status,
+                  void* stream) {
+    if (!tstate) return SCH_ERR_ARG;
+    return jitter_impl(ctx, N, nsteps, n_iter, 0.0, tstate, rho, seed, ctr, m_start, dW, lambda, y, nll, logG,
+                       m_end, u_end, accepts, iters, status, stream);
+}
+
+int pf_gated_stages(sch_ctx* ctx, int N, int nsteps, int n_stages, int first_stage, double ess_min, int mode,
+                    double rho, int n_jitter, uint64_t seed, uint64_t cycle, const void* y, void* const* bufs_a,
+                    void* const* bufs_b, const double* theta0, double* wbar, int32_t* idx, double* touts,
+                    int32_t* accepts, int32_t* iters, int32_t* status, void* const* events, void* stream) {
+    if (!ctx || N <= 0 || nsteps <= 0 || n_stages < 1 || first_stage < 0 || n_jitter < 1) return SCH_ERR_ARG;
+    if (!y || !bufs_a || !bufs_b || !theta0 || !wbar || !idx || !touts) return SCH_ERR_ARG;
+    for (int a = 0; a < PF_STAGE_ARRAYS - 1; ++a)
+        if (!bufs_a[a] || !bufs_b[a]) return SCH_ERR_ARG;
+    if ((bufs_a[PF_STAGE_ARRAYS - 1] == nullptr) != (bufs_b[PF_STAGE_ARRAYS - 1] == nullptr)) return SCH_ERR_ARG;
+    const size_t b = ctx->p.dtype == SCH_F32 ? 4 : 8;
+    const size_t rows[PF_STAGE_ARRAYS] = {ctx->p.n * b, ctx->p.n * b, ctx->p.n * b, (size_t)nsteps * ctx->p.K * b,
+                                          8, 8, (size_t)nsteps * ctx->p.K * b};
+    void* cur[PF_STAGE_ARRAYS];
+    void* nxt[PF_STAGE_ARRAYS];
+    for (int a = 0; a < PF_STAGE_ARRAYS; ++a) {
+        cur[a] = bufs_a[a];
+        nxt[a] = bufs_b[a];
+    }
+    cudaStream_t st = S(stream);
+    for (int k = 0; k < n_stages; ++k) {
+        const uint64_t stage_ctr = cycle * 1024 + (uint64_t)(first_stage + k);
+        double* out = touts + (size_t)k * 5;
+        int rc = pf_temper_dev(N, (const double*)cur[PF_NLL], (const double*)cur[PF_LOGG],
+                               k == 0 ? theta0 : touts + (size_t)(k - 1) * 5 + 2, ess_min, mode, wbar, out, stream);
+        if (rc != SCH_OK) return rc;
+        rc = pf_resample_gated(N, wbar, seed, stage_ctr, out + 4, idx, stream);
+        if (rc != SCH_OK) return rc;
+        // every state array in one gather launch, then the copies swap roles
+        const void* gs[PF_STAGE_ARRAYS];
+        void* gd[PF_STAGE_ARRAYS];
+        size_t gr[PF_STAGE_ARRAYS];
+        int na = 0;
+        for (int a = 0; a < PF_STAGE_ARRAYS; ++a) {
+            if (!cur[a]) continue;
+            gs[na] = cur[a];
+            gd[na] = nxt[a];
+            gr[na] = rows[a];
+            ++na;
+        }
+        rc = launch_gather_multi(N, idx, na, gs, gd, gr, st);
+        if (rc != SCH_OK) return rc;
+        for (int a = 0; a < PF_STAGE_ARRAYS; ++a) {
+            void* t = cur[a];
+            cur[a] = nxt[a];
+            nxt[a] = t;
+        }
+        if (events && events[2 * k]) cudaEventRecord((cudaEvent_t)events[2 * k], st);
+        rc = pf_jitter_dev(ctx, N, nsteps, n_jitter, out, rho, seed, stage_ctr * (uint64_t)n_jitter, cur[PF_M_START],
+                           cur[PF_DW], cur[PF_LAMBDA], y, (double*)cur[PF_NLL], (double*)cur[PF_LOGG], cur[PF_M_END],
+                           cur[PF_U_END], accepts, iters ? iters + (size_t)k * N : nullptr, status, stream);
+        if (rc != SCH_OK) return rc;
+        if (events && events[2 * k + 1]) cudaEventRecord((cudaEvent_t)events[2 * k + 1], st);
+    }
+    return SCH_OK;
 }
 
 int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, double scale, void* m, void* u,

@@ -86,12 +86,28 @@ __device__ __forceinline__ double ess_eval(double d, const double (&phi)[TEMPER_
 
 __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THREADS)
     temper_kernel(int N, const double* __restrict__ nll, const double* __restrict__ logG, double theta,
-                  double ess_min, double* __restrict__ wbar, double* __restrict__ out) {
+                  const double* __restrict__ theta_dev, double ess_min, int halving, double* __restrict__ wbar,
+                  double* __restrict__ out) {
     namespace cg = cooperative_groups;
     __shared__ TemperShm shm;
     TemperShm* sh = &shm;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
+    // device-gated stage: the temperature comes from the previous stage's result; a
+    // stage that starts at theta = 1 is inactive and only says so (out[4] = 0)
+    if (theta_dev) {
+        theta = *theta_dev;
+        if (theta >= 1.0) {
+            if (rank == 0 && threadIdx.x == 0) {
+                out[0] = 0.0;
+                out[1] = 0.0;
+                out[2] = 1.0;
+                out[3] = 0.0;
+                out[4] = 0.0;
+            }
+            return;
+        }
+    }
     const int gt = rank * TEMPER_THREADS + threadIdx.x;      // global thread index in the cluster
     constexpr int STRIDE = TEMPER_CTAS * TEMPER_THREADS;
     // thread gt owns particles gt, gt + STRIDE, ... (coalesced)
@@ -134,6 +150,17 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
     double d;
     if (ess >= ess_min) {
         d = rest;
+    } else if (halving) {
+        // the paper's search read literally: halve dtheta until the ESS passes, at most
+        // 60 times (the last point tried is kept if none passes)
+        d = rest;
+        for (int k = 1; k <= 60; ++k) {
+            d = ldexp(rest, -k);
+            double sc;
+            ess = ess_eval(d, phi, cnt, phimin, sh, parity, sc, wk);
+            s1 = sc;
+            if (ess >= ess_min) break;
+        }
     } else {
         const double dmin = ldexp(rest, -60);
         double lo = 0.0, glo = (double)N - ess_min, hi = rest, ghi = ess - ess_min;
@@ -183,6 +210,7 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
         out[1] = ess;
         out[2] = (d >= 1.0 - theta) ? 1.0 : theta + d;
         out[3] = ess_rest;
+        if (theta_dev) out[4] = 1.0;
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
@@ -193,10 +221,16 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
 // (equal to floor((i 2^53 + U) T / (N 2^53)) since 2^53 divides i 2^53 T).
 __global__ void __launch_bounds__(RESAMPLE_THREADS) resample_kernel(int N, const double* __restrict__ wbar,
                                                                     uint64_t seed, uint64_t stage_ctr,
+                                                                    const double* __restrict__ gate,
                                                                     int32_t* __restrict__ idx) {
     extern __shared__ __align__(16) unsigned long long Cs[];   // N inclusive sums
     __shared__ unsigned long long wsum[32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // an inactive device-gated stage keeps every particle in place
+    if (gate && *gate == 0.0) {
+        for (int i = t; i < N; i += blockDim.x) idx[i] = i;
+        return;
+    }
     const int per = (N + RESAMPLE_THREADS - 1) / RESAMPLE_THREADS;
     const int beg = t * per;
     const int end = min(N, beg + per);
@@ -254,23 +288,50 @@ __global__ void gather_kernel(int N, const int32_t* __restrict__ idx, const V* _
     }
 }
 
+// Row gathers of several arrays in one launch: blockIdx.y picks the array, whose rows
+// move in the widest vector (16, 8 or 4 bytes) that divides the row length.
+struct GatherSet {
+    const void* src[GATHER_MAX_ARRAYS];
+    void* dst[GATHER_MAX_ARRAYS];
+    size_t rowv[GATHER_MAX_ARRAYS];
+    int vw[GATHER_MAX_ARRAYS];
+};
+
+template <typename V>
+__device__ __forceinline__ void gather_rows(int N, const int32_t* __restrict__ idx, const V* __restrict__ src,
+                                            V* __restrict__ dst, size_t rowv) {
+    const size_t tot = (size_t)N * rowv;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < tot; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = q / rowv, col = q % rowv;
+        dst[q] = src[(size_t)idx[row] * rowv + col];
+    }
+}
+
+__global__ void gather_multi_kernel(int N, const int32_t* __restrict__ idx, GatherSet g) {
+    const int a = blockIdx.y;
+    if (g.vw[a] == 16) gather_rows<uint4>(N, idx, (const uint4*)g.src[a], (uint4*)g.dst[a], g.rowv[a]);
+    else if (g.vw[a] == 8) gather_rows<uint2>(N, idx, (const uint2*)g.src[a], (uint2*)g.dst[a], g.rowv[a]);
+    else gather_rows<unsigned>(N, idx, (const unsigned*)g.src[a], (unsigned*)g.dst[a], g.rowv[a]);
+}
+
 __global__ void copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, size_t n16) {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n16; q += (size_t)gridDim.x * blockDim.x)
         dst[q] = src[q];
 }
 
-int launch_temper(int N, const double* nll, const double* logG, double theta, double ess_min, double* wbar,
-                  double* out, cudaStream_t st) {
-    temper_kernel<<<TEMPER_CTAS, TEMPER_THREADS, 0, st>>>(N, nll, logG, theta, ess_min, wbar, out);
+int launch_temper(int N, const double* nll, const double* logG, double theta, const double* theta_dev,
+                  double ess_min, int halving, double* wbar, double* out, cudaStream_t st) {
+    temper_kernel<<<TEMPER_CTAS, TEMPER_THREADS, 0, st>>>(N, nll, logG, theta, theta_dev, ess_min, halving, wbar,
+                                                            out);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 
-int launch_resample_idx(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
-                        cudaStream_t st) {
+int launch_resample_idx(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, const double* gate,
+                        int32_t* idx, cudaStream_t st) {
     const size_t sm = (size_t)N * sizeof(unsigned long long);
     if (sm > 48 * 1024)
         cudaFuncSetAttribute(resample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    resample_kernel<<<1, RESAMPLE_THREADS, sm, st>>>(N, wbar, seed, stage_ctr, idx);
+    resample_kernel<<<1, RESAMPLE_THREADS, sm, st>>>(N, wbar, seed, stage_ctr, gate, idx);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 
@@ -293,6 +354,23 @@ int launch_gather(int N, const int32_t* idx, const void* src, void* dst, size_t 
         gather_kernel<unsigned><<<grid_for((size_t)N * rv), 256, 0, st>>>(N, idx, (const unsigned*)src,
                                                                          (unsigned*)dst, rv);
     }
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+int launch_gather_multi(int N, const int32_t* idx, int n, const void* const* src, void* const* dst,
+                        const size_t* row_bytes, cudaStream_t st) {
+    if (n < 1 || n > GATHER_MAX_ARRAYS) return SCH_ERR_ARG;
+    GatherSet g{};
+    size_t most = 0;
+    for (int a = 0; a < n; ++a) {
+        const int vw = row_bytes[a] % 16 == 0 ? 16 : (row_bytes[a] % 8 == 0 ? 8 : 4);
+        g.src[a] = src[a];
+        g.dst[a] = dst[a];
+        g.vw[a] = vw;
+        g.rowv[a] = row_bytes[a] / vw;
+        most = most > (size_t)N * g.rowv[a] ? most : (size_t)N * g.rowv[a];
+    }
+    gather_multi_kernel<<<dim3(grid_for(most), n), 256, 0, st>>>(N, idx, g);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 

@@ -58,7 +58,7 @@ extern "C" int pf_resample_static(int N, const double* wbar, uint64_t seed, uint
         if (rc != SCH_OK) return rc;
     }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    int rc = launch_resample_idx(N, wbar, seed, stage_ctr, idx, st);
+    int rc = launch_resample_idx(N, wbar, seed, stage_ctr, nullptr, idx, st);
     if (rc != SCH_OK) return rc;
     for (int a = 0; a < n_arrays; ++a) {
         rc = launch_gather(N, idx, arrays[a], ws, row_bytes[a], st);

@@ -113,6 +113,7 @@ template <typename R>
 struct JitterIO {
     int Ns, n_iter, particle0;
     double theta;
+    const double* tstate;   // device-gated stage: theta = tstate[2], active = tstate[4] != 0 (or null)
     R rho, sq1mr2;
     uint64_t seed, ctr;
     const R* m_start;
@@ -206,11 +207,15 @@ size_t wwindow_smem(int cs, int Ns, int K);
 size_t wjitter_smem(int cs, int Ns, int K);
 
 // filter kernels (pf_filter.cu)
-int launch_temper(int N, const double* nll, const double* logG, double theta, double ess_min, double* wbar,
+int launch_temper(int N, const double* nll, const double* logG, double theta, const double* theta_dev,
+                  double ess_min, int halving, double* wbar,
                   double* out, cudaStream_t st);
-int launch_resample_idx(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
-                        cudaStream_t st);
+int launch_resample_idx(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, const double* gate,
+                        int32_t* idx, cudaStream_t st);
 int launch_gather(int N, const int32_t* idx, const void* src, void* dst, size_t row_bytes, cudaStream_t st);
 int launch_copy(const void* src, void* dst, size_t bytes, cudaStream_t st);
+constexpr int GATHER_MAX_ARRAYS = 8;
+int launch_gather_multi(int N, const int32_t* idx, int n, const void* const* src, void* const* dst,
+                        const size_t* row_bytes, cudaStream_t st);
 
 }  // namespace sch

@@ -867,6 +867,9 @@ template <typename R, int C, int TP, int S>
 __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<R> A, JitterIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
+    // a device-gated stage reads its temperature, and does nothing when inactive
+    if (io.tstate && io.tstate[4] == 0.0) return;
+    const double theta = io.tstate ? io.tstate[2] : io.theta;
     const int p = blockIdx.x;
     const int Ns = io.Ns, K = A.K, NK = Ns * K;
     R* noise = reinterpret_cast<R*>(smem_raw + shm_base_bytes<R, TP>());
@@ -912,8 +915,8 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<
         block_sum2<R, TP>(sh, mis, gl);
         if (threadIdx.x == 0) {
             const double nll1 = 0.5 * mis, lg1 = -gl;
-            const double w0 = io.theta * (sh_state[0] - sh_state[1]);
-            const double w1 = io.theta * (nll1 - lg1);
+            const double w0 = theta * (sh_state[0] - sh_state[1]);
+            const double w1 = theta * (nll1 - lg1);
             const double logU = log(uniform_open0(io.seed, SCH_TAG_PCN_ACCEPT, (uint64_t)(io.particle0 + p), ctr));
             const int acc = (fl == 0) && (logU < w0 - w1);
             sh_acc = acc;

@@ -474,6 +474,9 @@ template <int CS, int P>
 __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, WArgs W, JitterIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* R0sm = reinterpret_cast<float2*>(smem_raw);
+    // a device-gated stage reads its temperature, and does nothing when inactive
+    if (io.tstate && io.tstate[4] == 0.0) return;
+    const double theta = io.tstate ? io.tstate[2] : io.theta;
     const int p = blockIdx.x;
     const int lane = threadIdx.x;
     const int Ns = io.Ns, K = A.K, NK = Ns * K;
@@ -515,8 +518,8 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
         const double nll1 = 0.5 * mis, lg1 = -gl;
         int acc = 0;
         if (lane == 0) {
-            const double w0 = io.theta * (nll0 - lg0);
-            const double w1 = io.theta * (nll1 - lg1);
+            const double w0 = theta * (nll0 - lg0);
+            const double w1 = theta * (nll1 - lg1);
             const double logU = log(uniform_open0(io.seed, SCH_TAG_PCN_ACCEPT, (uint64_t)(io.particle0 + p), ctr));
             acc = (fl == 0) && (logU < w0 - w1);
         }

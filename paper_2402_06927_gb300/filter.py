@@ -5,18 +5,22 @@ The cycle works on the (X_start, dW) representation of a particle
 window (with the fused likelihood epilogue), then repeat adaptive tempering,
 systematic resampling and PCN jittering until the temperature reaches one;
 finally the end state becomes the next window's start.  Every step is a call
-into the CUDA library; the host only reads back the 32-byte tempering result
-of each stage to decide whether another stage is needed.
+into the CUDA library.  By default the first `eager_stages` stages are all
+enqueued at once as device-gated stages (a stage that starts at temperature one
+does nothing), and the host reads the stages' tempering results back once per
+cycle; only a cycle that needs more stages continues stage by stage, reading back
+each stage's 40-byte result to decide whether another is needed.
 """
 from __future__ import annotations
 
+import ctypes as ct
 from dataclasses import dataclass, field
 from typing import List, Optional
 
 import torch
 
 from . import _lib
-from .api import SchModel, pf_gather_rows, pf_resample, pf_temper
+from .api import SchModel, pf_gather_rows, pf_resample, pf_resample_gated, pf_temper, pf_temper_dev
 
 
 @dataclass
@@ -36,7 +40,8 @@ class CycleStats:
 
 
 class KernelTimer:
-    """CUDA events around the jitter launches of a cycle (on the launching stream)."""
+    """CUDA events around the jitter launches of a cycle (on the launching stream);
+    launches of inactive device-gated stages are dropped after the cycle."""
 
     def __init__(self):
         self.pairs = []
@@ -50,8 +55,11 @@ class EnsembleFilter:
     """GPU state of an N-particle tempering + jittering filter."""
 
     def __init__(self, model: SchModel, N: int, Ns: int, ess_min: float, rho: float, n_jitter: int,
-                 seed: int, lam: Optional[torch.Tensor] = None):
+                 seed: int, lam: Optional[torch.Tensor] = None, temper_mode: str = "largest",
+                 eager_stages: int = 2):
         self.model, self.N, self.Ns = model, N, Ns
+        self.temper_mode = temper_mode   # "largest" or "halving" (pf_temper / pf_temper_halving)
+        self.eager_stages = eager_stages  # device-gated stages enqueued at once (0: stage by stage)
         self.ess_min, self.rho, self.n_jitter, self.seed = ess_min, rho, n_jitter, seed
         dt, dev, n, K = model.dtype, torch.device("cuda"), model.n, model.K
 
@@ -72,6 +80,10 @@ class EnsembleFilter:
         self.wbar = torch.zeros(N, dtype=torch.float64, device=dev)
         self.tout = torch.zeros(4, dtype=torch.float64, device=dev)
         self.tout_host = torch.zeros(4, dtype=torch.float64).pin_memory()
+        S = max(1, eager_stages)   # mean stages per cycle at the bench size: 1.24
+        self.touts = torch.zeros((S, 5), dtype=torch.float64, device=dev)
+        self.touts_host = torch.zeros((S, 5), dtype=torch.float64).pin_memory()
+        self.theta0 = torch.zeros(1, dtype=torch.float64, device=dev)
         self.idx = torch.zeros(N, dtype=torch.int32, device=dev)
         self.accepts = torch.zeros(N, dtype=torch.int32, device=dev)
         self.status = torch.zeros(N, dtype=torch.int32, device=dev)
@@ -90,8 +102,7 @@ class EnsembleFilter:
             self._b["lam"] = torch.empty_like(lam)
         self.lam.copy_(lam)
 
-    def _resample(self, stage_ctr: int) -> None:
-        pf_resample(self.wbar, self.seed, stage_ctr, idx=self.idx)
+    def _gather_all(self) -> None:
         names = ["m_start", "m_end", "u_end", "dW", "nll", "logG"] + (["lam"] if self.lam is not None else [])
         for name in names:
             cur = getattr(self, name)
@@ -99,6 +110,26 @@ class EnsembleFilter:
             pf_gather_rows(self.idx, cur, nxt)
             setattr(self, name, nxt)
             self._b[name] = cur
+
+    def _jitter(self, y, theta, stage_ctr, timer, tstate=None):
+        m = self.model
+        iters = None
+        if timer is not None:
+            iters = torch.zeros(self.N, dtype=torch.int32, device=self.nll.device)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record()
+        m.jitter(self.m_start, self.dW, self.lam, y, self.nll, self.logG, self.m_end, self.u_end, theta,
+                 self.rho, self.n_jitter, self.seed, stage_ctr * self.n_jitter, accepts=self.accepts,
+                 status=self.status, iters=iters, tstate=tstate)
+        if timer is not None:
+            ev1.record()
+            timer.pairs.append((ev0, ev1))
+            timer.iters.append(iters)
+
+    def _resample(self, stage_ctr: int) -> None:
+        pf_resample(self.wbar, self.seed, stage_ctr, idx=self.idx)
+        self._gather_all()
 
     def cycle(self, y: torch.Tensor, cycle: int, max_stages: int = 64,
               timer: Optional[KernelTimer] = None, dW: Optional[torch.Tensor] = None) -> CycleStats:
@@ -116,27 +147,67 @@ class EnsembleFilter:
         st.launches += 2
         st.ess0 = None
         theta, k = 0.0, 0
+        if self.eager_stages > 0:
+            # device-gated stages enqueued by one library call (pf_gated_stages): stage k
+            # reads its temperature from stage k-1's result and does nothing but copy the
+            # rows once the temperature is one; the host reads all results back once
+            S = min(self.eager_stages, max_stages)
+            names = ["m_start", "m_end", "u_end", "dW", "nll", "logG", "lam"]
+            cur = [getattr(self, nm) if nm != "lam" else self.lam for nm in names]
+            nxt = [self._b.get(nm) for nm in names]
+            ptr = lambda t: None if t is None else t.data_ptr()
+            bufs_a = (ct.c_void_p * 7)(*[ptr(t) for t in cur])
+            bufs_b = (ct.c_void_p * 7)(*[ptr(t) for t in nxt])
+            iters = evs = None
+            if timer is not None:
+                iters = torch.zeros((S, self.N), dtype=torch.int32, device=self.nll.device)
+                pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                         for _ in range(S)]
+                for a, b in pairs:   # create the events; the library records them again
+                    a.record()
+                    b.record()
+                evs = (ct.c_void_p * (2 * S))(*[e.cuda_event for ab in pairs for e in ab])
+            _lib.check(_lib.lib().pf_gated_stages(
+                m.handle, self.N, self.Ns, S, 0, self.ess_min, {"largest": 0, "halving": 1}[self.temper_mode],
+                self.rho, self.n_jitter, self.seed, cycle, ct.c_void_p(y.data_ptr()), bufs_a, bufs_b,
+                ct.c_void_p(self.theta0.data_ptr()), ct.c_void_p(self.wbar.data_ptr()),
+                ct.c_void_p(self.idx.data_ptr()), ct.c_void_p(self.touts.data_ptr()),
+                ct.c_void_p(self.accepts.data_ptr()), ct.c_void_p(ptr(iters)), ct.c_void_p(self.status.data_ptr()),
+                evs, ct.c_void_p(torch.cuda.current_stream().cuda_stream)), "pf_gated_stages")
+            if S % 2 == 1:   # every stage gathers a -> b: an odd count leaves the state in the b copies
+                for nm, c, n2 in zip(names, cur, nxt):
+                    if c is None:
+                        continue
+                    setattr(self, nm, n2)
+                    self._b[nm] = c
+            st.launches += S * 4
+            n0 = len(timer.pairs) if timer is not None else 0
+            if timer is not None:
+                timer.pairs.extend(pairs)
+                timer.iters.extend(iters[k] for k in range(S))
+            self.touts_host.copy_(self.touts, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            for k in range(S):
+                d, e, theta_new, e_rest, active = (float(v) for v in self.touts_host[k])
+                if active == 0.0:
+                    if timer is not None:
+                        del timer.pairs[n0 + k:], timer.iters[n0 + k:]
+                    break
+                st.forward_steps += self.N * self.Ns * self.n_jitter
+                st.stages.append(StageStats(d, e, theta_new))
+                if k == 0:
+                    st.ess0 = e_rest
+                theta = theta_new
+            k = len(st.stages)
         while theta < 1.0 and k < max_stages:
-            pf_temper(self.nll, self.logG, theta, self.ess_min, wbar=self.wbar, out=self.tout)
+            pf_temper(self.nll, self.logG, theta, self.ess_min, wbar=self.wbar, out=self.tout, mode=self.temper_mode)
             self.tout_host.copy_(self.tout, non_blocking=True)
             torch.cuda.current_stream().synchronize()
             d, e, theta_new = (float(v) for v in self.tout_host[:3])
             stage_ctr = cycle * 1024 + k
             self._resample(stage_ctr)
             theta = theta_new
-            iters = None
-            if timer is not None:
-                iters = torch.empty(self.N, dtype=torch.int32, device=self.nll.device)
-                ev0 = torch.cuda.Event(enable_timing=True)
-                ev1 = torch.cuda.Event(enable_timing=True)
-                ev0.record()
-            m.jitter(self.m_start, self.dW, self.lam, y, self.nll, self.logG, self.m_end, self.u_end, theta,
-                     self.rho, self.n_jitter, self.seed, stage_ctr * self.n_jitter, accepts=self.accepts,
-                     status=self.status, iters=iters)
-            if timer is not None:
-                ev1.record()
-                timer.pairs.append((ev0, ev1))
-                timer.iters.append(iters)
+            self._jitter(y, theta, stage_ctr, timer)
             st.forward_steps += self.N * self.Ns * self.n_jitter
             st.launches += 2 + len(self._b) + 1
             st.stages.append(StageStats(d, e, theta))

@@ -83,6 +83,12 @@ def test_host_argument_errors_need_no_gpu(lib):
     # empty ensembles are a no-op
     assert lib.sch_ensemble_step(h, 0, 5, None, None, None, None, None, None, None, None, None, None, None) == 0
     assert lib.pf_temper(0, None, None, 0.0, 1.0, None, None, None) == -1
+    assert lib.pf_temper_halving(0, None, None, 0.0, 1.0, None, None, None) == -1
+    # device-gated stage entry points: missing device scalars are argument errors
+    assert lib.pf_temper_dev(4, ct.c_void_p(16), None, None, 1.0, 0, ct.c_void_p(16), ct.c_void_p(16), None) == -1
+    assert lib.pf_temper_dev(4, ct.c_void_p(16), None, ct.c_void_p(16), 1.0, 7, ct.c_void_p(16), ct.c_void_p(16),
+                             None) == -1
+    assert lib.pf_resample_gated(4, ct.c_void_p(16), 0, 0, None, ct.c_void_p(16), None) == -1
     assert lib.pf_temper(4, ct.c_void_p(16), None, 1.0, 1.0, ct.c_void_p(16), ct.c_void_p(16), None) == -1
     assert lib.pf_resample(9000, ct.c_void_p(16), 0, 0, ct.c_void_p(16), 0, None, None, None, 0, None) == -1
     arr = (ct.c_void_p * 1)(16)

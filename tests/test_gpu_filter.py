@@ -44,6 +44,21 @@ def test_temper_matches_oracle(N, spread, theta):
     assert abs(out[3] - e_rest) <= 1e-12 * e_rest
 
 
+@pytest.mark.parametrize("N,spread,theta", [(7, 0.01, 0.0), (64, 5.0, 0.0), (1024, 30.0, 0.25), (8192, 80.0, 0.5)])
+def test_temper_halving_matches_oracle(N, spread, theta):
+    # the halving search tries exact dyadic points: dtheta equal to the oracle's unless an ESS
+    # lies within rounding of the threshold (then the neighbouring point)
+    api = require_lib()
+    phi = random_logweights(N, N + 7, spread)
+    w, out = api.pf_temper(tdev(phi, torch.float64), None, theta, 0.5 * N, mode="halving")
+    out = out.cpu().numpy()
+    d, wb, e = OF.temper(phi, theta, 0.5 * N, mode="halving")
+    assert out[0] == d or out[0] in (2 * d, 0.5 * d)
+    if out[0] == d:
+        assert abs(out[1] - e) <= 1e-12 * e
+        assert np.allclose(w.cpu().numpy(), wb, rtol=1e-11, atol=1e-300)
+
+
 @pytest.mark.parametrize("N", [1, 2, 5, 100, 1024, 8192])
 def test_resample_bit_exact_given_oracle_weights(N):
     api = require_lib()
@@ -127,7 +142,10 @@ def test_jitter_theta_zero_accepts_everything():
     assert np.all(acc.cpu().numpy() == 3)
 
 
-def test_cycle_matches_oracle_f64():
+@pytest.mark.parametrize("eager,mode", [(3, "largest"), (0, "largest"), (1, "largest"), (3, "halving")])
+def test_cycle_matches_oracle_f64(eager, mode):
+    # eager = 3: stages enqueued as device-gated stages; 0: stage by stage; 1: one gated
+    # stage, then the stage-by-stage fallback; halving: the paper's search read literally
     from paper_2402_06927_gb300.filter import EnsembleFilter
     cfg = get_config("cfg1_f64", N=16, n_jitter=2)
     g = gpu_model(cfg)
@@ -138,8 +156,10 @@ def test_cycle_matches_oracle_f64():
     y = random_obs(cfg, 71)
     seed, cycle = 9, 2
     dW = ORNG.window_increments(seed, ORNG.TAG_PRIOR_DW, N, cfg.Ns, cfg.K, cfg.dt, cycle)
-    ref = OF.assimilation_cycle(om, m0, y, cfg.sigma, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, cycle, dW=dW)
-    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    ref = OF.assimilation_cycle(om, m0, y, cfg.sigma, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, cycle, dW=dW,
+                                temper_mode=mode)
+    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, temper_mode=mode,
+                       eager_stages=eager)
     f.set_state(tdev(m0, g.dtype))
     st = f.cycle(tdev(y, g.dtype), cycle)
     assert len(st.stages) == len(ref["stages"])
@@ -148,3 +168,27 @@ def test_cycle_matches_oracle_f64():
         assert abs(a.theta - b["theta"]) <= 1e-9
     assert rel_err(f.u_end.cpu().numpy(), ref["u_end"]) < 1e-8
     assert rel_err(f.dW.cpu().numpy(), ref["dW"]) < 1e-8
+
+
+def test_gated_stages_equal_stage_by_stage_fp32():
+    # the same FP32 cycles with device-gated stages and stage by stage: the same kernels take
+    # the same decisions, so every array and stage statistic is bit-identical
+    from paper_2402_06927_gb300.filter import EnsembleFilter
+    from workloads import u0_profile
+    cfg = get_config("cfg2_f32")
+    g = gpu_model(cfg)
+    N = 256
+    u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
+    m0, _ = g.prior_sample(N, u0, 4, cfg.prior_scale)
+    fs = [EnsembleFilter(g, N, cfg.Ns, 0.5 * N, cfg.rho, 3, 11, eager_stages=e) for e in (3, 0)]
+    for f in fs:
+        f.set_state(m0)
+    for c in range(3):
+        y = g.synth_obs(u0, 20 + c, 1)
+        sts = [f.cycle(y, c) for f in fs]
+        assert [(s.dtheta, s.ess, s.theta) for s in sts[0].stages] == [(s.dtheta, s.ess, s.theta) for s in sts[1].stages]
+        assert sts[0].forward_steps == sts[1].forward_steps
+        for name in ("m_start", "m_end", "u_end", "dW", "nll", "logG"):
+            assert torch.equal(getattr(fs[0], name), getattr(fs[1], name)), name
+        for f in fs:
+            f.advance()

@@ -20,6 +20,7 @@ import pytest
 from scipy import stats
 
 from oracle import filter as F
+from workloads import random_logweights
 from oracle import rng
 
 
@@ -99,6 +100,25 @@ def test_temper_against_dense_scan():
             assert last - 1e-12 <= d <= last + step
             assert abs(e - ess_min) < 1e-6 * N
         assert np.isclose(wbar.sum(), 1.0)
+
+
+def test_temper_halving_against_enumeration():
+    # halving mode: the first passing point of the sequence (1 - theta) 2^-k, found by
+    # enumerating the sequence with the brute-force ESS
+    def ess_bf(w):
+        w = np.asarray(w, dtype=np.float64)
+        return w.sum() ** 2 / (w * w).sum()
+    for seed, spread, theta in ((1, 30.0, 0.0), (2, 3.0, 0.4), (3, 300.0, 0.9), (4, 0.001, 0.0)):
+        phi = random_logweights(64, seed, spread)
+        N = len(phi)
+        d, wbar, e = F.temper(phi, theta, 0.5 * N, mode="halving")
+        rest = 1.0 - theta
+        ks = [k for k in range(61) if ess_bf(np.exp(-rest * 2.0 ** -k * (phi - phi.min()))) >= 0.5 * N]
+        assert d == rest * 2.0 ** -(ks[0] if ks else 60)
+        assert np.isclose(wbar.sum(), 1.0)
+        # never above the largest passing point
+        d_big, _, _ = F.temper(phi, theta, 0.5 * N)
+        assert d <= d_big * (1 + 1e-12)
 
 
 def test_temper_stages_sum_to_one():
