@@ -304,13 +304,13 @@ def run_ours(args):
             c = args.warmup + k
             flush.fill_(float(k))                     # evict the ensemble from L2 (untimed)
             e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
             st = f.cycle(ys[c], c, timer=timer)
             f.advance()
-            e1.record()
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
+            # device time of the cycle: from before its first launch to after its last one
+            # (the filter records end_event after the cycle's last launch, before it waits)
+            f.end_event.synchronize()
+            step_ms.append(e0.elapsed_time(f.end_event))
             fwd += st.forward_steps
             launches += st.launches
             stages.append(len(st.stages))
@@ -347,7 +347,7 @@ def run_ours(args):
     mean_host = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
     dg_host = torch.empty(8, dtype=torch.float64).pin_memory()
     y_dev = torch.empty_like(ys[0])
-    e2e_steps = min(args.steps, 3)
+    e2e_steps = min(args.steps, 30)
     f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
     f2.set_state(m0)
     torch.cuda.synchronize()

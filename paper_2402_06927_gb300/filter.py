@@ -84,6 +84,8 @@ class EnsembleFilter:
         self.touts = torch.zeros((S, 5), dtype=torch.float64, device=dev)
         self.touts_host = torch.zeros((S, 5), dtype=torch.float64).pin_memory()
         self.theta0 = torch.zeros(1, dtype=torch.float64, device=dev)
+        # recorded after the last launch of each cycle: the end of the cycle's device work
+        self.end_event = torch.cuda.Event(enable_timing=True)
         self.idx = torch.zeros(N, dtype=torch.int32, device=dev)
         self.accepts = torch.zeros(N, dtype=torch.int32, device=dev)
         self.status = torch.zeros(N, dtype=torch.int32, device=dev)
@@ -174,6 +176,7 @@ class EnsembleFilter:
                 ct.c_void_p(self.idx.data_ptr()), ct.c_void_p(self.touts.data_ptr()),
                 ct.c_void_p(self.accepts.data_ptr()), ct.c_void_p(ptr(iters)), ct.c_void_p(self.status.data_ptr()),
                 evs, ct.c_void_p(torch.cuda.current_stream().cuda_stream)), "pf_gated_stages")
+            self.end_event.record()
             if S % 2 == 1:   # every stage gathers a -> b: an odd count leaves the state in the b copies
                 for nm, c, n2 in zip(names, cur, nxt):
                     if c is None:
@@ -208,6 +211,7 @@ class EnsembleFilter:
             self._resample(stage_ctr)
             theta = theta_new
             self._jitter(y, theta, stage_ctr, timer)
+            self.end_event.record()
             st.forward_steps += self.N * self.Ns * self.n_jitter
             st.launches += 2 + len(self._b) + 1
             st.stages.append(StageStats(d, e, theta))
