@@ -4,7 +4,9 @@ Sec. 3 of the paper: likelihood weights (Eq. loglikeq), effective sample size
 (Eq. ess), adaptive tempering (Sec. 3.1.2), systematic resampling
 (Sec. 3.1.1, Gordon et al. 1993), PCN jittering of the noise increments
 (Sec. 3.1.2), the discrete Girsanov weight of a nudged path
-(Eq. girsanov DG approx) and the diagnostics EMRE, RB, RES (Sec. 4.1.1).
+(Eq. girsanov DG approx), the diagnostics EMRE, RB, RES (Sec. 4.1.1) and a
+MALA jitter on the PCN jitter's target (the gradient-informed move Sec. 5
+lists as future work; preconditioner C = dt, the prior covariance of dW).
 
 Readings of the text that the code fixes:
 * observation points are the M distinct nodes x_j = j L / M, j = 0..M-1; an
@@ -207,6 +209,82 @@ def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, sta
         u_end[acc] = pu[acc]
         accepts += acc
     return dW, cur_nll, cur_logG, m_end, u_end, accepts
+
+
+# ---------------------------------------------------------------------- #
+# MALA jitter: the gradient-informed move Sec. 5 names as future work
+# ---------------------------------------------------------------------- #
+def mala_step(U, grad_U, x, h, C, z, logu):
+    """One preconditioned MALA step (Roberts and Tweedie 1996) for the density
+    exp(-U): the proposal x' = x - (h/2) C grad U(x) + sqrt(h C) z (C diagonal) is
+    accepted iff log u < U(x) - U(x') + log q(x | x') - log q(x' | x), with
+    log q(b | a) = -|b - a + (h/2) C grad U(a)|^2_{(h C)^-1} / 2.
+    A proposal where U is not finite is rejected.  Returns (x_next, accepted).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    C = np.broadcast_to(np.asarray(C, dtype=np.float64), x.shape)
+    g = grad_U(x)
+    xp = x - 0.5 * h * C * g + np.sqrt(h * C) * z
+    gp = grad_U(xp)
+
+    def logq(b, a, ga):
+        r = b - a + 0.5 * h * C * ga
+        return -0.5 * np.sum(r * r / (h * C))
+
+    log_alpha = U(x) - U(xp) + logq(x, xp, gp) - logq(xp, x, g)
+    ok = bool(np.isfinite(U(xp)) and logu < log_alpha)
+    return (xp if ok else x), ok
+
+
+def mala_target(model, m_start, dW, lam, y, sigma, theta):
+    """U(dW) and grad U for one particle's window noise dW [Ns, K] at temperature theta:
+    the PCN jitter's target exp(-theta (NLL - log G)) times the N(0, dt) prior of dW,
+
+        U(dW) = theta (NLL(dW) - log G(dW)) + |dW|^2 / (2 dt).
+
+    With J = NLL + 1/2 dt |lambda|^2, NLL - log G = J + sum lambda dW.  The noise
+    applied at a step is dW + lambda dt, so dNLL/ddW = (dNLL/dlambda) / dt, with
+    dNLL/dlambda = dJ/dlambda - dt lambda from the tangent-linear model, and
+    grad U = theta (dNLL/ddW + lambda) + dW / dt.
+    """
+    from oracle import nudge as _N
+    dt = model.dt
+    x = np.asarray(dW, dtype=np.float64)
+    la = np.zeros_like(x) if lam is None else np.asarray(lam, dtype=np.float64)
+    J, g_lam = _N.cost_and_gradient(model, m_start, x, la, y, sigma)
+    U = theta * (J + np.sum(la * x)) + np.sum(x * x) / (2.0 * dt)
+    gU = theta * ((g_lam - dt * la) / dt + la) + x / dt
+    return U, gU
+
+
+def mala_jitter(model, m_start, dW, lam, y, sigma, theta, h, n_iter, seed, ctr, particle0=0):
+    """n_iter MALA moves of every particle's window noise (``mala_target``) with
+    preconditioner C = dt (the prior covariance of dW).  For iteration j the
+    proposal normals are keyed (seed, TAG_MALA) at counter (k // 4, step,
+    particle0 + p, ctr + j) and the accept uniform (seed, TAG_MALA_ACCEPT) at
+    (0, 0, particle0 + p, ctr + j).  Returns (dW, nll, logG, accepts), nll and
+    logG those of the final noise.
+    """
+    N, Ns, K = np.shape(dW)
+    dt = model.dt
+    dW = np.array(dW, dtype=np.float64)
+    lam_arr = np.zeros_like(dW) if lam is None else np.asarray(lam, dtype=np.float64)
+    accepts = np.zeros(N, dtype=np.int64)
+    pidx = np.arange(particle0, particle0 + N, dtype=np.uint64)
+    for j in range(n_iter):
+        z = _rng.window_increments(seed, _rng.TAG_MALA, N, Ns, K, 1.0, ctr + j, particle0)
+        logu = np.log(_rng.uniform_open0(seed, _rng.TAG_MALA_ACCEPT, pidx, np.uint64(ctr + j)))
+        for p in range(N):
+            def U(x, p=p):
+                return mala_target(model, m_start[p], x, lam_arr[p], y, sigma, theta)[0]
+
+            def gU(x, p=p):
+                return mala_target(model, m_start[p], x, lam_arr[p], y, sigma, theta)[1]
+
+            dW[p], ok = mala_step(U, gU, dW[p], h, dt, z[p], logu[p])
+            accepts[p] += ok
+    _, u_end, _, _ = model.ensemble_window(m_start, dW, lam_arr)
+    return dW, nll(u_end, y, sigma), girsanov_logG(lam_arr, dW, dt), accepts
 
 
 # ---------------------------------------------------------------------- #

@@ -35,6 +35,8 @@ TAG_TRUTH = 5        # truth noise                   ctr = (block, step, 0, cycl
 TAG_OBS = 6          # observation noise             ctr = (block, 0, 0, cycle)
 TAG_INIT = 7         # prior ensemble perturbation   ctr = (block, 0, particle, 0)
 TAG_NUDGE = 8        # noise revealed during sequential nudging
+TAG_MALA = 9         # MALA proposal noise           ctr = (block, step, particle, iter ctr)
+TAG_MALA_ACCEPT = 10  # MALA accept uniform          ctr = (0, 0, particle, iter ctr)
 
 
 def philox4x64_scalar(ctr, key):
