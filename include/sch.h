@@ -78,7 +78,8 @@ enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
 
 enum {
     SCH_TAG_PRIOR_DW = 1, SCH_TAG_PCN = 2, SCH_TAG_PCN_ACCEPT = 3, SCH_TAG_RESAMPLE = 4,
-    SCH_TAG_TRUTH = 5, SCH_TAG_OBS = 6, SCH_TAG_INIT = 7, SCH_TAG_NUDGE = 8
+    SCH_TAG_TRUTH = 5, SCH_TAG_OBS = 6, SCH_TAG_INIT = 7, SCH_TAG_NUDGE = 8,
+    SCH_TAG_MALA = 9, SCH_TAG_MALA_ACCEPT = 10
 };
 
 #define SCH_MAX_K 64
@@ -266,6 +267,29 @@ int pf_jitter_dev(sch_ctx* ctx, int N, int nsteps, int n_iter, const double* tst
                   uint64_t seed, uint64_t ctr, const void* m_start, void* dW, const void* lambda,
                   const void* y, double* nll, double* logG, void* m_end, void* u_end,
                   int32_t* accepts, int32_t* iters, int32_t* status, void* stream);
+
+/* MALA jitter of the window noise: the gradient-informed jitter that Sec. 5 lists as
+ * future work, on the target of the PCN jitter (Sec. 3.1.2),
+ *   U(dW) = theta (NLL - log G) + |dW|^2 / (2 dt) = theta (J + sum lambda dW) + |dW|^2 / (2 dt),
+ * J the window cost of sch_adjoint_window, grad U = theta (dJ/ddW + lambda) + dW / dt,
+ * preconditioner C = dt (the prior covariance of dW).  One iteration j:
+ *   pf_mala_propose  dW' = dW - (h/2) dt grad U(dW) + sqrt(h dt) z, z ~ N(0, 1) keyed
+ *                    (seed, SCH_TAG_MALA) at counter (k / 4, step, particle0 + p, ctr);
+ *   sch_adjoint_window at dW', giving J' and gJ' = dJ'/ddW';
+ *   pf_mala_accept   accepts iff log u < U(dW) - U(dW') + log q(dW | dW') - log q(dW' | dW)
+ *                    and U(dW') is finite, log q(b | a) = -|b - a + (h/2) dt grad U(a)|^2
+ *                    / (2 h dt), u keyed (seed, SCH_TAG_MALA_ACCEPT) at counter
+ *                    (0, 0, particle0 + p, ctr); on acceptance dW, J and gJ take the
+ *                    proposal's values and accepts[p] (may be NULL) grows by one.
+ * dW, dW_prop, lambda (NULL: no drift), gJ, gJ_prop: real [N][nsteps][K], device;
+ * J, J_prop: double [N], device.  h > 0, theta in [0, 1], else SCH_ERR_ARG; N = 0 is a
+ * no-op.  Both enqueue one kernel on the stream and allocate nothing. */
+int pf_mala_propose(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint64_t seed, uint64_t ctr,
+                    int particle0, const void* dW, const void* lambda, const void* gJ, void* dW_prop,
+                    void* stream);
+int pf_mala_accept(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint64_t seed, uint64_t ctr,
+                   int particle0, void* dW, const void* dW_prop, const void* lambda, double* J,
+                   const double* J_prop, void* gJ, const void* gJ_prop, int32_t* accepts, void* stream);
 
 /* n_stages device-gated stages of an assimilation cycle (Sec. 3.1.2) enqueued in one
  * call, with no host round trip: for stage k, pf_temper_dev (temperature from

@@ -27,6 +27,7 @@ SCH_F32 = 1
 SCH_SOLVER_AUTO, SCH_SOLVER_LI, SCH_SOLVER_EA = 0, 1, 2
 
 TAG_PRIOR_DW, TAG_PCN, TAG_PCN_ACCEPT, TAG_RESAMPLE, TAG_TRUTH, TAG_OBS, TAG_INIT, TAG_NUDGE = range(1, 9)
+TAG_MALA, TAG_MALA_ACCEPT = 9, 10
 
 
 class SchParams(ct.Structure):
@@ -71,6 +72,8 @@ SIGNATURES = {
     "pf_resample_static": [I, P, U64, U64, P, I, P, P, P],
     "pf_jitter": [P, I, I, I, D, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
     "pf_jitter_dev": [P, I, I, I, P, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
+    "pf_mala_propose": [P, I, I, D, D, U64, U64, I, P, P, P, P, P],
+    "pf_mala_accept": [P, I, I, D, D, U64, U64, I, P, P, P, P, P, P, P, P, P],
     "pf_gated_stages": [P, I, I, I, I, D, I, D, I, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
     "sch_prior_sample": [P, I, P, U64, D, P, P, P],
     "sch_adjoint_window": [P, I, I, I, P, P, P, P, P, P, P, P, P, P, P, SZ, P],

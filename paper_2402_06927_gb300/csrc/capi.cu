@@ -621,6 +621,39 @@ int pf_gated_stages(sch_ctx* ctx, int N, int nsteps, int n_stages, int first_sta
     return SCH_OK;
 }
 
+static bool mala_args_ok(const sch_ctx* ctx, int N, int nsteps, int particle0, double theta, double h) {
+    return ctx && N >= 0 && nsteps > 0 && particle0 >= 0 && h > 0.0 && theta >= 0.0 && theta <= 1.0;
+}
+
+int pf_mala_propose(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint64_t seed, uint64_t ctr,
+                    int particle0, const void* dW, const void* lambda, const void* gJ, void* dW_prop, void* stream) {
+    if (!mala_args_ok(ctx, N, nsteps, particle0, theta, h)) return SCH_ERR_ARG;
+    if (N == 0) return SCH_OK;
+    if (!dW || !gJ || !dW_prop) return SCH_ERR_ARG;
+    const int K = ctx->p.K;
+    if (ctx->p.dtype == SCH_F32)
+        return launch_mala_propose<float>(N, nsteps, K, theta, h, ctx->p.dt, (const float*)dW, (const float*)lambda,
+                                          (const float*)gJ, seed, ctr, particle0, (float*)dW_prop, S(stream));
+    return launch_mala_propose<double>(N, nsteps, K, theta, h, ctx->p.dt, (const double*)dW, (const double*)lambda,
+                                       (const double*)gJ, seed, ctr, particle0, (double*)dW_prop, S(stream));
+}
+
+int pf_mala_accept(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint64_t seed, uint64_t ctr,
+                   int particle0, void* dW, const void* dW_prop, const void* lambda, double* J, const double* J_prop,
+                   void* gJ, const void* gJ_prop, int32_t* accepts, void* stream) {
+    if (!mala_args_ok(ctx, N, nsteps, particle0, theta, h)) return SCH_ERR_ARG;
+    if (N == 0) return SCH_OK;
+    if (!dW || !dW_prop || !J || !J_prop || !gJ || !gJ_prop) return SCH_ERR_ARG;
+    const int NK = nsteps * ctx->p.K;
+    if (ctx->p.dtype == SCH_F32)
+        return launch_mala_accept<float>(N, NK, theta, h, ctx->p.dt, seed, ctr, particle0, (float*)dW,
+                                         (const float*)dW_prop, (const float*)lambda, J, J_prop, (float*)gJ,
+                                         (const float*)gJ_prop, accepts, S(stream));
+    return launch_mala_accept<double>(N, NK, theta, h, ctx->p.dt, seed, ctr, particle0, (double*)dW,
+                                      (const double*)dW_prop, (const double*)lambda, J, J_prop, (double*)gJ,
+                                      (const double*)gJ_prop, accepts, S(stream));
+}
+
 int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, double scale, void* m, void* u,
                      void* stream) {
     if (!ctx || N < 0) return SCH_ERR_ARG;

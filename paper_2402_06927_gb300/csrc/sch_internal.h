@@ -206,6 +206,15 @@ int launch_wjitter(int cs, const ModelArgs<float>& A, const WArgs& W, const Jitt
 size_t wwindow_smem(int cs, int Ns, int K);
 size_t wjitter_smem(int cs, int Ns, int K);
 
+// MALA jitter (pf_mala.cu)
+template <typename R>
+int launch_mala_propose(int N, int Ns, int K, double theta, double h, double dt, const R* dW, const R* lam,
+                        const R* gJ, uint64_t seed, uint64_t ctr, int particle0, R* dWp, cudaStream_t st);
+template <typename R>
+int launch_mala_accept(int N, int NK, double theta, double h, double dt, uint64_t seed, uint64_t ctr, int particle0,
+                       R* dW, const R* dWp, const R* lam, double* J, const double* Jp, R* gJ, const R* gJp,
+                       int32_t* accepts, cudaStream_t st);
+
 // filter kernels (pf_filter.cu)
 int launch_temper(int N, const double* nll, const double* logG, double theta, const double* theta_dev,
                   double ess_min, int halving, double* wbar,

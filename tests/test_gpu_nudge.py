@@ -138,3 +138,26 @@ def test_nudge_sequential_matches_oracle():
                                       gtol=1e-12)
         assert np.allclose(out["dW"][p].cpu().numpy(), dW, rtol=1e-13, atol=1e-15)
         assert rel_err(out["lam"][p].cpu().numpy(), lam) < 1e-5
+
+
+@pytest.mark.parametrize("lam_on", [False, True])
+def test_mala_jitter_matches_oracle(lam_on):
+    # MALA with the gradient from the reverse-mode adjoint against the oracle's MALA
+    # with the tangent-linear gradient: the same keyed normals and uniforms, so the
+    # same decisions, and the same noise within the two gradients' agreement
+    cfg = get_config("cfg1_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la, y = _setup(cfg, 3, 31, Ns=3, lam_scale=0.2)
+    la = la if lam_on else None
+    theta, h, n_iter, seed, ctr = 0.7, 0.8, 3, 5, 40   # h large enough that some moves are rejected
+    ref_dW, ref_nll, ref_lg, ref_acc = OF.mala_jitter(om, m0, dW, la, y, cfg.sigma, theta, h, n_iter, seed, ctr)
+    dWd = tdev(dW, g.dtype)
+    out = g.mala_jitter(tdev(m0, g.dtype), dWd, None if la is None else tdev(la, g.dtype), tdev(y, g.dtype), theta,
+                        h, n_iter, seed, ctr, ckpt=2)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    assert np.array_equal(out["accepts"].cpu().numpy(), ref_acc)
+    assert 0 < ref_acc.sum() < 3 * n_iter
+    assert rel_err(dWd.cpu().numpy(), ref_dW) < 1e-8
+    assert np.allclose(out["nll"].cpu().numpy(), ref_nll, rtol=1e-8)
+    assert np.allclose(out["logG"].cpu().numpy(), ref_lg, rtol=1e-8, atol=1e-12)
