@@ -170,9 +170,11 @@ def test_cycle_matches_oracle_f64(eager, mode):
     assert rel_err(f.dW.cpu().numpy(), ref["dW"]) < 1e-8
 
 
-def test_gated_stages_equal_stage_by_stage_fp32():
+@pytest.mark.parametrize("nudged", [False, True])
+def test_gated_stages_equal_stage_by_stage_fp32(nudged):
     # the same FP32 cycles with device-gated stages and stage by stage: the same kernels take
-    # the same decisions, so every array and stage statistic is bit-identical
+    # the same decisions, so every array and stage statistic is bit-identical; with a drift
+    # the resampled drift rows are compared too
     from paper_2402_06927_gb300.filter import EnsembleFilter
     from workloads import u0_profile
     cfg = get_config("cfg2_f32")
@@ -183,12 +185,17 @@ def test_gated_stages_equal_stage_by_stage_fp32():
     fs = [EnsembleFilter(g, N, cfg.Ns, 0.5 * N, cfg.rho, 3, 11, eager_stages=e) for e in (3, 0)]
     for f in fs:
         f.set_state(m0)
+    names = ("m_start", "m_end", "u_end", "dW", "nll", "logG") + (("lam",) if nudged else ())
     for c in range(3):
         y = g.synth_obs(u0, 20 + c, 1)
+        if nudged:
+            lam = torch.tensor(random_drift(cfg, N, 60 + c, scale=0.2), dtype=torch.float32, device="cuda")
+            for f in fs:
+                f.set_drift(lam)
         sts = [f.cycle(y, c) for f in fs]
         assert [(s.dtheta, s.ess, s.theta) for s in sts[0].stages] == [(s.dtheta, s.ess, s.theta) for s in sts[1].stages]
         assert sts[0].forward_steps == sts[1].forward_steps
-        for name in ("m_start", "m_end", "u_end", "dW", "nll", "logG"):
+        for name in names:
             assert torch.equal(getattr(fs[0], name), getattr(fs[1], name)), name
         for f in fs:
             f.advance()
