@@ -109,10 +109,16 @@ static int splitk_for(int M, int N, int Kd) {
     return max(1, min(Kd / 256, 8 * 152 / tiles));
 }
 
+// k-chunks that sgemm launches for a split of splitk
+static int splitk_chunks(int Kd, int splitk) {
+    const int kchunk = (Kd + splitk - 1) / splitk;
+    return (Kd + kchunk - 1) / kchunk;
+}
+
 template <typename LA, typename LB, typename EP>
 static void sgemm(int batch, int M, int N, int Kd, int splitk, LA la, LB lb, EP ep, cudaStream_t st) {
     const int kchunk = (Kd + splitk - 1) / splitk;
-    const int nk = (Kd + kchunk - 1) / kchunk;
+    const int nk = splitk_chunks(Kd, splitk);
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch * nk);
     sgemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, kchunk, la, lb, ep);
 }
@@ -184,9 +190,13 @@ struct ConvXT {           // B((b, q), kk) = x[b][ci][(2q + j - 2) mod L]
         return x[(size_t)b * bstride + (size_t)ci * L + i];
     }
 };
-struct AtomicAdd2D {
-    float* out; int ld;
-    __device__ void operator()(int, int m, int n, float v) const { atomicAdd(&out[(size_t)m * ld + n], v); }
+// split-K partial of a batch-1 product: k-chunk blockIdx.z writes a slice of its own and
+// the slices are summed afterwards in a fixed order, so the gradients are reproducible
+struct StorePartial {
+    float* out; int ld; size_t slice;
+    __device__ void operator()(int, int m, int n, float v) const {
+        out[(size_t)blockIdx.z * slice + (size_t)m * ld + n] = v;
+    }
 };
 // generic row-major accessors
 struct RowMajor {         // A(m, k) = p[z * bs + m * ld + k]
@@ -250,6 +260,15 @@ __global__ void loss_kernel(int B, int O, const float* lam, size_t lstride, cons
     }
     acc = warp_sum(acc);
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
+}
+
+// out[e] = sum of the nk slices part[s][e], in slice order
+__global__ void sum_slices_kernel(size_t count, int nk, const float* __restrict__ part, float* __restrict__ out) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int s = 0; s < nk; ++s) acc += part[(size_t)s * count + e];
+        out[e] = acc;
+    }
 }
 
 // db[co] = sum over samples b and positions q of g[b][co][q].  Per-thread partial
@@ -345,11 +364,23 @@ size_t nn_param_count(const nn_shape* s) {
     return make_dims(s).nparam;
 }
 
+// floats of the split-K partials of the largest weight-gradient product
+static size_t partial_floats(const NNDims& d, int B) {
+    const int O = d.K * d.Ns, FF = d.C * d.K;
+    size_t m = (size_t)splitk_chunks(B, splitk_for(O, FF, B)) * O * FF;
+    for (int l = 0; l < 4; ++l) {
+        const int KK = d.cin[l] * 5, Kd = B * d.L[l + 1];
+        m = max(m, (size_t)splitk_chunks(Kd, splitk_for(d.C, KK, Kd)) * d.C * KK);
+    }
+    return m;
+}
+
 size_t nn_workspace_bytes(const nn_shape* s, int B) {
     if (!s || B <= 0 || nn_param_count(s) == 0) return 0;
     const NNDims d = make_dims(s);
-    // forward activations + two gradient buffers of one activation each + glam/gF
-    return ((size_t)B * d.act_total * 3 + 2 * (size_t)d.C * d.K * B + (size_t)d.K * d.Ns * B) * sizeof(float);
+    // forward activations + two gradient buffers of one activation each + glam/gF + split-K partials
+    return ((size_t)B * d.act_total * 3 + 2 * (size_t)d.C * d.K * B + (size_t)d.K * d.Ns * B +
+            partial_floats(d, B)) * sizeof(float);
 }
 
 static int nn_check(const nn_shape* s, int B, const void* params, const void* u, const void* y, void* ws,
@@ -387,13 +418,18 @@ int nn_backward(const nn_shape* s, int B, const float* params, const float* u_st
     float* gB = gA + (size_t)B * bs;           // (pong)
     float* gF = gB + (size_t)B * bs;           // [B][C K]
     float* glam = gF + (size_t)B * d.C * d.K;  // [B][O]
+    float* part = glam + (size_t)B * d.K * d.Ns; // split-K partials [chunk][rows][cols]
     const int O = d.K * d.Ns, FF = d.C * d.K, P = d.L[4];
     nn_forward_impl(d, B, params, u_start, y, y_stride, act, st);
     zero_kernel<<<grid_elems(d.nparam), 256, 0, st>>>(grads, d.nparam, loss);
     loss_kernel<<<grid_elems((size_t)B * O), 256, 0, st>>>(B, O, act + d.off_lam, bs, target, glam, loss);
     // head: dWh[o][f] = sum_b glam[b][o] F[b][f]; dbh[o] = sum_b glam[b][o]; gF = glam Wh
-    sgemm(1, O, FF, B, splitk_for(O, FF, B), RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
-          AtomicAdd2D{grads + d.off_wh, FF}, st);
+    {
+        const int sk = splitk_for(O, FF, B), nk = splitk_chunks(B, sk);
+        sgemm(1, O, FF, B, sk, RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
+              StorePartial{part, FF, (size_t)O * FF}, st);
+        sum_slices_kernel<<<grid_elems((size_t)O * FF), 256, 0, st>>>((size_t)O * FF, nk, part, grads + d.off_wh);
+    }
     bias_grad_kernel<<<O, 256, 0, st>>>(B, O, 1, glam, (size_t)O, grads + d.off_bh);
     sgemm(1, B, FF, O, 1, RowMajor{glam, 0, O}, RowMajor{params + d.off_wh, 0, FF}, Store{gF, 0, FF, nullptr}, st);
     // dh4[b][c][q] = sum_k gF[b][c][k] S[q][k], masked by ReLU(h4 > 0)
@@ -406,8 +442,11 @@ int nn_backward(const nn_shape* s, int B, const float* params, const float* u_st
         const int Ci = d.cin[l], Lin = d.L[l], Lo = d.L[l + 1];
         const float* gz = gcur;
         // weights: dw[co][kk] = sum_{b,q} gz[b][co][q] X(b, kk, q)
-        sgemm(1, d.C, Ci * 5, B * Lo, splitk_for(d.C, Ci * 5, B * Lo), GRowsBQ{gz, bs, Lo},
-              ConvXT{act + d.act_off[l], bs, Lin, Lo}, AtomicAdd2D{grads + d.off_w[l], Ci * 5}, st);
+        const int sk = splitk_for(d.C, Ci * 5, B * Lo), nk = splitk_chunks(B * Lo, sk);
+        const size_t wcount = (size_t)d.C * Ci * 5;
+        sgemm(1, d.C, Ci * 5, B * Lo, sk, GRowsBQ{gz, bs, Lo}, ConvXT{act + d.act_off[l], bs, Lin, Lo},
+              StorePartial{part, Ci * 5, wcount}, st);
+        sum_slices_kernel<<<grid_elems(wcount), 256, 0, st>>>(wcount, nk, part, grads + d.off_w[l]);
         bias_grad_kernel<<<d.C, 256, 0, st>>>(B, d.C, Lo, gz, bs, grads + d.off_b[l]);
         if (l > 0) {
             // data: dx[b][ci][i], masked by the ReLU of layer l-1's output

@@ -70,6 +70,28 @@ def test_forward_and_gradients_match_oracle(masked):
     assert np.all(np.isfinite(lam))
 
 
+def test_split_k_gradients_match_oracle_and_are_reproducible():
+    # B = 600: every weight gradient (the head's over the batch, the convolutions' over
+    # batch x positions) is split over k-chunks that are summed in a fixed order, so a
+    # second evaluation gives the same bits
+    api = require_lib()
+    n, K, Ns, C, M, sigma = 256, 4, 3, 16, 32, 0.05
+    p, u, y, target = _case(n, K, Ns, C, M, B=600, seed=3)
+    net = api.ProposalNet(n, K, Ns, M, sigma, C=C, params=torch.tensor(_flat(p), dtype=torch.float32))
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    td = torch.tensor(target, dtype=torch.float32, device="cuda")
+    _, g1 = net.loss_and_grad(ud, yd, td)
+    g1 = g1.cpu().numpy()
+    _, g2 = net.loss_and_grad(ud, yd, td)
+    assert np.array_equal(g1, g2.cpu().numpy())
+    x0 = np.stack([CN.features(u[b:b + 1], y[b], sigma)[0] for b in range(u.shape[0])])
+    _, g = CN.loss_and_grad(p, x0, target, K, Ns)
+    gg = _unflat(g1.astype(np.float64), p)
+    for k in g:
+        assert np.max(np.abs(gg[k] - g[k])) <= 2e-4 * max(1e-6, np.max(np.abs(g[k]))), k
+
+
 def test_adam_matches_oracle():
     api = require_lib()
     n, K, Ns, C, M, sigma = 128, 2, 2, 8, 16, 0.05
