@@ -459,6 +459,27 @@ ADJ_FLOPS_PER_NODE_STEP = 16
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12   # 2 DFMA lanes per SM per cycle, max SM clock
 
 
+def _nudging_inputs(g, cfg):
+    """Twin inputs of the nudging workload: the truth runs one window from u0, the
+    particles start from the prior around u0 with prior noise and a random drift."""
+    import torch
+    from workloads import u0_profile, random_drift
+    N, Ns = cfg.N, cfg.Ns
+    u0 = torch.tensor(u0_profile(cfg), dtype=g.dtype, device="cuda")
+    mt = g.m_from_u(u0[None].contiguous())
+    tr = g.ensemble_step(mt, g.draw_increments(1, Ns, 21, 5, 0), None)
+    y = g.synth_obs(tr["u"][0].contiguous(), 22, 1)
+    m0, _ = g.prior_sample(N, u0, 23, cfg.prior_scale)
+    dW = g.draw_increments(N, Ns, 24, 1, 0)
+    lam = torch.tensor(random_drift(cfg, N, 25, steps=Ns, scale=0.2), dtype=g.dtype, device="cuda")
+    return m0, dW, lam, y
+
+
+def _adjoint_flops(n, K, N, Ns, it_fwd, it_adj):
+    return (step_flops(n, K, "li", it_fwd, N * Ns)
+            + n * (ADJ_FLOPS_PER_NODE_ITER * it_adj + (ADJ_FLOPS_PER_NODE_STEP + 2 * K) * N * Ns))
+
+
 def run_adjoint(args):
     """--adjoint: gradient evaluations on the nudging workload (n = 1024, K = 8,
     20-step windows, N = 256, FP64, checkpoints every 5 steps).  One evaluation is
@@ -467,20 +488,13 @@ def run_adjoint(args):
     between timed calls, CUDA events; the oracle's gradient (tangent linear,
     dense Jacobians) is timed on the host beside it."""
     import torch
-    from workloads import get_config, u0_profile, random_drift
+    from workloads import get_config
     from paper_2402_06927_gb300.api import SchModel
     torch.cuda.set_device(0)
     cfg = get_config("cfg3_f64")
     g = SchModel.from_config(cfg)
     N, Ns, K, n = cfg.N, cfg.Ns, cfg.K, cfg.n
-    u0 = torch.tensor(u0_profile(cfg), dtype=g.dtype, device="cuda")
-    # twin: the truth runs one window from u0; the particles start from the prior around u0
-    mt = g.m_from_u(u0[None].contiguous())
-    tr = g.ensemble_step(mt, g.draw_increments(1, Ns, 21, 5, 0), None)
-    y = g.synth_obs(tr["u"][0].contiguous(), 22, 1)
-    m0, _ = g.prior_sample(N, u0, 23, cfg.prior_scale)
-    dW = g.draw_increments(N, Ns, 24, 1, 0)
-    lam = torch.tensor(random_drift(cfg, N, 25, steps=Ns, scale=0.2), dtype=g.dtype, device="cuda")
+    m0, dW, lam, y = _nudging_inputs(g, cfg)
     fwd = g.ensemble_step(m0, dW, lam, y)
     ws = None
     for _ in range(max(3, args.warmup)):
@@ -500,9 +514,7 @@ def run_adjoint(args):
     assert int(out["status"].abs().sum().item()) == 0, "adjoint status flags"
     it_fwd = int(fwd["iters"].sum().item())
     it_adj = int(out["iters"].sum().item()) - it_fwd
-    flops = (step_flops(n, K, "li", it_fwd, N * Ns)
-             + n * (ADJ_FLOPS_PER_NODE_ITER * it_adj + (ADJ_FLOPS_PER_NODE_STEP + 2 * K) * N * Ns))
-    achieved = flops / t / 1e12
+    achieved = _adjoint_flops(n, K, N, Ns, it_fwd, it_adj) / t / 1e12
     cpu = None
     if not args.no_cpu:
         import numpy as np
@@ -527,6 +539,95 @@ def run_adjoint(args):
         "config": {"workload": "adjoint window: n=1024 K=8 Ns=20 N=256 (FP64, LI Picard, checkpoints every 5 steps)",
                    "l2": "flushed between timed calls (256 MB write)",
                    "forward_picard_iters_per_step": it_fwd / (N * Ns), "adjoint_iters_per_step": it_adj / (N * Ns)},
+        "roofline": {"bound": "alu", "kernel": "adjoint_kernel<double,4,256,LI>", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_note": "FP64 pipe 152 SMs x 2 DFMA lanes x 2 x max SM clock; recomputation from "
+                                  "checkpoints is not credited"},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+MALA_THETA, MALA_H, MALA_ITERS = 1.0, 0.02, 10
+
+
+def run_mala(args):
+    """--mala: MALA jitter on the nudging workload (n = 1024, K = 8, 20-step windows,
+    N = 256, FP64, checkpoints every 5 steps) at theta = 1.  One timed step is one
+    SchModel.mala_jitter call of MALA_ITERS moves per particle: the initial gradient,
+    then per move pf_mala_propose, the adjoint window at the proposal and
+    pf_mala_accept, and the final window.  Inputs resident, L2 flushed before each
+    call, CUDA events.  The adjoint kernel dominates; its roofline is reported with
+    its share of the call, and the oracle's MALA move is timed on the host."""
+    import torch
+    from workloads import get_config
+    from paper_2402_06927_gb300.api import SchModel
+    torch.cuda.set_device(0)
+    cfg = get_config("cfg3_f64")
+    g = SchModel.from_config(cfg)
+    N, Ns, K, n = cfg.N, cfg.Ns, cfg.K, cfg.n
+    m0, dW0, lam, y = _nudging_inputs(g, cfg)
+    dW = dW0.clone()
+    S, theta, h = MALA_ITERS, MALA_THETA, MALA_H
+
+    def call(k):
+        return g.mala_jitter(m0, dW, lam, y, theta, h, S, 31, 1000 * k, ckpt=5)
+
+    for k in range(max(3, args.warmup)):
+        dW.copy_(dW0)
+        out = call(k)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream()
+    times, acc = [], 0
+    for k in range(args.steps):
+        dW.copy_(dW0)
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        out = call(100 + k)
+        e1.record(st)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        acc += int(out["accepts"].sum().item())
+    t = statistics.median(times)
+    assert int(out["status"].abs().sum().item()) == 0, "window status flags"
+    # parts: the adjoint window (dominant), proposal and decision kernels, each alone
+    ws = torch.empty(int(g.adjoint_workspace_bytes(N, Ns, 5)), dtype=torch.uint8, device="cuda")
+    fwd = g.ensemble_step(m0, dW0, lam, y)
+    adj = g.adjoint_window(m0, dW0, lam, y, ckpt=5, want_m0=False, ws=ws)
+    t_adj = _event_time(lambda: g.adjoint_window(m0, dW0, lam, y, ckpt=5, want_m0=False, ws=ws), 5, flush)
+    dWp, Jp, gJp = torch.empty_like(dW0), adj["J"].clone(), adj["g_dW"].clone()
+    J, gJ, dWc = adj["J"].clone(), adj["g_dW"].clone(), dW0.clone()
+    t_prop = _event_time(lambda: g.mala_propose(dWc, lam, gJ, dWp, theta, h, 31, 0), 20, flush)
+    t_acc = _event_time(lambda: g.mala_accept(dWc, dWp, lam, J, Jp, gJ, gJp, None, theta, h, 31, 0), 20, flush)
+    it_fwd = int(fwd["iters"].sum().item())
+    it_adj = int(adj["iters"].sum().item()) - it_fwd
+    achieved = _adjoint_flops(n, K, N, Ns, it_fwd, it_adj) / t_adj / 1e12
+    cpu = None
+    if not args.no_cpu:
+        from oracle.model import Model
+        from oracle import filter as OF
+        from workloads import mode_amplitudes
+        om = Model(L=cfg.L, n=n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg))
+        m0h, dWh, lamh, yh = (x.double().cpu().numpy() for x in (m0[:1], dW0[:1], lam[:1], y))
+        t0 = time.perf_counter()
+        OF.mala_jitter(om, m0h, dWh, lamh, yh, cfg.sigma, theta, h, 1, 31, 0)
+        el = time.perf_counter() - t0
+        cpu = {"value": 1.0 / el, "unit": "MALA moves/s", "cores": 1, "kind": "oracle",
+               "sample": "one oracle MALA move of one particle (tangent-linear gradients, FP64, one thread) "
+                         "and its final window, same inputs"}
+    line = {
+        "metric": "MALA moves/s", "value": N * S / t, "unit": "MALA moves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"MALA jitter: n=1024 K=8 Ns=20 N=256 (FP64, LI Picard, checkpoints every 5 "
+                               f"steps), {S} moves per call, theta={theta}, h={h}",
+                   "l2": "flushed between timed calls (256 MB write)",
+                   "acceptance": acc / (N * S * args.steps),
+                   "adjoint_ms": 1e3 * t_adj, "propose_us": 1e6 * t_prop, "accept_us": 1e6 * t_acc,
+                   "adjoint_share": (S + 1) * t_adj / t},
         "roofline": {"bound": "alu", "kernel": "adjoint_kernel<double,4,256,LI>", "achieved": achieved,
                      "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                      "traffic": None,
@@ -718,6 +819,8 @@ def main():
                     help="learned vs optimiser nudging comparison instead of the default workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the reverse-mode adjoint (gradient evaluations) on the nudging workload")
+    ap.add_argument("--mala", action="store_true",
+                    help="time the MALA jitter (moves/s) on the nudging workload")
     ap.add_argument("--filter-kernels", action="store_true",
                     help="time tempering, resampling and the row gather against their bounds")
     ap.add_argument("--proposal", action="store_true",
@@ -747,6 +850,10 @@ def main():
         if args.steps == 100:
             args.steps = 10
         return run_adjoint(args)
+    if args.mala:
+        if args.steps == 100:
+            args.steps = 5
+        return run_mala(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

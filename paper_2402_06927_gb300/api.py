@@ -222,6 +222,10 @@ class SchModel:
                                        _ptr(ws), ws.numel() * ws.element_size(), _stream()), "sch_adjoint_window")
         return dict(J=J, g_lam=g_lam, g_dW=g_dW, g_m0=g_m0, iters=iters, status=status)
 
+    def adjoint_workspace_bytes(self, N: int, nsteps: int, ckpt: int = 5) -> int:
+        """Bytes of the workspace sch_adjoint_window needs for N particles."""
+        return int(lib().sch_adjoint_workspace_bytes(self._h, N, nsteps, ckpt))
+
     def mala_jitter(self, m_start: torch.Tensor, dW: torch.Tensor, lam: Optional[torch.Tensor], y: torch.Tensor,
                     theta: float, h: float, n_iter: int, seed: int, ctr: int, particle0: int = 0, ckpt: int = 5):
         """n_iter MALA moves of every particle's window noise at temperature theta, updating dW in
@@ -230,22 +234,33 @@ class SchModel:
         Returns dict(accepts, m, u, nll, logG, status)."""
         N, nsteps, K = dW.shape
         _need(dW, self.dtype, (N, nsteps, self.K), "dW")
-        ws = torch.empty(int(lib().sch_adjoint_workspace_bytes(self._h, N, nsteps, ckpt)), dtype=torch.uint8,
-                         device=dW.device)
+        ws = torch.empty(self.adjoint_workspace_bytes(N, nsteps, ckpt), dtype=torch.uint8, device=dW.device)
         cur = self.adjoint_window(m_start, dW, lam, y, ckpt=ckpt, want_m0=False, ws=ws)
         J, gJ = cur["J"], cur["g_dW"]
         dWp = torch.empty_like(dW)
         acc = torch.zeros(N, dtype=torch.int32, device=dW.device)
-        st = _stream()
         for j in range(n_iter):
-            check(lib().pf_mala_propose(self._h, N, nsteps, theta, h, seed, ctr + j, particle0, _ptr(dW), _ptr(lam),
-                                        _ptr(gJ), _ptr(dWp), st), "pf_mala_propose")
+            self.mala_propose(dW, lam, gJ, dWp, theta, h, seed, ctr + j, particle0)
             prop = self.adjoint_window(m_start, dWp, lam, y, ckpt=ckpt, want_m0=False, ws=ws)
-            check(lib().pf_mala_accept(self._h, N, nsteps, theta, h, seed, ctr + j, particle0, _ptr(dW), _ptr(dWp),
-                                       _ptr(lam), _ptr(J), _ptr(prop["J"]), _ptr(gJ), _ptr(prop["g_dW"]),
-                                       _ptr(acc), st), "pf_mala_accept")
+            self.mala_accept(dW, dWp, lam, J, prop["J"], gJ, prop["g_dW"], acc, theta, h, seed, ctr + j, particle0)
         fin = self.ensemble_step(m_start, dW, lam, y)
         return dict(accepts=acc, m=fin["m"], u=fin["u"], nll=fin["nll"], logG=fin["logG"], status=fin["status"])
+
+    def mala_propose(self, dW: torch.Tensor, lam: Optional[torch.Tensor], gJ: torch.Tensor, dW_prop: torch.Tensor,
+                     theta: float, h: float, seed: int, ctr: int, particle0: int = 0) -> None:
+        """pf_mala_propose: dW_prop = dW - (h/2) dt grad U(dW) + sqrt(h dt) z."""
+        N, nsteps, _ = dW.shape
+        check(lib().pf_mala_propose(self._h, N, nsteps, theta, h, seed, ctr, particle0, _ptr(dW), _ptr(lam),
+                                    _ptr(gJ), _ptr(dW_prop), _stream()), "pf_mala_propose")
+
+    def mala_accept(self, dW: torch.Tensor, dW_prop: torch.Tensor, lam: Optional[torch.Tensor], J: torch.Tensor,
+                    J_prop: torch.Tensor, gJ: torch.Tensor, gJ_prop: torch.Tensor, accepts: Optional[torch.Tensor],
+                    theta: float, h: float, seed: int, ctr: int, particle0: int = 0) -> None:
+        """pf_mala_accept: the Metropolis-Hastings decision; accepted rows of dW, J, gJ take the proposal's."""
+        N, nsteps, _ = dW.shape
+        check(lib().pf_mala_accept(self._h, N, nsteps, theta, h, seed, ctr, particle0, _ptr(dW), _ptr(dW_prop),
+                                   _ptr(lam), _ptr(J), _ptr(J_prop), _ptr(gJ), _ptr(gJ_prop), _ptr(accepts),
+                                   _stream()), "pf_mala_accept")
 
     def nudge(self, m_start: torch.Tensor, y: torch.Tensor, nsteps: int, mode: str = "sequential",
               max_iter: int = 50, gtol: float = 1e-8, ckpt: int = 5, seed: int = 0, ctr: int = 0,
