@@ -10,9 +10,13 @@ Follows Sec. 2 of the paper:
   (m1 - m0, phi) + mu dt (mbar_x, phi_x) + (mbar dv_x, phi) - (mbar dv, phi_x) = 0
   with mbar = (m0 + m1) / 2 and dv = dt (u0 + u1) / 2 + dU  (the increment
   Delta v^{n+1/2} of the text under Eq. fde1);
-* SALT noise dU = sum_k xi_k dW^k (the mode expansion named in Sec. 2), with
-  the mode functions interpolated at the nodes, plus the nudging drift of
-  Sec. 3.1.3: dU_i = sum_k xi_k(x_i) (dW_k + lambda_k dt).
+* SALT noise, either the mode expansion named in Sec. 2, dU = sum_k xi_k dW^k
+  with the mode functions interpolated at the nodes, plus the nudging drift of
+  Sec. 3.1.3: dU_i = sum_k xi_k(x_i) (dW_k + lambda_k dt); or the paper's
+  Matern field (Eq. noise_solve, Eq. noise_solve2): one Brownian motion per
+  cell, dW_h = sum_c h^{-1/2} 1_c dW_c in DG0, and k chained P1 solves
+  (U_j, v) + kappa^{-2} (U_j', v') = eta (dW_h, v) for j = 1, (U_{j-1}, v)
+  after, dU = U_k; the drift lambda is a DG0 field added to dW.
 
 Every matrix is assembled element by element from exact integrals of products
 of linear functions on the reference element (no quadrature), and kept as a
@@ -59,13 +63,18 @@ class Model:
     tol: float = 1e-13
     max_iter: int = 100
     scheme: str = "li"
+    noise_model: str = "modes"   # "modes" or "matern"
+    kappa: float = 1.0           # Matern length scale 1 / kappa (Eq. noise_solve)
+    eta: float = 1.0
+    matern_k: int = 3
 
     @classmethod
     def from_config(cls, cfg, tol=None, max_iter=None, scheme="li") -> "Model":
         from workloads import mode_amplitudes
         return cls(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt,
                    amps=mode_amplitudes(cfg), tol=1e-13 if tol is None else tol,
-                   max_iter=100 if max_iter is None else max_iter, scheme=scheme)
+                   max_iter=100 if max_iter is None else max_iter, scheme=scheme,
+                   noise_model=cfg.noise, kappa=cfg.kappa, eta=cfg.eta, matern_k=cfg.matern_k)
 
     @property
     def h(self) -> float:
@@ -74,6 +83,11 @@ class Model:
     @property
     def K(self) -> int:
         return 2 * len(self.amps)
+
+    @property
+    def Q(self) -> int:
+        """Brownian motions per step: K for the mode expansion, one per cell for the Matern field."""
+        return self.n if self.noise_model == "matern" else self.K
 
     @property
     def x(self) -> np.ndarray:
@@ -194,11 +208,30 @@ class Model:
         return out
 
     def noise(self, dW: np.ndarray, lam=None) -> np.ndarray:
-        """dU_i = sum_k xi_k(x_i) (dW_k + lambda_k dt) for one step (dW, lam: [K])."""
+        """Nodal dU of one step from dW, lam: [Q].
+
+        Modes: dU_i = sum_k xi_k(x_i) (dW_k + lambda_k dt).  Matern: w = dW +
+        lambda dt on the cells (cell c = [x_c, x_{c+1}]), right-hand side
+        eta (dW_h, phi_i) = eta (sqrt(h) / 2) (w_{i-1} + w_i), then k solves with
+        M + kappa^{-2} K, the later ones with right-hand side M U_{j-1}.
+        """
         w = np.asarray(dW, dtype=np.float64).copy()
         if lam is not None:
             w = w + np.asarray(lam, dtype=np.float64) * self.dt
-        return self.modes().T @ w
+        if self.noise_model != "matern":
+            return self.modes().T @ w
+        G = self.matern_operator()
+        U = self.solve(G, self.eta * 0.5 * math.sqrt(self.h) * (np.roll(w, 1) + w))
+        for _ in range(self.matern_k - 1):
+            U = self.solve(G, self.apply(self.mass(), U))
+        return U
+
+    def matern_operator(self):
+        """M + kappa^{-2} K, the P1 form of (I - kappa^{-2} d_xx) (Eq. noise_solve2)."""
+        Ma, Mb, Mc = self.mass()
+        Ka, Kb, Kc = self.stiffness()
+        k2 = self.kappa ** -2
+        return (Ma + k2 * Ka, Mb + k2 * Kb, Mc + k2 * Kc)
 
     def residual(self, m1, m0, u1, u0, dU) -> np.ndarray:
         """Assembled residual of Eq. fde1 (second line) for all test functions."""
@@ -292,7 +325,7 @@ class Model:
         return m, u, iters, conv
 
     def ensemble_window(self, m0: np.ndarray, dW: np.ndarray, lam=None):
-        """Apply ``window`` to every particle: m0 [N, n], dW [N, Ns, K]."""
+        """Apply ``window`` to every particle: m0 [N, n], dW [N, Ns, Q]."""
         N = m0.shape[0]
         m_out = np.empty_like(m0, dtype=np.float64)
         u_out = np.empty_like(m0, dtype=np.float64)

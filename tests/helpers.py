@@ -20,6 +20,7 @@ def gpu_model(cfg, **over):
 
 def oracle_model(cfg, **over):
     kw = dict(tol=1e-13, max_iter=100)
+    kw.update(noise_model=cfg.noise, kappa=cfg.kappa, eta=cfg.eta, matern_k=cfg.matern_k)
     kw.update(over)
     return Model(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg), **kw)
 

@@ -61,6 +61,53 @@ def test_helmholtz_on_fourier_modes(j):
     assert np.allclose(m.u_from_m(v), v / ratio, rtol=0, atol=1e-14)
 
 
+def _matern(n=128, kappa=0.7, eta=1.3, k=3, L=40.0):
+    return Model(L=L, n=n, alpha=1.0, mu=0.02, dt=0.025, amps=np.full(2, 0.05), noise_model="matern",
+                 kappa=kappa, eta=eta, matern_k=k)
+
+
+@pytest.mark.parametrize("j", [0, 1, 4, 13])
+@pytest.mark.parametrize("k", [1, 3])
+def test_matern_noise_on_fourier_modes(j, k):
+    # cell values cos / sin(theta (c + 1/2)), theta = 2 pi j / n: the load is
+    # eta sqrt(h) cos(theta/2) times the nodal mode, and each solve divides by
+    # the symbol of M + kappa^-2 K, each later load multiplies by that of M
+    m = _matern(k=k)
+    th = 2 * math.pi * j / m.n
+    c = np.arange(m.n) + 0.5
+    i = np.arange(m.n)
+    Mh = m.h / 6 * (4 + 2 * math.cos(th))
+    Gh = Mh + m.kappa ** -2 * (2 - 2 * math.cos(th)) / m.h
+    amp = m.eta * math.sqrt(m.h) * math.cos(th / 2) * Mh ** (k - 1) / Gh ** k
+    for f in (np.cos, np.sin):
+        assert np.allclose(m.noise(f(th * c)), amp * f(th * i), rtol=0, atol=1e-12 * max(amp, 1e-3))
+
+
+def test_matern_noise_constant_field_and_drift():
+    # w = 1 on every cell: every load and solve keeps the constant, U = eta / sqrt(h);
+    # the drift enters as dW + lambda dt
+    m = _matern()
+    assert np.allclose(m.noise(np.ones(m.n)), m.eta / math.sqrt(m.h), rtol=1e-13)
+    r = np.random.default_rng(3)
+    dW, lam = r.normal(size=m.n), r.normal(size=m.n)
+    assert np.allclose(m.noise(dW, lam), m.noise(dW + m.dt * lam), rtol=1e-13, atol=1e-15)
+    assert m.Q == m.n
+
+
+def test_matern_noise_continuum_limit():
+    # a smooth cell field f(x) = cos(2 pi j x / L): the load is (h^-1/2 f, phi_i), so
+    # dU -> eta h^-1/2 (1 + (2 pi j / (L kappa))^2)^-k f at the nodes, with an O(h^2) error
+    j, errs = 3, []
+    for n in (64, 128, 256):
+        m = _matern(n=n)
+        x = (np.arange(n) + 0.5) * m.h
+        ref = m.eta / math.sqrt(m.h) * (1 + (2 * math.pi * j / (m.L * m.kappa)) ** 2) ** -m.matern_k
+        dU = m.noise(np.cos(2 * math.pi * j * x / m.L))
+        errs.append(np.max(np.abs(dU - ref * np.cos(2 * math.pi * j * m.x / m.L))) / ref)
+    assert errs[0] < 0.05
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
 def test_helmholtz_continuum_limit():
     # m/u -> 1 + alpha^2 k^2 with O(h^2) error for the fixed physical wavenumber k
     errs = []

@@ -19,6 +19,11 @@ Workloads (all synthetic twin experiments; the paper uses no public dataset):
 * ``cfg3_f64``  nudging, FP64: n=1024, K=8, N=256, 20-step window.
 * ``cfg4_f32``  learned proposal: n=1024, K=16, 20-step window, N=1024.
 * ``cfg5_f32``  large run: n=4096, K=32, N=8192, M=128, sigma=0.02.
+* ``cfg1m_f64``, ``cfg2m_f32``  cfg1 / cfg2 with the paper's Matern noise
+  (Eq. noise_solve: one Brownian motion per cell, k = 3 solves, kappa = 1)
+  instead of the mode expansion; eta = 0.2 puts the per-step noise at the
+  size of the mode-expansion workloads' (eta = 1 makes it about five times
+  the transport term u dt at dt = 0.025).
 
 The initial truth is u0(x) = 0.2 sech(x-27) + 0.5 sech(x-13) on [0, 40).
 """
@@ -61,6 +66,15 @@ class Config:
     max_iter: int = 60
     prior_scale: float = 0.05
     seed: int = 0
+    noise: str = "modes"    # "modes" (K mode functions) or "matern" (one Brownian motion per cell)
+    kappa: float = 1.0      # Matern: length scale 1 / kappa
+    eta: float = 1.0        # Matern: amplitude
+    matern_k: int = 3       # Matern: number of chained elliptic solves
+
+    @property
+    def Q(self) -> int:
+        """Brownian motions per model step (the last axis of dW and lambda)."""
+        return self.n if self.noise == "matern" else self.K
 
     @property
     def h(self) -> float:
@@ -82,6 +96,8 @@ class Config:
             raise ValueError("observation points must fall on nodes (n % M == 0)")
         if self.K % 2 != 0:
             raise ValueError("K counts sin/cos pairs, so it must be even")
+        if self.noise not in ("modes", "matern"):
+            raise ValueError("noise is 'modes' or 'matern'")
 
 
 CONFIGS = {
@@ -97,6 +113,10 @@ CONFIGS = {
     "cfg5_f32": Config(name="cfg5_f32", n=4096, K=32, amp_rule="inv_j", Ns=10, M=128,
                        sigma=0.02, N=8192, cycles=50, n_jitter=10, rho=0.9999,
                        dtype="f32", tol=1e-6, max_iter=40),
+    "cfg1m_f64": Config(name="cfg1m_f64", noise="matern", kappa=1.0, eta=0.2),
+    "cfg2m_f32": Config(name="cfg2m_f32", n=1024, K=8, amp_rule="inv_j", Ns=10, M=64,
+                        sigma=0.05, N=1024, n_jitter=10, rho=0.9999, dtype="f32",
+                        tol=1e-6, max_iter=40, noise="matern", kappa=1.0, eta=0.2),
 }
 
 
@@ -154,18 +174,18 @@ def random_state(cfg: Config, N: int, seed: int, scale: float = 0.05) -> np.ndar
 
 
 def random_increments(cfg: Config, N: int, seed: int, steps: Optional[int] = None) -> np.ndarray:
-    """dW ~ N(0, dt) iid: [N, Ns, K] float64."""
+    """dW ~ N(0, dt) iid: [N, Ns, Q] float64."""
     steps = cfg.Ns if steps is None else steps
     rng = np.random.default_rng(seed)
-    return rng.normal(scale=math.sqrt(cfg.dt), size=(N, steps, cfg.K))
+    return rng.normal(scale=math.sqrt(cfg.dt), size=(N, steps, cfg.Q))
 
 
 def random_drift(cfg: Config, N: int, seed: int, scale: float = 0.3,
                  steps: Optional[int] = None) -> np.ndarray:
-    """A synthetic nudging drift lambda: [N, Ns, K] float64."""
+    """A synthetic nudging drift lambda: [N, Ns, Q] float64."""
     steps = cfg.Ns if steps is None else steps
     rng = np.random.default_rng(seed)
-    return rng.normal(scale=scale, size=(N, steps, cfg.K))
+    return rng.normal(scale=scale, size=(N, steps, cfg.Q))
 
 
 def random_obs(cfg: Config, seed: int, noise: Optional[float] = None, upto: Optional[float] = None) -> np.ndarray:
