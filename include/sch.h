@@ -76,6 +76,21 @@ enum { SCH_SOLVER_AUTO = 0, SCH_SOLVER_LI = 1, SCH_SOLVER_EA = 2 };
  * Both compute the same iteration; results agree to rounding. */
 enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
 
+/* SALT noise model (sch_params.noise):
+ *   SCH_NOISE_MODES   dU = sum_k xi_k (dW_k + lambda_k dt) over K mode functions
+ *                     (the expansion Sec. 2 contrasts with its own); Q = K
+ *                     Brownian motions per step;
+ *   SCH_NOISE_MATERN  the paper's Matern field (Eq. noise_solve, Eq. noise_solve2):
+ *                     one Brownian motion per cell, dW_h = sum_c h^{-1/2} 1_c dW_c
+ *                     in DG0, and matern_k chained P1 solves
+ *                     (U_j, v) + kappa^-2 (U_j', v') = eta (dW_h, v) for j = 1,
+ *                     (U_{j-1}, v) after, dU = U_k; Q = n.  The drift lambda is a
+ *                     DG0 field added to dW (dW_c + lambda_c dt).  CTA layout,
+ *                     default solver of the precision; the adjoint, nudging and
+ *                     MALA entry points return SCH_ERR_UNSUPPORTED for it.
+ * Every noise array dW, lambda of this API is [N][nsteps][Q]. */
+enum { SCH_NOISE_MODES = 0, SCH_NOISE_MATERN = 1 };
+
 enum {
     SCH_TAG_PRIOR_DW = 1, SCH_TAG_PCN = 2, SCH_TAG_PCN_ACCEPT = 3, SCH_TAG_RESAMPLE = 4,
     SCH_TAG_TRUTH = 5, SCH_TAG_OBS = 6, SCH_TAG_INIT = 7, SCH_TAG_NUDGE = 8,
@@ -103,6 +118,10 @@ typedef struct {
     int32_t dtype;       /* SCH_F64 or SCH_F32: precision of fields, dW, lambda */
     int32_t solver;      /* SCH_SOLVER_* */
     int32_t layout;      /* SCH_LAYOUT_* */
+    int32_t noise;       /* SCH_NOISE_MODES (0) or SCH_NOISE_MATERN */
+    double kappa;        /* Matern: inverse length scale, > 0 */
+    double eta;          /* Matern: amplitude, >= 0 */
+    int32_t matern_k;    /* Matern: number of chained solves, 1 .. 8 */
 } sch_params;
 
 typedef struct sch_ctx sch_ctx;
@@ -117,6 +136,11 @@ int sch_destroy(sch_ctx* ctx);
  * SCH_LAYOUT_CTA or SCH_LAYOUT_WARP (SCH_LAYOUT_AUTO resolved); SCH_ERR_ARG
  * for a NULL context.  Host only. */
 int sch_layout(const sch_ctx* ctx);
+
+/* Q, the Brownian motions per model step: K for SCH_NOISE_MODES, n for
+ * SCH_NOISE_MATERN (the last axis of every dW and lambda array); SCH_ERR_ARG for
+ * a NULL context.  Host only. */
+int sch_noise_dim(const sch_ctx* ctx);
 
 /* Workspace bytes pf_resample needs to gather `row_bytes_total` bytes per
  * particle in place for N particles. */

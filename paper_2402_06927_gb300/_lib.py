@@ -36,6 +36,7 @@ class SchParams(ct.Structure):
         ("dt", ct.c_double), ("K", ct.c_int32), ("amps", ct.c_double * (SCH_MAX_K // 2)),
         ("M", ct.c_int32), ("sigma", ct.c_double), ("tol", ct.c_double), ("max_iter", ct.c_int32),
         ("dtype", ct.c_int32), ("solver", ct.c_int32), ("layout", ct.c_int32),
+        ("noise", ct.c_int32), ("kappa", ct.c_double), ("eta", ct.c_double), ("matern_k", ct.c_int32),
     ]
 
 
@@ -56,6 +57,7 @@ SIGNATURES = {
     "sch_create": [ct.POINTER(SchParams), ct.POINTER(P)],
     "sch_destroy": [P],
     "sch_layout": [P],
+    "sch_noise_dim": [P],
     "sch_u_from_m": [P, I, P, P, P],
     "sch_m_from_u": [P, I, P, P, P],
     "sch_draw_increments": [P, I, I, U64, U64, U64, I, P, P],

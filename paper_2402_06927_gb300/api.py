@@ -40,7 +40,8 @@ class SchModel:
 
     def __init__(self, L: float, n: int, alpha: float, mu: float, dt: float, amps: Sequence[float],
                  M: int, sigma: float, tol: float, max_iter: int, dtype: str = "f32", solver: str = "auto",
-                 layout: str = "auto"):
+                 layout: str = "auto", noise: str = "modes", kappa: float = 1.0, eta: float = 1.0,
+                 matern_k: int = 3):
         p = SchParams()
         p.L, p.n, p.alpha, p.mu, p.dt = L, n, alpha, mu, dt
         p.K = 2 * len(amps)
@@ -50,20 +51,27 @@ class SchModel:
         p.dtype = SCH_F32 if dtype == "f32" else SCH_F64
         p.solver = {"auto": 0, "li": 1, "ea": 2}[solver]
         p.layout = {"auto": 0, "cta": 1, "warp": 2}[layout]
+        p.noise = {"modes": 0, "matern": 1}[noise]
+        p.kappa, p.eta, p.matern_k = kappa, eta, matern_k
         self.params = p
-        self.n, self.K, self.M, self.dt = n, p.K, M, dt
+        self.n, self.M, self.dt = n, M, dt
         self.dtype = torch.float32 if dtype == "f32" else torch.float64
         h = ct.c_void_p()
         check(lib().sch_create(ct.byref(p), ct.byref(h)), "sch_create")
         self._h = h
         # the kernel layout the library chose: "warp" (one warp per particle) or "cta"
         self.layout = {1: "cta", 2: "warp"}[lib().sch_layout(h)]
+        # Brownian motions per step, the last axis of every dW and lambda: K mode
+        # functions, or one per cell for the Matern noise
+        self.K = int(lib().sch_noise_dim(h))
+        self.noise = noise
 
     @classmethod
     def from_config(cls, cfg, **over):
         from workloads import mode_amplitudes
         kw = dict(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=list(mode_amplitudes(cfg)),
-                  M=cfg.M, sigma=cfg.sigma, tol=cfg.tol, max_iter=cfg.max_iter, dtype=cfg.dtype)
+                  M=cfg.M, sigma=cfg.sigma, tol=cfg.tol, max_iter=cfg.max_iter, dtype=cfg.dtype,
+                  noise=cfg.noise, kappa=cfg.kappa, eta=cfg.eta, matern_k=cfg.matern_k)
         kw.update(over)
         return cls(**kw)
 

@@ -12,6 +12,8 @@ using namespace sch;
 struct sch_ctx {
     sch_params p;
     int C, tp;
+    int Q;            // Brownian motions per step: K (modes) or n (Matern)
+    int matern;       // 1 for SCH_NOISE_MATERN
     int wcs;          // sub-chunk length of the warp-per-particle kernels, 0 = CTA kernels
     WArgs wa;
     ModelArgs<float> af;
@@ -278,6 +280,19 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
     HBasis<double> hb;
     hbasis_host(tpic, th, C, h / 6.0, hb);
     cast_hb(hb, A.hb);
+    if (p.noise == SCH_NOISE_MATERN) {
+        // Q = n cell weights per step replace the K mode weights
+        A.K = p.n;
+        A.K2 = 0;
+        const double k2 = 1.0 / (p.kappa * p.kappa);
+        HTab tg;
+        ctab_host(h / 6.0 - k2 / h, 2.0 * h / 3.0 + 2.0 * k2 / h, C, tg);
+        cast_tab(tg, A.matern);
+        rtab_host(tg, TP, q);
+        cast_rtab(q, A.rmatern);
+        A.mz = (R)(p.eta * sqrt(h) / 8.0);
+        A.mk = p.matern_k;
+    }
 }
 
 // the warp-per-particle tables: sub-chunks of CS nodes, 64-row reduced systems
@@ -339,8 +354,16 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     const int tp = p.n / C;
     if (!pow2(tp) || tp < 32 || tp > 512) return SCH_ERR_UNSUPPORTED;
     if (p.layout < SCH_LAYOUT_AUTO || p.layout > SCH_LAYOUT_WARP) return SCH_ERR_ARG;
+    if (p.noise != SCH_NOISE_MODES && p.noise != SCH_NOISE_MATERN) return SCH_ERR_ARG;
     const int solver = (p.solver != SCH_SOLVER_AUTO) ? p.solver : (p.dtype == SCH_F32 ? SCH_SOLVER_EA : SCH_SOLVER_LI);
-    const bool warp_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && (p.n == 256 || p.n == 512 || p.n == 1024);
+    const bool matern = p.noise == SCH_NOISE_MATERN;
+    if (matern) {
+        if (!(p.kappa > 0) || !(p.eta >= 0) || p.matern_k < 1 || p.matern_k > 8) return SCH_ERR_ARG;
+        if (solver != (p.dtype == SCH_F32 ? SCH_SOLVER_EA : SCH_SOLVER_LI)) return SCH_ERR_UNSUPPORTED;
+        if (p.layout == SCH_LAYOUT_WARP) return SCH_ERR_UNSUPPORTED;
+    }
+    const bool warp_fits = !matern && p.dtype == SCH_F32 && solver == SCH_SOLVER_EA &&
+                           (p.n == 256 || p.n == 512 || p.n == 1024);
     if (p.layout == SCH_LAYOUT_WARP && !warp_fits) return SCH_ERR_UNSUPPORTED;
     const bool warp_ok = warp_fits && p.layout != SCH_LAYOUT_CTA;
     sch_ctx* c = (sch_ctx*)calloc(1, sizeof(sch_ctx));
@@ -348,6 +371,8 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     c->p = p;
     c->C = C;
     c->tp = tp;
+    c->matern = matern ? 1 : 0;
+    c->Q = matern ? p.n : p.K;
     fill_args(p, C, c->af);
     fill_args(p, C, c->ad);
     if (warp_ok) {
@@ -368,6 +393,11 @@ int sch_destroy(sch_ctx* ctx) {
 int sch_layout(const sch_ctx* ctx) {
     if (!ctx) return SCH_ERR_ARG;
     return ctx->wcs ? SCH_LAYOUT_WARP : SCH_LAYOUT_CTA;
+}
+
+int sch_noise_dim(const sch_ctx* ctx) {
+    if (!ctx) return SCH_ERR_ARG;
+    return ctx->Q;
 }
 
 size_t pf_resample_workspace_bytes(int N, size_t row_bytes_total) {
@@ -397,9 +427,9 @@ int sch_draw_increments(sch_ctx* ctx, int N, int nsteps, uint64_t seed, uint64_t
     if (!dW) return SCH_ERR_ARG;
     const double sq = sqrt(ctx->p.dt);
     if (ctx->p.dtype == SCH_F32)
-        return launch_draw<float>(N, nsteps, ctx->p.K, (float)sq, seed, tag, ctr, particle0, (float*)dW,
+        return launch_draw<float>(N, nsteps, ctx->Q, (float)sq, seed, tag, ctr, particle0, (float*)dW,
                                   S(stream));
-    return launch_draw<double>(N, nsteps, ctx->p.K, sq, seed, tag, ctr, particle0, (double*)dW, S(stream));
+    return launch_draw<double>(N, nsteps, ctx->Q, sq, seed, tag, ctr, particle0, (double*)dW, S(stream));
 }
 
 int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_out, void* u_out,
@@ -410,19 +440,21 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
     if (!m || !m_out || !u_out || (nsteps > 0 && !dW)) return SCH_ERR_ARG;
     if (y && !nll) return SCH_ERR_ARG;
     if (nsteps > 4096) return SCH_ERR_ARG;
-    const size_t sm = ctx->wcs ? wwindow_smem(ctx->wcs, nsteps, ctx->p.K)
-                      : (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
-                                                  : window_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
+    const size_t sm = ctx->wcs ? wwindow_smem(ctx->wcs, nsteps, ctx->Q)
+                      : (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->Q)
+                                                  : window_smem<double, 4>(ctx->tp, nsteps, ctx->Q);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
     if (ctx->p.dtype == SCH_F32) {
         WindowIO<float> io{nsteps, (const float*)m, (float*)m_out, (float*)u_out, (const float*)dW,
                            (const float*)lambda, (const float*)y, nll, logG, iters, status};
+        if (ctx->matern) return launch_window_matern<float, 8>(ctx->af, io, N, S(stream));
         if (ctx->wcs) return launch_wwindow(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_window<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_window<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }
     WindowIO<double> io{nsteps, (const double*)m, (double*)m_out, (double*)u_out, (const double*)dW,
                         (const double*)lambda, (const double*)y, nll, logG, iters, status};
+    if (ctx->matern) return launch_window_matern<double, 4>(ctx->ad, io, N, S(stream));
     return ctx->ad.solver == SCH_SOLVER_EA ? launch_window<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
                                            : launch_window<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
 }
@@ -526,15 +558,16 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
     if (N == 0 || n_iter == 0) return SCH_OK;
     if (!m_start || !dW || !y || !nll || !m_end || !u_end) return SCH_ERR_ARG;
     if (lambda && !logG) return SCH_ERR_ARG;
-    const size_t sm = ctx->wcs ? wjitter_smem(ctx->wcs, nsteps, ctx->p.K)
-                      : (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->p.K)
-                                                  : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->p.K);
+    const size_t sm = ctx->wcs ? wjitter_smem(ctx->wcs, nsteps, ctx->Q)
+                      : (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->Q)
+                                                  : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->Q);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
     const double sq = sqrt(1.0 - rho * rho);
     if (ctx->p.dtype == SCH_F32) {
         JitterIO<float> io{nsteps, n_iter, 0, theta, tstate, (float)rho, (float)sq, seed, ctr,
                            (const float*)m_start, (float*)dW, (const float*)lambda, (const float*)y, nll, logG,
                            (float*)m_end, (float*)u_end, accepts, iters, status};
+        if (ctx->matern) return launch_jitter_matern<float, 8>(ctx->af, io, N, S(stream));
         if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
@@ -542,6 +575,7 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
     JitterIO<double> io{nsteps, n_iter, 0, theta, tstate, rho, sq, seed, ctr, (const double*)m_start,
                         (double*)dW, (const double*)lambda, (const double*)y, nll, logG, (double*)m_end,
                         (double*)u_end, accepts, iters, status};
+    if (ctx->matern) return launch_jitter_matern<double, 4>(ctx->ad, io, N, S(stream));
     return ctx->ad.solver == SCH_SOLVER_EA ? launch_jitter<double, 4, SCH_SOLVER_EA>(ctx->ad, io, N, S(stream))
                                            : launch_jitter<double, 4, SCH_SOLVER_LI>(ctx->ad, io, N, S(stream));
 }
@@ -575,8 +609,8 @@ int pf_gated_stages(sch_ctx* ctx, int N, int nsteps, int n_stages, int first_sta
         if (!bufs_a[a] || !bufs_b[a]) return SCH_ERR_ARG;
     if ((bufs_a[PF_STAGE_ARRAYS - 1] == nullptr) != (bufs_b[PF_STAGE_ARRAYS - 1] == nullptr)) return SCH_ERR_ARG;
     const size_t b = ctx->p.dtype == SCH_F32 ? 4 : 8;
-    const size_t rows[PF_STAGE_ARRAYS] = {ctx->p.n * b, ctx->p.n * b, ctx->p.n * b, (size_t)nsteps * ctx->p.K * b,
-                                          8, 8, (size_t)nsteps * ctx->p.K * b};
+    const size_t rows[PF_STAGE_ARRAYS] = {ctx->p.n * b, ctx->p.n * b, ctx->p.n * b, (size_t)nsteps * ctx->Q * b,
+                                          8, 8, (size_t)nsteps * ctx->Q * b};
     void* cur[PF_STAGE_ARRAYS];
     void* nxt[PF_STAGE_ARRAYS];
     for (int a = 0; a < PF_STAGE_ARRAYS; ++a) {
@@ -628,6 +662,7 @@ static bool mala_args_ok(const sch_ctx* ctx, int N, int nsteps, int particle0, d
 int pf_mala_propose(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint64_t seed, uint64_t ctr,
                     int particle0, const void* dW, const void* lambda, const void* gJ, void* dW_prop, void* stream) {
     if (!mala_args_ok(ctx, N, nsteps, particle0, theta, h)) return SCH_ERR_ARG;
+    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!dW || !gJ || !dW_prop) return SCH_ERR_ARG;
     const int K = ctx->p.K;
@@ -642,6 +677,7 @@ int pf_mala_accept(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint
                    int particle0, void* dW, const void* dW_prop, const void* lambda, double* J, const double* J_prop,
                    void* gJ, const void* gJ_prop, int32_t* accepts, void* stream) {
     if (!mala_args_ok(ctx, N, nsteps, particle0, theta, h)) return SCH_ERR_ARG;
+    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!dW || !dW_prop || !J || !J_prop || !gJ || !gJ_prop) return SCH_ERR_ARG;
     const int NK = nsteps * ctx->p.K;
@@ -687,6 +723,7 @@ int sch_adjoint_window(sch_ctx* ctx, int N, int nsteps, int ckpt, const void* m_
                        const void* lambda, const void* y, double* J, void* g_lambda, void* g_dW, void* g_m0,
                        int32_t* iters, int32_t* status, void* ws, size_t ws_bytes, void* stream) {
     if (!ctx || N < 0 || nsteps <= 0 || ckpt <= 0 || nsteps > 4096) return SCH_ERR_ARG;
+    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!m_start || !dW || !y || !J || !g_lambda) return SCH_ERR_ARG;
     if (!ws || ws_bytes < sch_adjoint_workspace_bytes(ctx, N, nsteps, ckpt)) return SCH_ERR_WORKSPACE;
@@ -713,6 +750,7 @@ int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gto
     if (!ctx || N < 0 || nsteps <= 0 || ckpt <= 0 || max_iter < 0 || nsteps > 4096) return SCH_ERR_ARG;
     if (mode != PF_NUDGE_SEQUENTIAL && mode != PF_NUDGE_OPEN_LOOP) return SCH_ERR_ARG;
     if (!(gtol >= 0.0)) return SCH_ERR_ARG;
+    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!m_start || !y || !lambda || !dW || !J) return SCH_ERR_ARG;
     if (!ws || ws_bytes < pf_nudge_workspace_bytes(ctx, N, nsteps, ckpt)) return SCH_ERR_WORKSPACE;

@@ -65,6 +65,10 @@ struct ModelArgs {
     R rot_c[SCH_MAX_K / 2], rot_s[SCH_MAX_K / 2];   // cos(j 2 pi / n), sin(j 2 pi / n), j = 1..K/2
     RTab<R> rhel, rmass, rsmooth, rpic;
     HBasis<R> hb;
+    CTab<R> matern;         // M + kappa^-2 K (Matern noise)
+    RTab<R> rmatern;
+    R mz;                   // Matern cell weight scale eta sqrt(h) / 8
+    int mk;                 // Matern solves per step
 };
 
 // Sub-chunk coefficients of a constant symmetric circulant tridiagonal matrix
@@ -182,6 +186,12 @@ int launch_prior(const ModelArgs<R>& A, const R* u_truth, uint64_t seed, R scale
                  cudaStream_t st);
 template <typename R, int C>
 size_t jitter_smem(int tp, int Ns, int K);
+// window and jitter kernels with the Matern noise (sch_matern_{f32,f64}.cu): the
+// default solver of each precision only
+template <typename R, int C>
+int launch_window_matern(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st);
+template <typename R, int C>
+int launch_jitter_matern(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st);
 template <typename R>
 int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0,
                 R* dW, cudaStream_t st);

@@ -369,6 +369,38 @@ __device__ __forceinline__ void node_angle(int node, int n, R& s, R& c) {
     sincospi(R(2) * R(i) / R(n), &s, &c);
 }
 
+// Matern SALT increment dU/4 at the C + 2 nodes i0 - 1 .. i0 + C (Eq. noise_solve2):
+// wq holds the step's n cell weights eta sqrt(h)/8 (dW_c + lambda_c dt), so the
+// load eta (dW_h, phi_i) / 4 is wq_{i-1} + wq_i; then mk solves with the
+// tabulated G = M + kappa^-2 K, each later one loaded with M U_{j-1}.
+template <typename R, int C, int TP>
+__device__ __forceinline__ void matern_nodes(const ModelArgs<R>& A, Shm<R, TP>* sh, const R* wq, R (&nq)[C + 2]) {
+    const int i0 = threadIdx.x * C;
+    R r[C], U[C], Up, Un;
+    r[0] = wq[i0 == 0 ? A.n - 1 : i0 - 1] + wq[i0];
+#pragma unroll
+    for (int i = 1; i < C; ++i) r[i] = wq[i0 + i - 1] + wq[i0 + i];
+    const_solve<R, C, TP>(A.matern, A.rmatern, r, U, Up, Un, sh);
+    for (int j = 1; j < A.mk; ++j) {
+        mass_apply<R, C>(A.h6, U, Up, Un, r);
+        const_solve<R, C, TP>(A.matern, A.rmatern, r, U, Up, Un, sh);
+    }
+    nq[0] = Up;
+#pragma unroll
+    for (int i = 0; i < C; ++i) nq[i + 1] = U[i];
+    nq[C + 1] = Un;
+}
+
+// the step's noise at the chunk's nodes and its two neighbours, for noise model NZ
+template <int NZ, typename R, int C, int TP>
+__device__ __forceinline__ void noise_any(const ModelArgs<R>& A, Shm<R, TP>* sh, const R* wq, R s0, R c0,
+                                          R (&nq)[C + 2]) {
+    if constexpr (NZ == SCH_NOISE_MATERN)
+        matern_nodes<R, C, TP>(A, sh, wq, nq);
+    else
+        noise_nodes<R, C>(A, wq, s0, c0, nq);
+}
+
 // --------------------------------------------------------------------------
 // the per-thread state carried through a window
 // --------------------------------------------------------------------------
@@ -382,13 +414,13 @@ struct Field {
 // One implicit-midpoint step (Eq. fde1) for this thread's chunk.
 // wq: the K noise weights of the step, scaled by a_j / 4.
 // --------------------------------------------------------------------------
-template <typename R, int C, int TP>
+template <typename R, int C, int TP, int NZ = SCH_NOISE_MODES>
 __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, Field<R, C>& f, const R* wq,
                                          R s0, R c0, int& iters, int& flags) {
     const int t = threadIdx.x;
     // W0 = dt/8 u0 + dU/4, at the chunk and its two neighbour nodes
     R nq[C + 2];
-    noise_nodes<R, C>(A, wq, s0, c0, nq);
+    noise_any<NZ, R, C, TP>(A, sh, wq, s0, c0, nq);
     R W0[C];
 #pragma unroll
     for (int i = 0; i < C; ++i) W0[i] = A.dt8 * f.u[i] + nq[i + 1];
@@ -548,13 +580,13 @@ __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, 
 // iterate p is decided at the first barrier of iteration p + 1 (whose local
 // work is then discarded), so an iteration costs two barriers.
 // --------------------------------------------------------------------------
-template <typename R, int C, int TP>
+template <typename R, int C, int TP, int NZ = SCH_NOISE_MODES>
 __device__ __forceinline__ void sch_step_ea(const ModelArgs<R>& A, Shm<R, TP>* sh, Field<R, C>& f, const R* wq,
                                             R s0, R c0, int& iters, int& flags) {
     constexpr int RR = TP / 32;
     const int t = threadIdx.x;
     R nq[C + 2];
-    noise_nodes<R, C>(A, wq, s0, c0, nq);
+    noise_any<NZ, R, C, TP>(A, sh, wq, s0, c0, nq);
     // W0 = dt/8 u0 + dU/4, so that dv/4 = W0 + dt/8 u at an iterate
     R W0[C];
 #pragma unroll
@@ -725,13 +757,13 @@ __device__ __forceinline__ void sch_step_ea(const ModelArgs<R>& A, Shm<R, TP>* s
     f.un = uin;
 }
 
-template <int S, typename R, int C, int TP>
+template <int S, typename R, int C, int TP, int NZ = SCH_NOISE_MODES>
 __device__ __forceinline__ void step_any(const ModelArgs<R>& A, Shm<R, TP>* sh, Field<R, C>& f, const R* wq, R s0,
                                          R c0, int& iters, int& flags) {
     if constexpr (S == SCH_SOLVER_EA)
-        sch_step_ea<R, C, TP>(A, sh, f, wq, s0, c0, iters, flags);
+        sch_step_ea<R, C, TP, NZ>(A, sh, f, wq, s0, c0, iters, flags);
     else
-        sch_step<R, C, TP>(A, sh, f, wq, s0, c0, iters, flags);
+        sch_step<R, C, TP, NZ>(A, sh, f, wq, s0, c0, iters, flags);
 }
 
 // load m of a particle, exchange its chunk ends and solve for u
@@ -746,15 +778,18 @@ __device__ __forceinline__ void field_start(const ModelArgs<R>& A, Shm<R, TP>* s
     const_solve<R, C, TP>(A.hel, A.rhel, r, f.u, f.up, f.un, sh);
 }
 
-// the noise weights a_j/4 (dW + lambda dt) of a window, staged in smem
-template <typename R>
+// the noise weights of a window, staged in smem: a_j/4 (dW + lambda dt) per mode,
+// or eta sqrt(h)/8 (dW + lambda dt) per cell for the Matern field (A.K = n)
+template <typename R, int NZ = SCH_NOISE_MODES>
 __device__ __forceinline__ void stage_noise(const ModelArgs<R>& A, R* dst, const R* dW, const R* lam, int Ns) {
     const int tot = Ns * A.K;
     for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-        const int k = q % A.K;
         R v = dW[q];
         if (lam) v += lam[q] * A.dt;
-        dst[q] = A.amp4[k >> 1] * v;
+        if constexpr (NZ == SCH_NOISE_MATERN)
+            dst[q] = A.mz * v;
+        else
+            dst[q] = A.amp4[(q % A.K) >> 1] * v;
     }
 }
 
@@ -826,20 +861,20 @@ struct Occ {
                                     : (TP <= 32 ? 16 : (TP <= 64 ? 8 : (TP <= 128 ? 4 : (TP <= 256 ? 2 : 1))));
 };
 
-template <typename R, int C, int TP, int S>
+template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
 __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) window_kernel(ModelArgs<R> A, WindowIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     R* noise = reinterpret_cast<R*>(smem_raw + shm_base_bytes<R, TP>());
     const int p = blockIdx.x;
     const size_t NK = (size_t)io.Ns * A.K;
-    stage_noise(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
+    stage_noise<R, NZ>(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
     R s0, c0;
     node_angle<R>((int)threadIdx.x * C - 1, A.n, s0, c0);
     Field<R, C> f;
     field_start<R, C, TP>(A, sh, io.m_in + (size_t)p * A.n, f);   // its barriers publish the noise
     int iters = 0, flags = 0;
-    for (int s = 0; s < io.Ns; ++s) step_any<S, R, C, TP>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
+    for (int s = 0; s < io.Ns; ++s) step_any<S, R, C, TP, NZ>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
     const int i0 = threadIdx.x * C;
 #pragma unroll
     for (int i = 0; i < C; ++i) {
@@ -863,7 +898,7 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) window_kernel(ModelArgs<
 
 // PCN jittering: n_iter proposals of the window noise, each run through the
 // whole window from m_start and accepted with probability min(1, exp(w0 - w1)).
-template <typename R, int C, int TP, int S>
+template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
 __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<R> A, JitterIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
@@ -905,11 +940,11 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<
             }
         }
         __syncthreads();
-        stage_noise(A, noise, prop, lam, Ns);
+        stage_noise<R, NZ>(A, noise, prop, lam, Ns);
         Field<R, C> f;
         field_start<R, C, TP>(A, sh, io.m_start + (size_t)p * A.n, f);   // barriers publish the noise
         int fl = 0;
-        for (int s = 0; s < Ns; ++s) step_any<S, R, C, TP>(A, sh, f, noise + s * K, s0, c0, iters, fl);
+        for (int s = 0; s < Ns; ++s) step_any<S, R, C, TP, NZ>(A, sh, f, noise + s * K, s0, c0, iters, fl);
         double mis = chunk_misfit<R, C>(A, f.u, io.y);
         double gl = window_girsanov(A, prop, lam, Ns);
         block_sum2<R, TP>(sh, mis, gl);
@@ -1048,18 +1083,18 @@ struct Launch {
         if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
 
-    template <int S>
+    template <int S, int NZ = SCH_NOISE_MODES>
     static int window(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st) {
         const size_t sm = smem(io.Ns, A.K, 1);
-        prep(window_kernel<R, C, TP, S>, sm);
-        window_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
+        prep(window_kernel<R, C, TP, S, NZ>, sm);
+        window_kernel<R, C, TP, S, NZ><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
-    template <int S>
+    template <int S, int NZ = SCH_NOISE_MODES>
     static int jitter(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st) {
         const size_t sm = smem(io.Ns, A.K, 3);
-        prep(jitter_kernel<R, C, TP, S>, sm);
-        jitter_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
+        prep(jitter_kernel<R, C, TP, S, NZ>, sm);
+        jitter_kernel<R, C, TP, S, NZ><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
     static int helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cudaStream_t st) {

@@ -98,3 +98,37 @@ def test_host_argument_errors_need_no_gpu(lib):
     assert lib.pf_jitter(h, 4, 5, 1, 0.5, 1.5, 0, 0, *([None] * 12)) == -1
     assert lib.pf_resample_workspace_bytes(10, 48) == 480
     assert lib.sch_destroy(h) == 0
+
+
+@pytest.mark.parametrize("kw,rc", [({"noise": 1}, 0), ({"noise": 1, "dtype": 1}, 0),
+                                   ({"noise": 2}, -1), ({"noise": 1, "kappa": 0.0}, -1),
+                                   ({"noise": 1, "eta": -1.0}, -1), ({"noise": 1, "matern_k": 0}, -1),
+                                   ({"noise": 1, "matern_k": 9}, -1),
+                                   # Matern noise: CTA layout and each precision's default solver only
+                                   ({"noise": 1, "dtype": 1, "layout": 2}, -6), ({"noise": 1, "solver": 2}, -6),
+                                   ({"noise": 1, "dtype": 1, "solver": 1}, -6)])
+def test_create_validates_matern(lib, kw, rc):
+    base = {"kappa": 1.0, "eta": 0.2, "matern_k": 3}
+    base.update(kw)
+    p = _params(**base)
+    h = ct.c_void_p()
+    got = lib.sch_create(ct.byref(p), ct.byref(h))
+    assert got == rc
+    if got == 0:
+        # one Brownian motion per cell, CTA layout even where the warp layout would fit
+        assert lib.sch_noise_dim(h) == p.n
+        assert lib.sch_layout(h) == 1
+        # entry points built on the adjoint take the mode expansion only
+        assert lib.sch_adjoint_window(h, 1, 5, 1, None, None, None, None, None, None, None, None, None, None, None,
+                                      0, None) == -6
+        assert lib.pf_mala_propose(h, 1, 5, 0.5, 0.1, 0, 0, 0, None, None, None, None, None) == -6
+        assert lib.sch_destroy(h) == 0
+
+
+def test_noise_dim_of_the_mode_expansion(lib):
+    p = _params()
+    h = ct.c_void_p()
+    assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0
+    assert lib.sch_noise_dim(h) == 4
+    assert lib.sch_noise_dim(None) == -1
+    assert lib.sch_destroy(h) == 0

@@ -1,0 +1,132 @@
+"""GPU parity of the Matern SALT noise (Eq. noise_solve2) against the FP64 oracle.
+
+The window and jitter kernels with one Brownian motion per cell and three
+chained P1 solves per step.  Tolerances as for the mode expansion: FP64 fields
+1e-10 and FP32 fields 1e-4 relative to the oracle's max-norm after a window.
+"""
+import dataclasses
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from workloads import get_config, random_state, random_increments, random_drift, random_obs
+from oracle import filter as OF
+from oracle import rng as ORNG
+from tests.helpers import gpu_model, oracle_model, tdev, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(name):
+    base, _, over = name.partition("@")
+    cfg = get_config(base)
+    for kv in filter(None, over.split(",")):
+        key, val = kv.split("=")
+        cfg = dataclasses.replace(cfg, **{key: type(getattr(cfg, key))(val)})
+    return cfg
+
+
+def _case(cfg, N, seed, Ns=None, lam=False):
+    Ns = cfg.Ns if Ns is None else Ns
+    om = oracle_model(cfg)
+    u0 = random_state(cfg, N, seed)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    dW = random_increments(cfg, N, seed + 1, steps=Ns)
+    la = random_drift(cfg, N, seed + 2, steps=Ns, scale=0.3) if lam else None
+    return om, m0, dW, la
+
+
+@pytest.mark.parametrize("name,N", [("cfg1m_f64", 4), ("cfg1m_f64@n=1024,M=64,Ns=3", 2),
+                                    ("cfg1m_f64@eta=1.0,kappa=2.0,matern_k=1", 3), ("cfg1m_f64@n=128", 3)])
+@pytest.mark.parametrize("lam", [False, True])
+def test_matern_window_f64(name, N, lam):
+    cfg = _cfg(name)
+    g = gpu_model(cfg)
+    assert g.K == cfg.n and g.layout == "cta"
+    om, m0, dW, la = _case(cfg, N, 11, lam=lam)
+    ref = om.ensemble_window(m0, dW, la)
+    y = random_obs(cfg, 3)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), None if la is None else tdev(la, g.dtype),
+                          y=tdev(y, g.dtype))
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < 1e-10
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < 1e-10
+    assert np.all(np.abs(out["iters"].cpu().numpy() - ref[2].sum(axis=1)) <= cfg.Ns)
+    lg = OF.girsanov_logG(la, dW, cfg.dt) if la is not None else np.zeros(N)
+    assert np.allclose(out["nll"].cpu().numpy(), OF.nll(ref[1], y, cfg.sigma), rtol=1e-9)
+    assert np.allclose(out["logG"].cpu().numpy(), lg, rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,N", [("cfg2m_f32", 3), ("cfg2m_f32@n=256,M=64", 4), ("cfg2m_f32@n=4096,M=128,Ns=4", 2)])
+def test_matern_window_f32(name, N):
+    cfg = _cfg(name)
+    g = gpu_model(cfg)
+    om, m0, dW, la = _case(cfg, N, 31, lam=True)
+    ref = om.ensemble_window(m0, dW, la)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < 1e-4
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < 1e-4
+
+
+def test_matern_draw_increments_one_per_cell():
+    cfg = get_config("cfg1m_f64")
+    g = gpu_model(cfg)
+    dW = g.draw_increments(3, cfg.Ns, 123, ORNG.TAG_PRIOR_DW, 9, particle0=2).cpu().numpy()
+    ref = ORNG.window_increments(123, ORNG.TAG_PRIOR_DW, 3, cfg.Ns, cfg.n, cfg.dt, 9, particle0=2)
+    assert dW.shape == (3, cfg.Ns, cfg.n)
+    assert np.max(np.abs(dW - ref)) < 1e-13
+
+
+@pytest.mark.parametrize("lam", [False, True])
+def test_matern_jitter_matches_oracle(lam):
+    cfg = get_config("cfg1m_f64")
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    N, theta = 6, 0.6
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 50)])
+    dW = random_increments(cfg, N, 51)
+    la = random_drift(cfg, N, 52, scale=0.2) if lam else None
+    y = random_obs(cfg, 53)
+    n_iter, seed, ctr = 3, 77, 1000
+    ref = OF.jitter(om, m0, dW, la, y, cfg.sigma, theta, cfg.rho, n_iter, seed, ctr)
+    dt = g.dtype
+    m0d, dWd, yd = tdev(m0, dt), tdev(dW, dt), tdev(y, dt)
+    lad = None if la is None else tdev(la, dt)
+    st = g.ensemble_step(m0d, dWd, lad, yd)
+    nll, logG, m_end, u_end = st["nll"], st["logG"], st["m"], st["u"]
+    acc, _, status = g.jitter(m0d, dWd, lad, yd, nll, logG, m_end, u_end, theta, cfg.rho, n_iter, seed, ctr)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    acc_g = acc.cpu().numpy()
+    assert np.array_equal(acc_g, ref[5])
+    assert 0 < ref[5].sum() < N * n_iter
+    assert rel_err(dWd.cpu().numpy(), ref[0]) < 1e-10
+    assert rel_err(u_end.cpu().numpy(), ref[4]) < 1e-10
+    assert np.allclose(nll.cpu().numpy(), ref[1], rtol=1e-9)
+
+
+def test_matern_cycle_matches_oracle():
+    # a whole assimilation cycle (tempering, resampling, jittering) with the Matern noise
+    from paper_2402_06927_gb300.filter import EnsembleFilter
+    cfg = get_config("cfg1m_f64", N=16, n_jitter=2)
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    N = cfg.N
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 70, scale=0.1)])
+    y = random_obs(cfg, 71)
+    seed, cycle = 9, 2
+    dW = ORNG.window_increments(seed, ORNG.TAG_PRIOR_DW, N, cfg.Ns, cfg.n, cfg.dt, cycle)
+    ref = OF.assimilation_cycle(om, m0, y, cfg.sigma, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, cycle, dW=dW)
+    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed)
+    f.set_state(tdev(m0, g.dtype))
+    st = f.cycle(tdev(y, g.dtype), cycle)
+    assert len(st.stages) == len(ref["stages"]) >= 2
+    for a, b in zip(st.stages, ref["stages"]):
+        assert abs(a.dtheta - b["dtheta"]) <= 1e-9 * b["dtheta"]
+    assert rel_err(f.u_end.cpu().numpy(), ref["u_end"]) < 1e-8
+    assert rel_err(f.dW.cpu().numpy(), ref["dW"]) < 1e-8
