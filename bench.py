@@ -43,9 +43,18 @@ FLOPS_PER_NODE_ITER = {"li": 44, "ea": 30}
 FLOPS_PER_NODE_STEP_EXTRA = {"li": 0, "ea": 5}
 
 
-def step_flops(n, K, solver, iters, steps):
-    """Algorithmic flops of `steps` particle-steps that took `iters` Picard iterations in total."""
-    return n * (FLOPS_PER_NODE_ITER[solver] * iters + (2 * K + FLOPS_PER_NODE_STEP_EXTRA[solver]) * steps)
+# Matern noise synthesis per node and step (Eq. noise_solve2, k solves): staging 3
+# (dW + lambda dt, scale), load 1, per solve of the factored constant cyclic matrix
+# 6, per later load the mass product 4 -> 4 + 6k + 4(k - 1).
+def matern_flops_per_node(k):
+    return 4 + 6 * k + 4 * (k - 1)
+
+
+def step_flops(n, K, solver, iters, steps, noise_per_node=None):
+    """Algorithmic flops of `steps` particle-steps that took `iters` Picard iterations in total.
+    The noise costs 2K per node and step for the mode expansion, else noise_per_node."""
+    noise = 2 * K if noise_per_node is None else noise_per_node
+    return n * (FLOPS_PER_NODE_ITER[solver] * iters + (noise + FLOPS_PER_NODE_STEP_EXTRA[solver]) * steps)
 
 
 # DRAM traffic of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum
@@ -184,8 +193,8 @@ def oracle_sample(cfg, budget_s: float = 12.0, min_particles: int = 1, first: in
     of a seeded sample, for about budget_s seconds.  Returns (steps/s, description, seconds, steps)."""
     import numpy as np
     from oracle.model import Model
-    from workloads import mode_amplitudes, random_increments, random_state
-    om = Model(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg))
+    from workloads import random_increments, random_state
+    om = Model.from_config(cfg)
     u0 = random_state(cfg, first + count, 123)
     dW = random_increments(cfg, first + count, 124)
     t0 = time.perf_counter()
@@ -219,8 +228,10 @@ def oracle_parallel(name, budget_s: float = 10.0, per_core: int = 512):
         res = pool.map(_oracle_worker, jobs)
     steps = sum(r[0] for r in res)
     wall = max(r[1] for r in res)
+    from workloads import get_config
     return steps / wall, cores, (f"oracle window propagation (FP64) on {cores} processes, particles split across "
-                                 f"them, {steps} particle-steps of the n=1024 workload in {wall:.1f} s")
+                                 f"them, {steps} particle-steps of the n={get_config(name).n} workload in "
+                                 f"{wall:.1f} s")
 
 
 def run_reference(args):
@@ -267,7 +278,7 @@ def run_ours(args):
     rank, ws = dist_setup()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    cfg = get_config(WORKLOAD)
+    cfg = get_config(args.workload)
     g = SchModel.from_config(cfg)
     N = cfg.N
     seed = 1000 + rank          # independent replicas on each rank
@@ -327,12 +338,14 @@ def run_ours(args):
     it_sum = sum(int(t.sum().item()) for t in timer.iters)
     n_launch = len(jit_ms)
     solver = "ea" if cfg.dtype == "f32" else "li"
-    flops = step_flops(cfg.n, cfg.K, solver, it_sum, N * cfg.Ns * cfg.n_jitter * n_launch)
+    matern = cfg.noise == "matern"
+    flops = step_flops(cfg.n, cfg.K, solver, it_sum, N * cfg.Ns * cfg.n_jitter * n_launch,
+                       matern_flops_per_node(cfg.matern_k) if matern else None)
     jit_s = sum(jit_ms) / 1000.0
     # bytes a jitter launch must move: read m_start and dW, write dW, nll, logG and the
     # accepted end states (m_end, u_end); lower bound assumes the end states of each
     # particle are written once
-    algo_bytes = N * (cfg.n * 4 + 2 * cfg.Ns * cfg.K * 4 + 2 * 8 + 2 * cfg.n * 4)
+    algo_bytes = N * (cfg.n * 4 + 2 * cfg.Ns * cfg.Q * 4 + 2 * 8 + 2 * cfg.n * 4)
     achieved = flops / jit_s / 1e12
     peak = fp32_peak_tflops()
     mean_iters = it_sum / (N * cfg.Ns * cfg.n_jitter * n_launch)
@@ -369,7 +382,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         v1, sample1, _, _ = oracle_sample(cfg, budget_s=8.0)
-        v, cores, sample = oracle_parallel(WORKLOAD, budget_s=8.0)
+        v, cores, sample = oracle_parallel(args.workload, budget_s=8.0)
         cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample,
                "single_core": {"value": v1, "sample": sample1}}
 
@@ -378,9 +391,12 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "SCH twin experiment n=1024 K=8 N=1024 Ns=10 M=64 sigma=0.05 "
-                                   "N*=N/2 jitter=10 rho=0.9999 (FP32 fields, FP64 weights)",
-                       "n": cfg.n, "N": N, "Ns": cfg.Ns, "K": cfg.K, "M": cfg.M,
+            "config": {"workload": (f"SCH twin experiment n={cfg.n} "
+                                    + (f"Matern noise (kappa={cfg.kappa} eta={cfg.eta} k={cfg.matern_k}, "
+                                       f"{cfg.n} Brownian motions per step) " if matern else f"K={cfg.K} ")
+                                    + f"N={N} Ns={cfg.Ns} M={cfg.M} sigma={cfg.sigma} N*=N/2 "
+                                      f"jitter={cfg.n_jitter} rho={cfg.rho} (FP32 fields, FP64 weights)"),
+                       "n": cfg.n, "N": N, "Ns": cfg.Ns, "K": cfg.K, "Q": cfg.Q, "M": cfg.M,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write)",
                        "cycles_per_s": args.steps * ws / dev_s_max,
@@ -388,9 +404,11 @@ def run_ours(args):
                        "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
             "roofline": {"bound": "alu", "kernel": ("wjitter_kernel<8,2> (one warp per particle, EA)" if g.layout == "warp"
-                                    else f"jitter_kernel<float,8,128,{solver.upper()}>"),
+                                    else f"jitter_kernel<float,8,128,{solver.upper()}"
+                                         + (",MATERN>" if matern else ">")),
                          "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": jitter_traffic(),
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": jitter_traffic() if args.workload == WORKLOAD else None,
                          "algorithmic_bytes_per_launch": algo_bytes,
                          "peak_note": "FP32 FMA pipe 152 SMs x 128 lanes x 2 x max SM clock"},
             "gpu_launches": launches,
@@ -570,7 +588,7 @@ def run_mala(args):
     N, Ns, K, n = cfg.N, cfg.Ns, cfg.K, cfg.n
     m0, dW0, lam, y = _nudging_inputs(g, cfg)
     dW = dW0.clone()
-    S, theta, h = MALA_ITERS, MALA_THETA, MALA_H
+    S, theta, h = MALA_ITERS, MALA_THETA, (MALA_H if args.mala_h is None else args.mala_h)
 
     def call(k):
         return g.mala_jitter(m0, dW, lam, y, theta, h, S, 31, 1000 * k, ckpt=5)
@@ -819,6 +837,10 @@ def main():
                     help="learned vs optimiser nudging comparison instead of the default workload")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the reverse-mode adjoint (gradient evaluations) on the nudging workload")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["cfg2_f32", "cfg2m_f32"],
+                    help="filter workload of the main run: cfg2_f32 (mode-expansion noise, the headline) "
+                         "or cfg2m_f32 (the paper's Matern noise)")
+    ap.add_argument("--mala-h", type=float, default=None, help="MALA step size h (--mala)")
     ap.add_argument("--mala", action="store_true",
                     help="time the MALA jitter (moves/s) on the nudging workload")
     ap.add_argument("--filter-kernels", action="store_true",

@@ -440,7 +440,9 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
     if (!m || !m_out || !u_out || (nsteps > 0 && !dW)) return SCH_ERR_ARG;
     if (y && !nll) return SCH_ERR_ARG;
     if (nsteps > 4096) return SCH_ERR_ARG;
-    const size_t sm = ctx->wcs ? wwindow_smem(ctx->wcs, nsteps, ctx->Q)
+    // the Matern kernels hold one step's n cell weights in shared memory, the others a window's noise
+    const size_t sm = ctx->matern ? 0
+                      : ctx->wcs ? wwindow_smem(ctx->wcs, nsteps, ctx->Q)
                       : (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->Q)
                                                   : window_smem<double, 4>(ctx->tp, nsteps, ctx->Q);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;
@@ -558,7 +560,8 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
     if (N == 0 || n_iter == 0) return SCH_OK;
     if (!m_start || !dW || !y || !nll || !m_end || !u_end) return SCH_ERR_ARG;
     if (lambda && !logG) return SCH_ERR_ARG;
-    const size_t sm = ctx->wcs ? wjitter_smem(ctx->wcs, nsteps, ctx->Q)
+    const size_t sm = ctx->matern ? 0
+                      : ctx->wcs ? wjitter_smem(ctx->wcs, nsteps, ctx->Q)
                       : (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->Q)
                                                   : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->Q);
     if (sm > 200 * 1024) return SCH_ERR_UNSUPPORTED;

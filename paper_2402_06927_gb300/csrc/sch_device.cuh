@@ -49,9 +49,17 @@ __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, double& z0, d
     z1 = r * s;
 }
 
+// A 53-bit integer v times 2^-53 in float, from its high 32 and low 21 bits: two
+// 32-bit conversions (a 64-bit integer conversion would run on the narrow FP64 pipe).
+__device__ __forceinline__ float u53_to_float(uint64_t v) {
+    const float hi = __uint2float_rn((unsigned)(v >> 21));
+    const float lo = __uint2float_rn((unsigned)(v & 0x1FFFFFull));
+    return fmaf(hi, 0x1.0p-32f, lo * 0x1.0p-53f);
+}
+
 __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, float& z0, float& z1) {
-    const float u1 = (float)((a >> 11) + 1ull) * 0x1.0p-53f;
-    const float u2 = (float)(b >> 11) * 0x1.0p-53f;
+    const float u1 = u53_to_float((a >> 11) + 1ull);
+    const float u2 = u53_to_float(b >> 11);
     const float r = sqrtf(-2.0f * logf(u1));
     float s, c;
     sincospif(2.0f * u2, &s, &c);

@@ -778,18 +778,15 @@ __device__ __forceinline__ void field_start(const ModelArgs<R>& A, Shm<R, TP>* s
     const_solve<R, C, TP>(A.hel, A.rhel, r, f.u, f.up, f.un, sh);
 }
 
-// the noise weights of a window, staged in smem: a_j/4 (dW + lambda dt) per mode,
-// or eta sqrt(h)/8 (dW + lambda dt) per cell for the Matern field (A.K = n)
-template <typename R, int NZ = SCH_NOISE_MODES>
+// the noise weights a_j/4 (dW + lambda dt) of a window, staged in smem
+template <typename R>
 __device__ __forceinline__ void stage_noise(const ModelArgs<R>& A, R* dst, const R* dW, const R* lam, int Ns) {
     const int tot = Ns * A.K;
     for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+        const int k = q % A.K;
         R v = dW[q];
         if (lam) v += lam[q] * A.dt;
-        if constexpr (NZ == SCH_NOISE_MATERN)
-            dst[q] = A.mz * v;
-        else
-            dst[q] = A.amp4[(q % A.K) >> 1] * v;
+        dst[q] = A.amp4[k >> 1] * v;
     }
 }
 
@@ -861,20 +858,20 @@ struct Occ {
                                     : (TP <= 32 ? 16 : (TP <= 64 ? 8 : (TP <= 128 ? 4 : (TP <= 256 ? 2 : 1))));
 };
 
-template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
+template <typename R, int C, int TP, int S>
 __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) window_kernel(ModelArgs<R> A, WindowIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     R* noise = reinterpret_cast<R*>(smem_raw + shm_base_bytes<R, TP>());
     const int p = blockIdx.x;
     const size_t NK = (size_t)io.Ns * A.K;
-    stage_noise<R, NZ>(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
+    stage_noise(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
     R s0, c0;
     node_angle<R>((int)threadIdx.x * C - 1, A.n, s0, c0);
     Field<R, C> f;
     field_start<R, C, TP>(A, sh, io.m_in + (size_t)p * A.n, f);   // its barriers publish the noise
     int iters = 0, flags = 0;
-    for (int s = 0; s < io.Ns; ++s) step_any<S, R, C, TP, NZ>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
+    for (int s = 0; s < io.Ns; ++s) step_any<S, R, C, TP>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
     const int i0 = threadIdx.x * C;
 #pragma unroll
     for (int i = 0; i < C; ++i) {
@@ -898,7 +895,7 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) window_kernel(ModelArgs<
 
 // PCN jittering: n_iter proposals of the window noise, each run through the
 // whole window from m_start and accepted with probability min(1, exp(w0 - w1)).
-template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
+template <typename R, int C, int TP, int S>
 __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<R> A, JitterIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
@@ -940,11 +937,11 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) jitter_kernel(ModelArgs<
             }
         }
         __syncthreads();
-        stage_noise<R, NZ>(A, noise, prop, lam, Ns);
+        stage_noise(A, noise, prop, lam, Ns);
         Field<R, C> f;
         field_start<R, C, TP>(A, sh, io.m_start + (size_t)p * A.n, f);   // barriers publish the noise
         int fl = 0;
-        for (int s = 0; s < Ns; ++s) step_any<S, R, C, TP, NZ>(A, sh, f, noise + s * K, s0, c0, iters, fl);
+        for (int s = 0; s < Ns; ++s) step_any<S, R, C, TP>(A, sh, f, noise + s * K, s0, c0, iters, fl);
         double mis = chunk_misfit<R, C>(A, f.u, io.y);
         double gl = window_girsanov(A, prop, lam, Ns);
         block_sum2<R, TP>(sh, mis, gl);
@@ -1083,18 +1080,18 @@ struct Launch {
         if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     }
 
-    template <int S, int NZ = SCH_NOISE_MODES>
+    template <int S>
     static int window(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cudaStream_t st) {
         const size_t sm = smem(io.Ns, A.K, 1);
-        prep(window_kernel<R, C, TP, S, NZ>, sm);
-        window_kernel<R, C, TP, S, NZ><<<N, TP, sm, st>>>(A, io);
+        prep(window_kernel<R, C, TP, S>, sm);
+        window_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
-    template <int S, int NZ = SCH_NOISE_MODES>
+    template <int S>
     static int jitter(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st) {
         const size_t sm = smem(io.Ns, A.K, 3);
-        prep(jitter_kernel<R, C, TP, S, NZ>, sm);
-        jitter_kernel<R, C, TP, S, NZ><<<N, TP, sm, st>>>(A, io);
+        prep(jitter_kernel<R, C, TP, S>, sm);
+        jitter_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
     static int helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cudaStream_t st) {
