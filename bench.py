@@ -404,8 +404,8 @@ def run_ours(args):
                        "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
             "roofline": {"bound": "alu", "kernel": ("wjitter_kernel<8,2> (one warp per particle, EA)" if g.layout == "warp"
-                                    else f"jitter_kernel<float,8,128,{solver.upper()}"
-                                         + (",MATERN>" if matern else ">")),
+                                    else (f"matern_jitter_kernel<float,8,128,{solver.upper()}>" if matern
+                                          else f"jitter_kernel<float,8,128,{solver.upper()}>")),
                          "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": jitter_traffic() if args.workload == WORKLOAD else None,
