@@ -348,6 +348,33 @@ class Model:
         """int m dx = (m, 1)."""
         return float(np.sum(self.apply(self.mass(), m)))
 
+    def exp1_field(self, cells: np.ndarray, a: float, b: float) -> np.ndarray:
+        """The initial velocity of Eq. init_solve for one member: U^{0,1} solves
+        (U, v) + (U', v') = (|W|, v) for the DG0 field W with cell values ``cells``,
+        U^{0,j+1} solves the same with right-hand side (U^{0,j}, v), j = 1, 2, and
+        u = a^2 U^{0,3} + b^2."""
+        Ma = self.mass()
+        Ka = self.stiffness()
+        S = tuple(Ma[j] + Ka[j] for j in range(3))
+        w = np.abs(np.asarray(cells, dtype=np.float64))
+        U = self.solve(S, 0.5 * self.h * (np.roll(w, 1) + w))
+        for _ in range(2):
+            U = self.solve(S, self.apply(Ma, U))
+        return a * a * U + b * b
+
+    def prior_exp1(self, seed: int, N: int, particle0: int = 0):
+        """Members particle0 .. particle0 + N - 1 of the initial ensemble of Exp 1 (Sec. 4.1):
+        W_p has cell values N(0, h), a_p, b_p ~ N(0, 1), u_p = exp1_field(W_p, a_p, b_p).
+        The normals are Philox (seed, TAG_INIT) at counter (k // 4, 0, p, 0): k < n for the
+        cells, k = n and n + 1 for a_p and b_p.  Returns the momenta m [N, n] and velocities u [N, n]."""
+        from oracle import rng
+        p = np.arange(particle0, particle0 + N, dtype=np.uint64)
+        z = rng.normals(seed, rng.TAG_INIT, self.n + 2, np.uint64(0), p, np.uint64(0))
+        u = np.stack([self.exp1_field(math.sqrt(self.h) * z[q, : self.n], z[q, self.n], z[q, self.n + 1])
+                      for q in range(N)])
+        m = np.stack([self.m_from_u(uq) for uq in u])
+        return m, u
+
     def prior_sample(self, u_truth: np.ndarray, seed: int, N: int, scale: float):
         """Prior ensemble about a truth velocity (a reading of Eq. init_solve).
 

@@ -251,3 +251,31 @@ def test_both_picard_schemes_reach_the_same_step():
     assert np.max(np.abs(a[0] - b[0])) <= 1e-12 * np.max(np.abs(a[0]))
     # explicit advection contracts more slowly
     assert b[2].sum() >= a[2].sum()
+
+
+@pytest.mark.parametrize("j", [1, 5])
+def test_exp1_field_on_constant_and_fourier_loads(j):
+    # |W| = c on every cell: each (I - d_xx) solve keeps the constant, u = a^2 c + b^2.
+    # |W| = c + d cos(theta (cell + 1/2)) (c > d): the cosine part follows the symbols
+    # of M + K and M, as in the Matern map with kappa = 1
+    m = make(n=128)
+    a, b, c, d = 1.3, -0.7, 0.4, 0.25
+    assert np.allclose(m.exp1_field(np.full(m.n, -c), a, b), a * a * c + b * b, rtol=1e-13)
+    th = 2 * math.pi * j / m.n
+    cells = c + d * np.cos(th * (np.arange(m.n) + 0.5))
+    Mh = m.h / 6 * (4 + 2 * math.cos(th))
+    Sh = Mh + (2 - 2 * math.cos(th)) / m.h
+    amp = d * m.h * math.cos(th / 2) * Mh ** 2 / Sh ** 3
+    ref = a * a * (c + amp * np.cos(th * np.arange(m.n))) + b * b
+    assert np.allclose(m.exp1_field(cells, a, b), ref, rtol=0, atol=1e-13)
+
+
+def test_exp1_prior_is_positive_and_reproducible():
+    # the solves of (I - d_xx) keep a nonnegative load nonnegative (an M-matrix inverse
+    # applied to nonnegative data), so u >= b^2 >= 0 for every member
+    m = make(n=128)
+    mm, u = m.prior_exp1(7, 6)
+    assert np.all(u >= 0.0)
+    mm2, u2 = m.prior_exp1(7, 3, particle0=3)
+    assert np.array_equal(u[3:], u2)
+    assert np.allclose(np.stack([m.u_from_m(x) for x in mm]), u, rtol=1e-12, atol=1e-13)
