@@ -657,6 +657,47 @@ def run_mala(args):
     return 0
 
 
+def run_exp1(args):
+    """--exp1: Exp 1 of Sec. 4.1 on the exp1_f64 workload (N = 150, Matern noise with eta = 1,
+    k = 3, observations every 5 steps at 64 of 128 nodes).  The truth and the particles start
+    from the Exp 1 initial ensemble (Eq. init_solve).  Two filters assimilate the same
+    observations: the bootstrap filter (each step one tempering stage with the whole step,
+    resampling, no jittering) and the filter with adaptive tempering (ESS >= N/2) and 5 PCN
+    jittering steps (delta = 0.15) per stage.  EMRE, RB and RES of the analysis ensemble
+    against the truth are taken every step; the line reports them at steps 1, 100, 500 and 1000
+    and their means over the last 100 steps."""
+    import torch
+    from workloads import get_config
+    from paper_2402_06927_gb300.api import SchModel
+    from paper_2402_06927_gb300 import twin
+    torch.cuda.set_device(0)
+    cfg = get_config("exp1_f64")
+    if args.exp1_sigma is not None:
+        cfg = cfg.replace(sigma=args.exp1_sigma)
+    g = SchModel.from_config(cfg)
+    T = args.da_steps
+    out = twin.exp1(g, cfg, T)
+    res = {}
+    for name in ("bootstrap", "tempering_jittering"):
+        sr = out[name]["series"]
+        res[name] = {
+            "assimilation_steps_per_s": T / out[name]["seconds"],
+            "mean_tempering_stages": statistics.mean(out[name]["stages"]),
+            "emre_rb_res_at": {str(k): sr[k - 1].tolist() for k in (1, 100, 500, 1000) if k <= T},
+            "emre_rb_res_mean_last_100": sr[max(0, T - 100):].mean(axis=0).tolist(),
+        }
+    line = {"metric": "assimilation steps/s", "value": res["tempering_jittering"]["assimilation_steps_per_s"],
+            "unit": "assimilation steps/s", "n_gpus": 1, "steps": T, "warmup": 0, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"Exp 1: exp1_f64 (N={cfg.N}, n={cfg.n}, Matern eta={cfg.eta} k={cfg.matern_k} "
+                                   f"kappa={cfg.kappa}, Ns={cfg.Ns}, M={cfg.M}, sigma={cfg.sigma:.4g}, delta=0.15, "
+                                   f"{cfg.n_jitter} jitter steps per stage), {T} assimilation steps",
+                       "initial_emre_rb_res": out["initial"].tolist()},
+            "filters": res}
+    print(json.dumps(line))
+    return 0
+
+
 def _event_time(fn, reps, flush=None):
     """Median device time of fn() over reps calls (CUDA events; L2 flushed before each if given)."""
     import torch
@@ -841,6 +882,11 @@ def main():
                     help="filter workload of the main run: cfg2_f32 (mode-expansion noise, the headline) "
                          "or cfg2m_f32 (the paper's Matern noise)")
     ap.add_argument("--mala-h", type=float, default=None, help="MALA step size h (--mala)")
+    ap.add_argument("--exp1", action="store_true",
+                    help="Exp 1: bootstrap vs tempering + jittering filters over --da-steps assimilation steps")
+    ap.add_argument("--da-steps", type=int, default=1000)
+    ap.add_argument("--exp1-sigma", type=float, default=None,
+                    help="observation error standard deviation of --exp1 (default 0.05)")
     ap.add_argument("--mala", action="store_true",
                     help="time the MALA jitter (moves/s) on the nudging workload")
     ap.add_argument("--filter-kernels", action="store_true",
@@ -872,6 +918,8 @@ def main():
         if args.steps == 100:
             args.steps = 10
         return run_adjoint(args)
+    if args.exp1:
+        return run_exp1(args)
     if args.mala:
         if args.steps == 100:
             args.steps = 5

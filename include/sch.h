@@ -320,7 +320,8 @@ int pf_mala_accept(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint
  * theta0 for k = 0, else from stage k-1), pf_resample_gated with counter
  * cycle * 1024 + first_stage + k, out-of-place row gathers of every state array
  * from bufs_a to bufs_b, then pf_jitter_dev (jitter counter stage counter x
- * n_jitter).  A stage reached at temperature one does nothing but copy the rows.
+ * n_jitter; n_jitter = 0 jitters nothing, which with a tiny ess_min is the bootstrap
+ * filter).  A stage reached at temperature one does nothing but copy the rows.
  * bufs_a[PF_STAGE_ARRAYS], bufs_b[PF_STAGE_ARRAYS]: device pointers in the order
  * PF_M_START, PF_M_END, PF_U_END, PF_DW, PF_NLL, PF_LOGG, PF_LAMBDA (the last may be
  * NULL in both); every stage gathers a -> b and swaps the roles, so after n_stages
@@ -446,6 +447,13 @@ int nn_adam_step(size_t count, float* params, const float* grads, float* m, floa
  * the next two normals; writes m and u (real [N][n]).  u_truth real [n]. */
 int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, double scale,
                      void* m, void* u, void* stream);
+
+/* The initial ensemble of Exp 1 (Sec. 4.1, Eq. init_solve): for member p, W_p is a DG0
+ * field with cell values sqrt(h) z (z keyed (seed, SCH_TAG_INIT, (b, 0, particle0 + p, 0))),
+ * U^{0,1} solves (U, v) + (U', v') = (|W_p|, v), U^{0,j+1} the same with right-hand side
+ * (U^{0,j}, v), and u = a_p^2 U^{0,3} + b_p^2 with a_p, b_p the next two normals.  The
+ * truth is a member drawn under another seed.  Writes m and u (real [N][n]). */
+int sch_prior_exp1(sch_ctx* ctx, int N, uint64_t seed, int particle0, void* m, void* u, void* stream);
 
 #ifdef __cplusplus
 }

@@ -301,6 +301,13 @@ class SchModel:
               "sch_prior_sample")
         return m, u
 
+    def prior_exp1(self, N: int, seed: int, particle0: int = 0):
+        """sch_prior_exp1: members particle0 .. particle0 + N - 1 of the Exp 1 initial ensemble."""
+        m = torch.empty((N, self.n), dtype=self.dtype, device="cuda")
+        u = torch.empty_like(m)
+        check(lib().sch_prior_exp1(self._h, N, seed, particle0, _ptr(m), _ptr(u), _stream()), "sch_prior_exp1")
+        return m, u
+
 
 # ---------------------------------------------------------------------- #
 # filter entry points that need no model context

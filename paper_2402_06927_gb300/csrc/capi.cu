@@ -606,7 +606,7 @@ int pf_gated_stages(sch_ctx* ctx, int N, int nsteps, int n_stages, int first_sta
                     double rho, int n_jitter, uint64_t seed, uint64_t cycle, const void* y, void* const* bufs_a,
                     void* const* bufs_b, const double* theta0, double* wbar, int32_t* idx, double* touts,
                     int32_t* accepts, int32_t* iters, int32_t* status, void* const* events, void* stream) {
-    if (!ctx || N <= 0 || nsteps <= 0 || n_stages < 1 || first_stage < 0 || n_jitter < 1) return SCH_ERR_ARG;
+    if (!ctx || N <= 0 || nsteps <= 0 || n_stages < 1 || first_stage < 0 || n_jitter < 0) return SCH_ERR_ARG;
     if (!y || !bufs_a || !bufs_b || !theta0 || !wbar || !idx || !touts) return SCH_ERR_ARG;
     for (int a = 0; a < PF_STAGE_ARRAYS - 1; ++a)
         if (!bufs_a[a] || !bufs_b[a]) return SCH_ERR_ARG;
@@ -700,9 +700,19 @@ int sch_prior_sample(sch_ctx* ctx, int N, const void* u_truth, uint64_t seed, do
     if (!u_truth || !m || !u) return SCH_ERR_ARG;
     if (ctx->p.dtype == SCH_F32)
         return launch_prior<float, 8>(ctx->af, (const float*)u_truth, seed, (float)scale, (float*)m, (float*)u,
-                                      N, S(stream));
+                                      N, S(stream), 0, 0);
     return launch_prior<double, 4>(ctx->ad, (const double*)u_truth, seed, scale, (double*)m, (double*)u, N,
-                                   S(stream));
+                                   S(stream), 0, 0);
+}
+
+int sch_prior_exp1(sch_ctx* ctx, int N, uint64_t seed, int particle0, void* m, void* u, void* stream) {
+    if (!ctx || N < 0 || particle0 < 0) return SCH_ERR_ARG;
+    if (N == 0) return SCH_OK;
+    if (!m || !u) return SCH_ERR_ARG;
+    if (ctx->p.dtype == SCH_F32)
+        return launch_prior<float, 8>(ctx->af, nullptr, seed, 0.0f, (float*)m, (float*)u, N, S(stream), 1,
+                                      particle0);
+    return launch_prior<double, 4>(ctx->ad, nullptr, seed, 0.0, (double*)m, (double*)u, N, S(stream), 1, particle0);
 }
 
 static size_t adjoint_ws_per(const sch_ctx* ctx, int nsteps, int ckpt) {

@@ -183,7 +183,7 @@ template <typename R, int C>
 int launch_helm(const ModelArgs<R>& A, const R* in, R* out, int mode, int N, cudaStream_t st);
 template <typename R, int C>
 int launch_prior(const ModelArgs<R>& A, const R* u_truth, uint64_t seed, R scale, R* m, R* u, int N,
-                 cudaStream_t st);
+                 cudaStream_t st, int mode, int particle0);
 template <typename R, int C>
 size_t jitter_smem(int tp, int Ns, int K);
 // window and jitter kernels with the Matern noise (sch_matern_{f32,f64}.cu): the

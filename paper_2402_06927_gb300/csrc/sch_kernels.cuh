@@ -1009,11 +1009,14 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) helm_kernel(ModelArgs<R>
     for (int i = 0; i < C; ++i) out[(size_t)p * A.n + i0 + i] = x[i];
 }
 
-// Prior ensemble: u = u_truth + scale (a_p S^3 W_p + b_p), S the P1 solve of
-// (U, v) + (U_x, v_x) = (f, v); then m = M^{-1} H u.
+// Prior ensemble, S the P1 solve of (U, v) + (U_x, v_x) = (f, v), then m = M^{-1} H u:
+//   mode 0: u = u_truth + scale (a_p S^3 W_p + b_p);
+//   mode 1: u = a_p^2 S^3 |W_p| + b_p^2 (the Exp 1 ensemble of Eq. init_solve).
+// Member p uses Philox counter particle0 + p.
 template <typename R, int C, int TP>
 __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) prior_kernel(ModelArgs<R> A, const R* u_truth, uint64_t seed,
-                                                                 R scale, R* m_out, R* u_out) {
+                                                                 R scale, R* m_out, R* u_out, int mode,
+                                                                 int particle0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     const int p = blockIdx.x;
@@ -1024,15 +1027,16 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) prior_kernel(ModelArgs<R
     for (int i = 0; i < C; ++i) {
         const int e = i0 + i;
         R z[4];
-        normal4<R>(seed, SCH_TAG_INIT, (uint64_t)(e >> 2), 0, (uint64_t)p, 0, z);
+        normal4<R>(seed, SCH_TAG_INIT, (uint64_t)(e >> 2), 0, (uint64_t)(particle0 + p), 0, z);
         cell[i] = (R)sqrt((double)h) * z[e & 3];
+        if (mode == 1) cell[i] = fabs(cell[i]);
     }
     R ab[2];
     {
         const int k0 = A.n;
         R z[4], z2[4];
-        normal4<R>(seed, SCH_TAG_INIT, (uint64_t)(k0 >> 2), 0, (uint64_t)p, 0, z);
-        normal4<R>(seed, SCH_TAG_INIT, (uint64_t)((k0 + 1) >> 2), 0, (uint64_t)p, 0, z2);
+        normal4<R>(seed, SCH_TAG_INIT, (uint64_t)(k0 >> 2), 0, (uint64_t)(particle0 + p), 0, z);
+        normal4<R>(seed, SCH_TAG_INIT, (uint64_t)((k0 + 1) >> 2), 0, (uint64_t)(particle0 + p), 0, z2);
         ab[0] = z[k0 & 3];
         ab[1] = z2[(k0 + 1) & 3];
     }
@@ -1051,7 +1055,8 @@ __global__ void __launch_bounds__(TP, Occ<R, TP>::minb) prior_kernel(ModelArgs<R
     }
     R u[C], up, un;
 #pragma unroll
-    for (int i = 0; i < C; ++i) u[i] = u_truth[i0 + i] + scale * (ab[0] * U[i] + ab[1]);
+    for (int i = 0; i < C; ++i)
+        u[i] = (mode == 1) ? ab[0] * ab[0] * U[i] + ab[1] * ab[1] : u_truth[i0 + i] + scale * (ab[0] * U[i] + ab[1]);
     chunk_halo<R, C, TP>(u, up, un, sh);
 #pragma unroll
     for (int i = 0; i < C; ++i) {
@@ -1101,10 +1106,10 @@ struct Launch {
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
     static int prior(const ModelArgs<R>& A, const R* ut, uint64_t seed, R scale, R* m, R* u, int N,
-                     cudaStream_t st) {
+                     cudaStream_t st, int mode, int particle0) {
         const size_t sm = smem(0, A.K, 0);
         prep(prior_kernel<R, C, TP>, sm);
-        prior_kernel<R, C, TP><<<N, TP, sm, st>>>(A, ut, seed, scale, m, u);
+        prior_kernel<R, C, TP><<<N, TP, sm, st>>>(A, ut, seed, scale, m, u, mode, particle0);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
 };

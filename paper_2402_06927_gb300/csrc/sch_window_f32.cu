@@ -31,8 +31,8 @@ int launch_helm<float, 8>(const ModelArgs<float>& A, const float* in, float* out
 }
 template <>
 int launch_prior<float, 8>(const ModelArgs<float>& A, const float* ut, uint64_t seed, float scale, float* m, float* u,
-                            int N, cudaStream_t st) {
-    SCH_TP_SWITCH(A.n / 8, prior(A, ut, seed, scale, m, u, N, st))
+                            int N, cudaStream_t st, int mode, int particle0) {
+    SCH_TP_SWITCH(A.n / 8, prior(A, ut, seed, scale, m, u, N, st, mode, particle0))
 }
 
 #define SCH_TP_SMEM(tp, bufs)                                          \

@@ -31,8 +31,8 @@ int launch_helm<double, 4>(const ModelArgs<double>& A, const double* in, double*
 }
 template <>
 int launch_prior<double, 4>(const ModelArgs<double>& A, const double* ut, uint64_t seed, double scale, double* m, double* u,
-                            int N, cudaStream_t st) {
-    SCH_TP_SWITCH(A.n / 4, prior(A, ut, seed, scale, m, u, N, st))
+                            int N, cudaStream_t st, int mode, int particle0) {
+    SCH_TP_SWITCH(A.n / 4, prior(A, ut, seed, scale, m, u, N, st, mode, particle0))
 }
 
 #define SCH_TP_SMEM(tp, bufs)                                          \

@@ -193,6 +193,24 @@ def test_prior_sample_matches_oracle():
     assert rel_err(m.cpu().numpy(), m_ref) < 1e-10
 
 
+@pytest.mark.parametrize("name", ["exp1_f64", "cfg2m_f32"])
+def test_prior_exp1_matches_oracle(name):
+    # the Exp 1 initial ensemble (Eq. init_solve), members 3 .. 6 of a seeded draw
+    cfg = get_config(name)
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    m_ref, u_ref = om.prior_exp1(11, 4, particle0=3)
+    m, u = g.prior_exp1(4, 11, particle0=3)
+    tol = 1e-11 if cfg.dtype == "f64" else 1e-5
+    assert rel_err(u.cpu().numpy(), u_ref) < tol
+    # m = M^-1 (M + alpha^2 K) u amplifies the highest mesh mode by 1 + 12 alpha^2 / h^2
+    # (about 7,900 at n = 1024): in FP32 the bound is a few float epsilons times that
+    cond = 1 + 12 * cfg.alpha ** 2 / cfg.h ** 2
+    mtol = 10 * tol if cfg.dtype == "f64" else 4 * 2.0 ** -24 * cond
+    assert rel_err(m.cpu().numpy(), m_ref) < mtol
+    assert np.all(u.cpu().numpy() >= 0.0)
+
+
 def test_synth_obs_and_diagnostics():
     cfg = get_config("cfg1_f64")
     g = gpu_model(cfg)

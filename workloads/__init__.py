@@ -24,6 +24,14 @@ Workloads (all synthetic twin experiments; the paper uses no public dataset):
   instead of the mode expansion; eta = 0.2 puts the per-step noise at the
   size of the mode-expansion workloads' (eta = 1 makes it about five times
   the transport term u dt at dt = 0.025).
+* ``exp1_f64``  Exp 1 of Sec. 4.1: N=150 particles, the Matern noise with the
+  paper's eta = 1 and k = 3 (kappa = 1), observations every 5 steps at M=64 of
+  n=128 nodes (the paper's 81 points on 100 cells; 100 is not a compiled mesh
+  size) with sigma = 0.05, delta = 0.15, 5 jitter steps per tempering stage,
+  1000 assimilation steps, FP64.  Truth and particles start from the initial
+  ensemble of Eq. init_solve.  The paper's "N(0, 0.5)" errors, read as variance
+  0.5, give 1.9 tempering stages per step where the paper reports 7 to 10;
+  sigma = 0.05 gives 6.9.
 
 The initial truth is u0(x) = 0.2 sech(x-27) + 0.5 sech(x-13) on [0, 40).
 """
@@ -114,6 +122,8 @@ CONFIGS = {
                        sigma=0.02, N=8192, cycles=50, n_jitter=10, rho=0.9999,
                        dtype="f32", tol=1e-6, max_iter=40),
     "cfg1m_f64": Config(name="cfg1m_f64", noise="matern", kappa=1.0, eta=0.2),
+    "exp1_f64": Config(name="exp1_f64", n=128, M=64, sigma=0.05, N=150, cycles=1000,
+                       noise="matern", kappa=1.0, eta=1.0),
     "cfg2m_f32": Config(name="cfg2m_f32", n=1024, K=8, amp_rule="inv_j", Ns=10, M=64,
                         sigma=0.05, N=1024, n_jitter=10, rho=0.9999, dtype="f32",
                         tol=1e-6, max_iter=40, noise="matern", kappa=1.0, eta=0.2),
