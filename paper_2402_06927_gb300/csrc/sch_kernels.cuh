@@ -570,6 +570,25 @@ __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, 
     f.un = uin;
 }
 
+// Stop test of the explicit-advection Picard iteration after a step of size dm
+// (max-norm of the change of the iterate) against lim = tol max(1, max|m|).  It
+// stops when dm <= lim.  In FP32 it also stops when the contraction seen over the
+// last two steps (dm_prev is infinite before the second), rho = dm / dm_prev < 1/2,
+// puts the error of the current iterate,
+// at most about rho dm / (1 - rho), below lim: that saves the iteration whose only
+// purpose would be to confirm it (the iteration contracts by about 0.05 per
+// iteration, so the plain test stops about one iteration past the tolerance, with
+// the error already near float rounding).  FP64 keeps the plain test.
+template <typename R>
+__device__ __forceinline__ bool ea_converged(R dm, R dm_prev, R lim) {
+    if (dm <= lim) return true;
+    if constexpr (sizeof(R) == 4) {
+        // rho < 1/2 and rho dm <= lim (1 - rho), multiplied through by dm_prev > 0
+        return dm_prev < R(INFINITY) && R(2) * dm < dm_prev && dm * dm <= lim * (dm_prev - dm);
+    }
+    return false;
+}
+
 // --------------------------------------------------------------------------
 // One implicit-midpoint step by explicit-advection Picard iteration:
 //   (M + mu dt/2 K) m^{p+1} = (M - mu dt/2 K) m0 - A(mbar^p, dv^p),
@@ -606,6 +625,7 @@ __device__ __forceinline__ void sch_step_ea(const ModelArgs<R>& A, Shm<R, TP>* s
     for (int i = 0; i < C; ++i) { mi[i] = f.m[i]; ui[i] = f.u[i]; }
     R mip = f.mp, min_ = f.mn, uip = f.up, uin = f.un;
     const R m0p = f.mp, m0n = f.mn;
+    R dm_prev = R(INFINITY);   // warp 0: the step size of the previous test
 
     for (int it = 1;; ++it) {
         // local phase: right-hand side and chunk sweep of M + mu dt/2 K
@@ -663,8 +683,9 @@ __device__ __forceinline__ void sch_step_ea(const ModelArgs<R>& A, Shm<R, TP>* s
                 dm = warp_max(dm);
                 mm = warp_max(mm);
                 if (!(dm < R(INFINITY)) || !(mm < R(INFINITY))) fl = FLAG_STOP | FLAG_NONFINITE;
-                else if (dm <= A.tol * fmax(R(1), mm)) fl = FLAG_STOP | FLAG_CONVERGED;
+                else if (ea_converged(dm, dm_prev, A.tol * fmax(R(1), mm))) fl = FLAG_STOP | FLAG_CONVERGED;
                 else if (it > A.max_iter) fl = FLAG_STOP | FLAG_NOCONV;
+                dm_prev = dm;
             }
             if (!(fl & FLAG_STOP)) {
                 R pdr[RR], der[RR], hpr[RR], hdr[RR], Er[RR], Fr[RR];

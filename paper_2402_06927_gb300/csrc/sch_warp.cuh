@@ -21,8 +21,9 @@
 //         = R0_i - A(mbar, dv)_i    (the P1 advection operator)
 //   (M + mu dt/2 K) m_new = rhs            partitioned solve, reduced rows
 //   (6/h)(M + alpha^2 K) u_new = m_{i-1} + 4 m_i + m_{i+1}    likewise
-// followed by the stop test max|m_new - m_it| <= tol max(1, max|m_new|) on
-// the whole particle (two warp reductions).
+// followed by the stop test on the whole particle (two warp reductions):
+// max|m_new - m_it| <= tol max(1, max|m_new|), or the contraction estimate of
+// ea_converged.
 #pragma once
 
 #include "sch_kernels.cuh"
@@ -275,6 +276,7 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
 #pragma unroll
         for (int i = 0; i < CS; ++i) mi[p][i] = m[p][i];
     const float2 dt8 = f2b(A.dt8);
+    float dm_prev = INFINITY;
     for (int it = 1;; ++it) {
         // rhs_i = R0_i + w_{i-1} g_{i-1} - w_{i+1} g_i,  w = W0 + dt/8 u_it,  g_i = mb2_i + mb2_{i+1}
         float2 x[P][CS];
@@ -342,7 +344,8 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
             flags |= SCH_DEV_NONFINITE;
             break;
         }
-        if (dm <= A.tol * fmaxf(1.f, mm)) break;
+        if (ea_converged(dm, dm_prev, A.tol * fmaxf(1.f, mm))) break;
+        dm_prev = dm;
         if (it >= A.max_iter) {
             flags |= SCH_DEV_NOCONVERGE;
             break;
