@@ -130,3 +130,28 @@ def test_matern_cycle_matches_oracle():
         assert abs(a.dtheta - b["dtheta"]) <= 1e-9 * b["dtheta"]
     assert rel_err(f.u_end.cpu().numpy(), ref["u_end"]) < 1e-8
     assert rel_err(f.dW.cpu().numpy(), ref["dW"]) < 1e-8
+
+
+def test_matern_full_size_sampled():
+    # the Matern bench configuration (n = 1024, N = 1024, Ns = 10, FP32): every particle is
+    # propagated in one launch, as the bench runs it, and three sampled particles are
+    # recomputed by the oracle
+    cfg = get_config("cfg2m_f32")
+    g = gpu_model(cfg)
+    N = cfg.N
+    u0 = random_state(cfg, N, 41)
+    m0 = g.m_from_u(tdev(u0, g.dtype))
+    dW = g.draw_increments(N, cfg.Ns, 7, ORNG.TAG_PRIOR_DW, 0)
+    y = random_obs(cfg, 4)
+    out = g.ensemble_step(m0, dW, None, tdev(y, g.dtype))
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    om = oracle_model(cfg)
+    dWh = dW.double().cpu().numpy()
+    m0h = m0.double().cpu().numpy()
+    for p in (0, 517, N - 1):
+        mref, uref, _, ok = om.window(m0h[p], dWh[p])
+        assert ok
+        assert rel_err(out["m"][p].cpu().numpy(), mref) < 1e-4
+        assert rel_err(out["u"][p].cpu().numpy(), uref) < 1e-4
+        assert abs(out["nll"][p].item() - OF.nll(uref[None], y, cfg.sigma)[0]) < 1e-3 * max(1.0, out["nll"][p].item())
