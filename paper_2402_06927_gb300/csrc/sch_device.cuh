@@ -57,14 +57,28 @@ __device__ __forceinline__ float u53_to_float(uint64_t v) {
     return fmaf(hi, 0x1.0p-32f, lo * 0x1.0p-53f);
 }
 
+// The FP32 transform keeps to the FP32 pipes.  r^2 = -2 ln u1: for u1 <= 15/16 from the
+// __logf intrinsic (absolute error below 2^-21.4 on [1/2, 2], so below 6e-6 relative
+// here); nearer one, where that bound is large against the value, from the series
+// -ln(1 - x) = x + x^2/2 + x^3/3 + x^4/4 + x^5/5 on x = 1 - u1, which the integer gives
+// exactly (truncation below 2e-7 relative for x < 1/16).  The angle 2 pi u2 is taken
+// as theta + pi with theta = 2 pi (u2 - 1/2) in [-pi, pi), where __sincosf is accurate
+// to 2^-21.4, and the signs flipped back.  |z| is within about 4e-6 of the FP64 transform.
 __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, float& z0, float& z1) {
-    const float u1 = u53_to_float((a >> 11) + 1ull);
-    const float u2 = u53_to_float(b >> 11);
-    const float r = sqrtf(-2.0f * logf(u1));
+    const uint64_t v = (a >> 11) + 1ull;           // u1 = v 2^-53 in (0, 1]
+    const uint64_t w = (1ull << 53) - v;           // 1 - u1 = w 2^-53
+    float r2;
+    if (w < (1ull << 49)) {
+        const float x = u53_to_float(w);
+        r2 = 2.0f * x * (1.0f + x * (0.5f + x * (1.0f / 3.0f + x * (0.25f + x * 0.2f))));
+    } else {
+        r2 = -2.0f * __logf(u53_to_float(v));
+    }
+    const float r = sqrtf(r2);
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(6.28318531f * (u53_to_float(b >> 11) - 0.5f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 
 // Four normals of block (blk, c1, c2, c3) under key (seed, tag).
