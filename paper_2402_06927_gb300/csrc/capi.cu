@@ -330,6 +330,16 @@ void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
     rtab_host(th, rows, q);
     cast_rtab(q, W.rhel);
     wtab_cast(th, q, CS, W.hel);
+    if (p.noise == SCH_NOISE_MATERN) {
+        // the Matern operator scaled by 6/h like the Helmholtz one, and the weights likewise
+        const double k2 = 1.0 / (p.kappa * p.kappa);
+        HTab tg;
+        ctab_host((h / 6.0 - k2 / h) * 6.0 / h, (2.0 * h / 3.0 + 2.0 * k2 / h) * 6.0 / h, CS, tg);
+        rtab_host(tg, rows, q);
+        cast_rtab(q, W.rmat);
+        wtab_cast(tg, q, CS, W.mat);
+        W.mzw = (float)(p.eta * sqrt(h) / 8.0 * 6.0 / h);
+    }
 }
 
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
@@ -360,12 +370,13 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     if (matern) {
         if (!(p.kappa > 0) || !(p.eta >= 0) || p.matern_k < 1 || p.matern_k > 8) return SCH_ERR_ARG;
         if (solver != (p.dtype == SCH_F32 ? SCH_SOLVER_EA : SCH_SOLVER_LI)) return SCH_ERR_UNSUPPORTED;
-        if (p.layout == SCH_LAYOUT_WARP) return SCH_ERR_UNSUPPORTED;
     }
-    const bool warp_fits = !matern && p.dtype == SCH_F32 && solver == SCH_SOLVER_EA &&
-                           (p.n == 256 || p.n == 512 || p.n == 1024);
+    const bool warp_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && (p.n == 256 || p.n == 512 || p.n == 1024);
     if (p.layout == SCH_LAYOUT_WARP && !warp_fits) return SCH_ERR_UNSUPPORTED;
-    const bool warp_ok = warp_fits && p.layout != SCH_LAYOUT_CTA;
+    // the Matern noise runs in the CTA layout unless the warp layout is asked for: its
+    // jitter draws n normals per step, which a warp per particle generates at a quarter of
+    // the CTA layout's occupancy (20.7M against 40.0M particle-timesteps/s at n = 1024)
+    const bool warp_ok = warp_fits && (matern ? p.layout == SCH_LAYOUT_WARP : p.layout != SCH_LAYOUT_CTA);
     sch_ctx* c = (sch_ctx*)calloc(1, sizeof(sch_ctx));
     if (!c) return SCH_ERR_ARG;
     c->p = p;
@@ -449,7 +460,9 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
     if (ctx->p.dtype == SCH_F32) {
         WindowIO<float> io{nsteps, (const float*)m, (float*)m_out, (float*)u_out, (const float*)dW,
                            (const float*)lambda, (const float*)y, nll, logG, iters, status};
-        if (ctx->matern) return launch_window_matern<float, 8>(ctx->af, io, N, S(stream));
+        if (ctx->matern)
+            return ctx->wcs ? launch_wwindow_matern(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream))
+                            : launch_window_matern<float, 8>(ctx->af, io, N, S(stream));
         if (ctx->wcs) return launch_wwindow(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_window<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_window<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
@@ -570,7 +583,9 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
         JitterIO<float> io{nsteps, n_iter, 0, theta, tstate, (float)rho, (float)sq, seed, ctr,
                            (const float*)m_start, (float*)dW, (const float*)lambda, (const float*)y, nll, logG,
                            (float*)m_end, (float*)u_end, accepts, iters, status};
-        if (ctx->matern) return launch_jitter_matern<float, 8>(ctx->af, io, N, S(stream));
+        if (ctx->matern)
+            return ctx->wcs ? launch_wjitter_matern(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream))
+                            : launch_jitter_matern<float, 8>(ctx->af, io, N, S(stream));
         if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));

@@ -90,6 +90,13 @@ __device__ __forceinline__ void normal4(uint64_t seed, uint64_t tag, uint64_t bl
     box_muller(r.v2, r.v3, z[2], z[3]);
 }
 
+// PCN proposal rho dW + sqrt(1 - rho^2) sqrt(dt) z, rounded the same way wherever it
+// is formed (a window's noise and the stored accepted proposal agree bit for bit)
+template <typename R>
+__device__ __forceinline__ R pcn_value(R rho, R cur, R sq, R z) {
+    return fma(rho, cur, sq * z);
+}
+
 // Uniform in (0, 1] from word 0 of block (0, 0, c2, c3).
 __device__ __forceinline__ double uniform_open0(uint64_t seed, uint64_t tag, uint64_t c2, uint64_t c3) {
     const U64x4 r = philox4x64(0, 0, c2, c3, seed, tag);

@@ -96,6 +96,9 @@ struct WTab {
 struct WArgs {
     WTab pic, hel;           // M + mu dt/2 K ;  (6/h)(M + alpha^2 K)
     RTab<float> rpic, rhel;  // their 64-row reduced systems (two rows per lane)
+    WTab mat;                // Matern noise: (6/h)(M + kappa^-2 K)
+    RTab<float> rmat;
+    float mzw;               // Matern cell weight scale (6/h) eta sqrt(h) / 8
 };
 
 template <typename R>
@@ -186,6 +189,11 @@ int launch_prior(const ModelArgs<R>& A, const R* u_truth, uint64_t seed, R scale
                  cudaStream_t st, int mode, int particle0);
 template <typename R, int C>
 size_t jitter_smem(int tp, int Ns, int K);
+// window and jitter kernels with the Matern noise, warp layout (sch_matern_warp.cu)
+int launch_wwindow_matern(int cs, const ModelArgs<float>& A, const WArgs& W, const WindowIO<float>& io, int N,
+                          cudaStream_t st);
+int launch_wjitter_matern(int cs, const ModelArgs<float>& A, const WArgs& W, const JitterIO<float>& io, int N,
+                          cudaStream_t st);
 // window and jitter kernels with the Matern noise (sch_matern_{f32,f64}.cu): the
 // default solver of each precision only
 template <typename R, int C>

@@ -15,13 +15,6 @@
 
 namespace sch {
 
-// PCN proposal rho dW + sqrt(1 - rho^2) sqrt(dt) z, rounded the same way wherever it
-// is formed (the window's noise and the stored accepted proposal agree bit for bit)
-template <typename R>
-__device__ __forceinline__ R pcn_value(R rho, R cur, R sq, R z) {
-    return fma(rho, cur, sq * z);
-}
-
 // normals of cells [i0, i0 + C) of step s under (seed, tag) at particle counter pc
 template <typename R, int C>
 __device__ __forceinline__ void cell_normals(uint64_t seed, int i0, int s, uint64_t pc, uint64_t ctr, R (&z)[C]) {

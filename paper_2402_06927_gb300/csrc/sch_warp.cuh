@@ -246,17 +246,16 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* w
     }
 }
 
-// One implicit-midpoint step of this warp's particle: (m, u) in/out.
+// One implicit-midpoint step of this warp's particle: (m, u) in/out, W0 holding the
+// step's dU/4 at the lane's nodes on entry.
 // R0sm: this warp's [P][CS][32] float2 scratch for R0 = (M - mu dt/2 K) m0.
 template <int CS, int P>
-__device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
-                                      float2 (&u)[P][CS], float2* R0sm, const float* wq, const float2 (&s1)[P],
-                                      const float2 (&c1)[P], int& iters, int& flags) {
+__device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
+                                           float2 (&u)[P][CS], float2* R0sm, float2 (&W0)[P][CS], int& iters,
+                                           int& flags) {
     const int lane = threadIdx.x & 31;
     // W0 = dt/8 u0 + dU/4 (registers) and R0 (shared memory), fixed for the step
-    float2 W0[P][CS];
     {
-        wnoise<CS, P>(A, wq, s1, c1, W0);
         const float2 dt8 = f2b(A.dt8);
         float2 lo, hi;
         whalo<CS, P>(m, lo, hi);
@@ -355,6 +354,16 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
     for (int p = 0; p < P; ++p)
 #pragma unroll
         for (int i = 0; i < CS; ++i) m[p][i] = mi[p][i];
+}
+
+// One step with the mode-expansion noise of the step's K weights wq.
+template <int CS, int P>
+__device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
+                                      float2 (&u)[P][CS], float2* R0sm, const float* wq, const float2 (&s1)[P],
+                                      const float2 (&c1)[P], int& iters, int& flags) {
+    float2 W0[P][CS];
+    wnoise<CS, P>(A, wq, s1, c1, W0);
+    wstep_core<CS, P>(A, W, m, u, R0sm, W0, iters, flags);
 }
 
 // this lane's LN = 2 P CS nodes of a particle row <-> the paired registers:

@@ -104,9 +104,10 @@ def test_host_argument_errors_need_no_gpu(lib):
                                    ({"noise": 2}, -1), ({"noise": 1, "kappa": 0.0}, -1),
                                    ({"noise": 1, "eta": -1.0}, -1), ({"noise": 1, "matern_k": 0}, -1),
                                    ({"noise": 1, "matern_k": 9}, -1),
-                                   # Matern noise: CTA layout and each precision's default solver only
-                                   ({"noise": 1, "dtype": 1, "layout": 2}, -6), ({"noise": 1, "solver": 2}, -6),
-                                   ({"noise": 1, "dtype": 1, "solver": 1}, -6)])
+                                   # Matern noise: each precision's default solver only; the warp
+                                   # layout where it fits (FP32, n = 256, 512 or 1024)
+                                   ({"noise": 1, "dtype": 1, "layout": 2}, 0), ({"noise": 1, "layout": 2}, -6),
+                                   ({"noise": 1, "solver": 2}, -6), ({"noise": 1, "dtype": 1, "solver": 1}, -6)])
 def test_create_validates_matern(lib, kw, rc):
     base = {"kappa": 1.0, "eta": 0.2, "matern_k": 3}
     base.update(kw)
@@ -115,9 +116,9 @@ def test_create_validates_matern(lib, kw, rc):
     got = lib.sch_create(ct.byref(p), ct.byref(h))
     assert got == rc
     if got == 0:
-        # one Brownian motion per cell, CTA layout even where the warp layout would fit
+        # one Brownian motion per cell; the CTA layout unless the warp layout is asked for
         assert lib.sch_noise_dim(h) == p.n
-        assert lib.sch_layout(h) == 1
+        assert lib.sch_layout(h) == (2 if p.layout == 2 else 1)
         # entry points built on the adjoint take the mode expansion only
         assert lib.sch_adjoint_window(h, 1, 5, 1, None, None, None, None, None, None, None, None, None, None, None,
                                       0, None) == -6

@@ -155,3 +155,31 @@ def test_matern_full_size_sampled():
         assert rel_err(out["m"][p].cpu().numpy(), mref) < 1e-4
         assert rel_err(out["u"][p].cpu().numpy(), uref) < 1e-4
         assert abs(out["nll"][p].item() - OF.nll(uref[None], y, cfg.sigma)[0]) < 1e-3 * max(1.0, out["nll"][p].item())
+
+
+def test_matern_layouts_agree_at_full_ensemble_size():
+    # the warp-per-particle and CTA Matern kernels on the same 1024-particle window and
+    # jitter call: equal to FP32 rounding, with the same jitter decisions
+    cfg = get_config("cfg2m_f32")
+    gw, gc = gpu_model(cfg, layout="warp"), gpu_model(cfg, layout="cta")
+    assert gw.layout == "warp" and gc.layout == "cta"
+    N = cfg.N
+    u0 = torch.tensor(random_state(cfg, 1, 3)[0], dtype=torch.float32, device="cuda")
+    m0, _ = gw.prior_sample(N, u0, 5, 0.05)
+    dW = gw.draw_increments(N, cfg.Ns, 9, ORNG.TAG_PRIOR_DW, 0)
+    lam = torch.tensor(random_drift(cfg, N, 6, scale=0.2), dtype=torch.float32, device="cuda")
+    y = gw.synth_obs(u0, 2, 1)
+    outs = []
+    for g in (gw, gc):
+        d = dW.clone()
+        st = g.ensemble_step(m0, d, lam, y)
+        acc, _, status = g.jitter(m0, d, lam, y, st["nll"], st["logG"], st["m"], st["u"], 0.5, cfg.rho, 3, 11, 7)
+        torch.cuda.synchronize()
+        assert torch.all(st["status"] == 0) and torch.all(status == 0)
+        outs.append((st, acc, d))
+    (a, acc_a, d_a), (b, acc_b, d_b) = outs
+    scale = b["u"].abs().max().item()
+    assert (a["u"] - b["u"]).abs().max().item() < 1e-4 * scale
+    assert (acc_a != acc_b).float().mean().item() < 0.02     # decisions differ only at coin flips
+    same = acc_a == acc_b
+    assert (d_a[same] - d_b[same]).abs().max().item() < 1e-4
