@@ -139,12 +139,23 @@ class EnsembleFilter:
         (e.g. the ones revealed by pf_nudge); otherwise they are drawn from the prior."""
         m = self.model
         st = CycleStats()
+        if not (y.is_cuda and y.dtype == m.dtype and y.numel() == m.M and y.is_contiguous()):
+            raise ValueError(f"y must be a contiguous CUDA {m.dtype} vector of {m.M} observations")
+        # the forecast through the C ABI directly: the filter's own buffers have the shapes and
+        # types the library expects, so the argument checks of SchModel are not repeated (they
+        # cost about 20 us of host time per call, while the GPU waits for the cycle's first work)
+        L = _lib.lib()
+        stream = torch.cuda.current_stream().cuda_stream
         if dW is None:
-            m.draw_increments(self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, out=self.dW)
+            _lib.check(L.sch_draw_increments(m.handle, self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, 0,
+                                             self.dW.data_ptr(), stream), "sch_draw_increments")
         else:
             self.dW.copy_(dW)
-        m.ensemble_step(self.m_start, self.dW, self.lam, y, m_out=self.m_end, u_out=self.u_end,
-                        nll=self.nll, logG=self.logG, status=self.status, want_iters=False)
+        _lib.check(L.sch_ensemble_step(m.handle, self.N, self.Ns, self.m_start.data_ptr(), self.m_end.data_ptr(),
+                                       self.u_end.data_ptr(), self.dW.data_ptr(),
+                                       None if self.lam is None else self.lam.data_ptr(), y.data_ptr(),
+                                       self.nll.data_ptr(), self.logG.data_ptr(), None, self.status.data_ptr(),
+                                       stream), "sch_ensemble_step")
         st.forward_steps += self.N * self.Ns
         st.launches += 2
         st.ess0 = None
@@ -190,8 +201,9 @@ class EnsembleFilter:
                 timer.iters.extend(iters[k] for k in range(S))
             self.touts_host.copy_(self.touts, non_blocking=True)
             torch.cuda.current_stream().synchronize()
+            touts = self.touts_host.tolist()
             for k in range(S):
-                d, e, theta_new, e_rest, active = (float(v) for v in self.touts_host[k])
+                d, e, theta_new, e_rest, active = touts[k]
                 if active == 0.0:
                     if timer is not None:
                         del timer.pairs[n0 + k:], timer.iters[n0 + k:]
@@ -206,7 +218,7 @@ class EnsembleFilter:
             pf_temper(self.nll, self.logG, theta, self.ess_min, wbar=self.wbar, out=self.tout, mode=self.temper_mode)
             self.tout_host.copy_(self.tout, non_blocking=True)
             torch.cuda.current_stream().synchronize()
-            d, e, theta_new = (float(v) for v in self.tout_host[:3])
+            d, e, theta_new = self.tout_host[:3].tolist()
             stage_ctr = cycle * 1024 + k
             self._resample(stage_ctr)
             theta = theta_new
