@@ -405,7 +405,7 @@ int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gto
  * pf_nudge.  Any drift keeps the particle weights consistent through the
  * Girsanov factor (Eq. girsanov DG approx), so the network only changes how
  * close the proposal lands to the observations; the optimiser stays as the
- * fallback and the judge.
+ * fallback and as the standard the network is measured against.
  *   x0 = (u_start, (y - u_start(x_obs)) / sigma at the observation nodes)   [2][n]
  *   4 x (circular convolution, kernel 5, stride 2, C channels, ReLU)    -> [C][n/16]
  *   F[c][2(j-1)], F[c][2j-1] = (1/P) sum_q h[c][q] sin, cos(2 pi j q / P), P = n/16
