@@ -97,6 +97,24 @@ def test_host_argument_errors_need_no_gpu(lib):
     assert lib.pf_gather_rows(4, ct.c_void_p(16), ct.c_void_p(16), ct.c_void_p(32), 6, None) == -1
     assert lib.pf_jitter(h, 4, 5, 1, 0.5, 1.5, 0, 0, *([None] * 12)) == -1
     assert lib.pf_resample_workspace_bytes(10, 48) == 480
+    # MALA: step size, temperature and pointers checked on the host; an empty ensemble is a no-op
+    P16 = ct.c_void_p(16)
+    assert lib.pf_mala_propose(h, 4, 5, 0.5, 0.0, 0, 0, 0, P16, None, P16, P16, None) == -1
+    assert lib.pf_mala_propose(h, 4, 5, 1.5, 0.1, 0, 0, 0, P16, None, P16, P16, None) == -1
+    assert lib.pf_mala_propose(h, 4, 5, 0.5, 0.1, 0, 0, -1, P16, None, P16, P16, None) == -1
+    assert lib.pf_mala_propose(h, 4, 5, 0.5, 0.1, 0, 0, 0, None, None, P16, P16, None) == -1
+    assert lib.pf_mala_propose(h, 0, 5, 0.5, 0.1, 0, 0, 0, None, None, None, None, None) == 0
+    assert lib.pf_mala_accept(h, 4, 5, 0.5, 0.1, 0, 0, 0, P16, P16, None, P16, None, P16, P16, None, None) == -1
+    assert lib.pf_mala_accept(h, 0, 5, 0.5, 0.1, 0, 0, 0, *([None] * 9)) == 0
+    # the Exp 1 ensemble
+    assert lib.sch_prior_exp1(h, 4, 0, -1, P16, P16, None) == -1
+    assert lib.sch_prior_exp1(h, 4, 0, 0, None, P16, None) == -1
+    assert lib.sch_prior_exp1(h, 0, 0, 0, None, None, None) == 0
+    assert lib.sch_prior_exp1(None, 4, 0, 0, P16, P16, None) == -1
+    # gated stages: a negative jitter count is an argument error (zero jitters nothing)
+    bufs = (ct.c_void_p * 7)(*([16] * 6 + [None]))
+    assert lib.pf_gated_stages(h, 4, 5, 1, 0, 1.0, 0, 0.9, -1, 0, 0, P16, bufs, bufs, P16, P16, P16, P16, None, None,
+                               None, None, None) == -1
     assert lib.sch_destroy(h) == 0
 
 
