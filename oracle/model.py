@@ -226,6 +226,14 @@ class Model:
             U = self.solve(G, self.apply(self.mass(), U))
         return U
 
+    def noise_matrix(self) -> np.ndarray:
+        """d dU / dw [n, Q] for the increments w = dW + lambda dt of one step: the mode
+        functions at the nodes, or the Matern map (G^{-1} M)^{k-1} G^{-1} B, built column
+        by column from ``noise`` (it is linear in w)."""
+        if self.noise_model != "matern":
+            return self.modes().T
+        return np.stack([self.noise(e) for e in np.eye(self.n)], axis=1)
+
     def matern_operator(self):
         """M + kappa^{-2} K, the P1 form of (I - kappa^{-2} d_xx) (Eq. noise_solve2)."""
         Ma, Mb, Mc = self.mass()

@@ -88,13 +88,13 @@ def cost_and_gradient(model, m0, dW, lam, y, sigma, var_steps=None):
     """
     dW = np.asarray(dW, dtype=np.float64)
     lam = np.asarray(lam, dtype=np.float64)
-    Ns, K = dW.shape
+    Ns, K = dW.shape          # K: Brownian motions per step (the Matern noise: one per cell)
     var_steps = list(range(Ns)) if var_steps is None else list(var_steps)
     col = {s: i for i, s in enumerate(var_steps)}
     nvar = len(var_steps) * K
     _, u_end, _, _, traj = model.window(m0, dW, lam, return_traj=True)
     ops = dense_ops(model)
-    Xi = model.modes().T                      # [n, K]
+    Xi = model.noise_matrix()                 # d dU / d(dW + lambda dt): [n, K]
     D = np.zeros((model.n, nvar))             # d m_s / d lambda
     for s in range(Ns):
         m_s, m_s1 = traj[s][0], traj[s + 1][0]

@@ -155,3 +155,30 @@ def test_sequential_schedule():
     nll_nudged = OF.nll(m.window(m0, dW, lam)[1][None], y, sigma)[0]
     nll_plain = OF.nll(m.window(m0, dW)[1][None], y, sigma)[0]
     assert nll_nudged < nll_plain
+
+
+def test_matern_gradient_matches_finite_differences():
+    # the Matern noise (one Brownian motion per cell): the tangent-linear gradient over all
+    # n drifts of every step against central differences of the cost, with a drift present,
+    # and dJ/ddW = (dJ/dlambda - dt lambda) / dt (the noise depends on dW + lambda dt only)
+    m = Model(L=40.0, n=64, alpha=1.0, mu=0.02, dt=0.025, amps=np.full(2, 0.05), noise_model="matern",
+              kappa=1.0, eta=0.5, matern_k=3)
+    r = np.random.default_rng(8)
+    x = m.x
+    u0 = 0.3 / np.cosh(x - 20.0) + 0.05 * np.sin(2 * math.pi * x / m.L)
+    m0 = m.m_from_u(u0)
+    Ns = 3
+    dW = r.normal(scale=math.sqrt(m.dt), size=(Ns, m.n))
+    lam = r.normal(scale=0.3, size=(Ns, m.n))
+    y = u0[::4] + r.normal(scale=0.05, size=16)
+    sigma = 0.05
+    J, g = ON.cost_and_gradient(m, m0, dW, lam, y, sigma)
+    assert g.shape == (Ns, m.n)
+    assert np.isclose(J, ON.cost(m, m0, dW, lam, y, sigma), rtol=1e-14)
+    for _ in range(8):
+        d = r.normal(size=lam.shape)
+        eps = 1e-5
+        fd = (ON.cost(m, m0, dW, lam + eps * d, y, sigma) - ON.cost(m, m0, dW, lam - eps * d, y, sigma)) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) <= 1e-6 * max(1.0, abs(fd))
+        fdw = (ON.cost(m, m0, dW + eps * d, lam, y, sigma) - ON.cost(m, m0, dW - eps * d, lam, y, sigma)) / (2 * eps)
+        assert abs(fdw - np.sum((g - m.dt * lam) / m.dt * d)) <= 1e-6 * max(1.0, abs(fdw))
