@@ -680,10 +680,9 @@ static bool mala_args_ok(const sch_ctx* ctx, int N, int nsteps, int particle0, d
 int pf_mala_propose(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint64_t seed, uint64_t ctr,
                     int particle0, const void* dW, const void* lambda, const void* gJ, void* dW_prop, void* stream) {
     if (!mala_args_ok(ctx, N, nsteps, particle0, theta, h)) return SCH_ERR_ARG;
-    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!dW || !gJ || !dW_prop) return SCH_ERR_ARG;
-    const int K = ctx->p.K;
+    const int K = ctx->Q;
     if (ctx->p.dtype == SCH_F32)
         return launch_mala_propose<float>(N, nsteps, K, theta, h, ctx->p.dt, (const float*)dW, (const float*)lambda,
                                           (const float*)gJ, seed, ctr, particle0, (float*)dW_prop, S(stream));
@@ -695,10 +694,9 @@ int pf_mala_accept(sch_ctx* ctx, int N, int nsteps, double theta, double h, uint
                    int particle0, void* dW, const void* dW_prop, const void* lambda, double* J, const double* J_prop,
                    void* gJ, const void* gJ_prop, int32_t* accepts, void* stream) {
     if (!mala_args_ok(ctx, N, nsteps, particle0, theta, h)) return SCH_ERR_ARG;
-    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!dW || !dW_prop || !J || !J_prop || !gJ || !gJ_prop) return SCH_ERR_ARG;
-    const int NK = nsteps * ctx->p.K;
+    const int NK = nsteps * ctx->Q;
     if (ctx->p.dtype == SCH_F32)
         return launch_mala_accept<float>(N, NK, theta, h, ctx->p.dt, seed, ctr, particle0, (float*)dW,
                                          (const float*)dW_prop, (const float*)lambda, J, J_prop, (float*)gJ,
@@ -751,11 +749,23 @@ int sch_adjoint_window(sch_ctx* ctx, int N, int nsteps, int ckpt, const void* m_
                        const void* lambda, const void* y, double* J, void* g_lambda, void* g_dW, void* g_m0,
                        int32_t* iters, int32_t* status, void* ws, size_t ws_bytes, void* stream) {
     if (!ctx || N < 0 || nsteps <= 0 || ckpt <= 0 || nsteps > 4096) return SCH_ERR_ARG;
-    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!m_start || !dW || !y || !J || !g_lambda) return SCH_ERR_ARG;
     if (!ws || ws_bytes < sch_adjoint_workspace_bytes(ctx, N, nsteps, ckpt)) return SCH_ERR_WORKSPACE;
     const size_t per = adjoint_ws_per(ctx, nsteps, ckpt);
+    if (ctx->matern) {
+        // one step's cell weights in shared memory, gradients per cell (Q = n)
+        if (ctx->p.dtype == SCH_F32) {
+            AdjointIO<float> io{nsteps, ckpt, (const float*)m_start, (const float*)dW, (const float*)lambda,
+                                (const float*)y, J, (float*)g_lambda, (float*)g_dW, (float*)g_m0, (float*)ws,
+                                per / sizeof(float), iters, status};
+            return launch_adjoint_matern<float, 8>(ctx->af, io, N, S(stream));
+        }
+        AdjointIO<double> io{nsteps, ckpt, (const double*)m_start, (const double*)dW, (const double*)lambda,
+                             (const double*)y, J, (double*)g_lambda, (double*)g_dW, (double*)g_m0, (double*)ws,
+                             per / sizeof(double), iters, status};
+        return launch_adjoint_matern<double, 4>(ctx->ad, io, N, S(stream));
+    }
     if (ctx->p.dtype == SCH_F32) {
         if (adjoint_smem<float, 8>(ctx->tp, nsteps, ctx->p.K) > 200 * 1024) return SCH_ERR_UNSUPPORTED;
         AdjointIO<float> io{nsteps, ckpt, (const float*)m_start, (const float*)dW, (const float*)lambda,

@@ -264,20 +264,61 @@ __device__ __forceinline__ void load_field(const R* src, R (&v)[C]) {
     for (int i = 0; i < C; ++i) v[i] = src[i0 + i];
 }
 
+// Matern noise (Eq. noise_solve2): this thread's cell weights eta sqrt(h)/8 (dW_c +
+// lambda_c dt) of step s into the n-value buffer wbuf, published by a barrier
+template <typename R, int C>
+__device__ __forceinline__ void matern_stage_step(const ModelArgs<R>& A, R* wbuf, const R* dW, const R* lam, int s) {
+    const int i0 = threadIdx.x * C;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+        const size_t q = (size_t)s * A.n + i0 + i;
+        R v = dW[q];
+        if (lam) v += lam[q] * A.dt;
+        wbuf[i0 + i] = A.mz * v;
+    }
+    __syncthreads();
+}
+
+// dJ/dw for this thread's cells c = i0 .. i0 + C - 1 from dJ/ddU at its nodes: the
+// transpose of dU = (G^{-1} M)^{k-1} G^{-1} B w, i.e. B^T G^{-1} (M G^{-1})^{k-1}, with
+// G = M + kappa^-2 K symmetric and (B^T t)_c = eta sqrt(h)/2 (t_c + t_{c+1})
+template <typename R, int C, int TP>
+__device__ __forceinline__ void matern_adjoint_cells(const ModelArgs<R>& A, Shm<R, TP>* sh, const R (&gdu)[C],
+                                                     R (&gw)[C]) {
+    R t[C], x[C], xp, xn;
+#pragma unroll
+    for (int i = 0; i < C; ++i) t[i] = gdu[i];
+    for (int j = 1; j < A.mk; ++j) {
+        const_solve<R, C, TP>(A.matern, A.rmatern, t, x, xp, xn, sh);
+        mass_apply<R, C>(A.h6, x, xp, xn, t);
+    }
+    const_solve<R, C, TP>(A.matern, A.rmatern, t, x, xp, xn, sh);
+    const R b = R(4) * A.mz;
+#pragma unroll
+    for (int i = 0; i < C; ++i) gw[i] = b * (x[i] + ((i == C - 1) ? xn : x[i + 1]));
+}
+
 // --------------------------------------------------------------------------
 // Forward window from step n0 (state at `start`) to Ns, storing the state at
 // steps n0, n0 + ck, ... into ckp; returns J = NLL(u_end) + 1/2 dt sum_s sum_k
 // lam^2 (all steps) in every thread, and the end state in f.
-// noise: the weights a_j/4 (dW + lam dt) of all Ns steps (staged by the caller).
+// noise: the weights a_j/4 (dW + lam dt) of all Ns steps (staged by the caller); with
+// the Matern noise (NZ) an n-value buffer for one step's cell weights, formed here from
+// dW and lam.
 // --------------------------------------------------------------------------
-template <typename R, int C, int TP, int S>
-__device__ __forceinline__ double forward_ck(const ModelArgs<R>& A, Shm<R, TP>* sh, const R* noise, const R* start,
+template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
+__device__ __forceinline__ double forward_ck(const ModelArgs<R>& A, Shm<R, TP>* sh, R* noise, const R* start,
                                              int n0, int Ns, int ck, R* ckp, const R* lam, const R* y, R s0, R c0,
-                                             Field<R, C>& f, int& iters, int& flags) {
+                                             Field<R, C>& f, int& iters, int& flags, const R* dW = nullptr) {
     field_start<R, C, TP>(A, sh, start, f);
     for (int s = n0; s < Ns; ++s) {
         if ((s - n0) % ck == 0) store_field<R, C>(ckp + (size_t)((s - n0) / ck) * A.n, f.m);
-        step_any<S, R, C, TP>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
+        if constexpr (NZ == SCH_NOISE_MATERN) {
+            matern_stage_step<R, C>(A, noise, dW, lam, s);
+            step_any<S, R, C, TP, NZ>(A, sh, f, noise, s0, c0, iters, flags);
+        } else {
+            step_any<S, R, C, TP>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
+        }
     }
     double mis = chunk_misfit<R, C>(A, f.u, y);
     double reg = 0.0;
@@ -296,11 +337,12 @@ __device__ __forceinline__ double forward_ck(const ModelArgs<R>& A, Shm<R, TP>* 
 // glam[(s - v0) K + k] (and dJ/d dW into gdw when non-null), dJ/dm(n0) into g.
 // glam, gdw: any address space, written by threads k < K.
 // --------------------------------------------------------------------------
-template <typename R, int C, int TP, int S, typename GL, typename GW>
-__device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* sh, const R* noise, int n0, int Ns,
+template <typename R, int C, int TP, int S, typename GL, typename GW, int NZ = SCH_NOISE_MODES>
+__device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* sh, R* noise, int n0, int Ns,
                                             int ck, const R* ckp, R* seg, const R* lam, const R* y, R s0, R c0,
                                             R s1, R c1, const Field<R, C>& fend, int v0, int v1, double* red,
-                                            GL glam, GW gdw, R (&g)[C], int& iters, int& flags) {
+                                            GL glam, GW gdw, R (&g)[C], int& iters, int& flags,
+                                            const R* dW = nullptr) {
     const int t = threadIdx.x;
     const int i0 = t * C;
     const int K = A.K;
@@ -326,7 +368,12 @@ __device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* s
         store_field<R, C>(seg, h.m);
         store_field<R, C>(seg + A.n, h.u);
         for (int s = sa; s < sb; ++s) {
-            step_any<S, R, C, TP>(A, sh, h, noise + s * K, s0, c0, dummy_it, dummy_fl);
+            if constexpr (NZ == SCH_NOISE_MATERN) {
+                matern_stage_step<R, C>(A, noise, dW, lam, s);
+                step_any<S, R, C, TP, NZ>(A, sh, h, noise, s0, c0, dummy_it, dummy_fl);
+            } else {
+                step_any<S, R, C, TP>(A, sh, h, noise + s * K, s0, c0, dummy_it, dummy_fl);
+            }
             store_field<R, C>(seg + (size_t)(s - sa + 1) * 2 * A.n, h.m);
             store_field<R, C>(seg + (size_t)(s - sa + 1) * 2 * A.n + A.n, h.u);
         }
@@ -341,10 +388,28 @@ __device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* s
             chunk_halo2<R, C, TP>(st.m0, st.m0p, st.m0n, st.u0, st.u0p, st.u0n, sh);
             chunk_halo2<R, C, TP>(st.m1, st.m1p, st.m1n, st.u1, st.u1p, st.u1n, sh);
             R nq[C + 2];
-            noise_nodes<R, C>(A, noise + s * K, s0, c0, nq);
+            if constexpr (NZ == SCH_NOISE_MATERN) {
+                matern_stage_step<R, C>(A, noise, dW, lam, s);
+                matern_nodes<R, C, TP>(A, sh, noise, nq);
+            } else {
+                noise_nodes<R, C>(A, noise + s * K, s0, c0, nq);
+            }
             R gdu[C];
             adjoint_step<R, C, TP>(A, sh, st, nq, g, gp, gn, gdu, iters, flags);
-            if (s >= v0 && s < v1) {
+            if constexpr (NZ == SCH_NOISE_MATERN) {
+                // one drift per cell: dJ/dlambda_c = dt dJ/dw_c + dt lambda_c, dJ/ddW_c = dJ/dw_c
+                R gw[C];
+                matern_adjoint_cells<R, C, TP>(A, sh, gdu, gw);
+                if (s >= v0 && s < v1) {
+#pragma unroll
+                    for (int i = 0; i < C; ++i) {
+                        const size_t q = (size_t)(s - v0) * A.n + i0 + i;
+                        const double l = lam ? (double)lam[(size_t)s * A.n + i0 + i] : 0.0;
+                        glam[q] = A.dt_d * (double)gw[i] + l * A.dt_d;
+                        if (gdw) gdw[q] = gw[i];
+                    }
+                }
+            } else if (s >= v0 && s < v1) {
                 mode_sums_warp<R, C>(A, s1, c1, gdu, red);
                 __syncthreads();
                 for (int k = t; k < K; k += TP) {
@@ -372,8 +437,10 @@ __host__ __device__ inline size_t adj_smem_bytes(int Ns, int K) {
     return b;
 }
 
-// J and dJ/dlambda, dJ/ddW, dJ/dm0 of a whole window for every particle
-template <typename R, int C, int TP, int S>
+// J and dJ/dlambda, dJ/ddW, dJ/dm0 of a whole window for every particle.  With the
+// Matern noise (NZ) the shared noise buffer holds one step's n cell weights, formed per
+// step from dW and lambda, and the gradients have one entry per cell.
+template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
 __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) adjoint_kernel(ModelArgs<R> A, AdjointIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
@@ -384,7 +451,7 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) adjoint_kernel(ModelArgs
     const int NK = io.Ns * A.K;
     const R* dWp = io.dW + (size_t)p * NK;
     const R* lamp = io.lam ? io.lam + (size_t)p * NK : nullptr;
-    stage_noise(A, noise, dWp, lamp, io.Ns);
+    if constexpr (NZ != SCH_NOISE_MATERN) stage_noise(A, noise, dWp, lamp, io.Ns);
     R s0, c0, s1, c1;
     node_angle<R>((int)threadIdx.x * C - 1, A.n, s0, c0);
     node_angle<R>((int)threadIdx.x * C, A.n, s1, c1);
@@ -393,13 +460,13 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) adjoint_kernel(ModelArgs
     R* seg = ckp + (size_t)ncp * A.n;
     int iters = 0, flags = 0;
     Field<R, C> f;
-    const double J = forward_ck<R, C, TP, S>(A, sh, noise, io.m_start + (size_t)p * A.n, 0, io.Ns, io.ck, ckp, lamp,
-                                             io.y, s0, c0, f, iters, flags);
+    const double J = forward_ck<R, C, TP, S, NZ>(A, sh, noise, io.m_start + (size_t)p * A.n, 0, io.Ns, io.ck, ckp,
+                                                 lamp, io.y, s0, c0, f, iters, flags, dWp);
     if (threadIdx.x == 0) io.J[p] = J;
     R g[C];
-    backward_ck<R, C, TP, S>(A, sh, noise, 0, io.Ns, io.ck, ckp, seg, lamp, io.y, s0, c0, s1, c1, f, 0, io.Ns, red,
-                             io.g_lam + (size_t)p * NK, io.g_dW ? io.g_dW + (size_t)p * NK : (R*)nullptr, g, iters,
-                             flags);
+    backward_ck<R, C, TP, S, R*, R*, NZ>(A, sh, noise, 0, io.Ns, io.ck, ckp, seg, lamp, io.y, s0, c0, s1, c1, f, 0,
+                                         io.Ns, red, io.g_lam + (size_t)p * NK,
+                                         io.g_dW ? io.g_dW + (size_t)p * NK : (R*)nullptr, g, iters, flags, dWp);
     if (io.g_m0) store_field<R, C>(io.g_m0 + (size_t)p * A.n, g);
     if (threadIdx.x == 0) {
         if (io.iters) io.iters[p] = iters;
@@ -661,6 +728,16 @@ struct LaunchAdj {
         if (sm > 48 * 1024)
             cudaFuncSetAttribute(nudge_kernel<R, C, TP, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         nudge_kernel<R, C, TP, S><<<N, TP, sm, st>>>(A, io);
+        return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    }
+    // the Matern noise: the solver scratch and one step's n cell weights
+    template <int S>
+    static int adjoint_matern(const ModelArgs<R>& A, const AdjointIO<R>& io, int N, cudaStream_t st) {
+        const size_t sm = shm_base_bytes<R, TP>() + (size_t)A.n * sizeof(R);
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(adjoint_kernel<R, C, TP, S, SCH_NOISE_MATERN>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        adjoint_kernel<R, C, TP, S, SCH_NOISE_MATERN><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
     static size_t adj_smem(int Ns, int K) { return adj_smem_bytes<R, TP>(Ns, K); }

@@ -173,6 +173,9 @@ template <typename R, int C, int S>
 int launch_adjoint(const ModelArgs<R>& A, const AdjointIO<R>& io, int N, cudaStream_t st);
 template <typename R, int C, int S>
 int launch_nudge(const ModelArgs<R>& A, const NudgeIO<R>& io, int N, cudaStream_t st);
+// the adjoint window with the Matern noise (sch_adjoint_matern.cu): each precision's default solver
+template <typename R, int C>
+int launch_adjoint_matern(const ModelArgs<R>& A, const AdjointIO<R>& io, int N, cudaStream_t st);
 template <typename R, int C>
 size_t adjoint_smem(int tp, int Ns, int K);
 template <typename R, int C>

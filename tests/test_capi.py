@@ -137,10 +137,12 @@ def test_create_validates_matern(lib, kw, rc):
         # one Brownian motion per cell; the CTA layout unless the warp layout is asked for
         assert lib.sch_noise_dim(h) == p.n
         assert lib.sch_layout(h) == (2 if p.layout == 2 else 1)
-        # entry points built on the adjoint take the mode expansion only
+        # the nudging optimiser takes the mode expansion only; the adjoint and MALA check arguments
+        assert lib.pf_nudge(h, 1, 5, 0, 10, 1e-6, 1, 0, 0, None, None, None, None, None, None, None, None, 0,
+                            None) == -6
         assert lib.sch_adjoint_window(h, 1, 5, 1, None, None, None, None, None, None, None, None, None, None, None,
-                                      0, None) == -6
-        assert lib.pf_mala_propose(h, 1, 5, 0.5, 0.1, 0, 0, 0, None, None, None, None, None) == -6
+                                      0, None) == -1
+        assert lib.pf_mala_propose(h, 1, 5, 0.5, 0.1, 0, 0, 0, None, None, None, None, None) == -1
         assert lib.sch_destroy(h) == 0
 
 

@@ -183,3 +183,44 @@ def test_matern_layouts_agree_at_full_ensemble_size():
     assert (acc_a != acc_b).float().mean().item() < 0.02     # decisions differ only at coin flips
     same = acc_a == acc_b
     assert (d_a[same] - d_b[same]).abs().max().item() < 1e-4
+
+
+def test_matern_adjoint_matches_oracle_tangent_linear():
+    # the reverse-mode adjoint through the Matern noise map (its transpose: k solves per
+    # step) against the oracle's tangent-linear gradient over all n drifts of every step
+    from oracle import nudge as ON
+    cfg = get_config("cfg1m_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la = _case(cfg, 2, 61, Ns=3, lam=True)
+    la = 0.2 * la / 0.3
+    y = random_obs(cfg, 64)
+    out = g.adjoint_window(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype), ckpt=2)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in range(2):
+        J, grad = ON.cost_and_gradient(om, m0[p], dW[p], la[p], y, cfg.sigma)
+        assert abs(out["J"][p].item() - J) <= 1e-10 * J
+        assert rel_err(out["g_lam"][p].cpu().numpy(), grad) < 1e-8
+        assert rel_err(out["g_dW"][p].cpu().numpy(), (grad - cfg.dt * la[p]) / cfg.dt) < 1e-8
+
+
+def test_matern_mala_matches_oracle():
+    # MALA on the Matern noise (n drifts per step), gradients from the adjoint: the oracle's
+    # keyed decisions and noise
+    cfg = get_config("cfg1m_f64")
+    g = gpu_model(cfg)
+    om, m0, dW, la = _case(cfg, 2, 31, Ns=3, lam=True)
+    la = 0.2 * la / 0.3
+    y = random_obs(cfg, 34)
+    theta, h, n_iter, seed, ctr = 0.7, 0.25, 3, 5, 40
+    ref_dW, ref_nll, ref_lg, ref_acc = OF.mala_jitter(om, m0, dW, la, y, cfg.sigma, theta, h, n_iter, seed, ctr)
+    dWd = tdev(dW, g.dtype)
+    out = g.mala_jitter(tdev(m0, g.dtype), dWd, tdev(la, g.dtype), tdev(y, g.dtype), theta, h, n_iter, seed, ctr,
+                        ckpt=2)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    assert np.array_equal(out["accepts"].cpu().numpy(), ref_acc)
+    assert 0 < ref_acc.sum() < 2 * n_iter
+    assert rel_err(dWd.cpu().numpy(), ref_dW) < 1e-8
+    assert np.allclose(out["nll"].cpu().numpy(), ref_nll, rtol=1e-8)
+    assert np.allclose(out["logG"].cpu().numpy(), ref_lg, rtol=1e-8, atol=1e-12)
