@@ -87,9 +87,9 @@ enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
  *                     (U_{j-1}, v) after, dU = U_k; Q = n.  The drift lambda is a
  *                     DG0 field added to dW (dW_c + lambda_c dt).  Default solver
  *                     of the precision; CTA layout unless SCH_LAYOUT_WARP is asked
- *                     for (FP32, n = 256, 512, 1024).  sch_adjoint_window and the
- *                     MALA entry points take it (gradients per cell); pf_nudge returns
- *                     SCH_ERR_UNSUPPORTED for it.
+ *                     for (FP32, n = 256, 512, 1024).  The adjoint, nudging and MALA
+ *                     entry points take it: gradients and drifts per cell, and pf_nudge
+ *                     keeps the optimiser's vectors in its workspace.
  * Every noise array dW, lambda of this API is [N][nsteps][Q]. */
 enum { SCH_NOISE_MODES = 0, SCH_NOISE_MATERN = 1 };
 

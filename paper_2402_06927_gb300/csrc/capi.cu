@@ -739,10 +739,18 @@ size_t sch_adjoint_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ck
     return (size_t)N * adjoint_ws_per(ctx, nsteps, ckpt);
 }
 
+// elements per particle of pf_nudge's workspace: the window start and the adjoint's
+// region, and with the Matern noise the optimiser's vectors (nudge_matern_ws_elems)
+static size_t nudge_ws_per(const sch_ctx* ctx, int nsteps, int ckpt) {
+    const size_t b = (ctx->p.dtype == SCH_F32) ? sizeof(float) : sizeof(double);
+    const size_t adj = (adjoint_ws_per(ctx, nsteps, ckpt) + (size_t)ctx->p.n * b) / b;
+    return ctx->matern ? nudge_matern_ws_elems(adj, (size_t)nsteps * ctx->Q, b) : adj;
+}
+
 size_t pf_nudge_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt) {
     if (!ctx || N <= 0 || nsteps <= 0 || ckpt <= 0) return 0;
     const size_t b = (ctx->p.dtype == SCH_F32) ? sizeof(float) : sizeof(double);
-    return (size_t)N * (adjoint_ws_per(ctx, nsteps, ckpt) + (size_t)ctx->p.n * b);
+    return (size_t)N * nudge_ws_per(ctx, nsteps, ckpt) * b;
 }
 
 int sch_adjoint_window(sch_ctx* ctx, int N, int nsteps, int ckpt, const void* m_start, const void* dW,
@@ -788,12 +796,21 @@ int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gto
     if (!ctx || N < 0 || nsteps <= 0 || ckpt <= 0 || max_iter < 0 || nsteps > 4096) return SCH_ERR_ARG;
     if (mode != PF_NUDGE_SEQUENTIAL && mode != PF_NUDGE_OPEN_LOOP) return SCH_ERR_ARG;
     if (!(gtol >= 0.0)) return SCH_ERR_ARG;
-    if (ctx->matern) return SCH_ERR_UNSUPPORTED;
     if (N == 0) return SCH_OK;
     if (!m_start || !y || !lambda || !dW || !J) return SCH_ERR_ARG;
     if (!ws || ws_bytes < pf_nudge_workspace_bytes(ctx, N, nsteps, ckpt)) return SCH_ERR_WORKSPACE;
-    const size_t b = (ctx->p.dtype == SCH_F32) ? sizeof(float) : sizeof(double);
-    const size_t per = (adjoint_ws_per(ctx, nsteps, ckpt) + (size_t)ctx->p.n * b) / b;
+    const size_t per = nudge_ws_per(ctx, nsteps, ckpt);
+    if (ctx->matern) {
+        // one drift per cell; the optimiser's vectors in the workspace, one step's weights in smem
+        if (ctx->p.dtype == SCH_F32) {
+            NudgeIO<float> io{nsteps, ckpt, mode, max_iter, 0, gtol, seed, ctr, (const float*)m_start,
+                              (const float*)y, (float*)lambda, (float*)dW, J, (float*)ws, per, iters, status};
+            return launch_nudge_matern<float, 8>(ctx->af, io, N, S(stream));
+        }
+        NudgeIO<double> io{nsteps, ckpt, mode, max_iter, 0, gtol, seed, ctr, (const double*)m_start,
+                           (const double*)y, (double*)lambda, (double*)dW, J, (double*)ws, per, iters, status};
+        return launch_nudge_matern<double, 4>(ctx->ad, io, N, S(stream));
+    }
     if (ctx->p.dtype == SCH_F32) {
         if (nudge_smem<float, 8>(ctx->tp, nsteps, ctx->p.K) > 200 * 1024) return SCH_ERR_UNSUPPORTED;
         NudgeIO<float> io{nsteps, ckpt, mode, max_iter, 0, gtol, seed, ctr, (const float*)m_start,

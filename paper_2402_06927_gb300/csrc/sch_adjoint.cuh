@@ -475,7 +475,6 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) adjoint_kernel(ModelArgs
 }
 
 enum { NUDGE_SEQUENTIAL = 0, NUDGE_OPEN_LOOP = 1 };
-constexpr int LBFGS_M = 6;
 
 template <typename R, int TP>
 __host__ __device__ inline size_t nudge_smem_bytes(int Ns, int K) {
@@ -518,20 +517,36 @@ __device__ __forceinline__ double block_absmax(Shm<R, TP>* sh, const double* a, 
 // and drifts zero, then reveal dW^n (Philox, SCH_TAG_NUDGE, counter
 // (k/4, n, particle, ctr)) and advance the start state one step.
 // Open loop: optimise all drifts with every increment zero, then reveal all.
-template <typename R, int C, int TP, int S>
+//
+// With the Matern noise (NZ) the drift has one entry per cell (K = n), the shared noise
+// buffer holds one step's cell weights, and the window's drifts, increments and L-BFGS
+// vectors live in the particle's workspace (nudge_matern_ws_elems).
+template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
 __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R> A, NudgeIO<R> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Shm<R, TP>* sh = reinterpret_cast<Shm<R, TP>*>(smem_raw);
     const int Ns = io.Ns, K = A.K, NK = Ns * K;
     unsigned char* base = smem_raw + shm_base_bytes<R, TP>();
     R* noise = reinterpret_cast<R*>(base);
-    base += ((size_t)NK * sizeof(R) + 15) / 16 * 16;
-    double* red = reinterpret_cast<double*>(base);
-    base += (size_t)(TP / 32) * K * sizeof(double);
-    R* dWl = reinterpret_cast<R*>(base);
-    base += ((size_t)NK * sizeof(R) + 15) / 16 * 16;
-    R* laml = reinterpret_cast<R*>(base);
-    base += ((size_t)NK * sizeof(R) + 15) / 16 * 16;
+    double* red = nullptr;
+    R* dWl;
+    R* laml;
+    if constexpr (NZ == SCH_NOISE_MATERN) {
+        // after the adjoint's region: start (n), checkpoints, segment states
+        const size_t ws_adj = (size_t)A.n * (1 + (Ns + io.ck - 1) / io.ck + 2 * (io.ck + 1));
+        base = reinterpret_cast<unsigned char*>(io.ws + (size_t)blockIdx.x * io.ws_per) +
+               (ws_adj * sizeof(R) + 7) / 8 * 8;
+        dWl = reinterpret_cast<R*>(base + ((size_t)(5 + 2 * LBFGS_M) * NK + 2 * LBFGS_M) * sizeof(double));
+        laml = dWl + NK;
+    } else {
+        base += ((size_t)NK * sizeof(R) + 15) / 16 * 16;
+        red = reinterpret_cast<double*>(base);
+        base += (size_t)(TP / 32) * K * sizeof(double);
+        dWl = reinterpret_cast<R*>(base);
+        base += ((size_t)NK * sizeof(R) + 15) / 16 * 16;
+        laml = reinterpret_cast<R*>(base);
+        base += ((size_t)NK * sizeof(R) + 15) / 16 * 16;
+    }
     double* vx = reinterpret_cast<double*>(base);
     double* vg = vx + NK;
     double* vd = vg + NK;
@@ -580,15 +595,16 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
         auto set_lambda = [&](const double* x) {
             for (int q = t; q < nv; q += TP) laml[v0 * K + q] = (R)x[q];
             __syncthreads();
-            stage_noise(A, noise, dWl, laml, Ns);
+            if constexpr (NZ != SCH_NOISE_MATERN) stage_noise(A, noise, dWl, laml, Ns);
             __syncthreads();
         };
         Field<R, C> f;
         set_lambda(vx);
-        double J = forward_ck<R, C, TP, S>(A, sh, noise, start, n0, Ns, ck, ckp, laml, io.y, s0, c0, f, iters, flags);
+        double J = forward_ck<R, C, TP, S, NZ>(A, sh, noise, start, n0, Ns, ck, ckp, laml, io.y, s0, c0, f, iters,
+                                               flags, dWl);
         R gm[C];
-        backward_ck<R, C, TP, S>(A, sh, noise, n0, Ns, ck, ckp, seg, laml, io.y, s0, c0, s1, c1, f, v0, v1, red, vg,
-                                 (double*)nullptr, gm, iters, flags);
+        backward_ck<R, C, TP, S, double*, double*, NZ>(A, sh, noise, n0, Ns, ck, ckp, seg, laml, io.y, s0, c0, s1, c1,
+                                                       f, v0, v1, red, vg, (double*)nullptr, gm, iters, flags, dWl);
         __syncthreads();
         int hist = 0, head = 0;
         double gamma = 1.0;
@@ -631,7 +647,8 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
                 for (int q = t; q < nv; q += TP) vxt[q] = vx[q] + step * vd[q];
                 __syncthreads();
                 set_lambda(vxt);
-                Jt = forward_ck<R, C, TP, S>(A, sh, noise, start, n0, Ns, ck, ckp, laml, io.y, s0, c0, f, iters, flags);
+                Jt = forward_ck<R, C, TP, S, NZ>(A, sh, noise, start, n0, Ns, ck, ckp, laml, io.y, s0, c0, f, iters,
+                                                 flags, dWl);
                 if (Jt <= J + 1e-4 * step * gd) {
                     ok = true;
                     break;
@@ -642,8 +659,9 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
                 set_lambda(vx);
                 break;
             }
-            backward_ck<R, C, TP, S>(A, sh, noise, n0, Ns, ck, ckp, seg, laml, io.y, s0, c0, s1, c1, f, v0, v1, red,
-                                     vgt, (double*)nullptr, gm, iters, flags);
+            backward_ck<R, C, TP, S, double*, double*, NZ>(A, sh, noise, n0, Ns, ck, ckp, seg, laml, io.y, s0, c0, s1,
+                                                           c1, f, v0, v1, red, vgt, (double*)nullptr, gm, iters, flags,
+                                                           dWl);
             __syncthreads();
             // history update s = xt - x, y = gt - g
             for (int q = t; q < nv; q += TP) {
@@ -680,10 +698,16 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
                     if (4 * q + e < K) dWl[n0 * K + 4 * q + e] = (R)sqrt(A.dt_d) * z[e];
             }
             __syncthreads();
-            stage_noise(A, noise, dWl, laml, Ns);
             Field<R, C> h;
-            field_start<R, C, TP>(A, sh, start, h);
-            step_any<S, R, C, TP>(A, sh, h, noise + n0 * K, s0, c0, iters, flags);
+            if constexpr (NZ == SCH_NOISE_MATERN) {
+                field_start<R, C, TP>(A, sh, start, h);
+                matern_stage_step<R, C>(A, noise, dWl, laml, n0);
+                step_any<S, R, C, TP, NZ>(A, sh, h, noise, s0, c0, iters, flags);
+            } else {
+                stage_noise(A, noise, dWl, laml, Ns);
+                field_start<R, C, TP>(A, sh, start, h);
+                step_any<S, R, C, TP>(A, sh, h, noise + n0 * K, s0, c0, iters, flags);
+            }
             __syncthreads();
             store_field<R, C>(start, h.m);
             __syncthreads();
@@ -738,6 +762,15 @@ struct LaunchAdj {
             cudaFuncSetAttribute(adjoint_kernel<R, C, TP, S, SCH_NOISE_MATERN>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         adjoint_kernel<R, C, TP, S, SCH_NOISE_MATERN><<<N, TP, sm, st>>>(A, io);
+        return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    }
+    template <int S>
+    static int nudge_matern(const ModelArgs<R>& A, const NudgeIO<R>& io, int N, cudaStream_t st) {
+        const size_t sm = shm_base_bytes<R, TP>() + (size_t)A.n * sizeof(R);
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(nudge_kernel<R, C, TP, S, SCH_NOISE_MATERN>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        nudge_kernel<R, C, TP, S, SCH_NOISE_MATERN><<<N, TP, sm, st>>>(A, io);
         return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
     }
     static size_t adj_smem(int Ns, int K) { return adj_smem_bytes<R, TP>(Ns, K); }

@@ -173,9 +173,26 @@ template <typename R, int C, int S>
 int launch_adjoint(const ModelArgs<R>& A, const AdjointIO<R>& io, int N, cudaStream_t st);
 template <typename R, int C, int S>
 int launch_nudge(const ModelArgs<R>& A, const NudgeIO<R>& io, int N, cudaStream_t st);
-// the adjoint window with the Matern noise (sch_adjoint_matern.cu): each precision's default solver
+// the adjoint window and nudging with the Matern noise (sch_adjoint_matern.cu): each
+// precision's default solver
 template <typename R, int C>
 int launch_adjoint_matern(const ModelArgs<R>& A, const AdjointIO<R>& io, int N, cudaStream_t st);
+template <typename R, int C>
+int launch_nudge_matern(const ModelArgs<R>& A, const NudgeIO<R>& io, int N, cudaStream_t st);
+
+// L-BFGS memory of the nudging optimiser
+constexpr int LBFGS_M = 6;
+
+// With the Matern noise the nudging optimiser keeps the window's drifts, increments and
+// L-BFGS vectors in the particle's workspace after the adjoint's region of ws_adj
+// elements of rsize bytes: 5 + 2 LBFGS_M vectors of NK doubles and 2 LBFGS_M doubles
+// (8-byte aligned), then dW and lambda (NK elements each).  Elements per particle, even
+// so that every particle's region stays 8-byte aligned.
+inline size_t nudge_matern_ws_elems(size_t ws_adj, size_t NK, size_t rsize) {
+    const size_t dbl = (ws_adj * rsize + 7) / 8 + (5 + 2 * (size_t)LBFGS_M) * NK + 2 * LBFGS_M;
+    const size_t elems = (dbl * 8 + 2 * NK * rsize + rsize - 1) / rsize;
+    return (elems + 1) / 2 * 2;
+}
 template <typename R, int C>
 size_t adjoint_smem(int tp, int Ns, int K);
 template <typename R, int C>

@@ -137,9 +137,11 @@ def test_create_validates_matern(lib, kw, rc):
         # one Brownian motion per cell; the CTA layout unless the warp layout is asked for
         assert lib.sch_noise_dim(h) == p.n
         assert lib.sch_layout(h) == (2 if p.layout == 2 else 1)
-        # the nudging optimiser takes the mode expansion only; the adjoint and MALA check arguments
+        # the entry points built on the adjoint check their arguments; the nudging workspace holds
+        # the optimiser's vectors, 17 of nsteps x n doubles, besides the adjoint's region
         assert lib.pf_nudge(h, 1, 5, 0, 10, 1e-6, 1, 0, 0, None, None, None, None, None, None, None, None, 0,
-                            None) == -6
+                            None) == -1
+        assert lib.pf_nudge_workspace_bytes(h, 1, 5, 1) >= 17 * 5 * p.n * 8 + lib.sch_adjoint_workspace_bytes(h, 1, 5, 1)
         assert lib.sch_adjoint_window(h, 1, 5, 1, None, None, None, None, None, None, None, None, None, None, None,
                                       0, None) == -1
         assert lib.pf_mala_propose(h, 1, 5, 0.5, 0.1, 0, 0, 0, None, None, None, None, None) == -1

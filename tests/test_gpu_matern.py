@@ -224,3 +224,47 @@ def test_matern_mala_matches_oracle():
     assert rel_err(dWd.cpu().numpy(), ref_dW) < 1e-8
     assert np.allclose(out["nll"].cpu().numpy(), ref_nll, rtol=1e-8)
     assert np.allclose(out["logG"].cpu().numpy(), ref_lg, rtol=1e-8, atol=1e-12)
+
+
+def _matern_nudge_case():
+    cfg = get_config("cfg1m_f64", n=128, M=16, Ns=3)
+    om = oracle_model(cfg)
+    u0 = random_state(cfg, 2, 11)
+    m0 = np.stack([om.m_from_u(u) for u in u0])
+    y = random_obs(cfg, 12)
+    return cfg, om, m0, y
+
+
+def test_matern_nudge_open_loop_matches_oracle():
+    # L-BFGS over one drift per cell and step (Lambda in Q_h), the optimiser's vectors in the
+    # workspace: the oracle's minimiser (scipy L-BFGS-B on the tangent-linear gradient)
+    from oracle import nudge as ON
+    cfg, om, m0, y = _matern_nudge_case()
+    g = gpu_model(cfg)
+    out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="open_loop", max_iter=200, gtol=1e-10,
+                  ckpt=2, seed=4, ctr=1)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    lam = out["lam"].cpu().numpy()
+    assert lam.shape == (2, cfg.Ns, cfg.n)
+    for p in range(2):
+        ref, res = ON.nudge_open_loop(om, m0[p], y, cfg.sigma, cfg.Ns, cfg.Q, gtol=1e-12)
+        assert rel_err(lam[p], ref) < 1e-5
+        assert abs(out["J"][p].item() - res.fun) <= 1e-9 * res.fun
+        z = ORNG.normals(4, ORNG.TAG_NUDGE, cfg.Q, np.arange(cfg.Ns, dtype=np.uint64), np.uint64(p), np.uint64(1))
+        assert np.allclose(out["dW"][p].cpu().numpy(), math.sqrt(cfg.dt) * z, rtol=1e-13, atol=1e-15)
+
+
+def test_matern_nudge_sequential_matches_oracle():
+    from oracle import nudge as ON
+    cfg, om, m0, y = _matern_nudge_case()
+    g = gpu_model(cfg)
+    out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="sequential", max_iter=100, gtol=1e-10,
+                  ckpt=2, seed=3, ctr=7)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in range(2):
+        lam, dW = ON.nudge_sequential(om, m0[p], y, cfg.sigma, cfg.Ns, cfg.Q, seed=3, particle=p, ctr=7,
+                                      gtol=1e-12)
+        assert np.allclose(out["dW"][p].cpu().numpy(), dW, rtol=1e-13, atol=1e-15)
+        assert rel_err(out["lam"][p].cpu().numpy(), lam) < 1e-5
