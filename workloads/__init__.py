@@ -19,7 +19,7 @@ Workloads (all synthetic twin experiments; the paper uses no public dataset):
 * ``cfg3_f64``  nudging, FP64: n=1024, K=8, N=256, 20-step window.
 * ``cfg4_f32``  learned proposal: n=1024, K=16, 20-step window, N=1024.
 * ``cfg5_f32``  large run: n=4096, K=32, N=8192, M=128, sigma=0.02.
-* ``cfg1m_f64``, ``cfg2m_f32``  cfg1 / cfg2 with the paper's Matern noise
+* ``cfg1m_f64``, ``cfg2m_f32``, ``cfg3m_f64``  cfg1 / cfg2 / cfg3 with the paper's Matern noise
   (Eq. noise_solve: one Brownian motion per cell, k = 3 solves, kappa = 1)
   instead of the mode expansion; eta = 0.2 puts the per-step noise at the
   size of the mode-expansion workloads' (eta = 1 makes it about five times
@@ -122,6 +122,8 @@ CONFIGS = {
                        sigma=0.02, N=8192, cycles=50, n_jitter=10, rho=0.9999,
                        dtype="f32", tol=1e-6, max_iter=40),
     "cfg1m_f64": Config(name="cfg1m_f64", noise="matern", kappa=1.0, eta=0.2),
+    "cfg3m_f64": Config(name="cfg3m_f64", n=1024, K=8, amp_rule="inv_j", Ns=20, M=64,
+                        sigma=0.05, N=256, n_jitter=5, noise="matern", kappa=1.0, eta=0.2),
     "exp1_f64": Config(name="exp1_f64", n=128, M=64, sigma=0.05, N=150, cycles=1000,
                        noise="matern", kappa=1.0, eta=1.0),
     "cfg2m_f32": Config(name="cfg2m_f32", n=1024, K=8, amp_rule="inv_j", Ns=10, M=64,
