@@ -700,20 +700,23 @@ def run_exp1(args):
         cfg = cfg.replace(sigma=args.exp1_sigma)
     g = SchModel.from_config(cfg)
     T = args.da_steps
-    out = twin.exp1(g, cfg, T)
+    out = twin.exp2(g, cfg, T) if args.exp2 else twin.exp1(g, cfg, T)
     res = {}
     for name in ("bootstrap", "tempering_jittering"):
         sr = out[name]["series"]
+        hv = out[name]["halves"]
         res[name] = {
             "assimilation_steps_per_s": T / out[name]["seconds"],
             "mean_tempering_stages": statistics.mean(out[name]["stages"]),
             "emre_rb_res_at": {str(k): sr[k - 1].tolist() for k in (1, 100, 500, 1000) if k <= T},
             "emre_rb_res_mean_last_100": sr[max(0, T - 100):].mean(axis=0).tolist(),
+            "mean_error_first_second_half_last_100": hv[max(0, T - 100):].mean(axis=0).tolist(),
         }
     line = {"metric": "assimilation steps/s", "value": res["tempering_jittering"]["assimilation_steps_per_s"],
             "unit": "assimilation steps/s", "n_gpus": 1, "steps": T, "warmup": 0, "higher_is_better": True,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"Exp 1: exp1_f64 (N={cfg.N}, n={cfg.n}, Matern eta={cfg.eta} k={cfg.matern_k} "
+            "config": {"workload": ("Exp 2 (only [0, L/2] observed)" if args.exp2 else "Exp 1")
+                                   + f": exp1_f64 (N={cfg.N}, n={cfg.n}, Matern eta={cfg.eta} k={cfg.matern_k} "
                                    f"kappa={cfg.kappa}, Ns={cfg.Ns}, M={cfg.M}, sigma={cfg.sigma:.4g}, delta=0.15, "
                                    f"{cfg.n_jitter} jitter steps per stage), {T} assimilation steps",
                        "initial_emre_rb_res": out["initial"].tolist()},
@@ -910,6 +913,7 @@ def main():
     ap.add_argument("--exp1", action="store_true",
                     help="Exp 1: bootstrap vs tempering + jittering filters over --da-steps assimilation steps")
     ap.add_argument("--da-steps", type=int, default=1000)
+    ap.add_argument("--exp2", action="store_true", help="Exp 2: --exp1 with only [0, L/2] observed")
     ap.add_argument("--exp1-sigma", type=float, default=None,
                     help="observation error standard deviation of --exp1 (default 0.05)")
     ap.add_argument("--mala", action="store_true",
@@ -943,7 +947,7 @@ def main():
         if args.steps == 100:
             args.steps = 10
         return run_adjoint(args)
-    if args.exp1:
+    if args.exp1 or args.exp2:
         return run_exp1(args)
     if args.mala:
         if args.steps == 100:

@@ -32,3 +32,24 @@ def test_exp1_bootstrap_collapses_and_tempering_tracks():
     assert np.min(t[:, 2] / t[:, 0]) > 0.1
     assert t[late, 0].mean() < 0.9 * b[late, 0].mean()
     assert 3 <= np.mean(out["tempering_jittering"]["stages"]) <= 15
+
+
+def test_exp2_half_domain_observations():
+    # Exp 2 (only [0, L/2] observed), 200 steps: the tempered and jittered ensemble keeps its
+    # spread and its mean follows the truth on the observed half, much closer than on the
+    # other half and closer than the bootstrap ensemble's mean there
+    from paper_2402_06927_gb300 import twin
+    cfg = get_config("exp1_f64")
+    g = gpu_model(cfg)
+    T = 200
+    out = twin.exp2(g, cfg, T)
+    b, t = out["bootstrap"]["series"], out["tempering_jittering"]["series"]
+    hv = out["tempering_jittering"]["halves"]
+    late = slice(T // 2, T)
+    print("bootstrap", b[late].mean(axis=0), "tempered", t[late].mean(axis=0), "halves", hv[late].mean(axis=0),
+          "bootstrap halves", out["bootstrap"]["halves"][late].mean(axis=0),
+          "stages", np.mean(out["tempering_jittering"]["stages"]), "collapsed", np.sum(b[:, 2] < 1e-9))
+    hb = out["bootstrap"]["halves"]
+    assert np.min(t[:, 2] / t[:, 0]) > 0.1
+    assert hv[late, 0].mean() < hv[late, 1].mean() / 3
+    assert hv[late, 0].mean() < hb[late, 0].mean()
