@@ -592,7 +592,7 @@ def run_adjoint(args):
     return 0
 
 
-MALA_THETA, MALA_H, MALA_ITERS = 1.0, 0.02, 10
+MALA_THETA, MALA_H, MALA_ITERS = 1.0, 0.5, 10
 
 
 def run_mala(args):

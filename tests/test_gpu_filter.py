@@ -199,3 +199,35 @@ def test_gated_stages_equal_stage_by_stage_fp32(nudged):
             assert torch.equal(getattr(fs[0], name), getattr(fs[1], name)), name
         for f in fs:
             f.advance()
+
+
+def test_jitter_full_size_sampled():
+    # the jitter in the bench's launch configuration (n = 1024, N = 1024, Ns = 10, FP32, warp
+    # layout, 10 proposals): three sampled particles replayed by the oracle with their own
+    # Philox particle indices; decisions equal away from a coin flip, fields to FP32 tolerance
+    cfg = get_config("cfg2_f32")
+    g = gpu_model(cfg)
+    assert g.layout == "warp"
+    om = oracle_model(cfg)
+    N, theta, n_iter, seed, ctr = cfg.N, 0.5, cfg.n_jitter, 77, 1000
+    u0 = torch.tensor(random_state(cfg, 1, 3)[0], dtype=torch.float32, device="cuda")
+    m0, _ = g.prior_sample(N, u0, 5, cfg.prior_scale)
+    dW = g.draw_increments(N, cfg.Ns, 9, ORNG.TAG_PRIOR_DW, 0)
+    y = g.synth_obs(u0, 2, 1)
+    dW0 = dW.double().cpu().numpy()
+    st = g.ensemble_step(m0, dW, None, y)
+    acc, _, status = g.jitter(m0, dW, None, y, st["nll"], st["logG"], st["m"], st["u"], theta, cfg.rho, n_iter,
+                              seed, ctr)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    m0h, yh = m0.double().cpu().numpy(), y.double().cpu().numpy()
+    same = 0
+    for p in (0, 517, N - 1):
+        ref = OF.jitter(om, m0h[p:p + 1], dW0[p:p + 1], None, yh, cfg.sigma, theta, cfg.rho, n_iter, seed, ctr,
+                        particle0=p)
+        if acc[p].item() != ref[5][0]:
+            continue
+        same += 1
+        assert rel_err(dW[p].double().cpu().numpy(), ref[0][0]) < 1e-4
+        assert rel_err(st["u"][p].double().cpu().numpy(), ref[4][0]) < 1e-4
+    assert same >= 2
