@@ -369,7 +369,7 @@ def run_ours(args):
     y_host = [y.cpu().pin_memory() for y in ys]
     mean_host = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
     dg_host = torch.empty(8, dtype=torch.float64).pin_memory()
-    y_dev = torch.empty_like(ys[0])
+    y_dev = [torch.empty_like(ys[0]) for _ in range(2)]
     e2e_steps = min(args.steps, 30)
     f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
     f2.set_state(m0)
@@ -377,14 +377,18 @@ def run_ours(args):
     barrier(ws)
     t0 = time.perf_counter()
     fwd2 = 0
+    y_dev[0].copy_(y_host[0], non_blocking=True)
     for c in range(e2e_steps):
-        y_dev.copy_(y_host[c], non_blocking=True)
-        st = f2.cycle(y_dev, c)
+        def post(c=c):
+            # enqueued by the cycle before it waits for its stages: diagnostics of the analysis,
+            # their copy to the host, and the next step's observations to the device
+            g.diagnostics(f2.u_end, truths[c], ws=diag_ws, out=diag_out)
+            mean_host.copy_(diag_ws, non_blocking=True)
+            dg_host.copy_(diag_out, non_blocking=True)
+            if c + 1 < e2e_steps:
+                y_dev[(c + 1) % 2].copy_(y_host[c + 1], non_blocking=True)
+        st = f2.cycle(y_dev[c % 2], c, post=post)   # returns once its stages and post's work are done
         f2.advance()
-        g.diagnostics(f2.u_end, truths[c], ws=diag_ws, out=diag_out)
-        mean_host.copy_(diag_ws, non_blocking=True)
-        dg_host.copy_(diag_out, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
         fwd2 += st.forward_steps
     e2e_s = reduce_max(time.perf_counter() - t0, ws)
     e2e_val = reduce_sum(float(fwd2), ws) / e2e_s

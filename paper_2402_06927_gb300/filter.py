@@ -134,9 +134,14 @@ class EnsembleFilter:
         self._gather_all()
 
     def cycle(self, y: torch.Tensor, cycle: int, max_stages: int = 64,
-              timer: Optional[KernelTimer] = None, dW: Optional[torch.Tensor] = None) -> CycleStats:
+              timer: Optional[KernelTimer] = None, dW: Optional[torch.Tensor] = None,
+              post=None) -> CycleStats:
         """One assimilation cycle.  ``dW`` (optional) supplies the window increments
-        (e.g. the ones revealed by pf_nudge); otherwise they are drawn from the prior."""
+        (e.g. the ones revealed by pf_nudge); otherwise they are drawn from the prior.
+        ``post`` (optional, no arguments) enqueues work on the analysis ensemble, such as
+        diagnostics and their copy to the host, on the current stream.  It is called right
+        after the device-gated stages are enqueued, before the cycle waits for them, and
+        again after any later stage, so the work it enqueued last sees the final analysis."""
         m = self.model
         st = CycleStats()
         if not (y.is_cuda and y.dtype == m.dtype and y.numel() == m.M and y.is_contiguous()):
@@ -195,6 +200,8 @@ class EnsembleFilter:
                     setattr(self, nm, n2)
                     self._b[nm] = c
             st.launches += S * 4
+            if post is not None:
+                post()
             n0 = len(timer.pairs) if timer is not None else 0
             if timer is not None:
                 timer.pairs.extend(pairs)
@@ -230,6 +237,10 @@ class EnsembleFilter:
             if k == 0:
                 st.ess0 = float(self.tout_host[3])
             k += 1
+        if post is not None and (self.eager_stages == 0 or len(st.stages) > min(self.eager_stages, max_stages)):
+            # stages after the gated ones (or no gated ones): the work runs on the final analysis
+            post()
+            torch.cuda.current_stream().synchronize()
         st.accepts = self.accepts
         return st
 

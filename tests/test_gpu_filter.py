@@ -192,7 +192,11 @@ def test_gated_stages_equal_stage_by_stage_fp32(nudged):
             lam = torch.tensor(random_drift(cfg, N, 60 + c, scale=0.2), dtype=torch.float32, device="cuda")
             for f in fs:
                 f.set_drift(lam)
-        sts = [f.cycle(y, c) for f in fs]
+        snaps = [[], []]
+        sts = [f.cycle(y, c, post=lambda f=f, k=k: snaps[k].append(f.u_end.clone())) for k, f in enumerate(fs)]
+        # the work a cycle's post hook enqueued last sees the final analysis
+        for k, f in enumerate(fs):
+            assert snaps[k] and torch.equal(snaps[k][-1], f.u_end)
         assert [(s.dtheta, s.ess, s.theta) for s in sts[0].stages] == [(s.dtheta, s.ess, s.theta) for s in sts[1].stages]
         assert sts[0].forward_steps == sts[1].forward_steps
         for name in names:
