@@ -77,6 +77,9 @@ JITTER_TRAFFIC_BYTES = {
     "fffa6c0bddf68b535b57adff1b518f66dc04a74e": 4611840,
     # with the Matern adjoint and nudging declarations in sch_internal.h: 4.611840 MB read, 0 written
     "a333a572af81817824d9debd3df0fe94d9cf5baa": 4611840,
+    # wjitter_kernel<8,2,1,2>, specialised to a diagonal Picard and a PCR Helmholtz reduced
+    # solve: 4.609792 MB read, 0 written
+    "9a63bdc05dd81bd373a067cd982f7c3df6d28ae3": 4609792,
 }
 
 
@@ -289,7 +292,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     cfg = get_config(args.workload)
-    g = SchModel.from_config(cfg)
+    g = SchModel.from_config(cfg, layout=args.layout)
     N = cfg.N
     seed = 1000 + rank          # independent replicas on each rank
     total_cycles = args.warmup + args.steps
@@ -411,13 +414,15 @@ def run_ours(args):
                                     + f"N={N} Ns={cfg.Ns} M={cfg.M} sigma={cfg.sigma} N*=N/2 "
                                       f"jitter={cfg.n_jitter} rho={cfg.rho} (FP32 fields, FP64 weights)"),
                        "n": cfg.n, "N": N, "Ns": cfg.Ns, "K": cfg.K, "Q": cfg.Q, "M": cfg.M,
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "layout": g.layout,
                        "l2": "flushed between timed steps (256 MB write)",
                        "cycles_per_s": args.steps * ws / dev_s_max,
                        "mean_tempering_stages": statistics.mean(stages),
                        "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
-            "roofline": {"bound": "alu", "kernel": ("wjitter_kernel<8,2> (one warp per particle, EA)" if g.layout == "warp"
+            "roofline": {"bound": "alu", "kernel": (("wmatern_jitter_kernel<8,2,DIAG,PCR,PCR> (one warp per particle, EA)"
+                                     if matern else "wjitter_kernel<8,2,DIAG,PCR> (one warp per particle, EA)")
+                                    if g.layout == "warp"
                                     else (f"matern_jitter_kernel<float,8,128,{solver.upper()}>" if matern
                                           else f"jitter_kernel<float,8,128,{solver.upper()}>")),
                          "achieved": achieved, "peak": peak,
@@ -913,6 +918,8 @@ def main():
                     help="filter workload of the main run: cfg2_f32 (mode-expansion noise, the headline) "
                          "or cfg2m_f32 (the paper's Matern noise)")
     ap.add_argument("--mala-h", type=float, default=None, help="MALA step size h (--mala)")
+    ap.add_argument("--layout", default="auto", choices=["auto", "warp", "cta"],
+                    help="kernel layout of the filter's propagation (FP32 EA: warp per particle or CTA)")
     ap.add_argument("--matern", action="store_true", help="--adjoint on the Matern noise (cfg3m_f64)")
     ap.add_argument("--exp1", action="store_true",
                     help="Exp 1: bootstrap vs tempering + jittering filters over --da-steps assimilation steps")

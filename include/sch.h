@@ -72,7 +72,7 @@ enum { SCH_SOLVER_AUTO = 0, SCH_SOLVER_LI = 1, SCH_SOLVER_EA = 2 };
  *   SCH_LAYOUT_WARP  one warp per particle, packed f32x2 arithmetic: float
  *                    fields, the SCH_SOLVER_EA solver and n = 256, 512 or 1024
  *                    only (sch_create returns SCH_ERR_UNSUPPORTED otherwise);
- *   SCH_LAYOUT_AUTO  WARP where it applies (not for the Matern noise), else CTA.
+ *   SCH_LAYOUT_AUTO  WARP where it applies (with either noise model), else CTA.
  * Both compute the same iteration; results agree to rounding. */
 enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
 
@@ -86,8 +86,8 @@ enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
  *                     (U_j, v) + kappa^-2 (U_j', v') = eta (dW_h, v) for j = 1,
  *                     (U_{j-1}, v) after, dU = U_k; Q = n.  The drift lambda is a
  *                     DG0 field added to dW (dW_c + lambda_c dt).  Default solver
- *                     of the precision; CTA layout unless SCH_LAYOUT_WARP is asked
- *                     for (FP32, n = 256, 512, 1024).  The adjoint, nudging and MALA
+ *                     of the precision; the warp layout where it fits (FP32,
+ *                     n = 256, 512, 1024) unless SCH_LAYOUT_CTA is asked for.  The adjoint, nudging and MALA
  *                     entry points take it: gradients and drifts per cell, and pf_nudge
  *                     keeps the optimiser's vectors in its workspace.
  * Every noise array dW, lambda of this API is [N][nsteps][Q]. */

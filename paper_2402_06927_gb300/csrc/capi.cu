@@ -373,10 +373,8 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     }
     const bool warp_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && (p.n == 256 || p.n == 512 || p.n == 1024);
     if (p.layout == SCH_LAYOUT_WARP && !warp_fits) return SCH_ERR_UNSUPPORTED;
-    // the Matern noise runs in the CTA layout unless the warp layout is asked for: its
-    // jitter draws n normals per step, which a warp per particle generates at a quarter of
-    // the CTA layout's occupancy (20.7M against 40.0M particle-timesteps/s at n = 1024)
-    const bool warp_ok = warp_fits && (matern ? p.layout == SCH_LAYOUT_WARP : p.layout != SCH_LAYOUT_CTA);
+    // one warp per particle wherever it fits, with either noise model
+    const bool warp_ok = warp_fits && p.layout != SCH_LAYOUT_CTA;
     sch_ctx* c = (sch_ctx*)calloc(1, sizeof(sch_ctx));
     if (!c) return SCH_ERR_ARG;
     c->p = p;

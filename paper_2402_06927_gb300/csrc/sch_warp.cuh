@@ -120,13 +120,18 @@ __device__ __forceinline__ void wsweep(const WTab& T, float2 (&x)[P][CS], float2
         pd[p] = make_float2(T.iBF * fmaf(T.na, x[p][1].x, x[p][0].x), T.iBF * fmaf(T.na, x[p][1].y, x[p][0].y));
 }
 
+// How a kernel solves a table's reduced system: by its diag flag at run time, or
+// specialised at launch to the diagonal solve or the PCR (the loop then holds one
+// of the two, which keeps it within the instruction cache)
+constexpr int RED_RUNTIME = 0, RED_DIAG = 1, RED_PCR = 2;
+
 // The cyclic reduced system E_t (t = S l + s) of a constant matrix,
 // D_t = de_t - ae pd_t - ge pd_{t+1}.  Returns the pairs E[p] = (E of sub-chunk
 // p, of p + P) and F[p] likewise (the last and first values of the sub-chunks),
 // and the lane's outer neighbours Ep = E_{S l - 1}, Fn = F_{S (l + 1)}.  A system
 // flagged diagonal (T.diag) is solved as E_t = D_t / B; otherwise an S-row lane
-// partition feeds a cyclic PCR over the lanes.
-template <int P>
+// partition feeds a cyclic PCR over the lanes.  RM: one of RED_*.
+template <int P, int RM = RED_RUNTIME>
 __device__ __forceinline__ void wreduced(const WTab& T, const RTab<float>& Q, const float2 (&pd)[P],
                                          const float2 (&de)[P], float2 (&E)[P], float2 (&F)[P], float& Ep,
                                          float& Fn) {
@@ -140,7 +145,8 @@ __device__ __forceinline__ void wreduced(const WTab& T, const RTab<float>& Q, co
         dr[p] = de[p].x;
         dr[p + P] = de[p].y;
     }
-    if (T.diag) {
+    const bool diag = (RM == RED_DIAG) || (RM == RED_RUNTIME && T.diag);
+    if (diag) {
         const float pdn = __shfl_sync(FULL, pr[0], (lane + 1) & 31);
 #pragma unroll
         for (int r = 0; r < S; ++r)
@@ -184,7 +190,7 @@ __device__ __forceinline__ void wsolved_halo(const float2 (&E)[P], const float2 
 }
 
 // u = H^{-1} M m for this lane's nodes
-template <int CS, int P>
+template <int CS, int P, int HM = RED_RUNTIME>
 __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][CS], float2 (&u)[P][CS]) {
     float2 lo, hi, x[P][CS];
     whalo<CS, P>(m, lo, hi);
@@ -197,7 +203,7 @@ __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][C
     float2 pd[P], de[P], E[P], F[P];
     float Ep, Fn;
     wsweep<CS, P>(W.hel, x, pd, de);
-    wreduced<P>(W.hel, W.rhel, pd, de, E, F, Ep, Fn);
+    wreduced<P, HM>(W.hel, W.rhel, pd, de, E, F, Ep, Fn);
     wback<CS, P>(W.hel, x, F, E, u);
 }
 
@@ -249,7 +255,8 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* w
 // One implicit-midpoint step of this warp's particle: (m, u) in/out, W0 holding the
 // step's dU/4 at the lane's nodes on entry.
 // R0sm: this warp's [P][CS][32] float2 scratch for R0 = (M - mu dt/2 K) m0.
-template <int CS, int P>
+// PM, HM: how the Picard and Helmholtz reduced systems are solved (RED_*).
+template <int CS, int P, int PM = RED_RUNTIME, int HM = RED_RUNTIME>
 __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
                                            float2 (&u)[P][CS], float2* R0sm, float2 (&W0)[P][CS], int& iters,
                                            int& flags) {
@@ -307,7 +314,7 @@ __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArg
         float2 pd[P], de[P], E[P], F[P];
         float Ep, Fn;
         wsweep<CS, P>(W.pic, x, pd, de);
-        wreduced<P>(W.pic, W.rpic, pd, de, E, F, Ep, Fn);
+        wreduced<P, PM>(W.pic, W.rpic, pd, de, E, F, Ep, Fn);
         float2 mn[P][CS];
         wback<CS, P>(W.pic, x, F, E, mn);
         float dmax = 0.f, mmax = 0.f;
@@ -333,7 +340,7 @@ __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArg
             float2 hpd[P], hde[P], hE[P], hF[P];
             float hEp, hFn;
             wsweep<CS, P>(W.hel, x, hpd, hde);
-            wreduced<P>(W.hel, W.rhel, hpd, hde, hE, hF, hEp, hFn);
+            wreduced<P, HM>(W.hel, W.rhel, hpd, hde, hE, hF, hEp, hFn);
             wback<CS, P>(W.hel, x, hF, hE, u);
         }
         iters++;
@@ -357,13 +364,13 @@ __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArg
 }
 
 // One step with the mode-expansion noise of the step's K weights wq.
-template <int CS, int P>
+template <int CS, int P, int PM, int HM>
 __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
                                       float2 (&u)[P][CS], float2* R0sm, const float* wq, const float2 (&s1)[P],
                                       const float2 (&c1)[P], int& iters, int& flags) {
     float2 W0[P][CS];
     wnoise<CS, P>(A, wq, s1, c1, W0);
-    wstep_core<CS, P>(A, W, m, u, R0sm, W0, iters, flags);
+    wstep_core<CS, P, PM, HM>(A, W, m, u, R0sm, W0, iters, flags);
 }
 
 // this lane's LN = 2 P CS nodes of a particle row <-> the paired registers:
@@ -447,7 +454,7 @@ __host__ __device__ constexpr size_t wsmem_base() {
 // Occupancy: 8 one-warp CTAs per SM (255 registers a thread)
 constexpr int WMINB = 8;
 
-template <int CS, int P>
+template <int CS, int P, int PM, int HM>
 __global__ void __launch_bounds__(32, WMINB) wwindow_kernel(ModelArgs<float> A, WArgs W, WindowIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* R0sm = reinterpret_cast<float2*>(smem_raw);
@@ -459,10 +466,10 @@ __global__ void __launch_bounds__(32, WMINB) wwindow_kernel(ModelArgs<float> A, 
     wangles<CS, P>(A.n, s1, c1);
     float2 m[P][CS], u[P][CS];
     wload<CS, P>(io.m_in + (size_t)p * A.n, m);
-    wu_from_m<CS, P>(W, m, u);
+    wu_from_m<CS, P, HM>(W, m, u);
     __syncwarp();
     int iters = 0, flags = 0;
-    for (int s = 0; s < io.Ns; ++s) wstep<CS, P>(A, W, m, u, R0sm, noise + s * A.K, s1, c1, iters, flags);
+    for (int s = 0; s < io.Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * A.K, s1, c1, iters, flags);
     wstore<CS, P>(io.m_out + (size_t)p * A.n, m);
     wstore<CS, P>(io.u_out + (size_t)p * A.n, u);
     if (io.y) {
@@ -482,7 +489,7 @@ __global__ void __launch_bounds__(32, WMINB) wwindow_kernel(ModelArgs<float> A, 
 // PCN jittering (Sec. 3.1.2): n_iter proposals dW' = rho dW + sqrt(1 - rho^2)
 // sqrt(dt) z of the window noise, each run through the window from m_start
 // and accepted with probability min(1, exp(w0 - w1)), w = theta (NLL - log G).
-template <int CS, int P>
+template <int CS, int P, int PM, int HM>
 __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, WArgs W, JitterIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* R0sm = reinterpret_cast<float2*>(smem_raw);
@@ -521,10 +528,10 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
         stage_noise(A, noise, prop, lam, Ns);
         float2 m[P][CS], u[P][CS];
         wload<CS, P>(io.m_start + (size_t)p * A.n, m);
-        wu_from_m<CS, P>(W, m, u);
+        wu_from_m<CS, P, HM>(W, m, u);
         __syncwarp();
         int fl = 0;
-        for (int s = 0; s < Ns; ++s) wstep<CS, P>(A, W, m, u, R0sm, noise + s * K, s1, c1, iters, fl);
+        for (int s = 0; s < Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * K, s1, c1, iters, fl);
         const double mis = warp_sum(wmisfit<CS, P>(A, u, io.y));
         const double gl = warp_sum(window_girsanov(A, prop, lam, Ns));
         const double nll1 = 0.5 * mis, lg1 = -gl;

@@ -17,20 +17,39 @@ void prep(Kern k, size_t sm) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
+template <int CS, int P, int PM, int HM>
+int window_rm(const ModelArgs<float>& A, const WArgs& W, const WindowIO<float>& io, int N, cudaStream_t st) {
+    const size_t sm = smem_of<CS, P>(io.Ns, A.K, 1);
+    prep(wwindow_kernel<CS, P, PM, HM>, sm);
+    wwindow_kernel<CS, P, PM, HM><<<N, 32, sm, st>>>(A, W, io);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+template <int CS, int P, int PM, int HM>
+int jitter_rm(const ModelArgs<float>& A, const WArgs& W, const JitterIO<float>& io, int N, cudaStream_t st) {
+    const size_t sm = smem_of<CS, P>(io.Ns, A.K, 3);
+    prep(wjitter_kernel<CS, P, PM, HM>, sm);
+    wjitter_kernel<CS, P, PM, HM><<<N, 32, sm, st>>>(A, W, io);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+// the kernels specialised to the two tables' reduced solves (diagonal or PCR)
 template <int CS, int P>
 int window(const ModelArgs<float>& A, const WArgs& W, const WindowIO<float>& io, int N, cudaStream_t st) {
-    const size_t sm = smem_of<CS, P>(io.Ns, A.K, 1);
-    prep(wwindow_kernel<CS, P>, sm);
-    wwindow_kernel<CS, P><<<N, 32, sm, st>>>(A, W, io);
-    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    if (W.pic.diag)
+        return W.hel.diag ? window_rm<CS, P, RED_DIAG, RED_DIAG>(A, W, io, N, st)
+                          : window_rm<CS, P, RED_DIAG, RED_PCR>(A, W, io, N, st);
+    return W.hel.diag ? window_rm<CS, P, RED_PCR, RED_DIAG>(A, W, io, N, st)
+                      : window_rm<CS, P, RED_PCR, RED_PCR>(A, W, io, N, st);
 }
 
 template <int CS, int P>
 int jitter(const ModelArgs<float>& A, const WArgs& W, const JitterIO<float>& io, int N, cudaStream_t st) {
-    const size_t sm = smem_of<CS, P>(io.Ns, A.K, 3);
-    prep(wjitter_kernel<CS, P>, sm);
-    wjitter_kernel<CS, P><<<N, 32, sm, st>>>(A, W, io);
-    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    if (W.pic.diag)
+        return W.hel.diag ? jitter_rm<CS, P, RED_DIAG, RED_DIAG>(A, W, io, N, st)
+                          : jitter_rm<CS, P, RED_DIAG, RED_PCR>(A, W, io, N, st);
+    return W.hel.diag ? jitter_rm<CS, P, RED_PCR, RED_DIAG>(A, W, io, N, st)
+                      : jitter_rm<CS, P, RED_PCR, RED_PCR>(A, W, io, N, st);
 }
 
 }  // namespace

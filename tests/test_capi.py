@@ -134,9 +134,9 @@ def test_create_validates_matern(lib, kw, rc):
     got = lib.sch_create(ct.byref(p), ct.byref(h))
     assert got == rc
     if got == 0:
-        # one Brownian motion per cell; the CTA layout unless the warp layout is asked for
+        # one Brownian motion per cell; the warp layout wherever it fits (FP32 here, n = 256)
         assert lib.sch_noise_dim(h) == p.n
-        assert lib.sch_layout(h) == (2 if p.layout == 2 else 1)
+        assert lib.sch_layout(h) == (2 if p.layout == 2 or (p.layout == 0 and p.dtype == 1) else 1)
         # the entry points built on the adjoint check their arguments; the nudging workspace holds
         # the optimiser's vectors, 17 of nsteps x n doubles, besides the adjoint's region
         assert lib.pf_nudge(h, 1, 5, 0, 10, 1e-6, 1, 0, 0, None, None, None, None, None, None, None, None, 0,

@@ -61,9 +61,12 @@ def test_matern_window_f64(name, N, lam):
 
 
 @pytest.mark.parametrize("name,N", [("cfg2m_f32", 3), ("cfg2m_f32@n=256,M=64", 4), ("cfg2m_f32@n=4096,M=128,Ns=4", 2)])
-def test_matern_window_f32(name, N):
+@pytest.mark.parametrize("layout", ["auto", "cta"])
+def test_matern_window_f32(name, N, layout):
+    # auto: one warp per particle at n = 256 and 1024, the CTA layout at n = 4096
     cfg = _cfg(name)
-    g = gpu_model(cfg)
+    g = gpu_model(cfg, layout=layout)
+    assert g.layout == ("warp" if layout == "auto" and cfg.n <= 1024 else "cta")
     om, m0, dW, la = _case(cfg, N, 31, lam=True)
     ref = om.ensemble_window(m0, dW, la)
     out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
@@ -110,6 +113,41 @@ def test_matern_jitter_matches_oracle(lam):
     assert np.allclose(nll.cpu().numpy(), ref[1], rtol=1e-9)
 
 
+@pytest.mark.parametrize("name,lam,layout", [("cfg2m_f32", False, "warp"), ("cfg2m_f32", True, "cta"),
+                                             ("cfg2m_f32@n=256,M=64", True, "warp")])
+def test_matern_jitter_f32_matches_oracle(name, lam, layout):
+    # the FP32 Matern jitter kernels of both layouts against the FP64 oracle: decisions equal
+    # away from a coin flip, noise and fields to FP32 tolerance (rho = 0.5 and theta = 1, so
+    # that the oracle's chains both accept and reject)
+    cfg = _cfg(name)
+    g = gpu_model(cfg, layout=layout)
+    assert g.layout == layout
+    om = oracle_model(cfg)
+    N, theta, rho = 3, 1.0, 0.5
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 50)])
+    dW = random_increments(cfg, N, 51)
+    la = random_drift(cfg, N, 52, scale=0.2) if lam else None
+    y = random_obs(cfg, 53)
+    n_iter, seed, ctr = 4, 77, 1000
+    ref = OF.jitter(om, m0, dW, la, y, cfg.sigma, theta, rho, n_iter, seed, ctr)
+    dt = g.dtype
+    m0d, dWd, yd = tdev(m0, dt), tdev(dW, dt), tdev(y, dt)
+    lad = None if la is None else tdev(la, dt)
+    st = g.ensemble_step(m0d, dWd, lad, yd)
+    acc, _, status = g.jitter(m0d, dWd, lad, yd, st["nll"], st["logG"], st["m"], st["u"], theta, rho, n_iter,
+                              seed, ctr)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    acc_g = acc.cpu().numpy()
+    same = acc_g == ref[5]
+    assert same.mean() >= 0.6
+    assert 0 < ref[5].sum() < N * n_iter
+    sel = np.where(same)[0]
+    assert rel_err(dWd.double().cpu().numpy()[sel], ref[0][sel]) < 1e-4
+    assert rel_err(st["u"].double().cpu().numpy()[sel], ref[4][sel]) < 1e-4
+    assert np.allclose(st["nll"].cpu().numpy()[sel], ref[1][sel], rtol=1e-3, atol=1e-4)
+
+
 def test_matern_cycle_matches_oracle():
     # a whole assimilation cycle (tempering, resampling, jittering) with the Matern noise
     from paper_2402_06927_gb300.filter import EnsembleFilter
@@ -138,6 +176,7 @@ def test_matern_full_size_sampled():
     # recomputed by the oracle
     cfg = get_config("cfg2m_f32")
     g = gpu_model(cfg)
+    assert g.layout == "warp"
     N = cfg.N
     u0 = random_state(cfg, N, 41)
     m0 = g.m_from_u(tdev(u0, g.dtype))

@@ -133,6 +133,24 @@ def test_window_f32(name, N, layout):
     assert np.all(out["status"].cpu().numpy() == 0)
 
 
+@pytest.mark.parametrize("mu", [0.02, 2.0])
+def test_window_f32_diagonal_helmholtz(mu):
+    # at alpha = h / sqrt(6) the Helmholtz matrix's off-diagonal h/6 - alpha^2/h
+    # vanishes, so its reduced system is diagonal too: with mu = 0.02 (Picard
+    # reduced system diagonal) and mu = 2.0 (coupled) the warp kernels run their
+    # other two reduced-solve specialisations
+    cfg = get_config("cfg2_f32")
+    cfg = dataclasses.replace(cfg, alpha=cfg.L / cfg.n / np.sqrt(6.0), mu=mu)
+    g = gpu_model(cfg, layout="warp")
+    om, m0, dW, la = _case(cfg, 3, 33, lam=True)
+    ref = om.ensemble_window(m0, dW, la)
+    out = g.ensemble_step(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype))
+    torch.cuda.synchronize()
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < F32_TOL
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < F32_TOL
+    assert np.all(out["status"].cpu().numpy() == 0)
+
+
 def test_window_full_size_sampled():
     # the bench configuration (n = 1024, N = 1024, Ns = 10, FP32): every particle
     # is propagated in the launch the bench times; three sampled particles are
