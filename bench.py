@@ -525,9 +525,14 @@ def _adjoint_flops(n, K, N, Ns, it_fwd, it_adj, matern_k=None):
             + n * (ADJ_FLOPS_PER_NODE_ITER * it_adj + (ADJ_FLOPS_PER_NODE_STEP + 2 * mf) * N * Ns))
 
 
+def _ckpt_note(ckpt):
+    return "every state kept, nothing recomputed" if ckpt is None else f"checkpoints every {ckpt} steps"
+
+
 def run_adjoint(args):
     """--adjoint: gradient evaluations on the nudging workload (n = 1024, K = 8,
-    20-step windows, N = 256, FP64, checkpoints every 5 steps).  One evaluation is
+    20-step windows, N = 256, FP64; every state of the window kept from the forward
+    pass, or checkpoints every --ckpt steps).  One evaluation is
     sch_adjoint_window on one particle: the forward window and its reverse-mode
     adjoint, J and dJ/dlambda, dJ/ddW, dJ/dm0.  Inputs resident, L2 flushed
     between timed calls, CUDA events; the oracle's gradient (tangent linear,
@@ -543,7 +548,7 @@ def run_adjoint(args):
     fwd = g.ensemble_step(m0, dW, lam, y)
     ws = None
     for _ in range(max(3, args.warmup)):
-        out = g.adjoint_window(m0, dW, lam, y, ckpt=5)
+        out = g.adjoint_window(m0, dW, lam, y, ckpt=args.ckpt)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     st = torch.cuda.current_stream()
     times = []
@@ -551,7 +556,7 @@ def run_adjoint(args):
         flush.fill_(float(k))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        out = g.adjoint_window(m0, dW, lam, y, ckpt=5)
+        out = g.adjoint_window(m0, dW, lam, y, ckpt=args.ckpt)
         e1.record(st)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -585,7 +590,7 @@ def run_adjoint(args):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "adjoint window: n=1024 " + (f"Matern noise (kappa={cfg.kappa} eta={cfg.eta} "
                                                             f"k={cfg.matern_k}) " if args.matern else "K=8 ")
-                               + "Ns=20 N=256 (FP64, LI Picard, checkpoints every 5 steps)",
+                               + f"Ns=20 N=256 (FP64, LI Picard, {_ckpt_note(args.ckpt)})",
                    "l2": "flushed between timed calls (256 MB write)",
                    "forward_picard_iters_per_step": it_fwd / (N * Ns), "adjoint_iters_per_step": it_adj / (N * Ns)},
         "roofline": {"bound": "alu",
@@ -606,7 +611,7 @@ MALA_THETA, MALA_H, MALA_ITERS = 1.0, 0.5, 10
 
 def run_mala(args):
     """--mala: MALA jitter on the nudging workload (n = 1024, K = 8, 20-step windows,
-    N = 256, FP64, checkpoints every 5 steps) at theta = 1.  One timed step is one
+    N = 256, FP64, the adjoint keeping every state, or checkpoints every --ckpt steps) at theta = 1.  One timed step is one
     SchModel.mala_jitter call of MALA_ITERS moves per particle: the initial gradient,
     then per move pf_mala_propose, the adjoint window at the proposal and
     pf_mala_accept, and the final window.  Inputs resident, L2 flushed before each
@@ -624,7 +629,7 @@ def run_mala(args):
     S, theta, h = MALA_ITERS, MALA_THETA, (MALA_H if args.mala_h is None else args.mala_h)
 
     def call(k):
-        return g.mala_jitter(m0, dW, lam, y, theta, h, S, 31, 1000 * k, ckpt=5)
+        return g.mala_jitter(m0, dW, lam, y, theta, h, S, 31, 1000 * k, ckpt=args.ckpt)
 
     for k in range(max(3, args.warmup)):
         dW.copy_(dW0)
@@ -645,10 +650,11 @@ def run_mala(args):
     t = statistics.median(times)
     assert int(out["status"].abs().sum().item()) == 0, "window status flags"
     # parts: the adjoint window (dominant), proposal and decision kernels, each alone
-    ws = torch.empty(int(g.adjoint_workspace_bytes(N, Ns, 5)), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(int(g.adjoint_workspace_bytes(N, Ns, args.ckpt)), dtype=torch.uint8, device="cuda")
     fwd = g.ensemble_step(m0, dW0, lam, y)
-    adj = g.adjoint_window(m0, dW0, lam, y, ckpt=5, want_m0=False, ws=ws)
-    t_adj = _event_time(lambda: g.adjoint_window(m0, dW0, lam, y, ckpt=5, want_m0=False, ws=ws), 5, flush)
+    adj = g.adjoint_window(m0, dW0, lam, y, ckpt=args.ckpt, want_m0=False, ws=ws)
+    t_adj = _event_time(lambda: g.adjoint_window(m0, dW0, lam, y, ckpt=args.ckpt, want_m0=False, ws=ws), 5,
+                        flush)
     dWp, Jp, gJp = torch.empty_like(dW0), adj["J"].clone(), adj["g_dW"].clone()
     J, gJ, dWc = adj["J"].clone(), adj["g_dW"].clone(), dW0.clone()
     t_prop = _event_time(lambda: g.mala_propose(dWc, lam, gJ, dWp, theta, h, 31, 0), 20, flush)
@@ -673,8 +679,8 @@ def run_mala(args):
         "metric": "MALA moves/s", "value": N * S / t, "unit": "MALA moves/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t, "higher_is_better": True,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"MALA jitter: n=1024 K=8 Ns=20 N=256 (FP64, LI Picard, checkpoints every 5 "
-                               f"steps), {S} moves per call, theta={theta}, h={h}",
+        "config": {"workload": f"MALA jitter: n=1024 K=8 Ns=20 N=256 (FP64, LI Picard, {_ckpt_note(args.ckpt)}), "
+                               f"{S} moves per call, theta={theta}, h={h}",
                    "l2": "flushed between timed calls (256 MB write)",
                    "acceptance": acc / (N * S * args.steps),
                    "adjoint_ms": 1e3 * t_adj, "propose_us": 1e6 * t_prop, "accept_us": 1e6 * t_acc,
@@ -921,6 +927,8 @@ def main():
     ap.add_argument("--layout", default="auto", choices=["auto", "warp", "cta"],
                     help="kernel layout of the filter's propagation (FP32 EA: warp per particle or CTA)")
     ap.add_argument("--matern", action="store_true", help="--adjoint on the Matern noise (cfg3m_f64)")
+    ap.add_argument("--ckpt", type=int, default=None,
+                    help="--adjoint, --mala: checkpoint interval of the adjoint (default: keep every state)")
     ap.add_argument("--exp1", action="store_true",
                     help="Exp 1: bootstrap vs tempering + jittering filters over --da-steps assimilation steps")
     ap.add_argument("--da-steps", type=int, default=1000)

@@ -206,10 +206,14 @@ class SchModel:
         return out
 
     def adjoint_window(self, m_start: torch.Tensor, dW: torch.Tensor, lam: Optional[torch.Tensor],
-                       y: torch.Tensor, ckpt: int = 5, want_dW: bool = True, want_m0: bool = True,
+                       y: torch.Tensor, ckpt: Optional[int] = None, want_dW: bool = True, want_m0: bool = True,
                        ws: Optional[torch.Tensor] = None):
-        """sch_adjoint_window: J and its gradients for every particle."""
+        """sch_adjoint_window: J and its gradients for every particle.  ckpt: the
+        checkpoint interval; None keeps every state of the window from the forward
+        pass (one segment, nothing recomputed), a smaller interval trades
+        recomputation for workspace."""
         N, nsteps, K = dW.shape
+        ckpt = _ckpt(ckpt, nsteps)
         _need(m_start, self.dtype, (N, self.n), "m_start")
         _need(dW, self.dtype, (N, nsteps, self.K), "dW")
         _need(y, self.dtype, (self.M,), "y")
@@ -230,12 +234,13 @@ class SchModel:
                                        _ptr(ws), ws.numel() * ws.element_size(), _stream()), "sch_adjoint_window")
         return dict(J=J, g_lam=g_lam, g_dW=g_dW, g_m0=g_m0, iters=iters, status=status)
 
-    def adjoint_workspace_bytes(self, N: int, nsteps: int, ckpt: int = 5) -> int:
+    def adjoint_workspace_bytes(self, N: int, nsteps: int, ckpt: Optional[int] = None) -> int:
         """Bytes of the workspace sch_adjoint_window needs for N particles."""
-        return int(lib().sch_adjoint_workspace_bytes(self._h, N, nsteps, ckpt))
+        return int(lib().sch_adjoint_workspace_bytes(self._h, N, nsteps, _ckpt(ckpt, nsteps)))
 
     def mala_jitter(self, m_start: torch.Tensor, dW: torch.Tensor, lam: Optional[torch.Tensor], y: torch.Tensor,
-                    theta: float, h: float, n_iter: int, seed: int, ctr: int, particle0: int = 0, ckpt: int = 5):
+                    theta: float, h: float, n_iter: int, seed: int, ctr: int, particle0: int = 0,
+                    ckpt: Optional[int] = None):
         """n_iter MALA moves of every particle's window noise at temperature theta, updating dW in
         place: pf_mala_propose, sch_adjoint_window at the proposal, pf_mala_accept (iteration j
         keyed ctr + j).  The window is then run once at the final noise.
@@ -271,10 +276,12 @@ class SchModel:
                                    _stream()), "pf_mala_accept")
 
     def nudge(self, m_start: torch.Tensor, y: torch.Tensor, nsteps: int, mode: str = "sequential",
-              max_iter: int = 50, gtol: float = 1e-8, ckpt: int = 5, seed: int = 0, ctr: int = 0,
+              max_iter: int = 50, gtol: float = 1e-8, ckpt: Optional[int] = None, seed: int = 0, ctr: int = 0,
               lam0: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None):
-        """pf_nudge: L-BFGS nudging drifts and the revealed increments for every particle."""
+        """pf_nudge: L-BFGS nudging drifts and the revealed increments for every particle
+        (ckpt as in adjoint_window)."""
         N = m_start.shape[0]
+        ckpt = _ckpt(ckpt, nsteps)
         _need(m_start, self.dtype, (N, self.n), "m_start")
         _need(y, self.dtype, (self.M,), "y")
         dev = m_start.device
@@ -400,6 +407,11 @@ def pf_resample_workspace_bytes(N: int, row_bytes_total: int) -> int:
     return int(lib().pf_resample_workspace_bytes(N, row_bytes_total))
 
 
+def _ckpt(ckpt: Optional[int], nsteps: int) -> int:
+    """The adjoint's checkpoint interval: None is the whole window (every state kept)."""
+    return max(1, nsteps) if ckpt is None else ckpt
+
+
 class NudgingCost(torch.autograd.Function):
     """J(m_start, dW, lambda) = NLL(u_end) + 1/2 dt sum lambda^2 per particle, with the
     hand-written adjoint (sch_adjoint_window) as its backward.
@@ -410,7 +422,7 @@ class NudgingCost(torch.autograd.Function):
     """
 
     @staticmethod
-    def forward(ctx, model: SchModel, m_start, dW, lam, y, ckpt: int = 5):
+    def forward(ctx, model: SchModel, m_start, dW, lam, y, ckpt: Optional[int] = None):
         out = model.adjoint_window(m_start.contiguous(), dW.contiguous(), lam.contiguous(), y.contiguous(), ckpt)
         ctx.save_for_backward(out["g_m0"], out["g_dW"], out["g_lam"])
         return out["J"]

@@ -301,7 +301,10 @@ __device__ __forceinline__ void matern_adjoint_cells(const ModelArgs<R>& A, Shm<
 // --------------------------------------------------------------------------
 // Forward window from step n0 (state at `start`) to Ns, storing the state at
 // steps n0, n0 + ck, ... into ckp; returns J = NLL(u_end) + 1/2 dt sum_s sum_k
-// lam^2 (all steps) in every thread, and the end state in f.
+// lam^2 (all steps) in every thread, and the end state in f.  segst (may be null):
+// when the window is one segment (ck >= Ns - n0), every state (m, u) is also stored
+// there in backward_ck's segment layout, so that the reverse sweep need not
+// recompute it.
 // noise: the weights a_j/4 (dW + lam dt) of all Ns steps (staged by the caller); with
 // the Matern noise (NZ) an n-value buffer for one step's cell weights, formed here from
 // dW and lam.
@@ -309,8 +312,13 @@ __device__ __forceinline__ void matern_adjoint_cells(const ModelArgs<R>& A, Shm<
 template <typename R, int C, int TP, int S, int NZ = SCH_NOISE_MODES>
 __device__ __forceinline__ double forward_ck(const ModelArgs<R>& A, Shm<R, TP>* sh, R* noise, const R* start,
                                              int n0, int Ns, int ck, R* ckp, const R* lam, const R* y, R s0, R c0,
-                                             Field<R, C>& f, int& iters, int& flags, const R* dW = nullptr) {
+                                             Field<R, C>& f, int& iters, int& flags, const R* dW = nullptr,
+                                             R* segst = nullptr) {
     field_start<R, C, TP>(A, sh, start, f);
+    if (segst) {
+        store_field<R, C>(segst, f.m);
+        store_field<R, C>(segst + A.n, f.u);
+    }
     for (int s = n0; s < Ns; ++s) {
         if ((s - n0) % ck == 0) store_field<R, C>(ckp + (size_t)((s - n0) / ck) * A.n, f.m);
         if constexpr (NZ == SCH_NOISE_MATERN) {
@@ -318,6 +326,10 @@ __device__ __forceinline__ double forward_ck(const ModelArgs<R>& A, Shm<R, TP>* 
             step_any<S, R, C, TP, NZ>(A, sh, f, noise, s0, c0, iters, flags);
         } else {
             step_any<S, R, C, TP>(A, sh, f, noise + s * A.K, s0, c0, iters, flags);
+        }
+        if (segst) {
+            store_field<R, C>(segst + (size_t)(s - n0 + 1) * 2 * A.n, f.m);
+            store_field<R, C>(segst + (size_t)(s - n0 + 1) * 2 * A.n + A.n, f.u);
         }
     }
     double mis = chunk_misfit<R, C>(A, f.u, y);
@@ -335,14 +347,15 @@ __device__ __forceinline__ double forward_ck(const ModelArgs<R>& A, Shm<R, TP>* 
 // --------------------------------------------------------------------------
 // Reverse sweep after forward_ck: dJ/dlambda for steps [v0, v1) into
 // glam[(s - v0) K + k] (and dJ/d dW into gdw when non-null), dJ/dm(n0) into g.
-// glam, gdw: any address space, written by threads k < K.
+// glam, gdw: any address space, written by threads k < K.  seg_ready: forward_ck
+// stored the window's states in seg (one segment), so none is recomputed.
 // --------------------------------------------------------------------------
 template <typename R, int C, int TP, int S, typename GL, typename GW, int NZ = SCH_NOISE_MODES>
 __device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* sh, R* noise, int n0, int Ns,
                                             int ck, const R* ckp, R* seg, const R* lam, const R* y, R s0, R c0,
                                             R s1, R c1, const Field<R, C>& fend, int v0, int v1, double* red,
                                             GL glam, GW gdw, R (&g)[C], int& iters, int& flags,
-                                            const R* dW = nullptr) {
+                                            const R* dW = nullptr, bool seg_ready = false) {
     const int t = threadIdx.x;
     const int i0 = t * C;
     const int K = A.K;
@@ -362,20 +375,22 @@ __device__ __forceinline__ void backward_ck(const ModelArgs<R>& A, Shm<R, TP>* s
     for (int k = ncp - 1; k >= 0; --k) {
         const int sa = n0 + k * ck;
         const int sb = min(sa + ck, Ns);
-        Field<R, C> h;
-        int dummy_it = 0, dummy_fl = 0;
-        field_start<R, C, TP>(A, sh, ckp + (size_t)k * A.n, h);
-        store_field<R, C>(seg, h.m);
-        store_field<R, C>(seg + A.n, h.u);
-        for (int s = sa; s < sb; ++s) {
-            if constexpr (NZ == SCH_NOISE_MATERN) {
-                matern_stage_step<R, C>(A, noise, dW, lam, s);
-                step_any<S, R, C, TP, NZ>(A, sh, h, noise, s0, c0, dummy_it, dummy_fl);
-            } else {
-                step_any<S, R, C, TP>(A, sh, h, noise + s * K, s0, c0, dummy_it, dummy_fl);
+        if (!(seg_ready && ncp == 1)) {
+            Field<R, C> h;
+            int dummy_it = 0, dummy_fl = 0;
+            field_start<R, C, TP>(A, sh, ckp + (size_t)k * A.n, h);
+            store_field<R, C>(seg, h.m);
+            store_field<R, C>(seg + A.n, h.u);
+            for (int s = sa; s < sb; ++s) {
+                if constexpr (NZ == SCH_NOISE_MATERN) {
+                    matern_stage_step<R, C>(A, noise, dW, lam, s);
+                    step_any<S, R, C, TP, NZ>(A, sh, h, noise, s0, c0, dummy_it, dummy_fl);
+                } else {
+                    step_any<S, R, C, TP>(A, sh, h, noise + s * K, s0, c0, dummy_it, dummy_fl);
+                }
+                store_field<R, C>(seg + (size_t)(s - sa + 1) * 2 * A.n, h.m);
+                store_field<R, C>(seg + (size_t)(s - sa + 1) * 2 * A.n + A.n, h.u);
             }
-            store_field<R, C>(seg + (size_t)(s - sa + 1) * 2 * A.n, h.m);
-            store_field<R, C>(seg + (size_t)(s - sa + 1) * 2 * A.n + A.n, h.u);
         }
         for (int s = sb - 1; s >= sa; --s) {
             StepState<R, C> st;
@@ -460,13 +475,15 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) adjoint_kernel(ModelArgs
     R* seg = ckp + (size_t)ncp * A.n;
     int iters = 0, flags = 0;
     Field<R, C> f;
+    // a window of one segment keeps every state from the forward pass
+    const bool one = io.ck >= io.Ns;
     const double J = forward_ck<R, C, TP, S, NZ>(A, sh, noise, io.m_start + (size_t)p * A.n, 0, io.Ns, io.ck, ckp,
-                                                 lamp, io.y, s0, c0, f, iters, flags, dWp);
+                                                 lamp, io.y, s0, c0, f, iters, flags, dWp, one ? seg : nullptr);
     if (threadIdx.x == 0) io.J[p] = J;
     R g[C];
     backward_ck<R, C, TP, S, R*, R*, NZ>(A, sh, noise, 0, io.Ns, io.ck, ckp, seg, lamp, io.y, s0, c0, s1, c1, f, 0,
                                          io.Ns, red, io.g_lam + (size_t)p * NK,
-                                         io.g_dW ? io.g_dW + (size_t)p * NK : (R*)nullptr, g, iters, flags, dWp);
+                                         io.g_dW ? io.g_dW + (size_t)p * NK : (R*)nullptr, g, iters, flags, dWp, one);
     if (io.g_m0) store_field<R, C>(io.g_m0 + (size_t)p * A.n, g);
     if (threadIdx.x == 0) {
         if (io.iters) io.iters[p] = iters;
@@ -589,6 +606,9 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
         const int n0 = (io.mode == NUDGE_OPEN_LOOP) ? 0 : stage;
         const int v0 = n0, v1 = (io.mode == NUDGE_OPEN_LOOP) ? Ns : n0 + 1;
         const int nv = (v1 - v0) * K;
+        // a window of one segment keeps every state from the forward pass (the last
+        // forward before each reverse sweep is the accepted point's)
+        const bool one = ck >= Ns - n0;
         // x <- lambda of the variable steps
         for (int q = t; q < nv; q += TP) vx[q] = (double)laml[v0 * K + q];
         __syncthreads();
@@ -601,10 +621,11 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
         Field<R, C> f;
         set_lambda(vx);
         double J = forward_ck<R, C, TP, S, NZ>(A, sh, noise, start, n0, Ns, ck, ckp, laml, io.y, s0, c0, f, iters,
-                                               flags, dWl);
+                                               flags, dWl, one ? seg : nullptr);
         R gm[C];
         backward_ck<R, C, TP, S, double*, double*, NZ>(A, sh, noise, n0, Ns, ck, ckp, seg, laml, io.y, s0, c0, s1, c1,
-                                                       f, v0, v1, red, vg, (double*)nullptr, gm, iters, flags, dWl);
+                                                       f, v0, v1, red, vg, (double*)nullptr, gm, iters, flags, dWl,
+                                                       one);
         __syncthreads();
         int hist = 0, head = 0;
         double gamma = 1.0;
@@ -648,7 +669,7 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
                 __syncthreads();
                 set_lambda(vxt);
                 Jt = forward_ck<R, C, TP, S, NZ>(A, sh, noise, start, n0, Ns, ck, ckp, laml, io.y, s0, c0, f, iters,
-                                                 flags, dWl);
+                                                 flags, dWl, one ? seg : nullptr);
                 if (Jt <= J + 1e-4 * step * gd) {
                     ok = true;
                     break;
@@ -661,7 +682,7 @@ __global__ void __launch_bounds__(TP, OccAdj<TP>::minb) nudge_kernel(ModelArgs<R
             }
             backward_ck<R, C, TP, S, double*, double*, NZ>(A, sh, noise, n0, Ns, ck, ckp, seg, laml, io.y, s0, c0, s1,
                                                            c1, f, v0, v1, red, vgt, (double*)nullptr, gm, iters, flags,
-                                                           dWl);
+                                                           dWl, one);
             __syncthreads();
             // history update s = xt - x, y = gt - g
             for (int q = t; q < nv; q += TP) {

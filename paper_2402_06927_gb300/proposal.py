@@ -57,7 +57,7 @@ def generate_pairs(g: SchModel, N: int, Ns: int, cycles: int, seed: int, u0: tor
     for c in range(cycles):
         y = twin.ys[c]
         u_start = g.u_from_m(f.m_start)
-        nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter, gtol=gtol, ckpt=5, seed=seed,
+        nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter, gtol=gtol, seed=seed,
                      ctr=1_000_000 + c)
         U.append(u_start.float())
         Y.append(y.float()[None].expand(N, -1).contiguous())
@@ -127,7 +127,7 @@ def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycl
             if source == "hybrid":
                 lam0 = net.forward(g.u_from_m(f.m_start), y).to(g.dtype)
             nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter if source == "optimiser" else refine,
-                         gtol=gtol, ckpt=5, seed=seed, ctr=1_000_000 + c, lam0=lam0)
+                         gtol=gtol, seed=seed, ctr=1_000_000 + c, lam0=lam0)
             f.set_drift(nd["lam"])
             dW = nd["dW"]
         else:

@@ -224,16 +224,18 @@ def test_matern_layouts_agree_at_full_ensemble_size():
     assert (d_a[same] - d_b[same]).abs().max().item() < 1e-4
 
 
-def test_matern_adjoint_matches_oracle_tangent_linear():
+@pytest.mark.parametrize("ckpt", [2, None])
+def test_matern_adjoint_matches_oracle_tangent_linear(ckpt):
     # the reverse-mode adjoint through the Matern noise map (its transpose: k solves per
-    # step) against the oracle's tangent-linear gradient over all n drifts of every step
+    # step) against the oracle's tangent-linear gradient over all n drifts of every step;
+    # ckpt = 2 recomputes the second segment, None keeps every forward state
     from oracle import nudge as ON
     cfg = get_config("cfg1m_f64")
     g = gpu_model(cfg)
     om, m0, dW, la = _case(cfg, 2, 61, Ns=3, lam=True)
     la = 0.2 * la / 0.3
     y = random_obs(cfg, 64)
-    out = g.adjoint_window(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype), ckpt=2)
+    out = g.adjoint_window(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype), ckpt=ckpt)
     torch.cuda.synchronize()
     assert np.all(out["status"].cpu().numpy() == 0)
     for p in range(2):

@@ -52,13 +52,15 @@ def test_adjoint_matches_oracle_tangent_linear(upto):
         assert rel_err(out["g_lam"][p].cpu().numpy(), grad) < 1e-8
 
 
-@pytest.mark.parametrize("ck", [1, 3, 5])
+@pytest.mark.parametrize("ck", [2, 3, 5, 7, None])
 def test_adjoint_independent_of_checkpoint_interval(ck):
+    # against every state recomputed from a checkpoint per step (ckpt = 1); at ckpt >= 5
+    # (and None) the 5-step window is one segment whose states the forward pass keeps
     cfg = get_config("cfg1_f64")
     g = gpu_model(cfg)
     om, m0, dW, la, y = _setup(cfg, 2, 6, Ns=5)
     args = (tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype))
-    ref = g.adjoint_window(*args, ckpt=5)
+    ref = g.adjoint_window(*args, ckpt=1)
     out = g.adjoint_window(*args, ckpt=ck)
     for k in ("J", "g_lam", "g_dW", "g_m0"):
         assert torch.allclose(out[k], ref[k], rtol=1e-12, atol=1e-14), k
@@ -111,11 +113,13 @@ def _nudge_case():
     return cfg, om, m0, y
 
 
-def test_nudge_open_loop_matches_oracle():
+@pytest.mark.parametrize("ckpt", [2, None])
+def test_nudge_open_loop_matches_oracle(ckpt):
+    # ckpt = 2 recomputes each segment in the reverse sweep; None keeps the forward states
     cfg, om, m0, y = _nudge_case()
     g = gpu_model(cfg)
     out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="open_loop", max_iter=200, gtol=1e-10,
-                  ckpt=2, seed=4, ctr=1)
+                  ckpt=ckpt, seed=4, ctr=1)
     torch.cuda.synchronize()
     lam = out["lam"].cpu().numpy()
     for p in range(2):
@@ -126,11 +130,12 @@ def test_nudge_open_loop_matches_oracle():
         assert np.allclose(out["dW"][p].cpu().numpy(), math.sqrt(cfg.dt) * z, rtol=1e-13, atol=1e-15)
 
 
-def test_nudge_sequential_matches_oracle():
+@pytest.mark.parametrize("ckpt", [2, None])
+def test_nudge_sequential_matches_oracle(ckpt):
     cfg, om, m0, y = _nudge_case()
     g = gpu_model(cfg)
     out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="sequential", max_iter=100, gtol=1e-10,
-                  ckpt=2, seed=3, ctr=7)
+                  ckpt=ckpt, seed=3, ctr=7)
     torch.cuda.synchronize()
     assert np.all(out["status"].cpu().numpy() == 0)
     for p in range(2):
