@@ -8,7 +8,9 @@
 * gradients independent of the checkpoint interval;
 * the L-BFGS drift of both schedules against the oracle's (scipy L-BFGS-B)
   minimiser, and the revealed increments bit-for-bit keyed draws;
-* the torch.autograd.Function wrapper returns the adjoint's gradients.
+* the torch.autograd.Function wrapper returns the adjoint's gradients;
+* the FP32 adjoint, optimiser and MALA against the FP64 oracle (tolerances
+  derived beside those tests).
 """
 import math
 
@@ -166,3 +168,71 @@ def test_mala_jitter_matches_oracle(lam_on):
     assert rel_err(dWd.cpu().numpy(), ref_dW) < 1e-8
     assert np.allclose(out["nll"].cpu().numpy(), ref_nll, rtol=1e-8)
     assert np.allclose(out["logG"].cpu().numpy(), ref_lg, rtol=1e-8, atol=1e-12)
+
+
+# FP32 (explicit-advection Picard, the path the learned proposal's training pairs take).
+# Tolerances: the FP32 Picard iteration stops at 1e-6 relative, which the window's
+# sensitivity amplifies by about ten, so J within 2e-6 and gradients within 2e-5 relative
+# of the FP64 oracle (measured: 8e-8 and 8e-7).  The optimiser stops on FP32 gradients,
+# so its drift is held to 3e-4 of the oracle's minimiser (measured 4e-5); the revealed
+# increments are FP32 normals, within 4e-6 of the FP64 transform, times sqrt(dt).
+@pytest.mark.parametrize("n,M", [(256, 32), (1024, 64)])
+@pytest.mark.parametrize("ckpt", [2, None])
+def test_adjoint_f32_matches_oracle_tangent_linear(n, M, ckpt):
+    cfg = get_config("cfg2_f32", n=n, M=M)
+    g = gpu_model(cfg)
+    om, m0, dW, la, y = _setup(cfg, 2, 5, Ns=4)
+    out = g.adjoint_window(tdev(m0, g.dtype), tdev(dW, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype), ckpt=ckpt)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in range(2):
+        J, grad = ON.cost_and_gradient(om, m0[p], dW[p], la[p], y, cfg.sigma)
+        assert abs(out["J"][p].item() - J) <= 2e-6 * J
+        assert rel_err(out["g_lam"][p].double().cpu().numpy(), grad) < 2e-5
+        assert rel_err(out["g_dW"][p].double().cpu().numpy(), (grad - cfg.dt * la[p]) / cfg.dt) < 2e-5
+
+
+@pytest.mark.parametrize("mode", ["open_loop", "sequential"])
+def test_nudge_f32_matches_oracle(mode):
+    cfg = get_config("cfg2_f32", n=256, M=32, Ns=3)
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, 2, 11)])
+    y = random_obs(cfg, 12)
+    seed, ctr = (4, 1) if mode == "open_loop" else (3, 7)
+    out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode=mode, max_iter=200, gtol=1e-6, seed=seed,
+                  ctr=ctr)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    for p in range(2):
+        if mode == "open_loop":
+            lam, res = ON.nudge_open_loop(om, m0[p], y, cfg.sigma, cfg.Ns, cfg.K, gtol=1e-12)
+            z = ORNG.normals(seed, ORNG.TAG_NUDGE, cfg.K, np.arange(cfg.Ns, dtype=np.uint64), np.uint64(p),
+                             np.uint64(ctr))
+            dW = math.sqrt(cfg.dt) * z
+            assert abs(out["J"][p].item() - res.fun) <= 1e-5 * res.fun
+        else:
+            lam, dW = ON.nudge_sequential(om, m0[p], y, cfg.sigma, cfg.Ns, cfg.K, seed=seed, particle=p, ctr=ctr,
+                                          gtol=1e-12)
+        assert rel_err(out["lam"][p].double().cpu().numpy(), lam) < 3e-4
+        assert np.max(np.abs(out["dW"][p].double().cpu().numpy() - dW)) < 4e-6 * math.sqrt(cfg.dt) * 6
+
+
+@pytest.mark.parametrize("n,M", [(256, 32), (1024, 64)])
+def test_mala_f32_matches_oracle(n, M):
+    # FP32 MALA against the FP64 oracle's: decisions equal away from a coin flip, the noise and
+    # the misfit of the agreeing chains to FP32 tolerance
+    cfg = get_config("cfg2_f32", n=n, M=M)
+    g = gpu_model(cfg)
+    om, m0, dW, la, y = _setup(cfg, 3, 31, Ns=3, lam_scale=0.2)
+    theta, h, n_iter, seed, ctr = 0.7, 0.8, 3, 5, 40
+    ref_dW, ref_nll, ref_lg, ref_acc = OF.mala_jitter(om, m0, dW, la, y, cfg.sigma, theta, h, n_iter, seed, ctr)
+    dWd = tdev(dW, g.dtype)
+    out = g.mala_jitter(tdev(m0, g.dtype), dWd, tdev(la, g.dtype), tdev(y, g.dtype), theta, h, n_iter, seed, ctr)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    assert 0 < ref_acc.sum() < 3 * n_iter
+    same = out["accepts"].cpu().numpy() == ref_acc
+    assert same.sum() >= 2
+    assert rel_err(dWd.double().cpu().numpy()[same], ref_dW[same]) < 1e-5
+    assert np.allclose(out["nll"].cpu().numpy()[same], ref_nll[same], rtol=1e-5)
