@@ -390,7 +390,9 @@ class Model:
         P1 solves of (I - d_xx) give S^3 W_p; the velocity is
         u_truth + scale (a_p S^3 W_p + b_p) with a_p, b_p ~ N(0, 1).
         Returns the momenta m [N, n] and velocities u [N, n].
-        Parity unpinned: it only seeds test ensembles.
+        Pinned to its discrete Fourier symbol: the DFT of S^3 W is
+        h cos(theta/2) M^2 / G^3 times the half-cell-shifted DFT of the cells, with
+        M, G the symbols of the mass matrix and of M + K.
         """
         from oracle import rng
         p = np.arange(N, dtype=np.uint64)

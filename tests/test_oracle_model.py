@@ -279,3 +279,34 @@ def test_exp1_prior_is_positive_and_reproducible():
     mm2, u2 = m.prior_exp1(7, 3, particle0=3)
     assert np.array_equal(u[3:], u2)
     assert np.allclose(np.stack([m.u_from_m(x) for x in mm]), u, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_prior_sample_fourier_symbol(n):
+    # the prior (reading c-13 of Eq. init_solve): u_p = u_truth + s (a_p S^3 W_p + b_p) with W_p
+    # the DG0 field of cell values sqrt(h) z_c.  Its load h/2 (W_{i-1} + W_i) multiplies the
+    # half-cell-shifted cell DFT by h cos(theta/2); each of the three P1 solves of
+    # (U, v) + (U', v') divides by the symbol G = M + K, and the two mass products between
+    # them multiply by M.  So the DFT of S^3 W is h cos(theta/2) M^2 / G^3 times that of W,
+    # checked here through np.fft on the oracle's output and its keyed draws
+    from oracle import rng
+    m = make(n=n)
+    u_truth = np.cos(2 * math.pi * m.x / m.L) + 0.3 * np.sin(6 * math.pi * m.x / m.L)
+    seed, N, scale = 5, 3, 0.05
+    mm, u = m.prior_sample(u_truth, seed, N, scale)
+    z = rng.normals(seed, rng.TAG_INIT, m.n + 2, np.uint64(0), np.arange(N, dtype=np.uint64), np.uint64(0))
+    th = 2 * math.pi * np.arange(n) / n
+    Mh = m.h / 6 * (4 + 2 * np.cos(th))
+    Gh = Mh + (2 - 2 * np.cos(th)) / m.h
+    sym = m.h * np.cos(th / 2) * Mh ** 2 / Gh ** 3
+    for p in range(N):
+        a, b = z[p, n], z[p, n + 1]
+        S3W = (u[p] - u_truth - scale * b) / (scale * a)
+        W_hat = np.exp(-0.5j * th) * np.fft.fft(math.sqrt(m.h) * z[p, :n])
+        U_hat = np.fft.fft(S3W)
+        assert np.allclose(U_hat, sym * W_hat, rtol=0, atol=1e-11 * np.max(np.abs(U_hat)))
+        # the momenta are the velocities' through the Helmholtz relation (pinned above)
+        assert np.allclose(mm[p], m.m_from_u(u[p]), rtol=1e-13, atol=1e-13)
+    # scale 0 gives the truth itself
+    _, u0 = m.prior_sample(u_truth, seed, N, 0.0)
+    assert np.array_equal(u0, np.tile(u_truth, (N, 1)))
