@@ -9,8 +9,12 @@
 namespace sch {
 
 constexpr int TEMPER_CTAS = 8;          // one thread-block cluster
-constexpr int TEMPER_THREADS = 256;
 constexpr int TEMPER_PER_THREAD = 8;    // N <= 8 * 256 * 8 = 16384
+// threads per CTA: 128 up to N = 8 * 128 = 1024 (one particle per thread, every CTA
+// busy), else 256.  The FP64 pipe bounds an evaluation, and every thread's share of
+// the reductions runs on it; above N = 1024 the wider CTA shortens each thread's
+// serial chain of exponentials.
+constexpr int TEMPER_THREADS_SMALL = 128, TEMPER_THREADS_LARGE = 256;
 constexpr int RESAMPLE_THREADS = 1024;
 
 // Adaptive tempering on one cluster of TEMPER_CTAS CTAs: every CTA holds a
@@ -25,6 +29,7 @@ struct TemperShm {
     double minw[8];
 };
 
+template <int TPT>
 __device__ __forceinline__ double cta_min(double v, TemperShm* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -32,16 +37,21 @@ __device__ __forceinline__ double cta_min(double v, TemperShm* sh) {
     if (lane == 0) sh->minw[warp] = v;
     __syncthreads();
     double m = sh->minw[0];
-    for (int w = 1; w < TEMPER_THREADS / 32; ++w) m = fmin(m, sh->minw[w]);
+    for (int w = 1; w < TPT / 32; ++w) m = fmin(m, sh->minw[w]);
     __syncthreads();
     return m;
 }
 
-// ESS (Eq. ess) of the weights w_e = exp(-d phi_e - max), max = -d phi_min;
-// the thread's weights are returned in w, their cluster-wide sum in s1_out
-__device__ __forceinline__ double ess_eval(double d, const double (&phi)[TEMPER_PER_THREAD], int cnt, double phimin,
-                                           TemperShm* sh, int& parity, double& s1_out,
-                                           double (&w)[TEMPER_PER_THREAD]) {
+// The sums S1 = sum w_e and S2 = sum w_e^2 of the weights w_e = exp(-d phi_e - max),
+// max = -d phi_min, over the cluster (ESS = S1^2 / S2, Eq. ess); the thread's weights
+// are returned in w.  Every thread sums the CTAs' partials in rank order, so all CTAs
+// take identical decisions.  (Folding them over 8 lanes with shuffles instead, each
+// lane reading another CTA, measured slower at 256 threads: 216 us against 165 per
+// search at N = 8192.)
+template <int TPT>
+__device__ __forceinline__ void ess_sums(double d, const double (&phi)[TEMPER_PER_THREAD], int cnt, double phimin,
+                                         TemperShm* sh, int& parity, double& S1, double& S2,
+                                         double (&w)[TEMPER_PER_THREAD]) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const double mx = -d * phimin;
@@ -65,7 +75,7 @@ __device__ __forceinline__ double ess_eval(double d, const double (&phi)[TEMPER_
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < TEMPER_THREADS / 32; ++w) {
+        for (int w = 0; w < TPT / 32; ++w) {
             a += sh->warp[0][w];
             b += sh->warp[1][w];
         }
@@ -80,11 +90,12 @@ __device__ __forceinline__ double ess_eval(double d, const double (&phi)[TEMPER_
         t2 += o->part[parity][1];
     }
     parity ^= 1;
-    s1_out = t1;
-    return t1 * t1 / t2;
+    S1 = t1;
+    S2 = t2;
 }
 
-__global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THREADS)
+template <int TPT>
+__global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TPT)
     temper_kernel(int N, const double* __restrict__ nll, const double* __restrict__ logG, double theta,
                   const double* __restrict__ theta_dev, double ess_min, int halving, double* __restrict__ wbar,
                   double* __restrict__ out) {
@@ -108,8 +119,8 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
             return;
         }
     }
-    const int gt = rank * TEMPER_THREADS + threadIdx.x;      // global thread index in the cluster
-    constexpr int STRIDE = TEMPER_CTAS * TEMPER_THREADS;
+    const int gt = rank * TPT + threadIdx.x;                  // global thread index in the cluster
+    constexpr int STRIDE = TEMPER_CTAS * TPT;
     // thread gt owns particles gt, gt + STRIDE, ... (coalesced)
     double phi[TEMPER_PER_THREAD];
     int cnt = 0;
@@ -126,29 +137,32 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
         }
     }
     // cluster-wide minimum of phi
-    double cmin = cta_min(lmin, sh);
+    double cmin = cta_min<TPT>(lmin, sh);
     if (threadIdx.x == 0) sh->part[1][0] = cmin;
     cl.sync();
     double phimin = INFINITY;
     for (int r = 0; r < TEMPER_CTAS; ++r) phimin = fmin(phimin, cl.map_shared_rank(sh, r)->part[1][0]);
     int parity = 0;   // the next evaluation writes parity 0; parity 1 is free again after its barrier
     const double rest = 1.0 - theta;
-    // (ess, s1, wk): the ESS, weight sum and this thread's weights at the
-    // current answer, so that the normalised weights need no further pass
-    double s1, wk[TEMPER_PER_THREAD], wc[TEMPER_PER_THREAD];
-    double ess = ess_eval(rest, phi, cnt, phimin, sh, parity, s1, wk);
-    const double ess_rest = ess;
+    // (s1, s2, wk): the sums and this thread's weights at the current answer, so that
+    // the normalised weights need no further pass.  Whether the whole step passes is
+    // tested as S1^2 >= ess_min S2 (S2 > 0), without a division.
+    double s1, s2, wk[TEMPER_PER_THREAD], wc[TEMPER_PER_THREAD];
+    ess_sums<TPT>(rest, phi, cnt, phimin, sh, parity, s1, s2, wk);
+    const double s1_rest = s1, s2_rest = s2;
     // The largest dtheta with ESS >= ess_min.  ESS(d) falls monotonically in d
     // (its log-derivative is 2 (E_{w^2}[phi] - E_w[phi]) <= 0), so the root of
     // g(d) = ESS(d) - ess_min is bracketed by [0, rest] (g(0) = N - ess_min >= 0)
     // and found by the Illinois variant of regula falsi: the secant point of the
-    // bracket, with the function value at an end kept twice in a row halved,
-    // and a midpoint whenever the bracket failed to halve over three steps.  It
-    // stops at a relative width of 2^-46 and returns the passing end.  A root
-    // below rest 2^-60 (astronomically spread phi) gives rest 2^-60, the
-    // smallest point 60 bisection steps would try.
+    // bracket, with the function value at an end kept twice in a row halved, and a
+    // midpoint whenever the bracket failed to halve over three steps.  It stops at a
+    // relative width of 2^-46 and returns the passing end.  A root below rest 2^-60
+    // (astronomically spread phi) gives rest 2^-60, the smallest point 60 bisection
+    // steps would try.  (Run on S1^2 - ess_min S2 instead, which has the same root and
+    // saves the division, the secant steps needed more evaluations: 85 us against 70
+    // at N = 1024.)
     double d;
-    if (ess >= ess_min) {
+    if (s1 * s1 >= ess_min * s2) {
         d = rest;
     } else if (halving) {
         // the paper's search read literally: halve dtheta until the ESS passes, at most
@@ -156,32 +170,30 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
         d = rest;
         for (int k = 1; k <= 60; ++k) {
             d = ldexp(rest, -k);
-            double sc;
-            ess = ess_eval(d, phi, cnt, phimin, sh, parity, sc, wk);
-            s1 = sc;
-            if (ess >= ess_min) break;
+            ess_sums<TPT>(d, phi, cnt, phimin, sh, parity, s1, s2, wk);
+            if (s1 * s1 >= ess_min * s2) break;
         }
     } else {
-        const double dmin = ldexp(rest, -60);
-        double lo = 0.0, glo = (double)N - ess_min, hi = rest, ghi = ess - ess_min;
+        const double dmin = rest * 0x1.0p-60;
+        double lo = 0.0, glo = (double)N - ess_min, hi = rest, ghi = s1 * s1 / s2 - ess_min;
         double w3 = rest, w2 = rest, w1 = rest;   // bracket widths of the last three steps
         int side = 0;
         for (int it = 0; it < 200; ++it) {
             const double w = hi - lo;
-            if (w <= ldexp(hi, -46) || hi < dmin) break;
+            if (w <= hi * 0x1.0p-46 || hi < dmin) break;
             double c = (lo * ghi - hi * glo) / (ghi - glo);
             if (!(c > lo && c < hi) || w > 0.5 * w3) c = 0.5 * (lo + hi);
             w3 = w2;
             w2 = w1;
             w1 = w;
-            double sc;
-            const double ec = ess_eval(c, phi, cnt, phimin, sh, parity, sc, wc);
-            const double gc = ec - ess_min;
+            double sc, s2c;
+            ess_sums<TPT>(c, phi, cnt, phimin, sh, parity, sc, s2c, wc);
+            const double gc = sc * sc / s2c - ess_min;
             if (gc >= 0.0) {
                 lo = c;
                 glo = gc;
-                ess = ec;
                 s1 = sc;
+                s2 = s2c;
 #pragma unroll
                 for (int e = 0; e < TEMPER_PER_THREAD; ++e) wk[e] = wc[e];
                 if (side == 1) ghi *= 0.5;
@@ -197,9 +209,11 @@ __global__ void __cluster_dims__(TEMPER_CTAS, 1, 1) __launch_bounds__(TEMPER_THR
             d = lo;
         } else {
             d = fmax(hi, dmin);
-            ess = ess_eval(d, phi, cnt, phimin, sh, parity, s1, wk);
+            ess_sums<TPT>(d, phi, cnt, phimin, sh, parity, s1, s2, wk);
         }
     }
+    const double ess = s1 * s1 / s2;
+    const double ess_rest = s1_rest * s1_rest / s2_rest;
 #pragma unroll
     for (int e = 0; e < TEMPER_PER_THREAD; ++e) {
         const int i = gt + e * STRIDE;
@@ -321,8 +335,12 @@ __global__ void copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ d
 
 int launch_temper(int N, const double* nll, const double* logG, double theta, const double* theta_dev,
                   double ess_min, int halving, double* wbar, double* out, cudaStream_t st) {
-    temper_kernel<<<TEMPER_CTAS, TEMPER_THREADS, 0, st>>>(N, nll, logG, theta, theta_dev, ess_min, halving, wbar,
-                                                            out);
+    if (N <= TEMPER_CTAS * TEMPER_THREADS_SMALL)
+        temper_kernel<TEMPER_THREADS_SMALL><<<TEMPER_CTAS, TEMPER_THREADS_SMALL, 0, st>>>(
+            N, nll, logG, theta, theta_dev, ess_min, halving, wbar, out);
+    else
+        temper_kernel<TEMPER_THREADS_LARGE><<<TEMPER_CTAS, TEMPER_THREADS_LARGE, 0, st>>>(
+            N, nll, logG, theta, theta_dev, ess_min, halving, wbar, out);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 
