@@ -512,17 +512,33 @@ def _nudging_inputs(g, cfg):
     return m0, dW, lam, y
 
 
-def _adjoint_flops(n, K, N, Ns, it_fwd, it_adj, matern_k=None):
-    """Algorithmic flops of an adjoint window call.  The noise (and its transpose in the
-    reverse sweep) costs 2K per node and step for the mode expansion; with the Matern
+def _adjoint_flops(n, K, N, Ns, it_fwd, it_adj, matern_k=None, solver="li"):
+    """Algorithmic flops of an adjoint window call.  The forward window is credited with
+    the Picard solver's count (LI for FP64, EA for FP32).  The noise (and its transpose in
+    the reverse sweep) costs 2K per node and step for the mode expansion; with the Matern
     noise the forward noise is matern_flops_per_node(k) and the transposed map the same
     count again (k solves, k - 1 mass products, the B^T stencil)."""
     if matern_k is None:
-        return (step_flops(n, K, "li", it_fwd, N * Ns)
+        return (step_flops(n, K, solver, it_fwd, N * Ns)
                 + n * (ADJ_FLOPS_PER_NODE_ITER * it_adj + (ADJ_FLOPS_PER_NODE_STEP + 2 * K) * N * Ns))
     mf = matern_flops_per_node(matern_k)
-    return (step_flops(n, K, "li", it_fwd, N * Ns, mf)
+    return (step_flops(n, K, solver, it_fwd, N * Ns, mf)
             + n * (ADJ_FLOPS_PER_NODE_ITER * it_adj + (ADJ_FLOPS_PER_NODE_STEP + 2 * mf) * N * Ns))
+
+
+def _nudging_config(args, name):
+    """The nudging workload, on FP32 fields (EA Picard, tolerance 1e-6) with --f32."""
+    from workloads import get_config
+    return get_config(name, dtype="f32", tol=1e-6, max_iter=40) if args.f32 else get_config(name)
+
+
+def _precision(args):
+    """(dtype, solver label, adjoint kernel instantiation, roofline peak, peak note)"""
+    if args.f32:
+        return ("f32", "EA", "float,8,128,EA", fp32_peak_tflops(),
+                "FP32 FMA pipe 152 SMs x 128 lanes x 2 x max SM clock")
+    return ("f64", "LI", "double,4,256,LI", FP64_PEAK_TFLOPS,
+            "FP64 pipe 152 SMs x 2 DFMA lanes x 2 x max SM clock")
 
 
 def _ckpt_note(ckpt):
@@ -541,7 +557,8 @@ def run_adjoint(args):
     from workloads import get_config
     from paper_2402_06927_gb300.api import SchModel
     torch.cuda.set_device(0)
-    cfg = get_config("cfg3m_f64" if args.matern else "cfg3_f64")
+    cfg = _nudging_config(args, "cfg3m_f64" if args.matern else "cfg3_f64")
+    dtype, slabel, kinst, peak, pnote = _precision(args)
     g = SchModel.from_config(cfg)
     N, Ns, K, n = cfg.N, cfg.Ns, cfg.K, cfg.n
     m0, dW, lam, y = _nudging_inputs(g, cfg)
@@ -564,7 +581,8 @@ def run_adjoint(args):
     assert int(out["status"].abs().sum().item()) == 0, "adjoint status flags"
     it_fwd = int(fwd["iters"].sum().item())
     it_adj = int(out["iters"].sum().item()) - it_fwd
-    achieved = _adjoint_flops(n, K, N, Ns, it_fwd, it_adj, cfg.matern_k if args.matern else None) / t / 1e12
+    achieved = _adjoint_flops(n, K, N, Ns, it_fwd, it_adj, cfg.matern_k if args.matern else None,
+                              slabel.lower()) / t / 1e12
     cpu = None
     if not args.no_cpu:
         import numpy as np
@@ -587,19 +605,18 @@ def run_adjoint(args):
     line = {
         "metric": "gradient evaluations/s", "value": N / t, "unit": "gradient evaluations/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t, "higher_is_better": True,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": dtype, "data": "synthetic",
         "config": {"workload": "adjoint window: n=1024 " + (f"Matern noise (kappa={cfg.kappa} eta={cfg.eta} "
                                                             f"k={cfg.matern_k}) " if args.matern else "K=8 ")
-                               + f"Ns=20 N=256 (FP64, LI Picard, {_ckpt_note(args.ckpt)})",
+                               + f"Ns=20 N=256 ({dtype.upper()}, {slabel} Picard, {_ckpt_note(args.ckpt)})",
                    "l2": "flushed between timed calls (256 MB write)",
                    "forward_picard_iters_per_step": it_fwd / (N * Ns), "adjoint_iters_per_step": it_adj / (N * Ns)},
         "roofline": {"bound": "alu",
-                     "kernel": "adjoint_kernel<double,4,256,LI" + (",MATERN>" if args.matern else ">"),
+                     "kernel": f"adjoint_kernel<{kinst}" + (",MATERN>" if args.matern else ">"),
                      "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None,
-                     "peak_note": "FP64 pipe 152 SMs x 2 DFMA lanes x 2 x max SM clock; recomputation from "
-                                  "checkpoints is not credited"},
+                     "peak_note": pnote + "; recomputation from checkpoints is not credited"},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -621,7 +638,8 @@ def run_mala(args):
     from workloads import get_config
     from paper_2402_06927_gb300.api import SchModel
     torch.cuda.set_device(0)
-    cfg = get_config("cfg3_f64")
+    cfg = _nudging_config(args, "cfg3_f64")
+    dtype, slabel, kinst, peak, pnote = _precision(args)
     g = SchModel.from_config(cfg)
     N, Ns, K, n = cfg.N, cfg.Ns, cfg.K, cfg.n
     m0, dW0, lam, y = _nudging_inputs(g, cfg)
@@ -661,7 +679,7 @@ def run_mala(args):
     t_acc = _event_time(lambda: g.mala_accept(dWc, dWp, lam, J, Jp, gJ, gJp, None, theta, h, 31, 0), 20, flush)
     it_fwd = int(fwd["iters"].sum().item())
     it_adj = int(adj["iters"].sum().item()) - it_fwd
-    achieved = _adjoint_flops(n, K, N, Ns, it_fwd, it_adj) / t_adj / 1e12
+    achieved = _adjoint_flops(n, K, N, Ns, it_fwd, it_adj, solver=slabel.lower()) / t_adj / 1e12
     cpu = None
     if not args.no_cpu:
         from oracle.model import Model
@@ -678,18 +696,18 @@ def run_mala(args):
     line = {
         "metric": "MALA moves/s", "value": N * S / t, "unit": "MALA moves/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t, "higher_is_better": True,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"MALA jitter: n=1024 K=8 Ns=20 N=256 (FP64, LI Picard, {_ckpt_note(args.ckpt)}), "
+        "dtype": dtype, "data": "synthetic",
+        "config": {"workload": f"MALA jitter: n=1024 K=8 Ns=20 N=256 ({dtype.upper()}, {slabel} Picard, "
+                               f"{_ckpt_note(args.ckpt)}), "
                                f"{S} moves per call, theta={theta}, h={h}",
                    "l2": "flushed between timed calls (256 MB write)",
                    "acceptance": acc / (N * S * args.steps),
                    "adjoint_ms": 1e3 * t_adj, "propose_us": 1e6 * t_prop, "accept_us": 1e6 * t_acc,
                    "adjoint_share": (S + 1) * t_adj / t},
-        "roofline": {"bound": "alu", "kernel": "adjoint_kernel<double,4,256,LI>", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "kernel": f"adjoint_kernel<{kinst}>", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None,
-                     "peak_note": "FP64 pipe 152 SMs x 2 DFMA lanes x 2 x max SM clock; recomputation from "
-                                  "checkpoints is not credited"},
+                     "peak_note": pnote + "; recomputation from checkpoints is not credited"},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -927,6 +945,8 @@ def main():
     ap.add_argument("--layout", default="auto", choices=["auto", "warp", "cta"],
                     help="kernel layout of the filter's propagation (FP32 EA: warp per particle or CTA)")
     ap.add_argument("--matern", action="store_true", help="--adjoint on the Matern noise (cfg3m_f64)")
+    ap.add_argument("--f32", action="store_true",
+                    help="--adjoint, --mala: the nudging workload on FP32 fields (EA Picard)")
     ap.add_argument("--ckpt", type=int, default=None,
                     help="--adjoint, --mala: checkpoint interval of the adjoint (default: keep every state)")
     ap.add_argument("--exp1", action="store_true",
