@@ -361,12 +361,14 @@ int pf_diagnostics(sch_ctx* ctx, int N, const void* u, const void* u_truth, doub
  * ------------------------------------------------------------------------- */
 
 /* Workspace for sch_adjoint_window: per particle, the states at every ckpt-th
- * step plus 2 (ckpt + 1) recomputed states of n reals. */
+ * step plus 2 (ckpt + 1) segment states of n reals. */
 size_t sch_adjoint_workspace_bytes(const sch_ctx* ctx, int N, int nsteps, int ckpt);
 
 /* J, dJ/dlambda, dJ/d dW and dJ/dm_start of the window cost for every particle:
  * a forward pass storing the state every ckpt steps, then per segment a
- * forward recomputation and the adjoint steps in reverse order.  The adjoint
+ * forward recomputation and the adjoint steps in reverse order.  With
+ * ckpt >= nsteps the window is one segment: the forward pass keeps every state
+ * and the reverse sweep recomputes nothing (the same results).  The adjoint
  * of a step solves J1^T psi = g by the transposed Picard fixed point to
  * params.tol (Eq. fde1 differentiated at its solution).
  *   m_start real [N][n]; dW, lambda real [N][nsteps][K] (lambda may be NULL);
