@@ -1,6 +1,8 @@
 // Small kernels around the propagation: Philox draws of the window noise,
 // the standalone likelihood / Girsanov weight, synthetic observations of a
 // truth trajectory and the EMRE / RB / RES diagnostics of Sec. 4.1.1.
+#include <type_traits>
+
 #include "sch_internal.h"
 
 namespace sch {
@@ -97,6 +99,8 @@ __global__ void synth_obs_kernel(ModelArgs<R> A, const R* u, uint64_t seed, uint
 }
 
 // ensemble sum per node, particles split over gridDim.y groups: ws[i] += sum_p u[p][i]
+// (in double: the mean's error enters RB and the RMSE through u_a - mean, which is
+// small against u)
 template <typename R>
 __global__ void diag_sum_kernel(ModelArgs<R> A, int N, const R* u, double* ws) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -149,6 +153,59 @@ __global__ void diag_particle_kernel(ModelArgs<R> A, int N, const R* u, const R*
     }
 }
 
+// The same for float fields, with the arithmetic in float: each warp takes particles
+// w, w + W, ... and holds its lanes' nodes' mean and truth in registers (NPL = n / 32
+// nodes a lane, n <= 32 NPL); a particle's sums of squares run in float over the lane's
+// nodes and a 5-level warp tree (relative error below (NPL + 5) 2^-24), and only their
+// square roots are accumulated in double, then added once per block.
+template <int NPL>
+__global__ void diag_particle_f32_kernel(ModelArgs<float> A, int N, const float* u, const float* ua,
+                                         const double* ws, double* out) {
+    __shared__ double part[2][8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int W = gridDim.x * (blockDim.x >> 5);
+    float t[NPL], mn[NPL];
+#pragma unroll
+    for (int k = 0; k < NPL; ++k) {
+        const int i = lane + 32 * k;
+        t[k] = i < A.n ? ua[i] : 0.f;
+        mn[k] = i < A.n ? (float)ws[i] : 0.f;
+    }
+    double e = 0.0, f = 0.0;
+    for (int p = warp; p < N; p += W) {
+        float se = 0.f, sf = 0.f;
+#pragma unroll
+        for (int k = 0; k < NPL; ++k) {
+            const int i = lane + 32 * k;
+            if (i < A.n) {
+                const float v = u[(size_t)p * A.n + i];
+                const float d1 = v - t[k], d2 = v - mn[k];
+                se = fmaf(d1, d1, se);
+                sf = fmaf(d2, d2, sf);
+            }
+        }
+        se = warp_sum(se);
+        sf = warp_sum(sf);
+        e += (double)sqrtf(se);
+        f += (double)sqrtf(sf);
+    }
+    if (lane == 0) {
+        part[0][wib] = e;
+        part[1][wib] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += part[0][w];
+            b += part[1][w];
+        }
+        atomicAdd(&out[6], a);
+        atomicAdd(&out[7], b);
+    }
+}
+
 __global__ void diag_zero_kernel(int n, double* ws, double* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 8) out[i] = 0.0;
@@ -171,13 +228,33 @@ int launch_synth_obs(const ModelArgs<R>& A, const R* u, uint64_t seed, uint64_t 
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 
+// per-particle norms: double fields one warp per particle in double; float fields in
+// float with the mean and truth in registers, for n up to 32 * 32 (else as double)
+template <typename R>
+void launch_diag_particle(const ModelArgs<R>& A, int N, const R* u, const R* ua, const double* ws, double* out,
+                          cudaStream_t st) {
+    if constexpr (std::is_same<R, float>::value) {
+        // 8 warps a block, blocks enough for one or two particles a warp
+        const int blocks = (N + 15) / 16 < 1 ? 1 : (N + 15) / 16;
+        if (A.n <= 256) {
+            diag_particle_f32_kernel<8><<<blocks, 256, 0, st>>>(A, N, u, ua, ws, out);
+            return;
+        }
+        if (A.n <= 1024) {
+            diag_particle_f32_kernel<32><<<blocks, 256, 0, st>>>(A, N, u, ua, ws, out);
+            return;
+        }
+    }
+    diag_particle_kernel<R><<<(N * 32 + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
+}
+
 template <typename R>
 int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* ua, double* ws, double* out, cudaStream_t st) {
     const int nb = (A.n + 255) / 256;
     diag_zero_kernel<<<nb, 256, 0, st>>>(A.n, ws, out);
     diag_sum_kernel<R><<<dim3(nb, N < 64 ? N : 64), 256, 0, st>>>(A, N, u, ws);
     diag_mean_kernel<R><<<nb, 256, 0, st>>>(A, N, ua, ws, out);
-    diag_particle_kernel<R><<<(N * 32 + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
+    launch_diag_particle<R>(A, N, u, ua, ws, out, st);
     diag_final_kernel<R><<<1, 32, 0, st>>>(A, N, out);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }

@@ -314,3 +314,18 @@ def test_half_domain_observations(name, layout):
                                                 cfg.sigma), rtol=tol_ll)
     # the unobserved half carries no weight: the full-domain NLL is larger
     assert np.all(OF.nll(ref[1], random_obs(cfg, 62), cfg.sigma) > nll_ref)
+
+
+@pytest.mark.parametrize("n,N", [(256, 9), (1024, 1024)])
+def test_diagnostics_f32(n, N):
+    # float fields: the per-particle norms run in float (sums of at most 32 squares a lane and a
+    # 5-level warp tree: relative error below 37 2^-24, about 2.2e-6), the ensemble mean in double
+    cfg = get_config("cfg2_f32", n=n, M=n // 16)
+    g = gpu_model(cfg)
+    ut = u0_profile(cfg).astype(np.float32).astype(np.float64)
+    ens = random_state(cfg, N, 8).astype(np.float32).astype(np.float64)
+    d = g.diagnostics(tdev(ens, g.dtype), tdev(ut, g.dtype)).cpu().numpy()
+    assert np.isclose(d[0], OF.emre(ut, ens), rtol=1e-5)
+    assert np.isclose(d[1], OF.rb(ut, ens), rtol=1e-9)
+    assert np.isclose(d[2], OF.res(ut, ens), rtol=1e-5)
+    assert np.isclose(d[3], np.sqrt(np.mean((ens.mean(0) - ut) ** 2)), rtol=1e-9)
