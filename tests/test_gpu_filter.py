@@ -23,8 +23,10 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("N,spread,theta", [(1, 1.0, 0.0), (7, 0.01, 0.0), (64, 5.0, 0.0), (1024, 30.0, 0.25),
-                                            (8192, 80.0, 0.5), (16384, 5.0, 0.9)])
+                                            (1025, 30.0, 0.0), (1500, 10.0, 0.1), (8192, 80.0, 0.5),
+                                            (16384, 5.0, 0.9)])
 def test_temper_matches_oracle(N, spread, theta):
+    # N <= 1024 runs the cluster on 128-thread CTAs (one particle a thread), larger N on 256
     api = require_lib()
     phi = random_logweights(N, N, spread)
     lg = np.random.default_rng(N).normal(size=N)
