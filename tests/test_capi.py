@@ -155,3 +155,18 @@ def test_noise_dim_of_the_mode_expansion(lib):
     assert lib.sch_noise_dim(h) == 4
     assert lib.sch_noise_dim(None) == -1
     assert lib.sch_destroy(h) == 0
+
+
+def test_adjoint_workspace_sizes(lib):
+    # per particle: ceil(nsteps / ckpt) checkpoints and 2 (ckpt + 1) segment states of n reals;
+    # the binding's default interval is the whole window (one checkpoint, every state kept)
+    from paper_2402_06927_gb300.api import _ckpt
+    p = _params()          # FP64, n = 256
+    h = ct.c_void_p()
+    assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0
+    assert lib.sch_adjoint_workspace_bytes(h, 3, 20, 5) == 3 * (4 + 12) * 256 * 8
+    assert lib.sch_adjoint_workspace_bytes(h, 3, 20, 20) == 3 * (1 + 42) * 256 * 8
+    assert lib.sch_adjoint_workspace_bytes(h, 3, 20, 0) == 0
+    assert lib.sch_adjoint_workspace_bytes(h, 0, 20, 5) == 0
+    assert _ckpt(None, 20) == 20 and _ckpt(5, 20) == 5
+    assert lib.sch_destroy(h) == 0
