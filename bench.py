@@ -165,32 +165,35 @@ class ClockSampler:
 
 
 def dist_setup():
+    """(rank, world size) from the launcher's environment; with more than one rank, the
+    process group for the timing's barrier and reductions (NCCL where CUDA is, else gloo)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, ws
 
 
-def reduce_max(v: float, ws: int) -> float:
+def _all_reduce(v: float, ws: int, op: str) -> float:
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def reduce_max(v: float, ws: int) -> float:
+    return _all_reduce(v, ws, "max")
 
 
 def reduce_sum(v: float, ws: int) -> float:
-    if ws == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _all_reduce(v, ws, "sum")
 
 
 def barrier(ws: int):
