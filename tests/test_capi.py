@@ -170,3 +170,16 @@ def test_adjoint_workspace_sizes(lib):
     assert lib.sch_adjoint_workspace_bytes(h, 0, 20, 5) == 0
     assert _ckpt(None, 20) == 20 and _ckpt(5, 20) == 5
     assert lib.sch_destroy(h) == 0
+
+
+def test_matern_layout_choice(lib):
+    # SCH_LAYOUT_AUTO: one warp per particle for FP32 fields at n = 256, 512, 1024 with either
+    # noise model, the CTA layout at other sizes and for FP64; SCH_LAYOUT_CTA always honoured
+    for n, dtype, layout, want in [(512, 1, 0, 2), (1024, 1, 0, 2), (2048, 1, 0, 1), (1024, 0, 0, 1),
+                                   (1024, 1, 1, 1), (1024, 1, 2, 2)]:
+        p = _params(noise=1, kappa=1.0, eta=0.2, matern_k=3, n=n, M=64, dtype=dtype, layout=layout)
+        h = ct.c_void_p()
+        assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0, (n, dtype, layout)
+        assert lib.sch_layout(h) == want, (n, dtype, layout)
+        assert lib.sch_noise_dim(h) == n
+        assert lib.sch_destroy(h) == 0
