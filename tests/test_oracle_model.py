@@ -10,7 +10,10 @@ fix, not against a retyped copy of its own formulas:
 * the linearised viscous decay of Fourier modes (closed-form amplification);
 * exact conservation of H = 1/2 (m, u) by the midpoint rule at mu = 0 with no
   noise, and refinement behaviour of (m, 1);
-* a travelling CH peakon keeping its speed c.
+* a travelling CH peakon keeping its speed c;
+* the mode-expansion SALT noise on its Fourier content: each slot's unit increment
+  excites exactly its wavenumber, sin slots in the imaginary and cos slots in the
+  real part of the FFT, with amplitude a_j n / 2.
 """
 import math
 
@@ -310,3 +313,32 @@ def test_prior_sample_fourier_symbol(n):
     # scale 0 gives the truth itself
     _, u0 = m.prior_sample(u_truth, seed, N, 0.0)
     assert np.array_equal(u0, np.tile(u_truth, (N, 1)))
+
+
+@pytest.mark.parametrize("n,amps", [(64, [0.05, 0.05]), (256, [0.05 / j for j in range(1, 9)])])
+def test_mode_noise_fourier_content(n, amps):
+    """The mode-expansion noise (Sec. 2; SALT mode functions read as K/2 wavenumbers x
+    {sin, cos}): for the unit increment of slot k, the nodal field noise(e_k) has, under the
+    FFT (x_m -> sum_m x_m exp(-2 pi i q m / n)), energy only at wavenumbers q = j and n - j,
+    with j = k // 2 + 1.  A sin slot (even k) gives X_j = -i a_j n / 2 (purely imaginary), a
+    cos slot (odd k) X_j = a_j n / 2 (purely real).  A swapped sin/cos slot, a wrong
+    wavenumber factor or a wrong amplitude fails; the drift enters as dW + lambda dt."""
+    m = Model(L=40.0, n=n, alpha=1.0, mu=0.02, dt=0.025, amps=np.array(amps))
+    K = 2 * len(amps)
+    for k in range(K):
+        e = np.zeros(K)
+        e[k] = 1.0
+        X = np.fft.fft(m.noise(e))
+        j = k // 2 + 1
+        a = amps[j - 1]
+        expect = np.zeros(n, dtype=complex)
+        if k % 2 == 0:
+            expect[j], expect[n - j] = -0.5j * a * n, 0.5j * a * n
+        else:
+            expect[j], expect[n - j] = 0.5 * a * n, 0.5 * a * n
+        assert np.max(np.abs(X - expect)) <= 1e-12 * n
+    rng = np.random.default_rng(5)
+    dW, lam = rng.normal(size=K), rng.normal(size=K)
+    assert np.allclose(m.noise(dW, lam), m.noise(dW + m.dt * lam), rtol=0, atol=1e-15)
+    # the noise of a general increment is the sum of its slots' fields (linearity)
+    assert np.allclose(m.noise(dW), sum(dW[k] * m.noise(np.eye(K)[k]) for k in range(K)), rtol=0, atol=1e-14)
