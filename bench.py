@@ -468,7 +468,7 @@ def run_ours(args):
                                        f"{cfg.n} Brownian motions per step) " if matern else f"K={cfg.K} ")
                                     + f"N={N} Ns={cfg.Ns} M={cfg.M} sigma={cfg.sigma} N*=N/2 "
                                       f"jitter={cfg.n_jitter} rho={cfg.rho} "
-                                      f"({cfg.dtype.upper()} fields, FP64 weights)"),
+                                      f"({'FP32' if cfg.dtype == 'f32' else 'FP64'} fields, FP64 weights)"),
                        "n": cfg.n, "N": N, "Ns": cfg.Ns, "K": cfg.K, "Q": cfg.Q, "M": cfg.M,
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "layout": g.layout,
                        "l2": "flushed between timed steps (256 MB write)",
@@ -497,42 +497,63 @@ def run_ours(args):
 
 
 def run_nudging(args):
-    """--nudging: learned vs optimiser nudging on the learned-proposal workload.
+    """--nudging: learned vs optimiser nudging (learned-proposal workload cfg4_f32 by default:
+    n = 1024, K = 16 modes, 20-step windows, N = 1024, M = 64, sigma = 0.05; or
+    --nudging-workload cfg5_f32, the large run: n = 4096, K = 32, Ns = 10, N = 8192, M = 128,
+    sigma = 0.02), FP32 fields, the network in BF16 with FP32 accumulation.
 
-    n = 1024, K = 16 modes, 20-step windows, N = 1024, M = 64, sigma = 0.05,
-    FP32 fields.  Training pairs: pf_nudge (open loop, L-BFGS to max|grad| <=
-    1e-6) on `--train-cycles` cycles of a twin experiment x 1024 particles;
-    the network is trained with its own GPU kernels; then the same evaluation
-    twin is assimilated `--steps` cycles with learned, hybrid (the network's
-    drift refined by one L-BFGS iteration), optimiser and no nudging
-    (tempering + 10 jitter steps each).
-    """
+    Training pairs: pf_nudge (open loop, L-BFGS to max|grad| <= 1e-6) on `--train-cycles`
+    cycles of a twin experiment x N particles; the network is trained with its own GPU
+    kernels.  Then `--twins` fresh twin experiments are assimilated `--steps` cycles each with
+    learned nudging backed by the optimiser (pf_nudge for any cycle whose forecast ESS under
+    the network's drift is below N/4: the product path), the network alone, optimiser
+    nudging, the hybrid (the network's drift refined by one L-BFGS iteration) and no nudging
+    (tempering + jitter steps each).  Reported per source: cycles/s, analysis RMSE and
+    forecast ESS as mean and spread over the twins, fallback cycles, and the paired
+    learned/optimiser RMSE ratios."""
+    import math
     import torch
     from workloads import get_config, u0_profile
     from paper_2402_06927_gb300.api import ProposalNet, SchModel
     from paper_2402_06927_gb300 import proposal as PR
 
     torch.cuda.set_device(0)
-    cfg = get_config("cfg4_f32")
+    cfg = get_config(args.nudging_workload)
     g = SchModel.from_config(cfg)
     u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
-    U, Y, T, gst = PR.generate_pairs(g, cfg.N, cfg.Ns, args.train_cycles, 7, u0, cfg.ess_min, cfg.rho,
+    train_cycles = args.train_cycles if cfg.N <= 1024 else max(1, args.train_cycles * 1024 // cfg.N)
+    U, Y, T, gst = PR.generate_pairs(g, cfg.N, cfg.Ns, train_cycles, 7, u0, cfg.ess_min, cfg.rho,
                                      cfg.n_jitter, cfg.prior_scale, max_iter=60, gtol=1e-6)
-    net = ProposalNet(cfg.n, cfg.K, cfg.Ns, cfg.M, cfg.sigma, C=64, seed=1)
+    net = ProposalNet(cfg.n, cfg.K, cfg.Ns, cfg.M, cfg.sigma, C=64, seed=1, precision="bf16")
     tst = PR.train(net, U, Y, T, epochs=args.epochs, batch=256, lr=1e-3)
-    twin = PR.make_twin(g, cfg.Ns, args.steps, 99, u0)
-    res = {}
-    for src in ("none", "learned", "hybrid", "optimiser"):
-        res[src] = PR.run_nudged(g, src, net, cfg.N, cfg.Ns, args.steps, 99, u0, cfg.ess_min, cfg.rho,
-                                 cfg.n_jitter, cfg.prior_scale, twin, max_iter=60, gtol=1e-6, refine=1)
+    sources = ("learned_fb", "learned", "hybrid", "optimiser", "none")
+    runs = {src: [] for src in sources}
+    for t in range(args.twins):
+        tseed = 99 + 17 * t
+        twin = PR.make_twin(g, cfg.Ns, args.steps, tseed, u0)
+        for src in sources:
+            runs[src].append(PR.run_nudged(g, src, net, cfg.N, cfg.Ns, args.steps, tseed, u0, cfg.ess_min, cfg.rho,
+                                           cfg.n_jitter, cfg.prior_scale, twin, max_iter=60, gtol=1e-6, refine=1))
+
+    def stats(vals):
+        m = sum(vals) / len(vals)
+        sd = math.sqrt(sum((v - m) ** 2 for v in vals) / max(1, len(vals) - 1))
+        return {"mean": m, "sd": sd, "values": vals}
+
+    res = {src: {k: stats([r[k] for r in runs[src]])
+                 for k in ("cycles_per_s", "rmse", "mean_forecast_ess", "fallback_cycles")} for src in sources}
+    ratios = [a["rmse"] / b["rmse"] for a, b in zip(runs["learned_fb"], runs["optimiser"])]
     line = {
-        "metric": "assim. cycles/s (learned nudging)", "value": res["learned"]["cycles_per_s"], "unit": "cycles/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": True, "dtype": "f32",
+        "metric": "assim. cycles/s (learned nudging with optimiser fallback)",
+        "value": res["learned_fb"]["cycles_per_s"]["mean"], "unit": "cycles/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": 0, "higher_is_better": True, "dtype": "f32 fields, bf16 network",
         "data": "synthetic",
-        "config": {"workload": "SCH twin experiment n=1024 K=16 Ns=20 N=1024 M=64 sigma=0.05, learned vs "
-                               "optimiser nudging + tempering + 10 jitter steps",
+        "config": {"workload": f"{cfg.name}: SCH twin experiment n={cfg.n} K={cfg.K} Ns={cfg.Ns} N={cfg.N} "
+                               f"M={cfg.M} sigma={cfg.sigma}, learned vs optimiser nudging + tempering + "
+                               f"{cfg.n_jitter} jitter steps, {args.twins} twins x {args.steps} cycles",
                    "train_pairs": int(U.shape[0]), "generation": gst, "training": tst},
         "comparison": res,
+        "paired_rmse_ratio_learned_fb_over_optimiser": stats(ratios),
     }
     print(json.dumps(line))
     return 0
@@ -887,11 +908,12 @@ def run_filter_kernels(args):
 
 def run_proposal(args):
     """--proposal: the learned proposal network at the learned-proposal workload's size
-    (n = 1024, K = 16, Ns = 20, M = 64, 64 channels) on a batch of B = 1024 particles:
-    nn_forward, nn_backward (loss and all gradients) and nn_adam_step.  Algorithmic flops
-    are the multiply-adds of the convolutions, the Fourier-mode projection and the head
-    (2 per multiply-add); the kernels are FP32 SGEMMs on the FMA pipe.  The FP64 oracle
-    network is timed on one host core beside them."""
+    (n = 1024, K = 16, Ns = 20, M = 64, 64 channels) on a batch of B = 8192 particles:
+    nn_forward, nn_backward (loss and all gradients) and nn_adam_step, with BF16
+    operands and FP32 accumulation on the tensor cores (the product path) and with FP32
+    operands on the CUDA cores (the check path).  Algorithmic flops are the
+    multiply-adds of the convolutions, the Fourier-mode projection and the head (2 per
+    multiply-add).  The FP64 oracle network is timed on one host core beside them."""
     import numpy as np
     import torch
     from workloads import get_config
@@ -899,7 +921,7 @@ def run_proposal(args):
     from paper_2402_06927_gb300.api import ProposalNet
     torch.cuda.set_device(0)
     cfg = get_config("cfg4_f32")
-    n, K, Ns, M, C, B = cfg.n, cfg.K, cfg.Ns, cfg.M, 64, 1024
+    n, K, Ns, M, C, B = cfg.n, cfg.K, cfg.Ns, cfg.M, 64, 8192
     net = ProposalNet(n, K, Ns, M, cfg.sigma, C=C, seed=1)
     g = torch.Generator(device="cpu").manual_seed(5)
     u = (0.3 * torch.randn(B, n, generator=g)).cuda()
@@ -912,30 +934,39 @@ def run_proposal(args):
     conv_dx = sum(2 * (n >> (l + 1)) * C * C * 5 for l in range(1, 4))
     bwd = B * (conv + conv_dx + 2 * C * P * K + 2 * 2 * (C * K) * (K * Ns))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(3):
-        net.forward(u, y)
-        net.loss_and_grad(u, y, tgt)
     reps = max(5, args.steps)
-    tf = _event_time(lambda: net.forward(u, y), reps, flush)
-    tb = _event_time(lambda: net.loss_and_grad(u, y, tgt), reps, flush)
-    _, gr = net.loss_and_grad(u, y, tgt)
-    ta = _event_time(lambda: net.adam_step(gr), reps, flush)
-    peak = fp32_peak_tflops()
+    res = {}
+    for prec in ("bf16", "fp32"):
+        net.set_precision(prec)
+        for _ in range(3):
+            net.forward(u, y)
+            net.loss_and_grad(u, y, tgt)
+        tf = _event_time(lambda: net.forward(u, y), reps, flush)
+        tb = _event_time(lambda: net.loss_and_grad(u, y, tgt), reps, flush)
+        _, gr = net.loss_and_grad(u, y, tgt)
+        ta = _event_time(lambda: net.adam_step(gr), reps, flush)
+        res[prec] = (tf, tb, ta)
+    bf_peak = _peaks().get("bf16_tflops", 1922.7)
+    f32_peak = fp32_peak_tflops()
     p_np = OC.init_params(C, K, Ns, n, 1)
     x0 = OC.features(u[:4].double().cpu().numpy(), y.double().cpu().numpy(), cfg.sigma)
     tho_f = _host_time(lambda: OC.forward(p_np, x0, K, Ns), 2.0) / 4
     tho_b = _host_time(lambda: OC.loss_and_grad(p_np, x0, tgt[:4].double().cpu().numpy(), K, Ns), 2.0) / 4
+    tf, tb, ta = res["bf16"]
+    tf32, tb32, ta32 = res["fp32"]
     line = {
-        "metric": "network samples/s (forward)", "value": B / tf, "unit": "samples/s", "n_gpus": 1, "dtype": "f32",
+        "metric": "network samples/s (forward)", "value": B / tf, "unit": "samples/s", "n_gpus": 1, "dtype": "bf16",
         "data": "synthetic",
         "config": {"workload": f"learned proposal: n={n} K={K} Ns={Ns} M={M} C={C}, batch {B}",
                    "l2": "flushed before each timed call (256 MB write)"},
-        "forward": {"ms": 1e3 * tf, "tflops": fwd / tf / 1e12, "frac": fwd / tf / 1e12 / peak},
-        "backward": {"ms": 1e3 * tb, "tflops": bwd / tb / 1e12, "frac": bwd / tb / 1e12 / peak},
+        "forward": {"ms": 1e3 * tf, "tflops": fwd / tf / 1e12, "frac": fwd / tf / 1e12 / bf_peak},
+        "backward": {"ms": 1e3 * tb, "tflops": bwd / tb / 1e12, "frac": bwd / tb / 1e12 / bf_peak},
         "adam_ms": 1e3 * ta,
-        "roofline": {"bound": "alu", "kernel": "sgemm_kernel (nn_forward)", "achieved": fwd / tf / 1e12,
-                     "peak": peak, "unit": "TFLOP/s", "frac": fwd / tf / 1e12 / peak, "traffic": None,
-                     "peak_note": f"FP32 FMA pipe {sm_count()} SMs x 128 lanes x 2 x max SM clock"},
+        "fp32_check_path": {"forward_ms": 1e3 * tf32, "backward_ms": 1e3 * tb32,
+                            "forward_tflops": fwd / tf32 / 1e12, "forward_frac_of_fp32_peak": fwd / tf32 / 1e12 / f32_peak},
+        "roofline": {"bound": "tensor", "kernel": "hgemm_kernel (nn_forward, BF16 mma.sync m16n8k16, FP32 accumulation)",
+                     "achieved": fwd / tf / 1e12, "peak": bf_peak, "unit": "TFLOP/s", "frac": fwd / tf / 1e12 / bf_peak,
+                     "traffic": None, "peak_note": "measured cuBLAS BF16 burst (MEASURED_PEAKS.json bf16_tflops)"},
         "cpu_baseline": {"value": 1.0 / tho_f, "unit": "samples/s", "cores": 1, "kind": "oracle",
                          "sample": "FP64 oracle network forward on 4 samples (one thread); backward "
                                    f"{1.0 / tho_b:.1f} samples/s"},
@@ -994,8 +1025,9 @@ def main():
                     help="filter workload of the main run: cfg5_f32 (the large run, the headline), "
                          "cfg2_f32 (ensemble scale) or cfg2m_f32 (cfg2 with the paper's Matern noise)")
     ap.add_argument("--mala-h", type=float, default=None, help="MALA step size h (--mala)")
-    ap.add_argument("--layout", default="auto", choices=["auto", "warp", "cta"],
-                    help="kernel layout of the filter's propagation (FP32 EA: warp per particle or CTA)")
+    ap.add_argument("--layout", default="auto", choices=["auto", "warp", "group", "group16", "cta"],
+                    help="kernel layout of the filter's propagation (FP32 EA: one warp per particle, several "
+                         "warps per particle with 32 or 16 nodes a lane, or one CTA per particle)")
     ap.add_argument("--matern", action="store_true", help="--adjoint on the Matern noise (cfg3m_f64)")
     ap.add_argument("--f32", action="store_true",
                     help="--adjoint, --mala: the nudging workload on FP32 fields (EA Picard)")
@@ -1016,6 +1048,9 @@ def main():
     ap.add_argument("--occupancy", action="store_true",
                     help="jitter launch time at 1 .. 16 warps per SM (occupancy sweep)")
     ap.add_argument("--train-cycles", type=int, default=200)
+    ap.add_argument("--twins", type=int, default=5, help="--nudging: independent twin experiments")
+    ap.add_argument("--nudging-workload", default="cfg4_f32", choices=["cfg4_f32", "cfg5_f32"],
+                    help="--nudging: the learned-proposal workload or the large run")
     ap.add_argument("--epochs", type=int, default=10)
     args = ap.parse_args()
     if args.nudging:

@@ -68,13 +68,21 @@ enum { SCH_F64 = 0, SCH_F32 = 1 };
 enum { SCH_SOLVER_AUTO = 0, SCH_SOLVER_LI = 1, SCH_SOLVER_EA = 2 };
 
 /* Kernel layout of sch_ensemble_step and pf_jitter:
- *   SCH_LAYOUT_CTA   one CTA of n/8 (float) or n/4 (double) threads per particle;
- *   SCH_LAYOUT_WARP  one warp per particle, packed f32x2 arithmetic: float
- *                    fields, the SCH_SOLVER_EA solver and n = 256, 512 or 1024
- *                    only (sch_create returns SCH_ERR_UNSUPPORTED otherwise);
- *   SCH_LAYOUT_AUTO  WARP where it applies (with either noise model), else CTA.
- * Both compute the same iteration; results agree to rounding. */
-enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2 };
+ *   SCH_LAYOUT_CTA     one CTA of n/8 (float) or n/4 (double) threads per particle;
+ *   SCH_LAYOUT_WARP    one warp per particle, packed f32x2 arithmetic: float
+ *                      fields, the SCH_SOLVER_EA solver and n = 256, 512 or 1024
+ *                      only (sch_create returns SCH_ERR_UNSUPPORTED otherwise);
+ *   SCH_LAYOUT_GROUP   n/1024 warps per particle (one CTA), each warp holding 1024
+ *                      consecutive nodes in the WARP layout's registers (32 a lane);
+ *                      the cyclic solves are completed across the warps through
+ *                      shared memory, one CTA barrier per solve: float fields,
+ *                      SCH_SOLVER_EA, the mode expansion and n = 2048 or 4096 only;
+ *   SCH_LAYOUT_GROUP16 the same with 16 nodes a lane (n/512 warps per particle);
+ *   SCH_LAYOUT_AUTO    WARP where it applies (with either noise model), else
+ *                      GROUP where it applies, else CTA.
+ * All compute the same iteration; results agree to rounding. */
+enum { SCH_LAYOUT_AUTO = 0, SCH_LAYOUT_CTA = 1, SCH_LAYOUT_WARP = 2, SCH_LAYOUT_GROUP = 3,
+       SCH_LAYOUT_GROUP16 = 4 };
 
 /* SALT noise model (sch_params.noise):
  *   SCH_NOISE_MODES   dU = sum_k xi_k (dW_k + lambda_k dt) over K mode functions
@@ -135,8 +143,8 @@ int sch_create(const sch_params* params, sch_ctx** ctx);
 int sch_destroy(sch_ctx* ctx);
 
 /* The kernel layout a context runs sch_ensemble_step and pf_jitter with:
- * SCH_LAYOUT_CTA or SCH_LAYOUT_WARP (SCH_LAYOUT_AUTO resolved); SCH_ERR_ARG
- * for a NULL context.  Host only. */
+ * SCH_LAYOUT_CTA, SCH_LAYOUT_WARP, SCH_LAYOUT_GROUP or SCH_LAYOUT_GROUP16
+ * (SCH_LAYOUT_AUTO resolved); SCH_ERR_ARG for a NULL context.  Host only. */
 int sch_layout(const sch_ctx* ctx);
 
 /* Q, the Brownian motions per model step: K for SCH_NOISE_MODES, n for
@@ -227,7 +235,7 @@ int pf_temper_dev(int N, const double* nll, const double* logG, const double* th
  * If n_arrays > 0, also gathers each arrays[a] (device pointer, N rows of
  * row_bytes[a] bytes, rows 16-byte aligned) in place: row i <- old row idx[i],
  * staged through `ws` (ws_bytes >= pf_resample_workspace_bytes).  `arrays` and
- * `row_bytes` are host arrays.  N <= 16384. */
+ * `row_bytes` are host arrays.  N <= 8192 (SCH_ERR_ARG beyond). */
 int pf_resample(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
                 int n_arrays, void* const* arrays, const size_t* row_bytes, void* ws,
                 size_t ws_bytes, void* stream);
@@ -258,7 +266,11 @@ int pf_resample(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, in
  *    last call's contents (nothing in it needs to start at zero: each array is
  *    fully written before it is read back).  Calls whose execution overlaps on
  *    the GPU (on different streams, or from several host threads) race on the
- *    scratch and must be serialised by the caller. */
+ *    scratch and must be serialised by the caller;
+ *  - the cached address belongs to the device's current context: after
+ *    cudaDeviceReset on a device, do not call pf_resample_static on that device
+ *    again in the same process (the address would be stale).
+ */
 #define PF_RESAMPLE_STATIC_BYTES (16u * 1024u * 1024u)
 int pf_resample_static(int N, const double* wbar, uint64_t seed, uint64_t stage_ctr, int32_t* idx,
                        int n_arrays, void* const* arrays, const size_t* row_bytes, void* stream);
@@ -414,8 +426,14 @@ int pf_nudge(sch_ctx* ctx, int N, int nsteps, int mode, int max_iter, double gto
  *   F[c][2(j-1)], F[c][2j-1] = (1/P) sum_q h[c][q] sin, cos(2 pi j q / P), P = n/16
  *   lambda = Wh F + bh
  * Parameters are one FP32 vector (per layer w[C][Cin][5], b[C]; then Wh[K Ns][C K],
- * bh[K Ns]); activations FP32 with FP32 accumulation.
+ * bh[K Ns]); activations and gradients are FP32 in memory.  The contractions
+ * (every convolution, the mode projection and the head, forward and backward)
+ * run in the shape's precision:
+ *   NN_FP32  FP32 operands, FP32 accumulation (CUDA cores; the check path);
+ *   NN_BF16  operands rounded to BF16, FP32 accumulation (tensor cores,
+ *            mma.sync m16n8k16); Adam keeps FP32 master weights.
  * ------------------------------------------------------------------------- */
+enum { NN_FP32 = 0, NN_BF16 = 1 };
 typedef struct {
     int32_t n;       /* nodes (multiple of 16 and of M) */
     int32_t K;       /* drift modes (even) */
@@ -423,9 +441,10 @@ typedef struct {
     int32_t C;       /* channels */
     int32_t M;       /* observation points */
     float sigma;     /* observation noise, scales the innovation */
+    int32_t precision;  /* NN_FP32 or NN_BF16 (anything else: an invalid shape) */
 } nn_shape;
 
-/* Number of FP32 parameters (0 for an invalid shape). */
+/* Number of FP32 parameters (0 for an invalid shape or precision). */
 size_t nn_param_count(const nn_shape* shape);
 /* Workspace bytes for a batch of B samples (activations and gradients). */
 size_t nn_workspace_bytes(const nn_shape* shape, int B);

@@ -171,7 +171,7 @@ def pcn_propose(dW: np.ndarray, dW_hat: np.ndarray, rho: float) -> np.ndarray:
 
 
 def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, state=None,
-           particle0=0):
+           particle0=0, margins=False):
     """n_iter PCN moves of every particle's window noise at temperature theta.
 
     For iteration j the proposal noise is keyed (seed, TAG_PCN, ctr + j) and the
@@ -179,7 +179,10 @@ def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, sta
     the whole window from m_start; it is accepted iff log U < w0 - w1 with
     w = theta (NLL - logG).  ``state`` = (nll, logG, m_end, u_end) of the
     current noise, recomputed when omitted.
-    Returns (dW, nll, logG, m_end, u_end, accepts).
+    Returns (dW, nll, logG, m_end, u_end, accepts), and with ``margins`` also the
+    [n_iter, N] Metropolis margins (w0 - w1) - log U (a move is accepted iff its
+    margin is positive), the [n_iter, N] proposal NLLs and the [n_iter, N] NLLs of the
+    current state before each move.
     """
     N, Ns, K = dW.shape
     dW = np.array(dW, dtype=np.float64)
@@ -191,6 +194,9 @@ def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, sta
     else:
         cur_nll, cur_logG, m_end, u_end = (np.array(v, dtype=np.float64) for v in state)
     accepts = np.zeros(N, dtype=np.int64)
+    marg = np.zeros((n_iter, N))
+    prop_nll = np.zeros((n_iter, N))
+    prev_nll = np.zeros((n_iter, N))
     for j in range(n_iter):
         hat = _rng.window_increments(seed, _rng.TAG_PCN, N, Ns, K, model.dt, ctr + j, particle0)
         prop = pcn_propose(dW, hat, rho)
@@ -202,24 +208,31 @@ def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, sta
         pidx = np.arange(particle0, particle0 + N, dtype=np.uint64)
         logU = np.log(_rng.uniform_open0(seed, _rng.TAG_PCN_ACCEPT, pidx, np.uint64(ctr + j)))
         acc = logU < (w0 - w1)
+        marg[j] = (w0 - w1) - logU
+        prop_nll[j] = p_nll
+        prev_nll[j] = cur_nll
         dW[acc] = prop[acc]
         cur_nll[acc] = p_nll[acc]
         cur_logG[acc] = p_logG[acc]
         m_end[acc] = pm[acc]
         u_end[acc] = pu[acc]
         accepts += acc
+    if margins:
+        return dW, cur_nll, cur_logG, m_end, u_end, accepts, marg, prop_nll, prev_nll
     return dW, cur_nll, cur_logG, m_end, u_end, accepts
 
 
 # ---------------------------------------------------------------------- #
 # MALA jitter: the gradient-informed move Sec. 5 names as future work
 # ---------------------------------------------------------------------- #
-def mala_step(U, grad_U, x, h, C, z, logu):
+def mala_step(U, grad_U, x, h, C, z, logu, detail=False):
     """One preconditioned MALA step (Roberts and Tweedie 1996) for the density
     exp(-U): the proposal x' = x - (h/2) C grad U(x) + sqrt(h C) z (C diagonal) is
     accepted iff log u < U(x) - U(x') + log q(x | x') - log q(x' | x), with
     log q(b | a) = -|b - a + (h/2) C grad U(a)|^2_{(h C)^-1} / 2.
-    A proposal where U is not finite is rejected.  Returns (x_next, accepted).
+    A proposal where U is not finite is rejected.  Returns (x_next, accepted), and
+    with ``detail`` also a dict: the margin log alpha - log u, U(x), U(x'), the norms
+    of grad U(x), grad U(x') and of the two proposal residuals b - a + (h/2) C grad U(a), and x'.
     """
     x = np.asarray(x, dtype=np.float64)
     C = np.broadcast_to(np.asarray(C, dtype=np.float64), x.shape)
@@ -233,6 +246,10 @@ def mala_step(U, grad_U, x, h, C, z, logu):
 
     log_alpha = U(x) - U(xp) + logq(x, xp, gp) - logq(xp, x, g)
     ok = bool(np.isfinite(U(xp)) and logu < log_alpha)
+    if detail:
+        info = dict(margin=log_alpha - logu, xp=xp, U0=U(x), U1=U(xp), g=np.linalg.norm(g), gp=np.linalg.norm(gp),
+                    rf=np.linalg.norm(xp - x + 0.5 * h * C * g), rb=np.linalg.norm(x - xp + 0.5 * h * C * gp))
+        return (xp if ok else x), ok, info
     return (xp if ok else x), ok
 
 
@@ -257,13 +274,15 @@ def mala_target(model, m_start, dW, lam, y, sigma, theta):
     return U, gU
 
 
-def mala_jitter(model, m_start, dW, lam, y, sigma, theta, h, n_iter, seed, ctr, particle0=0):
+def mala_jitter(model, m_start, dW, lam, y, sigma, theta, h, n_iter, seed, ctr, particle0=0, margins=False):
     """n_iter MALA moves of every particle's window noise (``mala_target``) with
     preconditioner C = dt (the prior covariance of dW).  For iteration j the
     proposal normals are keyed (seed, TAG_MALA) at counter (k // 4, step,
     particle0 + p, ctr + j) and the accept uniform (seed, TAG_MALA_ACCEPT) at
     (0, 0, particle0 + p, ctr + j).  Returns (dW, nll, logG, accepts), nll and
-    logG those of the final noise.
+    logG those of the final noise; with ``margins`` also, per move and particle, the
+    ``mala_step`` details with the NLL at both points (NLL = (U - |x|^2 / (2 dt)) /
+    theta + log G(x)).
     """
     N, Ns, K = np.shape(dW)
     dt = model.dt
@@ -271,6 +290,7 @@ def mala_jitter(model, m_start, dW, lam, y, sigma, theta, h, n_iter, seed, ctr, 
     lam_arr = np.zeros_like(dW) if lam is None else np.asarray(lam, dtype=np.float64)
     accepts = np.zeros(N, dtype=np.int64)
     pidx = np.arange(particle0, particle0 + N, dtype=np.uint64)
+    details = []
     for j in range(n_iter):
         z = _rng.window_increments(seed, _rng.TAG_MALA, N, Ns, K, 1.0, ctr + j, particle0)
         logu = np.log(_rng.uniform_open0(seed, _rng.TAG_MALA_ACCEPT, pidx, np.uint64(ctr + j)))
@@ -281,9 +301,21 @@ def mala_jitter(model, m_start, dW, lam, y, sigma, theta, h, n_iter, seed, ctr, 
             def gU(x, p=p):
                 return mala_target(model, m_start[p], x, lam_arr[p], y, sigma, theta)[1]
 
-            dW[p], ok = mala_step(U, gU, dW[p], h, dt, z[p], logu[p])
+            if margins:
+                x0 = dW[p].copy()
+                dW[p], ok, info = mala_step(U, gU, x0, h, dt, z[p], logu[p], detail=True)
+                x1 = info["xp"]
+                for key, xx in (("nll0", x0), ("nll1", x1)):
+                    lg = -np.sum(lam_arr[p] * xx + 0.5 * lam_arr[p] ** 2 * dt)
+                    Ux = info["U0"] if key == "nll0" else info["U1"]
+                    info[key] = (Ux - np.sum(xx * xx) / (2.0 * dt)) / theta + lg
+                details.append((j, p, info))
+            else:
+                dW[p], ok = mala_step(U, gU, dW[p], h, dt, z[p], logu[p])
             accepts[p] += ok
     _, u_end, _, _ = model.ensemble_window(m_start, dW, lam_arr)
+    if margins:
+        return dW, nll(u_end, y, sigma), girsanov_logG(lam_arr, dW, dt), accepts, details
     return dW, nll(u_end, y, sigma), girsanov_logG(lam_arr, dW, dt), accepts
 
 

@@ -40,9 +40,12 @@ class SchParams(ct.Structure):
     ]
 
 
+NN_FP32, NN_BF16 = 0, 1
+
+
 class NNShape(ct.Structure):
     _fields_ = [("n", ct.c_int32), ("K", ct.c_int32), ("Ns", ct.c_int32), ("C", ct.c_int32),
-                ("M", ct.c_int32), ("sigma", ct.c_float)]
+                ("M", ct.c_int32), ("sigma", ct.c_float), ("precision", ct.c_int32)]
 
 
 P = ct.c_void_p

@@ -50,7 +50,7 @@ class SchModel:
         p.M, p.sigma, p.tol, p.max_iter = M, sigma, tol, max_iter
         p.dtype = SCH_F32 if dtype == "f32" else SCH_F64
         p.solver = {"auto": 0, "li": 1, "ea": 2}[solver]
-        p.layout = {"auto": 0, "cta": 1, "warp": 2}[layout]
+        p.layout = {"auto": 0, "cta": 1, "warp": 2, "group": 3, "group16": 4}[layout]
         p.noise = {"modes": 0, "matern": 1}[noise]
         p.kappa, p.eta, p.matern_k = kappa, eta, matern_k
         self.params = p
@@ -59,8 +59,11 @@ class SchModel:
         h = ct.c_void_p()
         check(lib().sch_create(ct.byref(p), ct.byref(h)), "sch_create")
         self._h = h
-        # the kernel layout the library chose: "warp" (one warp per particle) or "cta"
-        self.layout = {1: "cta", 2: "warp"}[lib().sch_layout(h)]
+        # the kernel layout the library chose: "warp" (one warp per particle), "group" or
+        # "group16" (n / 1024 or n / 512 warps per particle) or "cta"
+        self.layout = {1: "cta", 2: "warp", 3: "group", 4: "group16"}[lib().sch_layout(h)]
+        self.group_cs = 8 if self.layout == "group" else 4
+        self.group_warps = n // (128 * self.group_cs) if self.layout.startswith("group") else 0
         # Brownian motions per step, the last axis of every dW and lambda: K mode
         # functions, or one per cell for the Matern noise
         self.K = int(lib().sch_noise_dim(h))
@@ -439,12 +442,15 @@ class ProposalNet:
 
     ``params`` is the flat FP32 parameter vector in the library's layout
     (per layer w[C][Cin][5], b[C]; then Wh[K Ns][C K], bh[K Ns]); when omitted
-    it is initialised with a seeded He-normal draw.
+    it is initialised with a seeded He-normal draw.  ``precision`` is "fp32" (FP32
+    contractions on the CUDA cores) or "bf16" (BF16 operands, FP32 accumulation, on the
+    tensor cores); it can be changed later with ``set_precision``.
     """
 
     def __init__(self, n: int, K: int, Ns: int, M: int, sigma: float, C: int = 64,
-                 params: Optional[torch.Tensor] = None, seed: int = 0):
-        self.shape = NNShape(n, K, Ns, C, M, sigma)
+                 params: Optional[torch.Tensor] = None, seed: int = 0, precision: str = "fp32"):
+        self.shape = NNShape(n, K, Ns, C, M, sigma, self._prec(precision))
+        self.precision = precision
         self.n, self.K, self.Ns, self.C, self.M = n, K, Ns, C, M
         self.count = int(lib().nn_param_count(ct.byref(self.shape)))
         if self.count == 0:
@@ -466,6 +472,15 @@ class ProposalNet:
         self.v = torch.zeros_like(self.params)
         self.t = 0
         self._ws = None
+
+    @staticmethod
+    def _prec(precision: str) -> int:
+        return {"fp32": _lib.NN_FP32, "bf16": _lib.NN_BF16}[precision]
+
+    def set_precision(self, precision: str) -> None:
+        """Switch the contractions between FP32 ("fp32") and BF16 with FP32 accumulation ("bf16")."""
+        self.shape.precision = self._prec(precision)
+        self.precision = precision
 
     def _workspace(self, B: int):
         need = int(lib().nn_workspace_bytes(ct.byref(self.shape), B))

@@ -14,8 +14,10 @@ struct sch_ctx {
     int C, tp;
     int Q;            // Brownian motions per step: K (modes) or n (Matern)
     int matern;       // 1 for SCH_NOISE_MATERN
-    int wcs;          // sub-chunk length of the warp-per-particle kernels, 0 = CTA kernels
+    int wcs;          // sub-chunk length of the warp-per-particle or warp-group kernels, 0 = CTA kernels
+    int gw;           // warps per particle of the warp-group kernels, 0 = not the group layout
     WArgs wa;
+    GArgs ga;
     ModelArgs<float> af;
     ModelArgs<double> ad;
 };
@@ -342,6 +344,114 @@ void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
     }
 }
 
+// In-place inverse of a dense n x n matrix (Gauss-Jordan with partial pivoting,
+// double precision); returns false if it is singular to working precision.
+bool invert_dense(int n, double* a, double* inv) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(a[r * n + c]) > fabs(a[piv * n + c])) piv = r;
+        if (!(fabs(a[piv * n + c]) > 0.0)) return false;
+        if (piv != c)
+            for (int j = 0; j < n; ++j) {
+                double t = a[c * n + j];
+                a[c * n + j] = a[piv * n + j];
+                a[piv * n + j] = t;
+                t = inv[c * n + j];
+                inv[c * n + j] = inv[piv * n + j];
+                inv[piv * n + j] = t;
+            }
+        const double d = 1.0 / a[c * n + c];
+        for (int j = 0; j < n; ++j) {
+            a[c * n + j] *= d;
+            inv[c * n + j] *= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = a[r * n + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                a[r * n + j] -= f * a[c * n + j];
+                inv[r * n + j] -= f * inv[c * n + j];
+            }
+        }
+    }
+    return true;
+}
+
+// The cross-warp reduced solve of sub-chunk table T with the lane partition of Q
+// (S rows per lane) for W warps per particle (see GTab and sch_group.cuh).
+bool gtab_host(const HTab& T, const RTab<double>& Q, int S, int W, GTab& G) {
+    memset(&G, 0, sizeof(G));
+    if (S < 2 || W < 2 || W > GW_MAX) return false;
+    // the cyclic system of the lane-last unknowns (the rows of the warps' 32-lane PCR)
+    const double LA = -Q.aeL * Q.qa, LB = 1.0 - Q.aeL * Q.qc - Q.geL * Q.qa, LC = -Q.geL * Q.qc;
+    double t32[32 * 32], ti[32 * 32];
+    memset(t32, 0, sizeof(t32));
+    for (int l = 0; l < 32; ++l) {
+        t32[l * 32 + (l + 31) % 32] += LA;
+        t32[l * 32 + l] += LB;
+        t32[l * 32 + (l + 1) % 32] += LC;
+    }
+    if (!invert_dense(32, t32, ti)) return false;
+    // phi = T32^-1 LA e_0, psi = T32^-1 LC e_31, p2 = T32^-1 e_31 at lanes 0 and 31
+    const double phi0 = ti[0 * 32 + 0] * LA, phi31 = ti[31 * 32 + 0] * LA;
+    const double psi0 = ti[0 * 32 + 31] * LC, psi31 = ti[31 * 32 + 31] * LC;
+    // z = (a_0 .. a_{W-1}, b_0 .. b_{W-1}) from the corrected (y_0, y_31) of every warp:
+    //   a_w + phi_0 (b_{w-1} - b_w) + psi_0 (a_{w+1} - a_w) = y_0(w)
+    //   b_w + phi_31 (b_{w-1} - b_w) + psi_31 (a_{w+1} - a_w) = y_31(w)
+    const int n2 = 2 * W;
+    double sm[4 * GW_MAX * GW_MAX], gi[4 * GW_MAX * GW_MAX];
+    memset(sm, 0, sizeof(sm));
+    for (int w = 0; w < W; ++w) {
+        const int wp = (w + W - 1) % W, wn = (w + 1) % W;
+        double* ra = sm + w * n2;
+        double* rb = sm + (W + w) * n2;
+        ra[w] += 1.0;
+        ra[W + wp] += phi0;
+        ra[W + w] -= phi0;
+        ra[wn] += psi0;
+        ra[w] -= psi0;
+        rb[W + w] += 1.0;
+        rb[W + wp] += phi31;
+        rb[W + w] -= phi31;
+        rb[wn] += psi31;
+        rb[w] -= psi31;
+    }
+    if (!invert_dense(n2, sm, gi)) return false;
+    // weights of warp 0's b_{-1}, b_0, a_0, a_1 (block circulant: the same for every warp,
+    // indexed relative to it)
+    const int rows[4] = {W + W - 1, W, 0, 1 % W};
+    float* dst[4] = {G.bprev, G.bself, G.aself, G.anext};
+    for (int q = 0; q < 4; ++q)
+        for (int j = 0; j < n2; ++j) dst[q][j] = (float)gi[rows[q] * n2 + j];
+    G.LA = (float)LA;
+    G.LC = (float)LC;
+    G.iLC = (float)(1.0 / LC);
+    G.p2_0 = (float)ti[0 * 32 + 31];
+    G.p2_31 = (float)ti[31 * 32 + 31];
+    G.cq = (float)(T.ge * Q.q[S - 1]);
+    G.geL = (float)Q.geL;
+    return true;
+}
+
+// the warp-group tables: sub-chunks of CS nodes, S = 4 rows per lane, W warps
+bool fill_gargs(const sch_params& p, int CS, int W, GArgs& G) {
+    const double h = p.L / p.n;
+    const double a2 = p.alpha * p.alpha;
+    HTab tp, th;
+    RTab<double> q;
+    const int S = 4;
+    ctab_host(h / 6.0 - p.mu * p.dt / (2.0 * h), 2.0 * h / 3.0 + p.mu * p.dt / h, CS, tp);
+    ctab_host((h / 6.0 - a2 / h) * 6.0 / h, (2.0 * h / 3.0 + 2.0 * a2 / h) * 6.0 / h, CS, th);
+    rtab_host(tp, 32 * S, q);
+    if (!gtab_host(tp, q, S, W, G.pic)) return false;
+    rtab_host(th, 32 * S, q);
+    return gtab_host(th, q, S, W, G.hel);
+}
+
 bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -363,7 +473,6 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     if (p.n % C != 0) return SCH_ERR_UNSUPPORTED;
     const int tp = p.n / C;
     if (!pow2(tp) || tp < 32 || tp > 512) return SCH_ERR_UNSUPPORTED;
-    if (p.layout < SCH_LAYOUT_AUTO || p.layout > SCH_LAYOUT_WARP) return SCH_ERR_ARG;
     if (p.noise != SCH_NOISE_MODES && p.noise != SCH_NOISE_MATERN) return SCH_ERR_ARG;
     const int solver = (p.solver != SCH_SOLVER_AUTO) ? p.solver : (p.dtype == SCH_F32 ? SCH_SOLVER_EA : SCH_SOLVER_LI);
     const bool matern = p.noise == SCH_NOISE_MATERN;
@@ -375,6 +484,12 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     if (p.layout == SCH_LAYOUT_WARP && !warp_fits) return SCH_ERR_UNSUPPORTED;
     // one warp per particle wherever it fits, with either noise model
     const bool warp_ok = warp_fits && p.layout != SCH_LAYOUT_CTA;
+    // several warps per particle: float fields, explicit advection, the mode expansion,
+    // n = 2048 or 4096
+    const bool group_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && !matern && (p.n == 2048 || p.n == 4096);
+    if ((p.layout == SCH_LAYOUT_GROUP || p.layout == SCH_LAYOUT_GROUP16) && !group_fits) return SCH_ERR_UNSUPPORTED;
+    if (p.layout < SCH_LAYOUT_AUTO || p.layout > SCH_LAYOUT_GROUP16) return SCH_ERR_ARG;
+    const bool group_ok = group_fits && p.layout != SCH_LAYOUT_CTA && p.layout != SCH_LAYOUT_WARP;
     sch_ctx* c = (sch_ctx*)calloc(1, sizeof(sch_ctx));
     if (!c) return SCH_ERR_ARG;
     c->p = p;
@@ -389,6 +504,17 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
         const int P = warp_streams(p.n);
         c->wcs = p.n / (64 * P);
         fill_wargs(p, c->wcs, 64 * P, c->wa);
+    } else if (group_ok) {
+        // W warps per particle, each lane 2 streams x 2 sub-chunks of wcs nodes: 32 nodes a
+        // lane (SCH_LAYOUT_GROUP, the default) or 16 (SCH_LAYOUT_GROUP16)
+        const int lane_nodes = (p.layout == SCH_LAYOUT_GROUP16) ? 16 : 32;
+        c->wcs = lane_nodes / 4;
+        c->gw = p.n / (32 * lane_nodes);
+        fill_wargs(p, c->wcs, 128, c->wa);
+        if (!fill_gargs(p, c->wcs, c->gw, c->ga)) {
+            free(c);
+            return SCH_ERR_UNSUPPORTED;
+        }
     }
     *ctx = c;
     return SCH_OK;
@@ -401,6 +527,7 @@ int sch_destroy(sch_ctx* ctx) {
 
 int sch_layout(const sch_ctx* ctx) {
     if (!ctx) return SCH_ERR_ARG;
+    if (ctx->gw) return ctx->wcs == 4 ? SCH_LAYOUT_GROUP16 : SCH_LAYOUT_GROUP;
     return ctx->wcs ? SCH_LAYOUT_WARP : SCH_LAYOUT_CTA;
 }
 
@@ -451,6 +578,7 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
     if (nsteps > 4096) return SCH_ERR_ARG;
     // the Matern kernels hold one step's n cell weights in shared memory, the others a window's noise
     const size_t sm = ctx->matern ? 0
+                      : ctx->gw ? gwindow_smem(ctx->wcs, ctx->gw, nsteps, ctx->Q)
                       : ctx->wcs ? wwindow_smem(ctx->wcs, nsteps, ctx->Q)
                       : (ctx->p.dtype == SCH_F32) ? window_smem<float, 8>(ctx->tp, nsteps, ctx->Q)
                                                   : window_smem<double, 4>(ctx->tp, nsteps, ctx->Q);
@@ -461,6 +589,7 @@ int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_ou
         if (ctx->matern)
             return ctx->wcs ? launch_wwindow_matern(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream))
                             : launch_window_matern<float, 8>(ctx->af, io, N, S(stream));
+        if (ctx->gw) return launch_gwindow(ctx->wcs, ctx->gw, ctx->af, ctx->wa, ctx->ga, io, N, S(stream));
         if (ctx->wcs) return launch_wwindow(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_window<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_window<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
@@ -572,6 +701,7 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
     if (!m_start || !dW || !y || !nll || !m_end || !u_end) return SCH_ERR_ARG;
     if (lambda && !logG) return SCH_ERR_ARG;
     const size_t sm = ctx->matern ? 0
+                      : ctx->gw ? gjitter_smem(ctx->wcs, ctx->gw, nsteps, ctx->Q)
                       : ctx->wcs ? wjitter_smem(ctx->wcs, nsteps, ctx->Q)
                       : (ctx->p.dtype == SCH_F32) ? jitter_smem<float, 8>(ctx->tp, nsteps, ctx->Q)
                                                   : jitter_smem<double, 4>(ctx->tp, nsteps, ctx->Q);
@@ -584,6 +714,7 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
         if (ctx->matern)
             return ctx->wcs ? launch_wjitter_matern(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream))
                             : launch_jitter_matern<float, 8>(ctx->af, io, N, S(stream));
+        if (ctx->gw) return launch_gjitter(ctx->wcs, ctx->gw, ctx->af, ctx->wa, ctx->ga, io, N, S(stream));
         if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));

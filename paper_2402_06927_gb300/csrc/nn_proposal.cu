@@ -9,14 +9,20 @@
 //   four circular convolutions, kernel 5, stride 2, padding 2, C channels, ReLU  -> C x n/16
 //   Fourier-mode projection F[c][k] = (1/P) sum_q h[c][q] {sin,cos}(2 pi j q / P)
 //   linear head lambda = Wh F + bh
-// Every contraction runs through one tiled SGEMM kernel with gather functors
-// (implicit im2col for the convolutions), so no im2col buffer is formed.
+// Every contraction runs through one tiled GEMM kernel with gather functors
+// (implicit im2col for the convolutions), so no im2col buffer is formed: a SIMT
+// FP32 kernel (NN_FP32, the check path), or a tensor-core kernel that rounds both
+// operands to BF16 as it stages them in shared memory and accumulates in FP32
+// with mma.sync m16n8k16 (NN_BF16).  Parameters, activations and gradients stay
+// FP32 in memory in both (the FP32 master weights of Adam).
+#include <cuda_bf16.h>
+
 #include "sch_internal.h"
 
 namespace sch {
 
 struct NNDims {
-    int n, K, Ns, C, M;
+    int n, K, Ns, C, M, prec;
     float sigma;
     int L[5];     // positions at layers 0..4: n, n/2, n/4, n/8, n/16
     int cin[4];   // input channels of conv l
@@ -26,7 +32,7 @@ struct NNDims {
 
 static NNDims make_dims(const nn_shape* s) {
     NNDims d{};
-    d.n = s->n; d.K = s->K; d.Ns = s->Ns; d.C = s->C; d.M = s->M; d.sigma = s->sigma;
+    d.n = s->n; d.K = s->K; d.Ns = s->Ns; d.C = s->C; d.M = s->M; d.sigma = s->sigma; d.prec = s->precision;
     for (int l = 0; l <= 4; ++l) d.L[l] = s->n >> l;
     size_t o = 0;
     for (int l = 0; l < 4; ++l) {
@@ -102,6 +108,92 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int Kd, int kc
         }
 }
 
+// --------------------------------------------------------------------------
+// BF16 tensor-core GEMM with the same gather functors: C[m][n] (+)= sum_k A(m, k)
+// B(k, n), both operands rounded to BF16 (round to nearest) as they are staged in
+// shared memory, products accumulated in FP32 by mma.sync.m16n8k16 (row.col).
+// 64 x 64 tiles, k-chunks of 32, 128 threads: warp w computes the 32 x 32 quarter
+// (w / 2, w % 2) as 2 x 4 fragments of 16 x 8.  Shared rows are padded by 8
+// elements so that the 32-bit fragment loads of a warp fall in distinct banks.
+// --------------------------------------------------------------------------
+constexpr int HTM = 64, HTN = 64, HTK = 32, HPAD = 8;
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <typename LA, typename LB, typename EP>
+__global__ void __launch_bounds__(128) hgemm_kernel(int M, int N, int Kd, int kchunk, LA la, LB lb, EP ep) {
+    __shared__ __align__(16) __nv_bfloat16 As[HTM][HTK + HPAD];   // [m][k]
+    __shared__ __align__(16) __nv_bfloat16 Bs[HTN][HTK + HPAD];   // [n][k]
+    const int m0 = blockIdx.y * HTM, n0 = blockIdx.x * HTN;
+    const int nkc = max(1, (Kd + kchunk - 1) / kchunk);
+    const int kbeg = (int)(blockIdx.z % (unsigned)nkc) * kchunk;
+    const int zb = blockIdx.z / nkc;
+    const int kend = min(Kd, kbeg + kchunk);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int k0 = kbeg; k0 < kend; k0 += HTK) {
+        for (int e = threadIdx.x; e < HTK * HTM; e += 128) {
+            const int mm = e / HTK, kk = e % HTK;
+            const int gm = m0 + mm, gk = k0 + kk;
+            As[mm][kk] = __float2bfloat16_rn((gm < M && gk < kend) ? la(zb, gm, gk) : 0.f);
+        }
+        for (int e = threadIdx.x; e < HTK * HTN; e += 128) {
+            const int kk = e / HTN, nn = e % HTN;
+            const int gn = n0 + nn, gk = k0 + kk;
+            Bs[nn][kk] = __float2bfloat16_rn((gn < N && gk < kend) ? lb(zb, gk, gn) : 0.f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < HTK; ks += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + 16 * i + gq;
+                a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq]);
+                a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq]);
+                a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + 2 * tq + 8]);
+                a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + 8 * j + gq;
+                b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tq]);
+                b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][ks + 2 * tq + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    // fragment (i, j): rows wm + 16 i + gq (+ 8), columns wn + 8 j + 2 tq (+ 1)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int gm = m0 + wm + 16 * i + gq + ((e & 2) ? 8 : 0);
+                const int gn = n0 + wn + 8 * j + 2 * tq + (e & 1);
+                if (gm < M && gn < N) ep(zb, gm, gn, acc[i][j][e]);
+            }
+}
+
 // k-splits for a reduction with few output tiles (weight gradients: the sum runs over
 // batch x positions): about 8 CTAs per SM of 152, chunks of at least 256 k-values
 static int splitk_for(int M, int N, int Kd) {
@@ -115,12 +207,17 @@ static int splitk_chunks(int Kd, int splitk) {
     return (Kd + kchunk - 1) / kchunk;
 }
 
+// the GEMM in the network's precision: the FP32 SIMT kernel or the BF16 tensor-core kernel
+// (same tile sizes, so the split-K chunks and the partial buffers are the same)
 template <typename LA, typename LB, typename EP>
-static void sgemm(int batch, int M, int N, int Kd, int splitk, LA la, LB lb, EP ep, cudaStream_t st) {
+static void sgemm(int prec, int batch, int M, int N, int Kd, int splitk, LA la, LB lb, EP ep, cudaStream_t st) {
     const int kchunk = (Kd + splitk - 1) / splitk;
     const int nk = splitk_chunks(Kd, splitk);
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, batch * nk);
-    sgemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, kchunk, la, lb, ep);
+    if (prec == NN_BF16)
+        hgemm_kernel<<<grid, 128, 0, st>>>(M, N, Kd, kchunk, la, lb, ep);
+    else
+        sgemm_kernel<<<grid, 256, 0, st>>>(M, N, Kd, kchunk, la, lb, ep);
 }
 
 // --------------------------------------------------------------------------
@@ -340,16 +437,16 @@ static void nn_forward_impl(const NNDims& d, int B, const float* params, const f
                                                                  act + d.act_off[0], bs);
     for (int l = 0; l < 4; ++l) {
         const int Ci = d.cin[l], Lin = d.L[l], Lo = d.L[l + 1];
-        sgemm(B, d.C, Lo, Ci * 5, 1, ConvW{params + d.off_w[l], Ci * 5}, ConvX{act + d.act_off[l], bs, Lin},
+        sgemm(d.prec, B, d.C, Lo, Ci * 5, 1, ConvW{params + d.off_w[l], Ci * 5}, ConvX{act + d.act_off[l], bs, Lin},
               StoreAct{act + d.act_off[l + 1], bs, Lo, params + d.off_b[l]}, st);
     }
     const int P = d.L[4];
     // F[b][c][k] = sum_q h4[b][c][q] S[q][k]
-    sgemm(B, d.C, d.K, P, 1, RowMajor{act + d.act_off[4], bs, P}, ModeS{P},
+    sgemm(d.prec, B, d.C, d.K, P, 1, RowMajor{act + d.act_off[4], bs, P}, ModeS{P},
           Store{act + d.off_F, bs, d.K, nullptr}, st);
     // lambda[b][o] = sum_f F[b][f] Wh[o][f] + bh[o]   (one GEMM over the batch: rows b)
     const int O = d.K * d.Ns, FF = d.C * d.K;
-    sgemm(1, B, O, FF, 1, RowMajor{act + d.off_F, 0, (int)bs}, RowMajorT{params + d.off_wh, 0, FF},
+    sgemm(d.prec, 1, B, O, FF, 1, RowMajor{act + d.off_F, 0, (int)bs}, RowMajorT{params + d.off_wh, 0, FF},
           Store{act + d.off_lam, 0, (int)bs, params + d.off_bh}, st);
 }
 
@@ -361,6 +458,7 @@ extern "C" {
 
 size_t nn_param_count(const nn_shape* s) {
     if (!s || s->n <= 0 || (s->n % 16) || s->K <= 0 || s->Ns <= 0 || s->C <= 0) return 0;
+    if (s->precision != NN_FP32 && s->precision != NN_BF16) return 0;
     return make_dims(s).nparam;
 }
 
@@ -426,14 +524,14 @@ int nn_backward(const nn_shape* s, int B, const float* params, const float* u_st
     // head: dWh[o][f] = sum_b glam[b][o] F[b][f]; dbh[o] = sum_b glam[b][o]; gF = glam Wh
     {
         const int sk = splitk_for(O, FF, B), nk = splitk_chunks(B, sk);
-        sgemm(1, O, FF, B, sk, RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
+        sgemm(d.prec, 1, O, FF, B, sk, RowMajorT{glam, 0, O}, RowMajor{act + d.off_F, 0, (int)bs},
               StorePartial{part, FF, (size_t)O * FF}, st);
         sum_slices_kernel<<<grid_elems((size_t)O * FF), 256, 0, st>>>((size_t)O * FF, nk, part, grads + d.off_wh);
     }
     bias_grad_kernel<<<O, 256, 0, st>>>(B, O, 1, glam, (size_t)O, grads + d.off_bh);
-    sgemm(1, B, FF, O, 1, RowMajor{glam, 0, O}, RowMajor{params + d.off_wh, 0, FF}, Store{gF, 0, FF, nullptr}, st);
+    sgemm(d.prec, 1, B, FF, O, 1, RowMajor{glam, 0, O}, RowMajor{params + d.off_wh, 0, FF}, Store{gF, 0, FF, nullptr}, st);
     // dh4[b][c][q] = sum_k gF[b][c][k] S[q][k], masked by ReLU(h4 > 0)
-    sgemm(B, d.C, P, d.K, 1, RowMajor{gF, (size_t)FF, d.K}, ModeST{P}, StoreMasked{gA, act + d.act_off[4], bs, P, 1},
+    sgemm(d.prec, B, d.C, P, d.K, 1, RowMajor{gF, (size_t)FF, d.K}, ModeST{P}, StoreMasked{gA, act + d.act_off[4], bs, P, 1},
           st);
     // conv layers, last to first; gA holds dL/dz of layer l's output at offset act_off[l+1]
     float* gcur = gA;
@@ -444,13 +542,13 @@ int nn_backward(const nn_shape* s, int B, const float* params, const float* u_st
         // weights: dw[co][kk] = sum_{b,q} gz[b][co][q] X(b, kk, q)
         const int sk = splitk_for(d.C, Ci * 5, B * Lo), nk = splitk_chunks(B * Lo, sk);
         const size_t wcount = (size_t)d.C * Ci * 5;
-        sgemm(1, d.C, Ci * 5, B * Lo, sk, GRowsBQ{gz, bs, Lo}, ConvXT{act + d.act_off[l], bs, Lin, Lo},
+        sgemm(d.prec, 1, d.C, Ci * 5, B * Lo, sk, GRowsBQ{gz, bs, Lo}, ConvXT{act + d.act_off[l], bs, Lin, Lo},
               StorePartial{part, Ci * 5, wcount}, st);
         sum_slices_kernel<<<grid_elems(wcount), 256, 0, st>>>(wcount, nk, part, grads + d.off_w[l]);
         bias_grad_kernel<<<d.C, 256, 0, st>>>(B, d.C, Lo, gz, bs, grads + d.off_b[l]);
         if (l > 0) {
             // data: dx[b][ci][i], masked by the ReLU of layer l-1's output
-            sgemm(B, Ci, Lin, d.C * 5, 1, WT{params + d.off_w[l], Ci}, GatherG{gz, bs, Lin, Lo},
+            sgemm(d.prec, B, Ci, Lin, d.C * 5, 1, WT{params + d.off_w[l], Ci}, GatherG{gz, bs, Lin, Lo},
                   StoreMasked{gnext, act + d.act_off[l], bs, Lin, 1}, st);
             float* t = gcur;
             gcur = gnext;

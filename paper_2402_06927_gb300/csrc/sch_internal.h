@@ -101,6 +101,28 @@ struct WArgs {
     float mzw;               // Matern cell weight scale (6/h) eta sqrt(h) / 8
 };
 
+// Cross-warp reduced solve of a constant table for the warp-group kernels
+// (sch_group.cuh), W <= GW_MAX warps per particle.  The lane-last unknowns of the
+// 32 W lanes satisfy LA EL_{g-1} + LB EL_g + LC EL_{g+1} = LD_g (cyclic).  Each warp
+// solves its 32 rows as a cyclic system of their own, y = T32^{-1} LD; p2_0, p2_31
+// are entries 0 and 31 of T32^{-1} e_31, the response to the part m = cq pd_0 +
+// geL qd_0 of lane 31's row that comes from the next warp's lane 0.  The warp's
+// boundary values b_{w-1}, b_w (lane 31 of the previous and of this warp) and
+// a_w, a_{w+1} (lane 0 of this and of the next warp) are sums over k < W of the
+// tabulated weights times y_0 (entry k) and y_31 (entry W + k) of warp w + k, both
+// corrected by that warp's m.  Computed on the host in double precision.
+constexpr int GW_MAX = 8;
+struct GTab {
+    float LA, LC, iLC;
+    float p2_0, p2_31;
+    float cq, geL;
+    float bprev[2 * GW_MAX], bself[2 * GW_MAX], aself[2 * GW_MAX], anext[2 * GW_MAX];
+};
+
+struct GArgs {
+    GTab pic, hel;          // the cross-warp solves of M + mu dt/2 K and (6/h)(M + alpha^2 K)
+};
+
 template <typename R>
 struct WindowIO {
     int Ns;
@@ -243,6 +265,15 @@ int launch_wjitter(int cs, const ModelArgs<float>& A, const WArgs& W, const Jitt
                    cudaStream_t st);
 size_t wwindow_smem(int cs, int Ns, int K);
 size_t wjitter_smem(int cs, int Ns, int K);
+
+// warp-group kernels for float fields (sch_window_group.cu): W warps per particle,
+// each holding n / W nodes as 2 P sub-chunks of cs nodes per lane (n = 64 P cs W)
+int launch_gwindow(int cs, int W, const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
+                   const WindowIO<float>& io, int N, cudaStream_t st);
+int launch_gjitter(int cs, int W, const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
+                   const JitterIO<float>& io, int N, cudaStream_t st);
+size_t gwindow_smem(int cs, int W, int Ns, int K);
+size_t gjitter_smem(int cs, int W, int Ns, int K);
 
 // MALA jitter (pf_mala.cu)
 template <typename R>

@@ -373,11 +373,13 @@ __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W,
     wstep_core<CS, P, PM, HM>(A, W, m, u, R0sm, W0, iters, flags);
 }
 
-// this lane's LN = 2 P CS nodes of a particle row <-> the paired registers:
-// sub-chunk s < P is stream s's .x, sub-chunk s >= P is stream s - P's .y
+// this thread's LN = 2 P CS nodes of a particle row <-> the paired registers:
+// sub-chunk s < P is stream s's .x, sub-chunk s >= P is stream s - P's .y.  Thread t
+// of the CTA owns nodes [LN t, LN (t + 1)): lane t of a one-warp CTA, or lane t % 32
+// of warp t / 32 when several warps carry the particle (sch_group.cuh).
 template <int CS, int P>
 __device__ __forceinline__ void wload(const float* row, float2 (&v)[P][CS]) {
-    const float4* q4 = reinterpret_cast<const float4*>(row + (threadIdx.x & 31) * 2 * P * CS);
+    const float4* q4 = reinterpret_cast<const float4*>(row + threadIdx.x * 2 * P * CS);
 #pragma unroll
     for (int s = 0; s < 2 * P; ++s)
 #pragma unroll
@@ -394,7 +396,7 @@ __device__ __forceinline__ void wload(const float* row, float2 (&v)[P][CS]) {
 
 template <int CS, int P>
 __device__ __forceinline__ void wstore(float* row, const float2 (&v)[P][CS]) {
-    float4* q4 = reinterpret_cast<float4*>(row + (threadIdx.x & 31) * 2 * P * CS);
+    float4* q4 = reinterpret_cast<float4*>(row + threadIdx.x * 2 * P * CS);
 #pragma unroll
     for (int s = 0; s < 2 * P; ++s)
 #pragma unroll
@@ -406,11 +408,11 @@ __device__ __forceinline__ void wstore(float* row, const float2 (&v)[P][CS]) {
         }
 }
 
-// observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this lane's observed
+// observation misfit sum_j ((u(x_j) - y_j) / sigma)^2 over this thread's observed
 // nodes (y_j not NaN); node mod stride and the observation index advance node by node
 template <int CS, int P>
 __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float2 (&u)[P][CS], const float* y) {
-    const int base = (threadIdx.x & 31) * 2 * P * CS;
+    const int base = threadIdx.x * 2 * P * CS;
     double acc = 0.0;
     int rem = base % A.stride;
     int j = base / A.stride + (rem != 0);
@@ -435,7 +437,7 @@ __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float
 // sin and cos of the angles of the first nodes of stream p's sub-chunks p and p + P
 template <int CS, int P>
 __device__ __forceinline__ void wangles(int n, float2 (&s1)[P], float2 (&c1)[P]) {
-    const int base = (threadIdx.x & 31) * 2 * P * CS;
+    const int base = threadIdx.x * 2 * P * CS;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         float sx, cx, sy, cy;

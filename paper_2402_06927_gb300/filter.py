@@ -133,11 +133,29 @@ class EnsembleFilter:
         pf_resample(self.wbar, self.seed, stage_ctr, idx=self.idx)
         self._gather_all()
 
+    def forecast(self, y: torch.Tensor, dW: torch.Tensor) -> None:
+        """The window's forecast into the filter's own buffers: dW copied in, then every
+        particle propagated from m_start with the current drift (sch_ensemble_step with the
+        fused likelihood); a following ``cycle(..., forecast_done=True)`` starts from it."""
+        self.dW.copy_(dW)
+        self.model.ensemble_step(self.m_start, self.dW, self.lam, y, m_out=self.m_end, u_out=self.u_end,
+                                 nll=self.nll, logG=self.logG, status=self.status, want_iters=False)
+
+    def forecast_ess(self) -> float:
+        """ESS of the Girsanov-corrected weights exp(-(nll - logG)) of the current forecast
+        (pf_temper at theta = 0: its out[3]); reads 8 bytes back to the host."""
+        pf_temper(self.nll, self.logG, 0.0, self.ess_min, wbar=self.wbar, out=self.tout, mode=self.temper_mode)
+        self.tout_host.copy_(self.tout, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return float(self.tout_host[3])
+
     def cycle(self, y: torch.Tensor, cycle: int, max_stages: int = 64,
               timer: Optional[KernelTimer] = None, dW: Optional[torch.Tensor] = None,
-              post=None) -> CycleStats:
+              post=None, forecast_done: bool = False) -> CycleStats:
         """One assimilation cycle.  ``dW`` (optional) supplies the window increments
         (e.g. the ones revealed by pf_nudge); otherwise they are drawn from the prior.
+        With ``forecast_done`` the filter's buffers already hold this window's forecast
+        (``forecast``) and it is not run again.
         ``post`` (optional, no arguments) enqueues work on the analysis ensemble, such as
         diagnostics and their copy to the host, on the current stream.  It is called right
         after the device-gated stages are enqueued, before the cycle waits for them, and
@@ -151,18 +169,19 @@ class EnsembleFilter:
         # cost about 20 us of host time per call, while the GPU waits for the cycle's first work)
         L = _lib.lib()
         stream = torch.cuda.current_stream().cuda_stream
-        if dW is None:
-            _lib.check(L.sch_draw_increments(m.handle, self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, 0,
-                                             self.dW.data_ptr(), stream), "sch_draw_increments")
-        else:
-            self.dW.copy_(dW)
-        _lib.check(L.sch_ensemble_step(m.handle, self.N, self.Ns, self.m_start.data_ptr(), self.m_end.data_ptr(),
-                                       self.u_end.data_ptr(), self.dW.data_ptr(),
-                                       None if self.lam is None else self.lam.data_ptr(), y.data_ptr(),
-                                       self.nll.data_ptr(), self.logG.data_ptr(), None, self.status.data_ptr(),
-                                       stream), "sch_ensemble_step")
+        if not forecast_done:
+            if dW is None:
+                _lib.check(L.sch_draw_increments(m.handle, self.N, self.Ns, self.seed, _lib.TAG_PRIOR_DW, cycle, 0,
+                                                 self.dW.data_ptr(), stream), "sch_draw_increments")
+            else:
+                self.dW.copy_(dW)
+            _lib.check(L.sch_ensemble_step(m.handle, self.N, self.Ns, self.m_start.data_ptr(),
+                                           self.m_end.data_ptr(), self.u_end.data_ptr(), self.dW.data_ptr(),
+                                           None if self.lam is None else self.lam.data_ptr(), y.data_ptr(),
+                                           self.nll.data_ptr(), self.logG.data_ptr(), None, self.status.data_ptr(),
+                                           stream), "sch_ensemble_step")
+            st.launches += 2
         st.forward_steps += self.N * self.Ns
-        st.launches += 2
         st.ess0 = None
         theta, k = 0.0, 0
         if self.eager_stages > 0:

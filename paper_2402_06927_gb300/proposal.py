@@ -6,11 +6,12 @@ optimiser nudging (host orchestration of library calls only).
   computes each particle's optimal drift for the cycle's observations, giving
   (u_start, y, lambda*) training pairs.
 * ``train``: Adam on the network's kernels (nn_backward, nn_adam_step).
-* ``compare``: runs the same twin experiment twice, nudging each cycle's
-  ensemble either with the trained network (nn_forward) or with the optimiser
-  (pf_nudge), then tempering + jittering; reports cycles/s, the RMSE of the
-  analysis mean against the truth, and the ESS of the Girsanov-corrected
-  weights before tempering.
+* ``run_nudged``: runs a twin experiment, nudging each cycle's ensemble with the
+  trained network (nn_forward), with the network backed by the optimiser
+  (pf_nudge instead whenever the network's forecast ESS falls below N/4), with
+  the optimiser alone, or not at all, then tempering + jittering; reports
+  cycles/s, the RMSE of the analysis mean against the truth, the ESS of the
+  Girsanov-corrected weights before tempering and the fallback cycles.
 """
 from __future__ import annotations
 
@@ -99,12 +100,14 @@ def train(net: ProposalNet, U, Y, T, epochs: int = 20, batch: int = 256, lr: flo
 
 def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycles: int, seed: int,
                u0: torch.Tensor, ess_min: float, rho: float, n_jitter: int, prior_scale: float,
-               twin: Twin, max_iter: int = 30, gtol: float = 1e-4, refine: int = 1):
+               twin: Twin, max_iter: int = 30, gtol: float = 1e-4, refine: int = 1,
+               fallback_frac: float = 0.25):
     """Cycles of a nudged tempering + jittering filter.
 
-    source: 'learned' (network drift), 'optimiser' (pf_nudge from zero),
-    'hybrid' (pf_nudge started from the network's drift, `refine` L-BFGS
-    iterations) or 'none'.
+    source: 'learned' (network drift), 'learned_fb' (network drift, and the optimiser
+    instead for a cycle whose forecast ESS under the network's drift falls below
+    fallback_frac N), 'optimiser' (pf_nudge from zero), 'hybrid' (pf_nudge started
+    from the network's drift, `refine` L-BFGS iterations) or 'none'.
     """
     f = EnsembleFilter(g, N, Ns, ess_min, rho, n_jitter, seed)
     m0, _ = g.prior_sample(N, u0, seed, prior_scale)
@@ -112,16 +115,30 @@ def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycl
     diag_ws = torch.empty(g.n, dtype=torch.float64, device="cuda")
     diag = torch.empty(8, dtype=torch.float64, device="cuda")
     rmse, ess0, stages = [], [], []
+    fallbacks = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for c in range(cycles):
         y = twin.ys[c]
         dW = None
-        if source == "learned":
+        done = False
+        if source in ("learned", "learned_fb"):
             u_start = g.u_from_m(f.m_start)
             lam = net.forward(u_start, y)
             f.set_drift(lam.to(g.dtype))
             dW = g.draw_increments(N, Ns, seed, _lib.TAG_NUDGE, 1_000_000 + c)
+            if source == "learned_fb":
+                # the forecast under the network's drift; if its Girsanov-corrected weights
+                # have ESS below fallback_frac N, the optimiser nudges this cycle instead
+                f.forecast(y, dW)
+                done = True
+                if f.forecast_ess() < fallback_frac * N:
+                    nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter, gtol=gtol, seed=seed,
+                                 ctr=1_000_000 + c)
+                    f.set_drift(nd["lam"])
+                    dW = nd["dW"]
+                    done = False
+                    fallbacks += 1
         elif source in ("optimiser", "hybrid"):
             lam0 = None
             if source == "hybrid":
@@ -132,7 +149,7 @@ def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycl
             dW = nd["dW"]
         else:
             f.set_drift(None)
-        st = f.cycle(y, c, dW=dW)
+        st = f.cycle(y, c, dW=dW, forecast_done=done)
         ess0.append(st.ess0)
         stages.append(len(st.stages))
         f.advance()
@@ -141,4 +158,5 @@ def run_nudged(g: SchModel, source: str, net: ProposalNet, N: int, Ns: int, cycl
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     return dict(cycles_per_s=cycles / secs, rmse=float(torch.stack(rmse).mean().item()),
-                mean_stages=sum(stages) / len(stages), mean_forecast_ess=sum(ess0) / len(ess0))
+                mean_stages=sum(stages) / len(stages), mean_forecast_ess=sum(ess0) / len(ess0),
+                fallback_cycles=fallbacks)

@@ -57,18 +57,30 @@ def _params(**kw):
                                    ({"K": 66}, -1), ({"M": 33}, -1), ({"sigma": 0.0}, -1), ({"dt": -1.0}, -1),
                                    ({"dtype": 5}, -1), ({"n": 8192}, -6), ({"max_iter": 0}, -1),
                                    # kernel layouts: the warp-per-particle layout takes float fields, the
-                                   # explicit-advection solver and n = 256, 512 or 1024 only
-                                   ({"layout": 3}, -1), ({"layout": 2}, -6), ({"layout": 1}, 0),
+                                   # explicit-advection solver and n = 256, 512 or 1024 only; the warp-group
+                                   # layouts float fields, explicit advection, the mode expansion and
+                                   # n = 2048 or 4096 only
+                                   ({"layout": 5}, -1), ({"layout": 2}, -6), ({"layout": 1}, 0),
                                    ({"layout": 2, "dtype": 1}, 0), ({"layout": 2, "dtype": 1, "n": 1024, "M": 64}, 0),
                                    ({"layout": 2, "dtype": 1, "solver": 1}, -6),
-                                   ({"layout": 2, "dtype": 1, "n": 2048, "M": 64}, -6)])
+                                   ({"layout": 2, "dtype": 1, "n": 2048, "M": 64}, -6),
+                                   ({"layout": 3}, -6), ({"layout": 3, "dtype": 1}, -6),
+                                   ({"layout": 3, "dtype": 1, "n": 4096, "M": 128}, 0),
+                                   ({"layout": 4, "dtype": 1, "n": 4096, "M": 128}, 0),
+                                   ({"layout": 4, "dtype": 1, "n": 2048, "M": 64}, 0),
+                                   ({"dtype": 1, "n": 2048, "M": 64}, 0), ({"dtype": 1, "n": 4096, "M": 128}, 0),
+                                   ({"layout": 3, "dtype": 1, "n": 4096, "M": 128, "solver": 1}, -6),
+                                   ({"layout": 3, "dtype": 1, "n": 4096, "M": 128, "noise": 1, "kappa": 1.0, "eta": 1.0,
+                                     "matern_k": 3}, -6)])
 def test_create_validates(lib, kw, rc):
     p = _params(**kw)
     h = ct.c_void_p()
     got = lib.sch_create(ct.byref(p), ct.byref(h))
     assert got == rc
     if got == 0:
-        want = kw.get("layout", 0) or (2 if (p.dtype == 1 and p.solver != 1 and p.n in (256, 512, 1024)) else 1)
+        ea32 = p.dtype == 1 and p.solver != 1
+        auto = 2 if (ea32 and p.n in (256, 512, 1024)) else 3 if (ea32 and p.n in (2048, 4096)) else 1
+        want = kw.get("layout", 0) or auto
         assert lib.sch_layout(h) == want
         assert lib.sch_destroy(h) == 0
 

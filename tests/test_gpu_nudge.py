@@ -22,7 +22,7 @@ from workloads import get_config, random_state, random_increments, random_drift,
 from oracle import filter as OF
 from oracle import nudge as ON
 from oracle import rng as ORNG
-from tests.helpers import gpu_model, oracle_model, tdev, rel_err
+from tests.helpers import assert_decisions, gpu_model, nll_error_bound, oracle_model, rel_err, tdev
 
 pytestmark = pytest.mark.gpu
 
@@ -220,19 +220,37 @@ def test_nudge_f32_matches_oracle(mode):
 
 @pytest.mark.parametrize("n,M", [(256, 32), (1024, 64)])
 def test_mala_f32_matches_oracle(n, M):
-    # FP32 MALA against the FP64 oracle's: decisions equal away from a coin flip, the noise and
-    # the misfit of the agreeing chains to FP32 tolerance
+    # FP32 MALA against the FP64 oracle, move by move from the GPU's state (a one-move call
+    # keyed ctr + j is move j): decisions equal unless the oracle's margin log alpha - log u is
+    # within the change the FP32 tolerances can cause (the NLL at both points through fields
+    # within 1e-4, the gradient within the FP32 adjoint tolerance 2e-5 through the proposal and
+    # both proposal densities); the noise of moves both accept to FP32 tolerance
     cfg = get_config("cfg2_f32", n=n, M=M)
     g = gpu_model(cfg)
     om, m0, dW, la, y = _setup(cfg, 3, 31, Ns=3, lam_scale=0.2)
     theta, h, n_iter, seed, ctr = 0.7, 0.8, 3, 5, 40
-    ref_dW, ref_nll, ref_lg, ref_acc = OF.mala_jitter(om, m0, dW, la, y, cfg.sigma, theta, h, n_iter, seed, ctr)
     dWd = tdev(dW, g.dtype)
-    out = g.mala_jitter(tdev(m0, g.dtype), dWd, tdev(la, g.dtype), tdev(y, g.dtype), theta, h, n_iter, seed, ctr)
-    torch.cuda.synchronize()
-    assert np.all(out["status"].cpu().numpy() == 0)
-    assert 0 < ref_acc.sum() < 3 * n_iter
-    same = out["accepts"].cpu().numpy() == ref_acc
-    assert same.sum() >= 2
-    assert rel_err(dWd.double().cpu().numpy()[same], ref_dW[same]) < 1e-5
-    assert np.allclose(out["nll"].cpu().numpy()[same], ref_nll[same], rtol=1e-5)
+    m0d, lad, yd = tdev(m0, g.dtype), tdev(la, g.dtype), tdev(y, g.dtype)
+    m0h, lah, yh = m0d.double().cpu().numpy(), lad.double().cpu().numpy(), yd.double().cpu().numpy()
+    tau, ftol = 2e-5, 1e-4
+    recs = []
+    for j in range(n_iter):
+        before = dWd.double().cpu().numpy()
+        out = g.mala_jitter(m0d, dWd, lad, yd, theta, h, 1, seed, ctr + j)
+        torch.cuda.synchronize()
+        assert np.all(out["status"].cpu().numpy() == 0)
+        acc = out["accepts"].cpu().numpy()
+        u_scale = out["u"].abs().max().item()
+        for p in range(3):
+            r = OF.mala_jitter(om, m0h[p:p + 1], before[p:p + 1], lah[p:p + 1], yh, cfg.sigma, theta, h, 1, seed,
+                               ctr + j, particle0=p, margins=True)
+            dW_o, acc_o, info = r[0], r[3], r[4][0][2]
+            bound = (theta * (nll_error_bound(info["nll0"], M, u_scale, cfg.sigma, ftol)
+                              + nll_error_bound(info["nll1"], M, u_scale, cfg.sigma, ftol))
+                     + info["gp"] * 0.5 * h * cfg.dt * tau * info["g"]
+                     + 0.5 * tau * (info["rf"] * info["g"] + info["rb"] * info["gp"]))
+            recs.append((p, j, int(acc[p]), int(acc_o[0]), float(info["margin"]), float(bound)))
+            if acc[p] == 1 and acc_o[0] == 1:
+                assert rel_err(dWd[p].double().cpu().numpy(), dW_o[0]) < 1e-5
+    assert_decisions(recs, exact=False)
+    assert 0 < sum(r[3] for r in recs) < len(recs)

@@ -2,6 +2,11 @@
 
 FP32 kernels with FP32 accumulation: outputs within 1e-4 and parameter
 gradients within 2e-4 of each tensor's largest entry; Adam within 1e-5.
+BF16 operands with FP32 accumulation (the tensor-core path): outputs within 1e-2
+of the largest output (the precision stated for BF16 inference), and parameter
+gradients within 3e-2 of each tensor's largest entry (a BF16 rounding of 2^-9
+relative on both operands of every contraction, forward and backward, through the
+four layers and the head).
 """
 import numpy as np
 import pytest
@@ -113,6 +118,54 @@ def test_training_reduces_the_loss():
     n, K, Ns, C, M, sigma = 256, 4, 3, 16, 32, 0.05
     p, u, y, target = _case(n, K, Ns, C, M, B=64, seed=3)
     net = api.ProposalNet(n, K, Ns, M, sigma, C=C, seed=4)
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    td = torch.tensor(target, dtype=torch.float32, device="cuda")
+    first = net.train_step(ud, yd, td, lr=3e-3).item()
+    for _ in range(200):
+        last = net.train_step(ud, yd, td, lr=3e-3).item()
+    assert last < 0.5 * first
+
+
+@pytest.mark.parametrize("shape", [(256, 4, 3, 16, 32, 6), (1024, 16, 20, 64, 64, 3)])
+def test_bf16_forward_and_gradients_match_oracle(shape):
+    # the tensor-core path at a small shape and at the shape the bench and the learned nudging
+    # run (n = 1024, K = 16, Ns = 20, C = 64, M = 64), against the FP64 oracle network
+    api = require_lib()
+    n, K, Ns, C, M, B = shape
+    sigma = 0.05
+    p, u, y, target = _case(n, K, Ns, C, M, B=B, seed=7)
+    net = api.ProposalNet(n, K, Ns, M, sigma, C=C, params=torch.tensor(_flat(p), dtype=torch.float32),
+                          precision="bf16")
+    ud = torch.tensor(u, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    td = torch.tensor(target, dtype=torch.float32, device="cuda")
+    lam = net.forward(ud, yd).cpu().numpy()
+    x0 = np.stack([CN.features(u[b:b + 1], y[b], sigma)[0] for b in range(B)])
+    ref, _ = CN.forward(p, x0, K, Ns)
+    assert np.max(np.abs(lam - ref)) <= 1e-2 * np.max(np.abs(ref))
+    loss, grads = net.loss_and_grad(ud, yd, td)
+    L, g = CN.loss_and_grad(p, x0, target, K, Ns)
+    assert abs(loss.item() - L) <= 1e-2 * L
+    gg = _unflat(grads.cpu().numpy().astype(np.float64), p)
+    for k in g:
+        assert np.max(np.abs(gg[k] - g[k])) <= 3e-2 * max(1e-6, np.max(np.abs(g[k]))), k
+    if n == 1024:
+        # the FP32 path at the bench shape too
+        net.set_precision("fp32")
+        lam32 = net.forward(ud, yd).cpu().numpy()
+        assert np.max(np.abs(lam32 - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
+        _, g32 = net.loss_and_grad(ud, yd, td)
+        gg = _unflat(g32.cpu().numpy().astype(np.float64), p)
+        for k in g:
+            assert np.max(np.abs(gg[k] - g[k])) <= 2e-4 * max(1e-6, np.max(np.abs(g[k]))), k
+
+
+def test_bf16_training_reduces_the_loss():
+    api = require_lib()
+    n, K, Ns, C, M, sigma = 256, 4, 3, 16, 32, 0.05
+    p, u, y, target = _case(n, K, Ns, C, M, B=64, seed=3)
+    net = api.ProposalNet(n, K, Ns, M, sigma, C=C, seed=4, precision="bf16")
     ud = torch.tensor(u, dtype=torch.float32, device="cuda")
     yd = torch.tensor(y, dtype=torch.float32, device="cuda")
     td = torch.tensor(target, dtype=torch.float32, device="cuda")
