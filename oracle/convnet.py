@@ -21,6 +21,12 @@ m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, p <- p - lr mhat / (sqrt(vhat) + e
 
 Pinned by tests/test_oracle_convnet.py against torch's CPU conv1d (circular
 padding), autograd and torch.optim.Adam in FP64, and central differences.
+
+``operands="bf16"`` evaluates the same network with both operands of every
+contraction (each convolution, the mode projection and the head, forward and
+backward) rounded to BF16 first, as a BF16-operand, FP32-accumulating tensor-core
+path does; the sums themselves stay FP64.  The ReLU masks, decisions on the
+pre-activations, are then taken on the same BF16-operand products as such a path.
 """
 from __future__ import annotations
 
@@ -32,6 +38,24 @@ KSIZE = 5
 STRIDE = 2
 PAD = 2
 NLAYER = 4
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), through FP32 as a value held in
+    FP32 memory would be: keep the top 16 bits of the FP32 pattern after adding
+    0x7FFF plus the lowest kept bit."""
+    f = np.asarray(a, dtype=np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
+def _rounder(operands):
+    if operands is None or operands == "fp64":
+        return lambda a: a
+    if operands == "bf16":
+        return bf16_round
+    raise ValueError(operands)
 
 
 def init_params(C: int, K: int, Ns: int, n: int, seed: int):
@@ -64,24 +88,24 @@ def features(u_start: np.ndarray, y: np.ndarray, sigma: float) -> np.ndarray:
     return x
 
 
-def conv_forward(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+def conv_forward(x: np.ndarray, w: np.ndarray, b: np.ndarray, rnd=lambda a: a) -> np.ndarray:
     """out[b, co, q] = b[co] + sum_ci sum_j w[co, ci, j] x[b, ci, (2q + j - 2) mod L]."""
     B, Ci, L = x.shape
     Lo = L // STRIDE
     idx = (STRIDE * np.arange(Lo)[:, None] + np.arange(KSIZE)[None, :] - PAD) % L   # [Lo, k]
-    cols = x[:, :, idx]                                                               # [B, Ci, Lo, k]
-    return np.einsum("bcqj,ocj->boq", cols, w) + b[None, :, None]
+    cols = rnd(x)[:, :, idx]                                                          # [B, Ci, Lo, k]
+    return np.einsum("bcqj,ocj->boq", cols, rnd(w)) + b[None, :, None]
 
 
-def conv_backward(x: np.ndarray, w: np.ndarray, gout: np.ndarray):
+def conv_backward(x: np.ndarray, w: np.ndarray, gout: np.ndarray, rnd=lambda a: a):
     """Gradients of conv_forward: (dx, dw, db) given dL/dout."""
     B, Ci, L = x.shape
     Lo = L // STRIDE
     idx = (STRIDE * np.arange(Lo)[:, None] + np.arange(KSIZE)[None, :] - PAD) % L
-    cols = x[:, :, idx]
-    dw = np.einsum("boq,bcqj->ocj", gout, cols)
+    cols = rnd(x)[:, :, idx]
+    dw = np.einsum("boq,bcqj->ocj", rnd(gout), cols)
     db = gout.sum(axis=(0, 2))
-    dcols = np.einsum("boq,ocj->bcqj", gout, w)
+    dcols = np.einsum("boq,ocj->bcqj", rnd(gout), rnd(w))
     dx = np.zeros_like(x)
     for q in range(Lo):
         for j in range(KSIZE):
@@ -100,36 +124,38 @@ def mode_matrix(P: int, K: int) -> np.ndarray:
     return S
 
 
-def forward(params, x0: np.ndarray, K: int, Ns: int):
+def forward(params, x0: np.ndarray, K: int, Ns: int, operands=None):
     """lambda [B, Ns, K] and the cache of activations."""
+    rnd = _rounder(operands)
     acts = [x0]
     h = x0
     for l in range(NLAYER):
-        z = conv_forward(h, params[f"w{l}"], params[f"b{l}"])
+        z = conv_forward(h, params[f"w{l}"], params[f"b{l}"], rnd)
         h = np.maximum(z, 0.0)
         acts.append(h)
     B, C, P = h.shape
     S = mode_matrix(P, K)
-    F = np.einsum("bcq,qk->bck", h, S).reshape(B, C * K)
-    lam = F @ params["wh"].T + params["bh"][None, :]
+    F = np.einsum("bcq,qk->bck", rnd(h), rnd(S)).reshape(B, C * K)
+    lam = rnd(F) @ rnd(params["wh"]).T + params["bh"][None, :]
     return lam.reshape(B, Ns, K), (acts, F, S)
 
 
-def loss_and_grad(params, x0: np.ndarray, target: np.ndarray, K: int, Ns: int):
+def loss_and_grad(params, x0: np.ndarray, target: np.ndarray, K: int, Ns: int, operands=None):
     """L = 1/(2B) sum (lambda - target)^2 and dL/dparams (manual backward)."""
-    lam, (acts, F, S) = forward(params, x0, K, Ns)
+    rnd = _rounder(operands)
+    lam, (acts, F, S) = forward(params, x0, K, Ns, operands)
     B = x0.shape[0]
     diff = (lam - target).reshape(B, Ns * K)
     L = 0.5 * float(np.sum(diff * diff)) / B
     g = {}
     glam = diff / B                                   # [B, Ns K]
-    g["wh"] = glam.T @ F
+    g["wh"] = rnd(glam).T @ rnd(F)
     g["bh"] = glam.sum(axis=0)
-    gF = (glam @ params["wh"]).reshape(B, -1, K)      # [B, C, K]
-    gh = np.einsum("bck,qk->bcq", gF, S)
+    gF = (rnd(glam) @ rnd(params["wh"])).reshape(B, -1, K)      # [B, C, K]
+    gh = np.einsum("bck,qk->bcq", rnd(gF), rnd(S))
     for l in reversed(range(NLAYER)):
         gz = gh * (acts[l + 1] > 0.0)
-        dx, dw, db = conv_backward(acts[l], params[f"w{l}"], gz)
+        dx, dw, db = conv_backward(acts[l], params[f"w{l}"], gz, rnd)
         g[f"w{l}"] = dw
         g[f"b{l}"] = db
         gh = dx

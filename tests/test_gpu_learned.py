@@ -12,7 +12,7 @@ Against optimiser nudging on the same twins and cycles:
   not exceed t_{0.95, T-1} times its standard error (a systematic excess of the learned
   RMSE that the twin-to-twin spread cannot explain fails).
 With a network whose drifts are deliberately far off, the fallback fires on every cycle
-and the run equals optimiser nudging bit for bit.
+and the run is optimiser nudging (the same ensembles; the RMSE diagnostic to rounding).
 Training is deterministic (fixed shuffles, weight gradients summed in a fixed order), so
 the run is reproducible on one GPU type.
 """
@@ -75,5 +75,7 @@ def test_fallback_fires_for_a_bad_network():
            for src in ("learned", "learned_fb", "optimiser")}
     assert res["learned"]["mean_forecast_ess"] < cfg.N / 4
     assert res["learned_fb"]["fallback_cycles"] == 4
-    assert res["learned_fb"]["rmse"] == res["optimiser"]["rmse"]
+    # the same ensembles: the forecast ESS (a fixed-order reduction) agrees exactly, the RMSE to
+    # rounding (the diagnostics kernel adds its block partials with atomics, in any order)
     assert res["learned_fb"]["mean_forecast_ess"] == res["optimiser"]["mean_forecast_ess"]
+    assert abs(res["learned_fb"]["rmse"] - res["optimiser"]["rmse"]) <= 1e-12 * res["optimiser"]["rmse"]

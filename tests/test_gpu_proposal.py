@@ -3,10 +3,14 @@
 FP32 kernels with FP32 accumulation: outputs within 1e-4 and parameter
 gradients within 2e-4 of each tensor's largest entry; Adam within 1e-5.
 BF16 operands with FP32 accumulation (the tensor-core path): outputs within 1e-2
-of the largest output (the precision stated for BF16 inference), and parameter
-gradients within 3e-2 of each tensor's largest entry (a BF16 rounding of 2^-9
-relative on both operands of every contraction, forward and backward, through the
-four layers and the head).
+of the largest output of the FP64 oracle (the precision stated for BF16
+inference).  Its gradients differ from the FP64 oracle's by up to a fifth of a
+tensor's largest entry (ReLU masks flip where a pre-activation lies within BF16
+rounding of zero, and the backward signal passes through four layers of BF16
+operands), so they are compared with the oracle evaluated with the same BF16
+rounding of both operands of every contraction: outputs, loss and gradients
+within 2e-3 of the largest entry (FP32 against FP64 accumulation, and the rare
+operand that FP32 and FP64 values round to neighbouring BF16 values).
 """
 import numpy as np
 import pytest
@@ -144,21 +148,24 @@ def test_bf16_forward_and_gradients_match_oracle(shape):
     x0 = np.stack([CN.features(u[b:b + 1], y[b], sigma)[0] for b in range(B)])
     ref, _ = CN.forward(p, x0, K, Ns)
     assert np.max(np.abs(lam - ref)) <= 1e-2 * np.max(np.abs(ref))
+    ref_b, _ = CN.forward(p, x0, K, Ns, operands="bf16")
+    assert np.max(np.abs(lam - ref_b)) <= 2e-3 * np.max(np.abs(ref_b))
     loss, grads = net.loss_and_grad(ud, yd, td)
-    L, g = CN.loss_and_grad(p, x0, target, K, Ns)
-    assert abs(loss.item() - L) <= 1e-2 * L
+    L, g = CN.loss_and_grad(p, x0, target, K, Ns, operands="bf16")
+    assert abs(loss.item() - L) <= 2e-3 * L
     gg = _unflat(grads.cpu().numpy().astype(np.float64), p)
     for k in g:
-        assert np.max(np.abs(gg[k] - g[k])) <= 3e-2 * max(1e-6, np.max(np.abs(g[k]))), k
+        assert np.max(np.abs(gg[k] - g[k])) <= 2e-3 * max(1e-6, np.max(np.abs(g[k]))), k
     if n == 1024:
         # the FP32 path at the bench shape too
         net.set_precision("fp32")
         lam32 = net.forward(ud, yd).cpu().numpy()
         assert np.max(np.abs(lam32 - ref)) <= 1e-4 * max(1.0, np.max(np.abs(ref)))
         _, g32 = net.loss_and_grad(ud, yd, td)
+        _, g64 = CN.loss_and_grad(p, x0, target, K, Ns)
         gg = _unflat(g32.cpu().numpy().astype(np.float64), p)
-        for k in g:
-            assert np.max(np.abs(gg[k] - g[k])) <= 2e-4 * max(1e-6, np.max(np.abs(g[k]))), k
+        for k in g64:
+            assert np.max(np.abs(gg[k] - g64[k])) <= 2e-4 * max(1e-6, np.max(np.abs(g64[k]))), k
 
 
 def test_bf16_training_reduces_the_loss():

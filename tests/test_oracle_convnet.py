@@ -85,3 +85,21 @@ def test_features_scatter_innovation():
     xm = CN.features(u, ym, 0.5)
     assert np.allclose(xm[0, 1, 0:8:4], (y[:2] - u[0, 0:8:4]) / 0.5)
     assert np.all(xm[0, 1, 8::4] == 0) and np.all(np.isfinite(xm))
+
+
+def test_bf16_rounding_of_the_oracle():
+    # bf16_round keeps 8 significant bits, rounding to nearest with ties to even, like a
+    # BF16 conversion of an FP32 value: exact on BF16 values, ties go to the even neighbour
+    a = np.array([1.0, 1.0 + 2.0 ** -7, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -8 + 2.0 ** -20,
+                  -2.5, 0.0, 3.0 * 2.0 ** -130])
+    want = np.array([1.0, 1.0 + 2.0 ** -7, 1.0, 1.0 + 2.0 ** -6, 1.0 + 2.0 ** -7, -2.5, 0.0, 3.0 * 2.0 ** -130])
+    assert np.array_equal(CN.bf16_round(a), want)
+    r = np.random.default_rng(0).normal(size=1000)
+    d = np.abs(CN.bf16_round(r) - r) / np.abs(r)
+    assert d.max() <= 2.0 ** -8 + 1e-12
+    # the BF16-operand network agrees with the FP64 one to BF16 precision in its forward pass
+    p = CN.init_params(8, 4, 3, 64, 1)
+    x0 = np.random.default_rng(1).normal(size=(3, 2, 64))
+    a64, _ = CN.forward(p, x0, 4, 3)
+    a16, _ = CN.forward(p, x0, 4, 3, operands="bf16")
+    assert 0 < np.max(np.abs(a16 - a64)) <= 2e-2 * np.max(np.abs(a64))
