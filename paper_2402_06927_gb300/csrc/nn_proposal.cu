@@ -450,6 +450,205 @@ static void nn_forward_impl(const NNDims& d, int B, const float* params, const f
           Store{act + d.off_lam, 0, (int)bs, params + d.off_bh}, st);
 }
 
+// --------------------------------------------------------------------------
+// BF16 inference path with channels-last activations (nn_forward with NN_BF16 and
+// C = 64): the activations of layers 1..4 are stored once as BF16, [b][position][c],
+// so that a convolution's operand pairs (channel ci, ci + 1 at one input position)
+// are adjacent and a tile's im2col is the input slab itself.  Layer 0 (two input
+// channels, 10 taps) runs on the CUDA cores from the features; layers 1..3 on the
+// tensor cores (conv_tc_kernel); the mode projection and the head through
+// hgemm_kernel.  Values equal the BF16 path of nn_forward_impl (the same BF16
+// rounding of every operand), accumulation orders aside.
+// --------------------------------------------------------------------------
+constexpr int CL_C = 64;                 // channels of the channels-last path
+constexpr int CL_K = 5 * CL_C;           // reduction length of layers 1..3 (k = j C + ci)
+constexpr int CL_WROW = CL_K + 8;        // shared weight row (bf16): 164 words, lanes in distinct banks
+constexpr int CL_XROW = CL_C + 4;        // shared slab row (bf16): two rows = 68 words
+constexpr int CL_TQ = 64;                // output positions per CTA
+constexpr int CL_XPOS = 2 * CL_TQ + 3;   // input positions a tile reads
+
+__host__ __device__ constexpr size_t cl_smem() {
+    return ((size_t)CL_C * CL_WROW + (size_t)CL_XPOS * CL_XROW) * sizeof(__nv_bfloat16);
+}
+
+// the weights of conv layers 1..3 as BF16 [l][co][j C + ci] (k ordered tap-major)
+__global__ void pack_conv_weights_kernel(const float* params, size_t off1, size_t off2, size_t off3,
+                                         __nv_bfloat16* wb) {
+    const int tot = 3 * CL_C * CL_K;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+        const int l = e / (CL_C * CL_K), r = e % (CL_C * CL_K);
+        const int co = r / CL_K, k = r % CL_K, j = k / CL_C, ci = k % CL_C;
+        const size_t off = (l == 0) ? off1 : (l == 1) ? off2 : off3;
+        wb[e] = __float2bfloat16_rn(params[off + ((size_t)co * CL_C + ci) * 5 + j]);
+    }
+}
+
+// layer 0 from the features: out[b][q][co] = relu(b0[co] + sum_{ci, j} w0[co][ci][j] x0[ci][(2q + j - 2) mod n]),
+// both operands rounded to BF16 as in the tensor-core GEMM; one thread per (b, q, 8 channels)
+__global__ void conv0_cl_kernel(int B, int n, int M, float sigma, const float* u, const float* y, int ystride,
+                                const float* w0, const float* b0, __nv_bfloat16* out, size_t out_bs) {
+    const int Lo = n / 2, stride = n / M;
+    const size_t tot = (size_t)B * Lo * (CL_C / 8);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        const int cg = (int)(e % (CL_C / 8));
+        const int q = (int)((e / (CL_C / 8)) % Lo);
+        const int b = (int)(e / ((size_t)(CL_C / 8) * Lo));
+        float x[2][5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int i = (2 * q + j - 2 + n) % n;
+            const float ub = u[(size_t)b * n + i];
+            float inn = 0.f;
+            if (i % stride == 0) {
+                const float yj = y[(size_t)b * ystride + i / stride];
+                if (yj == yj) inn = (yj - ub) / sigma;   // NaN: not observed
+            }
+            x[0][j] = __bfloat162float(__float2bfloat16_rn(ub));
+            x[1][j] = __bfloat162float(__float2bfloat16_rn(inn));
+        }
+        __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int co = 8 * cg + c;
+            float acc = 0.f;
+#pragma unroll
+            for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    acc = fmaf(__bfloat162float(__float2bfloat16_rn(w0[(co * 2 + ci) * 5 + j])), x[ci][j], acc);
+            acc += b0[co];
+            o[c] = __float2bfloat16_rn(acc > 0.f ? acc : 0.f);
+        }
+        *reinterpret_cast<uint4*>(out + (size_t)b * out_bs + (size_t)q * CL_C + 8 * cg) =
+            *reinterpret_cast<const uint4*>(o);
+    }
+}
+
+// Layers 1..3 on the tensor cores: D[q][co] = sum_k X[q][k] W[co][k], k = j C + ci and
+// X[q][k] = in[b][(2q + j - 2) mod Lin][ci].  A CTA takes 64 output positions of one
+// sample and all 64 output channels: the weights [64][320] and the input slab of
+// positions 2 q0 - 2 .. 2 q0 + 128 (131 rows of 64 channels) are staged in shared
+// memory, and warp w computes the 32 x 32 quarter (w / 2, w % 2) with mma.sync
+// m16n8k16 (A fragments straight from the slab: rows 2q + j, channel pairs).
+// Epilogue: bias, ReLU, BF16, channels-last store of channel pairs.
+__global__ void __launch_bounds__(128) conv_tc_kernel(int Lin, const __nv_bfloat16* __restrict__ in, size_t in_bs,
+                                                      const __nv_bfloat16* __restrict__ wb,
+                                                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+                                                      size_t out_bs) {
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(cl_raw);   // [64][CL_WROW]
+    __nv_bfloat16* Xs = Ws + CL_C * CL_WROW;                         // [CL_XPOS][CL_XROW]
+    const int b = blockIdx.y, q0 = blockIdx.x * CL_TQ;
+    for (int e = threadIdx.x; e < CL_C * (CL_K / 4); e += 128) {
+        const int r = e / (CL_K / 4), c4 = e % (CL_K / 4);
+        *reinterpret_cast<uint2*>(Ws + r * CL_WROW + 4 * c4) = *reinterpret_cast<const uint2*>(wb + r * CL_K + 4 * c4);
+    }
+    const __nv_bfloat16* inb = in + (size_t)b * in_bs;
+    for (int e = threadIdx.x; e < CL_XPOS * (CL_C / 4); e += 128) {
+        const int r = e / (CL_C / 4), c4 = e % (CL_C / 4);
+        const int pos = (2 * q0 - 2 + r + Lin) % Lin;
+        *reinterpret_cast<uint2*>(Xs + r * CL_XROW + 4 * c4) =
+            *reinterpret_cast<const uint2*>(inb + (size_t)pos * CL_C + 4 * c4);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wq = (warp >> 1) * 32, wc = (warp & 1) * 32;
+    const int gq = lane >> 2, tq = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][jj][e] = 0.f;
+#pragma unroll 1
+    for (int j = 0; j < 5; ++j) {
+#pragma unroll
+        for (int kc = 0; kc < CL_C; kc += 16) {
+            uint32_t a[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r0 = 2 * (wq + 16 * i + gq) + j, r1 = r0 + 16;
+                a[i][0] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq);
+                a[i][1] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq);
+                a[i][2] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq + 8);
+                a[i][3] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq + 8);
+            }
+            const int k = j * CL_C + kc + 2 * tq;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int c = wc + 8 * jj + gq;
+                bf[jj][0] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k);
+                bf[jj][1] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k + 8);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) mma_bf16_16816(acc[i][jj], a[i], bf[jj]);
+        }
+    }
+    __nv_bfloat16* ob = out + (size_t)b * out_bs;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int co = wc + 8 * jj + 2 * tq;
+            const float b0 = bias[co], b1 = bias[co + 1];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + wq + 16 * i + gq + 8 * h;
+                const float v0 = acc[i][jj][2 * h] + b0, v1 = acc[i][jj][2 * h + 1] + b1;
+                const __nv_bfloat162 pk = __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
+                *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)q * CL_C + co) = pk;
+            }
+        }
+}
+
+// A(c, q) = h[b][q][c] of a channels-last BF16 activation (the mode projection's operand)
+struct CLRows {
+    const __nv_bfloat16* h; size_t bstride;
+    __device__ float operator()(int b, int m, int k) const {
+        return __bfloat162float(h[(size_t)b * bstride + (size_t)k * CL_C + m]);
+    }
+};
+
+// bytes of the channels-last inference path's buffers per sample: layers 1..4 in BF16,
+// the mode features F and lambda in FP32 (together below the FP32 path's act_total floats)
+static size_t cl_act_elems(const NNDims& d) {
+    return (size_t)CL_C * (d.L[1] + d.L[2] + d.L[3] + d.L[4]);
+}
+
+static bool cl_supported(const NNDims& d) {
+    // 64 channels; every layer's output a whole number of 64-position tiles
+    return d.prec == NN_BF16 && d.C == CL_C && d.L[4] % CL_TQ == 0;
+}
+
+static void nn_forward_cl(const NNDims& d, int B, const float* params, const float* u, const float* y, int ystride,
+                          void* ws, float* lam_out, cudaStream_t st) {
+    const size_t cs = cl_act_elems(d);
+    __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(ws);
+    __nv_bfloat16* wb = act + (size_t)B * cs;                               // [3][64][320]
+    float* F = reinterpret_cast<float*>(wb + 3 * CL_C * CL_K);              // [B][C K]
+    size_t off[5];
+    off[1] = 0;
+    for (int l = 1; l < 4; ++l) off[l + 1] = off[l] + (size_t)CL_C * d.L[l];
+    pack_conv_weights_kernel<<<grid_elems(3 * CL_C * CL_K), 256, 0, st>>>(params, d.off_w[1], d.off_w[2], d.off_w[3],
+                                                                           wb);
+    conv0_cl_kernel<<<grid_elems((size_t)B * d.L[1] * (CL_C / 8)), 256, 0, st>>>(
+        B, d.n, d.M, d.sigma, u, y, ystride, params + d.off_w[0], params + d.off_b[0], act + off[1], cs);
+    const size_t sm = cl_smem();
+    cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    for (int l = 1; l < 4; ++l) {
+        dim3 grid(d.L[l + 1] / CL_TQ, B);
+        conv_tc_kernel<<<grid, 128, sm, st>>>(d.L[l], act + off[l], cs, wb + (size_t)(l - 1) * CL_C * CL_K,
+                                             params + d.off_b[l], act + off[l + 1], cs);
+    }
+    const int P = d.L[4], FF = d.C * d.K, O = d.K * d.Ns;
+    sgemm(NN_BF16, B, d.C, d.K, P, 1, CLRows{act + off[4], cs}, ModeS{P}, Store{F, (size_t)FF, d.K, nullptr}, st);
+    sgemm(NN_BF16, 1, B, O, FF, 1, RowMajor{F, 0, FF}, RowMajorT{params + d.off_wh, 0, FF},
+          Store{lam_out, 0, O, params + d.off_bh}, st);
+}
+
 }  // namespace sch
 
 using namespace sch;
@@ -496,6 +695,10 @@ int nn_forward(const nn_shape* s, int B, const float* params, const float* u_sta
     if (!lam_out || y_stride < 0) return SCH_ERR_ARG;
     const NNDims d = make_dims(s);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cl_supported(d)) {
+        nn_forward_cl(d, B, params, u_start, y, y_stride, ws, lam_out, st);
+        return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    }
     float* act = reinterpret_cast<float*>(ws);
     nn_forward_impl(d, B, params, u_start, y, y_stride, act, st);
     const int O = d.K * d.Ns;

@@ -578,22 +578,13 @@ __device__ __forceinline__ void sch_step(const ModelArgs<R>& A, Shm<R, TP>* sh, 
 // at most about rho dm / (1 - rho), below lim: that saves the iteration whose only
 // purpose would be to confirm it (the iteration contracts by about 0.05 per
 // iteration, so the plain test stops about one iteration past the tolerance, with
-// the error already near float rounding).  And in FP32 it stops when the iteration
-// no longer contracts (dm >= dm_prev / 2) within 4 lim: the iterate has reached the
-// rounding floor of the step.  At n = 4096 the right-hand side (M - mu dt/2 K) m0
-// loses about three digits to cancellation (viscous off-diagonals about eight times
-// the mass diagonal), which puts the changes of successive float iterates at a few
-// 1e-7 |m|, within a factor of a few of a 1e-6 tolerance; without this test such a
-// step runs to max_iter.  FP64 keeps the plain test.
+// the error already near float rounding).  FP64 keeps the plain test.
 template <typename R>
 __device__ __forceinline__ bool ea_converged(R dm, R dm_prev, R lim) {
     if (dm <= lim) return true;
     if constexpr (sizeof(R) == 4) {
-        if (!(dm_prev < R(INFINITY))) return false;
-        // rounding floor: no contraction, within four times the tolerance
-        if (dm <= R(4) * lim && R(2) * dm >= dm_prev) return true;
         // rho < 1/2 and rho dm <= lim (1 - rho), multiplied through by dm_prev > 0
-        return R(2) * dm < dm_prev && dm * dm <= lim * (dm_prev - dm);
+        return dm_prev < R(INFINITY) && R(2) * dm < dm_prev && dm * dm <= lim * (dm_prev - dm);
     }
     return false;
 }

@@ -120,7 +120,9 @@ def test_jitter_matches_oracle(name, theta, lam, layout, upto):
     recs = jitter_moves_vs_oracle(g, om, cfg, tdev(m0, dt), tdev(dW, dt), None if la is None else tdev(la, dt),
                                   tdev(y, dt), theta, 4, 77, 1000, range(N), tol, rho=rho)
     assert_decisions(recs, exact=cfg.dtype == "f64")
-    assert len(recs) == 4 * N and 0 < sum(r[2] for r in recs) < len(recs)
+    assert len(recs) == 4 * N
+    if upto is None:   # both outcomes occur (with half the observations every move is accepted)
+        assert 0 < sum(r[2] for r in recs) < len(recs)
 
 
 def test_jitter_moves_equal_one_call():
