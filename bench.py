@@ -908,7 +908,8 @@ def run_filter_kernels(args):
 
 def run_proposal(args):
     """--proposal: the learned proposal network at the learned-proposal workload's size
-    (n = 1024, K = 16, Ns = 20, M = 64, 64 channels) on a batch of B = 8192 particles:
+    (n = 1024, K = 16, Ns = 20, M = 64, 64 channels) on a batch of B = 8192 particles
+    (--proposal-batch):
     nn_forward, nn_backward (loss and all gradients) and nn_adam_step, with BF16
     operands and FP32 accumulation on the tensor cores (the product path) and with FP32
     operands on the CUDA cores (the check path).  Algorithmic flops are the
@@ -921,7 +922,7 @@ def run_proposal(args):
     from paper_2402_06927_gb300.api import ProposalNet
     torch.cuda.set_device(0)
     cfg = get_config("cfg4_f32")
-    n, K, Ns, M, C, B = cfg.n, cfg.K, cfg.Ns, cfg.M, 64, 8192
+    n, K, Ns, M, C, B = cfg.n, cfg.K, cfg.Ns, cfg.M, 64, args.proposal_batch
     net = ProposalNet(n, K, Ns, M, cfg.sigma, C=C, seed=1)
     g = torch.Generator(device="cpu").manual_seed(5)
     u = (0.3 * torch.randn(B, n, generator=g)).cuda()
@@ -1047,6 +1048,7 @@ def main():
                     help="time the learned proposal network (forward, backward, Adam)")
     ap.add_argument("--occupancy", action="store_true",
                     help="jitter launch time at 1 .. 16 warps per SM (occupancy sweep)")
+    ap.add_argument("--proposal-batch", type=int, default=8192, help="--proposal: samples per call")
     ap.add_argument("--train-cycles", type=int, default=200)
     ap.add_argument("--twins", type=int, default=5, help="--nudging: independent twin experiments")
     ap.add_argument("--nudging-workload", default="cfg4_f32", choices=["cfg4_f32", "cfg5_f32"],
