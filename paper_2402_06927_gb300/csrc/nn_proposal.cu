@@ -468,7 +468,7 @@ constexpr int CL_TQ = 64;                // output positions per CTA
 constexpr int CL_XPOS = 2 * CL_TQ + 3;   // input positions a tile reads
 
 __host__ __device__ constexpr size_t cl_smem() {
-    return ((size_t)CL_C * CL_WROW + (size_t)CL_XPOS * CL_XROW) * sizeof(__nv_bfloat16);
+    return ((size_t)CL_C * CL_WROW + 2 * (size_t)CL_XPOS * CL_XROW) * sizeof(__nv_bfloat16);
 }
 
 // the weights of conv layers 1..3 as BF16 [l][co][j C + ci] (k ordered tap-major)
@@ -524,84 +524,110 @@ __global__ void conv0_cl_kernel(int B, int n, int M, float sigma, const float* u
     }
 }
 
-// Layers 1..3 on the tensor cores: D[q][co] = sum_k X[q][k] W[co][k], k = j C + ci and
-// X[q][k] = in[b][(2q + j - 2) mod Lin][ci].  A CTA takes 64 output positions of one
-// sample and all 64 output channels: the weights [64][320] and the input slab of
-// positions 2 q0 - 2 .. 2 q0 + 128 (131 rows of 64 channels) are staged in shared
-// memory, and warp w computes the 32 x 32 quarter (w / 2, w % 2) with mma.sync
-// m16n8k16 (A fragments straight from the slab: rows 2q + j, channel pairs).
-// Epilogue: bias, ReLU, BF16, channels-last store of channel pairs.
-__global__ void __launch_bounds__(128) conv_tc_kernel(int Lin, const __nv_bfloat16* __restrict__ in, size_t in_bs,
-                                                      const __nv_bfloat16* __restrict__ wb,
-                                                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
-                                                      size_t out_bs) {
-    extern __shared__ __align__(16) unsigned char cl_raw[];
-    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(cl_raw);   // [64][CL_WROW]
-    __nv_bfloat16* Xs = Ws + CL_C * CL_WROW;                         // [CL_XPOS][CL_XROW]
-    const int b = blockIdx.y, q0 = blockIdx.x * CL_TQ;
-    for (int e = threadIdx.x; e < CL_C * (CL_K / 4); e += 128) {
-        const int r = e / (CL_K / 4), c4 = e % (CL_K / 4);
-        *reinterpret_cast<uint2*>(Ws + r * CL_WROW + 4 * c4) = *reinterpret_cast<const uint2*>(wb + r * CL_K + 4 * c4);
-    }
+// 8-byte asynchronous copy global -> shared (cp.async, completion tracked by groups)
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// the input slab of tile (b, q0): positions 2 q0 - 2 .. 2 q0 + 128 (mod Lin), 64 channels each
+__device__ __forceinline__ void cl_issue_slab(__nv_bfloat16* Xs, const __nv_bfloat16* in, size_t in_bs, int Lin,
+                                              int b, int q0) {
     const __nv_bfloat16* inb = in + (size_t)b * in_bs;
     for (int e = threadIdx.x; e < CL_XPOS * (CL_C / 4); e += 128) {
         const int r = e / (CL_C / 4), c4 = e % (CL_C / 4);
         const int pos = (2 * q0 - 2 + r + Lin) % Lin;
-        *reinterpret_cast<uint2*>(Xs + r * CL_XROW + 4 * c4) =
-            *reinterpret_cast<const uint2*>(inb + (size_t)pos * CL_C + 4 * c4);
+        cp_async8(Xs + r * CL_XROW + 4 * c4, inb + (size_t)pos * CL_C + 4 * c4);
     }
-    __syncthreads();
+}
+
+// Layers 1..3 on the tensor cores: D[q][co] = sum_k X[q][k] W[co][k], k = j C + ci and
+// X[q][k] = in[b][(2q + j - 2) mod Lin][ci].  A persistent CTA stages the layer's weights
+// [64][320] in shared memory once, then takes tiles of 64 output positions of one sample
+// (all 64 output channels) in turn: the input slab of positions 2 q0 - 2 .. 2 q0 + 128
+// (131 rows of 64 channels) is copied with cp.async into one of two buffers while the
+// previous tile is computed.  Warp w computes the 32 x 32 quarter (w / 2, w % 2) of a
+// tile with mma.sync m16n8k16, its A fragments straight from the slab (rows 2q + j,
+// channel pairs).  Epilogue: bias, ReLU, BF16, channels-last store of channel pairs.
+__global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv_bfloat16* __restrict__ in,
+                                                      size_t in_bs, const __nv_bfloat16* __restrict__ wb,
+                                                      const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+                                                      size_t out_bs) {
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(cl_raw);   // [64][CL_WROW]
+    __nv_bfloat16* Xbuf = Ws + CL_C * CL_WROW;                       // [2][CL_XPOS][CL_XROW]
+    const int tpb = (Lin / 2) / CL_TQ, ntiles = B * tpb;
+    for (int e = threadIdx.x; e < CL_C * (CL_K / 4); e += 128) {
+        const int r = e / (CL_K / 4), c4 = e % (CL_K / 4);
+        *reinterpret_cast<uint2*>(Ws + r * CL_WROW + 4 * c4) = *reinterpret_cast<const uint2*>(wb + r * CL_K + 4 * c4);
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wq = (warp >> 1) * 32, wc = (warp & 1) * 32;
     const int gq = lane >> 2, tq = lane & 3;
-    float acc[2][4][4];
+    int t = blockIdx.x;
+    if (t < ntiles) cl_issue_slab(Xbuf, in, in_bs, Lin, t / tpb, (t % tpb) * CL_TQ);
+    cp_async_commit();
+    for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int tn = t + gridDim.x;
+        if (tn < ntiles)
+            cl_issue_slab(Xbuf + ((it + 1) & 1) * CL_XPOS * CL_XROW, in, in_bs, Lin, tn / tpb, (tn % tpb) * CL_TQ);
+        cp_async_commit();
+        cp_async_wait1();   // this tile's slab (the group before the one just committed)
+        __syncthreads();
+        const __nv_bfloat16* Xs = Xbuf + (it & 1) * CL_XPOS * CL_XROW;
+        const int b = t / tpb, q0 = (t % tpb) * CL_TQ;
+        float acc[2][4][4];
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
+            for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][jj][e] = 0.f;
+                for (int e = 0; e < 4; ++e) acc[i][jj][e] = 0.f;
 #pragma unroll 1
-    for (int j = 0; j < 5; ++j) {
+        for (int j = 0; j < 5; ++j) {
 #pragma unroll
-        for (int kc = 0; kc < CL_C; kc += 16) {
-            uint32_t a[2][4], bf[4][2];
+            for (int kc = 0; kc < CL_C; kc += 16) {
+                uint32_t a[2][4], bf[4][2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r0 = 2 * (wq + 16 * i + gq) + j, r1 = r0 + 16;
-                a[i][0] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq);
-                a[i][1] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq);
-                a[i][2] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq + 8);
-                a[i][3] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq + 8);
+                for (int i = 0; i < 2; ++i) {
+                    const int r0 = 2 * (wq + 16 * i + gq) + j, r1 = r0 + 16;
+                    a[i][0] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq);
+                    a[i][1] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq);
+                    a[i][2] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq + 8);
+                    a[i][3] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq + 8);
+                }
+                const int k = j * CL_C + kc + 2 * tq;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int c = wc + 8 * jj + gq;
+                    bf[jj][0] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k);
+                    bf[jj][1] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k + 8);
+                }
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) mma_bf16_16816(acc[i][jj], a[i], bf[jj]);
             }
-            const int k = j * CL_C + kc + 2 * tq;
+        }
+        __nv_bfloat16* ob = out + (size_t)b * out_bs;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
-                const int c = wc + 8 * jj + gq;
-                bf[jj][0] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k);
-                bf[jj][1] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k + 8);
+                const int co = wc + 8 * jj + 2 * tq;
+                const float b0 = bias[co], b1 = bias[co + 1];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = q0 + wq + 16 * i + gq + 8 * h;
+                    const float v0 = acc[i][jj][2 * h] + b0, v1 = acc[i][jj][2 * h + 1] + b1;
+                    const __nv_bfloat162 pk = __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
+                    *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)q * CL_C + co) = pk;
+                }
             }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) mma_bf16_16816(acc[i][jj], a[i], bf[jj]);
-        }
+        __syncthreads();   // every warp is done with this buffer before it is refilled
     }
-    __nv_bfloat16* ob = out + (size_t)b * out_bs;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-            const int co = wc + 8 * jj + 2 * tq;
-            const float b0 = bias[co], b1 = bias[co + 1];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int q = q0 + wq + 16 * i + gq + 8 * h;
-                const float v0 = acc[i][jj][2 * h] + b0, v1 = acc[i][jj][2 * h + 1] + b1;
-                const __nv_bfloat162 pk = __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
-                *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)q * CL_C + co) = pk;
-            }
-        }
 }
 
 // A(c, q) = h[b][q][c] of a channels-last BF16 activation (the mode projection's operand)
@@ -638,10 +664,17 @@ static void nn_forward_cl(const NNDims& d, int B, const float* params, const flo
         B, d.n, d.M, d.sigma, u, y, ystride, params + d.off_w[0], params + d.off_b[0], act + off[1], cs);
     const size_t sm = cl_smem();
     cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    // persistent CTAs: as many as fit on the device at once (two per SM at 78 KB of shared memory)
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, conv_tc_kernel, 128, sm);
+    const int resident = max(1, nsm * max(1, per_sm));
     for (int l = 1; l < 4; ++l) {
-        dim3 grid(d.L[l + 1] / CL_TQ, B);
-        conv_tc_kernel<<<grid, 128, sm, st>>>(d.L[l], act + off[l], cs, wb + (size_t)(l - 1) * CL_C * CL_K,
-                                             params + d.off_b[l], act + off[l + 1], cs);
+        const int ntiles = B * (d.L[l + 1] / CL_TQ);
+        conv_tc_kernel<<<min(ntiles, resident), 128, sm, st>>>(B, d.L[l], act + off[l], cs,
+                                                               wb + (size_t)(l - 1) * CL_C * CL_K, params + d.off_b[l],
+                                                               act + off[l + 1], cs);
     }
     const int P = d.L[4], FF = d.C * d.K, O = d.K * d.Ns;
     sgemm(NN_BF16, B, d.C, d.K, P, 1, CLRows{act + off[4], cs}, ModeS{P}, Store{F, (size_t)FF, d.K, nullptr}, st);

@@ -213,7 +213,8 @@ struct GState {
 };
 
 // One implicit-midpoint step of the particle (warp w's share), W0 holding the step's
-// dU/4 at this lane's nodes on entry (see wstep_core for the iteration).
+// dU/4 at this lane's nodes on entry (see wstep_core for the iteration).  R0sm is the
+// warp's three [P][CS][32] float2 slots: R0 = (M - mu dt/2 K) m0, W0 and m0.
 template <int CS, int P, int W>
 __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
                                             const GLane& gl, GState<CS, P>& X, float2* R0sm, float2 (&W0)[P][CS],
@@ -224,6 +225,8 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
     gends<W>(W0[0][0].x, W0[P - 1][CS - 1].y, nqL, nqR, gs, w, ex);
     const float dt8s = A.dt8;
     const float W0L = fmaf(dt8s, X.uL, nqL), W0R = fmaf(dt8s, X.uR, nqR);
+    float2* W0sm = R0sm + P * CS * 32;
+    float2* Msm = W0sm + P * CS * 32;
     {
         const float2 dt8 = f2b(A.dt8);
         float2 lo, hi;
@@ -233,9 +236,10 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
         for (int p = 0; p < P; ++p)
 #pragma unroll
             for (int i = 0; i < CS; ++i) {
-                W0[p][i] = f2fma(dt8, X.u[p][i], W0[p][i]);
+                W0sm[(p * CS + i) * 32 + lane] = f2fma(dt8, X.u[p][i], W0[p][i]);
                 R0sm[(p * CS + i) * 32 + lane] = f2fma(
                     c0p, f2add(wleft<CS, P>(X.m, p, i, lo), wright<CS, P>(X.m, p, i, hi)), f2mul(b0p, X.m[p][i]));
+                Msm[(p * CS + i) * 32 + lane] = X.m[p][i];
             }
     }
     float2 mi[P][CS];
@@ -254,8 +258,8 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
             for (int p = 0; p < P; ++p)
 #pragma unroll
                 for (int i = 0; i < CS; ++i) {
-                    wv[p][i] = f2fma(dt8, X.u[p][i], W0[p][i]);
-                    mb[p][i] = f2add(X.m[p][i], mi[p][i]);
+                    wv[p][i] = f2fma(dt8, X.u[p][i], W0sm[(p * CS + i) * 32 + lane]);
+                    mb[p][i] = f2add(Msm[(p * CS + i) * 32 + lane], mi[p][i]);
                 }
             float2 wl, wr, ml, mr;
             gwhalo<CS, P>(wv, fmaf(dt8s, X.uL, W0L), fmaf(dt8s, X.uR, W0R), wl, wr);
@@ -370,12 +374,15 @@ __device__ __forceinline__ void gsum2(GShared<W>* gs, double& a, double& b) {
 
 template <int CS, int P, int W>
 __host__ __device__ constexpr size_t gsmem_base() {
-    return (sizeof(GShared<W>) + 15) / 16 * 16 + (size_t)W * P * CS * 32 * sizeof(float2);
+    return (sizeof(GShared<W>) + 15) / 16 * 16 + (size_t)3 * W * P * CS * 32 * sizeof(float2);
 }
 
-// resident CTAs per SM the kernels are compiled for: 32 W threads each, with at most
-// 65536 / (2 x 32 W) registers a thread
-constexpr int GMINB = 2;
+// Resident CTAs per SM the kernels are compiled for: 32 W threads each, with at most
+// 65536 / (3 x 32 W) registers a thread (168 at W = 4).  To get there the step's fixed
+// fields W0 = dt/8 u0 + dU/4 and m0 live in shared memory beside R0, one [P][CS][32]
+// float2 slot each per warp, read once per Picard iteration; against two CTAs with
+// them in registers (233 registers) this ran the large-run filter 3% faster.
+constexpr int GMINB = 3;
 
 template <int CS, int P, int W>
 __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float>
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GShared<W>* gs = reinterpret_cast<GShared<W>*>(smem_raw);
     const int w = threadIdx.x >> 5;
-    float2* R0sm = reinterpret_cast<float2*>(smem_raw + (sizeof(GShared<W>) + 15) / 16 * 16) + w * P * CS * 32;
+    float2* R0sm = reinterpret_cast<float2*>(smem_raw + (sizeof(GShared<W>) + 15) / 16 * 16) + 3 * w * P * CS * 32;
     float* noise = reinterpret_cast<float*>(smem_raw + gsmem_base<CS, P, W>());
     const int p = blockIdx.x;
     const size_t NK = (size_t)io.Ns * A.K;
@@ -429,7 +436,7 @@ __global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float>
     if (io.tstate && io.tstate[4] == 0.0) return;
     GShared<W>* gs = reinterpret_cast<GShared<W>*>(smem_raw);
     const int t = threadIdx.x, w = t >> 5;
-    float2* R0sm = reinterpret_cast<float2*>(smem_raw + (sizeof(GShared<W>) + 15) / 16 * 16) + w * P * CS * 32;
+    float2* R0sm = reinterpret_cast<float2*>(smem_raw + (sizeof(GShared<W>) + 15) / 16 * 16) + 3 * w * P * CS * 32;
     const double theta = io.tstate ? io.tstate[2] : io.theta;
     const int p = blockIdx.x;
     const int Ns = io.Ns, K = A.K, NK = Ns * K;

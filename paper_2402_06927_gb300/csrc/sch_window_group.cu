@@ -61,12 +61,12 @@ int launch_gjitter(int cs, int W, const ModelArgs<float>& A, const WArgs& Wa, co
 }
 
 size_t gwindow_smem(int cs, int W, int Ns, int K) {
-    return (sizeof(GShared<GW_MAX>) + 15) / 16 * 16 + (size_t)W * GP * cs * 32 * sizeof(float2) +
+    return (sizeof(GShared<GW_MAX>) + 15) / 16 * 16 + (size_t)3 * W * GP * cs * 32 * sizeof(float2) +
            (size_t)Ns * K * sizeof(float);
 }
 
 size_t gjitter_smem(int cs, int W, int Ns, int K) {
-    return (sizeof(GShared<GW_MAX>) + 15) / 16 * 16 + (size_t)W * GP * cs * 32 * sizeof(float2) +
+    return (sizeof(GShared<GW_MAX>) + 15) / 16 * 16 + (size_t)3 * W * GP * cs * 32 * sizeof(float2) +
            (size_t)3 * Ns * K * sizeof(float);
 }
 
