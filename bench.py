@@ -503,7 +503,7 @@ def run_nudging(args):
     sigma = 0.02), FP32 fields, the network in BF16 with FP32 accumulation.
 
     Training pairs: pf_nudge (open loop, L-BFGS to max|grad| <= 1e-6) on `--train-cycles`
-    cycles of a twin experiment x N particles; the network is trained with its own GPU
+    cycles of a twin experiment x min(N, 1024) particles (every N/1024-th); the network is trained with its own GPU
     kernels.  Then `--twins` fresh twin experiments are assimilated `--steps` cycles each with
     learned nudging backed by the optimiser (pf_nudge for any cycle whose forecast ESS under
     the network's drift is below N/4: the product path), the network alone, optimiser
@@ -521,9 +521,10 @@ def run_nudging(args):
     cfg = get_config(args.nudging_workload)
     g = SchModel.from_config(cfg)
     u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
-    train_cycles = args.train_cycles if cfg.N <= 1024 else max(1, args.train_cycles * 1024 // cfg.N)
-    U, Y, T, gst = PR.generate_pairs(g, cfg.N, cfg.Ns, train_cycles, 7, u0, cfg.ess_min, cfg.rho,
-                                     cfg.n_jitter, cfg.prior_scale, max_iter=60, gtol=1e-6)
+    # at most 1024 particles nudged per cycle: N = 8192 spreads its pairs over eight times the cycles
+    keep = min(cfg.N, 1024)
+    U, Y, T, gst = PR.generate_pairs(g, cfg.N, cfg.Ns, args.train_cycles, 7, u0, cfg.ess_min, cfg.rho,
+                                     cfg.n_jitter, cfg.prior_scale, max_iter=60, gtol=1e-6, keep=keep)
     net = ProposalNet(cfg.n, cfg.K, cfg.Ns, cfg.M, cfg.sigma, C=64, seed=1, precision="bf16")
     tst = PR.train(net, U, Y, T, epochs=args.epochs, batch=256, lr=1e-3)
     sources = ("learned_fb", "learned", "hybrid", "optimiser", "none")

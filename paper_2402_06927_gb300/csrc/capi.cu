@@ -259,6 +259,8 @@ void fill_args(const sch_params& p, int C, ModelArgs<R>& A) {
         A.amp4[j] = (R)(0.25 * p.amps[j]);
         A.rot_c[j] = (R)cos(2.0 * M_PI * (j + 1) / p.n);
         A.rot_s[j] = (R)sin(2.0 * M_PI * (j + 1) / p.n);
+        const double sh = sin(M_PI * (j + 1) / p.n);
+        A.rot_d[j] = (R)(-4.0 * sh * sh);
     }
     const int TP = p.n / C;
     HTab th, tm, ts, tpic;

@@ -63,6 +63,7 @@ struct ModelArgs {
     CTab<R> smooth;         // M + K (the (I - d_xx) smoothing of the prior)
     CTab<R> pic;            // M + mu dt/2 K (explicit-advection Picard matrix)
     R rot_c[SCH_MAX_K / 2], rot_s[SCH_MAX_K / 2];   // cos(j 2 pi / n), sin(j 2 pi / n), j = 1..K/2
+    R rot_d[SCH_MAX_K / 2];  // 2 cos(j 2 pi / n) - 2 = -4 sin^2(j pi / n): the node-to-node recurrence
     RTab<R> rhel, rmass, rsmooth, rpic;
     HBasis<R> hb;
     CTab<R> matern;         // M + kappa^-2 K (Matern noise)

@@ -212,9 +212,11 @@ __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][C
 // wq_{2j-1} cos(j theta_i).  s1[p], c1[p]: sin and cos of the angles of the
 // first nodes of stream p's two sub-chunks; the harmonics' start values follow
 // the Chebyshev recurrence in j.  Along a sub-chunk each harmonic's value
-// v = a sin(j theta) + b cos(j theta) and its quadrature q = a cos(j theta) -
-// b sin(j theta) are rotated together by the angle j 2 pi / n, so a node costs
-// one rotation and one add per harmonic.
+// v_i = a sin(j theta_i) + b cos(j theta_i) obeys v_{i+1} = 2 cos(j dtheta) v_i -
+// v_{i-1} (dtheta = 2 pi / n), run in difference form for accuracy at small angles:
+// d_{i+1} = (2 cos(j dtheta) - 2) v_i + d_i, v_{i+1} = v_i + d_{i+1}, started from v_0
+// and v_1 (one rotation of v_0 with its quadrature).  A node costs three float-pair
+// operations per harmonic (recurrence and sum).
 template <int CS, int P>
 __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* wq, const float2 (&s1)[P],
                                        const float2 (&c1)[P], float2 (&nq)[P][CS]) {
@@ -228,19 +230,20 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* w
     }
     for (int j = 0; j < A.K2; ++j) {
         const float a = wq[2 * j], b = wq[2 * j + 1];
-        const float2 rc = f2b(A.rot_c[j]), rs = f2b(A.rot_s[j]), nrs = f2b(-A.rot_s[j]);
+        const float2 rc = f2b(A.rot_c[j]), rs = f2b(A.rot_s[j]), rd = f2b(A.rot_d[j]);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             float2 v = f2fma(f2b(a), sj[p], f2mul(f2b(b), cj[p]));
-            float2 q = f2fma(f2b(a), cj[p], f2mul(f2b(-b), sj[p]));
+            const float2 q = f2fma(f2b(a), cj[p], f2mul(f2b(-b), sj[p]));
+            float2 vn = f2fma(v, rc, f2mul(q, rs));
+            float2 d = f2sub(vn, v);
+            nq[p][0] = (j == 0) ? v : f2add(nq[p][0], v);
+            nq[p][1] = (j == 0) ? vn : f2add(nq[p][1], vn);
 #pragma unroll
-            for (int i = 0; i < CS; ++i) {
-                nq[p][i] = (j == 0) ? v : f2add(nq[p][i], v);
-                if (i < CS - 1) {
-                    const float2 v2 = f2fma(v, rc, f2mul(q, rs));
-                    q = f2fma(q, rc, f2mul(v, nrs));
-                    v = v2;
-                }
+            for (int i = 2; i < CS; ++i) {
+                d = f2fma(rd, vn, d);
+                vn = f2add(vn, d);
+                nq[p][i] = (j == 0) ? vn : f2add(nq[p][i], vn);
             }
             const float2 twoc = f2add(c1[p], c1[p]);
             const float2 sn2 = f2fma(twoc, sj[p], nsjm[p]), cn2 = f2fma(twoc, cj[p], ncjm[p]);

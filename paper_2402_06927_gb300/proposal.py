@@ -46,8 +46,11 @@ def make_twin(g: SchModel, Ns: int, cycles: int, seed: int, u0: torch.Tensor) ->
 
 
 def generate_pairs(g: SchModel, N: int, Ns: int, cycles: int, seed: int, u0: torch.Tensor, ess_min: float,
-                   rho: float, n_jitter: int, prior_scale: float, max_iter: int = 30, gtol: float = 1e-4):
-    """(U [P, n], Y [P, M], T [P, Ns, K]) with P = N cycles, plus generation statistics."""
+                   rho: float, n_jitter: int, prior_scale: float, max_iter: int = 30, gtol: float = 1e-4,
+                   keep: int = 0):
+    """(U [P, n], Y [P, M], T [P, Ns, K]) with P = N cycles (or keep cycles: only every
+    (N / keep)-th particle of each cycle's ensemble is nudged, which spreads the same number
+    of pairs over more cycles, i.e. more observation vectors), plus generation statistics."""
     twin = make_twin(g, Ns, cycles, seed, u0)
     f = EnsembleFilter(g, N, Ns, ess_min, rho, n_jitter, seed)
     m0, _ = g.prior_sample(N, u0, seed, prior_scale)
@@ -55,13 +58,15 @@ def generate_pairs(g: SchModel, N: int, Ns: int, cycles: int, seed: int, u0: tor
     U, Y, T = [], [], []
     t0 = time.perf_counter()
     iters = []
+    stride = N // keep if 0 < keep < N else 1
     for c in range(cycles):
         y = twin.ys[c]
-        u_start = g.u_from_m(f.m_start)
-        nd = g.nudge(f.m_start, y, Ns, mode="open_loop", max_iter=max_iter, gtol=gtol, seed=seed,
+        m_sel = f.m_start[::stride].contiguous()
+        u_start = g.u_from_m(m_sel)
+        nd = g.nudge(m_sel, y, Ns, mode="open_loop", max_iter=max_iter, gtol=gtol, seed=seed,
                      ctr=1_000_000 + c)
         U.append(u_start.float())
-        Y.append(y.float()[None].expand(N, -1).contiguous())
+        Y.append(y.float()[None].expand(m_sel.shape[0], -1).contiguous())
         T.append(nd["lam"].float())
         iters.append(nd["iters"].float().mean().item())
         f.set_drift(None)
