@@ -436,6 +436,8 @@ bool gtab_host(const HTab& T, const RTab<double>& Q, int S, int W, GTab& G) {
     G.p2_31 = (float)ti[31 * 32 + 31];
     G.cq = (float)(T.ge * Q.q[S - 1]);
     G.geL = (float)Q.geL;
+    G.ldiag = fmax(fabs(LA), fabs(LC)) <= ldexp(fabs(LB), -26) ? 1 : 0;
+    G.iLB = (float)(1.0 / LB);
     return true;
 }
 

@@ -179,6 +179,80 @@ __device__ __forceinline__ const GSlot* gwreduced(const WTab& T, const RTab<floa
     return sl;
 }
 
+// The same solve when the lane-level system is diagonal to float rounding (GTab.ldiag:
+// the Picard matrix at n = 4096 with 8-node sub-chunks couples neighbouring lanes by
+// 1.9e-9 of the diagonal): EL_g = LD_g / LB.  Only lane 31's row needs the next warp's
+// lane 0 (pd_0, qd_0), and lane 0's previous lane is the previous warp's lane 31, so each
+// warp publishes pd_0, qd_0 and LD_0 of its lane 0 and the part of lane 31's LD that is
+// its own; after one barrier every warp completes lane 31's row and forms the values
+// outside its ends.  Outputs as gwreduced.
+template <int P, int W>
+__device__ __forceinline__ void gwreduced_ldiag(const WTab& T, const RTab<float>& Q, const GTab& G,
+                                                const float2 (&pd)[P], const float2 (&de)[P], float2 (&E)[P],
+                                                float2 (&F)[P], float& Ep, float& Fn, float& Lv, float& Rv,
+                                                GShared<W>* gs, int w, int& ex) {
+    constexpr int S = 2 * P;
+    const int lane = threadIdx.x & 31;
+    float pr[S], dr[S];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        pr[p] = pd[p].x;
+        pr[p + P] = pd[p].y;
+        dr[p] = de[p].x;
+        dr[p + P] = de[p].y;
+    }
+    const float pdn = __shfl_sync(FULL, pr[0], (lane + 1) & 31);
+    const float pd_next = (lane == 31) ? 0.f : pdn;
+    float D[S];
+#pragma unroll
+    for (int r = 0; r < S; ++r) D[r] = dr[r] - T.ae * pr[r] - T.ge * ((r == S - 1) ? pd_next : pr[r + 1]);
+    float dl[S], dp[S];
+    dl[0] = 0.f;
+#pragma unroll
+    for (int r = 1; r < S; ++r) dl[r] = (D[r] - Q.A * dl[r - 1]) * Q.q[r];
+    dp[S - 1] = 0.f;
+    dp[0] = 0.f;
+#pragma unroll
+    for (int r = S - 2; r >= 1; --r) dp[r] = dl[r] - Q.ga[r] * dp[r + 1];
+    const float DF = (S == 2) ? D[0] : D[0] - Q.Cc * dp[1];
+    const float qd = DF * Q.iBF;
+    const float nqdr = __shfl_sync(FULL, qd, (lane + 1) & 31);
+    const float nqd = (lane == 31) ? 0.f : nqdr;
+    const float LD = dl[S - 1] - Q.aeL * qd - Q.geL * nqd;   // lane 31: without the next warp's part
+    const float ld31 = __shfl_sync(FULL, LD, 31);
+    GSlot* sl = gs->slot[ex & 1];
+    if (lane == 0) sl[w].a = make_float4(pr[0], qd, LD, ld31);
+    __syncthreads();
+    ++ex;
+    const float4 sp = sl[(w + W - 1) % W].a, so = sl[w].a, sn = sl[(w + 1) % W].a;
+    // lane 31's row of this warp and of the previous one, completed with the next warp's lane 0
+    const float el31 = (so.w - (G.cq * sn.x + G.geL * sn.y)) * G.iLB;
+    const float elp31 = (sp.w - (G.cq * so.x + G.geL * so.y)) * G.iLB;
+    const float EL = (lane == 31) ? el31 : LD * G.iLB;
+    const float Epr = __shfl_sync(FULL, EL, (lane + 31) & 31);
+    Ep = (lane == 0) ? elp31 : Epr;
+    const float Ff = qd - Q.qa * Ep - Q.qc * EL;
+    float Er[S], Fr[S];
+    Er[0] = Ff;
+#pragma unroll
+    for (int r = 1; r < S - 1; ++r) Er[r] = dp[r] - Q.alp[r] * Ff - Q.gap[r] * EL;
+    Er[S - 1] = EL;
+#pragma unroll
+    for (int r = 0; r < S; ++r) Fr[r] = pr[r] - T.pa * ((r == 0) ? Ep : Er[r - 1]) - T.pc * Er[r];
+    // the next warp's first node: its lane 0's first row
+    const float el0n = sn.z * G.iLB;
+    const float Ffn = sn.y - Q.qa * el31 - Q.qc * el0n;
+    Rv = sn.x - T.pa * el31 - T.pc * Ffn;
+    Lv = elp31;
+    const float Fnr = __shfl_sync(FULL, Fr[0], (lane + 1) & 31);
+    Fn = (lane == 31) ? Rv : Fnr;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        E[p] = make_float2(Er[p], Er[p + P]);
+        F[p] = make_float2(Fr[p], Fr[p + P]);
+    }
+}
+
 // per-lane vectors of the two tables and the CTA's exchange state
 struct GLane {
     float phi_p, psi_p, phi_h, psi_h;
@@ -215,7 +289,7 @@ struct GState {
 // One implicit-midpoint step of the particle (warp w's share), W0 holding the step's
 // dU/4 at this lane's nodes on entry (see wstep_core for the iteration).  R0sm is the
 // warp's three [P][CS][32] float2 slots: R0 = (M - mu dt/2 K) m0, W0 and m0.
-template <int CS, int P, int W>
+template <int CS, int P, int W, int PD>
 __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
                                             const GLane& gl, GState<CS, P>& X, float2* R0sm, float2 (&W0)[P][CS],
                                             GShared<W>* gs, int w, int& ex, int& iters, int& flags) {
@@ -280,8 +354,11 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
         float2 pd[P], de[P], E[P], F[P];
         float Ep, Fn;
         wsweep<CS, P>(Wa.pic, x, pd, de);
-        gwreduced<P, W>(Wa.pic, Wa.rpic, G.pic, gl.phi_p, gl.psi_p, pd, de, E, F, Ep, Fn, miL, miR, gs, w, ex,
-                        0.f, 0.f);
+        if constexpr (PD)
+            gwreduced_ldiag<P, W>(Wa.pic, Wa.rpic, G.pic, pd, de, E, F, Ep, Fn, miL, miR, gs, w, ex);
+        else
+            gwreduced<P, W>(Wa.pic, Wa.rpic, G.pic, gl.phi_p, gl.psi_p, pd, de, E, F, Ep, Fn, miL, miR, gs, w, ex,
+                            0.f, 0.f);
         float2 mn[P][CS];
         wback<CS, P>(Wa.pic, x, F, E, mn);
         float dmax = 0.f, mmax = 0.f;
@@ -384,7 +461,7 @@ __host__ __device__ constexpr size_t gsmem_base() {
 // them in registers (233 registers) this ran the large-run filter 3% faster.
 constexpr int GMINB = 3;
 
-template <int CS, int P, int W>
+template <int CS, int P, int W, int PD>
 __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
                                                                 WindowIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -407,7 +484,7 @@ __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float>
     for (int s = 0; s < io.Ns; ++s) {
         float2 W0[P][CS];
         wnoise<CS, P>(A, noise + s * A.K, s1, c1, W0);
-        gwstep_core<CS, P, W>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, flags);
+        gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, flags);
     }
     wstore<CS, P>(io.m_out + (size_t)p * A.n, X.m);
     wstore<CS, P>(io.u_out + (size_t)p * A.n, X.u);
@@ -428,7 +505,8 @@ __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float>
 
 // PCN jittering (Sec. 3.1.2) with W warps per particle: as wjitter_kernel, the
 // proposals drawn by the whole CTA, the decision taken by thread 0 and shared.
-template <int CS, int P, int W>
+// PD: the Picard solve's lane-level system is diagonal (gwreduced_ldiag).
+template <int CS, int P, int W, int PD>
 __global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
                                                                 JitterIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -476,7 +554,7 @@ __global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float>
         for (int s = 0; s < Ns; ++s) {
             float2 W0[P][CS];
             wnoise<CS, P>(A, noise + s * K, s1, c1, W0);
-            gwstep_core<CS, P, W>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl);
+            gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl);
         }
         double mis = wmisfit<CS, P>(A, X.u, io.y);
         double gsum = window_girsanov(A, prop, lam, Ns);

@@ -118,6 +118,11 @@ struct GTab {
     float p2_0, p2_31;
     float cq, geL;
     float bprev[2 * GW_MAX], bself[2 * GW_MAX], aself[2 * GW_MAX], anext[2 * GW_MAX];
+    // 1 when the lane-level system is diagonal to 2^-26 (|LA|, |LC| <= 2^-26 |LB|): then
+    // EL_g = LD_g / LB to well below float rounding, and the solve needs neither the PCR
+    // nor the 2W system, only the neighbouring warps' boundary rows
+    int ldiag;
+    float iLB;
 };
 
 struct GArgs {

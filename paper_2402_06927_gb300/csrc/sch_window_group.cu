@@ -20,22 +20,35 @@ void prep(Kern k, size_t sm) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
+template <int CS, int W, int PD>
+int window_pd(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G, const WindowIO<float>& io, int N,
+              cudaStream_t st) {
+    const size_t sm = smem_of<CS, W>(io.Ns, A.K, 1);
+    prep(gwindow_kernel<CS, GP, W, PD>, sm);
+    gwindow_kernel<CS, GP, W, PD><<<N, 32 * W, sm, st>>>(A, Wa, G, io);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+template <int CS, int W, int PD>
+int jitter_pd(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G, const JitterIO<float>& io, int N,
+              cudaStream_t st) {
+    const size_t sm = smem_of<CS, W>(io.Ns, A.K, 3);
+    prep(gjitter_kernel<CS, GP, W, PD>, sm);
+    gjitter_kernel<CS, GP, W, PD><<<N, 32 * W, sm, st>>>(A, Wa, G, io);
+    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+}
+
+// the kernels specialised to the Picard table's lane-level system (diagonal or not)
 template <int CS, int W>
 int window(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G, const WindowIO<float>& io, int N,
            cudaStream_t st) {
-    const size_t sm = smem_of<CS, W>(io.Ns, A.K, 1);
-    prep(gwindow_kernel<CS, GP, W>, sm);
-    gwindow_kernel<CS, GP, W><<<N, 32 * W, sm, st>>>(A, Wa, G, io);
-    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    return G.pic.ldiag ? window_pd<CS, W, 1>(A, Wa, G, io, N, st) : window_pd<CS, W, 0>(A, Wa, G, io, N, st);
 }
 
 template <int CS, int W>
 int jitter(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G, const JitterIO<float>& io, int N,
            cudaStream_t st) {
-    const size_t sm = smem_of<CS, W>(io.Ns, A.K, 3);
-    prep(gjitter_kernel<CS, GP, W>, sm);
-    gjitter_kernel<CS, GP, W><<<N, 32 * W, sm, st>>>(A, Wa, G, io);
-    return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
+    return G.pic.ldiag ? jitter_pd<CS, W, 1>(A, Wa, G, io, N, st) : jitter_pd<CS, W, 0>(A, Wa, G, io, N, st);
 }
 
 }  // namespace
