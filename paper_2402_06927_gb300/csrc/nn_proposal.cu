@@ -195,10 +195,10 @@ __global__ void __launch_bounds__(128) hgemm_kernel(int M, int N, int Kd, int kc
 }
 
 // k-splits for a reduction with few output tiles (weight gradients: the sum runs over
-// batch x positions): about 8 CTAs per SM of 152, chunks of at least 256 k-values
+// batch x positions): about 8 CTAs per SM, chunks of at least 256 k-values
 static int splitk_for(int M, int N, int Kd) {
     const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-    return max(1, min(Kd / 256, 8 * 152 / tiles));
+    return max(1, min(Kd / 256, 8 * device_sms() / tiles));
 }
 
 // k-chunks that sgemm launches for a split of splitk
@@ -425,7 +425,7 @@ __global__ void copy_rows_kernel(int B, int O, const float* src, size_t sstride,
 
 static int grid_elems(size_t n) {
     size_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > (size_t)device_sms() * 16) b = (size_t)device_sms() * 16;
     return (int)(b < 1 ? 1 : b);
 }
 

@@ -355,7 +355,7 @@ int launch_resample_idx(int N, const double* wbar, uint64_t seed, uint64_t stage
 
 static int grid_for(size_t work) {
     size_t b = (work + 255) / 256;
-    if (b > 152 * 8) b = 152 * 8;
+    if (b > (size_t)device_sms() * 8) b = (size_t)device_sms() * 8;
     if (b < 1) b = 1;
     return (int)b;
 }

@@ -95,7 +95,8 @@ int launch_mala_propose(int N, int Ns, int K, double theta, double h, double dt,
                         const R* gJ, uint64_t seed, uint64_t ctr, int particle0, R* dWp, cudaStream_t st) {
     const size_t tot = (size_t)N * Ns * ((K + 3) >> 2);
     const size_t blocks = (tot + 255) / 256;
-    const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+    const int cap = device_sms() * 16;
+    const int grid = (int)(blocks < (size_t)cap ? blocks : (size_t)cap);
     mala_propose_kernel<R><<<grid, 256, 0, st>>>(N, Ns, K, theta, h, dt, dW, lam, gJ, seed, ctr, particle0, dWp);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }

@@ -10,6 +10,20 @@
 
 namespace sch {
 
+// Streaming multiprocessors of the current device, queried once per device (grid sizes of
+// the grid-stride kernels are multiples of it).  1 if the query fails.
+inline int device_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
+}
+
 // A constant symmetric circulant tridiagonal matrix (off-diagonal a, diagonal b)
 // in chunk-partitioned form: the forward/backward sweep coefficients of a
 // chunk of C <= 8 rows and the coefficients of its reduced "first" and "last"

@@ -65,7 +65,7 @@ int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint6
     const long long tot = (long long)N * Ns * ((K + 3) / 4);
     const int threads = 256;
     long long blocks = (tot + threads - 1) / threads;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (long long)device_sms() * 16) blocks = (long long)device_sms() * 16;
     if (blocks < 1) blocks = 1;
     draw_kernel<R><<<(int)blocks, threads, 0, st>>>(N, Ns, K, sqdt, seed, tag, ctr, particle0, dW);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;

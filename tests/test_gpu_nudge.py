@@ -115,6 +115,25 @@ def _nudge_case():
     return cfg, om, m0, y
 
 
+@pytest.mark.slow
+def test_nudge_open_loop_matches_oracle_at_the_nudging_workload_size():
+    # pf_nudge at the full size of the nudging workload (n = 1024, K = 8, Ns = 20, FP64, L-BFGS
+    # vectors in shared memory, every forward state kept) against the oracle's minimiser on one
+    # particle; the drift within 1e-5 relative, the cost within 1e-9 relative
+    cfg = get_config("cfg3_f64")
+    g = gpu_model(cfg)
+    om = oracle_model(cfg)
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, 2, 11)])
+    y = random_obs(cfg, 12)
+    out = g.nudge(tdev(m0, g.dtype), tdev(y, g.dtype), cfg.Ns, mode="open_loop", max_iter=200, gtol=1e-10,
+                  seed=4, ctr=1)
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    ref, res = ON.nudge_open_loop(om, m0[0], y, cfg.sigma, cfg.Ns, cfg.K, gtol=1e-12)
+    assert rel_err(out["lam"][0].cpu().numpy(), ref) < 1e-5
+    assert abs(out["J"][0].item() - res.fun) <= 1e-9 * res.fun
+
+
 @pytest.mark.parametrize("ckpt", [2, None])
 def test_nudge_open_loop_matches_oracle(ckpt):
     # ckpt = 2 recomputes each segment in the reverse sweep; None keeps the forward states
