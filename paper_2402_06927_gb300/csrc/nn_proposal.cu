@@ -118,6 +118,20 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int Kd, int kc
 // --------------------------------------------------------------------------
 constexpr int HTM = 64, HTN = 64, HTK = 32, HPAD = 8;
 
+// How a gather functor's operand lies in memory.  By default consecutive k are adjacent
+// for an A operand and consecutive n for a B operand; a functor that declares
+// `static constexpr bool transposed = true` has them the other way round (consecutive m
+// adjacent as A, consecutive k as B).  The BF16 tile loaders walk the adjacent index
+// fastest, so that a warp's loads are coalesced.
+template <typename F, typename = void>
+struct is_transposed {
+    static constexpr bool value = false;
+};
+template <typename F>
+struct is_transposed<F, decltype((void)F::transposed)> {
+    static constexpr bool value = F::transposed;
+};
+
 __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
     asm volatile(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -147,12 +161,14 @@ __global__ void __launch_bounds__(128) hgemm_kernel(int M, int N, int Kd, int kc
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
     for (int k0 = kbeg; k0 < kend; k0 += HTK) {
         for (int e = threadIdx.x; e < HTK * HTM; e += 128) {
-            const int mm = e / HTK, kk = e % HTK;
+            const int mm = is_transposed<LA>::value ? e % HTM : e / HTK;
+            const int kk = is_transposed<LA>::value ? e / HTM : e % HTK;
             const int gm = m0 + mm, gk = k0 + kk;
             As[mm][kk] = __float2bfloat16_rn((gm < M && gk < kend) ? la(zb, gm, gk) : 0.f);
         }
         for (int e = threadIdx.x; e < HTK * HTN; e += 128) {
-            const int kk = e / HTN, nn = e % HTN;
+            const int kk = is_transposed<LB>::value ? e % HTK : e / HTN;
+            const int nn = is_transposed<LB>::value ? e / HTK : e % HTN;
             const int gn = n0 + nn, gk = k0 + kk;
             Bs[nn][kk] = __float2bfloat16_rn((gn < N && gk < kend) ? lb(zb, gk, gn) : 0.f);
         }
@@ -301,6 +317,7 @@ struct RowMajor {         // A(m, k) = p[z * bs + m * ld + k]
     __device__ float operator()(int z, int m, int k) const { return p[(size_t)z * bs + (size_t)m * ld + k]; }
 };
 struct RowMajorT {        // A(m, k) = p[z * bs + k * ld + m]
+    static constexpr bool transposed = true;
     const float* p; size_t bs; int ld;
     __device__ float operator()(int z, int m, int k) const { return p[(size_t)z * bs + (size_t)k * ld + m]; }
 };
@@ -462,10 +479,11 @@ static void nn_forward_impl(const NNDims& d, int B, const float* params, const f
 // --------------------------------------------------------------------------
 constexpr int CL_C = 64;                 // channels of the channels-last path
 constexpr int CL_K = 5 * CL_C;           // reduction length of layers 1..3 (k = j C + ci)
-constexpr int CL_WROW = CL_K + 8;        // shared weight row (bf16): 164 words, lanes in distinct banks
-constexpr int CL_XROW = CL_C + 4;        // shared slab row (bf16): two rows = 68 words
+constexpr int CL_WROW = CL_K + 8;        // shared weight row (bf16): 656 bytes, 16 mod 128
+constexpr int CL_XROW = CL_C + 8;        // shared slab row (bf16): 144 bytes, 16 mod 128
 constexpr int CL_TQ = 64;                // output positions per CTA
 constexpr int CL_XPOS = 2 * CL_TQ + 3;   // input positions a tile reads
+constexpr int CL_XEVEN = CL_TQ + 2;      // of which at even offsets from the slab's start
 
 __host__ __device__ constexpr size_t cl_smem() {
     return ((size_t)CL_C * CL_WROW + 2 * (size_t)CL_XPOS * CL_XROW) * sizeof(__nv_bfloat16);
@@ -483,63 +501,100 @@ __global__ void pack_conv_weights_kernel(const float* params, size_t off1, size_
     }
 }
 
-// layer 0 from the features: out[b][q][co] = relu(b0[co] + sum_{ci, j} w0[co][ci][j] x0[ci][(2q + j - 2) mod n]),
-// both operands rounded to BF16 as in the tensor-core GEMM; one thread per (b, q, 8 channels)
-__global__ void conv0_cl_kernel(int B, int n, int M, float sigma, const float* u, const float* y, int ystride,
-                                const float* w0, const float* b0, __nv_bfloat16* out, size_t out_bs) {
-    const int Lo = n / 2, stride = n / M;
-    const size_t tot = (size_t)B * Lo * (CL_C / 8);
+// Layer 0 from the features: out[b][q][co] = relu(b0[co] + sum_{ci, j} w0[co][ci][j]
+// x0[ci][(2q + j - 2) mod n]), both operands rounded to BF16 as in the tensor-core GEMM.
+// One thread per sample and four consecutive output positions: it forms the features of
+// the 11 input positions once and applies every BF16-rounded weight (staged in shared
+// memory, read as broadcasts) to the four positions, then stores 4 x 64 channels.
+constexpr int CONV0_Q = 4;
+
+__global__ void __launch_bounds__(256) conv0_cl_kernel(int B, int n, int M, float sigma, const float* u,
+                                                       const float* y, int ystride, const float* w0, const float* b0,
+                                                       __nv_bfloat16* out, size_t out_bs) {
+    __shared__ float ws[CL_C * 10 + CL_C];   // w0 [co][ci 5 + j] rounded to BF16, then the bias
+    for (int e = threadIdx.x; e < CL_C * 10; e += blockDim.x) ws[e] = __bfloat162float(__float2bfloat16_rn(w0[e]));
+    for (int e = threadIdx.x; e < CL_C; e += blockDim.x) ws[CL_C * 10 + e] = b0[e];
+    __syncthreads();
+    const int Lo = n / 2, stride = n / M, nq = Lo / CONV0_Q;
+    const size_t tot = (size_t)B * nq;
+    constexpr int NX = 2 * CONV0_Q + 3;   // input positions 2 q0 - 2 .. 2 q0 + 2 CONV0_Q
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int cg = (int)(e % (CL_C / 8));
-        const int q = (int)((e / (CL_C / 8)) % Lo);
-        const int b = (int)(e / ((size_t)(CL_C / 8) * Lo));
-        float x[2][5];
+        const int q0 = (int)(e % nq) * CONV0_Q;
+        const int b = (int)(e / nq);
+        float x[2][NX];
 #pragma unroll
-        for (int j = 0; j < 5; ++j) {
-            const int i = (2 * q + j - 2 + n) % n;
+        for (int r = 0; r < NX; ++r) {
+            const int i = (2 * q0 - 2 + r + n) % n;
             const float ub = u[(size_t)b * n + i];
             float inn = 0.f;
             if (i % stride == 0) {
                 const float yj = y[(size_t)b * ystride + i / stride];
                 if (yj == yj) inn = (yj - ub) / sigma;   // NaN: not observed
             }
-            x[0][j] = __bfloat162float(__float2bfloat16_rn(ub));
-            x[1][j] = __bfloat162float(__float2bfloat16_rn(inn));
+            x[0][r] = __bfloat162float(__float2bfloat16_rn(ub));
+            x[1][r] = __bfloat162float(__float2bfloat16_rn(inn));
         }
-        __align__(16) __nv_bfloat16 o[8];
+        __nv_bfloat16* ob = out + (size_t)b * out_bs + (size_t)q0 * CL_C;
+#pragma unroll 1
+        for (int cg = 0; cg < CL_C / 8; ++cg) {
+            __align__(16) __nv_bfloat16 o[CONV0_Q][8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int co = 8 * cg + c;
-            float acc = 0.f;
+            for (int c = 0; c < 8; ++c) {
+                const int co = 8 * cg + c;
+                float acc[CONV0_Q];
 #pragma unroll
-            for (int ci = 0; ci < 2; ++ci)
+                for (int qq = 0; qq < CONV0_Q; ++qq) acc[qq] = 0.f;
 #pragma unroll
-                for (int j = 0; j < 5; ++j)
-                    acc = fmaf(__bfloat162float(__float2bfloat16_rn(w0[(co * 2 + ci) * 5 + j])), x[ci][j], acc);
-            acc += b0[co];
-            o[c] = __float2bfloat16_rn(acc > 0.f ? acc : 0.f);
+                for (int ci = 0; ci < 2; ++ci)
+#pragma unroll
+                    for (int j = 0; j < 5; ++j) {
+                        const float wv = ws[co * 10 + ci * 5 + j];
+#pragma unroll
+                        for (int qq = 0; qq < CONV0_Q; ++qq) acc[qq] = fmaf(wv, x[ci][2 * qq + j], acc[qq]);
+                    }
+                const float bias = ws[CL_C * 10 + co];
+#pragma unroll
+                for (int qq = 0; qq < CONV0_Q; ++qq) {
+                    const float v = acc[qq] + bias;
+                    o[qq][c] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
+                }
+            }
+#pragma unroll
+            for (int qq = 0; qq < CONV0_Q; ++qq)
+                *reinterpret_cast<uint4*>(ob + (size_t)qq * CL_C + 8 * cg) = *reinterpret_cast<const uint4*>(o[qq]);
         }
-        *reinterpret_cast<uint4*>(out + (size_t)b * out_bs + (size_t)q * CL_C + 8 * cg) =
-            *reinterpret_cast<const uint4*>(o);
     }
 }
 
-// 8-byte asynchronous copy global -> shared (cp.async, completion tracked by groups)
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+// 16-byte asynchronous copy global -> shared (cp.async, completion tracked by groups)
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// the input slab of tile (b, q0): positions 2 q0 - 2 .. 2 q0 + 128 (mod Lin), 64 channels each
+// four 8 x 8 BF16 matrices from shared memory (lane l gives the address of row l % 8 of
+// matrix l / 8); register i receives matrix i in the mma fragment layout
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* smem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(sa));
+}
+
+// The input slab of tile (b, q0): positions 2 q0 - 2 + r, r = 0 .. 130 (mod Lin), 64 channels
+// each, stored de-interleaved: offset r at row r / 2 when r is even, CL_XEVEN + r / 2 when odd,
+// so that the rows 2q + j of the output positions q of a fragment are consecutive.
+__device__ __forceinline__ int cl_slab_row(int r) { return (r & 1) ? CL_XEVEN + (r >> 1) : (r >> 1); }
+
 __device__ __forceinline__ void cl_issue_slab(__nv_bfloat16* Xs, const __nv_bfloat16* in, size_t in_bs, int Lin,
                                               int b, int q0) {
     const __nv_bfloat16* inb = in + (size_t)b * in_bs;
-    for (int e = threadIdx.x; e < CL_XPOS * (CL_C / 4); e += 128) {
-        const int r = e / (CL_C / 4), c4 = e % (CL_C / 4);
+    for (int e = threadIdx.x; e < CL_XPOS * (CL_C / 8); e += 128) {
+        const int r = e / (CL_C / 8), c8 = e % (CL_C / 8);
         const int pos = (2 * q0 - 2 + r + Lin) % Lin;
-        cp_async8(Xs + r * CL_XROW + 4 * c4, inb + (size_t)pos * CL_C + 4 * c4);
+        cp_async16(Xs + cl_slab_row(r) * CL_XROW + 8 * c8, inb + (size_t)pos * CL_C + 8 * c8);
     }
 }
 
@@ -549,8 +604,9 @@ __device__ __forceinline__ void cl_issue_slab(__nv_bfloat16* Xs, const __nv_bflo
 // (all 64 output channels) in turn: the input slab of positions 2 q0 - 2 .. 2 q0 + 128
 // (131 rows of 64 channels) is copied with cp.async into one of two buffers while the
 // previous tile is computed.  Warp w computes the 32 x 32 quarter (w / 2, w % 2) of a
-// tile with mma.sync m16n8k16, its A fragments straight from the slab (rows 2q + j,
-// channel pairs).  Epilogue: bias, ReLU, BF16, channels-last store of channel pairs.
+// tile with mma.sync m16n8k16, its A fragments loaded by ldmatrix straight from the slab
+// (rows 2q + j, 16 channels), its B fragments from the weights.  Epilogue: bias, ReLU,
+// BF16, channels-last store of channel pairs.
 __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv_bfloat16* __restrict__ in,
                                                       size_t in_bs, const __nv_bfloat16* __restrict__ wb,
                                                       const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
@@ -559,11 +615,15 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
     __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(cl_raw);   // [64][CL_WROW]
     __nv_bfloat16* Xbuf = Ws + CL_C * CL_WROW;                       // [2][CL_XPOS][CL_XROW]
     const int tpb = (Lin / 2) / CL_TQ, ntiles = B * tpb;
-    for (int e = threadIdx.x; e < CL_C * (CL_K / 4); e += 128) {
-        const int r = e / (CL_K / 4), c4 = e % (CL_K / 4);
-        *reinterpret_cast<uint2*>(Ws + r * CL_WROW + 4 * c4) = *reinterpret_cast<const uint2*>(wb + r * CL_K + 4 * c4);
+    for (int e = threadIdx.x; e < CL_C * (CL_K / 8); e += 128) {
+        const int r = e / (CL_K / 8), c8 = e % (CL_K / 8);
+        *reinterpret_cast<uint4*>(Ws + r * CL_WROW + 8 * c8) = *reinterpret_cast<const uint4*>(wb + r * CL_K + 8 * c8);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the rows and column halves this lane addresses in ldmatrix: A (slab) matrices are
+    // (rows 0-7, 8-15) x (columns 0-7, 8-15), B (weight) matrices (k 0-7, 8-15) x (n 0-7, 8-15)
+    const int arow = (lane & 7) + 8 * ((lane >> 3) & 1), acol = 8 * (lane >> 4);
+    const int brow = (lane & 7) + 8 * (lane >> 4), bcol = 8 * ((lane >> 3) & 1);
     const int wq = (warp >> 1) * 32, wc = (warp & 1) * 32;
     const int gq = lane >> 2, tq = lane & 3;
     int t = blockIdx.x;
@@ -587,23 +647,22 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
                 for (int e = 0; e < 4; ++e) acc[i][jj][e] = 0.f;
 #pragma unroll 1
         for (int j = 0; j < 5; ++j) {
+            // slab rows of tap j: offset 2q + j is row q + j/2 (even j) or CL_XEVEN + q + (j-1)/2
+            const int jrow = (j & 1) ? CL_XEVEN + (j >> 1) : (j >> 1);
 #pragma unroll
             for (int kc = 0; kc < CL_C; kc += 16) {
                 uint32_t a[2][4], bf[4][2];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int r0 = 2 * (wq + 16 * i + gq) + j, r1 = r0 + 16;
-                    a[i][0] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq);
-                    a[i][1] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq);
-                    a[i][2] = *reinterpret_cast<const uint32_t*>(Xs + r0 * CL_XROW + kc + 2 * tq + 8);
-                    a[i][3] = *reinterpret_cast<const uint32_t*>(Xs + r1 * CL_XROW + kc + 2 * tq + 8);
-                }
-                const int k = j * CL_C + kc + 2 * tq;
+                for (int i = 0; i < 2; ++i)
+                    ldmatrix_x4(a[i], Xs + (jrow + wq + 16 * i + arow) * CL_XROW + kc + acol);
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int c = wc + 8 * jj + gq;
-                    bf[jj][0] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k);
-                    bf[jj][1] = *reinterpret_cast<const uint32_t*>(Ws + c * CL_WROW + k + 8);
+                for (int jj = 0; jj < 4; jj += 2) {
+                    uint32_t r4[4];
+                    ldmatrix_x4(r4, Ws + (wc + 8 * jj + brow) * CL_WROW + j * CL_C + kc + bcol);
+                    bf[jj][0] = r4[0];
+                    bf[jj][1] = r4[1];
+                    bf[jj + 1][0] = r4[2];
+                    bf[jj + 1][1] = r4[3];
                 }
 #pragma unroll
                 for (int i = 0; i < 2; ++i)
@@ -632,6 +691,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
 
 // A(c, q) = h[b][q][c] of a channels-last BF16 activation (the mode projection's operand)
 struct CLRows {
+    static constexpr bool transposed = true;
     const __nv_bfloat16* h; size_t bstride;
     __device__ float operator()(int b, int m, int k) const {
         return __bfloat162float(h[(size_t)b * bstride + (size_t)k * CL_C + m]);
@@ -660,7 +720,7 @@ static void nn_forward_cl(const NNDims& d, int B, const float* params, const flo
     for (int l = 1; l < 4; ++l) off[l + 1] = off[l] + (size_t)CL_C * d.L[l];
     pack_conv_weights_kernel<<<grid_elems(3 * CL_C * CL_K), 256, 0, st>>>(params, d.off_w[1], d.off_w[2], d.off_w[3],
                                                                            wb);
-    conv0_cl_kernel<<<grid_elems((size_t)B * d.L[1] * (CL_C / 8)), 256, 0, st>>>(
+    conv0_cl_kernel<<<grid_elems((size_t)B * (d.L[1] / CONV0_Q)), 256, 0, st>>>(
         B, d.n, d.M, d.sigma, u, y, ystride, params + d.off_w[0], params + d.off_b[0], act + off[1], cs);
     const size_t sm = cl_smem();
     cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
