@@ -68,6 +68,8 @@ def step_flops(n, K, solver, iters, steps, noise_per_node=None):
 JITTER_SOURCES = ["paper_2402_06927_gb300/csrc/sch_warp.cuh", "paper_2402_06927_gb300/csrc/sch_kernels.cuh",
                   "paper_2402_06927_gb300/csrc/sch_internal.h", "paper_2402_06927_gb300/csrc/sch_device.cuh",
                   "paper_2402_06927_gb300/csrc/sch_window_warp.cu"]
+# the large run's kernel (warp-group layout) also depends on these
+GROUP_SOURCES = ["paper_2402_06927_gb300/csrc/sch_group.cuh", "paper_2402_06927_gb300/csrc/sch_window_group.cu"]
 JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # wjitter_kernel<8,2>, profiles/wjitter_kernel_cfg2_n1024_N1024.md: 4.611328 MB read, 0 written
     "569ce94c7b5361360ae675fc15d9adc45ab3190e": 4611328,
@@ -84,6 +86,10 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # wjitter_kernel<8,2,1,2>, specialised to a diagonal Picard and a PCR Helmholtz reduced
     # solve: 4.609792 MB read, 0 written
     "9a63bdc05dd81bd373a067cd982f7c3df6d28ae3": 4609792,
+}, "cfg5_f32": {
+    # gjitter_kernel<8,2,4,1>, profiles/gjitter_kernel_cfg5_n4096_N8192.md: 148.514304 MB read,
+    # 226.438400 MB written
+    "6fce80f5f13a05b4970ec3ed280a4c0d9d5f84c0": 374952704,
 }}
 
 
@@ -93,7 +99,7 @@ def jitter_traffic(workload):
     import hashlib
     h = hashlib.sha1()
     try:
-        for f in JITTER_SOURCES:
+        for f in JITTER_SOURCES + (GROUP_SOURCES if workload == "cfg5_f32" else []):
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(hashlib.sha1(fh.read()).digest())
     except OSError:
