@@ -340,6 +340,12 @@ struct Store {            // out[z * bs + m * ld + n] = v (+ bias[n] if bias)
         out[(size_t)z * bs + (size_t)m * ld + n] = v + (bias ? bias[n] : 0.f);
     }
 };
+struct StoreBF16 {        // out[z * bs + m * ld + n] = v rounded to BF16
+    __nv_bfloat16* out; size_t bs; int ld;
+    __device__ void operator()(int z, int m, int n, float v) const {
+        out[(size_t)z * bs + (size_t)m * ld + n] = __float2bfloat16_rn(v);
+    }
+};
 
 // --------------------------------------------------------------------------
 // element-wise kernels
@@ -501,69 +507,73 @@ __global__ void pack_conv_weights_kernel(const float* params, size_t off1, size_
     }
 }
 
-// Layer 0 from the features: out[b][q][co] = relu(b0[co] + sum_{ci, j} w0[co][ci][j]
-// x0[ci][(2q + j - 2) mod n]), both operands rounded to BF16 as in the tensor-core GEMM.
-// One thread per sample and four consecutive output positions: it forms the features of
-// the 11 input positions once and applies every BF16-rounded weight (staged in shared
-// memory, read as broadcasts) to the four positions, then stores 4 x 64 channels.
-constexpr int CONV0_Q = 4;
+// Layer 0 on the tensor cores: out[b][q][co] = relu(b0[co] + sum_k X0[q][k] W0[co][k]) with
+// k = 2 j + ci (ten taps x channels, padded to 16 with zero weights), X0[q][k] the feature
+// of channel ci at input position 2q + j - 2.  A CTA takes 64 output positions of one
+// sample: its threads form the features of the positions 2 q0 - 2 .. 2 q0 + 133 as BF16
+// (u, innovation) pairs in shared memory, so that row q of X0 is 16 consecutive values
+// starting at pair 2q; warp w then computes the 32 x 32 quarter (w / 2, w % 2) of the
+// 64 x 64 output with one k-step of mma.sync m16n8k16.  Epilogue as conv_tc_kernel.
+constexpr int C0_TQ = 64;                 // output positions per CTA
+constexpr int C0_XPOS = 2 * C0_TQ + 8;    // feature positions staged (rows read 8 positions)
+constexpr int C0_WROW = 16 + 8;           // shared weight row (bf16)
 
-__global__ void __launch_bounds__(256) conv0_cl_kernel(int B, int n, int M, float sigma, const float* u,
-                                                       const float* y, int ystride, const float* w0, const float* b0,
+__global__ void __launch_bounds__(128) conv0_cl_kernel(int n, int M, float sigma, const float* u, const float* y,
+                                                       int ystride, const float* w0, const float* b0,
                                                        __nv_bfloat16* out, size_t out_bs) {
-    __shared__ float ws[CL_C * 10 + CL_C];   // w0 [co][ci 5 + j] rounded to BF16, then the bias
-    for (int e = threadIdx.x; e < CL_C * 10; e += blockDim.x) ws[e] = __bfloat162float(__float2bfloat16_rn(w0[e]));
-    for (int e = threadIdx.x; e < CL_C; e += blockDim.x) ws[CL_C * 10 + e] = b0[e];
-    __syncthreads();
-    const int Lo = n / 2, stride = n / M, nq = Lo / CONV0_Q;
-    const size_t tot = (size_t)B * nq;
-    constexpr int NX = 2 * CONV0_Q + 3;   // input positions 2 q0 - 2 .. 2 q0 + 2 CONV0_Q
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
-        const int q0 = (int)(e % nq) * CONV0_Q;
-        const int b = (int)(e / nq);
-        float x[2][NX];
-#pragma unroll
-        for (int r = 0; r < NX; ++r) {
-            const int i = (2 * q0 - 2 + r + n) % n;
-            const float ub = u[(size_t)b * n + i];
-            float inn = 0.f;
-            if (i % stride == 0) {
-                const float yj = y[(size_t)b * ystride + i / stride];
-                if (yj == yj) inn = (yj - ub) / sigma;   // NaN: not observed
-            }
-            x[0][r] = __bfloat162float(__float2bfloat16_rn(ub));
-            x[1][r] = __bfloat162float(__float2bfloat16_rn(inn));
-        }
-        __nv_bfloat16* ob = out + (size_t)b * out_bs + (size_t)q0 * CL_C;
-#pragma unroll 1
-        for (int cg = 0; cg < CL_C / 8; ++cg) {
-            __align__(16) __nv_bfloat16 o[CONV0_Q][8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int co = 8 * cg + c;
-                float acc[CONV0_Q];
-#pragma unroll
-                for (int qq = 0; qq < CONV0_Q; ++qq) acc[qq] = 0.f;
-#pragma unroll
-                for (int ci = 0; ci < 2; ++ci)
-#pragma unroll
-                    for (int j = 0; j < 5; ++j) {
-                        const float wv = ws[co * 10 + ci * 5 + j];
-#pragma unroll
-                        for (int qq = 0; qq < CONV0_Q; ++qq) acc[qq] = fmaf(wv, x[ci][2 * qq + j], acc[qq]);
-                    }
-                const float bias = ws[CL_C * 10 + co];
-#pragma unroll
-                for (int qq = 0; qq < CONV0_Q; ++qq) {
-                    const float v = acc[qq] + bias;
-                    o[qq][c] = __float2bfloat16_rn(v > 0.f ? v : 0.f);
-                }
-            }
-#pragma unroll
-            for (int qq = 0; qq < CONV0_Q; ++qq)
-                *reinterpret_cast<uint4*>(ob + (size_t)qq * CL_C + 8 * cg) = *reinterpret_cast<const uint4*>(o[qq]);
-        }
+    __shared__ __align__(16) __nv_bfloat16 Xs[2 * C0_XPOS];      // (u, innovation) per position
+    __shared__ __align__(16) __nv_bfloat16 Ws[CL_C * C0_WROW];   // [co][2 j + ci], zero for k >= 10
+    const int b = blockIdx.y, q0 = blockIdx.x * C0_TQ, stride = n / M;
+    for (int e = threadIdx.x; e < CL_C * 16; e += 128) {
+        const int co = e / 16, k = e % 16, j = k >> 1, ci = k & 1;
+        Ws[co * C0_WROW + k] = __float2bfloat16_rn(k < 10 ? w0[(co * 2 + ci) * 5 + j] : 0.f);
     }
+    for (int r = threadIdx.x; r < C0_XPOS; r += 128) {
+        const int i = (2 * q0 - 2 + r + n) % n;
+        const float ub = u[(size_t)b * n + i];
+        float inn = 0.f;
+        if (i % stride == 0) {
+            const float yj = y[(size_t)b * ystride + i / stride];
+            if (yj == yj) inn = (yj - ub) / sigma;   // NaN: not observed
+        }
+        *reinterpret_cast<__nv_bfloat162*>(Xs + 2 * r) = __floats2bfloat162_rn(ub, inn);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wq = (warp >> 1) * 32, wc = (warp & 1) * 32;
+    const int gq = lane >> 2, tq = lane & 3;
+    uint32_t a[2][4], bf[4][2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int q = wq + 16 * i + gq;   // row q starts at pair 2q; k pair (2t, 2t+1) is pair 2q + t
+        a[i][0] = *reinterpret_cast<const uint32_t*>(Xs + 2 * (2 * q + tq));
+        a[i][1] = *reinterpret_cast<const uint32_t*>(Xs + 2 * (2 * (q + 8) + tq));
+        a[i][2] = *reinterpret_cast<const uint32_t*>(Xs + 2 * (2 * q + tq + 4));
+        a[i][3] = *reinterpret_cast<const uint32_t*>(Xs + 2 * (2 * (q + 8) + tq + 4));
+    }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+        const int c = wc + 8 * jj + gq;
+        bf[jj][0] = *reinterpret_cast<const uint32_t*>(Ws + c * C0_WROW + 2 * tq);
+        bf[jj][1] = *reinterpret_cast<const uint32_t*>(Ws + c * C0_WROW + 2 * tq + 8);
+    }
+    __nv_bfloat16* ob = out + (size_t)b * out_bs;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_bf16_16816(acc, a[i], bf[jj]);
+            const int co = wc + 8 * jj + 2 * tq;
+            const float bb0 = b0[co], bb1 = b0[co + 1];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + wq + 16 * i + gq + 8 * h;
+                const float v0 = acc[2 * h] + bb0, v1 = acc[2 * h + 1] + bb1;
+                *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)q * CL_C + co) =
+                    __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
+            }
+        }
 }
 
 // 16-byte asynchronous copy global -> shared (cp.async, completion tracked by groups)
@@ -689,6 +699,89 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
     }
 }
 
+// BF16 weights of the head, Wh [K Ns][C K] in the parameters' layout
+__global__ void pack_bf16_kernel(size_t count, const float* src, __nv_bfloat16* dst) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < count; e += (size_t)gridDim.x * blockDim.x)
+        dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+// Dense GEMM with BF16 operands from memory and FP32 accumulation (the head of the
+// channels-last path): C[m][n] = sum_k A[m][k] B[n][k] + bias[n], A [M][Kd] and B [N][Kd]
+// row-major BF16, Kd a multiple of 32.  64 x 64 tiles, 128 threads (warp w: the 32 x 32
+// quarter (w / 2, w % 2)), k-chunks of 32 double-buffered with cp.async, fragments by
+// ldmatrix (80-byte shared rows: eight rows fall in distinct 16-byte bank groups).
+constexpr int DG_T = 64, DG_BK = 32, DG_ROW = DG_BK + 8;
+
+__global__ void __launch_bounds__(128) dense_bf16_gemm_kernel(int M, int N, int Kd,
+                                                              const __nv_bfloat16* __restrict__ A,
+                                                              const __nv_bfloat16* __restrict__ Bm,
+                                                              const float* __restrict__ bias, float* __restrict__ C,
+                                                              int ldc) {
+    __shared__ __align__(16) __nv_bfloat16 As[2][DG_T][DG_ROW];
+    __shared__ __align__(16) __nv_bfloat16 Bs[2][DG_T][DG_ROW];
+    const int m0 = blockIdx.y * DG_T, n0 = blockIdx.x * DG_T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gq = lane >> 2, tq = lane & 3;
+    const int arow = (lane & 7) + 8 * ((lane >> 3) & 1), acol = 8 * (lane >> 4);
+    const int brow = (lane & 7) + 8 * (lane >> 4), bcol = 8 * ((lane >> 3) & 1);
+    auto issue = [&](int buf, int k0) {
+        for (int e = threadIdx.x; e < DG_T * (DG_BK / 8); e += 128) {
+            const int r = e / (DG_BK / 8), c8 = e % (DG_BK / 8);
+            const int gm = min(m0 + r, M - 1), gn = min(n0 + r, N - 1);   // rows past the end: any row
+            cp_async16(&As[buf][r][8 * c8], A + (size_t)gm * Kd + k0 + 8 * c8);
+            cp_async16(&Bs[buf][r][8 * c8], Bm + (size_t)gn * Kd + k0 + 8 * c8);
+        }
+    };
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][jj][e] = 0.f;
+    const int nk = Kd / DG_BK;
+    issue(0, 0);
+    cp_async_commit();
+    for (int kt = 0; kt < nk; ++kt) {
+        if (kt + 1 < nk) issue((kt + 1) & 1, (kt + 1) * DG_BK);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int b = kt & 1;
+#pragma unroll
+        for (int ks = 0; ks < DG_BK; ks += 16) {
+            uint32_t a[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) ldmatrix_x4(a[i], &As[b][wm + 16 * i + arow][ks + acol]);
+#pragma unroll
+            for (int jj = 0; jj < 4; jj += 2) {
+                uint32_t r4[4];
+                ldmatrix_x4(r4, &Bs[b][wn + 8 * jj + brow][ks + bcol]);
+                bf[jj][0] = r4[0];
+                bf[jj][1] = r4[1];
+                bf[jj + 1][0] = r4[2];
+                bf[jj + 1][1] = r4[3];
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) mma_bf16_16816(acc[i][jj], a[i], bf[jj]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int gm = m0 + wm + 16 * i + gq + ((e & 2) ? 8 : 0);
+                const int gn = n0 + wn + 8 * jj + 2 * tq + (e & 1);
+                if (gm < M && gn < N) C[(size_t)gm * ldc + gn] = acc[i][jj][e] + bias[gn];
+            }
+}
+
 // A(c, q) = h[b][q][c] of a channels-last BF16 activation (the mode projection's operand)
 struct CLRows {
     static constexpr bool transposed = true;
@@ -705,23 +798,26 @@ static size_t cl_act_elems(const NNDims& d) {
 }
 
 static bool cl_supported(const NNDims& d) {
-    // 64 channels; every layer's output a whole number of 64-position tiles
-    return d.prec == NN_BF16 && d.C == CL_C && d.L[4] % CL_TQ == 0;
+    // 64 channels; every layer's output a whole number of 64-position tiles; the head's
+    // reduction C K a multiple of the dense GEMM's k-chunk
+    return d.prec == NN_BF16 && d.C == CL_C && d.L[4] % CL_TQ == 0 && (d.C * d.K) % DG_BK == 0;
 }
 
 static void nn_forward_cl(const NNDims& d, int B, const float* params, const float* u, const float* y, int ystride,
                           void* ws, float* lam_out, cudaStream_t st) {
     const size_t cs = cl_act_elems(d);
     __nv_bfloat16* act = reinterpret_cast<__nv_bfloat16*>(ws);
+    const int P = d.L[4], FF = d.C * d.K, O = d.K * d.Ns;
     __nv_bfloat16* wb = act + (size_t)B * cs;                               // [3][64][320]
-    float* F = reinterpret_cast<float*>(wb + 3 * CL_C * CL_K);              // [B][C K]
+    __nv_bfloat16* whb = wb + 3 * CL_C * CL_K;                              // [O][FF]
+    __nv_bfloat16* F = whb + (size_t)O * FF;                                // [B][C K]
     size_t off[5];
     off[1] = 0;
     for (int l = 1; l < 4; ++l) off[l + 1] = off[l] + (size_t)CL_C * d.L[l];
     pack_conv_weights_kernel<<<grid_elems(3 * CL_C * CL_K), 256, 0, st>>>(params, d.off_w[1], d.off_w[2], d.off_w[3],
                                                                            wb);
-    conv0_cl_kernel<<<grid_elems((size_t)B * (d.L[1] / CONV0_Q)), 256, 0, st>>>(
-        B, d.n, d.M, d.sigma, u, y, ystride, params + d.off_w[0], params + d.off_b[0], act + off[1], cs);
+    conv0_cl_kernel<<<dim3(d.L[1] / C0_TQ, B), 128, 0, st>>>(d.n, d.M, d.sigma, u, y, ystride, params + d.off_w[0],
+                                                            params + d.off_b[0], act + off[1], cs);
     const size_t sm = cl_smem();
     cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     // persistent CTAs: as many as fit on the device at once (two per SM at 78 KB of shared memory)
@@ -736,10 +832,11 @@ static void nn_forward_cl(const NNDims& d, int B, const float* params, const flo
                                                                wb + (size_t)(l - 1) * CL_C * CL_K, params + d.off_b[l],
                                                                act + off[l + 1], cs);
     }
-    const int P = d.L[4], FF = d.C * d.K, O = d.K * d.Ns;
-    sgemm(NN_BF16, B, d.C, d.K, P, 1, CLRows{act + off[4], cs}, ModeS{P}, Store{F, (size_t)FF, d.K, nullptr}, st);
-    sgemm(NN_BF16, 1, B, O, FF, 1, RowMajor{F, 0, FF}, RowMajorT{params + d.off_wh, 0, FF},
-          Store{lam_out, 0, O, params + d.off_bh}, st);
+    // F = h4 S / P in BF16 (the head's operand), then lambda = F Wh^T + bh
+    sgemm(NN_BF16, B, d.C, d.K, P, 1, CLRows{act + off[4], cs}, ModeS{P}, StoreBF16{F, (size_t)FF, d.K}, st);
+    pack_bf16_kernel<<<grid_elems((size_t)O * FF), 256, 0, st>>>((size_t)O * FF, params + d.off_wh, whb);
+    dim3 hg((O + DG_T - 1) / DG_T, (B + DG_T - 1) / DG_T);
+    dense_bf16_gemm_kernel<<<hg, 128, 0, st>>>(B, O, FF, F, whb, params + d.off_bh, lam_out, O);
 }
 
 }  // namespace sch
