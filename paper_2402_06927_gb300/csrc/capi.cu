@@ -334,6 +334,14 @@ void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
     rtab_host(th, rows, q);
     cast_rtab(q, W.rhel);
     wtab_cast(th, q, CS, W.hel);
+    // the mode-noise tables about the lane centre: rows / 64 streams of CS pairs, H nodes a half
+    const int H = rows / 64 * CS;
+    for (int j = 1; j <= p.K / 2 && j <= SCH_MAX_K / 2; ++j)
+        for (int q = 0; q < H / 2 && q < WNQ_MAX; ++q) {
+            const double dl = 2.0 * M_PI * (H - 1 - q + 0.5) / p.n, dr = 2.0 * M_PI * (q + 0.5) / p.n;
+            W.nco[j - 1][q] = make_float2((float)cos(j * dl), (float)cos(j * dr));
+            W.nsi[j - 1][q] = make_float2((float)sin(j * dl), (float)sin(j * dr));
+        }
     if (p.noise == SCH_NOISE_MATERN) {
         // the Matern operator scaled by 6/h like the Helmholtz one, and the weights likewise
         const double k2 = 1.0 / (p.kappa * p.kappa);

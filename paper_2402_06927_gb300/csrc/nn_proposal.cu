@@ -492,7 +492,8 @@ constexpr int CL_XPOS = 2 * CL_TQ + 3;   // input positions a tile reads
 constexpr int CL_XEVEN = CL_TQ + 2;      // of which at even offsets from the slab's start
 
 __host__ __device__ constexpr size_t cl_smem() {
-    return ((size_t)CL_C * CL_WROW + 2 * (size_t)CL_XPOS * CL_XROW) * sizeof(__nv_bfloat16);
+    return ((size_t)CL_C * CL_WROW + 2 * (size_t)CL_XPOS * CL_XROW + (size_t)CL_TQ * (CL_C + 8)) *
+           sizeof(__nv_bfloat16);
 }
 
 // the weights of conv layers 1..3 as BF16 [l][co][j C + ci] (k ordered tap-major)
@@ -513,7 +514,20 @@ __global__ void pack_conv_weights_kernel(const float* params, size_t off1, size_
 // sample: its threads form the features of the positions 2 q0 - 2 .. 2 q0 + 133 as BF16
 // (u, innovation) pairs in shared memory, so that row q of X0 is 16 consecutive values
 // starting at pair 2q; warp w then computes the 32 x 32 quarter (w / 2, w % 2) of the
-// 64 x 64 output with one k-step of mma.sync m16n8k16.  Epilogue as conv_tc_kernel.
+// 64 x 64 output with one k-step of mma.sync m16n8k16.  Epilogue: bias, ReLU, BF16, the
+// tile staged in shared memory and stored as 8 KB of contiguous rows.
+constexpr int CL_OROW = CL_C + 8;         // staged output row (bf16): 144 bytes, rows in distinct banks
+
+// a CTA's 64 x 64 output tile, staged in shared memory [64][CL_OROW], to the 64 consecutive
+// channels-last rows from dst (8 KB contiguous): 16-byte stores, 128 threads
+__device__ __forceinline__ void cl_store_tile(const __nv_bfloat16* Os, __nv_bfloat16* dst) {
+    for (int e = threadIdx.x; e < 64 * (CL_C / 8); e += 128) {
+        const int r = e / (CL_C / 8), c8 = e % (CL_C / 8);
+        *reinterpret_cast<uint4*>(dst + (size_t)r * CL_C + 8 * c8) =
+            *reinterpret_cast<const uint4*>(Os + r * CL_OROW + 8 * c8);
+    }
+}
+
 constexpr int C0_TQ = 64;                 // output positions per CTA
 constexpr int C0_XPOS = 2 * C0_TQ + 8;    // feature positions staged (rows read 8 positions)
 constexpr int C0_WROW = 16 + 8;           // shared weight row (bf16)
@@ -523,6 +537,7 @@ __global__ void __launch_bounds__(128) conv0_cl_kernel(int n, int M, float sigma
                                                        __nv_bfloat16* out, size_t out_bs) {
     __shared__ __align__(16) __nv_bfloat16 Xs[2 * C0_XPOS];      // (u, innovation) per position
     __shared__ __align__(16) __nv_bfloat16 Ws[CL_C * C0_WROW];   // [co][2 j + ci], zero for k >= 10
+    __shared__ __align__(16) __nv_bfloat16 Os[C0_TQ * CL_OROW];  // the output tile
     const int b = blockIdx.y, q0 = blockIdx.x * C0_TQ, stride = n / M;
     for (int e = threadIdx.x; e < CL_C * 16; e += 128) {
         const int co = e / 16, k = e % 16, j = k >> 1, ci = k & 1;
@@ -557,7 +572,6 @@ __global__ void __launch_bounds__(128) conv0_cl_kernel(int n, int M, float sigma
         bf[jj][0] = *reinterpret_cast<const uint32_t*>(Ws + c * C0_WROW + 2 * tq);
         bf[jj][1] = *reinterpret_cast<const uint32_t*>(Ws + c * C0_WROW + 2 * tq + 8);
     }
-    __nv_bfloat16* ob = out + (size_t)b * out_bs;
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -568,12 +582,14 @@ __global__ void __launch_bounds__(128) conv0_cl_kernel(int n, int M, float sigma
             const float bb0 = b0[co], bb1 = b0[co + 1];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int q = q0 + wq + 16 * i + gq + 8 * h;
+                const int q = wq + 16 * i + gq + 8 * h;
                 const float v0 = acc[2 * h] + bb0, v1 = acc[2 * h + 1] + bb1;
-                *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)q * CL_C + co) =
+                *reinterpret_cast<__nv_bfloat162*>(Os + q * CL_OROW + co) =
                     __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
             }
         }
+    __syncthreads();
+    cl_store_tile(Os, out + (size_t)b * out_bs + (size_t)q0 * CL_C);
 }
 
 // 16-byte asynchronous copy global -> shared (cp.async, completion tracked by groups)
@@ -616,7 +632,7 @@ __device__ __forceinline__ void cl_issue_slab(__nv_bfloat16* Xs, const __nv_bflo
 // previous tile is computed.  Warp w computes the 32 x 32 quarter (w / 2, w % 2) of a
 // tile with mma.sync m16n8k16, its A fragments loaded by ldmatrix straight from the slab
 // (rows 2q + j, 16 channels), its B fragments from the weights.  Epilogue: bias, ReLU,
-// BF16, channels-last store of channel pairs.
+// BF16, the tile staged in shared memory and stored as 8 KB of contiguous rows.
 __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv_bfloat16* __restrict__ in,
                                                       size_t in_bs, const __nv_bfloat16* __restrict__ wb,
                                                       const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
@@ -624,6 +640,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
     extern __shared__ __align__(16) unsigned char cl_raw[];
     __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(cl_raw);   // [64][CL_WROW]
     __nv_bfloat16* Xbuf = Ws + CL_C * CL_WROW;                       // [2][CL_XPOS][CL_XROW]
+    __nv_bfloat16* Os = Xbuf + 2 * CL_XPOS * CL_XROW;                // [CL_TQ][CL_OROW] output tile
     const int tpb = (Lin / 2) / CL_TQ, ntiles = B * tpb;
     for (int e = threadIdx.x; e < CL_C * (CL_K / 8); e += 128) {
         const int r = e / (CL_K / 8), c8 = e % (CL_K / 8);
@@ -680,7 +697,6 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
                     for (int jj = 0; jj < 4; ++jj) mma_bf16_16816(acc[i][jj], a[i], bf[jj]);
             }
         }
-        __nv_bfloat16* ob = out + (size_t)b * out_bs;
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -689,13 +705,15 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(int B, int Lin, const __nv
                 const float b0 = bias[co], b1 = bias[co + 1];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int q = q0 + wq + 16 * i + gq + 8 * h;
+                    const int q = wq + 16 * i + gq + 8 * h;
                     const float v0 = acc[i][jj][2 * h] + b0, v1 = acc[i][jj][2 * h + 1] + b1;
                     const __nv_bfloat162 pk = __floats2bfloat162_rn(v0 > 0.f ? v0 : 0.f, v1 > 0.f ? v1 : 0.f);
-                    *reinterpret_cast<__nv_bfloat162*>(ob + (size_t)q * CL_C + co) = pk;
+                    *reinterpret_cast<__nv_bfloat162*>(Os + q * CL_OROW + co) = pk;
                 }
             }
-        __syncthreads();   // every warp is done with this buffer before it is refilled
+        __syncthreads();
+        cl_store_tile(Os, out + (size_t)b * out_bs + (size_t)q0 * CL_C);
+        __syncthreads();   // every warp is done with this buffer and the output tile before reuse
     }
 }
 

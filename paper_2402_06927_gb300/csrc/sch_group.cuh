@@ -475,15 +475,15 @@ __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float>
     GLane gl;
     glane_vectors(Wa.rpic, G.pic, gl.phi_p, gl.psi_p);
     glane_vectors(Wa.rhel, G.hel, gl.phi_h, gl.psi_h);
-    float2 s1[P], c1[P];
-    wangles<CS, P>(A.n, s1, c1);
+    float sc, cc;
+    wcentre<CS, P>(A.n, sc, cc);
     int ex = 0;
     GState<CS, P> X;
     gwstart<CS, P, W>(Wa, G, gl, io.m_in + (size_t)p * A.n, X, gs, w, ex);   // its barriers also order the staging
     int iters = 0, flags = 0;
     for (int s = 0; s < io.Ns; ++s) {
         float2 W0[P][CS];
-        wnoise<CS, P>(A, noise + s * A.K, s1, c1, W0);
+        wnoise<CS, P>(A, Wa, noise + s * A.K, sc, cc, W0);
         gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, flags);
     }
     wstore<CS, P>(io.m_out + (size_t)p * A.n, X.m);
@@ -528,8 +528,8 @@ __global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float>
     GLane gl;
     glane_vectors(Wa.rpic, G.pic, gl.phi_p, gl.psi_p);
     glane_vectors(Wa.rhel, G.hel, gl.phi_h, gl.psi_h);
-    float2 s1[P], c1[P];
-    wangles<CS, P>(A.n, s1, c1);
+    float sc, cc;
+    wcentre<CS, P>(A.n, sc, cc);
     const float sq = io.sq1mr2 * (float)sqrt(A.dt_d);
     const int nblk = (K + 3) >> 2;
     int iters = 0, flags = 0, n_acc = 0, changed = 0, ex = 0;
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float>
         int fl = 0;
         for (int s = 0; s < Ns; ++s) {
             float2 W0[P][CS];
-            wnoise<CS, P>(A, noise + s * K, s1, c1, W0);
+            wnoise<CS, P>(A, Wa, noise + s * K, sc, cc, W0);
             gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl);
         }
         double mis = wmisfit<CS, P>(A, X.u, io.y);

@@ -108,12 +108,20 @@ struct WTab {
     float iB;                // 1 / B
 };
 
+// Mode-noise synthesis about each lane's centre (wnoise in sch_warp.cuh): a lane's
+// 2H nodes lie at the offsets -d_{H-1} .. -d_0, d_0 .. d_{H-1} from its centre, d_m =
+// (m + 1/2) 2 pi / n, with H = P CS <= 2 WNQ_MAX.
+constexpr int WNQ_MAX = 8;
+
 struct WArgs {
     WTab pic, hel;           // M + mu dt/2 K ;  (6/h)(M + alpha^2 K)
     RTab<float> rpic, rhel;  // their 64-row reduced systems (two rows per lane)
     WTab mat;                // Matern noise: (6/h)(M + kappa^-2 K)
     RTab<float> rmat;
     float mzw;               // Matern cell weight scale (6/h) eta sqrt(h) / 8
+    // for harmonic j = 1..K/2 and q < H/2: nco[j-1][q] = (cos j d_{H-1-q}, cos j d_q) and
+    // nsi[j-1][q] = (sin j d_{H-1-q}, sin j d_q)
+    float2 nco[SCH_MAX_K / 2][WNQ_MAX], nsi[SCH_MAX_K / 2][WNQ_MAX];
 };
 
 // Cross-warp reduced solve of a constant table for the warp-group kernels

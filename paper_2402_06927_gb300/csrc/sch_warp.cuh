@@ -209,50 +209,53 @@ __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][C
 
 // SALT increment dU/4 at this lane's nodes from the step's K weights
 // wq_k = a_j/4 (dW_k + lambda_k dt): dU_i/4 = sum_j wq_{2j-2} sin(j theta_i) +
-// wq_{2j-1} cos(j theta_i).  s1[p], c1[p]: sin and cos of the angles of the
-// first nodes of stream p's two sub-chunks; the harmonics' start values follow
-// the Chebyshev recurrence in j.  Along a sub-chunk each harmonic's value
-// v_i = a sin(j theta_i) + b cos(j theta_i) obeys v_{i+1} = 2 cos(j dtheta) v_i -
-// v_{i-1} (dtheta = 2 pi / n), run in difference form for accuracy at small angles:
-// d_{i+1} = (2 cos(j dtheta) - 2) v_i + d_i, v_{i+1} = v_i + d_{i+1}, started from v_0
-// and v_1 (one rotation of v_0 with its quadrature).  A node costs three float-pair
-// operations per harmonic (recurrence and sum).
+// wq_{2j-1} cos(j theta_i).  The lane's 2H nodes (H = P CS) sit at theta_c -+ d_m,
+// d_m = (m + 1/2) 2 pi / n, m < H, about its centre theta_c; by the angle-sum rules
+//   dU/4 (theta_c +- d) = E(d) +- O(d),  E(d) = sum_j v_j cos(j d),  O(d) = sum_j q_j sin(j d),
+//   v_j = wq_{2j-2} sin(j theta_c) + wq_{2j-1} cos(j theta_c),  q_j = wq_{2j-2} cos(j theta_c)
+//         - wq_{2j-1} sin(j theta_c),
+// so a harmonic costs the lane two FMAs for each pair of mirrored nodes (tabulated
+// cos(j d), sin(j d): WArgs nco, nsi) plus the rotation of (sin, cos)(j theta_c) to j + 1.
+// EP[q] = (E(d_{H-1-q}), E(d_q)), OP likewise, q < H/2.  sc, cc: sin and cos of theta_c.
 template <int CS, int P>
-__device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const float* wq, const float2 (&s1)[P],
-                                       const float2 (&c1)[P], float2 (&nq)[P][CS]) {
-    float2 sj[P], cj[P], nsjm[P], ncjm[P];   // nsjm = -sin((j-1) theta)
+__device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& Wa, const float* wq, float sc,
+                                       float cc, float2 (&nq)[P][CS]) {
+    constexpr int H = P * CS, Q = H / 2;
+    static_assert(H % 2 == 0 && Q <= WNQ_MAX, "a lane half of an even number of nodes within the tables");
+    float2 EP[Q], OP[Q];
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        sj[p] = s1[p];
-        cj[p] = c1[p];
-        nsjm[p] = f2b(0.f);
-        ncjm[p] = f2b(-1.f);
+    for (int q = 0; q < Q; ++q) {
+        EP[q] = f2b(0.f);
+        OP[q] = f2b(0.f);
     }
+    float sj = sc, cj = cc;
     for (int j = 0; j < A.K2; ++j) {
-        const float a = wq[2 * j], b = wq[2 * j + 1];
-        const float2 rc = f2b(A.rot_c[j]), rs = f2b(A.rot_s[j]), rd = f2b(A.rot_d[j]);
+        const float2 ab = *reinterpret_cast<const float2*>(wq + 2 * j);
+        const float2 v = f2b(fmaf(ab.x, sj, ab.y * cj));
+        const float2 qv = f2b(fmaf(ab.x, cj, -(ab.y * sj)));
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            float2 v = f2fma(f2b(a), sj[p], f2mul(f2b(b), cj[p]));
-            const float2 q = f2fma(f2b(a), cj[p], f2mul(f2b(-b), sj[p]));
-            float2 vn = f2fma(v, rc, f2mul(q, rs));
-            float2 d = f2sub(vn, v);
-            nq[p][0] = (j == 0) ? v : f2add(nq[p][0], v);
-            nq[p][1] = (j == 0) ? vn : f2add(nq[p][1], vn);
-#pragma unroll
-            for (int i = 2; i < CS; ++i) {
-                d = f2fma(rd, vn, d);
-                vn = f2add(vn, d);
-                nq[p][i] = (j == 0) ? vn : f2add(nq[p][i], vn);
-            }
-            const float2 twoc = f2add(c1[p], c1[p]);
-            const float2 sn2 = f2fma(twoc, sj[p], nsjm[p]), cn2 = f2fma(twoc, cj[p], ncjm[p]);
-            nsjm[p] = f2mul(sj[p], f2b(-1.f));
-            ncjm[p] = f2mul(cj[p], f2b(-1.f));
-            sj[p] = sn2;
-            cj[p] = cn2;
+        for (int q = 0; q < Q; ++q) {
+            EP[q] = f2fma(v, Wa.nco[j][q], EP[q]);
+            OP[q] = f2fma(qv, Wa.nsi[j][q], OP[q]);
         }
+        const float sn = fmaf(sj, cc, cj * sc);
+        cj = fmaf(cj, cc, -(sj * sc));
+        sj = sn;
     }
+    // pair (p, i), k = p CS + i: node k of the lane's first half is theta_c - d_{H-1-k},
+    // node H + k of its second half theta_c + d_k
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+#pragma unroll
+        for (int i = 0; i < CS; ++i) {
+            const int k = p * CS + i;
+            if (k < Q) {
+                nq[p][i] = make_float2(EP[k].x - OP[k].x, EP[k].y + OP[k].y);
+            } else {
+                const int q = H - 1 - k;
+                nq[p][i] = make_float2(EP[q].y - OP[q].y, EP[q].x + OP[q].x);
+            }
+        }
 }
 
 // One implicit-midpoint step of this warp's particle: (m, u) in/out, W0 holding the
@@ -369,10 +372,10 @@ __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArg
 // One step with the mode-expansion noise of the step's K weights wq.
 template <int CS, int P, int PM, int HM>
 __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
-                                      float2 (&u)[P][CS], float2* R0sm, const float* wq, const float2 (&s1)[P],
-                                      const float2 (&c1)[P], int& iters, int& flags) {
+                                      float2 (&u)[P][CS], float2* R0sm, const float* wq, float sc, float cc,
+                                      int& iters, int& flags) {
     float2 W0[P][CS];
-    wnoise<CS, P>(A, wq, s1, c1, W0);
+    wnoise<CS, P>(A, W, wq, sc, cc, W0);
     wstep_core<CS, P, PM, HM>(A, W, m, u, R0sm, W0, iters, flags);
 }
 
@@ -437,18 +440,15 @@ __device__ __forceinline__ double wmisfit(const ModelArgs<float>& A, const float
     return acc;
 }
 
-// sin and cos of the angles of the first nodes of stream p's sub-chunks p and p + P
+// sin and cos of the angle of this thread's lane centre, halfway between its nodes
+// H - 1 and H (H = P CS): 2 pi (LN t + H - 1/2) / n for thread t, LN = 2H
 template <int CS, int P>
-__device__ __forceinline__ void wangles(int n, float2 (&s1)[P], float2 (&c1)[P]) {
-    const int base = threadIdx.x * 2 * P * CS;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-        float sx, cx, sy, cy;
-        node_angle<float>(base + p * CS, n, sx, cx);
-        node_angle<float>(base + (p + P) * CS, n, sy, cy);
-        s1[p] = make_float2(sx, sy);
-        c1[p] = make_float2(cx, cy);
-    }
+__device__ __forceinline__ void wcentre(int n, float& sc, float& cc) {
+    constexpr int LN = 2 * P * CS;
+    double s, c;
+    sincospi((double)(2 * LN * (int)threadIdx.x + LN - 1) / (double)n, &s, &c);
+    sc = (float)s;
+    cc = (float)c;
 }
 
 template <int CS, int P>
@@ -467,14 +467,14 @@ __global__ void __launch_bounds__(32, WMINB) wwindow_kernel(ModelArgs<float> A, 
     const int p = blockIdx.x;
     const size_t NK = (size_t)io.Ns * A.K;
     stage_noise(A, noise, io.dW + p * NK, io.lam ? io.lam + p * NK : nullptr, io.Ns);
-    float2 s1[P], c1[P];
-    wangles<CS, P>(A.n, s1, c1);
+    float sc, cc;
+    wcentre<CS, P>(A.n, sc, cc);
     float2 m[P][CS], u[P][CS];
     wload<CS, P>(io.m_in + (size_t)p * A.n, m);
     wu_from_m<CS, P, HM>(W, m, u);
     __syncwarp();
     int iters = 0, flags = 0;
-    for (int s = 0; s < io.Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * A.K, s1, c1, iters, flags);
+    for (int s = 0; s < io.Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * A.K, sc, cc, iters, flags);
     wstore<CS, P>(io.m_out + (size_t)p * A.n, m);
     wstore<CS, P>(io.u_out + (size_t)p * A.n, u);
     if (io.y) {
@@ -511,8 +511,8 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
     const float* lam = io.lam ? io.lam + (size_t)p * NK : nullptr;
     for (int q = lane; q < NK; q += 32) cur[q] = dW[q];
     double nll0 = io.nll[p], lg0 = io.logG ? io.logG[p] : 0.0;
-    float2 s1[P], c1[P];
-    wangles<CS, P>(A.n, s1, c1);
+    float sc, cc;
+    wcentre<CS, P>(A.n, sc, cc);
     const float sq = io.sq1mr2 * (float)sqrt(A.dt_d);
     const int nblk = (K + 3) >> 2;
     int iters = 0, flags = 0, n_acc = 0, changed = 0;
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
         wu_from_m<CS, P, HM>(W, m, u);
         __syncwarp();
         int fl = 0;
-        for (int s = 0; s < Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * K, s1, c1, iters, fl);
+        for (int s = 0; s < Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * K, sc, cc, iters, fl);
         const double mis = warp_sum(wmisfit<CS, P>(A, u, io.y));
         const double gl = warp_sum(window_girsanov(A, prop, lam, Ns));
         const double nll1 = 0.5 * mis, lg1 = -gl;
