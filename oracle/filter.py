@@ -171,7 +171,7 @@ def pcn_propose(dW: np.ndarray, dW_hat: np.ndarray, rho: float) -> np.ndarray:
 
 
 def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, state=None,
-           particle0=0, margins=False):
+           particle0=0, margins=False, gen=_rng.GEN64):
     """n_iter PCN moves of every particle's window noise at temperature theta.
 
     For iteration j the proposal noise is keyed (seed, TAG_PCN, ctr + j) and the
@@ -179,6 +179,7 @@ def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, sta
     the whole window from m_start; it is accepted iff log U < w0 - w1 with
     w = theta (NLL - logG).  ``state`` = (nll, logG, m_end, u_end) of the
     current noise, recomputed when omitted.
+    ``gen``: the generator of the proposal normals (GEN32: the FP32 Matern kernels').
     Returns (dW, nll, logG, m_end, u_end, accepts), and with ``margins`` also the
     [n_iter, N] Metropolis margins (w0 - w1) - log U (a move is accepted iff its
     margin is positive), the [n_iter, N] proposal NLLs and the [n_iter, N] NLLs of the
@@ -198,7 +199,7 @@ def jitter(model, m_start, dW, lam, y, sigma, theta, rho, n_iter, seed, ctr, sta
     prop_nll = np.zeros((n_iter, N))
     prev_nll = np.zeros((n_iter, N))
     for j in range(n_iter):
-        hat = _rng.window_increments(seed, _rng.TAG_PCN, N, Ns, K, model.dt, ctr + j, particle0)
+        hat = _rng.window_increments(seed, _rng.TAG_PCN, N, Ns, K, model.dt, ctr + j, particle0, gen=gen)
         prop = pcn_propose(dW, hat, rho)
         pm, pu, _, _ = model.ensemble_window(m_start, prop, lam_arr)
         p_nll = nll(pu, y, sigma)
