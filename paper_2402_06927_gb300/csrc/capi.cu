@@ -574,10 +574,11 @@ int sch_draw_increments(sch_ctx* ctx, int N, int nsteps, uint64_t seed, uint64_t
     if (N == 0 || nsteps == 0) return SCH_OK;
     if (!dW) return SCH_ERR_ARG;
     const double sq = sqrt(ctx->p.dt);
+    // the FP32 Matern noise (one normal per cell) comes from Philox4x32-10
     if (ctx->p.dtype == SCH_F32)
-        return launch_draw<float>(N, nsteps, ctx->Q, (float)sq, seed, tag, ctr, particle0, (float*)dW,
-                                  S(stream));
-    return launch_draw<double>(N, nsteps, ctx->Q, sq, seed, tag, ctr, particle0, (double*)dW, S(stream));
+        return launch_draw<float>(N, nsteps, ctx->Q, (float)sq, seed, tag, ctr, particle0, ctx->matern,
+                                  (float*)dW, S(stream));
+    return launch_draw<double>(N, nsteps, ctx->Q, sq, seed, tag, ctr, particle0, 0, (double*)dW, S(stream));
 }
 
 int sch_ensemble_step(sch_ctx* ctx, int N, int nsteps, const void* m, void* m_out, void* u_out,

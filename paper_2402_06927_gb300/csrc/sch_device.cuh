@@ -1,7 +1,7 @@
 // Device building blocks of the SCH particle-filter kernels (sm_103a).
 //
-// * Philox4x64-10 counter-based generator (Salmon et al., SC'11) and the
-//   Box-Muller transform, so that every draw is a pure function of
+// * Philox4x64-10 and Philox4x32-10 counter-based generators (Salmon et al.,
+//   SC'11) and the Box-Muller transform, so that every draw is a pure function of
 //   (seed, purpose, block, step, particle, stream counter).
 // * Reciprocal and warp-reduction helpers.
 #pragma once
@@ -79,6 +79,63 @@ __device__ __forceinline__ void box_muller(uint64_t a, uint64_t b, float& z0, fl
     __sincosf(6.28318531f * (u53_to_float(b >> 11) - 0.5f), &s, &c);
     z0 = -r * c;
     z1 = -r * s;
+}
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (the same paper): ten rounds of two 32 x 32 -> 64-bit products on a
+// 4 x 32-bit counter, the 2 x 32-bit key bumped by two Weyl constants between rounds.
+// The FP32 Matern kernels draw one normal per cell and step from it, where the
+// 64-bit products of Philox4x64 would take a third of the step.  Key (seed mod 2^32,
+// (seed >> 32) mod 2^16 + tag 2^16), counter words taken mod 2^32.
+// --------------------------------------------------------------------------
+constexpr uint32_t PHILOX32_M0 = 0xD2511F53u;
+constexpr uint32_t PHILOX32_M1 = 0xCD9E8D57u;
+constexpr uint32_t PHILOX32_W0 = 0x9E3779B9u;
+constexpr uint32_t PHILOX32_W1 = 0xBB67AE85u;
+
+struct U32x4 { uint32_t v0, v1, v2, v3; };
+
+__device__ __forceinline__ U32x4 philox4x32(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                            uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = PHILOX32_M0 * c0, hi0 = __umulhi(PHILOX32_M0, c0);
+        const uint32_t lo1 = PHILOX32_M1 * c2, hi1 = __umulhi(PHILOX32_M1, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += PHILOX32_W0; k1 += PHILOX32_W1;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// Box-Muller in FP32 on two 32-bit words: u1 = (a + 1) 2^-32 in (0, 1], u2 = b 2^-32 in
+// [0, 1).  As the 53-bit transform: r^2 from __logf where u1 <= 15/16, from the series of
+// -ln(1 - x) on x = 1 - u1 = (~a) 2^-32 (exact as an integer) nearer one; the angle as
+// theta + pi with theta = 2 pi (u2 - 1/2).
+__device__ __forceinline__ void box_muller32(uint32_t a, uint32_t b, float& z0, float& z1) {
+    const uint32_t w = ~a;   // (1 - u1) 2^32
+    float r2;
+    if (w < (1u << 28)) {
+        const float x = __uint2float_rn(w) * 0x1.0p-32f;
+        r2 = 2.0f * x * (1.0f + x * (0.5f + x * (1.0f / 3.0f + x * (0.25f + x * 0.2f))));
+    } else {
+        r2 = -2.0f * __logf(fmaf(__uint2float_rn(a), 0x1.0p-32f, 0x1.0p-32f));
+    }
+    const float r = sqrtf(r2);
+    float s, c;
+    __sincosf(6.28318531f * fmaf(__uint2float_rn(b), 0x1.0p-32f, -0.5f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
+}
+
+// Four FP32 normals of Philox4x32 block (blk, c1, c2, c3) under (seed, tag)
+__device__ __forceinline__ void normal4_32(uint64_t seed, uint64_t tag, uint64_t blk, uint64_t c1, uint64_t c2,
+                                           uint64_t c3, float z[4]) {
+    const uint32_t k1 = ((uint32_t)(seed >> 32) & 0xFFFFu) | ((uint32_t)tag << 16);
+    const U32x4 r = philox4x32((uint32_t)blk, (uint32_t)c1, (uint32_t)c2, (uint32_t)c3, (uint32_t)seed, k1);
+    box_muller32(r.v0, r.v1, z[0], z[1]);
+    box_muller32(r.v2, r.v3, z[2], z[3]);
 }
 
 // Four normals of block (blk, c1, c2, c3) under key (seed, tag).

@@ -57,6 +57,21 @@ __device__ __forceinline__ void glane_vectors(const RTab<float>& Q, const GTab& 
     psi = pcr32_const(lane == 31 ? G.LC : 0.f, Q);
 }
 
+// The boundary values of the 2W system are four sums over its 2W inputs (y_0 and y_31 of
+// every warp): lane L takes sum o = L / 8 (bprev, bself, aself, anext) and the inputs e =
+// L % 8 + 8 t < 2W; its weights, fixed for the kernel, come from the table once.
+constexpr int GNT = (2 * GW_MAX + 7) / 8;
+template <int W>
+__device__ __forceinline__ void glane_weights(const GTab& G, float (&cw)[GNT]) {
+    const int lane = threadIdx.x & 31, o = lane >> 3;
+    const float* tab = (o == 0) ? G.bprev : (o == 1) ? G.bself : (o == 2) ? G.aself : G.anext;
+#pragma unroll
+    for (int t = 0; t < GNT; ++t) {
+        const int e = (lane & 7) + 8 * t;
+        cw[t] = (e < 2 * W) ? tab[e] : 0.f;
+    }
+}
+
 // The lane's outer chunk-end neighbours of a paired field (see whalo), with the
 // values at the nodes outside the warp, Lv (before its first node) and Rv (after
 // its last), taken by lanes 0 and 31.
@@ -92,7 +107,8 @@ __device__ __forceinline__ void gends(float first, float last, float& Lv, float&
 // slot buffer the exchange used (valid until the next exchange).
 template <int P, int W>
 __device__ __forceinline__ const GSlot* gwreduced(const WTab& T, const RTab<float>& Q, const GTab& G, float phi,
-                                                  float psi, const float2 (&pd)[P], const float2 (&de)[P],
+                                                  float psi, const float (&cw)[GNT], const float2 (&pd)[P],
+                                                  const float2 (&de)[P],
                                                   float2 (&E)[P], float2 (&F)[P], float& Ep, float& Fn, float& Lv,
                                                   float& Rv, GShared<W>* gs, int w, int& ex, float dm, float mm) {
     constexpr int S = 2 * P;
@@ -134,26 +150,28 @@ __device__ __forceinline__ const GSlot* gwreduced(const WTab& T, const RTab<floa
     }
     __syncthreads();
     ++ex;
-    // boundary values: every warp's y_0, y_31 corrected by its m, then the tabulated
-    // inverse of the 2W system, in warp order relative to this warp (k = 0: this warp)
-    float bp = 0.f, bs = 0.f, as = 0.f, an = 0.f, mw = 0.f;
-    float4 sn = sl[w].a;   // the slot of warp (w + k + 1) % W, starting at k = W - 1
-    float4 s1 = sn;
+    // boundary values: every warp's y_0, y_31 corrected by its m (the part of its lane 31's
+    // row from the next warp), then the tabulated inverse of the 2W system, in warp order
+    // relative to this warp (k = 0: this warp); lane L forms its inputs' terms of sum L / 8
+    float part = 0.f;
 #pragma unroll
-    for (int k = W - 1; k >= 0; --k) {
-        const float4 s = sl[(w + k) % W].a;
-        const float mk = G.cq * sn.z + G.geL * sn.w;
-        const float yh0 = s.x - mk * G.p2_0, yh31 = s.y - mk * G.p2_31;
-        bp = fmaf(G.bprev[k], yh0, fmaf(G.bprev[W + k], yh31, bp));
-        bs = fmaf(G.bself[k], yh0, fmaf(G.bself[W + k], yh31, bs));
-        as = fmaf(G.aself[k], yh0, fmaf(G.aself[W + k], yh31, as));
-        an = fmaf(G.anext[k], yh0, fmaf(G.anext[W + k], yh31, an));
-        if (k == 0) {
-            mw = mk;
-            s1 = sn;
+    for (int t = 0; t < GNT; ++t) {
+        const int e = (lane & 7) + 8 * t;
+        if (8 * t < 2 * W) {
+            const int k = e % W;
+            const float4 s = sl[(w + k) % W].a, sn = sl[(w + k + 1) % W].a;
+            const float mk = G.cq * sn.z + G.geL * sn.w;
+            const float yh = (e < W) ? s.x - mk * G.p2_0 : s.y - mk * G.p2_31;
+            part = fmaf(cw[t], yh, part);
         }
-        sn = s;
     }
+    part += __shfl_xor_sync(FULL, part, 1);
+    part += __shfl_xor_sync(FULL, part, 2);
+    part += __shfl_xor_sync(FULL, part, 4);
+    const float bp = __shfl_sync(FULL, part, 0), bs = __shfl_sync(FULL, part, 8);
+    const float as = __shfl_sync(FULL, part, 16), an = __shfl_sync(FULL, part, 24);
+    const float4 s1 = sl[(w + 1) % W].a;
+    const float mw = G.cq * s1.z + G.geL * s1.w;
     const float EL = y - (bp - bs) * phi - (an - as + mw * G.iLC) * psi;
     const float Epr = __shfl_sync(FULL, EL, (lane + 31) & 31);
     Ep = (lane == 0) ? bp : Epr;
@@ -256,6 +274,7 @@ __device__ __forceinline__ void gwreduced_ldiag(const WTab& T, const RTab<float>
 // per-lane vectors of the two tables and the CTA's exchange state
 struct GLane {
     float phi_p, psi_p, phi_h, psi_h;
+    float cw_p[GNT], cw_h[GNT];
 };
 
 // u = H^{-1} M m for this warp's nodes; m's outside values mL, mR in, u's out
@@ -274,7 +293,8 @@ __device__ __forceinline__ void gwu_from_m(const WArgs& Wa, const GArgs& G, cons
     float2 pd[P], de[P], E[P], F[P];
     float Ep, Fn;
     wsweep<CS, P>(Wa.hel, x, pd, de);
-    gwreduced<P, W>(Wa.hel, Wa.rhel, G.hel, gl.phi_h, gl.psi_h, pd, de, E, F, Ep, Fn, uL, uR, gs, w, ex, 0.f, 0.f);
+    gwreduced<P, W>(Wa.hel, Wa.rhel, G.hel, gl.phi_h, gl.psi_h, gl.cw_h, pd, de, E, F, Ep, Fn, uL, uR, gs, w, ex, 0.f,
+                    0.f);
     wback<CS, P>(Wa.hel, x, F, E, u);
 }
 
@@ -357,8 +377,8 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
         if constexpr (PD)
             gwreduced_ldiag<P, W>(Wa.pic, Wa.rpic, G.pic, pd, de, E, F, Ep, Fn, miL, miR, gs, w, ex);
         else
-            gwreduced<P, W>(Wa.pic, Wa.rpic, G.pic, gl.phi_p, gl.psi_p, pd, de, E, F, Ep, Fn, miL, miR, gs, w, ex,
-                            0.f, 0.f);
+            gwreduced<P, W>(Wa.pic, Wa.rpic, G.pic, gl.phi_p, gl.psi_p, gl.cw_p, pd, de, E, F, Ep, Fn, miL, miR, gs, w,
+                            ex, 0.f, 0.f);
         float2 mn[P][CS];
         wback<CS, P>(Wa.pic, x, F, E, mn);
         float dmax = 0.f, mmax = 0.f;
@@ -387,8 +407,8 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
             float2 hpd[P], hde[P], hE[P], hF[P];
             float hEp, hFn;
             wsweep<CS, P>(Wa.hel, x, hpd, hde);
-            sl = gwreduced<P, W>(Wa.hel, Wa.rhel, G.hel, gl.phi_h, gl.psi_h, hpd, hde, hE, hF, hEp, hFn, X.uL, X.uR,
-                                 gs, w, ex, dmw, mmw);
+            sl = gwreduced<P, W>(Wa.hel, Wa.rhel, G.hel, gl.phi_h, gl.psi_h, gl.cw_h, hpd, hde, hE, hF, hEp, hFn, X.uL,
+                                 X.uR, gs, w, ex, dmw, mmw);
             wback<CS, P>(Wa.hel, x, hF, hE, X.u);
         }
         iters++;
@@ -475,6 +495,8 @@ __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float>
     GLane gl;
     glane_vectors(Wa.rpic, G.pic, gl.phi_p, gl.psi_p);
     glane_vectors(Wa.rhel, G.hel, gl.phi_h, gl.psi_h);
+    glane_weights<W>(G.pic, gl.cw_p);
+    glane_weights<W>(G.hel, gl.cw_h);
     float sc, cc;
     wcentre<CS, P>(A.n, sc, cc);
     int ex = 0;
@@ -528,6 +550,8 @@ __global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float>
     GLane gl;
     glane_vectors(Wa.rpic, G.pic, gl.phi_p, gl.psi_p);
     glane_vectors(Wa.rhel, G.hel, gl.phi_h, gl.psi_h);
+    glane_weights<W>(G.pic, gl.cw_p);
+    glane_weights<W>(G.hel, gl.cw_h);
     float sc, cc;
     wcentre<CS, P>(A.n, sc, cc);
     const float sq = io.sq1mr2 * (float)sqrt(A.dt_d);

@@ -271,7 +271,7 @@ int launch_window_matern(const ModelArgs<R>& A, const WindowIO<R>& io, int N, cu
 template <typename R, int C>
 int launch_jitter_matern(const ModelArgs<R>& A, const JitterIO<R>& io, int N, cudaStream_t st);
 template <typename R>
-int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0,
+int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0, int gen32,
                 R* dW, cudaStream_t st);
 template <typename R>
 int launch_loglik(const ModelArgs<R>& A, int N, const R* u, const R* y, const R* dW, const R* lam, int Ns,

@@ -11,18 +11,24 @@
 // registers.
 #pragma once
 
+#include <type_traits>
+
 #include "sch_kernels.cuh"
 
 namespace sch {
 
-// normals of cells [i0, i0 + C) of step s under (seed, tag) at particle counter pc
+// normals of cells [i0, i0 + C) of step s under (seed, tag) at particle counter pc:
+// Philox4x32-10 in FP32, Philox4x64-10 in FP64
 template <typename R, int C>
 __device__ __forceinline__ void cell_normals(uint64_t seed, int i0, int s, uint64_t pc, uint64_t ctr, R (&z)[C]) {
     static_assert(C % 4 == 0, "a chunk covers whole Philox blocks");
 #pragma unroll
     for (int b = 0; b < C / 4; ++b) {
         R zb[4];
-        normal4<R>(seed, SCH_TAG_PCN, (uint64_t)((i0 >> 2) + b), (uint64_t)s, pc, ctr, zb);
+        if constexpr (std::is_same<R, float>::value)
+            normal4_32(seed, SCH_TAG_PCN, (uint64_t)((i0 >> 2) + b), (uint64_t)s, pc, ctr, zb);
+        else
+            normal4<R>(seed, SCH_TAG_PCN, (uint64_t)((i0 >> 2) + b), (uint64_t)s, pc, ctr, zb);
 #pragma unroll
         for (int e = 0; e < 4; ++e) z[4 * b + e] = zb[e];
     }

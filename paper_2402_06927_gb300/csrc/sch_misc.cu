@@ -7,10 +7,11 @@
 
 namespace sch {
 
-// dW[p][s][k] = sqrt(dt) z, z from block (k/4, s, particle0 + p, ctr)
+// dW[p][s][k] = sqrt(dt) z, z from block (k/4, s, particle0 + p, ctr): Philox4x32-10 when
+// gen32 (R float), else Philox4x64-10
 template <typename R>
 __global__ void draw_kernel(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr,
-                            int particle0, R* dW) {
+                            int particle0, int gen32, R* dW) {
     const int nblk = (K + 3) >> 2;
     const long long tot = (long long)N * Ns * nblk;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < tot;
@@ -19,7 +20,14 @@ __global__ void draw_kernel(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_
         const int s = (int)((q / nblk) % Ns);
         const int p = (int)(q / ((long long)nblk * Ns));
         R z[4];
-        normal4<R>(seed, tag, (uint64_t)b, (uint64_t)s, (uint64_t)(particle0 + p), ctr, z);
+        if constexpr (std::is_same<R, float>::value) {
+            if (gen32)
+                normal4_32(seed, tag, (uint64_t)b, (uint64_t)s, (uint64_t)(particle0 + p), ctr, z);
+            else
+                normal4<R>(seed, tag, (uint64_t)b, (uint64_t)s, (uint64_t)(particle0 + p), ctr, z);
+        } else {
+            normal4<R>(seed, tag, (uint64_t)b, (uint64_t)s, (uint64_t)(particle0 + p), ctr, z);
+        }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int k = 4 * b + e;
@@ -61,13 +69,13 @@ __global__ void loglik_kernel(ModelArgs<R> A, int N, const R* u, const R* y, con
 
 template <typename R>
 int launch_draw(int N, int Ns, int K, R sqdt, uint64_t seed, uint64_t tag, uint64_t ctr, int particle0,
-                R* dW, cudaStream_t st) {
+                int gen32, R* dW, cudaStream_t st) {
     const long long tot = (long long)N * Ns * ((K + 3) / 4);
     const int threads = 256;
     long long blocks = (tot + threads - 1) / threads;
     if (blocks > (long long)device_sms() * 16) blocks = (long long)device_sms() * 16;
     if (blocks < 1) blocks = 1;
-    draw_kernel<R><<<(int)blocks, threads, 0, st>>>(N, Ns, K, sqdt, seed, tag, ctr, particle0, dW);
+    draw_kernel<R><<<(int)blocks, threads, 0, st>>>(N, Ns, K, sqdt, seed, tag, ctr, particle0, gen32, dW);
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 
@@ -80,8 +88,9 @@ int launch_loglik(const ModelArgs<R>& A, int N, const R* u, const R* y, const R*
     return cudaGetLastError() == cudaSuccess ? SCH_OK : SCH_ERR_CUDA;
 }
 
-template int launch_draw<float>(int, int, int, float, uint64_t, uint64_t, uint64_t, int, float*, cudaStream_t);
-template int launch_draw<double>(int, int, int, double, uint64_t, uint64_t, uint64_t, int, double*,
+template int launch_draw<float>(int, int, int, float, uint64_t, uint64_t, uint64_t, int, int, float*,
+                                 cudaStream_t);
+template int launch_draw<double>(int, int, int, double, uint64_t, uint64_t, uint64_t, int, int, double*,
                                  cudaStream_t);
 template int launch_loglik<float>(const ModelArgs<float>&, int, const float*, const float*, const float*,
                                   const float*, int, double*, double*, cudaStream_t);

@@ -229,6 +229,7 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& W
         OP[q] = f2b(0.f);
     }
     float sj = sc, cj = cc;
+#pragma unroll 2
     for (int j = 0; j < A.K2; ++j) {
         const float2 ab = *reinterpret_cast<const float2*>(wq + 2 * j);
         const float2 v = f2b(fmaf(ab.x, sj, ab.y * cj));

@@ -48,7 +48,7 @@ __device__ __forceinline__ void wmatern_noise(const ModelArgs<float>& A, const W
     }
 }
 
-// PCN normals of this lane's cells at step s: Philox (seed, SCH_TAG_PCN) block c / 4
+// PCN normals of this lane's cells at step s: Philox4x32-10 (seed, SCH_TAG_PCN) block c / 4
 // gives the normals of cells c .. c + 3 (a sub-chunk holds whole blocks).  The blocks
 // are drawn in a rolled loop into the lane's column of zsm (cell k of the lane at
 // zsm[32 k + lane]; the lane reads back only what it wrote).
@@ -62,7 +62,7 @@ __device__ __forceinline__ void wcell_normals(uint64_t seed, int s, uint64_t pc,
 #pragma unroll 1
     for (int b = 0; b < NB; ++b) {
         float zb[4];
-        normal4<float>(seed, SCH_TAG_PCN, (uint64_t)(b0 + b), (uint64_t)s, pc, ctr, zb);
+        normal4_32(seed, SCH_TAG_PCN, (uint64_t)(b0 + b), (uint64_t)s, pc, ctr, zb);
 #pragma unroll
         for (int e = 0; e < 4; ++e) zsm[(4 * b + e) * 32 + lane] = zb[e];
     }

@@ -44,6 +44,14 @@ def nll_error_bound(nll, m_obs, u_scale, sigma, rel_tol):
     return np.sqrt(2.0 * max(nll, 0.0) * m_obs) * d + 0.5 * m_obs * d * d
 
 
+def pcn_generator(g):
+    """The oracle generator that matches a GPU model's per-cell draws: Philox4x32-10 for the
+    FP32 Matern noise, Philox4x64-10 otherwise."""
+    import torch
+    from oracle import rng as ORNG
+    return ORNG.GEN32 if (g.noise == "matern" and g.dtype == torch.float32) else ORNG.GEN64
+
+
 def jitter_moves_vs_oracle(g, om, cfg, m0d, dWd, lad, yd, theta, n_iter, seed, ctr, particles, field_tol, rho=None):
     """PCN jitter on the GPU one move at a time against the oracle, move by move.
 
@@ -59,6 +67,7 @@ def jitter_moves_vs_oracle(g, om, cfg, m0d, dWd, lad, yd, theta, n_iter, seed, c
     import torch
     from oracle import filter as OF
     rho = cfg.rho if rho is None else rho
+    gen = pcn_generator(g)
     st = g.ensemble_step(m0d, dWd, lad, yd)
     nll, logG, m_end, u_end = st["nll"], st["logG"], st["m"], st["u"]
     s0 = st["status"].cpu().numpy()
@@ -78,7 +87,7 @@ def jitter_moves_vs_oracle(g, om, cfg, m0d, dWd, lad, yd, theta, n_iter, seed, c
         for p in particles:
             la_p = None if lah is None else lah[p:p + 1]
             r = OF.jitter(om, m0h[p:p + 1], dW_before[p:p + 1], la_p, yh, cfg.sigma, theta, rho, 1, seed,
-                          ctr + j, particle0=p, margins=True)
+                          ctr + j, particle0=p, margins=True, gen=gen)
             dW_o, nll_o, _, _, u_o, acc_o, marg, prop_nll, prev_nll = r
             nll_cur = prev_nll[0, 0]
             u_scale = float(np.max(np.abs(u_o[0])))

@@ -85,6 +85,23 @@ def test_matern_draw_increments_one_per_cell():
     assert np.max(np.abs(dW - ref)) < 1e-13
 
 
+def test_matern_f32_draws_philox4x32():
+    # the FP32 Matern increments come from Philox4x32-10: the raw words equal the oracle's bit
+    # for bit, so the normals agree to the FP32 Box-Muller transform's error (a few 1e-6
+    # relative, 1e-5 absolute at |z| <= 6), across counters whose words exceed 32 bits
+    cfg = get_config("cfg2m_f32")
+    g = gpu_model(cfg)
+    for seed, ctr, p0 in ((123, 9, 2), (2**40 + 7, 2**33 + 5, 1000)):
+        dW = g.draw_increments(3, cfg.Ns, seed, ORNG.TAG_PRIOR_DW, ctr, particle0=p0).double().cpu().numpy()
+        ref = ORNG.window_increments(seed, ORNG.TAG_PRIOR_DW, 3, cfg.Ns, cfg.n, cfg.dt, ctr, particle0=p0,
+                                     gen=ORNG.GEN32)
+        other = ORNG.window_increments(seed, ORNG.TAG_PRIOR_DW, 3, cfg.Ns, cfg.n, cfg.dt, ctr, particle0=p0)
+        z, zr = dW / np.sqrt(cfg.dt), ref / np.sqrt(cfg.dt)
+        assert np.max(np.abs(z - zr)) < 1e-5
+        assert np.max(np.abs(z - zr) / np.maximum(1.0, np.abs(zr))) < 1e-5
+        assert np.max(np.abs(dW - other)) > 0.1   # not the 4x64 stream
+
+
 @pytest.mark.parametrize("lam", [False, True])
 def test_matern_jitter_matches_oracle(lam):
     cfg = get_config("cfg1m_f64")
