@@ -86,10 +86,15 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # wjitter_kernel<8,2,1,2>, specialised to a diagonal Picard and a PCR Helmholtz reduced
     # solve: 4.609792 MB read, 0 written
     "9a63bdc05dd81bd373a067cd982f7c3df6d28ae3": 4609792,
+    # with the mode noise synthesised about each lane's centre: 4.606208 MB read, 0 written
+    "89f00e16f90e5da10455045dc964eaeb5a808c25": 4606208,
 }, "cfg5_f32": {
     # gjitter_kernel<8,2,4,1>, profiles/gjitter_kernel_cfg5_n4096_N8192.md: 148.514304 MB read,
     # 226.438400 MB written
     "6fce80f5f13a05b4970ec3ed280a4c0d9d5f84c0": 374952704,
+    # with the mode noise about each lane's centre and the cross-warp boundary sums spread over
+    # the lanes: 146.914304 MB read, 224.452352 MB written
+    "ca8b3fbf873a39287412fb86b247418fef952395": 371366656,
 }}
 
 
@@ -369,6 +374,7 @@ def run_ours(args):
         f.cycle(ys[c], c)
         f.advance()
     torch.cuda.synchronize()
+    m_warm = f.m_start.clone()   # the end-to-end runs restart from here, on the timed cycles
     barrier(ws)
     torch.cuda.synchronize()
 
@@ -425,29 +431,31 @@ def run_ours(args):
     mean_host = torch.empty(cfg.n, dtype=torch.float64).pin_memory()
     dg_host = torch.empty(8, dtype=torch.float64).pin_memory()
     y_dev = [torch.empty_like(ys[0]) for _ in range(2)]
-    # E2E_RUNS runs of up to E2E_CYCLES cycles, each from the same start state; the median
-    # run is reported (a host stall on a shared machine moves a single short run by tens of
-    # percent), with every run's value beside it
+    # E2E_RUNS runs of up to E2E_CYCLES cycles, the same cycles as the timed loop (from the
+    # state after the warm-up cycles); the median run is reported (a host stall on a shared
+    # machine moves a single short run by tens of percent), with every run's value beside it
     e2e_steps = min(args.steps, E2E_CYCLES if cfg.N * cfg.n <= (1 << 20) else E2E_CYCLES // 3)
+    c0 = args.warmup
     e2e_runs = []
     for _ in range(E2E_RUNS):
         f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
-        f2.set_state(m0)
+        f2.set_state(m_warm)
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         fwd2 = 0
-        y_dev[0].copy_(y_host[0], non_blocking=True)
-        for c in range(e2e_steps):
-            def post(c=c, f2=f2):
+        y_dev[0].copy_(y_host[c0], non_blocking=True)
+        for k in range(e2e_steps):
+            c = c0 + k
+            def post(k=k, c=c, f2=f2):
                 # enqueued by the cycle before it waits for its stages: diagnostics of the analysis,
                 # their copy to the host, and the next step's observations to the device
                 g.diagnostics(f2.u_end, truths[c], ws=diag_ws, out=diag_out)
                 mean_host.copy_(diag_ws, non_blocking=True)
                 dg_host.copy_(diag_out, non_blocking=True)
-                if c + 1 < e2e_steps:
-                    y_dev[(c + 1) % 2].copy_(y_host[c + 1], non_blocking=True)
-            st = f2.cycle(y_dev[c % 2], c, post=post)   # returns once its stages and post's work are done
+                if k + 1 < e2e_steps:
+                    y_dev[(k + 1) % 2].copy_(y_host[c + 1], non_blocking=True)
+            st = f2.cycle(y_dev[k % 2], c, post=post)   # returns once its stages and post's work are done
             f2.advance()
             fwd2 += st.forward_steps
         e2e_s = reduce_max(time.perf_counter() - t0, ws)
@@ -985,8 +993,9 @@ def run_proposal(args):
 
 def run_occupancy(args):
     """--occupancy: one jitter launch of the bench workload (10 PCN proposals of a
-    10-step window, n = 1024, K = 8, FP32) at N = 152 .. 2432 particles, i.e. 1 .. 16
-    warps per SM in the warp layout; best of --steps timed launches (CUDA events) each."""
+    10-step window, n = 1024, K = 8, FP32) at N = 1 .. 16 particles per SM (152 .. 2432 on
+    a GB300), i.e. 1 .. 16 warps per SM in the warp layout; best of --steps timed launches
+    (CUDA events) each."""
     import torch
     from workloads import get_config, u0_profile
     from paper_2402_06927_gb300.api import SchModel
@@ -996,7 +1005,9 @@ def run_occupancy(args):
     u0 = torch.tensor(u0_profile(cfg), dtype=torch.float32, device="cuda")
     y = g.synth_obs(u0, 1, 1)
     rows = []
-    for N in (152, 304, 608, 912, 1216, 1824, 2432):
+    sms = sm_count()
+    for per_sm in (1, 2, 4, 6, 8, 12, 16):
+        N = per_sm * sms
         m0, _ = g.prior_sample(N, u0, 3, cfg.prior_scale)
         dW = g.draw_increments(N, cfg.Ns, 5, 1, 0)
         st = g.ensemble_step(m0, dW, None, y)
@@ -1010,7 +1021,7 @@ def run_occupancy(args):
             e1.record()
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
-        rows.append({"N": N, "warps_per_sm": N / 152, "ms_per_launch": min(ms[1:]),
+        rows.append({"N": N, "warps_per_sm": N / sms, "ms_per_launch": min(ms[1:]),
                      "picard_iters_per_step": it.float().mean().item() / (10 * cfg.Ns)})
     print(json.dumps({"occupancy_sweep": rows, "kernel": f"wjitter ({g.layout} layout)"}))
     return 0
