@@ -95,6 +95,9 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # with the mode noise about each lane's centre and the cross-warp boundary sums spread over
     # the lanes: 146.914304 MB read, 224.452352 MB written
     "ca8b3fbf873a39287412fb86b247418fef952395": 371366656,
+    # the same kernel code with the n = 1024 two-warp instantiation in the shared sources:
+    # 146.407424 MB read, 223.907072 MB written
+    "6d734c792c38fc1efbfce31cd3ea97b59f2aea75": 370314496,
 }}
 
 
@@ -303,13 +306,26 @@ def oracle_parallel(name, budget_s: float = 10.0, per_core: int = 512):
                                  f"{wall:.1f} s")
 
 
+def workload_config(cfg, ws):
+    """The keys of the bench line's `config` that name the workload (both arms)."""
+    matern = cfg.noise == "matern"
+    return {"workload": (f"{cfg.name}: SCH twin experiment n={cfg.n} "
+                         + (f"Matern noise (kappa={cfg.kappa} eta={cfg.eta} k={cfg.matern_k}, "
+                            f"{cfg.n} Brownian motions per step) " if matern else f"K={cfg.K} ")
+                         + f"N={cfg.N} Ns={cfg.Ns} M={cfg.M} sigma={cfg.sigma} N*=N/2 "
+                           f"jitter={cfg.n_jitter} rho={cfg.rho} "
+                           f"({'FP32' if cfg.dtype == 'f32' else 'FP64'} fields, FP64 weights)"),
+            "n": cfg.n, "N": cfg.N, "Ns": cfg.Ns, "K": cfg.K, "Q": cfg.Q, "M": cfg.M,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}
+
+
 def run_reference(args):
     """--impl reference: the oracle on the host cores, per step a bounded sample."""
     from workloads import get_config
     rank, ws = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
-    cfg = get_config(WORKLOAD)
+    cfg = get_config(args.workload)
     for _ in range(args.warmup):
         oracle_sample(cfg, budget_s=0.0, min_particles=1)
     rates = []
@@ -318,7 +334,7 @@ def run_reference(args):
     cores = 1
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r, cores, sample = oracle_parallel(WORKLOAD, budget_s=6.0)
+        r, cores, sample = oracle_parallel(args.workload, budget_s=6.0)
         rates.append(r)
         t_all += time.perf_counter() - t0
     value = statistics.mean(rates)
@@ -326,7 +342,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": cfg.n, "N": cfg.N, "Ns": cfg.Ns, "K": cfg.K},
+        "data": "synthetic", "config": workload_config(cfg, ws),
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -477,14 +493,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype, "data": "synthetic",
-            "config": {"workload": (f"{cfg.name}: SCH twin experiment n={cfg.n} "
-                                    + (f"Matern noise (kappa={cfg.kappa} eta={cfg.eta} k={cfg.matern_k}, "
-                                       f"{cfg.n} Brownian motions per step) " if matern else f"K={cfg.K} ")
-                                    + f"N={N} Ns={cfg.Ns} M={cfg.M} sigma={cfg.sigma} N*=N/2 "
-                                      f"jitter={cfg.n_jitter} rho={cfg.rho} "
-                                      f"({'FP32' if cfg.dtype == 'f32' else 'FP64'} fields, FP64 weights)"),
-                       "n": cfg.n, "N": N, "Ns": cfg.Ns, "K": cfg.K, "Q": cfg.Q, "M": cfg.M,
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU", "layout": g.layout,
+            "config": {**workload_config(cfg, ws), "layout": g.layout,
                        "l2": "flushed between timed steps (256 MB write)",
                        "cycles_per_s": args.steps * ws / dev_s_max,
                        "mean_tempering_stages": statistics.mean(stages),

@@ -77,7 +77,9 @@ enum { SCH_SOLVER_AUTO = 0, SCH_SOLVER_LI = 1, SCH_SOLVER_EA = 2 };
  *                      the cyclic solves are completed across the warps through
  *                      shared memory, one CTA barrier per solve: float fields,
  *                      SCH_SOLVER_EA, the mode expansion and n = 2048 or 4096 only;
- *   SCH_LAYOUT_GROUP16 the same with 16 nodes a lane (n/512 warps per particle);
+ *   SCH_LAYOUT_GROUP16 the same with 16 nodes a lane (n/512 warps per particle),
+ *                      also at n = 1024 (two warps per particle; only when asked
+ *                      for: AUTO takes WARP there);
  *   SCH_LAYOUT_AUTO    WARP where it applies (with either noise model), else
  *                      GROUP where it applies, else CTA.
  * All compute the same iteration; results agree to rounding. */

@@ -494,11 +494,12 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
     }
     const bool warp_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && (p.n == 256 || p.n == 512 || p.n == 1024);
     if (p.layout == SCH_LAYOUT_WARP && !warp_fits) return SCH_ERR_UNSUPPORTED;
-    // one warp per particle wherever it fits, with either noise model
-    const bool warp_ok = warp_fits && p.layout != SCH_LAYOUT_CTA;
+    // one warp per particle wherever it fits, with either noise model, unless another layout is asked for
+    const bool warp_ok = warp_fits && (p.layout == SCH_LAYOUT_AUTO || p.layout == SCH_LAYOUT_WARP);
     // several warps per particle: float fields, explicit advection, the mode expansion,
-    // n = 2048 or 4096
-    const bool group_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && !matern && (p.n == 2048 || p.n == 4096);
+    // n = 2048 or 4096; with 16 nodes a lane also n = 1024 (two warps per particle)
+    const bool group_n = p.n == 2048 || p.n == 4096 || (p.n == 1024 && p.layout == SCH_LAYOUT_GROUP16);
+    const bool group_fits = p.dtype == SCH_F32 && solver == SCH_SOLVER_EA && !matern && group_n;
     if ((p.layout == SCH_LAYOUT_GROUP || p.layout == SCH_LAYOUT_GROUP16) && !group_fits) return SCH_ERR_UNSUPPORTED;
     if (p.layout < SCH_LAYOUT_AUTO || p.layout > SCH_LAYOUT_GROUP16) return SCH_ERR_ARG;
     const bool group_ok = group_fits && p.layout != SCH_LAYOUT_CTA && p.layout != SCH_LAYOUT_WARP;

@@ -480,9 +480,15 @@ __host__ __device__ constexpr size_t gsmem_base() {
 // float2 slot each per warp, read once per Picard iteration; against two CTAs with
 // them in registers (233 registers) this ran the large-run filter 3% faster.
 constexpr int GMINB = 3;
+// n = 1024 in two warps of 16 nodes a lane (CS = 4, W = 2): seven 64-thread CTAs per SM (at most
+// 146 registers), so that a 1024-particle launch is one wave on 152 SMs
+template <int CS, int W>
+constexpr int gminb() {
+    return (CS == 4 && W == 2) ? 7 : GMINB;
+}
 
 template <int CS, int P, int W, int PD>
-__global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
+__global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gwindow_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
                                                                 WindowIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     GShared<W>* gs = reinterpret_cast<GShared<W>*>(smem_raw);
@@ -529,7 +535,7 @@ __global__ void __launch_bounds__(32 * W, GMINB) gwindow_kernel(ModelArgs<float>
 // proposals drawn by the whole CTA, the decision taken by thread 0 and shared.
 // PD: the Picard solve's lane-level system is diagonal (gwreduced_ldiag).
 template <int CS, int P, int W, int PD>
-__global__ void __launch_bounds__(32 * W, GMINB) gjitter_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
+__global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gjitter_kernel(ModelArgs<float> A, WArgs Wa, GArgs G,
                                                                 JitterIO<float> io) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // a device-gated stage reads its temperature, and does nothing when inactive

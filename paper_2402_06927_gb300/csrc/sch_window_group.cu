@@ -1,7 +1,7 @@
 // Instantiations of the warp-group window and jitter kernels for float fields:
 // W warps per particle, each lane holding 2 P = 4 sub-chunks of cs nodes
-// (n = 64 P cs W): (cs, W) = (8, 2) and (4, 4) for n = 2048, (8, 4) and (4, 8)
-// for n = 4096.
+// (n = 64 P cs W): (cs, W) = (4, 2) for n = 1024, (8, 2) and (4, 4) for n = 2048,
+// (8, 4) and (4, 8) for n = 4096.
 #include "sch_group.cuh"
 
 namespace sch {
@@ -56,6 +56,7 @@ int jitter(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G, const Jit
 int launch_gwindow(int cs, int W, const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
                    const WindowIO<float>& io, int N, cudaStream_t st) {
     if (A.n != 64 * GP * cs * W) return SCH_ERR_UNSUPPORTED;
+    if (cs == 4 && W == 2) return window<4, 2>(A, Wa, G, io, N, st);
     if (cs == 8 && W == 2) return window<8, 2>(A, Wa, G, io, N, st);
     if (cs == 4 && W == 4) return window<4, 4>(A, Wa, G, io, N, st);
     if (cs == 8 && W == 4) return window<8, 4>(A, Wa, G, io, N, st);
@@ -66,6 +67,7 @@ int launch_gwindow(int cs, int W, const ModelArgs<float>& A, const WArgs& Wa, co
 int launch_gjitter(int cs, int W, const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
                    const JitterIO<float>& io, int N, cudaStream_t st) {
     if (A.n != 64 * GP * cs * W) return SCH_ERR_UNSUPPORTED;
+    if (cs == 4 && W == 2) return jitter<4, 2>(A, Wa, G, io, N, st);
     if (cs == 8 && W == 2) return jitter<8, 2>(A, Wa, G, io, N, st);
     if (cs == 4 && W == 4) return jitter<4, 4>(A, Wa, G, io, N, st);
     if (cs == 8 && W == 4) return jitter<8, 4>(A, Wa, G, io, N, st);

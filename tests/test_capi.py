@@ -59,7 +59,7 @@ def _params(**kw):
                                    # kernel layouts: the warp-per-particle layout takes float fields, the
                                    # explicit-advection solver and n = 256, 512 or 1024 only; the warp-group
                                    # layouts float fields, explicit advection, the mode expansion and
-                                   # n = 2048 or 4096 only
+                                   # n = 2048 or 4096, and n = 1024 with 16 nodes a lane
                                    ({"layout": 5}, -1), ({"layout": 2}, -6), ({"layout": 1}, 0),
                                    ({"layout": 2, "dtype": 1}, 0), ({"layout": 2, "dtype": 1, "n": 1024, "M": 64}, 0),
                                    ({"layout": 2, "dtype": 1, "solver": 1}, -6),
@@ -68,6 +68,9 @@ def _params(**kw):
                                    ({"layout": 3, "dtype": 1, "n": 4096, "M": 128}, 0),
                                    ({"layout": 4, "dtype": 1, "n": 4096, "M": 128}, 0),
                                    ({"layout": 4, "dtype": 1, "n": 2048, "M": 64}, 0),
+                                   ({"layout": 4, "dtype": 1, "n": 1024, "M": 64}, 0),
+                                   ({"layout": 3, "dtype": 1, "n": 1024, "M": 64}, -6),
+                                   ({"layout": 4, "dtype": 1, "n": 512, "M": 64}, -6),
                                    ({"dtype": 1, "n": 2048, "M": 64}, 0), ({"dtype": 1, "n": 4096, "M": 128}, 0),
                                    ({"layout": 3, "dtype": 1, "n": 4096, "M": 128, "solver": 1}, -6),
                                    ({"layout": 3, "dtype": 1, "n": 4096, "M": 128, "noise": 1, "kappa": 1.0, "eta": 1.0,

@@ -98,6 +98,7 @@ def test_resample_degenerate_and_inplace():
                                                         ("cfg1_f64", 1.0, True, "auto", None),
                                                         ("cfg2_f32", 0.3, False, "warp", None),
                                                         ("cfg2_f32", 0.3, True, "cta", None),
+                                                        ("cfg2_f32", 0.3, True, "group16", None),
                                                         ("cfg2_f32", 0.3, False, "warp", 0.5)])
 def test_jitter_matches_oracle(name, theta, lam, layout, upto):
     # every move of every particle replayed by the oracle from the GPU's state: FP64 decisions

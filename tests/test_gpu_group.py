@@ -30,7 +30,8 @@ def _cfg(n, **over):
 
 @pytest.mark.parametrize("n,layout,Ns,lam,mu", [(4096, "group", 10, True, 0.02), (4096, "group16", 4, True, 0.02),
                                                 (2048, "group", 4, False, 0.02), (2048, "group16", 4, True, 0.02),
-                                                (4096, "group", 3, True, 2.0)])
+                                                (4096, "group", 3, True, 2.0), (1024, "group16", 10, True, 0.02),
+                                                (1024, "group16", 3, True, 2.0)])
 def test_group_window_matches_oracle(n, layout, Ns, lam, mu):
     cfg = _cfg(n, mu=mu)
     g = gpu_model(cfg, layout=layout)
@@ -52,6 +53,28 @@ def test_group_window_matches_oracle(n, layout, Ns, lam, mu):
     assert np.allclose(out["nll"].cpu().numpy(), nll, rtol=1e-3)
     if lam:
         assert np.allclose(out["logG"].cpu().numpy(), OF.girsanov_logG(la, dW, cfg.dt), rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n,layout,K", [(2048, "group", 2), (4096, "group", 64), (4096, "group16", 6),
+                                        (2048, "group16", 64), (1024, "group16", 8), (1024, "group16", 64)])
+def test_group_noise_extremes_match_oracle(n, layout, K):
+    # the lane-centred noise synthesis with one harmonic, an odd harmonic count and the largest
+    # K (32 harmonics, the whole table), in both warp-group layouts
+    cfg = _cfg(n, K=K)
+    g = gpu_model(cfg, layout=layout)
+    assert g.layout == layout
+    om = oracle_model(cfg)
+    N, Ns = 2, 3
+    m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 41)])
+    dW = random_increments(cfg, N, 42, steps=Ns)
+    la = random_drift(cfg, N, 43, steps=Ns)
+    ref = om.ensemble_window(m0, dW, la)
+    dt = g.dtype
+    out = g.ensemble_step(tdev(m0, dt), tdev(dW, dt), tdev(la, dt))
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    assert rel_err(out["m"].cpu().numpy(), ref[0]) < F32_TOL
+    assert rel_err(out["u"].cpu().numpy(), ref[1]) < F32_TOL
 
 
 def test_group_layouts_agree_with_cta_at_full_size():

@@ -112,7 +112,11 @@ def test_window_f64_multiwarp():
 
 @pytest.mark.parametrize("name,N,layout", [("cfg2_f32", 3, "warp"), ("cfg2_f32", 3, "cta"), ("cfg5_f32", 2, "auto"),
                                            ("cfg2_f32@n=256", 3, "warp"), ("cfg2_f32@n=512", 4, "warp"),
-                                           ("cfg2_f32@mu=2.0", 3, "warp"), ("cfg2_f32@mu=2.0", 2, "cta")])
+                                           ("cfg2_f32@mu=2.0", 3, "warp"), ("cfg2_f32@mu=2.0", 2, "cta"),
+                                           # the noise tables at their extremes: one harmonic, and 32
+                                           # (K = 64, the largest K), with an odd harmonic count too
+                                           ("cfg2_f32@K=2", 2, "warp"), ("cfg2_f32@K=64", 2, "warp"),
+                                           ("cfg2_f32@K=6", 2, "warp"), ("cfg2_f32@K=64", 2, "cta")])
 def test_window_f32(name, N, layout):
     # both kernel layouts against the oracle; the warp-per-particle kernels at
     # every sub-chunk length they are built for (n = 256, 512, 1024), and with a
