@@ -128,7 +128,7 @@ def jitter_kernel_name(g, cfg, solver):
     if g.layout == "warp":
         return ("wmatern_jitter_kernel<8,2,DIAG,PCR,PCR> (one warp per particle, EA)" if matern
                 else "wjitter_kernel<8,2,DIAG,PCR> (one warp per particle, EA)")
-    if g.layout == "group":
+    if g.layout in ("group", "group16"):
         return f"gjitter_kernel<{g.group_cs},2,{g.group_warps}> ({g.group_warps} warps per particle, EA)"
     return (f"matern_jitter_kernel<float,8,128,{solver.upper()}>" if matern
             else f"jitter_kernel<float,8,{cfg.n // 8},{solver.upper()}> (one CTA per particle)")
