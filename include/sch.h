@@ -168,7 +168,11 @@ int sch_m_from_u(sch_ctx* ctx, int N, const void* u, void* m, void* stream);
 
 /* Draw dW[p][s][k] = sqrt(dt) z, z ~ N(0,1) from Philox keyed
  * (seed, tag) and counter (k / 4, s, particle0 + p, ctr).  dW: real [N][nsteps][K].
- * The prior of the window increments: iid N(0, dt) (Sec. 3.1.2). */
+ * The prior of the window increments: iid N(0, dt) (Sec. 3.1.2).  The generator is
+ * Philox4x64-10 (Box-Muller on 53-bit uniforms), except for an FP32 context with the
+ * Matern noise, which draws from Philox4x32-10 (key (seed mod 2^32, (seed >> 32) mod
+ * 2^16 + 2^16 tag), counter words mod 2^32, Box-Muller on 32-bit uniforms); the PCN
+ * proposals of pf_jitter on such a context come from the same generator. */
 int sch_draw_increments(sch_ctx* ctx, int N, int nsteps, uint64_t seed, uint64_t tag,
                         uint64_t ctr, int particle0, void* dW, void* stream);
 
