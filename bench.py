@@ -45,6 +45,9 @@ E2E_CYCLES, E2E_RUNS = 100, 3   # the end-to-end measurement: runs of cycles thr
 # Per step: noise synthesis 2K, and for EA the right operator (M - mu dt/2 K) m0 5.
 FLOPS_PER_NODE_ITER = {"li": 44, "ea": 30}
 FLOPS_PER_NODE_STEP_EXTRA = {"li": 0, "ea": 5}
+# a warm-started step (the warp-group jitter with its workspace) first forms u = H^-1 M m of its
+# guess: the mass right-hand side (3 flops a node) and the Helmholtz solve (9)
+FLOPS_PER_NODE_WARM_START = 12
 
 
 # Matern noise synthesis per node and step (Eq. noise_solve2, k solves): staging 3
@@ -122,14 +125,15 @@ ORACLE_SOLVER_NOTE = ("; the oracle solves each step by linearly implicit Picard
                       "the GPU FP32 path by explicit-advection Picard to 1e-6")
 
 
-def jitter_kernel_name(g, cfg, solver):
+def jitter_kernel_name(g, cfg, solver, warm=False):
     """The dominant (PCN jitter) kernel instantiation the filter launches."""
     matern = cfg.noise == "matern"
     if g.layout == "warp":
         return ("wmatern_jitter_kernel<8,2,DIAG,PCR,PCR> (one warp per particle, EA)" if matern
                 else "wjitter_kernel<8,2,DIAG,PCR> (one warp per particle, EA)")
     if g.layout in ("group", "group16"):
-        return f"gjitter_kernel<{g.group_cs},2,{g.group_warps}> ({g.group_warps} warps per particle, EA)"
+        return (f"gjitter_kernel<{g.group_cs},2,{g.group_warps}> ({g.group_warps} warps per particle, EA"
+                + (", proposals warm-started from the previous one)" if warm else ")"))
     return (f"matern_jitter_kernel<float,8,128,{solver.upper()}>" if matern
             else f"jitter_kernel<float,8,{cfg.n // 8},{solver.upper()}> (one CTA per particle)")
 
@@ -379,7 +383,8 @@ def run_ours(args):
         m_truth = out["m"]
         truths.append(out["u"][0].clone())
         ys.append(g.synth_obs(out["u"][0].contiguous(), seed, c))
-    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
+    f = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages,
+                       warm_jitter=not args.cold_jitter)
     m0, _ = g.prior_sample(N, u_truth, seed, cfg.prior_scale)
     f.set_state(m0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -428,6 +433,12 @@ def run_ours(args):
     matern = cfg.noise == "matern"
     flops = step_flops(cfg.n, cfg.K, solver, it_sum, N * cfg.Ns * cfg.n_jitter * n_launch,
                        matern_flops_per_node(cfg.matern_k) if matern else None)
+    # warm starts: every proposal after the first of a launch (the bench's windows all finish
+    # cleanly) begins its steps with u = H^-1 M m of the guess
+    warm_steps = N * cfg.Ns * (cfg.n_jitter - 1) * n_launch if f.warm_jitter else 0
+    flops += cfg.n * FLOPS_PER_NODE_WARM_START * warm_steps
+    # the guess cache a launch writes and reads back (m of every step, proposals 0 .. n-2 and 1 .. n-1)
+    cache_bytes = 2 * N * cfg.Ns * (cfg.n_jitter - 1) * cfg.n * 4 if f.warm_jitter else 0
     jit_s = sum(jit_ms) / 1000.0
     # bytes a jitter launch must move: read m_start and dW, write dW, nll, logG and the
     # accepted end states (m_end, u_end); lower bound assumes the end states of each
@@ -454,7 +465,8 @@ def run_ours(args):
     c0 = args.warmup
     e2e_runs = []
     for _ in range(E2E_RUNS):
-        f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages)
+        f2 = EnsembleFilter(g, N, cfg.Ns, cfg.ess_min, cfg.rho, cfg.n_jitter, seed, eager_stages=args.eager_stages,
+                            warm_jitter=not args.cold_jitter)
         f2.set_state(m_warm)
         torch.cuda.synchronize()
         barrier(ws)
@@ -494,16 +506,19 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype, "data": "synthetic",
             "config": {**workload_config(cfg, ws), "layout": g.layout,
+                       "jitter_picard_start": ("the previous proposal's per-step states" if f.warm_jitter
+                                               else "each step's start state"),
                        "l2": "flushed between timed steps (256 MB write)",
                        "cycles_per_s": args.steps * ws / dev_s_max,
                        "mean_tempering_stages": statistics.mean(stages),
                        "mean_picard_iters_per_step": mean_iters, "picard_solver": solver,
                        "analysis_emre_rb_res_rmse": diag},
-            "roofline": {"bound": "alu", "kernel": jitter_kernel_name(g, cfg, solver),
+            "roofline": {"bound": "alu", "kernel": jitter_kernel_name(g, cfg, solver, f.warm_jitter),
                          "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": jitter_traffic(args.workload),
                          "algorithmic_bytes_per_launch": algo_bytes,
+                         "warm_start_cache_bytes_per_launch": cache_bytes,
                          "peak_note": f"FP32 FMA pipe {sm_count()} SMs x 128 lanes x 2 x max SM clock"},
             "gpu_launches": launches,
             "e2e": {"value": e2e_val, "unit": METRIC, "runs": e2e_runs, "cycles_per_run": e2e_steps,
@@ -1043,6 +1058,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cold-jitter", action="store_true",
+                    help="start every PCN proposal's Picard iterations from the steps' start states "
+                         "(no warm start from the previous proposal in the warp-group layout)")
     ap.add_argument("--eager-stages", type=int, default=2,
                     help="tempering stages enqueued at once as device-gated stages (0: stage by stage)")
     ap.add_argument("--nudging", action="store_true",

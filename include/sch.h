@@ -305,6 +305,23 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
               const void* y, double* nll, double* logG, void* m_end, void* u_end,
               int32_t* accepts, int32_t* iters, int32_t* status, void* stream);
 
+/* Optional jitter workspace, caller-owned device memory of at least
+ * sch_jitter_workspace_bytes(ctx, N, nsteps) bytes (16-byte aligned; the size is 0 where
+ * the layout does not use it: only SCH_LAYOUT_GROUP / GROUP16 does).  Once set, every
+ * pf_jitter, pf_jitter_dev and pf_gated_stages call on the context with at most N
+ * particles and nsteps steps and rho >= 0.99 starts the Picard iterations of each
+ * proposal after the first from the converged per-step states of the call's previous
+ * proposal (when that one finished cleanly: its m, kept in the workspace, and
+ * u = H^-1 M m), instead of from each step's start state.
+ * The fixed point and the stop test are unchanged, so results move only within the
+ * Picard tolerance; successive proposals at rho near one need about 40% fewer
+ * iterations.  The workspace serves one jitter call at a time: calls on several streams
+ * that share a context must not overlap.  ws NULL (or bytes 0) clears it; a workspace
+ * too small for a call is ignored by that call.  sch_set_jitter_workspace returns
+ * SCH_ERR_ARG for a misaligned ws. */
+size_t sch_jitter_workspace_bytes(const sch_ctx* ctx, int N, int nsteps);
+int sch_set_jitter_workspace(sch_ctx* ctx, void* ws, size_t bytes);
+
 /* pf_jitter for a device-gated stage: theta = tstate[2] and nothing is done when
  * tstate[4] == 0 (tstate: device pointer to the stage's out[5] of pf_temper_dev). */
 int pf_jitter_dev(sch_ctx* ctx, int N, int nsteps, int n_iter, const double* tstate, double rho,

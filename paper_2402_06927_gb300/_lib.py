@@ -78,6 +78,7 @@ SIGNATURES = {
     "pf_resample_static": [I, P, U64, U64, P, I, P, P, P],
     "pf_jitter": [P, I, I, I, D, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
     "pf_jitter_dev": [P, I, I, I, P, D, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
+    "sch_set_jitter_workspace": [P, P, SZ],
     "pf_mala_propose": [P, I, I, D, D, U64, U64, I, P, P, P, P, P],
     "pf_mala_accept": [P, I, I, D, D, U64, U64, I, P, P, P, P, P, P, P, P, P],
     "pf_gated_stages": [P, I, I, I, I, D, I, D, I, U64, U64, P, P, P, P, P, P, P, P, P, P, P, P],
@@ -91,6 +92,7 @@ SIGNATURES = {
 RESTYPES = {"pf_resample_workspace_bytes": (SZ, [I, SZ]),
             "sch_adjoint_workspace_bytes": (SZ, [P, I, I, I]),
             "pf_nudge_workspace_bytes": (SZ, [P, I, I, I]),
+            "sch_jitter_workspace_bytes": (SZ, [P, I, I]),
             "nn_param_count": (SZ, [P]),
             "nn_workspace_bytes": (SZ, [P, I])}
 

@@ -86,6 +86,30 @@ class SchModel:
         if getattr(self, "_h", None) is not None and self._h.value:
             lib().sch_destroy(self._h)
             self._h = ct.c_void_p()
+        self._jws = None
+
+    def jitter_workspace_bytes(self, N: int, nsteps: int) -> int:
+        """Bytes of the optional jitter workspace for N particles and nsteps steps (0 where the
+        layout does not use one)."""
+        return int(lib().sch_jitter_workspace_bytes(self._h, N, nsteps))
+
+    def ensure_jitter_workspace(self, N: int, nsteps: int) -> bool:
+        """Give the context a jitter workspace for up to N particles and nsteps steps (device
+        memory kept by this object): later jitter calls warm-start their proposals' Picard
+        iterations from the previous proposal of the call.  Returns whether the layout uses it."""
+        need = self.jitter_workspace_bytes(N, nsteps)
+        if need == 0:
+            return False
+        cur = getattr(self, "_jws", None)
+        if cur is None or cur.numel() < need:
+            self._jws = torch.empty(need, dtype=torch.uint8, device="cuda")
+            check(lib().sch_set_jitter_workspace(self._h, _ptr(self._jws), need), "sch_set_jitter_workspace")
+        return True
+
+    def clear_jitter_workspace(self) -> None:
+        """Every jitter proposal starts from the steps' start states again."""
+        check(lib().sch_set_jitter_workspace(self._h, None, 0), "sch_set_jitter_workspace")
+        self._jws = None
 
     def __del__(self):
         try:

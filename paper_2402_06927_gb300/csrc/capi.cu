@@ -20,6 +20,8 @@ struct sch_ctx {
     GArgs ga;
     ModelArgs<float> af;
     ModelArgs<double> ad;
+    void* jws;        // caller-owned jitter workspace (sch_set_jitter_workspace), or null
+    size_t jws_bytes;
 };
 
 namespace {
@@ -728,7 +730,10 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
         if (ctx->matern)
             return ctx->wcs ? launch_wjitter_matern(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream))
                             : launch_jitter_matern<float, 8>(ctx->af, io, N, S(stream));
-        if (ctx->gw) return launch_gjitter(ctx->wcs, ctx->gw, ctx->af, ctx->wa, ctx->ga, io, N, S(stream));
+        if (ctx->gw) {
+            if (ctx->jws && ctx->jws_bytes >= sch_jitter_workspace_bytes(ctx, N, nsteps)) io.guess = (float*)ctx->jws;
+            return launch_gjitter(ctx->wcs, ctx->gw, ctx->af, ctx->wa, ctx->ga, io, N, S(stream));
+        }
         if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
@@ -742,6 +747,19 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
 }
 
 }  // namespace
+
+size_t sch_jitter_workspace_bytes(const sch_ctx* ctx, int N, int nsteps) {
+    if (!ctx || N <= 0 || nsteps <= 0 || !ctx->gw) return 0;
+    return (size_t)N * nsteps * ctx->p.n * sizeof(float);
+}
+
+int sch_set_jitter_workspace(sch_ctx* ctx, void* ws, size_t bytes) {
+    if (!ctx) return SCH_ERR_ARG;
+    if (ws && (reinterpret_cast<uintptr_t>(ws) % 16 != 0)) return SCH_ERR_ARG;
+    ctx->jws = bytes ? ws : nullptr;
+    ctx->jws_bytes = ws ? bytes : 0;
+    return SCH_OK;
+}
 
 int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double rho, uint64_t seed,
               uint64_t ctr, const void* m_start, void* dW, const void* lambda, const void* y, double* nll,

@@ -298,6 +298,45 @@ __device__ __forceinline__ void gwu_from_m(const WArgs& Wa, const GArgs& G, cons
     wback<CS, P>(Wa.hel, x, F, E, u);
 }
 
+// A step's slot of the jitter's guess buffer: the converged m of the whole particle (n
+// floats) in the register order of its threads: thread t's pairs 2k and 2k + 1 (pair
+// e = p CS + i) form the float4 at index k TPB + t, TPB = 32 W threads, so that every
+// 16-byte access of a warp is contiguous.  u is not kept: the step recomputes it from the
+// guess (u = H^-1 M m, one Helmholtz solve), which costs less than moving it (a slot of
+// m alone for the CTAs resident at once stays in L2 between two proposals).
+template <int CS, int P, int W>
+__device__ __forceinline__ void gguess_store(float* slot, const float2 (&m)[P][CS]) {
+    constexpr int H = P * CS, TPB = 32 * W;
+    float4* m4 = reinterpret_cast<float4*>(slot);
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < H / 2; ++k) {
+        const int e0 = 2 * k, e1 = 2 * k + 1;
+        const float2 a = m[e0 / CS][e0 % CS], b = m[e1 / CS][e1 % CS];
+        m4[k * TPB + t] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// The guess of a step for this thread's nodes, and for the nodes just outside its warp (the
+// last node of the previous warp's lane 31, the first of the next warp's lane 0)
+template <int CS, int P, int W>
+__device__ __forceinline__ void gguess_load(const float* slot, float2 (&m)[P][CS], float& mL, float& mR) {
+    constexpr int H = P * CS, TPB = 32 * W;
+    static_assert(H % 2 == 0, "pairs loaded two at a time");
+    const float4* m4 = reinterpret_cast<const float4*>(slot);
+    const int t = threadIdx.x, w = t >> 5;
+#pragma unroll
+    for (int k = 0; k < H / 2; ++k) {
+        const int e0 = 2 * k, e1 = 2 * k + 1;
+        const float4 a = m4[k * TPB + t];
+        m[e0 / CS][e0 % CS] = make_float2(a.x, a.y);
+        m[e1 / CS][e1 % CS] = make_float2(a.z, a.w);
+    }
+    const int tl = (32 * w + TPB - 1) % TPB, tr = (32 * (w + 1)) % TPB;
+    mL = m4[(H / 2 - 1) * TPB + tl].w;
+    mR = m4[tr].x;
+}
+
 // The particle-wide state of a warp's nodes carried through a window: the fields and
 // the values of m and u at the two nodes outside the warp.
 template <int CS, int P>
@@ -312,7 +351,8 @@ struct GState {
 template <int CS, int P, int W, int PD>
 __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G,
                                             const GLane& gl, GState<CS, P>& X, float2* R0sm, float2 (&W0)[P][CS],
-                                            GShared<W>* gs, int w, int& ex, int& iters, int& flags) {
+                                            GShared<W>* gs, int w, int& ex, int& iters, int& flags,
+                                            const float* gin = nullptr, float* gout = nullptr) {
     const int lane = threadIdx.x & 31;
     // the increment at the nodes next to this warp's ends
     float nqL, nqR;
@@ -336,12 +376,23 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
                 Msm[(p * CS + i) * 32 + lane] = X.m[p][i];
             }
     }
+    // the Picard iterate starts from the step's start state, or from the guess: the converged
+    // m of this step in the call's previous proposal and its u = H^-1 M m (read before the
+    // step's first exchange after gends, so no warp has written this step's slot of the current
+    // proposal yet)
     float2 mi[P][CS];
+    float miL, miR;
+    if (gin) {
+        gguess_load<CS, P, W>(gin, mi, miL, miR);
+        gwu_from_m<CS, P, W>(Wa, G, gl, mi, miL, miR, X.u, X.uL, X.uR, gs, w, ex);
+    } else {
 #pragma unroll
-    for (int p = 0; p < P; ++p)
+        for (int p = 0; p < P; ++p)
 #pragma unroll
-        for (int i = 0; i < CS; ++i) mi[p][i] = X.m[p][i];
-    float miL = X.mL, miR = X.mR;
+            for (int i = 0; i < CS; ++i) mi[p][i] = X.m[p][i];
+        miL = X.mL;
+        miR = X.mR;
+    }
     const float2 dt8 = f2b(A.dt8);
     float dm_prev = INFINITY;
     for (int it = 1;; ++it) {
@@ -437,6 +488,7 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
         for (int i = 0; i < CS; ++i) X.m[p][i] = mi[p][i];
     X.mL = miL;
     X.mR = miR;
+    if (gout) gguess_store<CS, P, W>(gout, X.m);   // after the step's last exchange
 }
 
 // load a particle's window start: m from the row, its outside values, and u = H^{-1} M m
@@ -563,6 +615,12 @@ __global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gjitter_kernel(ModelAr
     const float sq = io.sq1mr2 * (float)sqrt(A.dt_d);
     const int nblk = (K + 3) >> 2;
     int iters = 0, flags = 0, n_acc = 0, changed = 0, ex = 0;
+    // Warm starts pay where successive proposals' trajectories nearly coincide (rho near one:
+    // at 0.9999 the proposal moves the noise by 1.4% of its spread, and a step then takes 2.2
+    // Picard iterations against 3.9 from the start state); for rho < 0.99 every proposal
+    // starts from the step's start state.
+    float* gbuf = (io.guess && io.rho >= 0.99f) ? io.guess : nullptr;
+    bool gvalid = false;
     __syncthreads();
     for (int j = 0; j < io.n_iter; ++j) {
         const uint64_t ctr = io.ctr + (uint64_t)j;
@@ -581,11 +639,18 @@ __global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gjitter_kernel(ModelAr
         GState<CS, P> X;
         gwstart<CS, P, W>(Wa, G, gl, io.m_start + (size_t)p * A.n, X, gs, w, ex);   // orders the staging
         int fl = 0;
+        // the guess slots of this particle: a proposal starts cold unless the previous one of
+        // this call finished cleanly (then it starts from that one's per-step states), and it
+        // leaves its own states for the next one (the last proposal leaves nothing)
+        float* gbase = gbuf ? gbuf + (size_t)p * Ns * A.n : nullptr;
         for (int s = 0; s < Ns; ++s) {
             float2 W0[P][CS];
             wnoise<CS, P>(A, Wa, noise + s * K, sc, cc, W0);
-            gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl);
+            float* slot = gbase ? gbase + (size_t)s * A.n : nullptr;
+            gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl, gvalid ? slot : nullptr,
+                                      j + 1 < io.n_iter ? slot : nullptr);
         }
+        gvalid = gbase && fl == 0;   // the same in every thread: the flags follow CTA-wide decisions
         double mis = wmisfit<CS, P>(A, X.u, io.y);
         double gsum = window_girsanov(A, prop, lam, Ns);
         gsum2<W>(gs, mis, gsum);

@@ -184,6 +184,10 @@ struct JitterIO {
     int32_t* accepts;
     int32_t* iters;
     int32_t* status;
+    // optional (warp-group kernels): per particle and step the converged m of the call's
+    // previous proposal, [N][Ns][n] in the kernel's register order; null: every proposal
+    // starts its Picard iterations from the step's start state
+    R* guess = nullptr;
 };
 
 template <typename R>

@@ -56,8 +56,12 @@ class EnsembleFilter:
 
     def __init__(self, model: SchModel, N: int, Ns: int, ess_min: float, rho: float, n_jitter: int,
                  seed: int, lam: Optional[torch.Tensor] = None, temper_mode: str = "largest",
-                 eager_stages: int = 2):
+                 eager_stages: int = 2, warm_jitter: bool = True):
         self.model, self.N, self.Ns = model, N, Ns
+        # warm_jitter: the model's jitter calls start each proposal after the first from the
+        # previous proposal's per-step states, where the layout supports it (a workspace the
+        # model keeps; the warp-group layout only)
+        self.warm_jitter = bool(warm_jitter) and model.ensure_jitter_workspace(N, Ns)
         self.temper_mode = temper_mode   # "largest" or "halving" (pf_temper / pf_temper_halving)
         self.eager_stages = eager_stages  # device-gated stages enqueued at once (0: stage by stage)
         self.ess_min, self.rho, self.n_jitter, self.seed = ess_min, rho, n_jitter, seed

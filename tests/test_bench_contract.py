@@ -19,6 +19,8 @@ def test_flop_counts():
     assert bench.step_flops(n, K, "li", 7, 2) == n * (44 * 7 + 2 * K * 2)
     assert bench.matern_flops_per_node(3) == 30 and bench.matern_flops_per_node(1) == 10
     assert bench.step_flops(n, K, "ea", 7, 2, bench.matern_flops_per_node(3)) == n * (30 * 7 + (30 + 5) * 2)
+    # a warm-started step's u = H^-1 M m: the mass right-hand side and one Helmholtz solve
+    assert bench.FLOPS_PER_NODE_WARM_START == 3 + 9
     # adjoint window: forward (LI) + 32 per adjoint iteration + (16 + 2K) per step, N Ns steps
     assert bench._adjoint_flops(n, K, 4, 5, 100, 90) == n * (44 * 100 + 2 * K * 20) + n * (32 * 90 + (16 + 2 * K) * 20)
 

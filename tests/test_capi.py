@@ -187,6 +187,25 @@ def test_adjoint_workspace_sizes(lib):
     assert lib.sch_destroy(h) == 0
 
 
+def test_jitter_workspace_size_and_checks(lib):
+    # the warm-start workspace: N Ns n floats for the warp-group layouts, none elsewhere;
+    # a misaligned pointer is refused, NULL clears it (no device memory is touched here)
+    from paper_2402_06927_gb300._lib import SCH_F32
+    for kw, per in [({"layout": 3, "dtype": SCH_F32, "n": 4096, "M": 128}, 4096),
+                    ({"layout": 4, "dtype": SCH_F32, "n": 1024, "M": 64}, 1024),
+                    ({"layout": 2, "dtype": SCH_F32, "n": 1024, "M": 64}, 0),
+                    ({"layout": 1}, 0)]:
+        p = _params(**kw)
+        h = ct.c_void_p()
+        assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0
+        assert lib.sch_jitter_workspace_bytes(h, 64, 10) == 64 * 10 * per * 4
+        assert lib.sch_jitter_workspace_bytes(h, 0, 10) == 0
+        assert lib.sch_set_jitter_workspace(h, ct.c_void_p(0x1000008), 1 << 20) == -1   # 8-byte aligned only
+        assert lib.sch_set_jitter_workspace(h, None, 0) == 0
+        assert lib.sch_destroy(h) == 0
+    assert lib.sch_set_jitter_workspace(None, None, 0) == -1
+
+
 def test_matern_layout_choice(lib):
     # SCH_LAYOUT_AUTO: one warp per particle for FP32 fields at n = 256, 512, 1024 with either
     # noise model, the CTA layout at other sizes and for FP64; SCH_LAYOUT_CTA always honoured

@@ -124,3 +124,44 @@ def test_group_nonfinite_and_nonconvergence_flags():
     g1 = gpu_model(dataclasses.replace(cfg, max_iter=1))
     out = g1.ensemble_step(tdev(np.nan_to_num(m0), g.dtype), tdev(dW, g.dtype))
     assert np.all(out["status"].cpu().numpy() & 1)
+
+
+def test_group_jitter_warm_start_matches_cold_start():
+    # the jitter workspace: every proposal after the first starts its Picard iterations from the
+    # previous proposal's converged per-step states (rho near one).  The proposals, and so the
+    # decisions and the stored noise, are those of the cold start; the windows move only within
+    # the Picard tolerance, with fewer iterations.  At rho < 0.99 the workspace is not used.
+    cfg = _cfg(4096)
+    g = gpu_model(cfg, layout="group")
+    om = oracle_model(cfg)
+    N = 64
+    dt = g.dtype
+    m0 = tdev(np.stack([om.m_from_u(u) for u in random_state(cfg, N, 61)]), dt)
+    dW0 = tdev(random_increments(cfg, N, 62), dt)
+    y = tdev(random_obs(cfg, 63), dt)
+
+    def run(warm, rho):
+        if warm:
+            assert g.ensure_jitter_workspace(N, cfg.Ns)
+        else:
+            g.clear_jitter_workspace()
+        d = dW0.clone()
+        st = g.ensemble_step(m0, d, None, y)
+        acc, it, status = g.jitter(m0, d, None, y, st["nll"], st["logG"], st["m"], st["u"], 0.5, rho, 5, 11, 100,
+                                   want_iters=True)
+        torch.cuda.synchronize()
+        assert np.all(status.cpu().numpy() == 0)
+        return acc.clone(), it.clone(), d, st
+
+    cold, warm = run(False, 0.9999), run(True, 0.9999)
+    assert torch.equal(cold[0], warm[0])
+    assert 0 < int(cold[0].sum()) < 5 * N
+    assert torch.equal(cold[2], warm[2])
+    assert rel_err(warm[3]["u"].cpu().numpy(), cold[3]["u"].double().cpu().numpy()) < F32_TOL
+    assert np.allclose(warm[3]["nll"].cpu().numpy(), cold[3]["nll"].cpu().numpy(), rtol=1e-4)
+    assert int(warm[1].sum()) < 0.8 * int(cold[1].sum())
+    cold2, warm2 = run(False, 0.5), run(True, 0.5)
+    g.clear_jitter_workspace()
+    for a, b in zip(cold2[:3], warm2[:3]):
+        assert torch.equal(a, b)
+    assert torch.equal(cold2[3]["u"], warm2[3]["u"]) and torch.equal(cold2[3]["nll"], warm2[3]["nll"])
