@@ -307,8 +307,7 @@ int pf_jitter(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, double 
 
 /* Optional jitter workspace, caller-owned device memory of at least
  * sch_jitter_workspace_bytes(ctx, N, nsteps) bytes (16-byte aligned; the size is 0 where
- * the layout does not use it: the warp-group and warp layouts with the mode expansion
- * use it, the CTA layout and the Matern noise do not).  Once set, every
+ * the layout does not use it: only SCH_LAYOUT_GROUP / GROUP16 does).  Once set, every
  * pf_jitter, pf_jitter_dev and pf_gated_stages call on the context with at most N
  * particles and nsteps steps and rho >= 0.99 starts the Picard iterations of each
  * proposal after the first from the converged per-step states of the call's previous

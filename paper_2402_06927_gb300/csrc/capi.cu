@@ -734,10 +734,7 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
             if (ctx->jws && ctx->jws_bytes >= sch_jitter_workspace_bytes(ctx, N, nsteps)) io.guess = (float*)ctx->jws;
             return launch_gjitter(ctx->wcs, ctx->gw, ctx->af, ctx->wa, ctx->ga, io, N, S(stream));
         }
-        if (ctx->wcs) {
-            if (ctx->jws && ctx->jws_bytes >= sch_jitter_workspace_bytes(ctx, N, nsteps)) io.guess = (float*)ctx->jws;
-            return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
-        }
+        if (ctx->wcs) return launch_wjitter(ctx->wcs, ctx->af, ctx->wa, io, N, S(stream));
         return ctx->af.solver == SCH_SOLVER_EA ? launch_jitter<float, 8, SCH_SOLVER_EA>(ctx->af, io, N, S(stream))
                                                : launch_jitter<float, 8, SCH_SOLVER_LI>(ctx->af, io, N, S(stream));
     }
@@ -752,8 +749,7 @@ int jitter_impl(sch_ctx* ctx, int N, int nsteps, int n_iter, double theta, const
 }  // namespace
 
 size_t sch_jitter_workspace_bytes(const sch_ctx* ctx, int N, int nsteps) {
-    // the warp-group and warp-per-particle jitter kernels of the mode expansion take it
-    if (!ctx || N <= 0 || nsteps <= 0 || !ctx->wcs || ctx->matern) return 0;
+    if (!ctx || N <= 0 || nsteps <= 0 || !ctx->gw) return 0;
     return (size_t)N * nsteps * ctx->p.n * sizeof(float);
 }
 

@@ -259,48 +259,14 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& W
         }
 }
 
-// A step's slot of the jitter's guess buffer (one warp per particle): the converged m of the
-// particle (n floats) in the register order of the lanes: lane l's pairs 2k and 2k + 1 (pair
-// e = p CS + i) form the float4 at index 32 k + l, so every 16-byte access of the warp is
-// contiguous.
-template <int CS, int P>
-__device__ __forceinline__ void wguess_store(float* slot, const float2 (&m)[P][CS]) {
-    constexpr int H = P * CS;
-    static_assert(H % 2 == 0, "pairs stored two at a time");
-    float4* m4 = reinterpret_cast<float4*>(slot);
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < H / 2; ++k) {
-        const int e0 = 2 * k, e1 = 2 * k + 1;
-        const float2 a = m[e0 / CS][e0 % CS], b = m[e1 / CS][e1 % CS];
-        m4[k * 32 + lane] = make_float4(a.x, a.y, b.x, b.y);
-    }
-}
-
-template <int CS, int P>
-__device__ __forceinline__ void wguess_load(const float* slot, float2 (&m)[P][CS]) {
-    constexpr int H = P * CS;
-    const float4* m4 = reinterpret_cast<const float4*>(slot);
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 0; k < H / 2; ++k) {
-        const int e0 = 2 * k, e1 = 2 * k + 1;
-        const float4 a = m4[k * 32 + lane];
-        m[e0 / CS][e0 % CS] = make_float2(a.x, a.y);
-        m[e1 / CS][e1 % CS] = make_float2(a.z, a.w);
-    }
-}
-
 // One implicit-midpoint step of this warp's particle: (m, u) in/out, W0 holding the
 // step's dU/4 at the lane's nodes on entry.
 // R0sm: this warp's [P][CS][32] float2 scratch for R0 = (M - mu dt/2 K) m0.
 // PM, HM: how the Picard and Helmholtz reduced systems are solved (RED_*).
-// gin, gout (optional): the step's guess slot to start the iteration from (the converged m of
-// the jitter's previous proposal, u = H^-1 M m formed from it) and to leave this step's m in.
 template <int CS, int P, int PM = RED_RUNTIME, int HM = RED_RUNTIME>
 __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
                                            float2 (&u)[P][CS], float2* R0sm, float2 (&W0)[P][CS], int& iters,
-                                           int& flags, const float* gin = nullptr, float* gout = nullptr) {
+                                           int& flags) {
     const int lane = threadIdx.x & 31;
     // W0 = dt/8 u0 + dU/4 (registers) and R0 (shared memory), fixed for the step
     {
@@ -318,15 +284,10 @@ __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArg
             }
     }
     float2 mi[P][CS];
-    if (gin) {
-        wguess_load<CS, P>(gin, mi);
-        wu_from_m<CS, P, HM>(W, mi, u);
-    } else {
 #pragma unroll
-        for (int p = 0; p < P; ++p)
+    for (int p = 0; p < P; ++p)
 #pragma unroll
-            for (int i = 0; i < CS; ++i) mi[p][i] = m[p][i];
-    }
+        for (int i = 0; i < CS; ++i) mi[p][i] = m[p][i];
     const float2 dt8 = f2b(A.dt8);
     float dm_prev = INFINITY;
     for (int it = 1;; ++it) {
@@ -407,17 +368,16 @@ __device__ __forceinline__ void wstep_core(const ModelArgs<float>& A, const WArg
     for (int p = 0; p < P; ++p)
 #pragma unroll
         for (int i = 0; i < CS; ++i) m[p][i] = mi[p][i];
-    if (gout) wguess_store<CS, P>(gout, m);
 }
 
 // One step with the mode-expansion noise of the step's K weights wq.
 template <int CS, int P, int PM, int HM>
 __device__ __forceinline__ void wstep(const ModelArgs<float>& A, const WArgs& W, float2 (&m)[P][CS],
                                       float2 (&u)[P][CS], float2* R0sm, const float* wq, float sc, float cc,
-                                      int& iters, int& flags, const float* gin = nullptr, float* gout = nullptr) {
+                                      int& iters, int& flags) {
     float2 W0[P][CS];
     wnoise<CS, P>(A, W, wq, sc, cc, W0);
-    wstep_core<CS, P, PM, HM>(A, W, m, u, R0sm, W0, iters, flags, gin, gout);
+    wstep_core<CS, P, PM, HM>(A, W, m, u, R0sm, W0, iters, flags);
 }
 
 // this thread's LN = 2 P CS nodes of a particle row <-> the paired registers:
@@ -557,10 +517,6 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
     const float sq = io.sq1mr2 * (float)sqrt(A.dt_d);
     const int nblk = (K + 3) >> 2;
     int iters = 0, flags = 0, n_acc = 0, changed = 0;
-    // warm starts from the previous proposal's per-step states where rho is near one (as the
-    // warp-group jitter kernel)
-    float* gbase = (io.guess && io.rho >= 0.99f) ? io.guess + (size_t)p * Ns * A.n : nullptr;
-    bool gvalid = false;
     __syncwarp();
     for (int j = 0; j < io.n_iter; ++j) {
         const uint64_t ctr = io.ctr + (uint64_t)j;
@@ -581,12 +537,7 @@ __global__ void __launch_bounds__(32, WMINB) wjitter_kernel(ModelArgs<float> A, 
         wu_from_m<CS, P, HM>(W, m, u);
         __syncwarp();
         int fl = 0;
-        for (int s = 0; s < Ns; ++s) {
-            float* slot = gbase ? gbase + (size_t)s * A.n : nullptr;
-            wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * K, sc, cc, iters, fl, gvalid ? slot : nullptr,
-                                 j + 1 < io.n_iter ? slot : nullptr);
-        }
-        gvalid = gbase && fl == 0;   // the flags follow warp-wide decisions
+        for (int s = 0; s < Ns; ++s) wstep<CS, P, PM, HM>(A, W, m, u, R0sm, noise + s * K, sc, cc, iters, fl);
         const double mis = warp_sum(wmisfit<CS, P>(A, u, io.y));
         const double gl = warp_sum(window_girsanov(A, prop, lam, Ns));
         const double nll1 = 0.5 * mis, lg1 = -gl;

@@ -60,7 +60,7 @@ class EnsembleFilter:
         self.model, self.N, self.Ns = model, N, Ns
         # warm_jitter: the model's jitter calls start each proposal after the first from the
         # previous proposal's per-step states, where the layout supports it (a workspace the
-        # model keeps; the warp-group and warp layouts of the mode expansion)
+        # model keeps; the warp-group layout only)
         self.warm_jitter = bool(warm_jitter) and model.ensure_jitter_workspace(N, Ns)
         self.temper_mode = temper_mode   # "largest" or "halving" (pf_temper / pf_temper_halving)
         self.eager_stages = eager_stages  # device-gated stages enqueued at once (0: stage by stage)

@@ -188,15 +188,12 @@ def test_adjoint_workspace_sizes(lib):
 
 
 def test_jitter_workspace_size_and_checks(lib):
-    # the warm-start workspace: N Ns n floats for the warp-group and warp layouts of the mode
-    # expansion, none for the CTA layout or the Matern noise;
+    # the warm-start workspace: N Ns n floats for the warp-group layouts, none elsewhere;
     # a misaligned pointer is refused, NULL clears it (no device memory is touched here)
     from paper_2402_06927_gb300._lib import SCH_F32
     for kw, per in [({"layout": 3, "dtype": SCH_F32, "n": 4096, "M": 128}, 4096),
                     ({"layout": 4, "dtype": SCH_F32, "n": 1024, "M": 64}, 1024),
-                    ({"layout": 2, "dtype": SCH_F32, "n": 1024, "M": 64}, 1024),
-                    ({"layout": 2, "dtype": SCH_F32, "n": 1024, "M": 64, "noise": 1, "kappa": 1.0, "eta": 1.0,
-                      "matern_k": 3}, 0),
+                    ({"layout": 2, "dtype": SCH_F32, "n": 1024, "M": 64}, 0),
                     ({"layout": 1}, 0)]:
         p = _params(**kw)
         h = ct.c_void_p()
