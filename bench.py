@@ -101,6 +101,9 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # the same kernel code with the n = 1024 two-warp instantiation in the shared sources:
     # 146.407424 MB read, 223.907072 MB written
     "6d734c792c38fc1efbfce31cd3ea97b59f2aea75": 370314496,
+    # proposals warm-started from the previous proposal's m (the guess cache written back to DRAM,
+    # its reads mostly from L2): 3.053932032 GB read, 12.257600512 GB written
+    "f8446f016778ac151f65880205d47b94f8188858": 15311532544,
 }}
 
 
