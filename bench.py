@@ -91,6 +91,8 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     "9a63bdc05dd81bd373a067cd982f7c3df6d28ae3": 4609792,
     # with the mode noise synthesised about each lane's centre: 4.606208 MB read, 0 written
     "89f00e16f90e5da10455045dc964eaeb5a808c25": 4606208,
+    # the same kernel code with the warm-start pointer in the jitter arguments: 4.606976 MB read
+    "a427e129ded961349af95ad6c01aef863a98e170": 4606976,
 }, "cfg5_f32": {
     # gjitter_kernel<8,2,4,1>, profiles/gjitter_kernel_cfg5_n4096_N8192.md: 148.514304 MB read,
     # 226.438400 MB written
