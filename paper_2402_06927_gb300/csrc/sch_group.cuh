@@ -354,6 +354,12 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
                                             GShared<W>* gs, int w, int& ex, int& iters, int& flags,
                                             const float* gin = nullptr, float* gout = nullptr) {
     const int lane = threadIdx.x & 31;
+    // the guess (if any) is read first, so that its latency passes in the barrier and the set-up
+    // below; no warp can have written this step's slot of the current proposal yet (each writes
+    // it at the end of its step, after the barriers that every warp reaches only after this read)
+    float2 mi[P][CS];
+    float miL = 0.f, miR = 0.f;
+    if (gin) gguess_load<CS, P, W>(gin, mi, miL, miR);
     // the increment at the nodes next to this warp's ends
     float nqL, nqR;
     gends<W>(W0[0][0].x, W0[P - 1][CS - 1].y, nqL, nqR, gs, w, ex);
@@ -377,13 +383,8 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
             }
     }
     // the Picard iterate starts from the step's start state, or from the guess: the converged
-    // m of this step in the call's previous proposal and its u = H^-1 M m (read before the
-    // step's first exchange after gends, so no warp has written this step's slot of the current
-    // proposal yet)
-    float2 mi[P][CS];
-    float miL, miR;
+    // m of this step in the call's previous proposal (read above) and its u = H^-1 M m
     if (gin) {
-        gguess_load<CS, P, W>(gin, mi, miL, miR);
         gwu_from_m<CS, P, W>(Wa, G, gl, mi, miL, miR, X.u, X.uL, X.uR, gs, w, ex);
     } else {
 #pragma unroll
