@@ -106,6 +106,8 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # proposals warm-started from the previous proposal's m (the guess cache written back to DRAM,
     # its reads mostly from L2): 3.053932032 GB read, 12.257600512 GB written
     "f8446f016778ac151f65880205d47b94f8188858": 15311532544,
+    # with the guess read before the step's first barrier: 2.879922944 GB read, 12.160525824 GB written
+    "8a9b29a4326730ba1429bc98e5937ed108b1c148": 15040448768,
 }}
 
 
