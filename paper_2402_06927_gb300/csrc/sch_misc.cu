@@ -215,6 +215,53 @@ __global__ void diag_particle_f32_kernel(ModelArgs<float> A, int N, const float*
     }
 }
 
+// The same for float fields of any n up to DIAG_SMEM_N: the truth and the mean staged in
+// shared memory as float (the block's threads load them once), then each warp as above.
+constexpr int DIAG_SMEM_N = 4096;   // 32 KB of shared memory, within the default limit
+__global__ void diag_particle_f32_smem_kernel(ModelArgs<float> A, int N, const float* u, const float* ua,
+                                              const double* ws, double* out) {
+    extern __shared__ float tm[];   // [n] truth, [n] mean
+    __shared__ double part[2][8];
+    const int n = A.n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        tm[i] = ua[i];
+        tm[n + i] = (float)ws[i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int W = gridDim.x * (blockDim.x >> 5);
+    double e = 0.0, f = 0.0;
+    for (int p = warp; p < N; p += W) {
+        const float* up = u + (size_t)p * n;
+        float se = 0.f, sf = 0.f;
+        for (int i = lane; i < n; i += 32) {
+            const float v = up[i];
+            const float d1 = v - tm[i], d2 = v - tm[n + i];
+            se = fmaf(d1, d1, se);
+            sf = fmaf(d2, d2, sf);
+        }
+        se = warp_sum(se);
+        sf = warp_sum(sf);
+        e += (double)sqrtf(se);
+        f += (double)sqrtf(sf);
+    }
+    if (lane == 0) {
+        part[0][wib] = e;
+        part[1][wib] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += part[0][w];
+            b += part[1][w];
+        }
+        atomicAdd(&out[6], a);
+        atomicAdd(&out[7], b);
+    }
+}
+
 __global__ void diag_zero_kernel(int n, double* ws, double* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 8) out[i] = 0.0;
@@ -238,7 +285,8 @@ int launch_synth_obs(const ModelArgs<R>& A, const R* u, uint64_t seed, uint64_t 
 }
 
 // per-particle norms: double fields one warp per particle in double; float fields in
-// float with the mean and truth in registers, for n up to 32 * 32 (else as double)
+// float with the mean and truth in registers for n up to 32 * 32, in shared memory up to
+// DIAG_SMEM_N (else as double)
 template <typename R>
 void launch_diag_particle(const ModelArgs<R>& A, int N, const R* u, const R* ua, const double* ws, double* out,
                           cudaStream_t st) {
@@ -253,6 +301,15 @@ void launch_diag_particle(const ModelArgs<R>& A, int N, const R* u, const R* ua,
             diag_particle_f32_kernel<32><<<blocks, 256, 0, st>>>(A, N, u, ua, ws, out);
             return;
         }
+        if (A.n <= DIAG_SMEM_N) {
+            // one pass over the ensemble at the memory's pace: a few warps a particle-row in flight
+            // on every SM, each block staging the truth and the mean once
+            int b2 = device_sms() * 4;
+            if (b2 > (N + 7) / 8) b2 = (N + 7) / 8;
+            if (b2 < 1) b2 = 1;
+            diag_particle_f32_smem_kernel<<<b2, 256, 2 * A.n * sizeof(float), st>>>(A, N, u, ua, ws, out);
+            return;
+        }
     }
     diag_particle_kernel<R><<<(N * 32 + 255) / 256, 256, 0, st>>>(A, N, u, ua, ws, out);
 }
@@ -261,7 +318,9 @@ template <typename R>
 int launch_diag(const ModelArgs<R>& A, int N, const R* u, const R* ua, double* ws, double* out, cudaStream_t st) {
     const int nb = (A.n + 255) / 256;
     diag_zero_kernel<<<nb, 256, 0, st>>>(A.n, ws, out);
-    diag_sum_kernel<R><<<dim3(nb, N < 64 ? N : 64), 256, 0, st>>>(A, N, u, ws);
+    // particles split over up to 512 groups: short chains of dependent adds per thread
+    const int groups = N < 512 ? N : 512;
+    diag_sum_kernel<R><<<dim3(nb, groups), 256, 0, st>>>(A, N, u, ws);
     diag_mean_kernel<R><<<nb, 256, 0, st>>>(A, N, ua, ws, out);
     launch_diag_particle<R>(A, N, u, ua, ws, out, st);
     diag_final_kernel<R><<<1, 32, 0, st>>>(A, N, out);
