@@ -154,6 +154,19 @@ int sch_layout(const sch_ctx* ctx);
  * a NULL context.  Host only. */
 int sch_noise_dim(const sch_ctx* ctx);
 
+/* How the warp and warp-group kernels synthesise the mode noise of Eq. sde1 at a
+ * lane's nodes (Sec. 2's K SALT modes; both forms sum the same trigonometric series
+ * about the lane's centre):
+ *   SCH_NOISE_FORM_TABLE  tabulated cos(j d), sin(j d) of the lane's node offsets d;
+ *   SCH_NOISE_FORM_POLY   per harmonic, polynomials in (d / d_max)^2 fitted on the host
+ *                         (Chebyshev interpolation, double precision), chosen when they
+ *                         reproduce cos(j d) and sin(j d) to 2^-30 at every offset and
+ *                         take the lane fewer operations than the tables;
+ *   SCH_NOISE_FORM_OTHER  neither (the CTA layout, the Matern noise).
+ * SCH_ERR_ARG for a NULL context.  Host only. */
+enum { SCH_NOISE_FORM_OTHER = 0, SCH_NOISE_FORM_TABLE = 1, SCH_NOISE_FORM_POLY = 2 };
+int sch_noise_form(const sch_ctx* ctx);
+
 /* Workspace bytes pf_resample needs to gather `row_bytes_total` bytes per
  * particle in place for N particles. */
 size_t pf_resample_workspace_bytes(int N, size_t row_bytes_total);

@@ -61,6 +61,7 @@ SIGNATURES = {
     "sch_destroy": [P],
     "sch_layout": [P],
     "sch_noise_dim": [P],
+    "sch_noise_form": [P],
     "sch_prior_exp1": [P, I, U64, I, P, P, P],
     "sch_u_from_m": [P, I, P, P, P],
     "sch_m_from_u": [P, I, P, P, P],

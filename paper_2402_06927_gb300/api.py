@@ -68,6 +68,10 @@ class SchModel:
         # functions, or one per cell for the Matern noise
         self.K = int(lib().sch_noise_dim(h))
         self.noise = noise
+        # how the warp and warp-group kernels sum the mode noise at a lane's nodes:
+        # "table" (tabulated cos/sin of the node offsets), "poly" (host-fitted polynomials
+        # of the offsets) or "other" (the CTA layout, the Matern noise)
+        self.noise_form = {0: "other", 1: "table", 2: "poly"}[lib().sch_noise_form(h)]
 
     @classmethod
     def from_config(cls, cfg, **over):

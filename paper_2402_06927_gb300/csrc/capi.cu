@@ -321,6 +321,56 @@ void wtab_cast(const HTab& s, const RTab<double>& q, int CS, WTab& d) {
     d.iB = (float)(1.0 / q.B);
 }
 
+bool invert_dense(int n, double* a, double* inv);
+
+// The polynomial form of the lane-centred noise (WArgs npc, npoly): for harmonic j <= K/2
+// and x = j d_{H-1}, the polynomials in s of degree WNP - 1 that interpolate cos(x sqrt s)
+// and sin(x sqrt s) / sqrt s at the WNP Chebyshev points of [0, 1].  npoly = 1 when they
+// reproduce cos(j d_m) and sin(j d_m) to 2^-30 at every offset d_m = tau_m d_{H-1}, m < H
+// (tau_m = (m + 1/2) / (H - 1/2)), and need fewer packed FMAs a lane than the tables:
+// K/2 WNP for the sums over j and H/2 (2 WNP - 1) for the evaluation, against K/2 H.
+static void fill_noise_poly(const sch_params& p, int H, WArgs& W) {
+    W.npoly = 0;
+    const int K2 = p.K / 2, Q = H / 2;
+    if (Q < 1 || Q > WNQ_MAX || K2 < 1 || K2 > SCH_MAX_K / 2) return;
+    if (K2 * WNP + Q * (2 * WNP - 1) >= K2 * 2 * Q) return;
+    const double dmax = 2.0 * M_PI * (H - 0.5) / p.n;
+    double V[WNP * WNP], Vi[WNP * WNP], sn[WNP];
+    for (int i = 0; i < WNP; ++i) {
+        sn[i] = 0.5 * (1.0 + cos(M_PI * (i + 0.5) / WNP));
+        for (int k = 0; k < WNP; ++k) V[i * WNP + k] = pow(sn[i], k);
+    }
+    if (!invert_dense(WNP, V, Vi)) return;
+    double err = 0.0;
+    for (int j = 1; j <= K2; ++j) {
+        const double x = j * dmax;
+        double fc[WNP], fs[WNP], cc[WNP], cs[WNP];
+        for (int i = 0; i < WNP; ++i) {
+            const double r = sqrt(sn[i]);
+            fc[i] = cos(x * r);
+            fs[i] = sin(x * r) / r;
+        }
+        for (int k = 0; k < WNP; ++k) {
+            cc[k] = cs[k] = 0.0;
+            for (int i = 0; i < WNP; ++i) {
+                cc[k] += Vi[k * WNP + i] * fc[i];
+                cs[k] += Vi[k * WNP + i] * fs[i];
+            }
+            W.npc[j - 1][k] = make_float2((float)cc[k], (float)cs[k]);
+        }
+        for (int m = 0; m < H; ++m) {
+            const double t = (m + 0.5) / (H - 0.5), s = t * t;
+            double ec = 0.0, es = 0.0;
+            for (int k = WNP - 1; k >= 0; --k) {
+                ec = ec * s + cc[k];
+                es = es * s + cs[k];
+            }
+            err = fmax(err, fmax(fabs(ec - cos(x * t)), fabs(t * es - sin(x * t))));
+        }
+    }
+    W.npoly = err <= ldexp(1.0, -30) ? 1 : 0;
+}
+
 void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
     memset(&W, 0, sizeof(W));
     const double h = p.L / p.n;
@@ -344,6 +394,7 @@ void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
             W.nco[j - 1][q] = make_float2((float)cos(j * dl), (float)cos(j * dr));
             W.nsi[j - 1][q] = make_float2((float)sin(j * dl), (float)sin(j * dr));
         }
+    fill_noise_poly(p, H, W);
     if (p.noise == SCH_NOISE_MATERN) {
         // the Matern operator scaled by 6/h like the Helmholtz one, and the weights likewise
         const double k2 = 1.0 / (p.kappa * p.kappa);
@@ -549,6 +600,12 @@ int sch_layout(const sch_ctx* ctx) {
 int sch_noise_dim(const sch_ctx* ctx) {
     if (!ctx) return SCH_ERR_ARG;
     return ctx->Q;
+}
+
+int sch_noise_form(const sch_ctx* ctx) {
+    if (!ctx) return SCH_ERR_ARG;
+    if (!ctx->wcs || ctx->matern) return SCH_NOISE_FORM_OTHER;
+    return ctx->wa.npoly ? SCH_NOISE_FORM_POLY : SCH_NOISE_FORM_TABLE;
 }
 
 size_t pf_resample_workspace_bytes(int N, size_t row_bytes_total) {

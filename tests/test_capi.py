@@ -5,6 +5,7 @@ import ctypes as ct
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -204,6 +205,53 @@ def test_jitter_workspace_size_and_checks(lib):
         assert lib.sch_set_jitter_workspace(h, None, 0) == 0
         assert lib.sch_destroy(h) == 0
     assert lib.sch_set_jitter_workspace(None, None, 0) == -1
+
+
+def _noise_poly_expected(n, H, K2, WNP=4):
+    # the rule the host applies, re-derived with numpy: per harmonic j, Chebyshev interpolants
+    # in s = tau^2 of cos(x sqrt s) and sin(x sqrt s) / sqrt s (x = j d_max) must reproduce
+    # cos(j d) and sin(j d) at the lane's H offsets to 2^-30, and cost fewer packed FMAs
+    Q = H // 2
+    if K2 * WNP + Q * (2 * WNP - 1) >= K2 * 2 * Q:
+        return False
+    dmax = 2 * np.pi * (H - 0.5) / n
+    sn = 0.5 * (1 + np.cos(np.pi * (np.arange(WNP) + 0.5) / WNP))
+    t = (np.arange(H) + 0.5) / (H - 0.5)
+    err = 0.0
+    for j in range(1, K2 + 1):
+        x = j * dmax
+        cc = np.polynomial.polynomial.polyfit(sn, np.cos(x * np.sqrt(sn)), WNP - 1)
+        cs = np.polynomial.polynomial.polyfit(sn, np.sin(x * np.sqrt(sn)) / np.sqrt(sn), WNP - 1)
+        ec = np.polynomial.polynomial.polyval(t * t, cc)
+        es = t * np.polynomial.polynomial.polyval(t * t, cs)
+        err = max(err, np.abs(ec - np.cos(x * t)).max(), np.abs(es - np.sin(x * t)).max())
+    return err <= 2.0 ** -30
+
+
+def test_noise_form_choice(lib):
+    # the lane-centred noise sums: polynomial fits where they are accurate to 2^-30 and cheaper,
+    # the tables elsewhere, neither for the CTA layout or the Matern noise
+    from paper_2402_06927_gb300._lib import SCH_F32
+    cases = [(4096, 32, 3, 16, 2), (4096, 64, 3, 16, 1), (4096, 48, 3, 16, 1), (2048, 32, 3, 16, 1),
+             (2048, 32, 4, 8, 2), (1024, 32, 4, 8, 1), (1024, 8, 2, 16, 1), (1024, 32, 2, 16, 1),
+             (4096, 4, 3, 16, 1), (256, 4, 2, 4, 1)]
+    for n, K, layout, H, want in cases:
+        assert (want == 2) == _noise_poly_expected(n, H, K // 2), (n, K, layout)
+        p = _params(n=n, M=64, K=K, dtype=SCH_F32, layout=layout, tol=1e-6)
+        for j in range(K // 2):
+            p.amps[j] = 0.05
+        h = ct.c_void_p()
+        assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0, (n, K, layout)
+        assert lib.sch_noise_form(h) == want, (n, K, layout)
+        assert lib.sch_destroy(h) == 0
+    for kw in [{"layout": 1}, {"noise": 1, "kappa": 1.0, "eta": 0.2, "matern_k": 3, "n": 1024, "M": 64,
+                                "dtype": SCH_F32, "layout": 2}]:
+        p = _params(**kw)
+        h = ct.c_void_p()
+        assert lib.sch_create(ct.byref(p), ct.byref(h)) == 0
+        assert lib.sch_noise_form(h) == 0
+        assert lib.sch_destroy(h) == 0
+    assert lib.sch_noise_form(None) == -1
 
 
 def test_matern_layout_choice(lib):
