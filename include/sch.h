@@ -159,9 +159,10 @@ int sch_noise_dim(const sch_ctx* ctx);
  * about the lane's centre):
  *   SCH_NOISE_FORM_TABLE  tabulated cos(j d), sin(j d) of the lane's node offsets d;
  *   SCH_NOISE_FORM_POLY   per harmonic, polynomials in (d / d_max)^2 fitted on the host
- *                         (Chebyshev interpolation, double precision), chosen when they
- *                         reproduce cos(j d) and sin(j d) to 2^-30 at every offset and
- *                         take the lane fewer operations than the tables;
+ *                         (Chebyshev interpolation, double precision), chosen in the
+ *                         warp-group layouts when they reproduce cos(j d) and sin(j d) to
+ *                         2^-30 at every offset and take the lane fewer operations than
+ *                         the tables;
  *   SCH_NOISE_FORM_OTHER  neither (the CTA layout, the Matern noise).
  * SCH_ERR_ARG for a NULL context.  Host only. */
 enum { SCH_NOISE_FORM_OTHER = 0, SCH_NOISE_FORM_TABLE = 1, SCH_NOISE_FORM_POLY = 2 };

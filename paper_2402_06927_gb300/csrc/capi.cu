@@ -329,6 +329,9 @@ bool invert_dense(int n, double* a, double* inv);
 // reproduce cos(j d_m) and sin(j d_m) to 2^-30 at every offset d_m = tau_m d_{H-1}, m < H
 // (tau_m = (m + 1/2) / (H - 1/2)), and need fewer packed FMAs a lane than the tables:
 // K/2 WNP for the sums over j and H/2 (2 WNP - 1) for the evaluation, against K/2 H.
+// Only the warp-group kernels compile the polynomial form: in the one-warp layout
+// (d_{H-1} near 2 pi / 64) it would qualify for K = 10 at n = 1024 alone, and save 4 of
+// 80 packed FMAs there.
 static void fill_noise_poly(const sch_params& p, int H, WArgs& W) {
     W.npoly = 0;
     const int K2 = p.K / 2, Q = H / 2;
@@ -394,7 +397,6 @@ void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
             W.nco[j - 1][q] = make_float2((float)cos(j * dl), (float)cos(j * dr));
             W.nsi[j - 1][q] = make_float2((float)sin(j * dl), (float)sin(j * dr));
         }
-    fill_noise_poly(p, H, W);
     if (p.noise == SCH_NOISE_MATERN) {
         // the Matern operator scaled by 6/h like the Helmholtz one, and the weights likewise
         const double k2 = 1.0 / (p.kappa * p.kappa);
@@ -577,6 +579,7 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
         c->wcs = lane_nodes / 4;
         c->gw = p.n / (32 * lane_nodes);
         fill_wargs(p, c->wcs, 128, c->wa);
+        fill_noise_poly(p, 2 * c->wcs, c->wa);   // H = 2 wcs nodes a lane half
         if (!fill_gargs(p, c->wcs, c->gw, c->ga)) {
             free(c);
             return SCH_ERR_UNSUPPORTED;

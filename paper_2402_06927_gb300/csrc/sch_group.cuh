@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gwindow_kernel(ModelAr
     int iters = 0, flags = 0;
     for (int s = 0; s < io.Ns; ++s) {
         float2 W0[P][CS];
-        wnoise<CS, P>(A, Wa, noise + s * A.K, sc, cc, W0);
+        wnoise<CS, P, true>(A, Wa, noise + s * A.K, sc, cc, W0);
         gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, flags);
     }
     wstore<CS, P>(io.m_out + (size_t)p * A.n, X.m);
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gjitter_kernel(ModelAr
         float* gbase = gbuf ? gbuf + (size_t)p * Ns * A.n : nullptr;
         for (int s = 0; s < Ns; ++s) {
             float2 W0[P][CS];
-            wnoise<CS, P>(A, Wa, noise + s * K, sc, cc, W0);
+            wnoise<CS, P, true>(A, Wa, noise + s * K, sc, cc, W0);
             float* slot = gbase ? gbase + (size_t)s * A.n : nullptr;
             gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl, gvalid ? slot : nullptr,
                                       j + 1 < io.n_iter ? slot : nullptr);

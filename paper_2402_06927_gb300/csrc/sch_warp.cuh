@@ -219,16 +219,17 @@ __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][C
 // Where the host fitted cos(j d) and sin(j d) / tau by polynomials in s = tau^2 (WArgs npc,
 // npoly; tau = d / d_{H-1}), the lane instead accumulates the WNP coefficient pairs
 //   (e_k, o_k) = sum_j (v_j c_jk, q_j s_jk),   E(d) = sum_k e_k s^k,  O(d) = tau sum_k o_k s^k,
-// and evaluates both at its H offsets by Horner's rule.
+// and evaluates both at its H offsets by Horner's rule.  POLY: the polynomial form is
+// compiled in (the warp-group kernels; the host fits it for no one-warp layout).
 // EP[q] = (E(d_{H-1-q}), E(d_q)), OP likewise, q < H/2.  sc, cc: sin and cos of theta_c.
-template <int CS, int P>
+template <int CS, int P, bool POLY = false>
 __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& Wa, const float* wq, float sc,
                                        float cc, float2 (&nq)[P][CS]) {
     constexpr int H = P * CS, Q = H / 2;
     static_assert(H % 2 == 0 && Q <= WNQ_MAX, "a lane half of an even number of nodes within the tables");
     float2 EP[Q], OP[Q];
     float sj = sc, cj = cc;
-    if (Wa.npoly) {
+    if (POLY && Wa.npoly) {
         float2 eo[WNP];
 #pragma unroll
         for (int k = 0; k < WNP; ++k) eo[k] = f2b(0.f);
