@@ -332,8 +332,8 @@ bool invert_dense(int n, double* a, double* inv);
 // Only the warp-group kernels compile the polynomial form: in the one-warp layout
 // (d_{H-1} near 2 pi / 64) it would qualify for K = 10 at n = 1024 alone, and save 4 of
 // 80 packed FMAs there.
-static void fill_noise_poly(const sch_params& p, int H, WArgs& W) {
-    W.npoly = 0;
+static void fill_noise_poly(const sch_params& p, int H, GArgs& G) {
+    G.npoly = 0;
     const int K2 = p.K / 2, Q = H / 2;
     if (Q < 1 || Q > WNQ_MAX || K2 < 1 || K2 > SCH_MAX_K / 2) return;
     if (K2 * WNP + Q * (2 * WNP - 1) >= K2 * 2 * Q) return;
@@ -359,7 +359,7 @@ static void fill_noise_poly(const sch_params& p, int H, WArgs& W) {
                 cc[k] += Vi[k * WNP + i] * fc[i];
                 cs[k] += Vi[k * WNP + i] * fs[i];
             }
-            W.npc[j - 1][k] = make_float2((float)cc[k], (float)cs[k]);
+            G.npc[j - 1][k] = make_float2((float)cc[k], (float)cs[k]);
         }
         for (int m = 0; m < H; ++m) {
             const double t = (m + 0.5) / (H - 0.5), s = t * t;
@@ -371,7 +371,7 @@ static void fill_noise_poly(const sch_params& p, int H, WArgs& W) {
             err = fmax(err, fmax(fabs(ec - cos(x * t)), fabs(t * es - sin(x * t))));
         }
     }
-    W.npoly = err <= ldexp(1.0, -30) ? 1 : 0;
+    G.npoly = err <= ldexp(1.0, -30) ? 1 : 0;
 }
 
 void fill_wargs(const sch_params& p, int CS, int rows, WArgs& W) {
@@ -579,11 +579,11 @@ int sch_create(const sch_params* params, sch_ctx** ctx) {
         c->wcs = lane_nodes / 4;
         c->gw = p.n / (32 * lane_nodes);
         fill_wargs(p, c->wcs, 128, c->wa);
-        fill_noise_poly(p, 2 * c->wcs, c->wa);   // H = 2 wcs nodes a lane half
         if (!fill_gargs(p, c->wcs, c->gw, c->ga)) {
             free(c);
             return SCH_ERR_UNSUPPORTED;
         }
+        fill_noise_poly(p, 2 * c->wcs, c->ga);   // H = 2 wcs nodes a lane half
     }
     *ctx = c;
     return SCH_OK;
@@ -608,7 +608,7 @@ int sch_noise_dim(const sch_ctx* ctx) {
 int sch_noise_form(const sch_ctx* ctx) {
     if (!ctx) return SCH_ERR_ARG;
     if (!ctx->wcs || ctx->matern) return SCH_NOISE_FORM_OTHER;
-    return ctx->wa.npoly ? SCH_NOISE_FORM_POLY : SCH_NOISE_FORM_TABLE;
+    return (ctx->gw && ctx->ga.npoly) ? SCH_NOISE_FORM_POLY : SCH_NOISE_FORM_TABLE;
 }
 
 size_t pf_resample_workspace_bytes(int N, size_t row_bytes_total) {

@@ -492,6 +492,55 @@ __device__ __forceinline__ void gwstep_core(const ModelArgs<float>& A, const WAr
     if (gout) gguess_store<CS, P, W>(gout, X.m);   // after the step's last exchange
 }
 
+// The step's SALT increment dU/4 at the lane's nodes, as wnoise (sch_warp.cuh) sums its
+// even and odd parts E(d) = sum_j v_j cos(j d) and O(d) = sum_j q_j sin(j d) about the
+// lane's centre.  Where the host fitted cos(j d) and sin(j d) / tau by polynomials in
+// s = tau^2 (GArgs npc, npoly; tau = d / d_{H-1}), the lane instead accumulates the WNP
+// coefficient pairs
+//   (e_k, o_k) = sum_j (v_j c_jk, q_j s_jk),   E(d) = sum_k e_k s^k,  O(d) = tau sum_k o_k s^k,
+// one packed FMA each a harmonic, and evaluates both at its H offsets by Horner's rule
+// (tau and s are compile-time constants of the layout).
+template <int CS, int P>
+__device__ __forceinline__ void gnoise(const ModelArgs<float>& A, const WArgs& Wa, const GArgs& G, const float* wq,
+                                       float sc, float cc, float2 (&nq)[P][CS]) {
+    constexpr int H = P * CS, Q = H / 2;
+    float2 EP[Q], OP[Q];
+    if (G.npoly) {
+        float2 eo[WNP];
+#pragma unroll
+        for (int k = 0; k < WNP; ++k) eo[k] = f2b(0.f);
+        float sj = sc, cj = cc;
+#pragma unroll 4
+        for (int j = 0; j < A.K2; ++j) {
+            const float2 ab = *reinterpret_cast<const float2*>(wq + 2 * j);
+            const float2 vq = make_float2(fmaf(ab.x, sj, ab.y * cj), fmaf(ab.x, cj, -(ab.y * sj)));
+#pragma unroll
+            for (int k = 0; k < WNP; ++k) eo[k] = f2fma(vq, G.npc[j][k], eo[k]);
+            const float sn = fmaf(sj, cc, cj * sc);
+            cj = fmaf(cj, cc, -(sj * sc));
+            sj = sn;
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            // tau of the offsets d_{H-1-q} and d_q, and their squares
+            const float ta = (float)(2 * (H - 1 - q) + 1) / (float)(2 * H - 1);
+            const float tb = (float)(2 * q + 1) / (float)(2 * H - 1);
+            const float2 tq = make_float2(ta, tb), s2 = make_float2(ta * ta, tb * tb);
+            float2 e = f2b(eo[WNP - 1].x), o = f2b(eo[WNP - 1].y);
+#pragma unroll
+            for (int k = WNP - 2; k >= 0; --k) {
+                e = f2fma(e, s2, f2b(eo[k].x));
+                o = f2fma(o, s2, f2b(eo[k].y));
+            }
+            EP[q] = e;
+            OP[q] = f2mul(o, tq);
+        }
+    } else {
+        wnoise_tab<CS, P>(A, Wa, wq, sc, cc, EP, OP);
+    }
+    wnoise_finish<CS, P>(EP, OP, nq);
+}
+
 // load a particle's window start: m from the row, its outside values, and u = H^{-1} M m
 template <int CS, int P, int W>
 __device__ __forceinline__ void gwstart(const WArgs& Wa, const GArgs& G, const GLane& gl, const float* row,
@@ -564,7 +613,7 @@ __global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gwindow_kernel(ModelAr
     int iters = 0, flags = 0;
     for (int s = 0; s < io.Ns; ++s) {
         float2 W0[P][CS];
-        wnoise<CS, P, true>(A, Wa, noise + s * A.K, sc, cc, W0);
+        gnoise<CS, P>(A, Wa, G, noise + s * A.K, sc, cc, W0);
         gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, flags);
     }
     wstore<CS, P>(io.m_out + (size_t)p * A.n, X.m);
@@ -646,7 +695,7 @@ __global__ void __launch_bounds__(32 * W, gminb<CS, W>()) gjitter_kernel(ModelAr
         float* gbase = gbuf ? gbuf + (size_t)p * Ns * A.n : nullptr;
         for (int s = 0; s < Ns; ++s) {
             float2 W0[P][CS];
-            wnoise<CS, P, true>(A, Wa, noise + s * K, sc, cc, W0);
+            gnoise<CS, P>(A, Wa, G, noise + s * K, sc, cc, W0);
             float* slot = gbase ? gbase + (size_t)s * A.n : nullptr;
             gwstep_core<CS, P, W, PD>(A, Wa, G, gl, X, R0sm, W0, gs, w, ex, iters, fl, gvalid ? slot : nullptr,
                                       j + 1 < io.n_iter ? slot : nullptr);

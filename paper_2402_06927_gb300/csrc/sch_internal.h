@@ -112,7 +112,7 @@ struct WTab {
 // 2H nodes lie at the offsets -d_{H-1} .. -d_0, d_0 .. d_{H-1} from its centre, d_m =
 // (m + 1/2) 2 pi / n, with H = P CS <= 2 WNQ_MAX.  With tau = d / d_{H-1} in (0, 1]
 // and s = tau^2, harmonic j's cos(j d) and sin(j d) / tau are smooth functions of s on
-// [0, 1]; where j d_{H-1} is small for every j <= K/2 the host fits each with a
+// [0, 1]; where j d_{H-1} is small for every j <= K/2 the host fits each (GArgs npc) with a
 // polynomial of WNP coefficients in s (Chebyshev interpolation), and a lane then
 // forms the WNP sums over j once and evaluates them at its H offsets.
 constexpr int WNQ_MAX = 8;
@@ -127,11 +127,6 @@ struct WArgs {
     // for harmonic j = 1..K/2 and q < H/2: nco[j-1][q] = (cos j d_{H-1-q}, cos j d_q) and
     // nsi[j-1][q] = (sin j d_{H-1-q}, sin j d_q)
     float2 nco[SCH_MAX_K / 2][WNQ_MAX], nsi[SCH_MAX_K / 2][WNQ_MAX];
-    // npc[j-1][k] = (c_k, s_k): cos(j d) ~ sum_k c_k s^k and sin(j d) ~ tau sum_k s_k s^k,
-    // k < WNP.  npoly = 1 when those fits hold to 2^-30 at every offset and cost the lane
-    // fewer operations than the tables; otherwise the tables above are used
-    float2 npc[SCH_MAX_K / 2][WNP];
-    int npoly;
 };
 
 // Cross-warp reduced solve of a constant table for the warp-group kernels
@@ -159,6 +154,12 @@ struct GTab {
 
 struct GArgs {
     GTab pic, hel;          // the cross-warp solves of M + mu dt/2 K and (6/h)(M + alpha^2 K)
+    // the polynomial form of the lane-centred noise (wnoise_poly in sch_group.cuh):
+    // npc[j-1][k] = (c_k, s_k) with cos(j d) ~ sum_k c_k s^k and sin(j d) ~ tau sum_k s_k s^k,
+    // k < WNP.  npoly = 1 when those fits hold to 2^-30 at every offset and cost the lane
+    // fewer operations than the tables of WArgs; otherwise the tables are used
+    float2 npc[SCH_MAX_K / 2][WNP];
+    int npoly;
 };
 
 template <typename R>

@@ -216,71 +216,43 @@ __device__ __forceinline__ void wu_from_m(const WArgs& W, const float2 (&m)[P][C
 //         - wq_{2j-1} sin(j theta_c),
 // so a harmonic costs the lane two FMAs for each pair of mirrored nodes (tabulated
 // cos(j d), sin(j d): WArgs nco, nsi) plus the rotation of (sin, cos)(j theta_c) to j + 1.
-// Where the host fitted cos(j d) and sin(j d) / tau by polynomials in s = tau^2 (WArgs npc,
-// npoly; tau = d / d_{H-1}), the lane instead accumulates the WNP coefficient pairs
-//   (e_k, o_k) = sum_j (v_j c_jk, q_j s_jk),   E(d) = sum_k e_k s^k,  O(d) = tau sum_k o_k s^k,
-// and evaluates both at its H offsets by Horner's rule.  POLY: the polynomial form is
-// compiled in (the warp-group kernels; the host fits it for no one-warp layout).
+// (The warp-group kernels can instead sum the harmonics through polynomials of the
+// offsets: gnoise in sch_group.cuh.)
 // EP[q] = (E(d_{H-1-q}), E(d_q)), OP likewise, q < H/2.  sc, cc: sin and cos of theta_c.
-template <int CS, int P, bool POLY = false>
-__device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& Wa, const float* wq, float sc,
-                                       float cc, float2 (&nq)[P][CS]) {
+template <int CS, int P>
+__device__ __forceinline__ void wnoise_tab(const ModelArgs<float>& A, const WArgs& Wa, const float* wq, float sc,
+                                           float cc, float2 (&EP)[P * CS / 2], float2 (&OP)[P * CS / 2]) {
     constexpr int H = P * CS, Q = H / 2;
     static_assert(H % 2 == 0 && Q <= WNQ_MAX, "a lane half of an even number of nodes within the tables");
-    float2 EP[Q], OP[Q];
-    float sj = sc, cj = cc;
-    if (POLY && Wa.npoly) {
-        float2 eo[WNP];
 #pragma unroll
-        for (int k = 0; k < WNP; ++k) eo[k] = f2b(0.f);
-#pragma unroll 4
-        for (int j = 0; j < A.K2; ++j) {
-            const float2 ab = *reinterpret_cast<const float2*>(wq + 2 * j);
-            const float2 vq = make_float2(fmaf(ab.x, sj, ab.y * cj), fmaf(ab.x, cj, -(ab.y * sj)));
-#pragma unroll
-            for (int k = 0; k < WNP; ++k) eo[k] = f2fma(vq, Wa.npc[j][k], eo[k]);
-            const float sn = fmaf(sj, cc, cj * sc);
-            cj = fmaf(cj, cc, -(sj * sc));
-            sj = sn;
-        }
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            // tau of the offsets d_{H-1-q} and d_q, and their squares
-            const float ta = (float)(2 * (H - 1 - q) + 1) / (float)(2 * H - 1);
-            const float tb = (float)(2 * q + 1) / (float)(2 * H - 1);
-            const float2 tq = make_float2(ta, tb), s2 = make_float2(ta * ta, tb * tb);
-            float2 e = f2b(eo[WNP - 1].x), o = f2b(eo[WNP - 1].y);
-#pragma unroll
-            for (int k = WNP - 2; k >= 0; --k) {
-                e = f2fma(e, s2, f2b(eo[k].x));
-                o = f2fma(o, s2, f2b(eo[k].y));
-            }
-            EP[q] = e;
-            OP[q] = f2mul(o, tq);
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            EP[q] = f2b(0.f);
-            OP[q] = f2b(0.f);
-        }
-#pragma unroll 2
-        for (int j = 0; j < A.K2; ++j) {
-            const float2 ab = *reinterpret_cast<const float2*>(wq + 2 * j);
-            const float2 v = f2b(fmaf(ab.x, sj, ab.y * cj));
-            const float2 qv = f2b(fmaf(ab.x, cj, -(ab.y * sj)));
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                EP[q] = f2fma(v, Wa.nco[j][q], EP[q]);
-                OP[q] = f2fma(qv, Wa.nsi[j][q], OP[q]);
-            }
-            const float sn = fmaf(sj, cc, cj * sc);
-            cj = fmaf(cj, cc, -(sj * sc));
-            sj = sn;
-        }
+    for (int q = 0; q < Q; ++q) {
+        EP[q] = f2b(0.f);
+        OP[q] = f2b(0.f);
     }
-    // pair (p, i), k = p CS + i: node k of the lane's first half is theta_c - d_{H-1-k},
-    // node H + k of its second half theta_c + d_k
+    float sj = sc, cj = cc;
+#pragma unroll 2
+    for (int j = 0; j < A.K2; ++j) {
+        const float2 ab = *reinterpret_cast<const float2*>(wq + 2 * j);
+        const float2 v = f2b(fmaf(ab.x, sj, ab.y * cj));
+        const float2 qv = f2b(fmaf(ab.x, cj, -(ab.y * sj)));
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            EP[q] = f2fma(v, Wa.nco[j][q], EP[q]);
+            OP[q] = f2fma(qv, Wa.nsi[j][q], OP[q]);
+        }
+        const float sn = fmaf(sj, cc, cj * sc);
+        cj = fmaf(cj, cc, -(sj * sc));
+        sj = sn;
+    }
+}
+
+// dU/4 at the lane's 2H nodes from the even and odd parts: pair (p, i), k = p CS + i:
+// node k of the lane's first half is theta_c - d_{H-1-k}, node H + k of its second half
+// theta_c + d_k
+template <int CS, int P>
+__device__ __forceinline__ void wnoise_finish(const float2 (&EP)[P * CS / 2], const float2 (&OP)[P * CS / 2],
+                                              float2 (&nq)[P][CS]) {
+    constexpr int H = P * CS, Q = H / 2;
 #pragma unroll
     for (int p = 0; p < P; ++p)
 #pragma unroll
@@ -293,6 +265,14 @@ __device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& W
                 nq[p][i] = make_float2(EP[q].y - OP[q].y, EP[q].x + OP[q].x);
             }
         }
+}
+
+template <int CS, int P>
+__device__ __forceinline__ void wnoise(const ModelArgs<float>& A, const WArgs& Wa, const float* wq, float sc,
+                                       float cc, float2 (&nq)[P][CS]) {
+    float2 EP[P * CS / 2], OP[P * CS / 2];
+    wnoise_tab<CS, P>(A, Wa, wq, sc, cc, EP, OP);
+    wnoise_finish<CS, P>(EP, OP, nq);
 }
 
 // One implicit-midpoint step of this warp's particle: (m, u) in/out, W0 holding the
