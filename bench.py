@@ -93,6 +93,9 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     "89f00e16f90e5da10455045dc964eaeb5a808c25": 4606208,
     # the same kernel code with the warm-start pointer in the jitter arguments: 4.606976 MB read
     "a427e129ded961349af95ad6c01aef863a98e170": 4606976,
+    # the same kernel code with the noise sums split into the table and finishing steps (the
+    # warp-group kernels' polynomial form beside them): 4.607488 MB read, 0 written
+    "c896a3cbb09194ec47c129fb655b2a831423f7b2": 4607488,
 }, "cfg5_f32": {
     # gjitter_kernel<8,2,4,1>, profiles/gjitter_kernel_cfg5_n4096_N8192.md: 148.514304 MB read,
     # 226.438400 MB written
@@ -111,6 +114,9 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # with the lane-centred noise summed through host-fitted polynomials of the node offsets:
     # 2.718679552 GB read, 12.011711744 GB written
     "ec426efb5be03e8d31ac2ad15955f84c151614a3": 14730391296,
+    # the same, with the coefficients in the warp-group arguments: 2.737210880 GB read,
+    # 12.007459072 GB written
+    "2232e9971dc678b5866299aa75c91b0b7672ad08": 14744669952,
 }}
 
 
