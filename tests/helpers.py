@@ -25,6 +25,29 @@ def oracle_model(cfg, **over):
     return Model(L=cfg.L, n=cfg.n, alpha=cfg.alpha, mu=cfg.mu, dt=cfg.dt, amps=mode_amplitudes(cfg), **kw)
 
 
+def noise_poly_expected(n, H, K2, WNP=4):
+    """Whether the warp-group kernels sum the mode noise of a lane with 2H nodes through
+    polynomials (sch_noise_form), re-derived with numpy: per harmonic j, the Chebyshev
+    interpolants in s = tau^2 of cos(x sqrt s) and sin(x sqrt s) / sqrt s (x = j d_max) must
+    reproduce cos(j d) and sin(j d) at the lane's H offsets to 2^-30, and cost fewer packed
+    FMAs than the tables."""
+    Q = H // 2
+    if K2 * WNP + Q * (2 * WNP - 1) >= K2 * 2 * Q:
+        return False
+    P = np.polynomial.polynomial
+    dmax = 2 * np.pi * (H - 0.5) / n
+    sn = 0.5 * (1 + np.cos(np.pi * (np.arange(WNP) + 0.5) / WNP))
+    t = (np.arange(H) + 0.5) / (H - 0.5)
+    err = 0.0
+    for j in range(1, K2 + 1):
+        x = j * dmax
+        cc = P.polyfit(sn, np.cos(x * np.sqrt(sn)), WNP - 1)
+        cs = P.polyfit(sn, np.sin(x * np.sqrt(sn)) / np.sqrt(sn), WNP - 1)
+        err = max(err, np.abs(P.polyval(t * t, cc) - np.cos(x * t)).max(),
+                  np.abs(t * P.polyval(t * t, cs) - np.sin(x * t)).max())
+    return err <= 2.0 ** -30
+
+
 def tdev(a, dtype):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 

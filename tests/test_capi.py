@@ -5,8 +5,9 @@ import ctypes as ct
 import os
 import re
 
-import numpy as np
 import pytest
+
+from tests.helpers import noise_poly_expected
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -207,27 +208,6 @@ def test_jitter_workspace_size_and_checks(lib):
     assert lib.sch_set_jitter_workspace(None, None, 0) == -1
 
 
-def _noise_poly_expected(n, H, K2, WNP=4):
-    # the rule the host applies, re-derived with numpy: per harmonic j, Chebyshev interpolants
-    # in s = tau^2 of cos(x sqrt s) and sin(x sqrt s) / sqrt s (x = j d_max) must reproduce
-    # cos(j d) and sin(j d) at the lane's H offsets to 2^-30, and cost fewer packed FMAs
-    Q = H // 2
-    if K2 * WNP + Q * (2 * WNP - 1) >= K2 * 2 * Q:
-        return False
-    dmax = 2 * np.pi * (H - 0.5) / n
-    sn = 0.5 * (1 + np.cos(np.pi * (np.arange(WNP) + 0.5) / WNP))
-    t = (np.arange(H) + 0.5) / (H - 0.5)
-    err = 0.0
-    for j in range(1, K2 + 1):
-        x = j * dmax
-        cc = np.polynomial.polynomial.polyfit(sn, np.cos(x * np.sqrt(sn)), WNP - 1)
-        cs = np.polynomial.polynomial.polyfit(sn, np.sin(x * np.sqrt(sn)) / np.sqrt(sn), WNP - 1)
-        ec = np.polynomial.polynomial.polyval(t * t, cc)
-        es = t * np.polynomial.polynomial.polyval(t * t, cs)
-        err = max(err, np.abs(ec - np.cos(x * t)).max(), np.abs(es - np.sin(x * t)).max())
-    return err <= 2.0 ** -30
-
-
 def test_noise_form_choice(lib):
     # the lane-centred noise sums: in the warp-group layouts polynomial fits where they are
     # accurate to 2^-30 and cheaper, the tables elsewhere; the one-warp layout always takes the
@@ -239,7 +219,7 @@ def test_noise_form_choice(lib):
              (1024, 8, 2, 16, False), (1024, 10, 2, 16, True), (1024, 32, 2, 16, False),
              (4096, 4, 3, 16, False), (256, 4, 2, 4, False)]
     for n, K, layout, H, fits in cases:
-        assert fits == _noise_poly_expected(n, H, K // 2), (n, K, layout)
+        assert fits == noise_poly_expected(n, H, K // 2), (n, K, layout)
         want = 2 if (fits and layout != 2) else 1
         p = _params(n=n, M=64, K=K, dtype=SCH_F32, layout=layout, tol=1e-6)
         for j in range(K // 2):

@@ -17,7 +17,7 @@ import torch
 
 from workloads import get_config, random_drift, random_increments, random_obs, random_state, u0_profile
 from oracle import filter as OF
-from tests.helpers import gpu_model, oracle_model, rel_err, tdev
+from tests.helpers import gpu_model, noise_poly_expected, oracle_model, rel_err, tdev
 
 pytestmark = pytest.mark.gpu
 
@@ -36,6 +36,9 @@ def test_group_window_matches_oracle(n, layout, Ns, lam, mu):
     cfg = _cfg(n, mu=mu)
     g = gpu_model(cfg, layout=layout)
     assert g.layout == layout and g.group_warps == n // (128 * g.group_cs)
+    # both noise forms: the polynomials at n = 4096 (both layouts) and at n = 2048 with 16
+    # nodes a lane, the tables elsewhere
+    assert g.noise_form == ("poly" if noise_poly_expected(n, 2 * g.group_cs, cfg.K // 2) else "table")
     om = oracle_model(cfg)
     N = 3
     m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 31)])
@@ -56,13 +59,17 @@ def test_group_window_matches_oracle(n, layout, Ns, lam, mu):
 
 
 @pytest.mark.parametrize("n,layout,K", [(2048, "group", 2), (4096, "group", 64), (4096, "group16", 6),
-                                        (2048, "group16", 64), (1024, "group16", 8), (1024, "group16", 64)])
+                                        (2048, "group16", 64), (1024, "group16", 8), (1024, "group16", 64),
+                                        (4096, "group", 42)])
 def test_group_noise_extremes_match_oracle(n, layout, K):
     # the lane-centred noise synthesis with one harmonic, an odd harmonic count and the largest
-    # K (32 harmonics, the whole table), in both warp-group layouts
+    # K (32 harmonics, the whole table), in both warp-group layouts; and the polynomial form at
+    # the most harmonics it takes (21 at n = 4096: fit error 2^-30.3)
     cfg = _cfg(n, K=K)
     g = gpu_model(cfg, layout=layout)
     assert g.layout == layout
+    assert g.noise_form == ("poly" if (n, K) == (4096, 42) else "table")
+    assert (g.noise_form == "poly") == noise_poly_expected(n, 2 * g.group_cs, K // 2)
     om = oracle_model(cfg)
     N, Ns = 2, 3
     m0 = np.stack([om.m_from_u(u) for u in random_state(cfg, N, 41)])
