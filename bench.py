@@ -521,7 +521,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * dev_s_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": cfg.dtype, "data": "synthetic",
-            "config": {**workload_config(cfg, ws), "layout": g.layout,
+            "config": {**workload_config(cfg, ws), "layout": g.layout, "noise_form": g.noise_form,
                        "jitter_picard_start": ("the previous proposal's per-step states" if f.warm_jitter
                                                else "each step's start state"),
                        "l2": "flushed between timed steps (256 MB write)",
