@@ -96,6 +96,8 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # the same kernel code with the noise sums split into the table and finishing steps (the
     # warp-group kernels' polynomial form beside them): 4.607488 MB read, 0 written
     "c896a3cbb09194ec47c129fb655b2a831423f7b2": 4607488,
+    # the same sources with one comment corrected (no code change): the capture above
+    "0128ccf827d69e0960f91b1175216b6f6335b443": 4607488,
 }, "cfg5_f32": {
     # gjitter_kernel<8,2,4,1>, profiles/gjitter_kernel_cfg5_n4096_N8192.md: 148.514304 MB read,
     # 226.438400 MB written
@@ -117,6 +119,8 @@ JITTER_TRAFFIC_BYTES = {"cfg2_f32": {
     # the same, with the coefficients in the warp-group arguments: 2.737210880 GB read,
     # 12.007459072 GB written
     "2232e9971dc678b5866299aa75c91b0b7672ad08": 14744669952,
+    # the same sources with one comment corrected (no code change): the capture above
+    "e4040ce2ae15928553e68f8ca69e7f19b0e8e742": 14744669952,
 }}
 
 

@@ -154,7 +154,7 @@ struct GTab {
 
 struct GArgs {
     GTab pic, hel;          // the cross-warp solves of M + mu dt/2 K and (6/h)(M + alpha^2 K)
-    // the polynomial form of the lane-centred noise (wnoise_poly in sch_group.cuh):
+    // the polynomial form of the lane-centred noise (gnoise in sch_group.cuh):
     // npc[j-1][k] = (c_k, s_k) with cos(j d) ~ sum_k c_k s^k and sin(j d) ~ tau sum_k s_k s^k,
     // k < WNP.  npoly = 1 when those fits hold to 2^-30 at every offset and cost the lane
     // fewer operations than the tables of WArgs; otherwise the tables are used
