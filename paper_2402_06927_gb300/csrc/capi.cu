@@ -323,7 +323,7 @@ void wtab_cast(const HTab& s, const RTab<double>& q, int CS, WTab& d) {
 
 bool invert_dense(int n, double* a, double* inv);
 
-// The polynomial form of the lane-centred noise (WArgs npc, npoly): for harmonic j <= K/2
+// The polynomial form of the lane-centred noise (GArgs npc, npoly): for harmonic j <= K/2
 // and x = j d_{H-1}, the polynomials in s of degree WNP - 1 that interpolate cos(x sqrt s)
 // and sin(x sqrt s) / sqrt s at the WNP Chebyshev points of [0, 1].  npoly = 1 when they
 // reproduce cos(j d_m) and sin(j d_m) to 2^-30 at every offset d_m = tau_m d_{H-1}, m < H
